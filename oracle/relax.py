@@ -1,0 +1,103 @@
+"""Subvolume relaxation (oracle; test infrastructure only).
+
+Sec. II: the trial coefficients are improved by minimising, in each subvolume U,
+the residual norm N with the coefficients outside U held fixed; relaxations of
+subvolumes that do not interact are independent and may run in parallel.
+
+Local problem (reading of Sec. II, the norm argument; the paper's own square
+Dirichlet form is noted there to be non-monotone): with G = M^dagger W M the
+Hermitian positive-definite normal matrix and g = M^dagger W f,
+    delta_U = argmin N(c + E_U delta) = G_UU^{-1} (g - G c)_U,
+i.e. exact block Gauss-Seidel on G c = g, which never increases N.
+
+Colouring: G couples points up to two stencil radii apart, so the 2^d classes
+"block index parity per axis" make same-colour subvolumes non-interacting
+(G_UV = 0) whenever every subvolume spans at least two points per axis.  The
+same-colour updates are therefore computed from one residual and applied
+together, which equals applying them one after another.
+"""
+from __future__ import annotations
+
+import itertools
+
+import numpy as np
+import scipy.linalg as sla
+
+
+def block_counts(shape, sub):
+    """Subvolumes per numpy axis; the last block on an axis may be short (ragged tail)."""
+    return tuple(-(-shape[a] // sub[a]) for a in range(len(shape)))
+
+
+def subvolumes(shape, sub):
+    """List of (colour, point indices) in block-lexicographic order (numpy axis order).
+
+    ``sub`` is given per numpy axis (slowest first).  The colour is
+    sum over axes of (block index mod 2) << axis_id with x = axis_id 0.
+    """
+    d = len(shape)
+    nb = block_counts(shape, sub)
+    strides = [int(np.prod(shape[a + 1:])) for a in range(d)]
+    out = []
+    for bidx in itertools.product(*[range(n) for n in nb]):
+        ranges = [range(bidx[a] * sub[a], min((bidx[a] + 1) * sub[a], shape[a])) for a in range(d)]
+        pts = []
+        for coord in itertools.product(*ranges):
+            pts.append(sum(coord[a] * strides[a] for a in range(d)))
+        colour = 0
+        for a in range(d):
+            axis_id = d - 1 - a          # numpy axis a is x (0) when a == d-1
+            colour |= (bidx[a] & 1) << axis_id
+        out.append((colour, np.array(sorted(pts), dtype=np.int64)))
+    return out
+
+
+def unknown_indices(points: np.ndarray, K: int) -> np.ndarray:
+    return (points[:, None] * K + np.arange(K)[None, :]).ravel()
+
+
+class BlockRelaxation:
+    """Exact coloured block Gauss-Seidel on a Hermitian positive-definite level operator G."""
+
+    def __init__(self, G, shape, sub, K):
+        self.G = G.tocsr()
+        self.K = K
+        self.ncolours = 1 << len(shape)
+        self.blocks = []
+        for colour, pts in subvolumes(shape, sub):
+            idx = unknown_indices(pts, K)
+            Guu = self.G[idx][:, idx].toarray()
+            self.blocks.append((colour, idx, sla.cho_factor(Guu, lower=True)))
+
+    def colour_pass(self, x, g, colour):
+        s = g - self.G @ x
+        updates = []
+        for col, idx, fac in self.blocks:
+            if col == colour:
+                updates.append((idx, sla.cho_solve(fac, s[idx])))
+        for idx, d in updates:
+            x[idx] += d
+
+    def sweep(self, x, g, after_colour=None):
+        """One sweep = one pass over every colour in order 0 .. 2^d - 1."""
+        for colour in range(self.ncolours):
+            self.colour_pass(x, g, colour)
+            if after_colour is not None:
+                after_colour(colour)
+
+
+def colouring_is_valid(G, shape, sub, K) -> bool:
+    """True when no two distinct same-colour subvolumes are coupled by G (pin for the colouring)."""
+    G = G.tocsr()
+    blocks = subvolumes(shape, sub)
+    owner = np.full(G.shape[0], -1, dtype=np.int64)
+    colour_of = []
+    for b, (colour, pts) in enumerate(blocks):
+        owner[unknown_indices(pts, K)] = b
+        colour_of.append(colour)
+    coo = G.tocoo()
+    nz = np.abs(coo.data) > 0
+    bi, bj = owner[coo.row[nz]], owner[coo.col[nz]]
+    cross = bi != bj
+    same = np.array(colour_of)[bi[cross]] == np.array(colour_of)[bj[cross]]
+    return not bool(np.any(same))

@@ -1,0 +1,199 @@
+"""Pins for the oracle's subvolume relaxation and multigrid (Secs. II, III, IV transfers)."""
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+from oracle import legendre_elements as le
+from oracle import multigrid, propagate, relax, system
+from paper_1111_4363_gb300 import workloads as wl
+
+
+def small_2d(n=16, levels=2, weight="dual"):
+    w = wl.softcore_2d(n=n, levels=levels)
+    w.weight = weight
+    prob = system.Problem.from_workload(w)
+    psi0 = wl.initial_state(w).ravel()
+    M, f, W = system.assemble(prob, 0.35, psi0, weight)
+    return w, prob, M, f, W
+
+
+def test_subvolume_partition_and_colours():
+    shape, sub = (10, 12), (4, 4)       # ragged tail on the slow axis
+    blocks = relax.subvolumes(shape, sub)
+    pts = np.concatenate([p for _, p in blocks])
+    assert sorted(pts.tolist()) == list(range(120))
+    assert len(blocks) == 3 * 3
+    assert sorted(set(c for c, _ in blocks)) == [0, 1, 2, 3]
+
+
+@pytest.mark.parametrize("weight", ["dual", "literal", "identity"])
+def test_colouring_valid_every_level(weight):
+    w, prob, M, f, W = small_2d(n=16, levels=3, weight=weight)
+    G0 = (M.conj().T @ W @ M).tocsr()
+    h = multigrid.Hierarchy(G0, prob.shape, prob.K, (4, 4), 3)
+    for G, shape in zip(h.G, h.shapes):
+        assert relax.colouring_is_valid(G, shape, (4, 4), prob.K)
+    # sanity of the check itself: a 2-colour checkerboard is NOT valid for the normal operator
+    blocks = relax.subvolumes(prob.shape, (4, 4))
+    owner = {}
+    for b, (c, p) in enumerate(blocks):
+        by, bx = divmod(b, 4)
+        for q in p:
+            owner[int(q)] = (by + bx) % 2
+    G = G0.tocoo()
+    pt_r, pt_c = G.row // prob.K, G.col // prob.K
+    blk = {}
+    for b, (c, p) in enumerate(blocks):
+        for q in p:
+            blk[int(q)] = b
+    bad = any(blk[int(a)] != blk[int(b)] and owner[int(a)] == owner[int(b)] for a, b in zip(pt_r, pt_c))
+    assert bad
+
+
+def test_block_update_minimises_N_over_the_block():
+    w, prob, M, f, W = small_2d(n=12, levels=1)
+    G = (M.conj().T @ W @ M).tocsr()
+    g = M.conj().T @ (W @ f)
+    R = relax.BlockRelaxation(G, prob.shape, (4, 4), prob.K)
+    c = wl.random_state(M.shape[1], 2) * 0.01
+    R.colour_pass(c, g, 0)
+    r = system.residual(M, f, c)
+    grad = M.conj().T @ (W @ r)          # -dN/dc^* / 1
+    for col, idx, _ in R.blocks:
+        if col == 0:
+            assert np.max(np.abs(grad[idx])) < 1e-10 * np.max(np.abs(g))
+    # and a random perturbation inside a block never lowers N
+    N = system.action_norm(r, W)
+    rng = np.random.default_rng(0)
+    idx = R.blocks[0][1]
+    for _ in range(5):
+        d = np.zeros_like(c)
+        d[idx] = 1e-3 * (rng.standard_normal(len(idx)) + 1j * rng.standard_normal(len(idx)))
+        assert system.action_norm(system.residual(M, f, c + d), W) >= N * (1 - 1e-14)
+
+
+def test_same_colour_updates_are_independent():
+    # computing all same-colour corrections from one residual equals applying them one by one
+    w, prob, M, f, W = small_2d(n=16, levels=1)
+    G = (M.conj().T @ W @ M).tocsr()
+    g = M.conj().T @ (W @ f)
+    R = relax.BlockRelaxation(G, prob.shape, (4, 4), prob.K)
+    c0 = wl.random_state(M.shape[1], 4) * 0.01
+    a = c0.copy()
+    R.colour_pass(a, g, 1)
+    b = c0.copy()
+    import scipy.linalg as sla
+    for col, idx, fac in R.blocks:
+        if col == 1:
+            s = g - G @ b
+            b[idx] += sla.cho_solve(fac, s[idx])
+    np.testing.assert_allclose(a, b, atol=1e-13 * np.max(np.abs(a)))
+
+
+@pytest.mark.parametrize("weight", ["dual", "literal"])
+def test_action_never_increases(weight):
+    """N is non-increasing after every colour pass and after every coarse-grid correction."""
+    w, prob, M, f, W = small_2d(n=16, levels=3, weight=weight)
+    hist = []
+    state = {}
+
+    def hook(colour):
+        hist.append(system.action_norm(system.residual(M, f, state["c"]), W))
+
+    G0 = (M.conj().T @ W @ M).tocsr()
+    g0 = M.conj().T @ (W @ f)
+    h = multigrid.Hierarchy(G0, prob.shape, prob.K, (4, 4), 3, 1, 1, 2)
+    c = np.zeros(M.shape[1], complex)
+    state["c"] = c
+    hist.append(system.action_norm(f, W))
+    for _ in range(4):
+        h.vcycle(0, c, g0, hook)
+    assert len(hist) > 20
+    for a, b in zip(hist[:-1], hist[1:]):
+        assert b <= a * (1 + 1e-12) + 1e-30
+    assert min(hist) >= 0
+
+
+def test_1d_relaxation_converges_to_direct_solution():
+    w = wl.harmonic_1d()
+    prob = system.Problem.from_workload(w)
+    psi0 = wl.initial_state(w).ravel()
+    M, f, W = system.assemble(prob, 0.0, psi0)
+    cd = system.direct_solve(M, f)
+    c, hist, cyc, _ = multigrid.solve_step(M, f, W, prob.shape, prob.K, (8,), 1, 1, 0, 0, tol=1e-26,
+                                           max_cycles=60)
+    assert hist[-1] <= 1e-26 * hist[0]
+    assert np.linalg.norm(c - cd) / np.linalg.norm(cd) < 1e-10
+    assert cyc < 20
+
+
+def test_2d_vcycle_converges_to_direct_solution():
+    w, prob, M, f, W = small_2d(n=32, levels=3)
+    cd = system.direct_solve(M, f)
+    c, hist, cyc, _ = multigrid.solve_step(M, f, W, prob.shape, prob.K, (4, 4), 3, 1, 1, 2, tol=1e-24,
+                                           max_cycles=40)
+    assert hist[-1] <= 1e-24 * hist[0]
+    assert np.linalg.norm(c - cd) / np.linalg.norm(cd) < 1e-9
+    assert cyc <= 15
+
+
+def test_coarse_correction_is_galerkin_optimal():
+    """With an exact coarse solve, c + I e_c minimises N over the coarse space (Eq. correction_fine)."""
+    w, prob, M, f, W = small_2d(n=16, levels=2)
+    G0 = (M.conj().T @ W @ M).tocsr()
+    g0 = M.conj().T @ (W @ f)
+    I = multigrid.interpolation(tuple(n // 2 for n in prob.shape), prob.K)
+    c = wl.random_state(M.shape[1], 9) * 0.01
+    s = g0 - G0 @ c
+    Gc = (I.T @ G0 @ I).toarray()
+    np.testing.assert_allclose(Gc, Gc.conj().T, atol=1e-12 * np.max(np.abs(Gc)))
+    assert np.min(np.linalg.eigvalsh(Gc)) > 0
+    ec = np.linalg.solve(Gc, I.T @ s)
+    c2 = c + I @ ec
+    grad_coarse = I.T @ (g0 - G0 @ c2)
+    assert np.max(np.abs(grad_coarse)) < 1e-10 * np.max(np.abs(I.T @ s))
+
+
+def test_fd_interpolation_reproduces_linear_functions():
+    # cell-centred fine points x_{2J} = X_J - H/4, x_{2J+1} = X_J + H/4: 3/4, 1/4 weights are exact for
+    # linear functions away from the walls
+    nc = 9
+    I1 = multigrid.interpolation_1d(nc).toarray()
+    X = wl.axis_coordinates(nc, 2.0)
+    x = wl.axis_coordinates(2 * nc, 1.0)
+    u = 0.3 + 1.7 * X
+    v = I1 @ u
+    np.testing.assert_allclose(v[1:-1], 0.3 + 1.7 * x[1:-1], atol=1e-14)
+    # 2D tensor product keeps the time index untouched
+    I2 = multigrid.interpolation((3, 4), 2)
+    assert I2.shape == (6 * 8 * 2, 3 * 4 * 2)
+
+
+@pytest.mark.parametrize("nmax", [1, 2, 3, 5])
+def test_legendre_element_transfers(nmax):
+    """Sec. IV: (P^(L) + P^(R)) (I^(L) + I^(R)) = identity on the parent basis; E reproduces parent
+    functions exactly on each child; O_parent = (1/2) E^T O_f E from the change of variables."""
+    E = le.interpolation(nmax)
+    P = le.projection(nmax)
+    np.testing.assert_allclose(P @ E, np.eye(nmax + 1), atol=1e-13)
+    O = le.overlap(nmax)
+    np.testing.assert_allclose(O, np.diag([2.0 / (2 * n + 1) for n in range(nmax + 1)]), atol=1e-14)
+    Of = np.block([[O, 0 * O], [0 * O, O]])
+    np.testing.assert_allclose(0.5 * E.T @ Of @ E, O, atol=1e-13)
+    from oracle.timebasis import legendre_P
+    yp = np.linspace(-1, 1, 11)
+    a = np.random.default_rng(nmax).standard_normal(nmax + 1)
+    parent_left = a @ legendre_P(nmax, 0.5 * (yp - 1))
+    child_left = (E[: nmax + 1] @ a) @ legendre_P(nmax, yp)
+    np.testing.assert_allclose(child_left, parent_left, atol=1e-13)
+
+
+def test_legendre_kinetic_matrix_closed_form():
+    """Eq. Tmatelt: for i > j with i - j even the paper prints (-i(i+1) + j(j+1))/(2m), and 0 for i - j odd.
+    The quadrature of the first line, -P_i P_j' |_{-1}^{1} + int P_i' P_j', reproduces it with the boundary
+    term's indices exchanged (i.e. the printed value is T[j, i]); the reading is recorded with the others."""
+    T = le.kinetic(7)
+    for i in range(8):
+        for j in range(i):
+            expected = (-i * (i + 1) + j * (j + 1)) / 2.0 if (i - j) % 2 == 0 else 0.0
+            assert T[j, i] == pytest.approx(expected, abs=1e-12)
