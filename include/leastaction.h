@@ -1,0 +1,144 @@
+/*
+ * leastaction.h -- C ABI of the GB300 least-action propagator.
+ *
+ * The library propagates psi(x, t) under H = T + V0(x) + E(t) x_axis by the
+ * least-action principle (Walters, "An efficient parallel method for relaxing to
+ * the minimum action wavefunction", Sec. I): in each time step [t0, t0+dt]
+ *     phi(x, t) = sum_{p,n} C_pn chi_p(x) P_n(tau),  tau = 2 (t - t0)/dt - 1,
+ * with Legendre time functions P_0..P_K, the initial condition phi(t0) = psi(t0)
+ * imposed exactly (C_p0 eliminated), and the remaining K coefficients per point
+ * the solution of the stationarity condition (Eq. stationaryphase)
+ *     M c = f.
+ * M c = f is not solved directly: the coefficients are relaxed by minimising the
+ * residual norm N = r^dagger W r of the action residual r = f - M c
+ * (Eqs. actionresidual, residnorm) over small spacetime subvolumes of all K time
+ * functions of a block of grid points, non-interacting subvolumes in parallel
+ * (Sec. II), inside a multigrid V-cycle with Galerkin coarse operators
+ * (Sec. III, Eqs. residual_rough and correction_fine).
+ *
+ * Spatial basis: uniform finite-difference grid, x_k = (k - (n-1)/2) h per axis,
+ * Dirichlet walls one spacing beyond the outermost points, T = -1/2 Laplacian
+ * (second-order 3/5/7-point stencil in 1/2/3 D), mass 1.
+ *
+ * Memory layout of every complex array: interleaved double2 (re, im).
+ *   psi, V0:          point index p = (z*ny + y)*nx + x (x fastest).
+ *   coefficients c:   index p*K + (n-1), n = 1..K (point-major, time function fastest).
+ * A pointer argument may be host or device memory unless stated otherwise; the
+ * library detects which (cudaPointerGetAttributes) and copies host data through
+ * the context's stream.  Device pointers must stay valid until the call returns.
+ *
+ * Threading and streams: a context is used by one host thread at a time; all
+ * work is ordered on the CUDA stream given to la_init (0 = legacy default
+ * stream).  Calls that return numbers to the host synchronise that stream.
+ *
+ * Errors: every call returns la_status; no exception crosses the ABI; the text
+ * of the last error of a context is available from la_last_error.  After
+ * LA_ECUDA the context should be finalised.
+ */
+#ifndef LEASTACTION_H_
+#define LEASTACTION_H_
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  LA_OK = 0,
+  LA_EINVAL = 1,    /* invalid argument or configuration */
+  LA_ENOMEM = 2,    /* device allocation failed */
+  LA_ECUDA = 3,     /* CUDA runtime error */
+  LA_ENOTCONV = 4,  /* max_cycles reached before rel <= tol (the state is still advanced) */
+  LA_ESTATE = 5     /* call out of order (e.g. la_step before la_set_hamiltonian) */
+} la_status;
+
+typedef struct la_ctx la_ctx;
+
+/* Problem and relaxation configuration. */
+typedef struct {
+  int dim;              /* 1, 2 or 3 */
+  int n[3];             /* grid points per axis (x, y, z); unused axes must be 1 */
+  double h[3];          /* grid spacing per axis */
+  int nt;               /* K: free Legendre time functions per point, 1..8 */
+  double dt;            /* time step */
+  int sub[3];           /* subvolume extent in points per axis (>= 2 on used axes); the last
+                           subvolume on an axis may be shorter (ragged tail) */
+  int levels;           /* multigrid levels, >= 1; every level but the coarsest must have an even
+                           number of points per used axis */
+  int nu1, nu2;         /* pre/post sweeps per level in a V(nu1, nu2) cycle; one level: nu1+nu2 sweeps */
+  int coarse_sweeps;    /* sweeps on the coarsest level (levels > 1) */
+  int max_cycles;       /* cycles per time step, >= 1 */
+  double tol;           /* stop when N(c)/N(0) <= tol; tol <= 0 runs exactly max_cycles */
+  int weight;           /* residual-norm weight W: 0 = (O x U)^{-1} (default), 1 = O x U, 2 = identity */
+  int precision;        /* 0 = FP64 throughout; 1 = mixed: complex64 factors and V-cycle, FP64
+                           residual, action and refinement update */
+  int laser_axis;       /* axis of the dipole coupling E(t) x_axis */
+} la_config;
+
+/* Laser field E(t) = sum_k amp[k] * env_k(t) * sin(omega[k] t), env_k = exp(-((t - t_center[k])/sigma[k])^2)
+   for sigma[k] > 0, else 1.  Host arrays of length ncomp; ncomp = 0 means no field. */
+typedef struct {
+  int ncomp;
+  const double* amp;
+  const double* omega;
+  const double* t_center;
+  const double* sigma;
+} la_pulse;
+
+typedef struct {
+  int cycles;           /* V-cycles run in the step */
+  int fine_sweeps;      /* fine-level sweeps (every colour once) run in the step */
+  double action;        /* N of the final iterate */
+  double rel_action;    /* N / N(0) */
+} la_step_stats;
+
+/* Allocate a context for one grid and configuration; validates the configuration.
+   cuda_stream: a cudaStream_t (0 = default stream).  Errors: LA_EINVAL, LA_ENOMEM, LA_ECUDA. */
+la_status la_init(const la_config* cfg, void* cuda_stream, la_ctx** out);
+
+/* Static potential V0 (real, one double per grid point, host or device) and the laser pulse
+   (host struct and arrays, copied).  Builds the Galerkin coarse operators of every level
+   (Sec. III, P A P^T) for the static part; the per-step time-matrix factors are combined later.
+   Errors: LA_EINVAL (null V0, ncomp < 0), LA_ECUDA. */
+la_status la_set_hamiltonian(la_ctx* ctx, const double* V0, const la_pulse* pulse);
+
+/* Propagate psi (complex128[Np], host or device, in: psi(t0), out: psi(t0 + nsteps dt)) by nsteps
+   least-action steps starting at time t0.  per_step (host, nullable) receives nsteps records.
+   Each step: time matrices (Sec. IV Legendre overlaps, Gauss-Legendre quadrature of E(t)), subvolume
+   factorisation on every level, V-cycles until N/N(0) <= tol, then psi(t0+dt) = phi(tau = 1).
+   Returns LA_ENOTCONV if some step hit max_cycles (psi is still advanced). */
+la_status la_step(la_ctx* ctx, void* psi, int nsteps, double t0, la_step_stats* per_step);
+
+/* N and N/N(0) (Eq. residnorm) of the final iterate of the last time step; synchronises. */
+la_status la_action(la_ctx* ctx, double* action, double* rel_action);
+
+/* One step's coefficients without advancing: relax M c = f for initial state psi0 (complex128[Np])
+   at time t0 and write c (complex128[Np*K]).  ncycles > 0 runs exactly that many cycles;
+   ncycles == 0 runs until tol or max_cycles.  Used to compare iterates with a reference. */
+la_status la_solve_step(la_ctx* ctx, const void* psi0, double t0, int ncycles, void* c_out,
+                        la_step_stats* stats);
+
+/* Action residual r = f - M c (Eq. actionresidual, complex128[Np*K]) of trial coefficients c for
+   initial state psi0 at time t0, and its norm N = r^dagger W r.  r_out may be null. */
+la_status la_residual(la_ctx* ctx, const void* psi0, double t0, const void* c, void* r_out,
+                      double* action);
+
+/* One relaxation pass of a single colour on the finest level (Sec. II): every subvolume of
+   that colour is replaced by the minimiser of N over its coefficients, the others fixed.
+   c (complex128[Np*K]) is read and overwritten.  colour in [0, 2^dim). */
+la_status la_relax_colour(la_ctx* ctx, const void* psi0, double t0, int colour, void* c);
+
+/* Per-step time matrices at t0 (row-major K x K unless noted), for inspection:
+   out[0..K*K)    U_b  = (dt/2) int b_m b_n            out[K*K..2K*K)  Q_b = int b_m b_n'
+   out[2K*K..3K*K) E_b  = (dt/2) int b_m b_n E(t)      out[3K*K..3K*K+K) U_b0 = (dt/2) int b_m P_0
+   out[3K*K+K..3K*K+2K) E_b0                              out[.. +K*K) W_t (time part of W)
+   with b_n = P_n - (-1)^n P_0.  out is a host array of 4*K*K + 2*K doubles. */
+la_status la_time_matrices(la_ctx* ctx, double t0, double* out);
+
+la_status la_finalize(la_ctx* ctx);
+const char* la_last_error(const la_ctx* ctx);
+const char* la_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LEASTACTION_H_ */

@@ -1,0 +1,208 @@
+"""ctypes binding of the C ABI in include/leastaction.h (argument marshalling only).
+
+Every numerical step runs in the CUDA library; this module converts Python/torch/numpy
+arguments to pointers and sizes and raises ``LeastActionError`` on a non-zero status.
+Loading fails loudly when the library is missing: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libleastaction.so")
+
+LA_OK, LA_EINVAL, LA_ENOMEM, LA_ECUDA, LA_ENOTCONV, LA_ESTATE = range(6)
+STATUS_NAMES = {0: "LA_OK", 1: "LA_EINVAL", 2: "LA_ENOMEM", 3: "LA_ECUDA", 4: "LA_ENOTCONV", 5: "LA_ESTATE"}
+WEIGHTS = {"dual": 0, "literal": 1, "identity": 2}
+
+EXPORTS = ["la_init", "la_set_hamiltonian", "la_step", "la_action", "la_solve_step", "la_residual",
+           "la_relax_colour", "la_time_matrices", "la_finalize", "la_last_error", "la_version"]
+
+
+class LeastActionError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {message}")
+        self.status = status
+
+
+class la_config(C.Structure):
+    _fields_ = [("dim", C.c_int), ("n", C.c_int * 3), ("h", C.c_double * 3), ("nt", C.c_int), ("dt", C.c_double),
+                ("sub", C.c_int * 3), ("levels", C.c_int), ("nu1", C.c_int), ("nu2", C.c_int),
+                ("coarse_sweeps", C.c_int), ("max_cycles", C.c_int), ("tol", C.c_double), ("weight", C.c_int),
+                ("precision", C.c_int), ("laser_axis", C.c_int)]
+
+
+class la_pulse(C.Structure):
+    _fields_ = [("ncomp", C.c_int), ("amp", C.POINTER(C.c_double)), ("omega", C.POINTER(C.c_double)),
+                ("t_center", C.POINTER(C.c_double)), ("sigma", C.POINTER(C.c_double))]
+
+
+class la_step_stats(C.Structure):
+    _fields_ = [("cycles", C.c_int), ("fine_sweeps", C.c_int), ("action", C.c_double), ("rel_action", C.c_double)]
+
+
+_lib = None
+
+
+def lib() -> C.CDLL:
+    """Load the CUDA library (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"CUDA library not built: {LIB_PATH} (run __graft_entry__.build())")
+        L = C.CDLL(LIB_PATH)
+        vp, i, d = C.c_void_p, C.c_int, C.c_double
+        L.la_init.argtypes = [C.POINTER(la_config), vp, C.POINTER(vp)]
+        L.la_set_hamiltonian.argtypes = [vp, vp, C.POINTER(la_pulse)]
+        L.la_step.argtypes = [vp, vp, i, d, C.POINTER(la_step_stats)]
+        L.la_action.argtypes = [vp, C.POINTER(d), C.POINTER(d)]
+        L.la_solve_step.argtypes = [vp, vp, d, i, vp, C.POINTER(la_step_stats)]
+        L.la_residual.argtypes = [vp, vp, d, vp, vp, C.POINTER(d)]
+        L.la_relax_colour.argtypes = [vp, vp, d, i, vp]
+        L.la_time_matrices.argtypes = [vp, d, C.POINTER(d)]
+        L.la_finalize.argtypes = [vp]
+        L.la_last_error.argtypes = [vp]
+        L.la_last_error.restype = C.c_char_p
+        L.la_version.restype = C.c_char_p
+        for name in EXPORTS:
+            if name not in ("la_last_error", "la_version"):
+                getattr(L, name).restype = C.c_int
+        _lib = L
+    return _lib
+
+
+def _ptr(x):
+    """Data pointer of a torch tensor or numpy array (must be contiguous)."""
+    if x is None:
+        return None
+    if hasattr(x, "data_ptr"):
+        if not x.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return C.c_void_p(x.data_ptr())
+    if isinstance(x, np.ndarray):
+        if not x.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be C-contiguous")
+        return C.c_void_p(x.ctypes.data)
+    raise TypeError(f"unsupported buffer type {type(x)}")
+
+
+def _stream_handle(stream):
+    if stream is None:
+        try:
+            import torch
+            if torch.cuda.is_available():
+                return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+        except Exception:
+            pass
+        return C.c_void_p(0)
+    if hasattr(stream, "cuda_stream"):
+        return C.c_void_p(stream.cuda_stream)
+    return C.c_void_p(int(stream))
+
+
+def config_from_workload(w, precision: int = 0, **overrides) -> la_config:
+    cfg = la_config()
+    cfg.dim = w.dim
+    for a in range(3):
+        cfg.n[a] = w.n[a] if a < w.dim else 1
+        cfg.h[a] = w.h[a]
+        cfg.sub[a] = w.sub[a] if a < w.dim else 1
+    cfg.nt, cfg.dt = w.nt, w.dt
+    cfg.levels, cfg.nu1, cfg.nu2 = w.levels, w.nu1, w.nu2
+    cfg.coarse_sweeps, cfg.max_cycles, cfg.tol = max(w.coarse_sweeps, 1), w.max_cycles, w.tol
+    cfg.weight = WEIGHTS[w.weight]
+    cfg.precision = precision
+    cfg.laser_axis = w.pulse.axis if w.pulse is not None else 0
+    for k, v in overrides.items():
+        setattr(cfg, k, v)
+    return cfg
+
+
+class Context:
+    """One least-action propagator context (la_init ... la_finalize)."""
+
+    def __init__(self, cfg: la_config, stream=None):
+        self._lib = lib()
+        self.cfg = cfg
+        h = C.c_void_p()
+        st = self._lib.la_init(C.byref(cfg), _stream_handle(stream), C.byref(h))
+        if st != LA_OK:
+            raise LeastActionError(st, self._lib.la_last_error(None).decode())
+        self.handle = h
+        self.K = cfg.nt
+        self.npoints = int(np.prod([cfg.n[a] for a in range(cfg.dim)]))
+        self._keep = []
+
+    def _check(self, st, allow=()):
+        if st != LA_OK and st not in allow:
+            raise LeastActionError(st, self._lib.la_last_error(self.handle).decode())
+        return st
+
+    def set_hamiltonian(self, V0, pulse=None):
+        arrs = []
+        p = la_pulse()
+        if pulse is not None and pulse.ncomp > 0:
+            for name, src in (("amp", pulse.amp), ("omega", pulse.omega), ("t_center", pulse.t_center),
+                              ("sigma", pulse.sigma)):
+                a = np.ascontiguousarray(np.asarray(src, dtype=np.float64))
+                arrs.append(a)
+                setattr(p, name, a.ctypes.data_as(C.POINTER(C.c_double)))
+            p.ncomp = pulse.ncomp
+        self._keep = arrs
+        return self._check(self._lib.la_set_hamiltonian(self.handle, _ptr(V0), C.byref(p)))
+
+    def step(self, psi, nsteps: int, t0: float = 0.0, stats: bool = False, allow_notconv: bool = False):
+        rec = (la_step_stats * max(nsteps, 1))()
+        st = self._check(self._lib.la_step(self.handle, _ptr(psi), int(nsteps), float(t0), rec),
+                         allow=(LA_ENOTCONV,) if allow_notconv else ())
+        if stats:
+            return st, [(r.cycles, r.fine_sweeps, r.action, r.rel_action) for r in rec[:nsteps]]
+        return st
+
+    def action(self):
+        N, rel = C.c_double(), C.c_double()
+        self._check(self._lib.la_action(self.handle, C.byref(N), C.byref(rel)))
+        return N.value, rel.value
+
+    def solve_step(self, psi0, t0: float, c_out, ncycles: int = 0):
+        rec = la_step_stats()
+        st = self._check(self._lib.la_solve_step(self.handle, _ptr(psi0), float(t0), int(ncycles), _ptr(c_out),
+                                                 C.byref(rec)), allow=(LA_ENOTCONV,))
+        return st, (rec.cycles, rec.fine_sweeps, rec.action, rec.rel_action)
+
+    def residual(self, psi0, t0: float, c, r_out=None) -> float:
+        N = C.c_double()
+        self._check(self._lib.la_residual(self.handle, _ptr(psi0), float(t0), _ptr(c), _ptr(r_out), C.byref(N)))
+        return N.value
+
+    def relax_colour(self, psi0, t0: float, colour: int, c):
+        return self._check(self._lib.la_relax_colour(self.handle, _ptr(psi0), float(t0), int(colour), _ptr(c)))
+
+    def time_matrices(self, t0: float):
+        K = self.K
+        out = np.zeros(4 * K * K + 2 * K)
+        self._check(self._lib.la_time_matrices(self.handle, float(t0), out.ctypes.data_as(C.POINTER(C.c_double))))
+        KK = K * K
+        return {"Ub": out[:KK].reshape(K, K), "Qb": out[KK:2 * KK].reshape(K, K),
+                "Eb": out[2 * KK:3 * KK].reshape(K, K), "Ub0": out[3 * KK:3 * KK + K],
+                "Eb0": out[3 * KK + K:3 * KK + 2 * K], "Wt": out[3 * KK + 2 * K:].reshape(K, K)}
+
+    def close(self):
+        if getattr(self, "handle", None):
+            self._lib.la_finalize(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()

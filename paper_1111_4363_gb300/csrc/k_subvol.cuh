@@ -1,0 +1,651 @@
+// Subvolume relaxation kernels (Sec. II), templated on the arithmetic type R (double or float).
+//
+// A subvolume U is a block of grid points with all K time functions: n = |U| K unknowns,
+// padded to NPAD (multiple of 16) with identity rows.  Its local least-squares problem
+// (minimise the residual norm N over c_U, everything else fixed) has the Hermitian
+// positive-definite matrix G_UU = sum_kk' Sigma_kk'[U, U] (x) Theta_kk' and right-hand side
+// (M~^dagger Wt r)_U (finest level) or (g - G e)_U (Galerkin levels).
+//
+// Factor store of one subvolume: lower Cholesky factor L of G_UU in 16 x 16 blocks, block rows
+// I = 0..NB-1 and block columns J <= I in the order (0,0), (1,0), (1,1), (2,0), ...; block
+// (I, I) holds inv(L_II) instead of L_II so that every triangular-solve step is a mat-vec.
+#pragma once
+#include "la_internal.cuh"
+
+namespace la {
+
+template <typename CT> struct Re;
+template <> struct Re<double2> { typedef double T; };
+template <> struct Re<float2> { typedef float T; };
+
+template <typename CT> __device__ __forceinline__ CT mkc(typename Re<CT>::T a, typename Re<CT>::T b) {
+  CT r; r.x = a; r.y = b; return r;
+}
+// acc += a * b
+template <typename CT> __device__ __forceinline__ void cfma(CT& acc, const CT a, const CT b) {
+  acc.x = fma(a.x, b.x, acc.x); acc.x = fma(-a.y, b.y, acc.x);
+  acc.y = fma(a.x, b.y, acc.y); acc.y = fma(a.y, b.x, acc.y);
+}
+// acc += conj(a) * b
+template <typename CT> __device__ __forceinline__ void cfma_conj(CT& acc, const CT a, const CT b) {
+  acc.x = fma(a.x, b.x, acc.x); acc.x = fma(a.y, b.y, acc.x);
+  acc.y = fma(a.x, b.y, acc.y); acc.y = fma(-a.y, b.x, acc.y);
+}
+template <typename CT> __device__ __forceinline__ CT shfl_xor_c(CT v, int m) {
+  v.x = __shfl_xor_sync(0xffffffffu, v.x, m);
+  v.y = __shfl_xor_sync(0xffffffffu, v.y, m);
+  return v;
+}
+
+constexpr int kFactorThreads = 256;
+constexpr int kSweepThreads = 128;
+
+__device__ __forceinline__ void local_coords(int i, const int e[3], int& x, int& y, int& z) {
+  x = i % e[0];
+  int r = i / e[0];
+  y = r % e[1];
+  z = r / e[1];
+}
+
+// ======================================================================== factorisation
+// One CTA per subvolume of a level.  Each thread owns E fixed entries of the lower triangle
+// (entries ordered by descending column, so every trailing triangle is spread evenly over the
+// threads) and keeps them in registers through a right-looking Cholesky; per column only the
+// scaled column is exchanged through shared memory.
+template <typename R, int NPAD>
+__global__ void __launch_bounds__(kFactorThreads)
+k_factor(LevelGeom L, FineOp g, int is_fine, int nptsmax, const double* __restrict__ sigma,
+         const TimeMats* __restrict__ tm, typename C2<R>::T* __restrict__ factors, int* __restrict__ status) {
+  typedef typename C2<R>::T CT;
+  constexpr int NTRI = NPAD * (NPAD + 1) / 2;
+  constexpr int E = (NTRI + kFactorThreads - 1) / kFactorThreads;
+  constexpr int NB = NPAD / LA_BLK;
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int K = tm->K, KK = K * K;
+  double* sP = reinterpret_cast<double*>(smem);                      // [9][K*K]
+  double* sSig = sP + LA_NPAIR * LA_KMAX * LA_KMAX;                  // [npts*npts][9]
+  CT* sCol = reinterpret_cast<CT*>(sSig + (((size_t)nptsmax * nptsmax * LA_NPAIR + 1) & ~(size_t)1));  // [NPAD]
+  CT* sDiag = sCol + NPAD;                                           // [NB][256]
+  R* sInvd = reinterpret_cast<R*>(sDiag + NB * LA_BLK * LA_BLK);
+
+  const int tid = threadIdx.x;
+  const int b = blockIdx.x;
+  int o[3], e[3];
+  subvol_box(L, b, o, e);
+  const int npts = e[0] * e[1] * e[2];
+  const int n = npts * K;
+
+  for (int i = tid; i < LA_NPAIR * KK; i += kFactorThreads) sP[i] = tm->P[i / KK][i % KK];
+  for (int i = tid; i < NB * LA_BLK * LA_BLK; i += kFactorThreads) sDiag[i] = mkc<CT>(0, 0);
+  const int nbox = box5_count(L.dim);
+  for (int t = tid; t < npts * npts; t += kFactorThreads) {
+    const int i = t / npts, j = t % npts;
+    int ix, iy, iz, jx, jy, jz;
+    local_coords(i, e, ix, iy, iz);
+    local_coords(j, e, jx, jy, jz);
+    const int px = o[0] + ix, py = o[1] + iy, pz = o[2] + iz;
+    const int qx = o[0] + jx, qy = o[1] + jy, qz = o[2] + jz;
+    double s[LA_NPAIR];
+    if (is_fine) {
+      fine_sigma(g, px, py, pz, qx, qy, qz, s);
+    } else {
+      const int dx = qx - px, dy = qy - py, dz = qz - pz;
+      if (abs(dx) <= 2 && abs(dy) <= 2 && abs(dz) <= 2) {
+        const int p = (pz * L.n[1] + py) * L.n[0] + px;
+        const int ofs = box5_index(L.dim, dx, dy, dz);
+        for (int k = 0; k < LA_NPAIR; ++k) s[k] = sigma[sigma_offset(p, k, ofs, nbox)];
+      } else {
+        for (int k = 0; k < LA_NPAIR; ++k) s[k] = 0.0;
+      }
+    }
+    for (int k = 0; k < LA_NPAIR; ++k) sSig[(size_t)t * LA_NPAIR + k] = s[k];
+  }
+  __syncthreads();
+
+  // ---- assemble owned entries: G_UU[(i,m),(j,n)] = sum_kk' Sigma_kk'[p_i, p_j] Theta_kk'[m, n]
+  CT a[E];
+  int rc[E];
+#pragma unroll
+  for (int s = 0; s < E; ++s) {
+    const int eidx = tid + s * kFactorThreads;
+    rc[s] = -1;
+    a[s] = mkc<CT>(0, 0);
+    if (eidx < NTRI) {
+      // descending column order: column c holds NPAD - c entries; m = NPAD - c
+      int m = (int)((1.0f + sqrtf(1.0f + 8.0f * (float)eidx)) * 0.5f);
+      while ((m - 1) * m / 2 > eidx) --m;
+      while (m * (m + 1) / 2 <= eidx) ++m;
+      const int c = NPAD - m;
+      const int r = c + (eidx - (m - 1) * m / 2);
+      rc[s] = r | (c << 16);
+      double re = 0.0, im = 0.0;
+      if (r >= n || c >= n) {
+        re = (r == c) ? 1.0 : 0.0;
+      } else {
+        const int i = r / K, mm = r % K, j = c / K, nn = c % K;
+        const double* sg = sSig + (size_t)(i * npts + j) * LA_NPAIR;
+#pragma unroll
+        for (int kk = 0; kk < LA_NPAIR; ++kk) {
+          const double v = sg[kk] * sP[kk * KK + mm * K + nn];
+          const int ph = theta_phase(kk);
+          if (ph == 0) re += v; else if (ph == 1) im += v; else im -= v;
+        }
+      }
+      a[s] = mkc<CT>((R)re, (R)im);
+    }
+  }
+
+  // ---- right-looking Cholesky, entries resident in registers
+  for (int j = 0; j < NPAD; ++j) {
+    const int diag = j | (j << 16);
+#pragma unroll
+    for (int s = 0; s < E; ++s) {
+      if (rc[s] == diag) {
+        R d2 = a[s].x;
+        if (!(d2 > (R)0)) {
+          atomicOr(status, 1);
+          d2 = (R)1;
+        }
+        const R d = sqrt(d2);
+        a[s] = mkc<CT>(d, (R)0);
+        sInvd[0] = (R)1 / d;
+      }
+    }
+    __syncthreads();
+    const R invd = sInvd[0];
+#pragma unroll
+    for (int s = 0; s < E; ++s) {
+      const int c = rc[s] >> 16, r = rc[s] & 0xffff;
+      if (rc[s] >= 0 && c == j && r > j) {
+        a[s].x *= invd;
+        a[s].y *= invd;
+        sCol[r] = a[s];
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int s = 0; s < E; ++s) {
+      const int c = rc[s] >> 16, r = rc[s] & 0xffff;
+      if (rc[s] >= 0 && c > j) {
+        const CT x = sCol[r], y = sCol[c];
+        // a -= x * conj(y)
+        a[s].x = fma(-x.x, y.x, a[s].x); a[s].x = fma(-x.y, y.y, a[s].x);
+        a[s].y = fma(-x.y, y.x, a[s].y); a[s].y = fma(x.x, y.y, a[s].y);
+      }
+    }
+  }
+
+  // ---- write off-diagonal blocks; diagonal blocks go through shared memory for inversion
+  CT* F = factors + (size_t)b * L.fsize;
+#pragma unroll
+  for (int s = 0; s < E; ++s) {
+    if (rc[s] < 0) continue;
+    const int c = rc[s] >> 16, r = rc[s] & 0xffff;
+    const int I = r / LA_BLK, J = c / LA_BLK;
+    if (I == J) sDiag[I * 256 + (r % LA_BLK) * LA_BLK + (c % LA_BLK)] = a[s];
+    else F[(size_t)(I * (I + 1) / 2 + J) * 256 + (r % LA_BLK) * LA_BLK + (c % LA_BLK)] = a[s];
+  }
+  __syncthreads();
+  // inv(L_II): thread (I, column jj) solves L_II x = e_jj by forward substitution
+  if (tid < NB * LA_BLK) {
+    const int I = tid / LA_BLK, jj = tid % LA_BLK;
+    const CT* Ld = sDiag + I * 256;
+    CT x[LA_BLK];
+#pragma unroll
+    for (int i = 0; i < LA_BLK; ++i) {
+      CT acc = mkc<CT>(0, 0);
+#pragma unroll
+      for (int k = 0; k < i; ++k)
+        if (k >= jj) cfma(acc, Ld[i * LA_BLK + k], x[k]);
+      const R rinv = (R)1 / Ld[i * LA_BLK + i].x;
+      if (i < jj) x[i] = mkc<CT>(0, 0);
+      else if (i == jj) x[i] = mkc<CT>(rinv, (R)0);
+      else x[i] = mkc<CT>(-acc.x * rinv, -acc.y * rinv);
+    }
+    CT* D = F + (size_t)(I * (I + 1) / 2 + I) * 256;
+#pragma unroll
+    for (int i = 0; i < LA_BLK; ++i) D[i * LA_BLK + jj] = x[i];
+  }
+}
+
+// ======================================================================== triangular solves
+// x = (L L^dagger)^{-1} rhs with the blocked factor F; 128 threads.  rhs is overwritten by x.
+template <typename CT, int NPAD>
+__device__ __forceinline__ void subvol_solve(const CT* __restrict__ F, CT* rhs, CT* y, CT* tvec, CT* red) {
+  constexpr int NB = NPAD / LA_BLK;
+  const int tid = threadIdx.x;
+  {  // forward: y_I = inv(L_II) (rhs_I - sum_{J<I} L_IJ y_J)
+    const int r = tid >> 3, l = tid & 7;
+    for (int I = 0; I < NB; ++I) {
+      const CT* rowblk = F + (size_t)(I * (I + 1) / 2) * 256;
+      CT acc = mkc<CT>(0, 0);
+      for (int J = 0; J < I; ++J) {
+        const CT* blk = rowblk + J * 256 + r * LA_BLK;
+        cfma(acc, blk[l], y[J * LA_BLK + l]);
+        cfma(acc, blk[l + 8], y[J * LA_BLK + l + 8]);
+      }
+      acc.x += __shfl_xor_sync(0xffffffffu, acc.x, 1); acc.y += __shfl_xor_sync(0xffffffffu, acc.y, 1);
+      acc.x += __shfl_xor_sync(0xffffffffu, acc.x, 2); acc.y += __shfl_xor_sync(0xffffffffu, acc.y, 2);
+      acc.x += __shfl_xor_sync(0xffffffffu, acc.x, 4); acc.y += __shfl_xor_sync(0xffffffffu, acc.y, 4);
+      if (l == 0) tvec[r] = mkc<CT>(rhs[I * LA_BLK + r].x - acc.x, rhs[I * LA_BLK + r].y - acc.y);
+      __syncthreads();
+      const CT* dblk = rowblk + I * 256 + r * LA_BLK;
+      acc = mkc<CT>(0, 0);
+      if (l <= r) cfma(acc, dblk[l], tvec[l]);
+      if (l + 8 <= r) cfma(acc, dblk[l + 8], tvec[l + 8]);
+      acc.x += __shfl_xor_sync(0xffffffffu, acc.x, 1); acc.y += __shfl_xor_sync(0xffffffffu, acc.y, 1);
+      acc.x += __shfl_xor_sync(0xffffffffu, acc.x, 2); acc.y += __shfl_xor_sync(0xffffffffu, acc.y, 2);
+      acc.x += __shfl_xor_sync(0xffffffffu, acc.x, 4); acc.y += __shfl_xor_sync(0xffffffffu, acc.y, 4);
+      if (l == 0) y[I * LA_BLK + r] = acc;
+      __syncthreads();
+    }
+  }
+  {  // backward: x_I = inv(L_II)^dagger (y_I - sum_{J>I} L_JI^dagger x_J), x stored in rhs
+    const int r = tid & 15, gq = tid >> 4;
+    for (int I = NB - 1; I >= 0; --I) {
+      CT acc = mkc<CT>(0, 0);
+      for (int J = I + 1; J < NB; ++J) {
+        const CT* blk = F + (size_t)(J * (J + 1) / 2 + I) * 256;
+        cfma_conj(acc, blk[gq * LA_BLK + r], rhs[J * LA_BLK + gq]);
+        cfma_conj(acc, blk[(gq + 8) * LA_BLK + r], rhs[J * LA_BLK + gq + 8]);
+      }
+      red[gq * LA_BLK + r] = acc;
+      __syncthreads();
+      if (tid < LA_BLK) {
+        CT s = y[I * LA_BLK + tid];
+        for (int q = 0; q < 8; ++q) { s.x -= red[q * LA_BLK + tid].x; s.y -= red[q * LA_BLK + tid].y; }
+        tvec[tid] = s;
+      }
+      __syncthreads();
+      const CT* dblk = F + (size_t)(I * (I + 1) / 2 + I) * 256;
+      acc = mkc<CT>(0, 0);
+      if (gq >= r) cfma_conj(acc, dblk[gq * LA_BLK + r], tvec[gq]);
+      if (gq + 8 >= r) cfma_conj(acc, dblk[(gq + 8) * LA_BLK + r], tvec[gq + 8]);
+      red[gq * LA_BLK + r] = acc;
+      __syncthreads();
+      if (tid < LA_BLK) {
+        CT s = mkc<CT>(0, 0);
+        for (int q = 0; q < 8; ++q) { s.x += red[q * LA_BLK + tid].x; s.y += red[q * LA_BLK + tid].y; }
+        rhs[I * LA_BLK + tid] = s;
+      }
+      __syncthreads();
+    }
+  }
+}
+
+// ======================================================================== finest-level sweep
+// Matrix-free (M-form): residual r = f - M~ c on the footprint F = U + 1 from c on U + 2,
+// z = Wt r, right-hand side (M~^dagger z)_U, solve, c_U += delta.
+template <typename R, int NPAD>
+__global__ void __launch_bounds__(kSweepThreads)
+k_sweep_fine(LevelGeom L, FineOp g, const TimeMats* __restrict__ tm, const typename C2<R>::T* __restrict__ f,
+             typename C2<R>::T* __restrict__ c, const typename C2<R>::T* __restrict__ factors, int colour) {
+  typedef typename C2<R>::T CT;
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int K = tm->K, KK = K * K;
+  const int tid = threadIdx.x;
+  const int b = colour_subvol(L, colour, blockIdx.x);
+  int o[3], e[3];
+  subvol_box(L, b, o, e);
+  int ec[3], ef[3], oc[3], of_[3];
+  for (int a = 0; a < 3; ++a) {
+    const bool used = a < L.dim;
+    ec[a] = used ? e[a] + 4 : 1;  oc[a] = used ? o[a] - 2 : o[a];
+    ef[a] = used ? e[a] + 2 : 1;  of_[a] = used ? o[a] - 1 : o[a];
+  }
+  const int nbc = ec[0] * ec[1] * ec[2], nbf = ef[0] * ef[1] * ef[2], npts = e[0] * e[1] * e[2];
+  const int sx = L.sub[0] + 4, sy = L.dim > 1 ? L.sub[1] + 4 : 1, sz = L.dim > 2 ? L.sub[2] + 4 : 1;
+  const int nbc_max = sx * sy * sz;
+
+  R* sQ = reinterpret_cast<R*>(smem);
+  R* sU = sQ + LA_KMAX * LA_KMAX;
+  R* sW = sU + LA_KMAX * LA_KMAX;
+  R* sE = sW + LA_KMAX * LA_KMAX;
+  R* sV = sE + LA_KMAX * LA_KMAX;                     // V0 on the footprint box [nbc_max]
+  CT* sC = reinterpret_cast<CT*>(sV + ((nbc_max + 3) & ~3));  // c on U+2  [nbc_max * K]
+  CT* sA = sC + (size_t)nbc_max * K;                  // Hc, then z   [nbc_max * K]
+  CT* sB = sA + (size_t)nbc_max * K;                  // r, then Hz   [nbc_max * K]
+  CT* sRhs = sB + (size_t)nbc_max * K;                // [NPAD]
+  CT* sY = sRhs + NPAD;                               // [NPAD]
+  CT* sT = sY + NPAD;                                 // [16]
+  CT* sRed = sT + LA_BLK;                             // [128]
+
+  for (int i = tid; i < KK; i += kSweepThreads) {
+    sQ[i] = (R)tm->Qb[i]; sU[i] = (R)tm->Ub[i]; sW[i] = (R)tm->Wt[i]; sE[i] = (R)tm->Eb[i];
+  }
+  for (int t = tid; t < nbc * K; t += kSweepThreads) {
+    const int i = t / K, m = t % K;
+    int lx, ly, lz;
+    local_coords(i, ec, lx, ly, lz);
+    const int gx = oc[0] + lx, gy = oc[1] + ly, gz = oc[2] + lz;
+    CT v = mkc<CT>(0, 0);
+    if (fine_in(g, gx, gy, gz)) v = c[(size_t)((gz * g.n[1] + gy) * g.n[0] + gx) * K + m];
+    sC[t] = v;
+  }
+  for (int i = tid; i < nbf; i += kSweepThreads) {
+    int lx, ly, lz;
+    local_coords(i, ef, lx, ly, lz);
+    const int gx = of_[0] + lx, gy = of_[1] + ly, gz = of_[2] + lz;
+    sV[i] = fine_in(g, gx, gy, gz) ? (R)(g.dsum + g.V0[(gz * g.n[1] + gy) * g.n[0] + gx]) : (R)0;
+  }
+  __syncthreads();
+  // c-box index of footprint point (lx, ly, lz): (lx+1, ly+1, lz+1) on used axes
+  const int dcx = 1, dcy = L.dim > 1 ? ec[0] : 0, dcz = L.dim > 2 ? ec[0] * ec[1] : 0;
+  const R wx = (R)(-0.5 * g.ih2[0]), wy = (R)(-0.5 * g.ih2[1]), wz = (R)(-0.5 * g.ih2[2]);
+  // stage 1: Hc on the footprint
+  for (int t = tid; t < nbf * K; t += kSweepThreads) {
+    const int i = t / K, m = t % K;
+    int lx, ly, lz;
+    local_coords(i, ef, lx, ly, lz);
+    const int cx = L.dim > 0 ? lx + 1 : lx, cy = L.dim > 1 ? ly + 1 : ly, cz = L.dim > 2 ? lz + 1 : lz;
+    const int ci = (cz * ec[1] + cy) * ec[0] + cx;
+    const CT v = sC[ci * K + m];
+    CT h = mkc<CT>(sV[i] * v.x, sV[i] * v.y);
+    {
+      const CT a1 = sC[(ci + dcx) * K + m], a2 = sC[(ci - dcx) * K + m];
+      h.x += wx * (a1.x + a2.x); h.y += wx * (a1.y + a2.y);
+    }
+    if (L.dim > 1) {
+      const CT a1 = sC[(ci + dcy) * K + m], a2 = sC[(ci - dcy) * K + m];
+      h.x += wy * (a1.x + a2.x); h.y += wy * (a1.y + a2.y);
+    }
+    if (L.dim > 2) {
+      const CT a1 = sC[(ci + dcz) * K + m], a2 = sC[(ci - dcz) * K + m];
+      h.x += wz * (a1.x + a2.x); h.y += wz * (a1.y + a2.y);
+    }
+    sA[t] = h;
+  }
+  __syncthreads();
+  // stage 2: r = f - (i Qb c - Ub Hc - x Eb c) on the footprint (0 outside the grid)
+  for (int t = tid; t < nbf * K; t += kSweepThreads) {
+    const int i = t / K, m = t % K;
+    int lx, ly, lz;
+    local_coords(i, ef, lx, ly, lz);
+    const int gx = of_[0] + lx, gy = of_[1] + ly, gz = of_[2] + lz;
+    CT r = mkc<CT>(0, 0);
+    if (fine_in(g, gx, gy, gz)) {
+      const int cx = L.dim > 0 ? lx + 1 : lx, cy = L.dim > 1 ? ly + 1 : ly, cz = L.dim > 2 ? lz + 1 : lz;
+      const int ci = (cz * ec[1] + cy) * ec[0] + cx;
+      const R xl = (R)fine_x(g, gx, gy, gz);
+      R qr = 0, qi = 0, ur = 0, ui = 0, er = 0, ei = 0;
+      for (int nn = 0; nn < K; ++nn) {
+        const CT cv = sC[ci * K + nn], hv = sA[i * K + nn];
+        const R q = sQ[m * K + nn], u = sU[m * K + nn], ee = sE[m * K + nn];
+        qr = fma(q, cv.x, qr); qi = fma(q, cv.y, qi);
+        ur = fma(u, hv.x, ur); ui = fma(u, hv.y, ui);
+        er = fma(ee, cv.x, er); ei = fma(ee, cv.y, ei);
+      }
+      const CT fv = f ? f[(size_t)((gz * g.n[1] + gy) * g.n[0] + gx) * K + m] : mkc<CT>(0, 0);
+      r.x = fv.x - (-qi - ur - xl * er);
+      r.y = fv.y - (qr - ui - xl * ei);
+    }
+    sB[t] = r;
+  }
+  __syncthreads();
+  // stage 3: z = Wt r
+  for (int t = tid; t < nbf * K; t += kSweepThreads) {
+    const int i = t / K, m = t % K;
+    R zr = 0, zi = 0;
+    for (int nn = 0; nn < K; ++nn) {
+      const R w = sW[m * K + nn];
+      const CT rv = sB[i * K + nn];
+      zr = fma(w, rv.x, zr); zi = fma(w, rv.y, zi);
+    }
+    sA[t] = mkc<CT>(zr, zi);
+  }
+  __syncthreads();
+  // stage 4: Hz on U (footprint index of U point = local + 1 on used axes)
+  const int dfy = L.dim > 1 ? ef[0] : 0, dfz = L.dim > 2 ? ef[0] * ef[1] : 0;
+  for (int t = tid; t < npts * K; t += kSweepThreads) {
+    const int i = t / K, m = t % K;
+    int lx, ly, lz;
+    local_coords(i, e, lx, ly, lz);
+    const int fx = L.dim > 0 ? lx + 1 : lx, fy = L.dim > 1 ? ly + 1 : ly, fz = L.dim > 2 ? lz + 1 : lz;
+    const int fi = (fz * ef[1] + fy) * ef[0] + fx;
+    const CT v = sA[fi * K + m];
+    CT h = mkc<CT>(sV[fi] * v.x, sV[fi] * v.y);
+    {
+      const CT a1 = sA[(fi + 1) * K + m], a2 = sA[(fi - 1) * K + m];
+      h.x += wx * (a1.x + a2.x); h.y += wx * (a1.y + a2.y);
+    }
+    if (L.dim > 1) {
+      const CT a1 = sA[(fi + dfy) * K + m], a2 = sA[(fi - dfy) * K + m];
+      h.x += wy * (a1.x + a2.x); h.y += wy * (a1.y + a2.y);
+    }
+    if (L.dim > 2) {
+      const CT a1 = sA[(fi + dfz) * K + m], a2 = sA[(fi - dfz) * K + m];
+      h.x += wz * (a1.x + a2.x); h.y += wz * (a1.y + a2.y);
+    }
+    sB[t] = h;
+  }
+  __syncthreads();
+  // stage 5: rhs = -i Qb^T z - Ub Hz - x Eb z on U; padding 0
+  for (int t = tid; t < NPAD; t += kSweepThreads) {
+    CT out = mkc<CT>(0, 0);
+    if (t < npts * K) {
+      const int i = t / K, m = t % K;
+      int lx, ly, lz;
+      local_coords(i, e, lx, ly, lz);
+      const int fx = L.dim > 0 ? lx + 1 : lx, fy = L.dim > 1 ? ly + 1 : ly, fz = L.dim > 2 ? lz + 1 : lz;
+      const int fi = (fz * ef[1] + fy) * ef[0] + fx;
+      const R xl = (R)fine_x(g, o[0] + lx, o[1] + ly, o[2] + lz);
+      R qr = 0, qi = 0, ur = 0, ui = 0, er = 0, ei = 0;
+      for (int nn = 0; nn < K; ++nn) {
+        const CT zv = sA[fi * K + nn], hv = sB[i * K + nn];
+        const R q = sQ[nn * K + m], u = sU[m * K + nn], ee = sE[m * K + nn];
+        qr = fma(q, zv.x, qr); qi = fma(q, zv.y, qi);
+        ur = fma(u, hv.x, ur); ui = fma(u, hv.y, ui);
+        er = fma(ee, zv.x, er); ei = fma(ee, zv.y, ei);
+      }
+      out.x = qi - ur - xl * er;
+      out.y = -qr - ui - xl * ei;
+    }
+    sRhs[t] = out;
+  }
+  __syncthreads();
+  subvol_solve<CT, NPAD>(factors + (size_t)b * L.fsize, sRhs, sY, sT, sRed);
+  for (int t = tid; t < npts * K; t += kSweepThreads) {
+    const int i = t / K, m = t % K;
+    int lx, ly, lz;
+    local_coords(i, e, lx, ly, lz);
+    const size_t gi = (size_t)(((o[2] + lz) * g.n[1] + (o[1] + ly)) * g.n[0] + (o[0] + lx)) * K + m;
+    CT v = c[gi];
+    v.x += sRhs[t].x;
+    v.y += sRhs[t].y;
+    c[gi] = v;
+  }
+}
+
+// ======================================================================== Galerkin-level sweep
+// rhs = (g - G e)_U with G = sum_kk' Sigma_kk' (x) Theta_kk' from the stored stencils, solve,
+// e_U += delta.
+template <typename R, int NPAD>
+__global__ void __launch_bounds__(kSweepThreads)
+k_sweep_coarse(LevelGeom L, const double* __restrict__ sigma, const TimeMats* __restrict__ tm,
+               const typename C2<R>::T* __restrict__ gvec, typename C2<R>::T* __restrict__ ev,
+               const typename C2<R>::T* __restrict__ factors, int colour) {
+  typedef typename C2<R>::T CT;
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int K = tm->K, KK = K * K;
+  const int tid = threadIdx.x;
+  const int b = colour_subvol(L, colour, blockIdx.x);
+  int o[3], e[3];
+  subvol_box(L, b, o, e);
+  int ec[3], oc[3];
+  for (int a = 0; a < 3; ++a) {
+    const bool used = a < L.dim;
+    ec[a] = used ? e[a] + 4 : 1;  oc[a] = used ? o[a] - 2 : o[a];
+  }
+  const int nbc = ec[0] * ec[1] * ec[2], npts = e[0] * e[1] * e[2];
+  const int sx = L.sub[0] + 4, sy = L.dim > 1 ? L.sub[1] + 4 : 1, sz = L.dim > 2 ? L.sub[2] + 4 : 1;
+  const int nbc_max = sx * sy * sz;
+  const int nptsmax = L.sub[0] * L.sub[1] * L.sub[2];
+
+  R* sP = reinterpret_cast<R*>(smem);                                // [9][K*K]
+  CT* sE = reinterpret_cast<CT*>(sP + LA_NPAIR * LA_KMAX * LA_KMAX); // e on U+2 [nbc_max*K]
+  CT* sTmp = sE + (size_t)nbc_max * K;                               // [nptsmax][9][K]
+  CT* sRhs = sTmp + (size_t)nptsmax * LA_NPAIR * K;
+  CT* sY = sRhs + NPAD;
+  CT* sT = sY + NPAD;
+  CT* sRed = sT + LA_BLK;
+
+  for (int i = tid; i < LA_NPAIR * KK; i += kSweepThreads) sP[i] = (R)tm->P[i / KK][i % KK];
+  for (int t = tid; t < nbc * K; t += kSweepThreads) {
+    const int i = t / K, m = t % K;
+    int lx, ly, lz;
+    local_coords(i, ec, lx, ly, lz);
+    const int gx = oc[0] + lx, gy = oc[1] + ly, gz = oc[2] + lz;
+    CT v = mkc<CT>(0, 0);
+    if (gx >= 0 && gy >= 0 && gz >= 0 && gx < L.n[0] && gy < L.n[1] && gz < L.n[2])
+      v = ev[(size_t)((gz * L.n[1] + gy) * L.n[0] + gx) * K + m];
+    sE[t] = v;
+  }
+  __syncthreads();
+  const int nbox = box5_count(L.dim);
+  const int rz = L.dim > 2 ? 2 : 0, ry = L.dim > 1 ? 2 : 0;
+  // stage 1: per (U point, pair): Theta_kk' (Sigma_kk' e)_p
+  for (int t = tid; t < npts * LA_NPAIR; t += kSweepThreads) {
+    const int i = t / LA_NPAIR, kk = t % LA_NPAIR;
+    int lx, ly, lz;
+    local_coords(i, e, lx, ly, lz);
+    const int p = ((o[2] + lz) * L.n[1] + (o[1] + ly)) * L.n[0] + (o[0] + lx);
+    const int cx = L.dim > 0 ? lx + 2 : lx, cy = L.dim > 1 ? ly + 2 : ly, cz = L.dim > 2 ? lz + 2 : lz;
+    CT u[LA_KMAX];
+    for (int m = 0; m < K; ++m) u[m] = mkc<CT>(0, 0);
+    const double* sg = sigma + sigma_offset(p, kk, 0, nbox);
+    for (int oz = -rz; oz <= rz; ++oz)
+      for (int oy = -ry; oy <= ry; ++oy)
+        for (int ox = -2; ox <= 2; ++ox) {
+          const R s = (R)sg[box5_index(L.dim, ox, oy, oz)];
+          if (s == (R)0) continue;
+          const CT* ep = sE + (size_t)(((cz + oz) * ec[1] + (cy + oy)) * ec[0] + (cx + ox)) * K;
+          for (int m = 0; m < K; ++m) { u[m].x = fma(s, ep[m].x, u[m].x); u[m].y = fma(s, ep[m].y, u[m].y); }
+        }
+    const int ph = theta_phase(kk);
+    for (int m = 0; m < K; ++m) {
+      R vr = 0, vi = 0;
+      for (int nn = 0; nn < K; ++nn) {
+        const R pv = sP[kk * KK + m * K + nn];
+        vr = fma(pv, u[nn].x, vr); vi = fma(pv, u[nn].y, vi);
+      }
+      CT w;
+      if (ph == 0) w = mkc<CT>(vr, vi);
+      else if (ph == 1) w = mkc<CT>(-vi, vr);
+      else w = mkc<CT>(vi, -vr);
+      sTmp[((size_t)i * LA_NPAIR + kk) * K + m] = w;
+    }
+  }
+  __syncthreads();
+  // stage 2: rhs = g - sum over pairs (fixed order)
+  for (int t = tid; t < NPAD; t += kSweepThreads) {
+    CT out = mkc<CT>(0, 0);
+    if (t < npts * K) {
+      const int i = t / K, m = t % K;
+      int lx, ly, lz;
+      local_coords(i, e, lx, ly, lz);
+      const int p = ((o[2] + lz) * L.n[1] + (o[1] + ly)) * L.n[0] + (o[0] + lx);
+      out = gvec[(size_t)p * K + m];
+      for (int kk = 0; kk < LA_NPAIR; ++kk) {
+        const CT w = sTmp[((size_t)i * LA_NPAIR + kk) * K + m];
+        out.x -= w.x; out.y -= w.y;
+      }
+    }
+    sRhs[t] = out;
+  }
+  __syncthreads();
+  subvol_solve<CT, NPAD>(factors + (size_t)b * L.fsize, sRhs, sY, sT, sRed);
+  for (int t = tid; t < npts * K; t += kSweepThreads) {
+    const int i = t / K, m = t % K;
+    int lx, ly, lz;
+    local_coords(i, e, lx, ly, lz);
+    const size_t gi = (size_t)(((o[2] + lz) * L.n[1] + (o[1] + ly)) * L.n[0] + (o[0] + lx)) * K + m;
+    CT v = ev[gi];
+    v.x += sRhs[t].x;
+    v.y += sRhs[t].y;
+    ev[gi] = v;
+  }
+}
+
+// ======================================================================== host dispatch
+inline size_t factor_smem(const LevelGeom& L, int nptsmax, size_t csize) {
+  return sizeof(double) * (LA_NPAIR * LA_KMAX * LA_KMAX + (((size_t)nptsmax * nptsmax * LA_NPAIR + 1) & ~(size_t)1)) +
+         csize * ((size_t)L.npad + (size_t)L.nblk * 256) + 16;
+}
+inline size_t sweep_fine_smem(const LevelGeom& L, int K, size_t rsize, size_t csize) {
+  const int sx = L.sub[0] + 4, sy = L.dim > 1 ? L.sub[1] + 4 : 1, sz = L.dim > 2 ? L.sub[2] + 4 : 1;
+  const size_t nbc = (size_t)sx * sy * sz;
+  return rsize * (4 * LA_KMAX * LA_KMAX + ((nbc + 3) & ~(size_t)3)) + csize * (3 * nbc * K + 2 * (size_t)L.npad + LA_BLK + 128);
+}
+inline size_t sweep_coarse_smem(const LevelGeom& L, int K, size_t rsize, size_t csize) {
+  const int sx = L.sub[0] + 4, sy = L.dim > 1 ? L.sub[1] + 4 : 1, sz = L.dim > 2 ? L.sub[2] + 4 : 1;
+  const size_t nbc = (size_t)sx * sy * sz;
+  const size_t nptsmax = (size_t)L.sub[0] * L.sub[1] * L.sub[2];
+  return rsize * (LA_NPAIR * LA_KMAX * LA_KMAX) + csize * (nbc * K + nptsmax * LA_NPAIR * K + 2 * (size_t)L.npad + LA_BLK + 128);
+}
+
+template <typename R, int NPAD>
+cudaError_t launch_factor_n(const LevelGeom& L, const FineOp* fine, const double* sigma, const TimeMats* tm,
+                            typename C2<R>::T* factors, int* status, cudaStream_t s) {
+  const int nptsmax = L.sub[0] * L.sub[1] * L.sub[2];
+  const size_t smem = factor_smem(L, nptsmax, sizeof(typename C2<R>::T));
+  auto kern = k_factor<R, NPAD>;
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+    if (err != cudaSuccess) return err;
+    attr_set = true;
+  }
+  if (smem > 227 * 1024) return cudaErrorInvalidValue;
+  FineOp g = fine ? *fine : FineOp{};
+  kern<<<L.nsub, kFactorThreads, smem, s>>>(L, g, fine ? 1 : 0, nptsmax, sigma, tm, factors, status);
+  return cudaGetLastError();
+}
+template <typename R, int NPAD>
+cudaError_t launch_sweep_fine_n(const LevelGeom& L, const FineOp& g, const TimeMats* tm, int K,
+                                const typename C2<R>::T* f, typename C2<R>::T* c, const typename C2<R>::T* factors,
+                                int colour, cudaStream_t s) {
+  const int nblocks = colour_count(L, colour);
+  if (nblocks == 0) return cudaSuccess;
+  const size_t smem = sweep_fine_smem(L, K, sizeof(R), sizeof(typename C2<R>::T));
+  auto kern = k_sweep_fine<R, NPAD>;
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+    if (err != cudaSuccess) return err;
+    attr_set = true;
+  }
+  if (smem > 227 * 1024) return cudaErrorInvalidValue;
+  kern<<<nblocks, kSweepThreads, smem, s>>>(L, g, tm, f, c, factors, colour);
+  return cudaGetLastError();
+}
+template <typename R, int NPAD>
+cudaError_t launch_sweep_coarse_n(const LevelGeom& L, const double* sigma, const TimeMats* tm, int K,
+                                  const typename C2<R>::T* gvec, typename C2<R>::T* e,
+                                  const typename C2<R>::T* factors, int colour, cudaStream_t s) {
+  const int nblocks = colour_count(L, colour);
+  if (nblocks == 0) return cudaSuccess;
+  const size_t smem = sweep_coarse_smem(L, K, sizeof(R), sizeof(typename C2<R>::T));
+  auto kern = k_sweep_coarse<R, NPAD>;
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+    if (err != cudaSuccess) return err;
+    attr_set = true;
+  }
+  if (smem > 227 * 1024) return cudaErrorInvalidValue;
+  kern<<<nblocks, kSweepThreads, smem, s>>>(L, sigma, tm, gvec, e, factors, colour);
+  return cudaGetLastError();
+}
+
+#define LA_NPAD_DISPATCH(NPADV, CALL) \
+  switch (NPADV) {                    \
+    case 16: return CALL(16);         \
+    case 32: return CALL(32);         \
+    case 48: return CALL(48);         \
+    case 64: return CALL(64);         \
+    case 96: return CALL(96);         \
+    case 128: return CALL(128);       \
+    default: return cudaErrorInvalidValue; \
+  }
+
+}  // namespace la

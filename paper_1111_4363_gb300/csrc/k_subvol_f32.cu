@@ -1,0 +1,26 @@
+// FP32 (complex64) instantiations of the subvolume kernels.
+#include "k_subvol.cuh"
+namespace la {
+template <>
+cudaError_t launch_factor<float>(const LevelGeom& L, const FineOp* fine, const double* sigma, const TimeMats* tm,
+                                  float2* factors, int* status, cudaStream_t s) {
+#define LA_CALL(N) launch_factor_n<float, N>(L, fine, sigma, tm, factors, status, s)
+  LA_NPAD_DISPATCH(L.npad, LA_CALL)
+#undef LA_CALL
+}
+template <>
+cudaError_t launch_sweep_fine<float>(const LevelGeom& L, const FineOp& g, const TimeMats* tm, int K, const float2* f,
+                                      float2* c, const float2* factors, int colour, cudaStream_t s) {
+#define LA_CALL(N) launch_sweep_fine_n<float, N>(L, g, tm, K, f, c, factors, colour, s)
+  LA_NPAD_DISPATCH(L.npad, LA_CALL)
+#undef LA_CALL
+}
+template <>
+cudaError_t launch_sweep_coarse<float>(const LevelGeom& L, const double* sigma, const TimeMats* tm, int K,
+                                        const float2* gvec, float2* e, const float2* factors, int colour,
+                                        cudaStream_t s) {
+#define LA_CALL(N) launch_sweep_coarse_n<float, N>(L, sigma, tm, K, gvec, e, factors, colour, s)
+  LA_NPAD_DISPATCH(L.npad, LA_CALL)
+#undef LA_CALL
+}
+}  // namespace la

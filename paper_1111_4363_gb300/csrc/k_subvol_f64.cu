@@ -1,0 +1,26 @@
+// FP64 instantiations of the subvolume kernels.
+#include "k_subvol.cuh"
+namespace la {
+template <>
+cudaError_t launch_factor<double>(const LevelGeom& L, const FineOp* fine, const double* sigma, const TimeMats* tm,
+                                  double2* factors, int* status, cudaStream_t s) {
+#define LA_CALL(N) launch_factor_n<double, N>(L, fine, sigma, tm, factors, status, s)
+  LA_NPAD_DISPATCH(L.npad, LA_CALL)
+#undef LA_CALL
+}
+template <>
+cudaError_t launch_sweep_fine<double>(const LevelGeom& L, const FineOp& g, const TimeMats* tm, int K, const double2* f,
+                                      double2* c, const double2* factors, int colour, cudaStream_t s) {
+#define LA_CALL(N) launch_sweep_fine_n<double, N>(L, g, tm, K, f, c, factors, colour, s)
+  LA_NPAD_DISPATCH(L.npad, LA_CALL)
+#undef LA_CALL
+}
+template <>
+cudaError_t launch_sweep_coarse<double>(const LevelGeom& L, const double* sigma, const TimeMats* tm, int K,
+                                        const double2* gvec, double2* e, const double2* factors, int colour,
+                                        cudaStream_t s) {
+#define LA_CALL(N) launch_sweep_coarse_n<double, N>(L, sigma, tm, K, gvec, e, factors, colour, s)
+  LA_NPAD_DISPATCH(L.npad, LA_CALL)
+#undef LA_CALL
+}
+}  // namespace la

@@ -1,0 +1,623 @@
+// C ABI of the least-action propagator: context, configuration checks, time-basis constants,
+// and the per-step driver (factorisation, V-cycles, convergence test, step advance).
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "la_internal.cuh"
+#include "../../include/leastaction.h"
+
+using namespace la;
+
+#define LA_MAX_LEVELS 8
+
+struct la_ctx {
+  la_config cfg;
+  cudaStream_t stream = 0;
+  std::string err;
+  int K = 0, L = 0, dim = 0, np0 = 0;
+  long long nunk0 = 0;
+  double hd = 1.0;          // h^d
+  double nscale = 1.0;      // N = nscale * r~^dagger Wt r~
+  FineOp fine{};
+  LevelGeom geo[LA_MAX_LEVELS];
+  TimeMats htm{};           // host copy of the static part
+  TimeMats* d_tm = nullptr;
+  double* d_V0 = nullptr;
+  // finest level, FP64
+  double2 *d_psi = nullptr, *d_f = nullptr, *d_c = nullptr, *d_r = nullptr, *d_z = nullptr, *d_s = nullptr;
+  // finest level, FP32 (mixed precision correction problem)
+  float2 *d_f32 = nullptr, *d_e32 = nullptr, *d_r32 = nullptr, *d_z32 = nullptr, *d_s32 = nullptr;
+  // levels >= 1 (precision of the V-cycle), and factors of every level
+  void* d_e[LA_MAX_LEVELS] = {};
+  void* d_g[LA_MAX_LEVELS] = {};
+  void* d_sl[LA_MAX_LEVELS] = {};
+  void* d_fac[LA_MAX_LEVELS] = {};
+  double* d_sigma[LA_MAX_LEVELS] = {};
+  double* d_partials = nullptr;
+  double* d_N = nullptr;
+  int* d_status = nullptr;
+  int nparts = 0;
+  bool have_ham = false;
+  bool have_step = false;
+  double last_N = 0.0, last_rel = 0.0;
+  std::vector<void*> allocs;
+};
+
+static la_status fail(la_ctx* c, la_status s, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  if (c) c->err = buf;
+  return s;
+}
+#define LA_CUDA(ctx, call)                                                                       \
+  do {                                                                                           \
+    cudaError_t e_ = (call);                                                                     \
+    if (e_ != cudaSuccess) return fail(ctx, LA_ECUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+  } while (0)
+#define LA_CHECK_LAUNCH(ctx) LA_CUDA(ctx, cudaGetLastError())
+#define LA_TRY(expr)                   \
+  do {                                 \
+    la_status s_ = (expr);             \
+    if (s_ != LA_OK) return s_;        \
+  } while (0)
+
+static la_status dalloc(la_ctx* c, void** p, size_t bytes) {
+  if (getenv("LA_FAIL_ALLOC")) return fail(c, LA_ENOMEM, "allocation of %zu bytes refused (LA_FAIL_ALLOC)", bytes);
+  cudaError_t e = cudaMalloc(p, bytes ? bytes : 16);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    *p = nullptr;
+    return fail(c, LA_ENOMEM, "cudaMalloc(%zu): %s", bytes, cudaGetErrorString(e));
+  }
+  c->allocs.push_back(*p);
+  return LA_OK;
+}
+
+// ------------------------------------------------------------------ time-basis constants (host)
+// Legendre P_0..P_n at y by the three-term recurrence.
+static void legendre_all(int n, double y, double* P) {
+  P[0] = 1.0;
+  if (n >= 1) P[1] = y;
+  for (int k = 2; k <= n; ++k) P[k] = ((2.0 * k - 1.0) * y * P[k - 1] - (k - 1.0) * P[k - 2]) / k;
+}
+// Gauss-Legendre nodes and weights on [-1, 1] by Newton iteration on P_q.
+static void gauss_legendre(int q, double* x, double* w) {
+  std::vector<double> P(q + 1);
+  for (int i = 0; i < q; ++i) {
+    double y = std::cos(M_PI * (i + 0.75) / (q + 0.5));
+    for (int it = 0; it < 100; ++it) {
+      legendre_all(q, y, P.data());
+      double dp = q * (y * P[q] - P[q - 1]) / (y * y - 1.0);
+      double dy = P[q] / dp;
+      y -= dy;
+      if (std::fabs(dy) < 1e-16) break;
+    }
+    legendre_all(q, y, P.data());
+    double dp = q * (y * P[q] - P[q - 1]) / (y * y - 1.0);
+    x[i] = y;
+    w[i] = 2.0 / ((1.0 - y * y) * dp * dp);
+  }
+}
+static bool invert_small(int n, const double* A, double* Ainv) {
+  double M[LA_KMAX][2 * LA_KMAX];
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < 2 * n; ++j) M[i][j] = j < n ? A[i * n + j] : (j - n == i ? 1.0 : 0.0);
+  for (int col = 0; col < n; ++col) {
+    int piv = col;
+    for (int r = col + 1; r < n; ++r)
+      if (std::fabs(M[r][col]) > std::fabs(M[piv][col])) piv = r;
+    if (std::fabs(M[piv][col]) < 1e-300) return false;
+    for (int j = 0; j < 2 * n; ++j) std::swap(M[col][j], M[piv][j]);
+    double d = M[col][col];
+    for (int j = 0; j < 2 * n; ++j) M[col][j] /= d;
+    for (int r = 0; r < n; ++r) {
+      if (r == col) continue;
+      double f = M[r][col];
+      for (int j = 0; j < 2 * n; ++j) M[r][j] -= f * M[col][j];
+    }
+  }
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j) Ainv[i * n + j] = M[i][n + j];
+  return true;
+}
+// Closed forms from Sec. IV (orthogonality 2 delta/(2n+1), Q_nm = 2 for n > m with n - m odd,
+// P_n(+-1) = (+-1)^n) in the basis b_n = P_n - (-1)^n P_0, n = 1..K.
+static bool build_time_constants(la_ctx* c) {
+  const int K = c->K;
+  const double dt = c->cfg.dt;
+  TimeMats& t = c->htm;
+  memset(&t, 0, sizeof t);
+  t.K = K;
+  t.dt = dt;
+  for (int m = 1; m <= K; ++m) {
+    const double sm = (m % 2) ? -1.0 : 1.0;
+    t.Ub0[m - 1] = -sm * dt;
+    t.endv[m - 1] = 1.0 - sm;
+    for (int n = 1; n <= K; ++n) {
+      const double sn = (n % 2) ? -1.0 : 1.0;
+      t.Ub[(m - 1) * K + (n - 1)] = dt * ((m == n ? 1.0 / (2 * m + 1) : 0.0) + sm * sn);
+      const double q = (n > m && ((n - m) % 2 == 1)) ? 2.0 : 0.0;
+      t.Qb[(m - 1) * K + (n - 1)] = q - sm * (1.0 - sn);
+    }
+  }
+  if (c->cfg.weight == 0) {
+    if (!invert_small(K, t.Ub, t.Wt)) return false;
+  } else if (c->cfg.weight == 1) {
+    memcpy(t.Wt, t.Ub, sizeof(double) * K * K);
+  } else {
+    for (int i = 0; i < K; ++i) t.Wt[i * K + i] = 1.0;
+  }
+  t.nq = K + 8;
+  gauss_legendre(t.nq, t.tau, t.wq);
+  std::vector<double> P(K + 1);
+  for (int q = 0; q < t.nq; ++q) {
+    legendre_all(K, t.tau[q], P.data());
+    for (int m = 1; m <= K; ++m) t.bq[q * LA_KMAX + (m - 1)] = P[m] - ((m % 2) ? -1.0 : 1.0);
+  }
+  return true;
+}
+
+static int round_npad(int n) {
+  const int sizes[6] = {16, 32, 48, 64, 96, 128};
+  for (int s : sizes)
+    if (n <= s) return s;
+  return -1;
+}
+
+static size_t csize(const la_ctx* c) { return c->cfg.precision ? sizeof(float2) : sizeof(double2); }
+
+// ------------------------------------------------------------------ ABI
+extern "C" const char* la_version(void) { return "leastaction-gb300 0.1 (sm_103a)"; }
+
+// message of the last failed la_init on this thread (the context does not exist then)
+static thread_local std::string g_init_error = "no error";
+
+extern "C" const char* la_last_error(const la_ctx* ctx) { return ctx ? ctx->err.c_str() : g_init_error.c_str(); }
+
+extern "C" la_status la_init(const la_config* cfg, void* stream, la_ctx** out) {
+  if (!cfg || !out) return LA_EINVAL;
+  *out = nullptr;
+  la_ctx* c = new (std::nothrow) la_ctx();
+  if (!c) return LA_ENOMEM;
+  c->cfg = *cfg;
+  c->stream = (cudaStream_t)stream;
+  const la_config& k = *cfg;
+  la_status st = LA_OK;
+  auto bad = [&](const char* why) {
+    st = fail(c, LA_EINVAL, "invalid configuration: %s", why);
+  };
+  if (k.dim < 1 || k.dim > 3) bad("dim must be 1, 2 or 3");
+  else if (k.nt < 1 || k.nt > LA_KMAX) bad("nt must be in [1, 8]");
+  else if (!(k.dt > 0)) bad("dt must be positive");
+  else if (k.levels < 1 || k.levels > LA_MAX_LEVELS) bad("levels must be in [1, 8]");
+  else if (k.max_cycles < 1) bad("max_cycles must be >= 1");
+  else if (k.nu1 < 0 || k.nu2 < 0 || k.nu1 + k.nu2 < 1) bad("nu1, nu2 >= 0 with nu1 + nu2 >= 1");
+  else if (k.levels > 1 && k.coarse_sweeps < 1) bad("coarse_sweeps must be >= 1 with multigrid");
+  else if (k.weight < 0 || k.weight > 2) bad("weight must be 0, 1 or 2");
+  else if (k.precision < 0 || k.precision > 1) bad("precision must be 0 or 1");
+  else if (k.laser_axis < 0 || k.laser_axis >= k.dim) bad("laser_axis must be a used axis");
+  if (st == LA_OK) {
+    for (int a = 0; a < 3 && st == LA_OK; ++a) {
+      if (a < k.dim) {
+        if (k.n[a] < 1) bad("n must be >= 1 on used axes");
+        else if (!(k.h[a] > 0)) bad("h must be positive on used axes");
+        else if (k.sub[a] < 2) bad("sub must be >= 2 on used axes (same-colour subvolumes must not interact)");
+        else if (k.n[a] % (1 << (k.levels - 1))) bad("n must be divisible by 2^(levels-1) on used axes");
+      } else if (k.n[a] != 1) bad("unused axes must have n = 1");
+    }
+  }
+  if (st != LA_OK) {
+    g_init_error = c->err;
+    delete c;
+    return st;
+  }
+  c->K = k.nt;
+  c->L = k.levels;
+  c->dim = k.dim;
+  int subpts = 1;
+  for (int a = 0; a < k.dim; ++a) subpts *= k.sub[a];
+  if (subpts > LA_NPTS_MAX || round_npad(subpts * k.nt) < 0) {
+    g_init_error = "invalid configuration: a subvolume may hold at most 32 points and 128 unknowns";
+    delete c;
+    return LA_EINVAL;
+  }
+  // fine operator
+  FineOp& g = c->fine;
+  g.dim = k.dim;
+  g.dsum = 0.0;
+  c->hd = 1.0;
+  for (int a = 0; a < 3; ++a) {
+    g.n[a] = a < k.dim ? k.n[a] : 1;
+    g.h[a] = a < k.dim ? k.h[a] : 1.0;
+    g.ih2[a] = a < k.dim ? 1.0 / (k.h[a] * k.h[a]) : 0.0;
+    g.x0[a] = -0.5 * (g.n[a] - 1) * g.h[a];
+    if (a < k.dim) {
+      g.dsum += g.ih2[a];
+      c->hd *= k.h[a];
+    }
+  }
+  g.lax = k.laser_axis;
+  c->np0 = g.n[0] * g.n[1] * g.n[2];
+  c->nunk0 = (long long)c->np0 * c->K;
+  c->nscale = k.weight == 0 ? c->hd : (k.weight == 1 ? c->hd * c->hd * c->hd : c->hd * c->hd);
+  // levels
+  for (int l = 0; l < c->L; ++l) {
+    LevelGeom& G = c->geo[l];
+    G.dim = k.dim;
+    G.np = 1;
+    for (int a = 0; a < 3; ++a) {
+      G.n[a] = a < k.dim ? (g.n[a] >> l) : 1;
+      G.sub[a] = a < k.dim ? k.sub[a] : 1;
+      G.nb[a] = (G.n[a] + G.sub[a] - 1) / G.sub[a];
+      G.np *= G.n[a];
+    }
+    G.nsub = G.nb[0] * G.nb[1] * G.nb[2];
+    G.npad = round_npad(subpts * k.nt);
+    G.nblk = G.npad / LA_BLK;
+    G.fsize = (long long)G.nblk * (G.nblk + 1) / 2 * LA_BLK * LA_BLK;
+  }
+  if (!build_time_constants(c)) {
+    g_init_error = "invalid configuration: singular time-basis Gram matrix";
+    delete c;
+    return LA_EINVAL;
+  }
+  // allocations
+  const size_t v64 = sizeof(double2) * (size_t)c->nunk0;
+  const size_t v32 = sizeof(float2) * (size_t)c->nunk0;
+  void* p;
+#define ALLOC(field, bytes)                                         \
+  do {                                                              \
+    st = dalloc(c, &p, (bytes));                                    \
+    if (st != LA_OK) { g_init_error = c->err; la_finalize(c); return st; } \
+    field = (decltype(field))p;                                     \
+  } while (0)
+  ALLOC(c->d_tm, sizeof(TimeMats));
+  ALLOC(c->d_V0, sizeof(double) * c->np0);
+  ALLOC(c->d_psi, sizeof(double2) * c->np0);
+  ALLOC(c->d_f, v64);
+  ALLOC(c->d_c, v64);
+  ALLOC(c->d_r, v64);
+  ALLOC(c->d_z, v64);
+  ALLOC(c->d_s, v64);
+  if (k.precision == 1) {
+    ALLOC(c->d_f32, v32);
+    ALLOC(c->d_e32, v32);
+    ALLOC(c->d_r32, v32);
+    ALLOC(c->d_z32, v32);
+    ALLOC(c->d_s32, v32);
+  }
+  for (int l = 0; l < c->L; ++l) {
+    const LevelGeom& G = c->geo[l];
+    ALLOC(c->d_fac[l], csize(c) * (size_t)G.nsub * G.fsize);
+    if (l >= 1) {
+      const size_t vb = csize(c) * (size_t)G.np * c->K;
+      ALLOC(c->d_e[l], vb);
+      ALLOC(c->d_g[l], vb);
+      ALLOC(c->d_sl[l], vb);
+      ALLOC(c->d_sigma[l], sizeof(double) * (size_t)G.np * LA_NPAIR * box5_count(k.dim));
+    }
+  }
+  c->nparts = norm_blocks(c->np0);
+  ALLOC(c->d_partials, sizeof(double) * c->nparts);
+  ALLOC(c->d_N, sizeof(double) * 2);
+  ALLOC(c->d_status, sizeof(int));
+#undef ALLOC
+  c->fine.V0 = c->d_V0;
+  cudaError_t e = cudaMemcpyAsync(c->d_tm, &c->htm, sizeof(TimeMats), cudaMemcpyHostToDevice, c->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->d_status, 0, sizeof(int), c->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->d_V0, 0, sizeof(double) * c->np0, c->stream);
+  if (e != cudaSuccess) {
+    la_finalize(c);
+    return LA_ECUDA;
+  }
+  *out = c;
+  return LA_OK;
+}
+
+extern "C" la_status la_finalize(la_ctx* c) {
+  if (!c) return LA_EINVAL;
+  cudaStreamSynchronize(c->stream);
+  for (void* p : c->allocs) cudaFree(p);
+  delete c;
+  return LA_OK;
+}
+
+static bool is_device_ptr(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+// copy n bytes from a host-or-device pointer into device memory dst
+static la_status load_any(la_ctx* c, void* dst, const void* src, size_t n) {
+  LA_CUDA(c, cudaMemcpyAsync(dst, src, n, is_device_ptr(src) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                             c->stream));
+  return LA_OK;
+}
+static la_status store_any(la_ctx* c, void* dst, const void* src, size_t n) {
+  LA_CUDA(c, cudaMemcpyAsync(dst, src, n, is_device_ptr(dst) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                             c->stream));
+  return LA_OK;
+}
+
+extern "C" la_status la_set_hamiltonian(la_ctx* c, const double* V0, const la_pulse* pulse) {
+  if (!c) return LA_EINVAL;
+  if (!V0) return fail(c, LA_EINVAL, "V0 is null");
+  int nc = pulse ? pulse->ncomp : 0;
+  if (nc < 0 || nc > LA_NCOMP_MAX) return fail(c, LA_EINVAL, "pulse ncomp must be in [0, %d]", LA_NCOMP_MAX);
+  if (nc > 0 && (!pulse->amp || !pulse->omega || !pulse->t_center || !pulse->sigma))
+    return fail(c, LA_EINVAL, "pulse arrays must not be null");
+  c->htm.ncomp = nc;
+  for (int k = 0; k < nc; ++k) {
+    c->htm.amp[k] = pulse->amp[k];
+    c->htm.omega[k] = pulse->omega[k];
+    c->htm.tc[k] = pulse->t_center[k];
+    c->htm.sigma[k] = pulse->sigma[k];
+  }
+  LA_TRY(load_any(c, c->d_V0, V0, sizeof(double) * c->np0));
+  LA_CUDA(c, cudaMemcpyAsync(c->d_tm, &c->htm, sizeof(TimeMats), cudaMemcpyHostToDevice, c->stream));
+  // Galerkin spatial factors of every coarse level (static)
+  for (int l = 1; l < c->L; ++l) {
+    if (l == 1) launch_galerkin_from_fine(c->fine, c->geo[1], c->d_sigma[1], c->stream);
+    else launch_galerkin_coarse(c->geo[l - 1], c->d_sigma[l - 1], c->geo[l], c->d_sigma[l], c->stream);
+    LA_CHECK_LAUNCH(c);
+  }
+  LA_CUDA(c, cudaStreamSynchronize(c->stream));
+  c->have_ham = true;
+  return LA_OK;
+}
+
+// ------------------------------------------------------------------ V-cycle
+template <typename R> struct Fine;
+template <> struct Fine<double> {
+  static double2* f(la_ctx* c) { return c->d_f; }
+  static double2* e(la_ctx* c) { return c->d_c; }
+  static double2* r(la_ctx* c) { return c->d_r; }
+  static double2* z(la_ctx* c) { return c->d_z; }
+  static double2* s(la_ctx* c) { return c->d_s; }
+};
+template <> struct Fine<float> {
+  static float2* f(la_ctx* c) { return c->d_f32; }
+  static float2* e(la_ctx* c) { return c->d_e32; }
+  static float2* r(la_ctx* c) { return c->d_r32; }
+  static float2* z(la_ctx* c) { return c->d_z32; }
+  static float2* s(la_ctx* c) { return c->d_s32; }
+};
+
+template <typename R>
+static la_status factor_all(la_ctx* c) {
+  typedef typename C2<R>::T CT;
+  for (int l = 0; l < c->L; ++l) {
+    cudaError_t e = launch_factor<R>(c->geo[l], l == 0 ? &c->fine : nullptr, c->d_sigma[l], c->d_tm,
+                                     (CT*)c->d_fac[l], c->d_status, c->stream);
+    if (e != cudaSuccess) return fail(c, LA_ECUDA, "factor level %d: %s", l, cudaGetErrorString(e));
+  }
+  return LA_OK;
+}
+
+template <typename R>
+static la_status sweep_level(la_ctx* c, int l, int nsweeps) {
+  typedef typename C2<R>::T CT;
+  const int ncol = 1 << c->dim;
+  for (int s = 0; s < nsweeps; ++s)
+    for (int col = 0; col < ncol; ++col) {
+      cudaError_t e;
+      if (l == 0)
+        e = launch_sweep_fine<R>(c->geo[0], c->fine, c->d_tm, c->K, Fine<R>::f(c), Fine<R>::e(c),
+                                 (const CT*)c->d_fac[0], col, c->stream);
+      else
+        e = launch_sweep_coarse<R>(c->geo[l], c->d_sigma[l], c->d_tm, c->K, (const CT*)c->d_g[l], (CT*)c->d_e[l],
+                                   (const CT*)c->d_fac[l], col, c->stream);
+      if (e != cudaSuccess) return fail(c, LA_ECUDA, "sweep level %d colour %d: %s", l, col, cudaGetErrorString(e));
+    }
+  return LA_OK;
+}
+
+template <typename R>
+static la_status vcycle(la_ctx* c, int l) {
+  typedef typename C2<R>::T CT;
+  const la_config& k = c->cfg;
+  if (c->L == 1) return sweep_level<R>(c, 0, k.nu1 + k.nu2);
+  if (l == c->L - 1) return sweep_level<R>(c, l, k.coarse_sweeps);
+  LA_TRY(sweep_level<R>(c, l, k.nu1));
+  CT* sfine;
+  if (l == 0) {
+    // normal residual s = M~^dagger Wt (f - M~ e) on the finest level
+    launch_mresid<R>(c->fine, c->d_tm, Fine<R>::f(c), Fine<R>::e(c), nullptr, Fine<R>::z(c), nullptr, c->nparts,
+                     c->stream);
+    launch_mnormal<R>(c->fine, c->d_tm, Fine<R>::z(c), Fine<R>::s(c), c->stream);
+    sfine = Fine<R>::s(c);
+  } else {
+    launch_gresid<R>(c->geo[l], c->d_tm, c->d_sigma[l], (const CT*)c->d_g[l], (const CT*)c->d_e[l], (CT*)c->d_sl[l],
+                     c->stream);
+    sfine = (CT*)c->d_sl[l];
+  }
+  launch_restrict<R>(c->geo[l], c->geo[l + 1], c->K, sfine, (CT*)c->d_g[l + 1], c->stream);
+  LA_CHECK_LAUNCH(c);
+  LA_CUDA(c, cudaMemsetAsync(c->d_e[l + 1], 0, sizeof(CT) * (size_t)c->geo[l + 1].np * c->K, c->stream));
+  LA_TRY(vcycle<R>(c, l + 1));
+  CT* efine = l == 0 ? Fine<R>::e(c) : (CT*)c->d_e[l];
+  launch_prolong_add<R>(c->geo[l], c->geo[l + 1], c->K, (const CT*)c->d_e[l + 1], efine, c->stream);
+  LA_CHECK_LAUNCH(c);
+  return sweep_level<R>(c, l, k.nu2);
+}
+
+// N of the current FP64 iterate (stores r~ = f~ - M~ c in d_r); synchronises.
+static la_status action_now(la_ctx* c, double* N) {
+  launch_mresid<double>(c->fine, c->d_tm, c->d_f, c->d_c, c->d_r, nullptr, c->d_partials, c->nparts, c->stream);
+  launch_norm_final(c->d_partials, c->nparts, c->nscale, c->d_N, c->stream);
+  LA_CHECK_LAUNCH(c);
+  LA_CUDA(c, cudaMemcpyAsync(N, c->d_N, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  LA_CUDA(c, cudaStreamSynchronize(c->stream));
+  return LA_OK;
+}
+
+// time matrices and right-hand side for initial state d_psi at t0
+static la_status setup_step(la_ctx* c, double t0) {
+  launch_time_matrices(c->d_tm, t0, c->stream);
+  launch_rhs(c->fine, c->d_tm, c->d_psi, c->d_f, c->stream);
+  LA_CHECK_LAUNCH(c);
+  return LA_OK;
+}
+
+// Relax the step's coefficients from c = 0.  ncycles > 0: exactly that many cycles.
+static la_status solve_current(la_ctx* c, int ncycles, la_step_stats* st) {
+  const la_config& k = c->cfg;
+  if (k.precision == 0) LA_TRY(factor_all<double>(c));
+  else LA_TRY(factor_all<float>(c));
+  LA_CUDA(c, cudaMemsetAsync(c->d_c, 0, sizeof(double2) * (size_t)c->nunk0, c->stream));
+  double N0 = 0.0, N = 0.0;
+  LA_TRY(action_now(c, &N0));
+  N = N0;
+  int cyc = 0;
+  const int maxc = ncycles > 0 ? ncycles : k.max_cycles;
+  const bool check = ncycles <= 0 && k.tol > 0;
+  while (cyc < maxc) {
+    if (check && N <= k.tol * N0) break;
+    if (k.precision == 0) {
+      LA_TRY(vcycle<double>(c, 0));
+    } else {
+      // refinement: correction problem M~ e = r~ (r~ from the last action evaluation) in complex64
+      launch_c128_to_c64(c->nunk0, c->d_r, c->d_f32, c->stream);
+      LA_CUDA(c, cudaMemsetAsync(c->d_e32, 0, sizeof(float2) * (size_t)c->nunk0, c->stream));
+      LA_TRY(vcycle<float>(c, 0));
+      launch_axpy_c64_to_c128(c->nunk0, c->d_e32, c->d_c, c->stream);
+      LA_CHECK_LAUNCH(c);
+    }
+    ++cyc;
+    LA_TRY(action_now(c, &N));
+  }
+  int status = 0;
+  LA_CUDA(c, cudaMemcpy(&status, c->d_status, sizeof(int), cudaMemcpyDeviceToHost));
+  if (status) {
+    cudaMemsetAsync(c->d_status, 0, sizeof(int), c->stream);
+    return fail(c, LA_ECUDA, "a subvolume matrix was not positive definite (status %d)", status);
+  }
+  c->last_N = N;
+  c->last_rel = N0 > 0 ? N / N0 : 0.0;
+  c->have_step = true;
+  const int fine_per_cycle = c->L == 1 ? k.nu1 + k.nu2 : k.nu1 + k.nu2;
+  if (st) {
+    st->cycles = cyc;
+    st->fine_sweeps = cyc * fine_per_cycle;
+    st->action = N;
+    st->rel_action = c->last_rel;
+  }
+  if (check && !(N <= k.tol * N0)) return fail(c, LA_ENOTCONV, "not converged after %d cycles (rel %.3e)", cyc, c->last_rel);
+  return LA_OK;
+}
+
+extern "C" la_status la_step(la_ctx* c, void* psi, int nsteps, double t0, la_step_stats* per_step) {
+  if (!c || !psi || nsteps < 0) return c ? fail(c, LA_EINVAL, "null psi or negative nsteps") : LA_EINVAL;
+  if (!c->have_ham) return fail(c, LA_ESTATE, "la_set_hamiltonian must be called first");
+  const bool dev = is_device_ptr(psi);
+  const size_t bytes = sizeof(double2) * (size_t)c->np0;
+  LA_CUDA(c, cudaMemcpyAsync(c->d_psi, psi, bytes, dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->stream));
+  la_status worst = LA_OK;
+  for (int s = 0; s < nsteps; ++s) {
+    LA_TRY(setup_step(c, t0 + s * c->cfg.dt));
+    la_status st = solve_current(c, 0, per_step ? per_step + s : nullptr);
+    if (st == LA_ENOTCONV) worst = LA_ENOTCONV;
+    else if (st != LA_OK) return st;
+    launch_advance(c->np0, c->d_tm, c->d_c, c->d_psi, c->stream);
+    LA_CHECK_LAUNCH(c);
+  }
+  LA_CUDA(c, cudaMemcpyAsync(psi, c->d_psi, bytes, dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->stream));
+  LA_CUDA(c, cudaStreamSynchronize(c->stream));
+  return worst;
+}
+
+extern "C" la_status la_action(la_ctx* c, double* N, double* rel) {
+  if (!c) return LA_EINVAL;
+  if (!c->have_step) return fail(c, LA_ESTATE, "no step has been computed");
+  if (N) *N = c->last_N;
+  if (rel) *rel = c->last_rel;
+  return LA_OK;
+}
+
+extern "C" la_status la_solve_step(la_ctx* c, const void* psi0, double t0, int ncycles, void* c_out,
+                                   la_step_stats* stats) {
+  if (!c || !psi0 || !c_out || ncycles < 0) return c ? fail(c, LA_EINVAL, "invalid argument") : LA_EINVAL;
+  if (!c->have_ham) return fail(c, LA_ESTATE, "la_set_hamiltonian must be called first");
+  LA_TRY(load_any(c, c->d_psi, psi0, sizeof(double2) * (size_t)c->np0));
+  LA_TRY(setup_step(c, t0));
+  la_status st = solve_current(c, ncycles, stats);
+  if (st != LA_OK && st != LA_ENOTCONV) return st;
+  LA_TRY(store_any(c, c_out, c->d_c, sizeof(double2) * (size_t)c->nunk0));
+  LA_CUDA(c, cudaStreamSynchronize(c->stream));
+  return st;
+}
+
+extern "C" la_status la_residual(la_ctx* c, const void* psi0, double t0, const void* cin, void* r_out,
+                                 double* action) {
+  if (!c || !psi0 || !cin) return c ? fail(c, LA_EINVAL, "invalid argument") : LA_EINVAL;
+  if (!c->have_ham) return fail(c, LA_ESTATE, "la_set_hamiltonian must be called first");
+  LA_TRY(load_any(c, c->d_psi, psi0, sizeof(double2) * (size_t)c->np0));
+  LA_TRY(load_any(c, c->d_c, cin, sizeof(double2) * (size_t)c->nunk0));
+  LA_TRY(setup_step(c, t0));
+  double N = 0.0;
+  LA_TRY(action_now(c, &N));
+  if (action) *action = N;
+  if (r_out) LA_TRY(store_any(c, r_out, c->d_r, sizeof(double2) * (size_t)c->nunk0));
+  LA_CUDA(c, cudaStreamSynchronize(c->stream));
+  return LA_OK;
+}
+
+extern "C" la_status la_relax_colour(la_ctx* c, const void* psi0, double t0, int colour, void* cio) {
+  if (!c || !psi0 || !cio) return c ? fail(c, LA_EINVAL, "invalid argument") : LA_EINVAL;
+  if (colour < 0 || colour >= (1 << c->dim)) return fail(c, LA_EINVAL, "colour out of range");
+  if (!c->have_ham) return fail(c, LA_ESTATE, "la_set_hamiltonian must be called first");
+  LA_TRY(load_any(c, c->d_psi, psi0, sizeof(double2) * (size_t)c->np0));
+  LA_TRY(load_any(c, c->d_c, cio, sizeof(double2) * (size_t)c->nunk0));
+  LA_TRY(setup_step(c, t0));
+  cudaError_t e;
+  if (c->cfg.precision == 0) {
+    LA_TRY(factor_all<double>(c));
+    e = launch_sweep_fine<double>(c->geo[0], c->fine, c->d_tm, c->K, c->d_f, c->d_c, (const double2*)c->d_fac[0],
+                                  colour, c->stream);
+  } else {
+    LA_TRY(factor_all<float>(c));
+    launch_c128_to_c64(c->nunk0, c->d_f, c->d_f32, c->stream);
+    launch_c128_to_c64(c->nunk0, c->d_c, c->d_e32, c->stream);
+    e = launch_sweep_fine<float>(c->geo[0], c->fine, c->d_tm, c->K, c->d_f32, c->d_e32, (const float2*)c->d_fac[0],
+                                 colour, c->stream);
+    LA_CUDA(c, cudaMemsetAsync(c->d_c, 0, sizeof(double2) * (size_t)c->nunk0, c->stream));
+    launch_axpy_c64_to_c128(c->nunk0, c->d_e32, c->d_c, c->stream);
+  }
+  if (e != cudaSuccess) return fail(c, LA_ECUDA, "sweep: %s", cudaGetErrorString(e));
+  LA_CHECK_LAUNCH(c);
+  LA_TRY(store_any(c, cio, c->d_c, sizeof(double2) * (size_t)c->nunk0));
+  LA_CUDA(c, cudaStreamSynchronize(c->stream));
+  int status = 0;
+  LA_CUDA(c, cudaMemcpy(&status, c->d_status, sizeof(int), cudaMemcpyDeviceToHost));
+  if (status) return fail(c, LA_ECUDA, "a subvolume matrix was not positive definite");
+  return LA_OK;
+}
+
+extern "C" la_status la_time_matrices(la_ctx* c, double t0, double* out) {
+  if (!c || !out) return LA_EINVAL;
+  launch_time_matrices(c->d_tm, t0, c->stream);
+  LA_CHECK_LAUNCH(c);
+  TimeMats t;
+  LA_CUDA(c, cudaMemcpyAsync(&t, c->d_tm, sizeof(TimeMats), cudaMemcpyDeviceToHost, c->stream));
+  LA_CUDA(c, cudaStreamSynchronize(c->stream));
+  const int K = c->K, KK = K * K;
+  memcpy(out, t.Ub, sizeof(double) * KK);
+  memcpy(out + KK, t.Qb, sizeof(double) * KK);
+  memcpy(out + 2 * KK, t.Eb, sizeof(double) * KK);
+  memcpy(out + 3 * KK, t.Ub0, sizeof(double) * K);
+  memcpy(out + 3 * KK + K, t.Eb0, sizeof(double) * K);
+  memcpy(out + 3 * KK + 2 * K, t.Wt, sizeof(double) * KK);
+  return LA_OK;
+}

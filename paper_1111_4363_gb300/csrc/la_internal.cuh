@@ -1,0 +1,217 @@
+// Internal declarations of the least-action CUDA library (not part of the C ABI).
+//
+// Notation (Walters, Secs. I-III).  One time step: unknowns c[p, n], p a grid point,
+// n = 1..K the free Legendre time functions b_n = P_n - (-1)^n P_0.  Without the
+// overlap factor h^d the least-action operator is the Kronecker sum
+//     M~ = sum_k S_k (x) T_k,   S = (I, H, X),   T = (i Qb, -Ub, -Eb(t0)),
+// H = T_kin + V0 (FD stencil), X = diag(x_laser).  The normal matrix of the
+// residual norm is  G~ = M~^dagger (I (x) Wt) M~ = sum_{k,k'} (S_k S_k') (x) Theta_kk',
+// Theta_kk' = T_k^dagger Wt T_k'.  Coarse levels keep this form with spatial
+// factors Sigma^l_kk' = I^T Sigma^{l-1}_kk' I (Galerkin, Sec. III), stored as
+// radius-2 box stencils.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stddef.h>
+
+#define LA_KMAX 8          // largest K (free time functions per point)
+#define LA_NPAIR 9         // (k, k') pairs of the Kronecker normal operator
+#define LA_BLK 16          // block size of the subvolume factor layout
+#define LA_NPAD_MAX 128    // largest padded subvolume size (unknowns)
+#define LA_NPTS_MAX 32     // largest number of grid points in one subvolume
+#define LA_NQ_MAX 32       // largest number of Gauss nodes per step
+#define LA_NCOMP_MAX 64    // largest number of pulse components
+
+namespace la {
+
+// Per-context time-basis data, in device global memory.  Static parts are written by the
+// host at init; Eb, Eb0 and Theta are rewritten by k_time_matrices for every step.
+struct TimeMats {
+  int K;
+  int nq;
+  double dt;
+  double Qb[LA_KMAX * LA_KMAX];   // int b_m b_n'          (test m, trial n)
+  double Ub[LA_KMAX * LA_KMAX];   // (dt/2) int b_m b_n
+  double Wt[LA_KMAX * LA_KMAX];   // time part of the residual-norm weight
+  double Ub0[LA_KMAX];            // (dt/2) int b_m P_0
+  double endv[LA_KMAX];           // b_n(+1)
+  double tau[LA_NQ_MAX], wq[LA_NQ_MAX];          // Gauss-Legendre rule on [-1, 1]
+  double bq[LA_NQ_MAX * LA_KMAX];                // b_m(tau_q)
+  int ncomp;
+  double amp[LA_NCOMP_MAX], omega[LA_NCOMP_MAX], tc[LA_NCOMP_MAX], sigma[LA_NCOMP_MAX];
+  // per step
+  double t0;
+  double Eb[LA_KMAX * LA_KMAX];
+  double Eb0[LA_KMAX];
+  double P[LA_NPAIR][LA_KMAX * LA_KMAX];  // R_k^T Wt R_k', R = (Qb, Ub, Eb)
+};
+// Theta_kk' = phase_kk' * P_kk' with phase = conj(alpha_k) alpha_k', alpha = (i, -1, -1):
+// (0,0) -> 1, (0,1),(0,2) -> +i, (1,0),(2,0) -> -i, others 1.
+__host__ __device__ inline int theta_phase(int kk) {  // 0: real +1, 1: +i, 2: -i
+  int k = kk / 3, kp = kk % 3;
+  if (k == 0 && kp != 0) return 1;
+  if (kp == 0 && k != 0) return 2;
+  return 0;
+}
+
+// Geometry of one multigrid level.
+struct LevelGeom {
+  int dim;
+  int n[3];        // points per axis (unused axes 1)
+  int np;          // points
+  int sub[3];      // subvolume extent per axis (unused axes 1)
+  int nb[3];       // subvolumes per axis
+  int nsub;        // subvolumes
+  int npad;        // padded unknowns per subvolume, multiple of LA_BLK
+  int nblk;        // npad / LA_BLK
+  long long fsize; // complex entries per subvolume factor: nblk(nblk+1)/2 * LA_BLK^2
+};
+
+// Finest-level spatial operator: H = -1/2 Laplacian + V0, X = x along laser_axis.
+struct FineOp {
+  int dim;
+  int n[3];
+  double h[3];
+  double ih2[3];   // 1/h^2 (0 on unused axes)
+  double x0[3];    // coordinate of point 0: -(n-1)/2 h
+  double dsum;     // diagonal of the kinetic stencil: sum_a 1/h_a^2
+  int lax;         // laser axis
+  const double* V0;
+};
+
+// index of offset (ox, oy, oz), each in [-2, 2] on used axes and 0 on unused ones, in a radius-2 box
+__host__ __device__ inline int box5_index(int dim, int ox, int oy, int oz) {
+  return dim == 1 ? ox + 2 : (dim == 2 ? (ox + 2) + 5 * (oy + 2) : (ox + 2) + 5 * (oy + 2) + 25 * (oz + 2));
+}
+__host__ __device__ inline int box5_count(int dim) { return dim == 1 ? 5 : (dim == 2 ? 25 : 125); }
+// stencil storage of a coarse level: [point][pair][box5]
+__host__ __device__ inline long long sigma_offset(int p, int kk, int o, int nbox) {
+  return ((long long)p * LA_NPAIR + kk) * nbox + o;
+}
+
+__device__ inline double fine_H(const FineOp& g, int px, int py, int pz, int qx, int qy, int qz) {
+  int dx = qx - px, dy = qy - py, dz = qz - pz;
+  if (dx == 0 && dy == 0 && dz == 0) return g.dsum + g.V0[(pz * g.n[1] + py) * g.n[0] + px];
+  int ad = abs(dx) + abs(dy) + abs(dz);
+  if (ad != 1) return 0.0;
+  if (dx) return -0.5 * g.ih2[0];
+  if (dy) return -0.5 * g.ih2[1];
+  return -0.5 * g.ih2[2];
+}
+__device__ inline double fine_x(const FineOp& g, int px, int py, int pz) {
+  int c = g.lax == 0 ? px : (g.lax == 1 ? py : pz);
+  return g.x0[g.lax] + c * g.h[g.lax];
+}
+__device__ inline bool fine_in(const FineOp& g, int x, int y, int z) {
+  return x >= 0 && y >= 0 && z >= 0 && x < g.n[0] && y < g.n[1] && z < g.n[2];
+}
+// Sigma^0_kk'[p, q] = (S_k S_k')[p, q] for the 9 pairs, p and q inside the grid.
+__device__ inline void fine_sigma(const FineOp& g, int px, int py, int pz, int qx, int qy, int qz, double s[9]) {
+  double Hpq = fine_H(g, px, py, pz, qx, qy, qz);
+  // (H^2)_pq = sum over r in {p, p +- e_a} inside the grid of H_pr H_rq
+  double H2 = 0.0;
+  const int off[7][3] = {{0, 0, 0}, {1, 0, 0}, {-1, 0, 0}, {0, 1, 0}, {0, -1, 0}, {0, 0, 1}, {0, 0, -1}};
+  int nofs = 1 + 2 * g.dim;
+#pragma unroll 1
+  for (int t = 0; t < nofs; ++t) {
+    int rx = px + off[t][0], ry = py + off[t][1], rz = pz + off[t][2];
+    if (!fine_in(g, rx, ry, rz)) continue;
+    int ex = abs(qx - rx), ey = abs(qy - ry), ez = abs(qz - rz);
+    if (ex + ey + ez > 1) continue;
+    H2 += fine_H(g, px, py, pz, rx, ry, rz) * fine_H(g, rx, ry, rz, qx, qy, qz);
+  }
+  bool same = (px == qx && py == qy && pz == qz);
+  double xp = fine_x(g, px, py, pz), xq = fine_x(g, qx, qy, qz);
+  s[0] = same ? 1.0 : 0.0;      // (0,0) I
+  s[1] = Hpq;                   // (0,1) H
+  s[2] = same ? xp : 0.0;       // (0,2) X
+  s[3] = Hpq;                   // (1,0) H
+  s[4] = H2;                    // (1,1) H^2
+  s[5] = Hpq * xq;              // (1,2) H X
+  s[6] = same ? xp : 0.0;       // (2,0) X
+  s[7] = xp * Hpq;              // (2,1) X H
+  s[8] = same ? xp * xp : 0.0;  // (2,2) X^2
+}
+
+// Subvolume b (lexicographic, x fastest) of a level -> origin and extent.
+__device__ inline void subvol_box(const LevelGeom& L, int b, int o[3], int e[3]) {
+  int bx = b % L.nb[0];
+  int rest = b / L.nb[0];
+  int by = rest % L.nb[1];
+  int bz = rest / L.nb[1];
+  int bb[3] = {bx, by, bz};
+  for (int a = 0; a < 3; ++a) {
+    o[a] = bb[a] * L.sub[a];
+    int r = L.n[a] - o[a];
+    e[a] = r < L.sub[a] ? r : L.sub[a];
+  }
+}
+// j-th subvolume of colour `colour` -> subvolume index.  colour bit a = parity of block index on axis a.
+__device__ inline int colour_subvol(const LevelGeom& L, int colour, int j) {
+  int cb[3] = {colour & 1, (colour >> 1) & 1, (colour >> 2) & 1};
+  int cnt[3];
+  for (int a = 0; a < 3; ++a) cnt[a] = (L.nb[a] - cb[a] + 1) / 2;
+  int ix = j % cnt[0];
+  int r = j / cnt[0];
+  int iy = r % cnt[1];
+  int iz = r / cnt[1];
+  int bx = 2 * ix + cb[0], by = 2 * iy + cb[1], bz = 2 * iz + cb[2];
+  return (bz * L.nb[1] + by) * L.nb[0] + bx;
+}
+__host__ inline int colour_count(const LevelGeom& L, int colour) {
+  int c = 1;
+  for (int a = 0; a < 3; ++a) {
+    int cb = (colour >> a) & 1;
+    if (a >= L.dim && cb) return 0;
+    c *= (L.nb[a] - cb + 1) / 2;
+  }
+  return c;
+}
+
+template <typename R> struct C2;
+template <> struct C2<double> { typedef double2 T; };
+template <> struct C2<float> { typedef float2 T; };
+
+// ---------------------------------------------------------------- launch wrappers
+// time basis
+void launch_time_matrices(TimeMats* tm, double t0, cudaStream_t s);
+// grid kernels (FP64 unless noted)
+void launch_rhs(const FineOp& g, const TimeMats* tm, const double2* psi0, double2* f, cudaStream_t s);
+template <typename R>
+void launch_mresid(const FineOp& g, const TimeMats* tm, const typename C2<R>::T* f, const typename C2<R>::T* c,
+                   typename C2<R>::T* r, typename C2<R>::T* z, double* partials, int nblocks_norm, cudaStream_t s);
+template <typename R>
+void launch_mnormal(const FineOp& g, const TimeMats* tm, const typename C2<R>::T* z, typename C2<R>::T* out,
+                    cudaStream_t s);
+template <typename R>
+void launch_gresid(const LevelGeom& L, const TimeMats* tm, const double* sigma, const typename C2<R>::T* gvec,
+                   const typename C2<R>::T* e, typename C2<R>::T* out, cudaStream_t s);
+template <typename R>
+void launch_restrict(const LevelGeom& fine, const LevelGeom& coarse, int K, const typename C2<R>::T* sf,
+                     typename C2<R>::T* gc, cudaStream_t s);
+template <typename R>
+void launch_prolong_add(const LevelGeom& fine, const LevelGeom& coarse, int K, const typename C2<R>::T* ec,
+                        typename C2<R>::T* ef, cudaStream_t s);
+void launch_norm_final(const double* partials, int n, double scale, double* out, cudaStream_t s);
+int norm_blocks(int np);
+void launch_advance(int np, const TimeMats* tm, const double2* c, double2* psi, cudaStream_t s);
+void launch_axpy_c64_to_c128(long long n, const float2* x, double2* y, cudaStream_t s);
+void launch_c128_to_c64(long long n, const double2* x, float2* y, cudaStream_t s);
+// Galerkin coarse stencils
+void launch_galerkin_from_fine(const FineOp& g, const LevelGeom& coarse, double* sigma_c, cudaStream_t s);
+void launch_galerkin_coarse(const LevelGeom& fine, const double* sigma_f, const LevelGeom& coarse, double* sigma_c,
+                            cudaStream_t s);
+// subvolume factorisation and sweeps (dispatch over the padded subvolume size)
+template <typename R>
+cudaError_t launch_factor(const LevelGeom& L, const FineOp* fine, const double* sigma, const TimeMats* tm,
+                          typename C2<R>::T* factors, int* status, cudaStream_t s);
+template <typename R>
+cudaError_t launch_sweep_fine(const LevelGeom& L, const FineOp& g, const TimeMats* tm, int K,
+                              const typename C2<R>::T* f, typename C2<R>::T* c, const typename C2<R>::T* factors,
+                              int colour, cudaStream_t s);
+template <typename R>
+cudaError_t launch_sweep_coarse(const LevelGeom& L, const double* sigma, const TimeMats* tm, int K,
+                                const typename C2<R>::T* gvec, typename C2<R>::T* e,
+                                const typename C2<R>::T* factors, int colour, cudaStream_t s);
+
+}  // namespace la

@@ -1,0 +1,60 @@
+"""The C-ABI library builds for sm_103a, loads without a GPU and exports every declared symbol."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            text = open(os.path.join(ROOT, "include", fn)).read()
+            text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+            names |= set(re.findall(r"\b(la_[a-z_]+)\s*\(", text))
+    return sorted(names)
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ("la_init", "la_set_hamiltonian", "la_step", "la_action", "la_finalize"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol():
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1111_4363_gb300 import binding
+    lib = ctypes.CDLL(binding.LIB_PATH)
+    missing = [n for n in declared_functions() if not hasattr(lib, n)]
+    assert not missing, missing
+    assert b"sm_103a" in binding.lib().la_version()
+    assert set(binding.EXPORTS) <= set(declared_functions())
+
+
+def test_init_rejects_invalid_configs_without_touching_the_gpu():
+    from paper_1111_4363_gb300 import binding as B
+    from paper_1111_4363_gb300 import workloads as wl
+    w = wl.softcore_2d(n=32, levels=3)
+    bad = [dict(dim=4), dict(nt=0), dict(nt=9), dict(dt=0.0), dict(levels=0), dict(max_cycles=0),
+           dict(weight=3), dict(precision=2), dict(laser_axis=2), dict(nu1=0, nu2=0)]
+    for kw in bad:
+        cfg = B.config_from_workload(w, **kw)
+        with pytest.raises(B.LeastActionError) as e:
+            B.Context(cfg)
+        assert e.value.status == B.LA_EINVAL, kw
+    cfg = B.config_from_workload(w)
+    cfg.sub[0] = 1
+    with pytest.raises(B.LeastActionError, match="sub must be"):
+        B.Context(cfg)
+    cfg = B.config_from_workload(w)
+    cfg.n[0] = 30          # not divisible by 2^(levels-1) = 4
+    with pytest.raises(B.LeastActionError, match="divisible"):
+        B.Context(cfg)
+    cfg = B.config_from_workload(w)
+    cfg.sub[0] = cfg.sub[1] = 8   # 64 points per subvolume > 32
+    with pytest.raises(B.LeastActionError):
+        B.Context(cfg)

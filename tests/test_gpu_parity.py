@@ -1,0 +1,179 @@
+"""CUDA path vs the CPU oracle, element by element, through the C ABI (GB300 required)."""
+import numpy as np
+import pytest
+
+from oracle import multigrid, relax, system, timebasis as tb
+from oracle.propagate import numpy_sub
+from paper_1111_4363_gb300 import workloads as wl
+from tests.helpers import gpu_context, oracle_system, ragged_2d, rel_l2, small_3d, to_dev, variant
+
+pytestmark = pytest.mark.gpu
+
+# FP64 tolerance: both sides evaluate the same FP64 expressions in different orders; the local
+# solves amplify rounding by the subvolume condition number (<~1e4 here), so 1e-11 relative L2.
+TOL64 = 1e-11
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+
+
+WORKLOADS = {
+    "1d": lambda: wl.harmonic_1d(),
+    "2d": lambda: wl.softcore_2d(n=32, levels=3),
+    "2d_ragged": lambda: ragged_2d(levels=2),
+    "3d": lambda: small_3d(levels=2),
+}
+
+
+@pytest.mark.parametrize("name", list(WORKLOADS))
+@pytest.mark.parametrize("weight", ["dual", "literal", "identity"])
+def test_time_matrices(name, weight):
+    w = variant(WORKLOADS[name](), weight=weight)
+    ctx = gpu_context(w)
+    prob = system.Problem.from_workload(w)
+    for t0 in (0.0, 1.35):
+        got = ctx.time_matrices(t0)
+        Ub, Qb, Ub0, Eb, Eb0 = system.time_matrices(prob, t0)
+        for key, ref in (("Ub", Ub), ("Qb", Qb), ("Ub0", Ub0), ("Eb", Eb), ("Eb0", Eb0)):
+            assert np.max(np.abs(got[key] - ref)) <= 1e-14 * max(1.0, np.max(np.abs(ref))), key
+        Wref = {"dual": np.linalg.inv(Ub), "literal": Ub, "identity": np.eye(w.nt)}[weight]
+        assert np.max(np.abs(got["Wt"] - Wref)) <= 1e-12 * np.max(np.abs(Wref))
+
+
+@pytest.mark.parametrize("name", list(WORKLOADS))
+def test_action_residual_and_norm(name):
+    w = WORKLOADS[name]()
+    ctx = gpu_context(w)
+    psi0 = wl.initial_state(w).ravel()
+    t0 = 0.4
+    prob, M, f, W = oracle_system(w, psi0, t0)
+    c = wl.random_state(M.shape[1], 11) * 0.05
+    r = np.zeros_like(c)
+    N = ctx.residual(psi0, t0, c, r)
+    r_ref = system.residual(M, f, c)
+    assert rel_l2(r, r_ref) < 1e-13
+    N_ref = system.action_norm(r_ref, W)
+    assert N == pytest.approx(N_ref, rel=1e-12)
+    # c = 0: r = f (the right-hand side carries the initial condition)
+    N0 = ctx.residual(psi0, t0, np.zeros_like(c), r)
+    assert rel_l2(r, f) < 1e-13
+    assert N0 == pytest.approx(system.action_norm(f, W), rel=1e-12)
+
+
+@pytest.mark.parametrize("name", list(WORKLOADS))
+def test_single_colour_pass(name):
+    """One coloured pass of exact subvolume minimisation (factor + sweep kernels) vs the oracle."""
+    w = WORKLOADS[name]()
+    ctx = gpu_context(w)
+    psi0 = wl.initial_state(w).ravel()
+    t0 = 0.25
+    prob, M, f, W = oracle_system(w, psi0, t0)
+    G = (M.conj().T @ W @ M).tocsr()
+    g = M.conj().T @ (W @ f)
+    R = relax.BlockRelaxation(G, prob.shape, numpy_sub(w), prob.K)
+    c0 = wl.random_state(M.shape[1], 3) * 0.05
+    for colour in range(1 << w.dim):
+        ref = c0.copy()
+        R.colour_pass(ref, g, colour)
+        got = c0.copy()
+        ctx.relax_colour(psi0, t0, colour, got)
+        assert rel_l2(got - c0, ref - c0) < 1e-10, colour
+        assert rel_l2(got, ref) < TOL64
+
+
+@pytest.mark.parametrize("name,ncycles", [("1d", 3), ("2d", 2), ("2d_ragged", 2), ("3d", 2)])
+def test_fixed_schedule_iterates(name, ncycles):
+    """ncycles V-cycles (or sweeps) from c = 0 with the identical schedule: same iterate."""
+    w = WORKLOADS[name]()
+    ctx = gpu_context(w)
+    psi0 = wl.initial_state(w).ravel()
+    t0 = 0.1
+    prob, M, f, W = oracle_system(w, psi0, t0)
+    c_ref, hist, cyc, _ = multigrid.solve_step(M, f, W, prob.shape, prob.K, numpy_sub(w), w.levels, w.nu1, w.nu2,
+                                               w.coarse_sweeps, ncycles=ncycles)
+    c = np.zeros(M.shape[1], dtype=np.complex128)
+    st, (cycles, sweeps, N, rel) = ctx.solve_step(psi0, t0, c, ncycles=ncycles)
+    assert cycles == ncycles
+    assert rel_l2(c, c_ref) < TOL64
+    assert N == pytest.approx(hist[-1], rel=1e-9)
+
+
+@pytest.mark.parametrize("name", ["1d", "2d", "3d"])
+def test_converged_step_matches_direct_solve(name):
+    w = WORKLOADS[name]()
+    ctx = gpu_context(w, tol=1e-24, max_cycles=60)
+    psi0 = wl.initial_state(w).ravel()
+    prob, M, f, W = oracle_system(w, psi0, 0.0)
+    cd = system.direct_solve(M, f)
+    c = np.zeros(M.shape[1], dtype=np.complex128)
+    st, (cycles, sweeps, N, rel) = ctx.solve_step(psi0, 0.0, c)
+    assert rel <= 1e-24
+    assert rel_l2(c, cd) < 1e-9
+
+
+def test_multistep_propagation_1d():
+    """20 steps of the 1D harmonic workload to rel action 1e-12 vs the oracle's direct steps."""
+    w = wl.harmonic_1d()
+    ctx = gpu_context(w)
+    psi = wl.initial_state(w).ravel().copy()
+    st, stats = ctx.step(psi, w.nsteps, 0.0, stats=True)
+    assert all(s[3] <= w.tol for s in stats)
+    ref = wl.initial_state(w).ravel()
+    prob = system.Problem.from_workload(w)
+    from oracle import propagate
+    for k in range(w.nsteps):
+        ref, _ = propagate.step_direct(prob, ref, k * w.dt)
+    # the relaxation stops at rel <= 1e-12 (residual ~1e-6 relative); the coefficient error is bounded by it
+    assert rel_l2(psi, ref) < 1e-6
+
+
+def test_step_host_and_device_buffers_agree():
+    import torch
+    w = wl.softcore_2d(n=32, levels=3)
+    ctx = gpu_context(w)
+    psi_h = wl.initial_state(w).ravel().copy()
+    psi_d = to_dev(psi_h.copy())
+    ctx.step(psi_h, 2, 0.0)
+    ctx.step(psi_d, 2, 0.0)
+    assert rel_l2(psi_d.cpu().numpy(), psi_h) < 1e-14
+
+
+def test_mixed_precision_refines_to_fp64_solution():
+    """complex64 factors and V-cycle with FP64 residual refinement reach the FP64 direct solution."""
+    w = wl.softcore_2d(n=32, levels=3)
+    psi0 = wl.initial_state(w).ravel()
+    prob, M, f, W = oracle_system(w, psi0, 0.0)
+    cd = system.direct_solve(M, f)
+    ctx = gpu_context(w, precision=1, tol=1e-22, max_cycles=60)
+    c = np.zeros(M.shape[1], dtype=np.complex128)
+    st, (cycles, sweeps, N, rel) = ctx.solve_step(psi0, 0.0, c)
+    assert rel <= 1e-22
+    assert rel_l2(c, cd) < 1e-9
+    # at the production tolerance the error against the direct solution is that of the FP64 path
+    ctx64 = gpu_context(w, precision=0)
+    c64 = np.zeros_like(c)
+    ctx64.solve_step(psi0, 0.0, c64)
+    ctxm = gpu_context(w, precision=1)
+    cm = np.zeros_like(c)
+    st, (cyc_m, _, _, rel_m) = ctxm.solve_step(psi0, 0.0, cm)
+    assert rel_m <= w.tol
+    assert rel_l2(cm, cd) < 10 * max(rel_l2(c64, cd), 1e-7)
+
+
+def test_action_monotone_over_cycles():
+    w = wl.softcore_2d(n=32, levels=3)
+    ctx = gpu_context(w)
+    psi0 = wl.initial_state(w).ravel()
+    last = None
+    c = np.zeros(32 * 32 * 6, dtype=np.complex128)
+    for ncyc in range(1, 5):
+        st, (cycles, sweeps, N, rel) = ctx.solve_step(psi0, 0.0, c, ncycles=ncyc)
+        if last is not None:
+            assert N <= last * (1 + 1e-12)
+        last = N
