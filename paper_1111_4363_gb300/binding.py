@@ -19,7 +19,8 @@ STATUS_NAMES = {0: "LA_OK", 1: "LA_EINVAL", 2: "LA_ENOMEM", 3: "LA_ECUDA", 4: "L
 WEIGHTS = {"dual": 0, "literal": 1, "identity": 2}
 
 EXPORTS = ["la_init", "la_set_hamiltonian", "la_step", "la_action", "la_solve_step", "la_residual",
-           "la_relax_colour", "la_time_matrices", "la_finalize", "la_last_error", "la_version"]
+           "la_relax_colour", "la_time_matrices", "la_profile_enable", "la_profile_read", "la_finalize",
+           "la_last_error", "la_version"]
 
 
 class LeastActionError(RuntimeError):
@@ -44,6 +45,12 @@ class la_step_stats(C.Structure):
     _fields_ = [("cycles", C.c_int), ("fine_sweeps", C.c_int), ("action", C.c_double), ("rel_action", C.c_double)]
 
 
+class la_profile(C.Structure):
+    _fields_ = [("launches", C.c_longlong), ("n_factor", C.c_int), ("ms_factor", C.c_double),
+                ("flops_factor", C.c_double), ("n_sweep", C.c_int), ("ms_sweep", C.c_double),
+                ("flops_sweep", C.c_double)]
+
+
 _lib = None
 
 
@@ -63,6 +70,8 @@ def lib() -> C.CDLL:
         L.la_residual.argtypes = [vp, vp, d, vp, vp, C.POINTER(d)]
         L.la_relax_colour.argtypes = [vp, vp, d, i, vp]
         L.la_time_matrices.argtypes = [vp, d, C.POINTER(d)]
+        L.la_profile_enable.argtypes = [vp, i]
+        L.la_profile_read.argtypes = [vp, C.POINTER(la_profile)]
         L.la_finalize.argtypes = [vp]
         L.la_last_error.argtypes = [vp]
         L.la_last_error.restype = C.c_char_p
@@ -189,6 +198,14 @@ class Context:
         return {"Ub": out[:KK].reshape(K, K), "Qb": out[KK:2 * KK].reshape(K, K),
                 "Eb": out[2 * KK:3 * KK].reshape(K, K), "Ub0": out[3 * KK:3 * KK + K],
                 "Eb0": out[3 * KK + K:3 * KK + 2 * K], "Wt": out[3 * KK + 2 * K:].reshape(K, K)}
+
+    def profile_enable(self, on: bool = True):
+        return self._check(self._lib.la_profile_enable(self.handle, 1 if on else 0))
+
+    def profile_read(self) -> dict:
+        p = la_profile()
+        self._check(self._lib.la_profile_read(self.handle, C.byref(p)))
+        return {k: getattr(p, k) for k, _ in la_profile._fields_}
 
     def close(self):
         if getattr(self, "handle", None):

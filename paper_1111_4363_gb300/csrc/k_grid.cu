@@ -442,6 +442,15 @@ __global__ void k_c128_to_c64(long long n, const double2* __restrict__ x, float2
 void launch_axpy_c64_to_c128(long long n, const float2* x, double2* y, cudaStream_t s) {
   k_axpy_c64_to_c128<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, x, y);
 }
+__global__ void k_scale_c128(long long n, double a, const double2* __restrict__ x, double2* __restrict__ y) {
+  long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double2 v = x[i];
+  y[i] = make_double2(a * v.x, a * v.y);
+}
+void launch_scale_c128(long long n, double a, const double2* x, double2* y, cudaStream_t s) {
+  k_scale_c128<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, a, x, y);
+}
 void launch_c128_to_c64(long long n, const double2* x, float2* y, cudaStream_t s) {
   k_c128_to_c64<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, x, y);
 }

@@ -1,5 +1,6 @@
 // C ABI of the least-action propagator: context, configuration checks, time-basis constants,
 // and the per-step driver (factorisation, V-cycles, convergence test, step advance).
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -46,7 +47,41 @@ struct la_ctx {
   bool have_step = false;
   double last_N = 0.0, last_rel = 0.0;
   std::vector<void*> allocs;
+  // profiling
+  bool prof = false;
+  long long launches = 0;
+  std::vector<cudaEvent_t> ev_pool;
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_factor, ev_sweep;
+  size_t ev_next = 0;
+  double ms_factor = 0.0, ms_sweep = 0.0;
+  int n_factor = 0, n_sweep = 0;
+  double flops_factor = 0.0, flops_sweep = 0.0;
 };
+
+static cudaEvent_t prof_event(la_ctx* c) {
+  if (c->ev_next == c->ev_pool.size()) {
+    cudaEvent_t e;
+    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+    c->ev_pool.push_back(e);
+  }
+  return c->ev_pool[c->ev_next++];
+}
+// Drain recorded event pairs into the totals (synchronises).
+static void prof_drain(la_ctx* c) {
+  if (c->ev_factor.empty() && c->ev_sweep.empty()) return;
+  cudaStreamSynchronize(c->stream);
+  for (auto& p : c->ev_factor) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, p.first, p.second) == cudaSuccess) { c->ms_factor += ms; ++c->n_factor; }
+  }
+  for (auto& p : c->ev_sweep) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, p.first, p.second) == cudaSuccess) { c->ms_sweep += ms; ++c->n_sweep; }
+  }
+  c->ev_factor.clear();
+  c->ev_sweep.clear();
+  c->ev_next = 0;
+}
 
 static la_status fail(la_ctx* c, la_status s, const char* fmt, ...) {
   char buf[512];
@@ -322,9 +357,54 @@ extern "C" la_status la_init(const la_config* cfg, void* stream, la_ctx** out) {
   return LA_OK;
 }
 
+// algorithmic flops of the finest-level factorisation and of one full sweep
+static void finest_flops(la_ctx* c) {
+  const LevelGeom& G = c->geo[0];
+  double ff = 0.0, fs = 0.0;
+  for (int bz = 0; bz < G.nb[2]; ++bz)
+    for (int by = 0; by < G.nb[1]; ++by)
+      for (int bx = 0; bx < G.nb[0]; ++bx) {
+        int e[3], bb[3] = {bx, by, bz};
+        for (int a = 0; a < 3; ++a) e[a] = std::min(G.sub[a], G.n[a] - bb[a] * G.sub[a]);
+        const double n = (double)e[0] * e[1] * e[2] * c->K;
+        ff += 4.0 / 3.0 * n * n * n;
+        fs += 8.0 * n * n;
+      }
+  c->flops_factor = ff;
+  c->flops_sweep = fs;
+}
+
+extern "C" la_status la_profile_enable(la_ctx* c, int enable) {
+  if (!c) return LA_EINVAL;
+  prof_drain(c);
+  c->prof = enable != 0;
+  if (c->prof) {
+    c->launches = 0;
+    c->ms_factor = c->ms_sweep = 0.0;
+    c->n_factor = c->n_sweep = 0;
+    finest_flops(c);
+  }
+  return LA_OK;
+}
+
+extern "C" la_status la_profile_read(la_ctx* c, la_profile* out) {
+  if (!c || !out) return LA_EINVAL;
+  prof_drain(c);
+  LA_CUDA(c, cudaStreamSynchronize(c->stream));
+  out->launches = c->launches;
+  out->n_factor = c->n_factor;
+  out->ms_factor = c->ms_factor;
+  out->flops_factor = c->flops_factor;
+  out->n_sweep = c->n_sweep;
+  out->ms_sweep = c->ms_sweep;
+  out->flops_sweep = c->flops_sweep;
+  return LA_OK;
+}
+
 extern "C" la_status la_finalize(la_ctx* c) {
   if (!c) return LA_EINVAL;
   cudaStreamSynchronize(c->stream);
+  for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
   for (void* p : c->allocs) cudaFree(p);
   delete c;
   return LA_OK;
@@ -399,9 +479,16 @@ template <typename R>
 static la_status factor_all(la_ctx* c) {
   typedef typename C2<R>::T CT;
   for (int l = 0; l < c->L; ++l) {
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (c->prof && l == 0 && (e0 = prof_event(c)) && (e1 = prof_event(c))) cudaEventRecord(e0, c->stream);
     cudaError_t e = launch_factor<R>(c->geo[l], l == 0 ? &c->fine : nullptr, c->d_sigma[l], c->d_tm,
                                      (CT*)c->d_fac[l], c->d_status, c->stream);
     if (e != cudaSuccess) return fail(c, LA_ECUDA, "factor level %d: %s", l, cudaGetErrorString(e));
+    ++c->launches;
+    if (e1) {
+      cudaEventRecord(e1, c->stream);
+      c->ev_factor.push_back({e0, e1});
+    }
   }
   return LA_OK;
 }
@@ -413,6 +500,9 @@ static la_status sweep_level(la_ctx* c, int l, int nsweeps) {
   for (int s = 0; s < nsweeps; ++s)
     for (int col = 0; col < ncol; ++col) {
       cudaError_t e;
+      if (colour_count(c->geo[l], col) > 0) ++c->launches;
+      cudaEvent_t e0 = nullptr, e1 = nullptr;
+      if (c->prof && l == 0 && (e0 = prof_event(c)) && (e1 = prof_event(c))) cudaEventRecord(e0, c->stream);
       if (l == 0)
         e = launch_sweep_fine<R>(c->geo[0], c->fine, c->d_tm, c->K, Fine<R>::f(c), Fine<R>::e(c),
                                  (const CT*)c->d_fac[0], col, c->stream);
@@ -420,6 +510,10 @@ static la_status sweep_level(la_ctx* c, int l, int nsweeps) {
         e = launch_sweep_coarse<R>(c->geo[l], c->d_sigma[l], c->d_tm, c->K, (const CT*)c->d_g[l], (CT*)c->d_e[l],
                                    (const CT*)c->d_fac[l], col, c->stream);
       if (e != cudaSuccess) return fail(c, LA_ECUDA, "sweep level %d colour %d: %s", l, col, cudaGetErrorString(e));
+      if (e1) {
+        cudaEventRecord(e1, c->stream);
+        c->ev_sweep.push_back({e0, e1});
+      }
     }
   return LA_OK;
 }
@@ -437,18 +531,22 @@ static la_status vcycle(la_ctx* c, int l) {
     launch_mresid<R>(c->fine, c->d_tm, Fine<R>::f(c), Fine<R>::e(c), nullptr, Fine<R>::z(c), nullptr, c->nparts,
                      c->stream);
     launch_mnormal<R>(c->fine, c->d_tm, Fine<R>::z(c), Fine<R>::s(c), c->stream);
+    c->launches += 2;
     sfine = Fine<R>::s(c);
   } else {
     launch_gresid<R>(c->geo[l], c->d_tm, c->d_sigma[l], (const CT*)c->d_g[l], (const CT*)c->d_e[l], (CT*)c->d_sl[l],
                      c->stream);
+    ++c->launches;
     sfine = (CT*)c->d_sl[l];
   }
   launch_restrict<R>(c->geo[l], c->geo[l + 1], c->K, sfine, (CT*)c->d_g[l + 1], c->stream);
+  ++c->launches;
   LA_CHECK_LAUNCH(c);
   LA_CUDA(c, cudaMemsetAsync(c->d_e[l + 1], 0, sizeof(CT) * (size_t)c->geo[l + 1].np * c->K, c->stream));
   LA_TRY(vcycle<R>(c, l + 1));
   CT* efine = l == 0 ? Fine<R>::e(c) : (CT*)c->d_e[l];
   launch_prolong_add<R>(c->geo[l], c->geo[l + 1], c->K, (const CT*)c->d_e[l + 1], efine, c->stream);
+  ++c->launches;
   LA_CHECK_LAUNCH(c);
   return sweep_level<R>(c, l, k.nu2);
 }
@@ -457,6 +555,7 @@ static la_status vcycle(la_ctx* c, int l) {
 static la_status action_now(la_ctx* c, double* N) {
   launch_mresid<double>(c->fine, c->d_tm, c->d_f, c->d_c, c->d_r, nullptr, c->d_partials, c->nparts, c->stream);
   launch_norm_final(c->d_partials, c->nparts, c->nscale, c->d_N, c->stream);
+  c->launches += 2;
   LA_CHECK_LAUNCH(c);
   LA_CUDA(c, cudaMemcpyAsync(N, c->d_N, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
   LA_CUDA(c, cudaStreamSynchronize(c->stream));
@@ -467,6 +566,7 @@ static la_status action_now(la_ctx* c, double* N) {
 static la_status setup_step(la_ctx* c, double t0) {
   launch_time_matrices(c->d_tm, t0, c->stream);
   launch_rhs(c->fine, c->d_tm, c->d_psi, c->d_f, c->stream);
+  c->launches += 2;
   LA_CHECK_LAUNCH(c);
   return LA_OK;
 }
@@ -493,6 +593,7 @@ static la_status solve_current(la_ctx* c, int ncycles, la_step_stats* st) {
       LA_CUDA(c, cudaMemsetAsync(c->d_e32, 0, sizeof(float2) * (size_t)c->nunk0, c->stream));
       LA_TRY(vcycle<float>(c, 0));
       launch_axpy_c64_to_c128(c->nunk0, c->d_e32, c->d_c, c->stream);
+      c->launches += 2;
       LA_CHECK_LAUNCH(c);
     }
     ++cyc;
@@ -531,8 +632,10 @@ extern "C" la_status la_step(la_ctx* c, void* psi, int nsteps, double t0, la_ste
     if (st == LA_ENOTCONV) worst = LA_ENOTCONV;
     else if (st != LA_OK) return st;
     launch_advance(c->np0, c->d_tm, c->d_c, c->d_psi, c->stream);
+    ++c->launches;
     LA_CHECK_LAUNCH(c);
   }
+  prof_drain(c);
   LA_CUDA(c, cudaMemcpyAsync(psi, c->d_psi, bytes, dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->stream));
   LA_CUDA(c, cudaStreamSynchronize(c->stream));
   return worst;
@@ -569,7 +672,12 @@ extern "C" la_status la_residual(la_ctx* c, const void* psi0, double t0, const v
   double N = 0.0;
   LA_TRY(action_now(c, &N));
   if (action) *action = N;
-  if (r_out) LA_TRY(store_any(c, r_out, c->d_r, sizeof(double2) * (size_t)c->nunk0));
+  if (r_out) {
+    // the kernels work with r~ = r / h^d (overlap factor O = h^d dropped); return the paper's r
+    launch_scale_c128(c->nunk0, c->hd, c->d_r, c->d_z, c->stream);
+    LA_CHECK_LAUNCH(c);
+    LA_TRY(store_any(c, r_out, c->d_z, sizeof(double2) * (size_t)c->nunk0));
+  }
   LA_CUDA(c, cudaStreamSynchronize(c->stream));
   return LA_OK;
 }
