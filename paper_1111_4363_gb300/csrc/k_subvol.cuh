@@ -48,27 +48,33 @@ __device__ __forceinline__ void local_coords(int i, const int e[3], int& x, int&
 }
 
 // ======================================================================== factorisation
-// One CTA per subvolume of a level.  Each thread owns E fixed entries of the lower triangle
-// (entries ordered by descending column, so every trailing triangle is spread evenly over the
-// threads) and keeps them in registers through a right-looking Cholesky; per column only the
-// scaled column is exchanged through shared memory.
+// One 256-thread CTA per subvolume of a level.  The padded matrix lives in shared memory as a
+// packed lower triangle; thread (ti, tk) = (tid / 16, tid % 16) owns the entries
+// (16 I + ti, 16 J + tk), J <= I (16 x 16 tile-cyclic), so its block indices are compile-time
+// constants and each column value it reads serves a whole row or column of its tiles.
+// Right-looking Cholesky, two barriers per column: (A) the owners of column j scale it by
+// 1/L_jj and publish it, (B) everyone updates the trailing entries; the owner of the next
+// pivot updates that entry first and computes its reciprocal square root while the other
+// threads are still updating (lookahead), so the pivot chain is off the critical path.
+__host__ __device__ constexpr int tri_index(int r, int c) { return r * (r + 1) / 2 + c; }
+
 template <typename R, int NPAD>
-__global__ void __launch_bounds__(kFactorThreads)
+__global__ void __launch_bounds__(kFactorThreads, 2)
 k_factor(LevelGeom L, FineOp g, int is_fine, int nptsmax, const double* __restrict__ sigma,
          const TimeMats* __restrict__ tm, typename C2<R>::T* __restrict__ factors, int* __restrict__ status) {
   typedef typename C2<R>::T CT;
   constexpr int NTRI = NPAD * (NPAD + 1) / 2;
-  constexpr int E = (NTRI + kFactorThreads - 1) / kFactorThreads;
   constexpr int NB = NPAD / LA_BLK;
   extern __shared__ __align__(16) unsigned char smem[];
   const int K = tm->K, KK = K * K;
-  double* sP = reinterpret_cast<double*>(smem);                      // [9][K*K]
-  double* sSig = sP + LA_NPAIR * LA_KMAX * LA_KMAX;                  // [npts*npts][9]
-  CT* sCol = reinterpret_cast<CT*>(sSig + (((size_t)nptsmax * nptsmax * LA_NPAIR + 1) & ~(size_t)1));  // [NPAD]
-  CT* sDiag = sCol + NPAD;                                           // [NB][256]
-  R* sInvd = reinterpret_cast<R*>(sDiag + NB * LA_BLK * LA_BLK);
+  CT* sA = reinterpret_cast<CT*>(smem);                       // [NTRI] packed lower triangle
+  CT* sCol = sA + NTRI;                                       // [NPAD] scaled column j
+  R* sInv = reinterpret_cast<R*>(sCol + NPAD);                // [4] 1/L_jj, double-buffered
+  double* sP = reinterpret_cast<double*>(sInv + 4);           // [9][K*K]
+  double* sPair = sP + LA_NPAIR * LA_KMAX * LA_KMAX;          // [npts*npts][nv]
+  const int nv = is_fine ? 2 : LA_NPAIR;
 
-  const int tid = threadIdx.x;
+  const int tid = threadIdx.x, ti = tid >> 4, tk = tid & 15;
   const int b = blockIdx.x;
   int o[3], e[3];
   subvol_box(L, b, o, e);
@@ -76,7 +82,6 @@ k_factor(LevelGeom L, FineOp g, int is_fine, int nptsmax, const double* __restri
   const int n = npts * K;
 
   for (int i = tid; i < LA_NPAIR * KK; i += kFactorThreads) sP[i] = tm->P[i / KK][i % KK];
-  for (int i = tid; i < NB * LA_BLK * LA_BLK; i += kFactorThreads) sDiag[i] = mkc<CT>(0, 0);
   const int nbox = box5_count(L.dim);
   for (int t = tid; t < npts * npts; t += kFactorThreads) {
     const int i = t / npts, j = t % npts;
@@ -85,119 +90,140 @@ k_factor(LevelGeom L, FineOp g, int is_fine, int nptsmax, const double* __restri
     local_coords(j, e, jx, jy, jz);
     const int px = o[0] + ix, py = o[1] + iy, pz = o[2] + iz;
     const int qx = o[0] + jx, qy = o[1] + jy, qz = o[2] + jz;
-    double s[LA_NPAIR];
+    double* dst = sPair + (size_t)t * nv;
     if (is_fine) {
-      fine_sigma(g, px, py, pz, qx, qy, qz, s);
+      double s9[LA_NPAIR];
+      fine_sigma(g, px, py, pz, qx, qy, qz, s9);
+      dst[0] = s9[1];   // H_pq
+      dst[1] = s9[4];   // (H^2)_pq
     } else {
       const int dx = qx - px, dy = qy - py, dz = qz - pz;
-      if (abs(dx) <= 2 && abs(dy) <= 2 && abs(dz) <= 2) {
-        const int p = (pz * L.n[1] + py) * L.n[0] + px;
-        const int ofs = box5_index(L.dim, dx, dy, dz);
-        for (int k = 0; k < LA_NPAIR; ++k) s[k] = sigma[sigma_offset(p, k, ofs, nbox)];
-      } else {
-        for (int k = 0; k < LA_NPAIR; ++k) s[k] = 0.0;
-      }
+      const bool near = abs(dx) <= 2 && abs(dy) <= 2 && abs(dz) <= 2;
+      const int p = (pz * L.n[1] + py) * L.n[0] + px;
+      const int ofs = near ? box5_index(L.dim, dx, dy, dz) : 0;
+      for (int k = 0; k < LA_NPAIR; ++k) dst[k] = near ? sigma[sigma_offset(p, k, ofs, nbox)] : 0.0;
     }
-    for (int k = 0; k < LA_NPAIR; ++k) sSig[(size_t)t * LA_NPAIR + k] = s[k];
   }
   __syncthreads();
 
-  // ---- assemble owned entries: G_UU[(i,m),(j,n)] = sum_kk' Sigma_kk'[p_i, p_j] Theta_kk'[m, n]
-  CT a[E];
-  int rc[E];
+  // ---- assemble: G_UU[(i,m),(j,n)] = sum_kk' Sigma_kk'[p_i, p_j] Theta_kk'[m, n]
 #pragma unroll
-  for (int s = 0; s < E; ++s) {
-    const int eidx = tid + s * kFactorThreads;
-    rc[s] = -1;
-    a[s] = mkc<CT>(0, 0);
-    if (eidx < NTRI) {
-      // descending column order: column c holds NPAD - c entries; m = NPAD - c
-      int m = (int)((1.0f + sqrtf(1.0f + 8.0f * (float)eidx)) * 0.5f);
-      while ((m - 1) * m / 2 > eidx) --m;
-      while (m * (m + 1) / 2 <= eidx) ++m;
-      const int c = NPAD - m;
-      const int r = c + (eidx - (m - 1) * m / 2);
-      rc[s] = r | (c << 16);
+  for (int I = 0; I < NB; ++I) {
+#pragma unroll
+    for (int J = 0; J <= I; ++J) {
+      const int r = LA_BLK * I + ti, c = LA_BLK * J + tk;
+      if (I == J && ti < tk) continue;
       double re = 0.0, im = 0.0;
       if (r >= n || c >= n) {
         re = (r == c) ? 1.0 : 0.0;
       } else {
         const int i = r / K, mm = r % K, j = c / K, nn = c % K;
-        const double* sg = sSig + (size_t)(i * npts + j) * LA_NPAIR;
+        double s9[LA_NPAIR];
+        const double* pr = sPair + (size_t)(i * npts + j) * nv;
+        if (is_fine) {
+          int ix, iy, iz, jx, jy, jz;
+          local_coords(i, e, ix, iy, iz);
+          local_coords(j, e, jx, jy, jz);
+          const double xp = fine_x(g, o[0] + ix, o[1] + iy, o[2] + iz);
+          const double xq = fine_x(g, o[0] + jx, o[1] + jy, o[2] + jz);
+          const double same = (i == j) ? 1.0 : 0.0, Hpq = pr[0];
+          s9[0] = same; s9[1] = Hpq; s9[2] = same * xp; s9[3] = Hpq; s9[4] = pr[1];
+          s9[5] = Hpq * xq; s9[6] = same * xp; s9[7] = xp * Hpq; s9[8] = same * xp * xp;
+        } else {
+#pragma unroll
+          for (int kk = 0; kk < LA_NPAIR; ++kk) s9[kk] = pr[kk];
+        }
 #pragma unroll
         for (int kk = 0; kk < LA_NPAIR; ++kk) {
-          const double v = sg[kk] * sP[kk * KK + mm * K + nn];
+          const double v = s9[kk] * sP[kk * KK + mm * K + nn];
           const int ph = theta_phase(kk);
           if (ph == 0) re += v; else if (ph == 1) im += v; else im -= v;
         }
       }
-      a[s] = mkc<CT>((R)re, (R)im);
+      sA[tri_index(r, c)] = mkc<CT>((R)re, (R)im);
     }
-  }
-
-  // ---- right-looking Cholesky, entries resident in registers
-  for (int j = 0; j < NPAD; ++j) {
-    const int diag = j | (j << 16);
-#pragma unroll
-    for (int s = 0; s < E; ++s) {
-      if (rc[s] == diag) {
-        R d2 = a[s].x;
-        if (!(d2 > (R)0)) {
-          atomicOr(status, 1);
-          d2 = (R)1;
-        }
-        const R d = sqrt(d2);
-        a[s] = mkc<CT>(d, (R)0);
-        sInvd[0] = (R)1 / d;
-      }
-    }
-    __syncthreads();
-    const R invd = sInvd[0];
-#pragma unroll
-    for (int s = 0; s < E; ++s) {
-      const int c = rc[s] >> 16, r = rc[s] & 0xffff;
-      if (rc[s] >= 0 && c == j && r > j) {
-        a[s].x *= invd;
-        a[s].y *= invd;
-        sCol[r] = a[s];
-      }
-    }
-    __syncthreads();
-#pragma unroll
-    for (int s = 0; s < E; ++s) {
-      const int c = rc[s] >> 16, r = rc[s] & 0xffff;
-      if (rc[s] >= 0 && c > j) {
-        const CT x = sCol[r], y = sCol[c];
-        // a -= x * conj(y)
-        a[s].x = fma(-x.x, y.x, a[s].x); a[s].x = fma(-x.y, y.y, a[s].x);
-        a[s].y = fma(-x.y, y.x, a[s].y); a[s].y = fma(x.x, y.y, a[s].y);
-      }
-    }
-  }
-
-  // ---- write off-diagonal blocks; diagonal blocks go through shared memory for inversion
-  CT* F = factors + (size_t)b * L.fsize;
-#pragma unroll
-  for (int s = 0; s < E; ++s) {
-    if (rc[s] < 0) continue;
-    const int c = rc[s] >> 16, r = rc[s] & 0xffff;
-    const int I = r / LA_BLK, J = c / LA_BLK;
-    if (I == J) sDiag[I * 256 + (r % LA_BLK) * LA_BLK + (c % LA_BLK)] = a[s];
-    else F[(size_t)(I * (I + 1) / 2 + J) * 256 + (r % LA_BLK) * LA_BLK + (c % LA_BLK)] = a[s];
   }
   __syncthreads();
+  if (tid == 0) {
+    R d2 = sA[0].x;
+    if (!(d2 > (R)0)) { atomicOr(status, 1); d2 = (R)1; }
+    const R inv = rsqrt(d2);
+    sA[0] = mkc<CT>(d2 * inv, (R)0);
+    sInv[0] = inv;
+  }
+  __syncthreads();
+
+  // ---- right-looking Cholesky
+  for (int j = 0; j < NPAD; ++j) {
+    const int J0 = j >> 4, jj = j & 15;
+    // (A) scale and publish column j
+    if (tk == jj) {
+      const R inv = sInv[j & 1];
+#pragma unroll
+      for (int I = 0; I < NB; ++I) {
+        const int r = LA_BLK * I + ti;
+        if (I >= J0 && r > j) {
+          CT v = sA[tri_index(r, j)];
+          v.x *= inv; v.y *= inv;
+          sA[tri_index(r, j)] = v;
+          sCol[r] = v;
+        }
+      }
+    }
+    __syncthreads();
+    // (B) lookahead pivot, then the trailing update
+    const int j1 = j + 1;
+    if (j1 < NPAD) {
+      if (ti == tk && ti == (j1 & 15)) {
+        CT v = sA[tri_index(j1, j1)];
+        const CT x = sCol[j1];
+        R d2 = v.x - (x.x * x.x + x.y * x.y);
+        if (!(d2 > (R)0)) { atomicOr(status, 1); d2 = (R)1; }
+        const R inv = rsqrt(d2);
+        sA[tri_index(j1, j1)] = mkc<CT>(d2 * inv, (R)0);
+        sInv[j1 & 1] = inv;
+      }
+      // runtime bounds: blocks left of the current block column are skipped by uniform
+      // branches, so no FP64 instruction is issued for finished entries
+#pragma unroll 1
+      for (int I = J0; I < NB; ++I) {
+        const int r = LA_BLK * I + ti;
+        if (r <= j) continue;
+        const CT xr = sCol[r];
+        CT* rowp = sA + tri_index(r, 0);
+#pragma unroll 2
+        for (int J = J0; J <= I; ++J) {
+          const int c = LA_BLK * J + tk;
+          if (c <= j || c > r || (r == j1 && c == j1)) continue;
+          const CT y = sCol[c];
+          CT a = rowp[c];
+          a.x = fma(-xr.x, y.x, a.x); a.x = fma(-xr.y, y.y, a.x);
+          a.y = fma(-xr.y, y.x, a.y); a.y = fma(xr.x, y.y, a.y);
+          rowp[c] = a;
+        }
+      }
+    }
+    __syncthreads();
+  }
+
+  // ---- store: off-diagonal blocks as they are, diagonal blocks inverted
+  CT* F = factors + (size_t)b * L.fsize;
+#pragma unroll
+  for (int I = 1; I < NB; ++I)
+#pragma unroll
+    for (int J = 0; J < I; ++J)
+      F[(size_t)(I * (I + 1) / 2 + J) * 256 + ti * LA_BLK + tk] = sA[tri_index(LA_BLK * I + ti, LA_BLK * J + tk)];
   // inv(L_II): thread (I, column jj) solves L_II x = e_jj by forward substitution
   if (tid < NB * LA_BLK) {
-    const int I = tid / LA_BLK, jj = tid % LA_BLK;
-    const CT* Ld = sDiag + I * 256;
+    const int I = tid / LA_BLK, jj = tid % LA_BLK, base = LA_BLK * I;
     CT x[LA_BLK];
 #pragma unroll
     for (int i = 0; i < LA_BLK; ++i) {
       CT acc = mkc<CT>(0, 0);
 #pragma unroll
       for (int k = 0; k < i; ++k)
-        if (k >= jj) cfma(acc, Ld[i * LA_BLK + k], x[k]);
-      const R rinv = (R)1 / Ld[i * LA_BLK + i].x;
+        if (k >= jj) cfma(acc, sA[tri_index(base + i, base + k)], x[k]);
+      const R rinv = (R)1 / sA[tri_index(base + i, base + i)].x;
       if (i < jj) x[i] = mkc<CT>(0, 0);
       else if (i == jj) x[i] = mkc<CT>(rinv, (R)0);
       else x[i] = mkc<CT>(-acc.x * rinv, -acc.y * rinv);
@@ -567,9 +593,10 @@ k_sweep_coarse(LevelGeom L, const double* __restrict__ sigma, const TimeMats* __
 }
 
 // ======================================================================== host dispatch
-inline size_t factor_smem(const LevelGeom& L, int nptsmax, size_t csize) {
-  return sizeof(double) * (LA_NPAIR * LA_KMAX * LA_KMAX + (((size_t)nptsmax * nptsmax * LA_NPAIR + 1) & ~(size_t)1)) +
-         csize * ((size_t)L.npad + (size_t)L.nblk * 256) + 16;
+inline size_t factor_smem(const LevelGeom& L, int nptsmax, size_t csize, bool fine) {
+  const size_t ntri = (size_t)L.npad * (L.npad + 1) / 2;
+  return csize * (ntri + L.npad) + 4 * (csize / 2) +
+         sizeof(double) * (LA_NPAIR * LA_KMAX * LA_KMAX + (size_t)nptsmax * nptsmax * (fine ? 2 : LA_NPAIR));
 }
 inline size_t sweep_fine_smem(const LevelGeom& L, int K, size_t rsize, size_t csize) {
   const int sx = L.sub[0] + 4, sy = L.dim > 1 ? L.sub[1] + 4 : 1, sz = L.dim > 2 ? L.sub[2] + 4 : 1;
@@ -587,7 +614,7 @@ template <typename R, int NPAD>
 cudaError_t launch_factor_n(const LevelGeom& L, const FineOp* fine, const double* sigma, const TimeMats* tm,
                             typename C2<R>::T* factors, int* status, cudaStream_t s) {
   const int nptsmax = L.sub[0] * L.sub[1] * L.sub[2];
-  const size_t smem = factor_smem(L, nptsmax, sizeof(typename C2<R>::T));
+  const size_t smem = factor_smem(L, nptsmax, sizeof(typename C2<R>::T), fine != nullptr);
   auto kern = k_factor<R, NPAD>;
   static bool attr_set = false;
   if (!attr_set) {
