@@ -153,6 +153,22 @@ la_status la_profile_enable(la_ctx* ctx, int enable);
 /* Totals since enabling; synchronises the stream. */
 la_status la_profile_read(la_ctx* ctx, la_profile* out);
 
+/* Residual norm without device allocation.  The paper has no counterpart to this entry point; it
+   exists for callers that may not call cudaMalloc (code running inside a framework that owns all
+   device memory through its own pool, or a process whose device memory budget is already spent).
+   Computes N = r^dagger W r of trial coefficients c (complex128[Np*K]) for initial state psi0
+   (complex128[Np]) at time t0, exactly as la_residual does, but with no context and no allocation:
+   V0, psi0 and c must be device pointers; *action is a host double.  Scratch (per-step time
+   matrices, per-block partial sums, the result) lives in one static device array of about 140 KB
+   that every GPU loading the library keeps until exit; grids of more than LA_NOALLOC_MAX_POINTS
+   points are rejected with LA_EINVAL.  All calls share that array and overwrite it completely, so
+   calls that overlap on the GPU race and must be serialised by the caller.  The first call on a
+   device looks up the array's address with that device current; make it before any stream capture.
+   Synchronises cuda_stream.  Errors: LA_EINVAL (message in la_last_error(NULL)), LA_ECUDA. */
+#define LA_NOALLOC_MAX_POINTS (1 << 22)
+la_status la_action_noalloc(const la_config* cfg, const double* V0, const la_pulse* pulse, const void* psi0,
+                            double t0, const void* c, double* action, void* cuda_stream);
+
 la_status la_finalize(la_ctx* ctx);
 const char* la_last_error(const la_ctx* ctx);
 const char* la_version(void);

@@ -19,8 +19,9 @@ STATUS_NAMES = {0: "LA_OK", 1: "LA_EINVAL", 2: "LA_ENOMEM", 3: "LA_ECUDA", 4: "L
 WEIGHTS = {"dual": 0, "literal": 1, "identity": 2}
 
 EXPORTS = ["la_init", "la_set_hamiltonian", "la_step", "la_action", "la_solve_step", "la_residual",
-           "la_relax_colour", "la_time_matrices", "la_profile_enable", "la_profile_read", "la_finalize",
-           "la_last_error", "la_version"]
+           "la_relax_colour", "la_time_matrices", "la_profile_enable", "la_profile_read", "la_action_noalloc",
+           "la_finalize", "la_last_error", "la_version"]
+NOALLOC_MAX_POINTS = 1 << 22
 
 
 class LeastActionError(RuntimeError):
@@ -72,6 +73,7 @@ def lib() -> C.CDLL:
         L.la_time_matrices.argtypes = [vp, d, C.POINTER(d)]
         L.la_profile_enable.argtypes = [vp, i]
         L.la_profile_read.argtypes = [vp, C.POINTER(la_profile)]
+        L.la_action_noalloc.argtypes = [C.POINTER(la_config), vp, C.POINTER(la_pulse), vp, d, vp, C.POINTER(d), vp]
         L.la_finalize.argtypes = [vp]
         L.la_last_error.argtypes = [vp]
         L.la_last_error.restype = C.c_char_p
@@ -128,6 +130,31 @@ def config_from_workload(w, precision: int = 0, **overrides) -> la_config:
     for k, v in overrides.items():
         setattr(cfg, k, v)
     return cfg
+
+
+def _pulse_struct(pulse):
+    p = la_pulse()
+    keep = []
+    if pulse is not None and pulse.ncomp > 0:
+        for name, src in (("amp", pulse.amp), ("omega", pulse.omega), ("t_center", pulse.t_center),
+                          ("sigma", pulse.sigma)):
+            a = np.ascontiguousarray(np.asarray(src, dtype=np.float64))
+            keep.append(a)
+            setattr(p, name, a.ctypes.data_as(C.POINTER(C.c_double)))
+        p.ncomp = pulse.ncomp
+    return p, keep
+
+
+def action_noalloc(cfg: la_config, V0, pulse, psi0, t0: float, c, stream=None) -> float:
+    """la_action_noalloc: residual norm N of device coefficients c without any device allocation."""
+    L = lib()
+    p, keep = _pulse_struct(pulse)
+    N = C.c_double()
+    st = L.la_action_noalloc(C.byref(cfg), _ptr(V0), C.byref(p), _ptr(psi0), float(t0), _ptr(c), C.byref(N),
+                             _stream_handle(stream))
+    if st != LA_OK:
+        raise LeastActionError(st, L.la_last_error(None).decode())
+    return N.value
 
 
 class Context:

@@ -217,6 +217,19 @@ static thread_local std::string g_init_error = "no error";
 
 extern "C" const char* la_last_error(const la_ctx* ctx) { return ctx ? ctx->err.c_str() : g_init_error.c_str(); }
 
+namespace la {
+// time-basis constants of a configuration without a context (used by la_action_noalloc)
+bool time_constants_for(const la_config& cfg, TimeMats& out) {
+  la_ctx tmp;
+  tmp.cfg = cfg;
+  tmp.K = cfg.nt;
+  if (!build_time_constants(&tmp)) return false;
+  out = tmp.htm;
+  return true;
+}
+void set_thread_error(const char* msg) { g_init_error = msg ? msg : "unknown error"; }
+}  // namespace la
+
 extern "C" la_status la_init(const la_config* cfg, void* stream, la_ctx** out) {
   if (!cfg || !out) return LA_EINVAL;
   *out = nullptr;
