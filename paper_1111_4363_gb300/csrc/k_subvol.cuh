@@ -48,14 +48,13 @@ __device__ __forceinline__ void local_coords(int i, const int e[3], int& x, int&
 }
 
 // ======================================================================== factorisation
-// One 256-thread CTA per subvolume of a level.  The padded matrix lives in shared memory as a
-// packed lower triangle; thread (ti, tk) = (tid / 16, tid % 16) owns the entries
-// (16 I + ti, 16 J + tk), J <= I (16 x 16 tile-cyclic), so its block indices are compile-time
-// constants and each column value it reads serves a whole row or column of its tiles.
-// Right-looking Cholesky, two barriers per column: (A) the owners of column j scale it by
-// 1/L_jj and publish it, (B) everyone updates the trailing entries; the owner of the next
-// pivot updates that entry first and computes its reciprocal square root while the other
-// threads are still updating (lookahead), so the pivot chain is off the critical path.
+// One 256-thread CTA per subvolume of a level; two CTAs per SM.  The padded matrix lives in
+// shared memory as a packed lower triangle (assembled tile-cyclically: thread (tid/16, tid%16)
+// writes entries (16 I + tid/16, 16 J + tid%16)).  Right-looking Cholesky with two barriers per
+// column: (A) column j is scaled by 1/L_jj and published, (B) the trailing triangle is updated
+// with its entries spread linearly over the threads; the thread that updates the next pivot does
+// it first and computes its reciprocal square root while the others are still updating
+// (lookahead), so the pivot chain is off the critical path.
 __host__ __device__ constexpr int tri_index(int r, int c) { return r * (r + 1) / 2 + c; }
 
 template <typename R, int NPAD>
@@ -153,55 +152,43 @@ k_factor(LevelGeom L, FineOp g, int is_fine, int nptsmax, const double* __restri
   }
   __syncthreads();
 
-  // ---- right-looking Cholesky
+  // ---- right-looking Cholesky.  Work of each phase is spread linearly over exactly the active
+  // entries (consecutive threads take consecutive entries of a row), so every issued FP64
+  // instruction has all lanes busy except in the last warp of a phase.
   for (int j = 0; j < NPAD; ++j) {
-    const int J0 = j >> 4, jj = j & 15;
-    // (A) scale and publish column j
-    if (tk == jj) {
+    // (A) scale and publish column j: rows j+1 .. NPAD-1
+    {
       const R inv = sInv[j & 1];
-#pragma unroll
-      for (int I = 0; I < NB; ++I) {
-        const int r = LA_BLK * I + ti;
-        if (I >= J0 && r > j) {
-          CT v = sA[tri_index(r, j)];
-          v.x *= inv; v.y *= inv;
-          sA[tri_index(r, j)] = v;
-          sCol[r] = v;
-        }
+      for (int r = j + 1 + tid; r < NPAD; r += kFactorThreads) {
+        CT v = sA[tri_index(r, j)];
+        v.x *= inv; v.y *= inv;
+        sA[tri_index(r, j)] = v;
+        sCol[r] = v;
       }
     }
     __syncthreads();
-    // (B) lookahead pivot, then the trailing update
-    const int j1 = j + 1;
-    if (j1 < NPAD) {
-      if (ti == tk && ti == (j1 & 15)) {
-        CT v = sA[tri_index(j1, j1)];
-        const CT x = sCol[j1];
-        R d2 = v.x - (x.x * x.x + x.y * x.y);
+    // (B) trailing update of the entries (r, c), j < c <= r; entry e of the trailing triangle
+    // lies in row r = j + m with (m-1) m / 2 <= e < m (m+1) / 2.  e = 0 is the next pivot: its
+    // thread finishes it first and computes the reciprocal square root (lookahead).
+    const int m1 = NPAD - 1 - j;
+    const int T = m1 * (m1 + 1) / 2;
+    for (int e = tid; e < T; e += kFactorThreads) {
+      int m = (int)((1.0f + sqrtf(1.0f + 8.0f * (float)e)) * 0.5f);
+      while ((m - 1) * m / 2 > e) --m;
+      while (m * (m + 1) / 2 <= e) ++m;
+      const int r = j + m, c = j + 1 + (e - (m - 1) * m / 2);
+      const CT xr = sCol[r], y = sCol[c];
+      CT a = sA[tri_index(r, c)];
+      a.x = fma(-xr.x, y.x, a.x); a.x = fma(-xr.y, y.y, a.x);
+      a.y = fma(-xr.y, y.x, a.y); a.y = fma(xr.x, y.y, a.y);
+      if (e == 0) {
+        R d2 = a.x;
         if (!(d2 > (R)0)) { atomicOr(status, 1); d2 = (R)1; }
         const R inv = rsqrt(d2);
-        sA[tri_index(j1, j1)] = mkc<CT>(d2 * inv, (R)0);
-        sInv[j1 & 1] = inv;
+        a = mkc<CT>(d2 * inv, (R)0);
+        sInv[(j + 1) & 1] = inv;
       }
-      // runtime bounds: blocks left of the current block column are skipped by uniform
-      // branches, so no FP64 instruction is issued for finished entries
-#pragma unroll 1
-      for (int I = J0; I < NB; ++I) {
-        const int r = LA_BLK * I + ti;
-        if (r <= j) continue;
-        const CT xr = sCol[r];
-        CT* rowp = sA + tri_index(r, 0);
-#pragma unroll 2
-        for (int J = J0; J <= I; ++J) {
-          const int c = LA_BLK * J + tk;
-          if (c <= j || c > r || (r == j1 && c == j1)) continue;
-          const CT y = sCol[c];
-          CT a = rowp[c];
-          a.x = fma(-xr.x, y.x, a.x); a.x = fma(-xr.y, y.y, a.x);
-          a.y = fma(-xr.y, y.x, a.y); a.y = fma(xr.x, y.y, a.y);
-          rowp[c] = a;
-        }
-      }
+      sA[tri_index(r, c)] = a;
     }
     __syncthreads();
   }
@@ -483,40 +470,57 @@ k_sweep_fine(LevelGeom L, FineOp g, const TimeMats* __restrict__ tm, const typen
 }
 
 // ======================================================================== Galerkin-level sweep
-// rhs = (g - G e)_U with G = sum_kk' Sigma_kk' (x) Theta_kk' from the stored stencils, solve,
-// e_U += delta.
-template <typename R, int NPAD>
-__global__ void __launch_bounds__(kSweepThreads)
-k_sweep_coarse(LevelGeom L, const double* __restrict__ sigma, const TimeMats* __restrict__ tm,
-               const typename C2<R>::T* __restrict__ gvec, typename C2<R>::T* __restrict__ ev,
-               const typename C2<R>::T* __restrict__ factors, int colour) {
+// rhs = (g - G e)_U with G = sum_kk' Sigma_kk' (x) Theta_kk' from the stored stencils.  The
+// subvolume's stencils (|U| x 9 x box) and e on U + 2 are staged in shared memory with
+// coalesced loads first, so the stencil sums run from shared memory with short dependency
+// chains: (i, kk', n) tasks form u = Sigma_kk' e, then (i, m) tasks combine the nine pairs.
+template <typename R>
+struct CoarseSmem {
   typedef typename C2<R>::T CT;
-  extern __shared__ __align__(16) unsigned char smem[];
+  R* P; CT* E; R* Sg; CT* U; CT* Rhs; CT* Y; CT* T; CT* Red;
+};
+__host__ __device__ inline size_t coarse_sg_count(const LevelGeom& L) {
+  const size_t nptsmax = (size_t)L.sub[0] * L.sub[1] * L.sub[2];
+  return (nptsmax * LA_NPAIR * box5_count(L.dim) + 3) & ~(size_t)3;
+}
+__host__ __device__ inline size_t coarse_box_count(const LevelGeom& L) {
+  const int sx = L.sub[0] + 4, sy = L.dim > 1 ? L.sub[1] + 4 : 1, sz = L.dim > 2 ? L.sub[2] + 4 : 1;
+  return (size_t)sx * sy * sz;
+}
+template <typename R>
+__device__ inline CoarseSmem<R> coarse_smem_layout(unsigned char* smem, const LevelGeom& L, int K, int npad) {
+  typedef typename C2<R>::T CT;
+  CoarseSmem<R> m;
+  const size_t nptsmax = (size_t)L.sub[0] * L.sub[1] * L.sub[2];
+  m.P = reinterpret_cast<R*>(smem);
+  m.E = reinterpret_cast<CT*>(m.P + LA_NPAIR * LA_KMAX * LA_KMAX);
+  m.Sg = reinterpret_cast<R*>(m.E + coarse_box_count(L) * K);
+  m.U = reinterpret_cast<CT*>(m.Sg + coarse_sg_count(L));
+  m.Rhs = m.U + nptsmax * LA_NPAIR * K;
+  m.Y = m.Rhs + npad;
+  m.T = m.Y + npad;
+  m.Red = m.T + LA_BLK;
+  return m;
+}
+
+// Fills S.Rhs[0..npad) with (g - G e) on the subvolume with origin o and extent e (0 in padding).
+template <typename R>
+__device__ inline void coarse_rhs(const LevelGeom& L, const double* __restrict__ sigma,
+                                  const TimeMats* __restrict__ tm, const typename C2<R>::T* __restrict__ gvec,
+                                  const typename C2<R>::T* __restrict__ ev, const int o[3], const int e[3], int npad,
+                                  const CoarseSmem<R>& S) {
+  typedef typename C2<R>::T CT;
   const int K = tm->K, KK = K * K;
-  const int tid = threadIdx.x;
-  const int b = colour_subvol(L, colour, blockIdx.x);
-  int o[3], e[3];
-  subvol_box(L, b, o, e);
+  const int tid = threadIdx.x, nthr = blockDim.x;
   int ec[3], oc[3];
   for (int a = 0; a < 3; ++a) {
     const bool used = a < L.dim;
     ec[a] = used ? e[a] + 4 : 1;  oc[a] = used ? o[a] - 2 : o[a];
   }
   const int nbc = ec[0] * ec[1] * ec[2], npts = e[0] * e[1] * e[2];
-  const int sx = L.sub[0] + 4, sy = L.dim > 1 ? L.sub[1] + 4 : 1, sz = L.dim > 2 ? L.sub[2] + 4 : 1;
-  const int nbc_max = sx * sy * sz;
-  const int nptsmax = L.sub[0] * L.sub[1] * L.sub[2];
-
-  R* sP = reinterpret_cast<R*>(smem);                                // [9][K*K]
-  CT* sE = reinterpret_cast<CT*>(sP + LA_NPAIR * LA_KMAX * LA_KMAX); // e on U+2 [nbc_max*K]
-  CT* sTmp = sE + (size_t)nbc_max * K;                               // [nptsmax][9][K]
-  CT* sRhs = sTmp + (size_t)nptsmax * LA_NPAIR * K;
-  CT* sY = sRhs + NPAD;
-  CT* sT = sY + NPAD;
-  CT* sRed = sT + LA_BLK;
-
-  for (int i = tid; i < LA_NPAIR * KK; i += kSweepThreads) sP[i] = (R)tm->P[i / KK][i % KK];
-  for (int t = tid; t < nbc * K; t += kSweepThreads) {
+  const int nbox = box5_count(L.dim);
+  for (int i = tid; i < LA_NPAIR * KK; i += nthr) S.P[i] = (R)tm->P[i / KK][i % KK];
+  for (int t = tid; t < nbc * K; t += nthr) {
     const int i = t / K, m = t % K;
     int lx, ly, lz;
     local_coords(i, ec, lx, ly, lz);
@@ -524,46 +528,43 @@ k_sweep_coarse(LevelGeom L, const double* __restrict__ sigma, const TimeMats* __
     CT v = mkc<CT>(0, 0);
     if (gx >= 0 && gy >= 0 && gz >= 0 && gx < L.n[0] && gy < L.n[1] && gz < L.n[2])
       v = ev[(size_t)((gz * L.n[1] + gy) * L.n[0] + gx) * K + m];
-    sE[t] = v;
+    S.E[t] = v;
   }
-  __syncthreads();
-  const int nbox = box5_count(L.dim);
-  const int rz = L.dim > 2 ? 2 : 0, ry = L.dim > 1 ? 2 : 0;
-  // stage 1: per (U point, pair): Theta_kk' (Sigma_kk' e)_p
-  for (int t = tid; t < npts * LA_NPAIR; t += kSweepThreads) {
-    const int i = t / LA_NPAIR, kk = t % LA_NPAIR;
+  const int per_pt = LA_NPAIR * nbox;
+  for (int t = tid; t < npts * per_pt; t += nthr) {
+    const int i = t / per_pt, w = t % per_pt;
     int lx, ly, lz;
     local_coords(i, e, lx, ly, lz);
     const int p = ((o[2] + lz) * L.n[1] + (o[1] + ly)) * L.n[0] + (o[0] + lx);
-    const int cx = L.dim > 0 ? lx + 2 : lx, cy = L.dim > 1 ? ly + 2 : ly, cz = L.dim > 2 ? lz + 2 : lz;
-    CT u[LA_KMAX];
-    for (int m = 0; m < K; ++m) u[m] = mkc<CT>(0, 0);
-    const double* sg = sigma + sigma_offset(p, kk, 0, nbox);
-    for (int oz = -rz; oz <= rz; ++oz)
-      for (int oy = -ry; oy <= ry; ++oy)
-        for (int ox = -2; ox <= 2; ++ox) {
-          const R s = (R)sg[box5_index(L.dim, ox, oy, oz)];
-          if (s == (R)0) continue;
-          const CT* ep = sE + (size_t)(((cz + oz) * ec[1] + (cy + oy)) * ec[0] + (cx + ox)) * K;
-          for (int m = 0; m < K; ++m) { u[m].x = fma(s, ep[m].x, u[m].x); u[m].y = fma(s, ep[m].y, u[m].y); }
-        }
-    const int ph = theta_phase(kk);
-    for (int m = 0; m < K; ++m) {
-      R vr = 0, vi = 0;
-      for (int nn = 0; nn < K; ++nn) {
-        const R pv = sP[kk * KK + m * K + nn];
-        vr = fma(pv, u[nn].x, vr); vi = fma(pv, u[nn].y, vi);
-      }
-      CT w;
-      if (ph == 0) w = mkc<CT>(vr, vi);
-      else if (ph == 1) w = mkc<CT>(-vi, vr);
-      else w = mkc<CT>(vi, -vr);
-      sTmp[((size_t)i * LA_NPAIR + kk) * K + m] = w;
-    }
+    S.Sg[t] = (R)sigma[(size_t)p * per_pt + w];
   }
   __syncthreads();
-  // stage 2: rhs = g - sum over pairs (fixed order)
-  for (int t = tid; t < NPAD; t += kSweepThreads) {
+  // u[i][kk][n] = sum_o Sigma_kk[p_i][o] e[p_i + o][n]
+  const int ry = L.dim > 1 ? 2 : 0, rz = L.dim > 2 ? 2 : 0;
+  for (int t = tid; t < npts * LA_NPAIR * K; t += nthr) {
+    const int n = t % K, ikk = t / K, kk = ikk % LA_NPAIR, i = ikk / LA_NPAIR;
+    int lx, ly, lz;
+    local_coords(i, e, lx, ly, lz);
+    const int cx = lx + 2, cy = L.dim > 1 ? ly + 2 : ly, cz = L.dim > 2 ? lz + 2 : lz;
+    const R* sg = S.Sg + (size_t)ikk * nbox;
+    R ur0 = 0, ui0 = 0, ur1 = 0, ui1 = 0;
+    int q = 0;
+    for (int oz = -rz; oz <= rz; ++oz)
+      for (int oy = -ry; oy <= ry; ++oy) {
+        const CT* ep = S.E + (size_t)(((cz + oz) * ec[1] + (cy + oy)) * ec[0] + (cx - 2)) * K + n;
+#pragma unroll
+        for (int ox = 0; ox < 5; ++ox, ++q) {
+          const R sv = sg[q];
+          const CT v = ep[ox * K];
+          if (ox & 1) { ur1 = fma(sv, v.x, ur1); ui1 = fma(sv, v.y, ui1); }
+          else { ur0 = fma(sv, v.x, ur0); ui0 = fma(sv, v.y, ui0); }
+        }
+      }
+    S.U[t] = mkc<CT>(ur0 + ur1, ui0 + ui1);
+  }
+  __syncthreads();
+  // rhs[i, m] = g - sum_kk phase_kk sum_n P_kk[m][n] u[i][kk][n]   (pairs in fixed order)
+  for (int t = tid; t < npad; t += nthr) {
     CT out = mkc<CT>(0, 0);
     if (t < npts * K) {
       const int i = t / K, m = t % K;
@@ -571,24 +572,69 @@ k_sweep_coarse(LevelGeom L, const double* __restrict__ sigma, const TimeMats* __
       local_coords(i, e, lx, ly, lz);
       const int p = ((o[2] + lz) * L.n[1] + (o[1] + ly)) * L.n[0] + (o[0] + lx);
       out = gvec[(size_t)p * K + m];
+#pragma unroll
       for (int kk = 0; kk < LA_NPAIR; ++kk) {
-        const CT w = sTmp[((size_t)i * LA_NPAIR + kk) * K + m];
-        out.x -= w.x; out.y -= w.y;
+        const CT* u = S.U + ((size_t)i * LA_NPAIR + kk) * K;
+        const R* pr = S.P + kk * KK + m * K;
+        R vr = 0, vi = 0;
+        for (int nn = 0; nn < K; ++nn) { vr = fma(pr[nn], u[nn].x, vr); vi = fma(pr[nn], u[nn].y, vi); }
+        const int ph = theta_phase(kk);
+        if (ph == 0) { out.x -= vr; out.y -= vi; }
+        else if (ph == 1) { out.x += vi; out.y -= vr; }   // -(i v)
+        else { out.x -= vi; out.y += vr; }                // -(-i v)
       }
     }
-    sRhs[t] = out;
+    S.Rhs[t] = out;
   }
   __syncthreads();
-  subvol_solve<CT, NPAD>(factors + (size_t)b * L.fsize, sRhs, sY, sT, sRed);
-  for (int t = tid; t < npts * K; t += kSweepThreads) {
+}
+
+template <typename R, int NPAD>
+__global__ void __launch_bounds__(kSweepThreads)
+k_sweep_coarse(LevelGeom L, const double* __restrict__ sigma, const TimeMats* __restrict__ tm,
+               const typename C2<R>::T* __restrict__ gvec, typename C2<R>::T* __restrict__ ev,
+               const typename C2<R>::T* __restrict__ factors, int colour) {
+  typedef typename C2<R>::T CT;
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int K = tm->K;
+  const int b = colour_subvol(L, colour, blockIdx.x);
+  int o[3], e[3];
+  subvol_box(L, b, o, e);
+  const int npts = e[0] * e[1] * e[2];
+  CoarseSmem<R> S = coarse_smem_layout<R>(smem, L, K, NPAD);
+  coarse_rhs<R>(L, sigma, tm, gvec, ev, o, e, NPAD, S);
+  subvol_solve<CT, NPAD>(factors + (size_t)b * L.fsize, S.Rhs, S.Y, S.T, S.Red);
+  for (int t = threadIdx.x; t < npts * K; t += kSweepThreads) {
     const int i = t / K, m = t % K;
     int lx, ly, lz;
     local_coords(i, e, lx, ly, lz);
     const size_t gi = (size_t)(((o[2] + lz) * L.n[1] + (o[1] + ly)) * L.n[0] + (o[0] + lx)) * K + m;
     CT v = ev[gi];
-    v.x += sRhs[t].x;
-    v.y += sRhs[t].y;
+    v.x += S.Rhs[t].x;
+    v.y += S.Rhs[t].y;
     ev[gi] = v;
+  }
+}
+
+// s = g - G e on every point of a Galerkin level, one CTA per subvolume (all colours at once).
+template <typename R>
+__global__ void __launch_bounds__(kSweepThreads)
+k_gresid_tiles(LevelGeom L, const double* __restrict__ sigma, const TimeMats* __restrict__ tm,
+               const typename C2<R>::T* __restrict__ gvec, const typename C2<R>::T* __restrict__ ev,
+               typename C2<R>::T* __restrict__ out, int npad) {
+  typedef typename C2<R>::T CT;
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int K = tm->K;
+  int o[3], e[3];
+  subvol_box(L, blockIdx.x, o, e);
+  const int npts = e[0] * e[1] * e[2];
+  CoarseSmem<R> S = coarse_smem_layout<R>(smem, L, K, npad);
+  coarse_rhs<R>(L, sigma, tm, gvec, ev, o, e, npad, S);
+  for (int t = threadIdx.x; t < npts * K; t += kSweepThreads) {
+    const int i = t / K, m = t % K;
+    int lx, ly, lz;
+    local_coords(i, e, lx, ly, lz);
+    out[(size_t)(((o[2] + lz) * L.n[1] + (o[1] + ly)) * L.n[0] + (o[0] + lx)) * K + m] = S.Rhs[t];
   }
 }
 
@@ -604,10 +650,9 @@ inline size_t sweep_fine_smem(const LevelGeom& L, int K, size_t rsize, size_t cs
   return rsize * (4 * LA_KMAX * LA_KMAX + ((nbc + 3) & ~(size_t)3)) + csize * (3 * nbc * K + 2 * (size_t)L.npad + LA_BLK + 128);
 }
 inline size_t sweep_coarse_smem(const LevelGeom& L, int K, size_t rsize, size_t csize) {
-  const int sx = L.sub[0] + 4, sy = L.dim > 1 ? L.sub[1] + 4 : 1, sz = L.dim > 2 ? L.sub[2] + 4 : 1;
-  const size_t nbc = (size_t)sx * sy * sz;
   const size_t nptsmax = (size_t)L.sub[0] * L.sub[1] * L.sub[2];
-  return rsize * (LA_NPAIR * LA_KMAX * LA_KMAX) + csize * (nbc * K + nptsmax * LA_NPAIR * K + 2 * (size_t)L.npad + LA_BLK + 128);
+  return rsize * (LA_NPAIR * LA_KMAX * LA_KMAX + coarse_sg_count(L)) +
+         csize * (coarse_box_count(L) * K + nptsmax * LA_NPAIR * K + 2 * (size_t)L.npad + LA_BLK + 128);
 }
 
 template <typename R, int NPAD>
@@ -661,6 +706,23 @@ cudaError_t launch_sweep_coarse_n(const LevelGeom& L, const double* sigma, const
   }
   if (smem > 227 * 1024) return cudaErrorInvalidValue;
   kern<<<nblocks, kSweepThreads, smem, s>>>(L, sigma, tm, gvec, e, factors, colour);
+  return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t launch_gresid_tiles_r(const LevelGeom& L, const double* sigma, const TimeMats* tm, int K,
+                                  const typename C2<R>::T* gvec, const typename C2<R>::T* e, typename C2<R>::T* out,
+                                  cudaStream_t s) {
+  const size_t smem = sweep_coarse_smem(L, K, sizeof(R), sizeof(typename C2<R>::T));
+  auto kern = k_gresid_tiles<R>;
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+    if (err != cudaSuccess) return err;
+    attr_set = true;
+  }
+  if (smem > 227 * 1024) return cudaErrorInvalidValue;
+  kern<<<L.nsub, kSweepThreads, smem, s>>>(L, sigma, tm, gvec, e, out, L.npad);
   return cudaGetLastError();
 }
 

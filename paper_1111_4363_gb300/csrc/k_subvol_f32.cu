@@ -23,4 +23,9 @@ cudaError_t launch_sweep_coarse<float>(const LevelGeom& L, const double* sigma, 
   LA_NPAD_DISPATCH(L.npad, LA_CALL)
 #undef LA_CALL
 }
+template <>
+cudaError_t launch_gresid_tiles<float>(const LevelGeom& L, const double* sigma, const TimeMats* tm, int K,
+                                     const float2* gvec, const float2* e, float2* out, cudaStream_t s) {
+  return launch_gresid_tiles_r<float>(L, sigma, tm, K, gvec, e, out, s);
+}
 }  // namespace la

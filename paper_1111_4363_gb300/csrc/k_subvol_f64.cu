@@ -23,4 +23,9 @@ cudaError_t launch_sweep_coarse<double>(const LevelGeom& L, const double* sigma,
   LA_NPAD_DISPATCH(L.npad, LA_CALL)
 #undef LA_CALL
 }
+template <>
+cudaError_t launch_gresid_tiles<double>(const LevelGeom& L, const double* sigma, const TimeMats* tm, int K,
+                                     const double2* gvec, const double2* e, double2* out, cudaStream_t s) {
+  return launch_gresid_tiles_r<double>(L, sigma, tm, K, gvec, e, out, s);
+}
 }  // namespace la

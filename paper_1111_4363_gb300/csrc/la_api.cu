@@ -547,8 +547,9 @@ static la_status vcycle(la_ctx* c, int l) {
     c->launches += 2;
     sfine = Fine<R>::s(c);
   } else {
-    launch_gresid<R>(c->geo[l], c->d_tm, c->d_sigma[l], (const CT*)c->d_g[l], (const CT*)c->d_e[l], (CT*)c->d_sl[l],
-                     c->stream);
+    cudaError_t ge = launch_gresid_tiles<R>(c->geo[l], c->d_sigma[l], c->d_tm, c->K, (const CT*)c->d_g[l],
+                                            (const CT*)c->d_e[l], (CT*)c->d_sl[l], c->stream);
+    if (ge != cudaSuccess) return fail(c, LA_ECUDA, "coarse residual level %d: %s", l, cudaGetErrorString(ge));
     ++c->launches;
     sfine = (CT*)c->d_sl[l];
   }

@@ -211,6 +211,10 @@ cudaError_t launch_sweep_fine(const LevelGeom& L, const FineOp& g, const TimeMat
                               const typename C2<R>::T* f, typename C2<R>::T* c, const typename C2<R>::T* factors,
                               int colour, cudaStream_t s);
 template <typename R>
+cudaError_t launch_gresid_tiles(const LevelGeom& L, const double* sigma, const TimeMats* tm, int K,
+                                const typename C2<R>::T* gvec, const typename C2<R>::T* e, typename C2<R>::T* out,
+                                cudaStream_t s);
+template <typename R>
 cudaError_t launch_sweep_coarse(const LevelGeom& L, const double* sigma, const TimeMats* tm, int K,
                                 const typename C2<R>::T* gvec, typename C2<R>::T* e,
                                 const typename C2<R>::T* factors, int colour, cudaStream_t s);
