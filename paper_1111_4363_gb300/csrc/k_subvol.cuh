@@ -68,8 +68,8 @@ k_factor(LevelGeom L, FineOp g, int is_fine, int nptsmax, const double* __restri
   const int K = tm->K, KK = K * K;
   CT* sA = reinterpret_cast<CT*>(smem);                       // [NTRI] packed lower triangle
   CT* sCol = sA + NTRI;                                       // [NPAD] scaled column j
-  R* sInv = reinterpret_cast<R*>(sCol + NPAD);                // [4] 1/L_jj, double-buffered
-  double* sP = reinterpret_cast<double*>(sInv + 4);           // [9][K*K]
+  R* sInv = reinterpret_cast<R*>(sCol + NPAD);                // [NPAD] 1/L_jj
+  double* sP = reinterpret_cast<double*>(sInv + NPAD);        // [9][K*K]
   double* sPair = sP + LA_NPAIR * LA_KMAX * LA_KMAX;          // [npts*npts][nv]
   const int nv = is_fine ? 2 : LA_NPAIR;
 
@@ -158,7 +158,7 @@ k_factor(LevelGeom L, FineOp g, int is_fine, int nptsmax, const double* __restri
   for (int j = 0; j < NPAD; ++j) {
     // (A) scale and publish column j: rows j+1 .. NPAD-1
     {
-      const R inv = sInv[j & 1];
+      const R inv = sInv[j];
       for (int r = j + 1 + tid; r < NPAD; r += kFactorThreads) {
         CT v = sA[tri_index(r, j)];
         v.x *= inv; v.y *= inv;
@@ -186,7 +186,7 @@ k_factor(LevelGeom L, FineOp g, int is_fine, int nptsmax, const double* __restri
         if (!(d2 > (R)0)) { atomicOr(status, 1); d2 = (R)1; }
         const R inv = rsqrt(d2);
         a = mkc<CT>(d2 * inv, (R)0);
-        sInv[(j + 1) & 1] = inv;
+        sInv[j + 1] = inv;
       }
       sA[tri_index(r, c)] = a;
     }
@@ -210,7 +210,7 @@ k_factor(LevelGeom L, FineOp g, int is_fine, int nptsmax, const double* __restri
 #pragma unroll
       for (int k = 0; k < i; ++k)
         if (k >= jj) cfma(acc, sA[tri_index(base + i, base + k)], x[k]);
-      const R rinv = (R)1 / sA[tri_index(base + i, base + i)].x;
+      const R rinv = sInv[base + i];
       if (i < jj) x[i] = mkc<CT>(0, 0);
       else if (i == jj) x[i] = mkc<CT>(rinv, (R)0);
       else x[i] = mkc<CT>(-acc.x * rinv, -acc.y * rinv);
@@ -231,12 +231,13 @@ __device__ __forceinline__ void subvol_solve(const CT* __restrict__ F, CT* rhs, 
     const int r = tid >> 3, l = tid & 7;
     for (int I = 0; I < NB; ++I) {
       const CT* rowblk = F + (size_t)(I * (I + 1) / 2) * 256;
-      CT acc = mkc<CT>(0, 0);
+      CT acc = mkc<CT>(0, 0), acc1 = mkc<CT>(0, 0);
       for (int J = 0; J < I; ++J) {
         const CT* blk = rowblk + J * 256 + r * LA_BLK;
         cfma(acc, blk[l], y[J * LA_BLK + l]);
-        cfma(acc, blk[l + 8], y[J * LA_BLK + l + 8]);
+        cfma(acc1, blk[l + 8], y[J * LA_BLK + l + 8]);
       }
+      acc.x += acc1.x; acc.y += acc1.y;
       acc.x += __shfl_xor_sync(0xffffffffu, acc.x, 1); acc.y += __shfl_xor_sync(0xffffffffu, acc.y, 1);
       acc.x += __shfl_xor_sync(0xffffffffu, acc.x, 2); acc.y += __shfl_xor_sync(0xffffffffu, acc.y, 2);
       acc.x += __shfl_xor_sync(0xffffffffu, acc.x, 4); acc.y += __shfl_xor_sync(0xffffffffu, acc.y, 4);
@@ -256,12 +257,13 @@ __device__ __forceinline__ void subvol_solve(const CT* __restrict__ F, CT* rhs, 
   {  // backward: x_I = inv(L_II)^dagger (y_I - sum_{J>I} L_JI^dagger x_J), x stored in rhs
     const int r = tid & 15, gq = tid >> 4;
     for (int I = NB - 1; I >= 0; --I) {
-      CT acc = mkc<CT>(0, 0);
+      CT acc = mkc<CT>(0, 0), acc1 = mkc<CT>(0, 0);
       for (int J = I + 1; J < NB; ++J) {
         const CT* blk = F + (size_t)(J * (J + 1) / 2 + I) * 256;
         cfma_conj(acc, blk[gq * LA_BLK + r], rhs[J * LA_BLK + gq]);
-        cfma_conj(acc, blk[(gq + 8) * LA_BLK + r], rhs[J * LA_BLK + gq + 8]);
+        cfma_conj(acc1, blk[(gq + 8) * LA_BLK + r], rhs[J * LA_BLK + gq + 8]);
       }
+      acc.x += acc1.x; acc.y += acc1.y;
       red[gq * LA_BLK + r] = acc;
       __syncthreads();
       if (tid < LA_BLK) {
@@ -542,7 +544,7 @@ __device__ inline void coarse_rhs(const LevelGeom& L, const double* __restrict__
   // u[i][kk][n] = sum_o Sigma_kk[p_i][o] e[p_i + o][n]
   const int ry = L.dim > 1 ? 2 : 0, rz = L.dim > 2 ? 2 : 0;
   for (int t = tid; t < npts * LA_NPAIR * K; t += nthr) {
-    const int n = t % K, ikk = t / K, kk = ikk % LA_NPAIR, i = ikk / LA_NPAIR;
+    const int n = t % K, ikk = t / K, i = ikk / LA_NPAIR;
     int lx, ly, lz;
     local_coords(i, e, lx, ly, lz);
     const int cx = lx + 2, cy = L.dim > 1 ? ly + 2 : ly, cz = L.dim > 2 ? lz + 2 : lz;
@@ -641,7 +643,7 @@ k_gresid_tiles(LevelGeom L, const double* __restrict__ sigma, const TimeMats* __
 // ======================================================================== host dispatch
 inline size_t factor_smem(const LevelGeom& L, int nptsmax, size_t csize, bool fine) {
   const size_t ntri = (size_t)L.npad * (L.npad + 1) / 2;
-  return csize * (ntri + L.npad) + 4 * (csize / 2) +
+  return csize * (ntri + L.npad) + (size_t)L.npad * (csize / 2) +
          sizeof(double) * (LA_NPAIR * LA_KMAX * LA_KMAX + (size_t)nptsmax * nptsmax * (fine ? 2 : LA_NPAIR));
 }
 inline size_t sweep_fine_smem(const LevelGeom& L, int K, size_t rsize, size_t csize) {

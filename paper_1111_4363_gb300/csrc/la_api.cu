@@ -56,6 +56,20 @@ struct la_ctx {
   double ms_factor = 0.0, ms_sweep = 0.0;
   int n_factor = 0, n_sweep = 0;
   double flops_factor = 0.0, flops_sweep = 0.0;
+  // one captured cycle (V-cycle + action norm + read-back), replayed on an internal stream
+  struct CycleGraph {
+    cudaGraphExec_t exec = nullptr;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> pairs;  // profiling event nodes
+    long long launches = 0;
+  };
+  CycleGraph cg[2];               // [0] plain, [1] with profiling events
+  bool use_graph = true;
+  bool capturing = false;
+  long long cycles_run = 0;
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> cap_pairs;
+  cudaStream_t cap = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  double* h_N = nullptr;          // pinned
 };
 
 static cudaEvent_t prof_event(la_ctx* c) {
@@ -359,6 +373,15 @@ extern "C" la_status la_init(const la_config* cfg, void* stream, la_ctx** out) {
   ALLOC(c->d_status, sizeof(int));
 #undef ALLOC
   c->fine.V0 = c->d_V0;
+  c->use_graph = getenv("LA_NO_GRAPH") == nullptr;
+  if (cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) != cudaSuccess ||
+      cudaMallocHost(&c->h_N, sizeof(double) * 2) != cudaSuccess) {
+    g_init_error = "stream, event or pinned-buffer creation failed";
+    la_finalize(c);
+    return LA_ECUDA;
+  }
   cudaError_t e = cudaMemcpyAsync(c->d_tm, &c->htm, sizeof(TimeMats), cudaMemcpyHostToDevice, c->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(c->d_status, 0, sizeof(int), c->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(c->d_V0, 0, sizeof(double) * c->np0, c->stream);
@@ -418,6 +441,14 @@ extern "C" la_status la_finalize(la_ctx* c) {
   if (!c) return LA_EINVAL;
   cudaStreamSynchronize(c->stream);
   for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
+  for (auto& g : c->cg) {
+    if (g.exec) cudaGraphExecDestroy(g.exec);
+    for (auto& p : g.pairs) { cudaEventDestroy(p.first); cudaEventDestroy(p.second); }
+  }
+  if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+  if (c->ev_join) cudaEventDestroy(c->ev_join);
+  if (c->cap) cudaStreamDestroy(c->cap);
+  if (c->h_N) cudaFreeHost(c->h_N);
   for (void* p : c->allocs) cudaFree(p);
   delete c;
   return LA_OK;
@@ -515,7 +546,18 @@ static la_status sweep_level(la_ctx* c, int l, int nsweeps) {
       cudaError_t e;
       if (colour_count(c->geo[l], col) > 0) ++c->launches;
       cudaEvent_t e0 = nullptr, e1 = nullptr;
-      if (c->prof && l == 0 && (e0 = prof_event(c)) && (e1 = prof_event(c))) cudaEventRecord(e0, c->stream);
+      if (c->prof && l == 0) {
+        if (c->capturing) {
+          if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) e0 = e1 = nullptr;
+        } else {
+          e0 = prof_event(c);
+          e1 = e0 ? prof_event(c) : nullptr;
+        }
+        if (e1) {
+          if (c->capturing) cudaEventRecordWithFlags(e0, c->stream, cudaEventRecordExternal);
+          else cudaEventRecord(e0, c->stream);
+        }
+      }
       if (l == 0)
         e = launch_sweep_fine<R>(c->geo[0], c->fine, c->d_tm, c->K, Fine<R>::f(c), Fine<R>::e(c),
                                  (const CT*)c->d_fac[0], col, c->stream);
@@ -524,8 +566,10 @@ static la_status sweep_level(la_ctx* c, int l, int nsweeps) {
                                    (const CT*)c->d_fac[l], col, c->stream);
       if (e != cudaSuccess) return fail(c, LA_ECUDA, "sweep level %d colour %d: %s", l, col, cudaGetErrorString(e));
       if (e1) {
-        cudaEventRecord(e1, c->stream);
-        c->ev_sweep.push_back({e0, e1});
+        // inside a capture the records must be graph nodes (external), not capture-internal joins
+        if (c->capturing) cudaEventRecordWithFlags(e1, c->stream, cudaEventRecordExternal);
+        else cudaEventRecord(e1, c->stream);
+        (c->capturing ? c->cap_pairs : c->ev_sweep).push_back({e0, e1});
       }
     }
   return LA_OK;
@@ -566,13 +610,87 @@ static la_status vcycle(la_ctx* c, int l) {
 }
 
 // N of the current FP64 iterate (stores r~ = f~ - M~ c in d_r); synchronises.
-static la_status action_now(la_ctx* c, double* N) {
+static la_status action_enqueue(la_ctx* c) {
   launch_mresid<double>(c->fine, c->d_tm, c->d_f, c->d_c, c->d_r, nullptr, c->d_partials, c->nparts, c->stream);
   launch_norm_final(c->d_partials, c->nparts, c->nscale, c->d_N, c->stream);
   c->launches += 2;
   LA_CHECK_LAUNCH(c);
-  LA_CUDA(c, cudaMemcpyAsync(N, c->d_N, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  LA_CUDA(c, cudaMemcpyAsync(c->h_N, c->d_N, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  return LA_OK;
+}
+static la_status action_now(la_ctx* c, double* N) {
+  LA_TRY(action_enqueue(c));
   LA_CUDA(c, cudaStreamSynchronize(c->stream));
+  *N = *c->h_N;
+  return LA_OK;
+}
+
+// One cycle: V-cycle (FP64) or complex64 correction V-cycle with FP64 refinement, then N.
+static la_status cycle_body(la_ctx* c) {
+  if (c->cfg.precision == 0) {
+    LA_TRY(vcycle<double>(c, 0));
+  } else {
+    // refinement: correction problem M~ e = r~ (r~ from the last action evaluation) in complex64
+    launch_c128_to_c64(c->nunk0, c->d_r, c->d_f32, c->stream);
+    LA_CUDA(c, cudaMemsetAsync(c->d_e32, 0, sizeof(float2) * (size_t)c->nunk0, c->stream));
+    LA_TRY(vcycle<float>(c, 0));
+    launch_axpy_c64_to_c128(c->nunk0, c->d_e32, c->d_c, c->stream);
+    c->launches += 2;
+    LA_CHECK_LAUNCH(c);
+  }
+  return action_enqueue(c);
+}
+
+// Run one cycle and return N.  After the first cycle of a context the cycle is captured once into
+// a CUDA graph and replayed on an internal stream joined to the caller's stream by events.
+static la_status run_cycle(la_ctx* c, double* N) {
+  if (!c->use_graph || c->cycles_run == 0) {
+    LA_TRY(cycle_body(c));
+    LA_CUDA(c, cudaStreamSynchronize(c->stream));
+    *N = *c->h_N;
+    ++c->cycles_run;
+    return LA_OK;
+  }
+  la_ctx::CycleGraph& g = c->cg[c->prof ? 1 : 0];
+  if (!g.exec) {
+    cudaStream_t user = c->stream;
+    const long long l0 = c->launches;
+    c->stream = c->cap;
+    c->capturing = true;
+    c->cap_pairs.clear();
+    LA_CUDA(c, cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal));
+    la_status st = cycle_body(c);
+    cudaGraph_t graph = nullptr;
+    cudaError_t ce = cudaStreamEndCapture(c->cap, &graph);
+    c->stream = user;
+    c->capturing = false;
+    if (st != LA_OK) {
+      if (graph) cudaGraphDestroy(graph);
+      return st;
+    }
+    if (ce != cudaSuccess) return fail(c, LA_ECUDA, "cycle capture: %s", cudaGetErrorString(ce));
+    ce = cudaGraphInstantiate(&g.exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ce != cudaSuccess) return fail(c, LA_ECUDA, "cycle graph instantiate: %s", cudaGetErrorString(ce));
+    g.pairs.swap(c->cap_pairs);
+    g.launches = c->launches - l0;
+    c->launches = l0;
+  }
+  LA_CUDA(c, cudaEventRecord(c->ev_fork, c->stream));
+  LA_CUDA(c, cudaStreamWaitEvent(c->cap, c->ev_fork, 0));
+  LA_CUDA(c, cudaGraphLaunch(g.exec, c->cap));
+  LA_CUDA(c, cudaEventRecord(c->ev_join, c->cap));
+  LA_CUDA(c, cudaStreamWaitEvent(c->stream, c->ev_join, 0));
+  LA_CUDA(c, cudaStreamSynchronize(c->stream));
+  *N = *c->h_N;
+  c->launches += g.launches;
+  if (c->prof) {
+    for (auto& p : g.pairs) {
+      float ms = 0.f;
+      if (cudaEventElapsedTime(&ms, p.first, p.second) == cudaSuccess) { c->ms_sweep += ms; ++c->n_sweep; }
+    }
+  }
+  ++c->cycles_run;
   return LA_OK;
 }
 
@@ -599,19 +717,8 @@ static la_status solve_current(la_ctx* c, int ncycles, la_step_stats* st) {
   const bool check = ncycles <= 0 && k.tol > 0;
   while (cyc < maxc) {
     if (check && N <= k.tol * N0) break;
-    if (k.precision == 0) {
-      LA_TRY(vcycle<double>(c, 0));
-    } else {
-      // refinement: correction problem M~ e = r~ (r~ from the last action evaluation) in complex64
-      launch_c128_to_c64(c->nunk0, c->d_r, c->d_f32, c->stream);
-      LA_CUDA(c, cudaMemsetAsync(c->d_e32, 0, sizeof(float2) * (size_t)c->nunk0, c->stream));
-      LA_TRY(vcycle<float>(c, 0));
-      launch_axpy_c64_to_c128(c->nunk0, c->d_e32, c->d_c, c->stream);
-      c->launches += 2;
-      LA_CHECK_LAUNCH(c);
-    }
+    LA_TRY(run_cycle(c, &N));
     ++cyc;
-    LA_TRY(action_now(c, &N));
   }
   int status = 0;
   LA_CUDA(c, cudaMemcpy(&status, c->d_status, sizeof(int), cudaMemcpyDeviceToHost));
