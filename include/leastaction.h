@@ -72,6 +72,7 @@ typedef struct {
   int precision;        /* 0 = FP64 throughout; 1 = mixed: complex64 factors and V-cycle, FP64
                            residual, action and refinement update */
   int laser_axis;       /* axis of the dipole coupling E(t) x_axis */
+  int ckpt_every;       /* > 0: la_step keeps psi every ckpt_every steps for la_backward; 0: no recording */
 } la_config;
 
 /* Laser field E(t) = sum_k amp[k] * env_k(t) * sin(omega[k] t), env_k = exp(-((t - t_center[k])/sigma[k])^2)
@@ -110,6 +111,17 @@ la_status la_step(la_ctx* ctx, void* psi, int nsteps, double t0, la_step_stats* 
 
 /* N and N/N(0) (Eq. residnorm) of the final iterate of the last time step; synchronises. */
 la_status la_action(la_ctx* ctx, double* action, double* rel_action);
+
+/* Discrete adjoint of the last la_step call (which must have run with ckpt_every > 0).
+   Input dJ_dpsiT (complex128[Np], host or device): the conjugate Wirtinger derivative dJ/dpsi_T^* of a
+   real objective J of the final state.  Output grad_amp (host, ncomp doubles, nullable): dJ/da_j for
+   the pulse amplitudes; dJ_dpsi0 (complex128[Np], host or device, nullable): dJ/dpsi_0^*.
+   Per step, backwards (segments of ckpt_every steps are recomputed from their checkpoint):
+   mu = M^{-dagger} B^T lambda is obtained by relaxing G z = B^T lambda with the step's factors
+   (G = M^dagger W M is Hermitian, so the adjoint is a second relaxation), mu = W M z;
+   dJ/da_j += 2 Re mu^dagger (dF/da_j psi_k - dM/da_j c_k); lambda += F_k^T mu (Sec. I, stationarity
+   and the initial-condition multipliers define M and F).  Errors: LA_ESTATE, LA_EINVAL, LA_ECUDA. */
+la_status la_backward(la_ctx* ctx, const void* dJ_dpsiT, double* grad_amp, void* dJ_dpsi0);
 
 /* One step's coefficients without advancing: relax M c = f for initial state psi0 (complex128[Np])
    at time t0 and write c (complex128[Np*K]).  ncycles > 0 runs exactly that many cycles;

@@ -19,7 +19,7 @@ STATUS_NAMES = {0: "LA_OK", 1: "LA_EINVAL", 2: "LA_ENOMEM", 3: "LA_ECUDA", 4: "L
 WEIGHTS = {"dual": 0, "literal": 1, "identity": 2}
 
 EXPORTS = ["la_init", "la_set_hamiltonian", "la_step", "la_action", "la_solve_step", "la_residual",
-           "la_relax_colour", "la_time_matrices", "la_profile_enable", "la_profile_read", "la_action_noalloc",
+           "la_relax_colour", "la_time_matrices", "la_backward", "la_profile_enable", "la_profile_read", "la_action_noalloc",
            "la_finalize", "la_last_error", "la_version"]
 NOALLOC_MAX_POINTS = 1 << 22
 
@@ -34,7 +34,7 @@ class la_config(C.Structure):
     _fields_ = [("dim", C.c_int), ("n", C.c_int * 3), ("h", C.c_double * 3), ("nt", C.c_int), ("dt", C.c_double),
                 ("sub", C.c_int * 3), ("levels", C.c_int), ("nu1", C.c_int), ("nu2", C.c_int),
                 ("coarse_sweeps", C.c_int), ("max_cycles", C.c_int), ("tol", C.c_double), ("weight", C.c_int),
-                ("precision", C.c_int), ("laser_axis", C.c_int)]
+                ("precision", C.c_int), ("laser_axis", C.c_int), ("ckpt_every", C.c_int)]
 
 
 class la_pulse(C.Structure):
@@ -71,6 +71,7 @@ def lib() -> C.CDLL:
         L.la_residual.argtypes = [vp, vp, d, vp, vp, C.POINTER(d)]
         L.la_relax_colour.argtypes = [vp, vp, d, i, vp]
         L.la_time_matrices.argtypes = [vp, d, C.POINTER(d)]
+        L.la_backward.argtypes = [vp, vp, C.POINTER(d), vp]
         L.la_profile_enable.argtypes = [vp, i]
         L.la_profile_read.argtypes = [vp, C.POINTER(la_profile)]
         L.la_action_noalloc.argtypes = [C.POINTER(la_config), vp, C.POINTER(la_pulse), vp, d, vp, C.POINTER(d), vp]
@@ -208,6 +209,13 @@ class Context:
         st = self._check(self._lib.la_solve_step(self.handle, _ptr(psi0), float(t0), int(ncycles), _ptr(c_out),
                                                  C.byref(rec)), allow=(LA_ENOTCONV,))
         return st, (rec.cycles, rec.fine_sweeps, rec.action, rec.rel_action)
+
+    def backward(self, dJ_dpsiT, ncomp: int, dJ_dpsi0=None) -> np.ndarray:
+        """la_backward: dJ/d(amplitudes) (numpy) and, if given, dJ/dpsi_0^* written into dJ_dpsi0."""
+        g = np.zeros(max(ncomp, 1))
+        self._check(self._lib.la_backward(self.handle, _ptr(dJ_dpsiT), g.ctypes.data_as(C.POINTER(C.c_double)),
+                                          _ptr(dJ_dpsi0)))
+        return g[:ncomp]
 
     def residual(self, psi0, t0: float, c, r_out=None) -> float:
         N = C.c_double()

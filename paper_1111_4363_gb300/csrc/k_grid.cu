@@ -199,7 +199,8 @@ template void launch_mresid<float>(const FineOp&, const TimeMats*, const float2*
 // s = M~^dagger z: s_p = -i Qb^T z_p - Ub (H z)_p - x_p Eb z_p.
 template <typename CT>
 __global__ void __launch_bounds__(256) k_mnormal(FineOp g, const TimeMats* __restrict__ tm,
-                                                 const CT* __restrict__ zin, CT* __restrict__ out) {
+                                                 const CT* __restrict__ zin, CT* __restrict__ out,
+                                                 const CT* __restrict__ yadd) {
   typedef typename CR<CT>::R RR;
   __shared__ RR Qb[LA_KMAX * LA_KMAX], Ub[LA_KMAX * LA_KMAX], Eb[LA_KMAX * LA_KMAX];
   const int K = tm->K;
@@ -225,18 +226,26 @@ __global__ void __launch_bounds__(256) k_mnormal(FineOp g, const TimeMats* __res
       er += e * zp[n].x; ei += e * zp[n].y;
     }
     // -i (qr + i qi) = qi - i qr
-    out[(long long)p * K + m] = cmk<CT>(qi - ur - xl * er, -qr - ui - xl * ei);
+    CT v = cmk<CT>(qi - ur - xl * er, -qr - ui - xl * ei);
+    if (yadd) {
+      const CT ya = yadd[(long long)p * K + m];
+      v.x += ya.x;
+      v.y += ya.y;
+    }
+    out[(long long)p * K + m] = v;
   }
 }
 
 template <typename R>
 void launch_mnormal(const FineOp& g, const TimeMats* tm, const typename C2<R>::T* z, typename C2<R>::T* out,
-                    cudaStream_t s) {
+                    cudaStream_t s, const typename C2<R>::T* yadd) {
   int np = g.n[0] * g.n[1] * g.n[2];
-  k_mnormal<typename C2<R>::T><<<(np + 255) / 256, 256, 0, s>>>(g, tm, z, out);
+  k_mnormal<typename C2<R>::T><<<(np + 255) / 256, 256, 0, s>>>(g, tm, z, out, yadd);
 }
-template void launch_mnormal<double>(const FineOp&, const TimeMats*, const double2*, double2*, cudaStream_t);
-template void launch_mnormal<float>(const FineOp&, const TimeMats*, const float2*, float2*, cudaStream_t);
+template void launch_mnormal<double>(const FineOp&, const TimeMats*, const double2*, double2*, cudaStream_t,
+                                     const double2*);
+template void launch_mnormal<float>(const FineOp&, const TimeMats*, const float2*, float2*, cudaStream_t,
+                                    const float2*);
 
 // ------------------------------------------------------------------ Galerkin-level residual
 // out_p = g_p - sum_{kk'} Theta_kk' sum_o Sigma[p][kk'][o] e_{p+o}  (coarse levels, all points)

@@ -294,7 +294,8 @@ __device__ __forceinline__ void subvol_solve(const CT* __restrict__ F, CT* rhs, 
 template <typename R, int NPAD>
 __global__ void __launch_bounds__(kSweepThreads)
 k_sweep_fine(LevelGeom L, FineOp g, const TimeMats* __restrict__ tm, const typename C2<R>::T* __restrict__ f,
-             typename C2<R>::T* __restrict__ c, const typename C2<R>::T* __restrict__ factors, int colour) {
+             const typename C2<R>::T* __restrict__ yx, typename C2<R>::T* __restrict__ c,
+             const typename C2<R>::T* __restrict__ factors, int colour) {
   typedef typename C2<R>::T CT;
   extern __shared__ __align__(16) unsigned char smem[];
   const int K = tm->K, KK = K * K;
@@ -454,6 +455,11 @@ k_sweep_fine(LevelGeom L, FineOp g, const TimeMats* __restrict__ tm, const typen
       }
       out.x = qi - ur - xl * er;
       out.y = -qr - ui - xl * ei;
+      if (yx) {  // additive right-hand side (adjoint relaxation of G z = y)
+        const CT yv = yx[(size_t)(((o[2] + lz) * g.n[1] + (o[1] + ly)) * g.n[0] + (o[0] + lx)) * K + m];
+        out.x += yv.x;
+        out.y += yv.y;
+      }
     }
     sRhs[t] = out;
   }
@@ -676,8 +682,8 @@ cudaError_t launch_factor_n(const LevelGeom& L, const FineOp* fine, const double
 }
 template <typename R, int NPAD>
 cudaError_t launch_sweep_fine_n(const LevelGeom& L, const FineOp& g, const TimeMats* tm, int K,
-                                const typename C2<R>::T* f, typename C2<R>::T* c, const typename C2<R>::T* factors,
-                                int colour, cudaStream_t s) {
+                                const typename C2<R>::T* f, const typename C2<R>::T* yx, typename C2<R>::T* c,
+                                const typename C2<R>::T* factors, int colour, cudaStream_t s) {
   const int nblocks = colour_count(L, colour);
   if (nblocks == 0) return cudaSuccess;
   const size_t smem = sweep_fine_smem(L, K, sizeof(R), sizeof(typename C2<R>::T));
@@ -689,7 +695,7 @@ cudaError_t launch_sweep_fine_n(const LevelGeom& L, const FineOp& g, const TimeM
     attr_set = true;
   }
   if (smem > 227 * 1024) return cudaErrorInvalidValue;
-  kern<<<nblocks, kSweepThreads, smem, s>>>(L, g, tm, f, c, factors, colour);
+  kern<<<nblocks, kSweepThreads, smem, s>>>(L, g, tm, f, yx, c, factors, colour);
   return cudaGetLastError();
 }
 template <typename R, int NPAD>

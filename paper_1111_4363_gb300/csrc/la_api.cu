@@ -45,6 +45,19 @@ struct la_ctx {
   int nparts = 0;
   bool have_ham = false;
   bool have_step = false;
+  // adjoint relaxation mode: finest-level right-hand side is y (added), not f
+  bool adj = false;
+  const void* adj_y = nullptr;
+  // forward recording for la_backward
+  bool have_rec = false;
+  double rec_t0 = 0.0;
+  int rec_nsteps = 0;
+  double2* d_ckpt = nullptr;        // checkpoints psi_{s C}
+  int ckpt_cap = 0;
+  double2 *d_seg_psi = nullptr, *d_seg_c = nullptr, *d_lam = nullptr, *d_y = nullptr, *d_rho = nullptr;
+  double2* d_gpart = nullptr;
+  double* d_grad = nullptr;
+  int seg_cap = 0;
   double last_N = 0.0, last_rel = 0.0;
   std::vector<void*> allocs;
   // profiling
@@ -266,6 +279,7 @@ extern "C" la_status la_init(const la_config* cfg, void* stream, la_ctx** out) {
   else if (k.weight < 0 || k.weight > 2) bad("weight must be 0, 1 or 2");
   else if (k.precision < 0 || k.precision > 1) bad("precision must be 0 or 1");
   else if (k.laser_axis < 0 || k.laser_axis >= k.dim) bad("laser_axis must be a used axis");
+  else if (k.ckpt_every < 0) bad("ckpt_every must be >= 0");
   if (st == LA_OK) {
     for (int a = 0; a < 3 && st == LA_OK; ++a) {
       if (a < k.dim) {
@@ -559,8 +573,9 @@ static la_status sweep_level(la_ctx* c, int l, int nsweeps) {
         }
       }
       if (l == 0)
-        e = launch_sweep_fine<R>(c->geo[0], c->fine, c->d_tm, c->K, Fine<R>::f(c), Fine<R>::e(c),
-                                 (const CT*)c->d_fac[0], col, c->stream);
+        e = launch_sweep_fine<R>(c->geo[0], c->fine, c->d_tm, c->K, c->adj ? nullptr : Fine<R>::f(c),
+                                 c->adj ? (const CT*)c->adj_y : nullptr, Fine<R>::e(c), (const CT*)c->d_fac[0], col,
+                                 c->stream);
       else
         e = launch_sweep_coarse<R>(c->geo[l], c->d_sigma[l], c->d_tm, c->K, (const CT*)c->d_g[l], (CT*)c->d_e[l],
                                    (const CT*)c->d_fac[l], col, c->stream);
@@ -585,9 +600,11 @@ static la_status vcycle(la_ctx* c, int l) {
   CT* sfine;
   if (l == 0) {
     // normal residual s = M~^dagger Wt (f - M~ e) on the finest level
-    launch_mresid<R>(c->fine, c->d_tm, Fine<R>::f(c), Fine<R>::e(c), nullptr, Fine<R>::z(c), nullptr, c->nparts,
-                     c->stream);
-    launch_mnormal<R>(c->fine, c->d_tm, Fine<R>::z(c), Fine<R>::s(c), c->stream);
+    // (adjoint mode: s = y - G~ e)
+    launch_mresid<R>(c->fine, c->d_tm, c->adj ? nullptr : Fine<R>::f(c), Fine<R>::e(c), nullptr, Fine<R>::z(c),
+                     nullptr, c->nparts, c->stream);
+    launch_mnormal<R>(c->fine, c->d_tm, Fine<R>::z(c), Fine<R>::s(c), c->stream,
+                      c->adj ? (const CT*)c->adj_y : nullptr);
     c->launches += 2;
     sfine = Fine<R>::s(c);
   } else {
@@ -747,7 +764,23 @@ extern "C" la_status la_step(la_ctx* c, void* psi, int nsteps, double t0, la_ste
   const size_t bytes = sizeof(double2) * (size_t)c->np0;
   LA_CUDA(c, cudaMemcpyAsync(c->d_psi, psi, bytes, dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->stream));
   la_status worst = LA_OK;
+  const int C = c->cfg.ckpt_every;
+  if (C > 0 && nsteps > 0) {
+    const int need = (nsteps + C - 1) / C;
+    if (need > c->ckpt_cap) {
+      void* p = nullptr;
+      LA_TRY(dalloc(c, &p, sizeof(double2) * (size_t)c->np0 * need));
+      c->d_ckpt = (double2*)p;
+      c->ckpt_cap = need;
+    }
+    c->rec_t0 = t0;
+    c->rec_nsteps = nsteps;
+    c->have_rec = true;
+  }
   for (int s = 0; s < nsteps; ++s) {
+    if (C > 0 && s % C == 0)
+      LA_CUDA(c, cudaMemcpyAsync(c->d_ckpt + (size_t)(s / C) * c->np0, c->d_psi, bytes, cudaMemcpyDeviceToDevice,
+                                 c->stream));
     LA_TRY(setup_step(c, t0 + s * c->cfg.dt));
     la_status st = solve_current(c, 0, per_step ? per_step + s : nullptr);
     if (st == LA_ENOTCONV) worst = LA_ENOTCONV;
@@ -760,6 +793,118 @@ extern "C" la_status la_step(la_ctx* c, void* psi, int nsteps, double t0, la_ste
   LA_CUDA(c, cudaMemcpyAsync(psi, c->d_psi, bytes, dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->stream));
   LA_CUDA(c, cudaStreamSynchronize(c->stream));
   return worst;
+}
+
+// Relax G~ z = y~ (y~ in d_y) from z = 0 into d_c with the step's factors; on return d_z holds
+// Wt (0 - M~ z) = -mu of the final z.  Stops when |y~ - G~ z|^2 <= tol |y~|^2 or at max_cycles.
+static la_status adjoint_solve(la_ctx* c, int* cycles) {
+  const la_config& k = c->cfg;
+  const long long n = c->nunk0;
+  const int nb = (int)std::min<long long>((n + 255) / 256, 4096);
+  LA_CUDA(c, cudaMemsetAsync(c->d_c, 0, sizeof(double2) * (size_t)n, c->stream));
+  auto rho_norm = [&](double* out) -> la_status {
+    launch_mresid<double>(c->fine, c->d_tm, nullptr, c->d_c, nullptr, c->d_z, nullptr, c->nparts, c->stream);
+    launch_mnormal<double>(c->fine, c->d_tm, c->d_z, c->d_rho, c->stream, c->d_y);
+    launch_norm2_partials(n, c->d_rho, c->d_partials, std::min(nb, c->nparts), c->stream);
+    launch_norm_final(c->d_partials, std::min(nb, c->nparts), 1.0, c->d_N, c->stream);
+    c->launches += 4;
+    LA_CHECK_LAUNCH(c);
+    LA_CUDA(c, cudaMemcpyAsync(c->h_N, c->d_N, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    LA_CUDA(c, cudaStreamSynchronize(c->stream));
+    *out = *c->h_N;
+    return LA_OK;
+  };
+  double N0 = 0.0, N = 0.0;
+  LA_TRY(rho_norm(&N0));
+  N = N0;
+  int cyc = 0;
+  while (cyc < k.max_cycles && N > k.tol * N0) {
+    c->adj = true;
+    la_status st;
+    if (k.precision == 0) {
+      c->adj_y = c->d_y;
+      st = vcycle<double>(c, 0);
+    } else {
+      launch_c128_to_c64(n, c->d_rho, c->d_f32, c->stream);
+      cudaMemsetAsync(c->d_e32, 0, sizeof(float2) * (size_t)n, c->stream);
+      c->adj_y = c->d_f32;
+      st = vcycle<float>(c, 0);
+      launch_axpy_c64_to_c128(n, c->d_e32, c->d_c, c->stream);
+      c->launches += 2;
+    }
+    c->adj = false;
+    c->adj_y = nullptr;
+    LA_TRY(st);
+    ++cyc;
+    LA_TRY(rho_norm(&N));
+  }
+  if (cycles) *cycles = cyc;
+  return LA_OK;
+}
+
+extern "C" la_status la_backward(la_ctx* c, const void* dJ_dpsiT, double* grad_amp, void* dJ_dpsi0) {
+  if (!c || !dJ_dpsiT) return c ? fail(c, LA_EINVAL, "null dJ/dpsi_T") : LA_EINVAL;
+  if (!c->have_rec || c->rec_nsteps < 1)
+    return fail(c, LA_ESTATE, "la_backward needs a preceding la_step with ckpt_every > 0");
+  const int C = c->cfg.ckpt_every, nsteps = c->rec_nsteps, K = c->K;
+  const size_t vb = sizeof(double2) * (size_t)c->np0, cb = sizeof(double2) * (size_t)c->nunk0;
+  if (C > c->seg_cap) {
+    void* p = nullptr;
+    LA_TRY(dalloc(c, &p, vb * C)); c->d_seg_psi = (double2*)p;
+    LA_TRY(dalloc(c, &p, cb * C)); c->d_seg_c = (double2*)p;
+    if (!c->d_lam) {
+      LA_TRY(dalloc(c, &p, vb)); c->d_lam = (double2*)p;
+      LA_TRY(dalloc(c, &p, cb)); c->d_y = (double2*)p;
+      LA_TRY(dalloc(c, &p, cb)); c->d_rho = (double2*)p;
+      LA_TRY(dalloc(c, &p, sizeof(double2) * (size_t)((c->np0 + 255) / 256) * K * (K + 1))); c->d_gpart = (double2*)p;
+      LA_TRY(dalloc(c, &p, sizeof(double) * LA_NCOMP_MAX)); c->d_grad = (double*)p;
+    }
+    c->seg_cap = C;
+  }
+  LA_TRY(load_any(c, c->d_lam, dJ_dpsiT, vb));
+  LA_CUDA(c, cudaMemsetAsync(c->d_grad, 0, sizeof(double) * LA_NCOMP_MAX, c->stream));
+  const int nseg = (nsteps + C - 1) / C;
+  for (int sgm = nseg - 1; sgm >= 0; --sgm) {
+    const int k0 = sgm * C, k1 = std::min(k0 + C, nsteps);
+    // recompute the segment's states and converged coefficients from its checkpoint
+    LA_CUDA(c, cudaMemcpyAsync(c->d_psi, c->d_ckpt + (size_t)sgm * c->np0, vb, cudaMemcpyDeviceToDevice, c->stream));
+    for (int kk = k0; kk < k1; ++kk) {
+      LA_CUDA(c, cudaMemcpyAsync(c->d_seg_psi + (size_t)(kk - k0) * c->np0, c->d_psi, vb, cudaMemcpyDeviceToDevice,
+                                 c->stream));
+      LA_TRY(setup_step(c, c->rec_t0 + kk * c->cfg.dt));
+      la_status st = solve_current(c, 0, nullptr);
+      if (st != LA_OK && st != LA_ENOTCONV) return st;
+      LA_CUDA(c, cudaMemcpyAsync(c->d_seg_c + (size_t)(kk - k0) * c->nunk0, c->d_c, cb, cudaMemcpyDeviceToDevice,
+                                 c->stream));
+      launch_advance(c->np0, c->d_tm, c->d_c, c->d_psi, c->stream);
+      ++c->launches;
+    }
+    // backward through the segment
+    for (int kk = k1 - 1; kk >= k0; --kk) {
+      const double tk = c->rec_t0 + kk * c->cfg.dt;
+      LA_CUDA(c, cudaMemcpyAsync(c->d_psi, c->d_seg_psi + (size_t)(kk - k0) * c->np0, vb, cudaMemcpyDeviceToDevice,
+                                 c->stream));
+      LA_TRY(setup_step(c, tk));
+      if (c->cfg.precision == 0) LA_TRY(factor_all<double>(c));
+      else LA_TRY(factor_all<float>(c));
+      launch_bt_lambda(c->np0, c->d_tm, 1.0 / c->hd, c->d_lam, c->d_y, c->stream);
+      ++c->launches;
+      LA_TRY(adjoint_solve(c, nullptr));
+      launch_grad_contract(c->fine, c->d_tm, K, tk, c->hd, c->d_z, c->d_psi, c->d_seg_c + (size_t)(kk - k0) * c->nunk0,
+                           c->d_gpart, c->d_grad, c->stream);
+      launch_lambda_update(c->fine, c->d_tm, c->hd, c->d_z, c->d_lam, c->stream);
+      c->launches += 3;
+      LA_CHECK_LAUNCH(c);
+    }
+  }
+  if (dJ_dpsi0) LA_TRY(store_any(c, dJ_dpsi0, c->d_lam, vb));
+  if (grad_amp && c->htm.ncomp > 0)
+    LA_CUDA(c, cudaMemcpyAsync(grad_amp, c->d_grad, sizeof(double) * c->htm.ncomp, cudaMemcpyDeviceToHost, c->stream));
+  LA_CUDA(c, cudaStreamSynchronize(c->stream));
+  int status = 0;
+  LA_CUDA(c, cudaMemcpy(&status, c->d_status, sizeof(int), cudaMemcpyDeviceToHost));
+  if (status) return fail(c, LA_ECUDA, "a subvolume matrix was not positive definite");
+  return LA_OK;
 }
 
 extern "C" la_status la_action(la_ctx* c, double* N, double* rel) {
@@ -813,14 +958,14 @@ extern "C" la_status la_relax_colour(la_ctx* c, const void* psi0, double t0, int
   cudaError_t e;
   if (c->cfg.precision == 0) {
     LA_TRY(factor_all<double>(c));
-    e = launch_sweep_fine<double>(c->geo[0], c->fine, c->d_tm, c->K, c->d_f, c->d_c, (const double2*)c->d_fac[0],
-                                  colour, c->stream);
+    e = launch_sweep_fine<double>(c->geo[0], c->fine, c->d_tm, c->K, c->d_f, nullptr, c->d_c,
+                                  (const double2*)c->d_fac[0], colour, c->stream);
   } else {
     LA_TRY(factor_all<float>(c));
     launch_c128_to_c64(c->nunk0, c->d_f, c->d_f32, c->stream);
     launch_c128_to_c64(c->nunk0, c->d_c, c->d_e32, c->stream);
-    e = launch_sweep_fine<float>(c->geo[0], c->fine, c->d_tm, c->K, c->d_f32, c->d_e32, (const float2*)c->d_fac[0],
-                                 colour, c->stream);
+    e = launch_sweep_fine<float>(c->geo[0], c->fine, c->d_tm, c->K, c->d_f32, nullptr, c->d_e32,
+                                 (const float2*)c->d_fac[0], colour, c->stream);
     LA_CUDA(c, cudaMemsetAsync(c->d_c, 0, sizeof(double2) * (size_t)c->nunk0, c->stream));
     launch_axpy_c64_to_c128(c->nunk0, c->d_e32, c->d_c, c->stream);
   }

@@ -182,7 +182,14 @@ void launch_mresid(const FineOp& g, const TimeMats* tm, const typename C2<R>::T*
                    typename C2<R>::T* r, typename C2<R>::T* z, double* partials, int nblocks_norm, cudaStream_t s);
 template <typename R>
 void launch_mnormal(const FineOp& g, const TimeMats* tm, const typename C2<R>::T* z, typename C2<R>::T* out,
-                    cudaStream_t s);
+                    cudaStream_t s, const typename C2<R>::T* yadd = nullptr);
+// adjoint
+void launch_bt_lambda(int np, const TimeMats* tm, double inv_hd, const double2* lam, double2* y, cudaStream_t s);
+void launch_norm2_partials(long long n, const double2* v, double* partials, int nblocks, cudaStream_t s);
+void launch_grad_contract(const FineOp& g, const TimeMats* tm, int K, double t0, double hd, const double2* zneg,
+                          const double2* psi, const double2* c, double2* partials, double* grad, cudaStream_t s);
+void launch_lambda_update(const FineOp& g, const TimeMats* tm, double hd, const double2* zneg, double2* lam,
+                          cudaStream_t s);
 template <typename R>
 void launch_gresid(const LevelGeom& L, const TimeMats* tm, const double* sigma, const typename C2<R>::T* gvec,
                    const typename C2<R>::T* e, typename C2<R>::T* out, cudaStream_t s);
@@ -208,8 +215,8 @@ cudaError_t launch_factor(const LevelGeom& L, const FineOp* fine, const double* 
                           typename C2<R>::T* factors, int* status, cudaStream_t s);
 template <typename R>
 cudaError_t launch_sweep_fine(const LevelGeom& L, const FineOp& g, const TimeMats* tm, int K,
-                              const typename C2<R>::T* f, typename C2<R>::T* c, const typename C2<R>::T* factors,
-                              int colour, cudaStream_t s);
+                              const typename C2<R>::T* f, const typename C2<R>::T* yx, typename C2<R>::T* c,
+                              const typename C2<R>::T* factors, int colour, cudaStream_t s);
 template <typename R>
 cudaError_t launch_gresid_tiles(const LevelGeom& L, const double* sigma, const TimeMats* tm, int K,
                                 const typename C2<R>::T* gvec, const typename C2<R>::T* e, typename C2<R>::T* out,

@@ -1,0 +1,90 @@
+"""la_backward (discrete adjoint on the forward factors) vs the oracle adjoint and finite differences."""
+import dataclasses
+
+import numpy as np
+import pytest
+
+from oracle import adjoint, system
+from paper_1111_4363_gb300 import workloads as wl
+from tests.helpers import gpu_context, rel_l2
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+
+
+def pulsed(kind: str) -> wl.Workload:
+    rng = np.random.default_rng(11)
+    if kind == "1d":
+        w = wl.harmonic_1d()
+        w = dataclasses.replace(w, levels=1)
+    elif kind == "2d":
+        w = wl.softcore_2d(n=16, levels=2)
+        w = dataclasses.replace(w, nt=4)
+    else:
+        w = wl.hydrogen_3d(n=8, nsteps=5, ncomp=3, sub=2)
+        w = dataclasses.replace(w, levels=2)
+    T = 5 * w.dt
+    pulse = wl.Pulse(amp=list(rng.normal(0.0, 0.4, 3)), omega=[1.3, 2.1, 0.7], t_center=[0.0, T / 2, T],
+                     sigma=[T / 2, T / 3, 0.0], axis=0)
+    return dataclasses.replace(w, pulse=pulse)
+
+
+def run_forward(w, precision, psi0, nsteps, ckpt):
+    ctx = gpu_context(w, precision=precision, tol=1e-22, max_cycles=80, ckpt_every=ckpt)
+    psi = psi0.copy()
+    ctx.step(psi, nsteps, 0.0)
+    return ctx, psi
+
+
+@pytest.mark.parametrize("kind,precision", [("1d", 0), ("2d", 0), ("2d", 1), ("3d", 0)])
+def test_backward_matches_oracle_adjoint(kind, precision):
+    w = pulsed(kind)
+    nsteps, ckpt = 5, 2          # segments of 2, 2, 1 steps
+    prob = system.Problem.from_workload(w)
+    psi0 = wl.initial_state(w).ravel()
+    ctx, psiT = run_forward(w, precision, psi0, nsteps, ckpt)
+    _, dJ = adjoint.dipole_objective(prob, psiT)
+    dpsi0 = np.zeros_like(psi0)
+    g = ctx.backward(dJ, w.pulse.ncomp, dpsi0)
+    g_ref, lam_ref = adjoint.gradients(prob, psi0, nsteps)
+    assert rel_l2(g, g_ref) < 1e-8, (g, g_ref)
+    assert rel_l2(dpsi0, lam_ref) < 1e-8
+
+
+def test_backward_matches_finite_differences_of_the_gpu_forward():
+    w = pulsed("2d")
+    nsteps = 4
+    prob = system.Problem.from_workload(w)
+    psi0 = wl.initial_state(w).ravel()
+    ctx, psiT = run_forward(w, 0, psi0, nsteps, 3)
+    _, dJ = adjoint.dipole_objective(prob, psiT)
+    g = ctx.backward(dJ, w.pulse.ncomp)
+    eps = 1e-4
+    fd = np.zeros(w.pulse.ncomp)
+    for j in range(w.pulse.ncomp):
+        vals = []
+        for sgn in (1, -1):
+            amp = list(w.pulse.amp)
+            amp[j] += sgn * eps
+            w2 = dataclasses.replace(w, pulse=dataclasses.replace(w.pulse, amp=amp))
+            _, pT = run_forward(w2, 0, psi0, nsteps, 0)
+            vals.append(system.dipole(prob, pT))
+        fd[j] = (vals[0] - vals[1]) / (2 * eps)
+    np.testing.assert_allclose(g, fd, rtol=1e-6, atol=1e-9 * np.max(np.abs(fd)))
+
+
+def test_backward_requires_a_recorded_forward():
+    from paper_1111_4363_gb300 import binding as B
+    w = pulsed("1d")
+    ctx = gpu_context(w)
+    with pytest.raises(B.LeastActionError) as e:
+        ctx.backward(np.zeros(w.npoints, dtype=np.complex128), w.pulse.ncomp)
+    assert e.value.status == B.LA_ESTATE
