@@ -219,14 +219,15 @@ def run_ours(args):
 def oracle_cycle_rate(w: wl.Workload, budget_s: float):
     """Time the CPU oracle on the workload: one step's setup, then V-cycles until ``budget_s`` is used."""
     from oracle import multigrid, system
-    from oracle.propagate import numpy_sub
+    from oracle.propagate import numpy_coarse_sub, numpy_sub
     prob = system.Problem.from_workload(w)
     psi0 = wl.initial_state(w).ravel()
     t_a = time.perf_counter()
     M, f, W = system.assemble(prob, 0.0, psi0, w.weight)
     G0 = (M.conj().T @ W @ M).tocsr()
     g0 = M.conj().T @ (W @ f)
-    hier = multigrid.Hierarchy(G0, prob.shape, prob.K, numpy_sub(w), w.levels, w.nu1, w.nu2, w.coarse_sweeps)
+    hier = multigrid.Hierarchy(G0, prob.shape, prob.K, numpy_sub(w), w.levels, w.nu1, w.nu2, w.coarse_sweeps,
+                                     numpy_coarse_sub(w))
     setup_s = time.perf_counter() - t_a
     c = np.zeros(M.shape[1], dtype=np.complex128)
     ncyc = 0
@@ -260,14 +261,15 @@ def run_reference(args):
     cores = len(os.sched_getaffinity(0))
     # each step = one oracle V-cycle on the full workload after an untimed setup; bounded to a few minutes
     from oracle import multigrid, system
-    from oracle.propagate import numpy_sub
+    from oracle.propagate import numpy_coarse_sub, numpy_sub
     prob = system.Problem.from_workload(w)
     psi0 = wl.initial_state(w).ravel()
     t_a = time.perf_counter()
     M, f, W = system.assemble(prob, 0.0, psi0, w.weight)
     G0 = (M.conj().T @ W @ M).tocsr()
     g0 = M.conj().T @ (W @ f)
-    hier = multigrid.Hierarchy(G0, prob.shape, prob.K, numpy_sub(w), w.levels, w.nu1, w.nu2, w.coarse_sweeps)
+    hier = multigrid.Hierarchy(G0, prob.shape, prob.K, numpy_sub(w), w.levels, w.nu1, w.nu2, w.coarse_sweeps,
+                                     numpy_coarse_sub(w))
     setup_s = time.perf_counter() - t_a
     c = np.zeros(M.shape[1], dtype=np.complex128)
     for _ in range(min(args.warmup, 1)):

@@ -73,6 +73,7 @@ typedef struct {
                            residual, action and refinement update */
   int laser_axis;       /* axis of the dipole coupling E(t) x_axis */
   int ckpt_every;       /* > 0: la_step keeps psi every ckpt_every steps for la_backward; 0: no recording */
+  int coarse_sub[3];    /* subvolume extent on the Galerkin levels (>= 2 on used axes); 0 = same as sub */
 } la_config;
 
 /* Laser field E(t) = sum_k amp[k] * env_k(t) * sin(omega[k] t), env_k = exp(-((t - t_center[k])/sigma[k])^2)

@@ -44,7 +44,7 @@ def interpolation(coarse_shape, K: int) -> sp.csr_matrix:
 class Hierarchy:
     """Levels 0 (finest) .. L-1, each with its Galerkin operator and block relaxation."""
 
-    def __init__(self, G0, shape0, K, sub, levels, nu1=1, nu2=1, coarse_sweeps=2):
+    def __init__(self, G0, shape0, K, sub, levels, nu1=1, nu2=1, coarse_sweeps=2, coarse_sub=None):
         self.K, self.L = K, levels
         self.nu1, self.nu2, self.coarse_sweeps = nu1, nu2, coarse_sweeps
         self.shapes = [tuple(shape0)]
@@ -59,7 +59,9 @@ class Hierarchy:
             self.I.append(Il)
             self.G.append((Il.T @ self.G[-1] @ Il).tocsr())
             self.shapes.append(coarse)
-        self.relax = [relax.BlockRelaxation(G, s, sub, K) for G, s in zip(self.G, self.shapes)]
+        # the finest level uses ``sub``; Galerkin levels use ``coarse_sub`` when given
+        subs = [sub] + [coarse_sub if coarse_sub is not None else sub] * (levels - 1)
+        self.relax = [relax.BlockRelaxation(G, s, sb, K) for G, s, sb in zip(self.G, self.shapes, subs)]
 
     def vcycle(self, l, x, g, after_colour=None):
         """Improve x for G_l x = g by one V(nu1, nu2) cycle rooted at level l."""
@@ -89,14 +91,14 @@ class Hierarchy:
 
 
 def solve_step(M, f, W, shape, K, sub, levels, nu1, nu2, coarse_sweeps, ncycles=None, tol=None,
-               max_cycles=200, after_colour=None, c0=None):
+               max_cycles=200, after_colour=None, c0=None, coarse_sub=None):
     """Relax from c0 (default 0) by V-cycles; returns (c, history of N, cycles run).
 
     Exactly ``ncycles`` cycles when given, else until N(c)/N(0) <= tol or ``max_cycles``.
     """
     G0 = (M.conj().T @ W @ M).tocsr()
     g0 = M.conj().T @ (W @ f)
-    hier = Hierarchy(G0, shape, K, sub, levels, nu1, nu2, coarse_sweeps)
+    hier = Hierarchy(G0, shape, K, sub, levels, nu1, nu2, coarse_sweeps, coarse_sub)
     c = np.zeros(M.shape[1], dtype=np.complex128) if c0 is None else c0.astype(np.complex128).copy()
     N0 = system.action_norm(f, W)
     hist = [system.action_norm(system.residual(M, f, c), W)]

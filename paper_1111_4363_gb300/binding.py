@@ -34,7 +34,8 @@ class la_config(C.Structure):
     _fields_ = [("dim", C.c_int), ("n", C.c_int * 3), ("h", C.c_double * 3), ("nt", C.c_int), ("dt", C.c_double),
                 ("sub", C.c_int * 3), ("levels", C.c_int), ("nu1", C.c_int), ("nu2", C.c_int),
                 ("coarse_sweeps", C.c_int), ("max_cycles", C.c_int), ("tol", C.c_double), ("weight", C.c_int),
-                ("precision", C.c_int), ("laser_axis", C.c_int), ("ckpt_every", C.c_int)]
+                ("precision", C.c_int), ("laser_axis", C.c_int), ("ckpt_every", C.c_int),
+                ("coarse_sub", C.c_int * 3)]
 
 
 class la_pulse(C.Structure):
@@ -128,6 +129,9 @@ def config_from_workload(w, precision: int = 0, **overrides) -> la_config:
     cfg.weight = WEIGHTS[w.weight]
     cfg.precision = precision
     cfg.laser_axis = w.pulse.axis if w.pulse is not None else 0
+    if getattr(w, "coarse_sub", None) is not None:
+        for a in range(w.dim):
+            cfg.coarse_sub[a] = w.coarse_sub[a]
     for k, v in overrides.items():
         setattr(cfg, k, v)
     return cfg

@@ -286,6 +286,7 @@ extern "C" la_status la_init(const la_config* cfg, void* stream, la_ctx** out) {
         if (k.n[a] < 1) bad("n must be >= 1 on used axes");
         else if (!(k.h[a] > 0)) bad("h must be positive on used axes");
         else if (k.sub[a] < 2) bad("sub must be >= 2 on used axes (same-colour subvolumes must not interact)");
+        else if (k.coarse_sub[a] == 1 || k.coarse_sub[a] < 0) bad("coarse_sub must be 0 or >= 2 on used axes");
         else if (k.n[a] % (1 << (k.levels - 1))) bad("n must be divisible by 2^(levels-1) on used axes");
       } else if (k.n[a] != 1) bad("unused axes must have n = 1");
     }
@@ -298,9 +299,13 @@ extern "C" la_status la_init(const la_config* cfg, void* stream, la_ctx** out) {
   c->K = k.nt;
   c->L = k.levels;
   c->dim = k.dim;
-  int subpts = 1;
-  for (int a = 0; a < k.dim; ++a) subpts *= k.sub[a];
-  if (subpts > LA_NPTS_MAX || round_npad(subpts * k.nt) < 0) {
+  int subpts = 1, csubpts = 1;
+  for (int a = 0; a < k.dim; ++a) {
+    subpts *= k.sub[a];
+    csubpts *= k.coarse_sub[a] > 0 ? k.coarse_sub[a] : k.sub[a];
+  }
+  if (subpts > LA_NPTS_MAX || round_npad(subpts * k.nt) < 0 || csubpts > LA_NPTS_MAX ||
+      round_npad(csubpts * k.nt) < 0) {
     g_init_error = "invalid configuration: a subvolume may hold at most 32 points and 128 unknowns";
     delete c;
     return LA_EINVAL;
@@ -331,12 +336,12 @@ extern "C" la_status la_init(const la_config* cfg, void* stream, la_ctx** out) {
     G.np = 1;
     for (int a = 0; a < 3; ++a) {
       G.n[a] = a < k.dim ? (g.n[a] >> l) : 1;
-      G.sub[a] = a < k.dim ? k.sub[a] : 1;
+      G.sub[a] = a < k.dim ? ((l > 0 && k.coarse_sub[a] > 0) ? k.coarse_sub[a] : k.sub[a]) : 1;
       G.nb[a] = (G.n[a] + G.sub[a] - 1) / G.sub[a];
       G.np *= G.n[a];
     }
     G.nsub = G.nb[0] * G.nb[1] * G.nb[2];
-    G.npad = round_npad(subpts * k.nt);
+    G.npad = round_npad((l > 0 ? csubpts : subpts) * k.nt);
     G.nblk = G.npad / LA_BLK;
     G.fsize = (long long)G.nblk * (G.nblk + 1) / 2 * LA_BLK * LA_BLK;
   }
@@ -536,7 +541,20 @@ template <> struct Fine<float> {
 template <typename R>
 static la_status factor_all(la_ctx* c) {
   typedef typename C2<R>::T CT;
-  for (int l = 0; l < c->L; ++l) {
+  // Galerkin levels are factored on the internal stream, concurrently with the finest level
+  // (their few CTAs would otherwise leave most SMs idle); joined before returning.
+  const bool side = !c->capturing && c->L > 1 && c->cap;
+  if (side) {
+    LA_CUDA(c, cudaEventRecord(c->ev_fork, c->stream));
+    LA_CUDA(c, cudaStreamWaitEvent(c->cap, c->ev_fork, 0));
+    for (int l = 1; l < c->L; ++l) {
+      cudaError_t e = launch_factor<R>(c->geo[l], nullptr, c->d_sigma[l], c->d_tm, (CT*)c->d_fac[l], c->d_status,
+                                       c->cap);
+      if (e != cudaSuccess) return fail(c, LA_ECUDA, "factor level %d: %s", l, cudaGetErrorString(e));
+      ++c->launches;
+    }
+  }
+  for (int l = 0; l < (side ? 1 : c->L); ++l) {
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (c->prof && l == 0 && (e0 = prof_event(c)) && (e1 = prof_event(c))) cudaEventRecord(e0, c->stream);
     cudaError_t e = launch_factor<R>(c->geo[l], l == 0 ? &c->fine : nullptr, c->d_sigma[l], c->d_tm,
@@ -547,6 +565,10 @@ static la_status factor_all(la_ctx* c) {
       cudaEventRecord(e1, c->stream);
       c->ev_factor.push_back({e0, e1});
     }
+  }
+  if (side) {
+    LA_CUDA(c, cudaEventRecord(c->ev_join, c->cap));
+    LA_CUDA(c, cudaStreamWaitEvent(c->stream, c->ev_join, 0));
   }
   return LA_OK;
 }

@@ -47,7 +47,7 @@ class Workload:
     h: Tuple[float, float, float]    # spacing per axis
     nt: int                          # K: free Legendre time functions per point
     dt: float
-    sub: Tuple[int, int, int]        # subvolume extent in points per axis
+    sub: Tuple[int, int, int]        # subvolume extent in points per axis (finest level)
     levels: int                      # multigrid levels (1 = single-level relaxation)
     nu1: int = 1
     nu2: int = 1
@@ -61,6 +61,7 @@ class Workload:
     pulse: Optional[Pulse] = None
     psi_kind: str = "gaussian"       # "displaced_noisy" | "gaussian"
     seed: int = 0
+    coarse_sub: Optional[Tuple[int, int, int]] = None   # subvolume extent on Galerkin levels (None: sub)
 
     @property
     def shape(self) -> Tuple[int, ...]:
@@ -155,10 +156,10 @@ def harmonic_1d() -> Workload:
 def softcore_2d(n: int = 256, levels: int = 4, nsteps: int = 200) -> Workload:
     """2D, n x n points, h = 0.2, soft-core Coulomb -1/sqrt(r^2+1), laser 0.05 sin(0.057 t) x, K = 6."""
     return Workload(name=f"2d_softcore_{n}x{n}_K6", dim=2, n=(n, n, 1), h=(0.2, 0.2, 1.0), nt=6, dt=0.05,
-                    sub=(4, 4, 1), levels=levels, nu1=1, nu2=1, coarse_sweeps=2, max_cycles=60, tol=1e-10,
+                    sub=(4, 4, 1), levels=levels, nu1=1, nu2=1, coarse_sweeps=1, max_cycles=60, tol=1e-10,
                     nsteps=nsteps, potential="softcore", softcore_a=1.0,
                     pulse=Pulse(amp=[0.05], omega=[0.057], t_center=[0.0], sigma=[0.0], axis=0),
-                    psi_kind="gaussian", seed=0)
+                    psi_kind="gaussian", seed=0, coarse_sub=(2, 2, 1))
 
 
 def batched_2d(index: int) -> Workload:

@@ -88,3 +88,24 @@ def test_backward_requires_a_recorded_forward():
     with pytest.raises(B.LeastActionError) as e:
         ctx.backward(np.zeros(w.npoints, dtype=np.complex128), w.pulse.ncomp)
     assert e.value.status == B.LA_ESTATE
+
+
+def test_autograd_function_gradients():
+    """Gradients through torch.autograd (dipole objective written in torch) equal the oracle's."""
+    import torch
+    from paper_1111_4363_gb300 import autograd as A
+    w = pulsed("2d")
+    nsteps = 3
+    prob = system.Problem.from_workload(w)
+    psi0_np = wl.initial_state(w).ravel()
+    ctx = gpu_context(w, tol=1e-22, max_cycles=80, ckpt_every=2)
+    V0 = torch.tensor(wl.potential(w).ravel(), dtype=torch.float64, device="cuda")
+    amp = torch.tensor(w.pulse.amp, dtype=torch.float64, requires_grad=True)
+    psi0 = torch.from_numpy(psi0_np.copy()).cuda().requires_grad_(True)
+    psiT = A.propagate(ctx, V0, w.pulse, amp, psi0, nsteps)
+    x = torch.from_numpy(prob.xlaser).cuda()
+    J = prob.vol * (x * psiT.abs() ** 2).sum()
+    J.backward()
+    g_ref, lam_ref = adjoint.gradients(prob, psi0_np, nsteps)
+    assert rel_l2(amp.grad.numpy(), g_ref) < 1e-8
+    assert rel_l2(psi0.grad.cpu().numpy(), 2 * lam_ref) < 1e-8

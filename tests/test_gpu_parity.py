@@ -3,7 +3,7 @@ import numpy as np
 import pytest
 
 from oracle import multigrid, relax, system, timebasis as tb
-from oracle.propagate import numpy_sub
+from oracle.propagate import numpy_coarse_sub, numpy_sub
 from paper_1111_4363_gb300 import workloads as wl
 from tests.helpers import gpu_context, oracle_system, ragged_2d, rel_l2, small_3d, to_dev, variant
 
@@ -96,7 +96,8 @@ def test_fixed_schedule_iterates(name, ncycles):
     t0 = 0.1
     prob, M, f, W = oracle_system(w, psi0, t0)
     c_ref, hist, cyc, _ = multigrid.solve_step(M, f, W, prob.shape, prob.K, numpy_sub(w), w.levels, w.nu1, w.nu2,
-                                               w.coarse_sweeps, ncycles=ncycles)
+                                               w.coarse_sweeps, ncycles=ncycles,
+                                               coarse_sub=numpy_coarse_sub(w))
     c = np.zeros(M.shape[1], dtype=np.complex128)
     st, (cycles, sweeps, N, rel) = ctx.solve_step(psi0, t0, c, ncycles=ncycles)
     assert cycles == ncycles
