@@ -221,6 +221,192 @@ k_factor(LevelGeom L, FineOp g, int is_fine, int nptsmax, const double* __restri
   }
 }
 
+// ------------------------------------------------------------------------ complex64 variant
+// For complex64 the whole factor fits in registers: thread (ti, tk) keeps its tile-cyclic entries
+// (16 I + ti, 16 J + tk), J <= I, in registers with compile-time tile indices, so the trailing
+// update is pure FFMA plus one shared-memory read per tile row and column (the shared-memory
+// resident form is bound by shared-memory bandwidth in FP32).  Same two barriers per column and
+// the same pivot lookahead as above.
+template <int NPAD>
+__global__ void __launch_bounds__(kFactorThreads, 2)
+k_factor_c64(LevelGeom L, FineOp g, int is_fine, int nptsmax, const double* __restrict__ sigma,
+             const TimeMats* __restrict__ tm, float2* __restrict__ factors, int* __restrict__ status) {
+  typedef float2 CT;
+  constexpr int NB = NPAD / LA_BLK;
+  constexpr int NT = NB * (NB + 1) / 2;
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int K = tm->K, KK = K * K;
+  CT* sCol = reinterpret_cast<CT*>(smem);                      // [NPAD]
+  float* sInv = reinterpret_cast<float*>(sCol + NPAD);          // [NPAD]
+  CT* sDiag = reinterpret_cast<CT*>(sInv + NPAD);               // [NB][256]
+  float* sP = reinterpret_cast<float*>(sDiag + NB * 256);       // [9][K*K]
+  float* sPair = sP + LA_NPAIR * LA_KMAX * LA_KMAX;             // [npts*npts][nv]
+  const int nv = is_fine ? 2 : LA_NPAIR;
+
+  const int tid = threadIdx.x, ti = tid >> 4, tk = tid & 15;
+  const int b = blockIdx.x;
+  int o[3], e[3];
+  subvol_box(L, b, o, e);
+  const int npts = e[0] * e[1] * e[2];
+  const int n = npts * K;
+  for (int i = tid; i < LA_NPAIR * KK; i += kFactorThreads) sP[i] = (float)tm->P[i / KK][i % KK];
+  for (int i = tid; i < NB * 256; i += kFactorThreads) sDiag[i] = make_float2(0.f, 0.f);
+  const int nbox = box5_count(L.dim);
+  for (int t = tid; t < npts * npts; t += kFactorThreads) {
+    const int i = t / npts, j = t % npts;
+    int ix, iy, iz, jx, jy, jz;
+    local_coords(i, e, ix, iy, iz);
+    local_coords(j, e, jx, jy, jz);
+    const int px = o[0] + ix, py = o[1] + iy, pz = o[2] + iz;
+    const int qx = o[0] + jx, qy = o[1] + jy, qz = o[2] + jz;
+    float* dst = sPair + (size_t)t * nv;
+    if (is_fine) {
+      double s9[LA_NPAIR];
+      fine_sigma(g, px, py, pz, qx, qy, qz, s9);
+      dst[0] = (float)s9[1];
+      dst[1] = (float)s9[4];
+    } else {
+      const int dx = qx - px, dy = qy - py, dz = qz - pz;
+      const bool near = abs(dx) <= 2 && abs(dy) <= 2 && abs(dz) <= 2;
+      const int p = (pz * L.n[1] + py) * L.n[0] + px;
+      const int ofs = near ? box5_index(L.dim, dx, dy, dz) : 0;
+      for (int k = 0; k < LA_NPAIR; ++k) dst[k] = near ? (float)sigma[sigma_offset(p, k, ofs, nbox)] : 0.f;
+    }
+  }
+  __syncthreads();
+
+  CT a[NT];
+#pragma unroll
+  for (int I = 0; I < NB; ++I) {
+#pragma unroll
+    for (int J = 0; J <= I; ++J) {
+      const int r = LA_BLK * I + ti, c = LA_BLK * J + tk;
+      // assembled in FP32: this factor only preconditions the FP64-refined iteration
+      float re = 0.f, im = 0.f;
+      if (I == J && ti < tk) {
+      } else if (r >= n || c >= n) {
+        re = (r == c) ? 1.f : 0.f;
+      } else {
+        const int i = r / K, mm = r % K, j = c / K, nn = c % K;
+        float s9[LA_NPAIR];
+        const float* pr = sPair + (size_t)(i * npts + j) * nv;
+        if (is_fine) {
+          int ix, iy, iz, jx, jy, jz;
+          local_coords(i, e, ix, iy, iz);
+          local_coords(j, e, jx, jy, jz);
+          const int cxp = g.lax == 0 ? ix : (g.lax == 1 ? iy : iz), cxq = g.lax == 0 ? jx : (g.lax == 1 ? jy : jz);
+          const float xp = (float)g.x0[g.lax] + (float)(o[g.lax] + cxp) * (float)g.h[g.lax];
+          const float xq = (float)g.x0[g.lax] + (float)(o[g.lax] + cxq) * (float)g.h[g.lax];
+          const float same = (i == j) ? 1.f : 0.f, Hpq = pr[0];
+          s9[0] = same; s9[1] = Hpq; s9[2] = same * xp; s9[3] = Hpq; s9[4] = pr[1];
+          s9[5] = Hpq * xq; s9[6] = same * xp; s9[7] = xp * Hpq; s9[8] = same * xp * xp;
+        } else {
+#pragma unroll
+          for (int kk = 0; kk < LA_NPAIR; ++kk) s9[kk] = pr[kk];
+        }
+#pragma unroll
+        for (int kk = 0; kk < LA_NPAIR; ++kk) {
+          const float v = s9[kk] * sP[kk * KK + mm * K + nn];
+          const int ph = theta_phase(kk);
+          if (ph == 0) re += v; else if (ph == 1) im += v; else im -= v;
+        }
+      }
+      a[I * (I + 1) / 2 + J] = make_float2(re, im);
+    }
+  }
+  if (tid == 0) {
+    float d2 = a[0].x;
+    if (!(d2 > 0.f)) { atomicOr(status, 1); d2 = 1.f; }
+    const float inv = rsqrtf(d2);
+    a[0] = make_float2(d2 * inv, 0.f);
+    sInv[0] = inv;
+  }
+  __syncthreads();
+
+  for (int j = 0; j < NPAD; ++j) {
+    const int J0 = j >> 4, jj = j & 15;
+    // (A) owners of column j scale it and publish it
+    if (tk == jj) {
+      const float inv = sInv[j];
+#pragma unroll
+      for (int I = 0; I < NB; ++I)
+#pragma unroll
+        for (int J = 0; J <= I; ++J)
+          if (J == J0 && LA_BLK * I + ti > j) {
+            CT& v = a[I * (I + 1) / 2 + J];
+            v.x *= inv;
+            v.y *= inv;
+            sCol[LA_BLK * I + ti] = v;
+          }
+    }
+    __syncthreads();
+    // (B) trailing update; the owner of the next pivot finishes it and takes its rsqrt
+    const int j1 = j + 1;
+    CT cc[NB];
+#pragma unroll
+    for (int J = 0; J < NB; ++J) {
+      const int c = LA_BLK * J + tk;
+      cc[J] = (J >= J0 && c > j) ? sCol[c] : make_float2(0.f, 0.f);
+    }
+#pragma unroll
+    for (int I = 0; I < NB; ++I) {
+      if (I < J0) continue;
+      const int r = LA_BLK * I + ti;
+      const CT xr = (r > j) ? sCol[r] : make_float2(0.f, 0.f);
+#pragma unroll
+      for (int J = 0; J <= I; ++J) {
+        if (J < J0) continue;
+        const int c = LA_BLK * J + tk;
+        if (c <= j || c > r || r <= j) continue;
+        CT& v = a[I * (I + 1) / 2 + J];
+        const CT y = cc[J];
+        v.x = fmaf(-xr.x, y.x, v.x); v.x = fmaf(-xr.y, y.y, v.x);
+        v.y = fmaf(-xr.y, y.x, v.y); v.y = fmaf(xr.x, y.y, v.y);
+        if (r == j1 && c == j1) {
+          float d2 = v.x;
+          if (!(d2 > 0.f)) { atomicOr(status, 1); d2 = 1.f; }
+          const float inv = rsqrtf(d2);
+          v = make_float2(d2 * inv, 0.f);
+          sInv[j1] = inv;
+        }
+      }
+    }
+    __syncthreads();
+  }
+
+  float2* F = factors + (size_t)b * L.fsize;
+#pragma unroll
+  for (int I = 0; I < NB; ++I)
+#pragma unroll
+    for (int J = 0; J <= I; ++J) {
+      if (I == J) {
+        if (ti >= tk) sDiag[I * 256 + ti * LA_BLK + tk] = a[I * (I + 1) / 2 + J];
+      } else {
+        F[(size_t)(I * (I + 1) / 2 + J) * 256 + ti * LA_BLK + tk] = a[I * (I + 1) / 2 + J];
+      }
+    }
+  __syncthreads();
+  if (tid < NB * LA_BLK) {
+    const int I = tid / LA_BLK, jj = tid % LA_BLK, base = LA_BLK * I;
+    const CT* Ld = sDiag + I * 256;
+    CT x[LA_BLK];
+#pragma unroll
+    for (int i = 0; i < LA_BLK; ++i) {
+      CT acc = make_float2(0.f, 0.f);
+#pragma unroll
+      for (int k = 0; k < i; ++k)
+        if (k >= jj) cfma(acc, Ld[i * LA_BLK + k], x[k]);
+      const float rinv = sInv[base + i];
+      if (i < jj) x[i] = make_float2(0.f, 0.f);
+      else if (i == jj) x[i] = make_float2(rinv, 0.f);
+      else x[i] = make_float2(-acc.x * rinv, -acc.y * rinv);
+    }
+    float2* D = F + (size_t)(I * (I + 1) / 2 + I) * 256;
+#pragma unroll
+    for (int i = 0; i < LA_BLK; ++i) D[i * LA_BLK + jj] = x[i];
+  }
+}
+
 // ======================================================================== triangular solves
 // x = (L L^dagger)^{-1} rhs with the blocked factor F; 128 threads.  rhs is overwritten by x.
 template <typename CT, int NPAD>
@@ -661,6 +847,25 @@ inline size_t sweep_coarse_smem(const LevelGeom& L, int K, size_t rsize, size_t 
   const size_t nptsmax = (size_t)L.sub[0] * L.sub[1] * L.sub[2];
   return rsize * (LA_NPAIR * LA_KMAX * LA_KMAX + coarse_sg_count(L)) +
          csize * (coarse_box_count(L) * K + nptsmax * LA_NPAIR * K + 2 * (size_t)L.npad + LA_BLK + 128);
+}
+
+template <int NPAD>
+cudaError_t launch_factor_c64_n(const LevelGeom& L, const FineOp* fine, const double* sigma, const TimeMats* tm,
+                                float2* factors, int* status, cudaStream_t s) {
+  const int nptsmax = L.sub[0] * L.sub[1] * L.sub[2];
+  const size_t smem = sizeof(float2) * (NPAD + (size_t)(NPAD / LA_BLK) * 256) + sizeof(float) * NPAD +
+                      sizeof(float) * (LA_NPAIR * LA_KMAX * LA_KMAX + (size_t)nptsmax * nptsmax * (fine ? 2 : LA_NPAIR));
+  auto kern = k_factor_c64<NPAD>;
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+    if (err != cudaSuccess) return err;
+    attr_set = true;
+  }
+  if (smem > 227 * 1024) return cudaErrorInvalidValue;
+  FineOp g = fine ? *fine : FineOp{};
+  kern<<<L.nsub, kFactorThreads, smem, s>>>(L, g, fine ? 1 : 0, nptsmax, sigma, tm, factors, status);
+  return cudaGetLastError();
 }
 
 template <typename R, int NPAD>
