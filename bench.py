@@ -29,6 +29,10 @@ import numpy as np  # noqa: E402
 from paper_1111_4363_gb300 import workloads as wl  # noqa: E402
 
 METRIC = "spacetime unknowns relaxed/s"
+# DRAM bytes (read + write) per finest-level subvolume from one ncu capture of the current kernels
+# (profiles/k_sweep_fine_2d_softcore_128x128_fp64.md, profiles/k_factor_2d_softcore_128x128_fp64.md),
+# scaled to a launch by the number of subvolumes it processes.  Set to None when a kernel changes.
+NCU_BYTES_PER_SUBVOLUME = {("sweep", 0): (23.114240e6 + 256) / 256, ("factor", 0): (0.327168e6 + 43.886592e6) / 1024}
 FP64_PEAK_TFLOPS = 152 * 4 * 2070e6 / 1e12   # 152 SMs x 4 FP64 flop/clk/SM x 2070 MHz (derived)
 L2_BYTES = 129 * 2 ** 20
 
@@ -36,6 +40,8 @@ L2_BYTES = 129 * 2 ** 20
 def workload(name: str) -> wl.Workload:
     if name == "2d":
         return wl.softcore_2d(n=256, levels=4, nsteps=200)
+    if name == "2d-small":          # the same problem on 128 x 128, for ncu captures of single kernels
+        return wl.softcore_2d(n=128, levels=4, nsteps=200)
     if name == "1d":
         return wl.harmonic_1d()
     raise ValueError(name)
@@ -178,15 +184,19 @@ def run_ours(args):
     fac_ms = prof["ms_factor"] / max(prof["n_factor"], 1)
     ncol = 1 << w.dim
     swp_ms_full = prof["ms_sweep"] / max(prof["n_sweep"], 1) * ncol
+    nsub = (w.n[0] // w.sub[0]) * (w.n[1] // w.sub[1] if w.dim > 1 else 1)
     if prof["ms_factor"] >= prof["ms_sweep"]:
-        dom, flops, dms = "k_factor (finest level)", prof["flops_factor"], fac_ms
+        dom, flops, dms, cls = "k_factor (finest level)", prof["flops_factor"], fac_ms, "factor"
     else:
-        dom, flops, dms = "k_sweep_fine (one sweep, all colours)", prof["flops_sweep"], swp_ms_full
+        dom, flops, dms, cls = "k_sweep_fine (one sweep, all colours)", prof["flops_sweep"], swp_ms_full, "sweep"
+    bps = NCU_BYTES_PER_SUBVOLUME.get((cls, args.precision)) if args.workload.startswith("2d") else None
+    traffic = round(bps * nsub) if bps else None
     achieved = flops / (dms * 1e-3) / 1e12
     prec_tag = "f64" if args.precision == 0 else "c64 local solves + f64 refinement"
     peak = FP64_PEAK_TFLOPS
     roofline = {"bound": "alu", "kernel": dom, "achieved": round(achieved, 4), "peak": round(peak, 4),
-                "unit": "TFLOP/s", "frac": round(achieved / peak, 4), "traffic": None,
+                "unit": "TFLOP/s", "frac": round(achieved / peak, 4), "traffic": traffic,
+                "traffic_note": "DRAM bytes per launch unit from one ncu capture at 128x128, scaled by subvolumes",
                 "peak_note": "FP64 pipe: 152 SMs x 4 flop/clk x 2070 MHz (derived); probe measured 1.19 at 1995 MHz",
                 "kernel_ms": {"factor_per_launch": round(fac_ms, 4), "sweep_full": round(swp_ms_full, 4),
                               "factor_share": round(prof["ms_factor"] / max(ms, 1e-9), 3),
@@ -298,7 +308,7 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="2d", choices=["2d", "1d"])
+    ap.add_argument("--workload", default="2d", choices=["2d", "2d-small", "1d"])
     ap.add_argument("--precision", type=int, default=0, choices=[0, 1])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
