@@ -110,6 +110,17 @@ la_status la_set_hamiltonian(la_ctx* ctx, const double* V0, const la_pulse* puls
    Returns LA_ENOTCONV if some step hit max_cycles (psi is still advanced). */
 la_status la_step(la_ctx* ctx, void* psi, int nsteps, double t0, la_step_stats* per_step);
 
+/* Many independent propagations stepped together (each context its own grid, potential, pulse and
+   configuration).  psis[i] (complex128[Np_i], host or device) is advanced by nsteps steps from time
+   t0s[i].  Every context works on its own internal stream for the whole call; per time step all
+   contexts' factorisations are enqueued, then relaxation cycles are issued in rounds -- one captured
+   cycle per unconverged context, then one synchronisation per context -- until every context reached
+   its tolerance, so the small per-context launches of different problems run concurrently.
+   stats (host, nullable): nctx * nsteps records, context-major.  Returns LA_ENOTCONV if some step of
+   some context hit max_cycles.  Errors: LA_EINVAL (null or repeated context), LA_ESTATE, LA_ECUDA. */
+la_status la_step_batch(la_ctx* const* ctxs, int nctx, void* const* psis, int nsteps, const double* t0s,
+                        la_step_stats* stats);
+
 /* N and N/N(0) (Eq. residnorm) of the final iterate of the last time step; synchronises. */
 la_status la_action(la_ctx* ctx, double* action, double* rel_action);
 

@@ -19,7 +19,7 @@ STATUS_NAMES = {0: "LA_OK", 1: "LA_EINVAL", 2: "LA_ENOMEM", 3: "LA_ECUDA", 4: "L
 WEIGHTS = {"dual": 0, "literal": 1, "identity": 2}
 
 EXPORTS = ["la_init", "la_set_hamiltonian", "la_step", "la_action", "la_solve_step", "la_residual",
-           "la_relax_colour", "la_time_matrices", "la_backward", "la_profile_enable", "la_profile_read", "la_action_noalloc",
+           "la_relax_colour", "la_time_matrices", "la_backward", "la_step_batch", "la_profile_enable", "la_profile_read", "la_action_noalloc",
            "la_finalize", "la_last_error", "la_version"]
 NOALLOC_MAX_POINTS = 1 << 22
 
@@ -73,6 +73,7 @@ def lib() -> C.CDLL:
         L.la_relax_colour.argtypes = [vp, vp, d, i, vp]
         L.la_time_matrices.argtypes = [vp, d, C.POINTER(d)]
         L.la_backward.argtypes = [vp, vp, C.POINTER(d), vp]
+        L.la_step_batch.argtypes = [C.POINTER(vp), i, C.POINTER(vp), i, C.POINTER(d), C.POINTER(la_step_stats)]
         L.la_profile_enable.argtypes = [vp, i]
         L.la_profile_read.argtypes = [vp, C.POINTER(la_profile)]
         L.la_action_noalloc.argtypes = [C.POINTER(la_config), vp, C.POINTER(la_pulse), vp, d, vp, C.POINTER(d), vp]
@@ -160,6 +161,22 @@ def action_noalloc(cfg: la_config, V0, pulse, psi0, t0: float, c, stream=None) -
     if st != LA_OK:
         raise LeastActionError(st, L.la_last_error(None).decode())
     return N.value
+
+
+def step_batch(contexts, psis, nsteps: int, t0s=None, allow_notconv: bool = False):
+    """la_step_batch over Context objects; returns per-context lists of (cycles, sweeps, N, rel)."""
+    L = lib()
+    n = len(contexts)
+    hs = (C.c_void_p * n)(*[c.handle.value for c in contexts])
+    ps = (C.c_void_p * n)(*[_ptr(p).value for p in psis])
+    t0 = (C.c_double * n)(*([0.0] * n if t0s is None else [float(t) for t in t0s]))
+    rec = (la_step_stats * max(n * nsteps, 1))()
+    st = L.la_step_batch(hs, n, ps, int(nsteps), t0, rec)
+    if st != LA_OK and not (allow_notconv and st == LA_ENOTCONV):
+        msgs = "; ".join(L.la_last_error(c.handle).decode() for c in contexts[:3])
+        raise LeastActionError(st, msgs)
+    return [[(r.cycles, r.fine_sweeps, r.action, r.rel_action) for r in rec[i * nsteps:(i + 1) * nsteps]]
+            for i in range(n)]
 
 
 class Context:

@@ -76,6 +76,7 @@ struct la_ctx {
     long long launches = 0;
   };
   CycleGraph cg[2];               // [0] plain, [1] with profiling events
+  CycleGraph* pending_graph = nullptr;
   bool use_graph = true;
   bool capturing = false;
   long long cycles_run = 0;
@@ -682,14 +683,9 @@ static la_status cycle_body(la_ctx* c) {
 
 // Run one cycle and return N.  After the first cycle of a context the cycle is captured once into
 // a CUDA graph and replayed on an internal stream joined to the caller's stream by events.
-static la_status run_cycle(la_ctx* c, double* N) {
-  if (!c->use_graph || c->cycles_run == 0) {
-    LA_TRY(cycle_body(c));
-    LA_CUDA(c, cudaStreamSynchronize(c->stream));
-    *N = *c->h_N;
-    ++c->cycles_run;
-    return LA_OK;
-  }
+static la_status cycle_issue(la_ctx* c) {
+  c->pending_graph = nullptr;
+  if (!c->use_graph || c->cycles_run == 0) return cycle_body(c);
   la_ctx::CycleGraph& g = c->cg[c->prof ? 1 : 0];
   if (!g.exec) {
     cudaStream_t user = c->stream;
@@ -720,17 +716,33 @@ static la_status run_cycle(la_ctx* c, double* N) {
   LA_CUDA(c, cudaGraphLaunch(g.exec, c->cap));
   LA_CUDA(c, cudaEventRecord(c->ev_join, c->cap));
   LA_CUDA(c, cudaStreamWaitEvent(c->stream, c->ev_join, 0));
+  c->pending_graph = &g;
+  return LA_OK;
+}
+
+static la_status cycle_complete(la_ctx* c, double* N) {
   LA_CUDA(c, cudaStreamSynchronize(c->stream));
   *N = *c->h_N;
-  c->launches += g.launches;
-  if (c->prof) {
-    for (auto& p : g.pairs) {
-      float ms = 0.f;
-      if (cudaEventElapsedTime(&ms, p.first, p.second) == cudaSuccess) { c->ms_sweep += ms; ++c->n_sweep; }
+  if (c->pending_graph) {
+    la_ctx::CycleGraph& g = *c->pending_graph;
+    c->launches += g.launches;
+    if (c->prof) {
+      for (auto& p : g.pairs) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, p.first, p.second) == cudaSuccess) { c->ms_sweep += ms; ++c->n_sweep; }
+      }
     }
+    c->pending_graph = nullptr;
   }
   ++c->cycles_run;
   return LA_OK;
+}
+
+// Run one cycle and return N.  After the first cycle of a context the cycle is captured once into
+// a CUDA graph and replayed on an internal stream joined to the caller's stream by events.
+static la_status run_cycle(la_ctx* c, double* N) {
+  LA_TRY(cycle_issue(c));
+  return cycle_complete(c, N);
 }
 
 // time matrices and right-hand side for initial state d_psi at t0
@@ -927,6 +939,108 @@ extern "C" la_status la_backward(la_ctx* c, const void* dJ_dpsiT, double* grad_a
   LA_CUDA(c, cudaMemcpy(&status, c->d_status, sizeof(int), cudaMemcpyDeviceToHost));
   if (status) return fail(c, LA_ECUDA, "a subvolume matrix was not positive definite");
   return LA_OK;
+}
+
+extern "C" la_status la_step_batch(la_ctx* const* ctxs, int nctx, void* const* psis, int nsteps, const double* t0s,
+                                   la_step_stats* stats) {
+  if (!ctxs || !psis || !t0s || nctx < 1 || nsteps < 0) return LA_EINVAL;
+  for (int i = 0; i < nctx; ++i) {
+    if (!ctxs[i] || !psis[i]) return LA_EINVAL;
+    if (!ctxs[i]->have_ham) return fail(ctxs[i], LA_ESTATE, "la_set_hamiltonian must be called first");
+    for (int j = 0; j < i; ++j)
+      if (ctxs[j] == ctxs[i]) return fail(ctxs[i], LA_EINVAL, "a context appears twice in the batch");
+  }
+  std::vector<cudaStream_t> user(nctx);
+  std::vector<char> dev(nctx);
+  std::vector<double> N0(nctx), N(nctx);
+  std::vector<int> cyc(nctx), active(nctx);
+  la_status worst = LA_OK;
+  // every context works on its own internal stream for the whole call (forked from its stream)
+  for (int i = 0; i < nctx; ++i) {
+    la_ctx* c = ctxs[i];
+    user[i] = c->stream;
+    LA_CUDA(c, cudaEventRecord(c->ev_fork, c->stream));
+    LA_CUDA(c, cudaStreamWaitEvent(c->cap, c->ev_fork, 0));
+    c->stream = c->cap;
+    dev[i] = is_device_ptr(psis[i]);
+    LA_CUDA(c, cudaMemcpyAsync(c->d_psi, psis[i], sizeof(double2) * (size_t)c->np0,
+                               dev[i] ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->stream));
+  }
+  la_status st = LA_OK;
+  for (int s = 0; s < nsteps && st == LA_OK; ++s) {
+    for (int i = 0; i < nctx && st == LA_OK; ++i) {
+      la_ctx* c = ctxs[i];
+      st = setup_step(c, t0s[i] + s * c->cfg.dt);
+      if (st == LA_OK) st = c->cfg.precision == 0 ? factor_all<double>(c) : factor_all<float>(c);
+      if (st == LA_OK && cudaMemsetAsync(c->d_c, 0, sizeof(double2) * (size_t)c->nunk0, c->stream) != cudaSuccess)
+        st = fail(c, LA_ECUDA, "memset failed");
+      if (st == LA_OK) st = action_enqueue(c);
+    }
+    for (int i = 0; i < nctx && st == LA_OK; ++i) {
+      st = cycle_complete(ctxs[i], &N0[i]);
+      --ctxs[i]->cycles_run;   // the initial action is not a cycle
+      N[i] = N0[i];
+      cyc[i] = 0;
+      active[i] = 1;
+    }
+    // relaxation rounds: one cycle per unconverged context, then one synchronisation per context
+    bool any = true;
+    while (any && st == LA_OK) {
+      any = false;
+      for (int i = 0; i < nctx && st == LA_OK; ++i) {
+        la_ctx* c = ctxs[i];
+        const bool check = c->cfg.tol > 0;
+        if (!active[i]) continue;
+        if ((check && N[i] <= c->cfg.tol * N0[i]) || cyc[i] >= c->cfg.max_cycles) {
+          active[i] = 0;
+          continue;
+        }
+        st = cycle_issue(c);
+        any = true;
+      }
+      for (int i = 0; i < nctx && st == LA_OK; ++i) {
+        if (!active[i]) continue;
+        st = cycle_complete(ctxs[i], &N[i]);
+        ++cyc[i];
+      }
+    }
+    for (int i = 0; i < nctx && st == LA_OK; ++i) {
+      la_ctx* c = ctxs[i];
+      int status = 0;
+      if (cudaMemcpy(&status, c->d_status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess || status) {
+        st = fail(c, LA_ECUDA, "a subvolume matrix was not positive definite");
+        break;
+      }
+      c->last_N = N[i];
+      c->last_rel = N0[i] > 0 ? N[i] / N0[i] : 0.0;
+      c->have_step = true;
+      if (stats) {
+        la_step_stats& r = stats[(size_t)i * nsteps + s];
+        r.cycles = cyc[i];
+        r.fine_sweeps = cyc[i] * (c->cfg.nu1 + c->cfg.nu2);
+        r.action = N[i];
+        r.rel_action = c->last_rel;
+      }
+      if (c->cfg.tol > 0 && !(N[i] <= c->cfg.tol * N0[i])) worst = LA_ENOTCONV;
+      launch_advance(c->np0, c->d_tm, c->d_c, c->d_psi, c->stream);
+      ++c->launches;
+    }
+  }
+  // results back, streams restored and joined
+  for (int i = 0; i < nctx; ++i) {
+    la_ctx* c = ctxs[i];
+    if (st == LA_OK)
+      cudaMemcpyAsync(psis[i], c->d_psi, sizeof(double2) * (size_t)c->np0,
+                      dev[i] ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->stream);
+    cudaEventRecord(c->ev_join, c->cap);
+    c->stream = user[i];
+    cudaStreamWaitEvent(c->stream, c->ev_join, 0);
+  }
+  for (int i = 0; i < nctx; ++i) {
+    if (cudaStreamSynchronize(ctxs[i]->stream) != cudaSuccess && st == LA_OK)
+      st = fail(ctxs[i], LA_ECUDA, "synchronisation failed");
+  }
+  return st != LA_OK ? st : worst;
 }
 
 extern "C" la_status la_action(la_ctx* c, double* N, double* rel) {

@@ -1,0 +1,61 @@
+"""la_step_batch: independent propagations stepped together equal the same propagations stepped alone."""
+import dataclasses
+
+import numpy as np
+import pytest
+
+from paper_1111_4363_gb300 import workloads as wl
+from tests.helpers import gpu_context, rel_l2
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+
+
+def members():
+    a = wl.batched_2d(3)
+    a = dataclasses.replace(a, n=(48, 48, 1), levels=3)
+    b = wl.batched_2d(5)
+    b = dataclasses.replace(b, n=(32, 32, 1), levels=2, sub=(2, 2, 1))
+    c = wl.harmonic_1d()
+    return [a, b, c]
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_batch_equals_individual_steps(precision):
+    import torch
+    from paper_1111_4363_gb300 import binding as B
+    ws = members()
+    nsteps = 3
+    alone = []
+    for w in ws:
+        ctx = gpu_context(w, precision=precision)
+        psi = torch.from_numpy(wl.initial_state(w).ravel().copy()).cuda()
+        st, stats = ctx.step(psi, nsteps, 0.2, stats=True)
+        alone.append((psi.cpu().numpy(), stats))
+    ctxs = [gpu_context(w, precision=precision) for w in ws]
+    psis = [torch.from_numpy(wl.initial_state(w).ravel().copy()).cuda() for w in ws[:2]]
+    psis.append(wl.initial_state(ws[2]).ravel().copy())            # host buffer for the third member
+    stats = B.step_batch(ctxs, psis, nsteps, [0.2] * 3)
+    for i, (psi_ref, st_ref) in enumerate(alone):
+        got = psis[i].cpu().numpy() if hasattr(psis[i], "cpu") else psis[i]
+        assert rel_l2(got, psi_ref) < 1e-14, i
+        assert [s[0] for s in stats[i]] == [s[0] for s in st_ref]
+        assert all(s[3] <= ws[i].tol for s in stats[i])
+
+
+def test_batch_rejects_repeated_context():
+    import torch
+    from paper_1111_4363_gb300 import binding as B
+    w = members()[1]
+    ctx = gpu_context(w)
+    psi = torch.from_numpy(wl.initial_state(w).ravel().copy()).cuda()
+    with pytest.raises(B.LeastActionError):
+        B.step_batch([ctx, ctx], [psi, psi.clone()], 1)
