@@ -302,18 +302,78 @@ def run_reference(args):
     print(json.dumps(out))
 
 
+def run_batched(args):
+    """512 independent 2D propagations of uneven size (64^2 .. 256^2, K = 4): la_step_batch vs stepping
+    the same contexts one after another, at the same tolerance.  The schedule is autotuned on a
+    128 x 128 member."""
+    import dataclasses
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1111_4363_gb300 import autotune
+    from paper_1111_4363_gb300 import binding as B
+    members = [wl.batched_2d(i) for i in range(args.batch)]
+    rep = dataclasses.replace(members[0], n=(128, 128, 1))
+    best = autotune.tune(rep, precision=args.precision)
+    ws = [dataclasses.replace(m, **best) for m in members]
+    ctxs, psis = [], []
+    for w in ws:
+        ctx = B.Context(B.config_from_workload(w, precision=args.precision))
+        ctx.set_hamiltonian(torch.tensor(wl.potential(w).ravel(), dtype=torch.float64, device="cuda"), w.pulse)
+        ctxs.append(ctx)
+        psis.append(torch.from_numpy(wl.initial_state(w).ravel()).cuda())
+    t0s = [0.0] * len(ws)
+    B.step_batch(ctxs, psis, args.warmup, t0s)
+    t0s = [args.warmup * w.dt for w in ws]
+    torch.cuda.synchronize()
+    clocks = ClockSampler(0)
+    clocks.start()
+    a = time.perf_counter()
+    stats = B.step_batch(ctxs, psis, args.steps, t0s)
+    torch.cuda.synchronize()
+    el = time.perf_counter() - a
+    clk = clocks.stop()
+    work = sum(w.nunknowns * sum(s[1] for s in st) for w, st in zip(ws, stats))
+    value = work / el
+    # the same contexts stepped one after another (plain per-context la_step), same number of steps
+    t1s = [t + args.steps * w.dt for t, w in zip(t0s, ws)]
+    torch.cuda.synchronize()
+    a = time.perf_counter()
+    work_seq = 0
+    for ctx, psi, w, t in zip(ctxs, psis, ws, t1s):
+        st, sts = ctx.step(psi, args.steps, t, stats=True)
+        work_seq += w.nunknowns * sum(x[1] for x in sts)
+    torch.cuda.synchronize()
+    el_seq = time.perf_counter() - a
+    value_seq = work_seq / el_seq
+    out = {"metric": METRIC, "value": value, "unit": "unknowns/s", "n_gpus": 1, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.precision == 0 else "c64 local solves + f64 refinement",
+           "data": "synthetic",
+           "config": {"workload": f"2d_batched_{args.batch}_K4", "members": args.batch,
+                      "grids": "seeded n in {64, 80, ..., 256}", "unknowns_total": sum(w.nunknowns for w in ws),
+                      "autotuned": best, "tol_rel_action": ws[0].tol, "precision": args.precision},
+           "sequential": {"value": value_seq, "ms_per_step": 1e3 * el_seq / args.steps},
+           "speedup_vs_sequential": value / value_seq,
+           "max_rel_action": max(s[3] for st in stats for s in st), "clocks": clk}
+    print(json.dumps(out))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="2d", choices=["2d", "2d-small", "1d"])
+    ap.add_argument("--workload", default="2d", choices=["2d", "2d-small", "1d", "batched"])
+    ap.add_argument("--batch", type=int, default=512)
     ap.add_argument("--precision", type=int, default=0, choices=[0, 1])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "batched":
+        run_batched(args)
     else:
         run_ours(args)
 

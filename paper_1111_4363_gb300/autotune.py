@@ -1,0 +1,88 @@
+"""Autotuner for the relaxation schedule: subvolume shape, Galerkin-level subvolume shape, levels.
+
+Every candidate reaches the same tolerance on N/N(0) (the minimiser does not depend on the
+schedule), so candidates are ranked by measured time per least-action step on the GPU.  The
+colouring is not a free parameter: same-colour subvolumes must not interact through the radius-2
+normal operator, which leaves the 2^d block-parity classes (a checkerboard is invalid).  Results
+are cached in JSON next to the built library, keyed by grid, K, precision and weight.
+"""
+from __future__ import annotations
+
+import dataclasses
+import json
+import os
+import time
+
+from . import binding as B
+from . import workloads as wl
+
+CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build", "autotune.json")
+
+
+def candidates(w: wl.Workload):
+    out = []
+    subs = [(2, 2), (4, 2), (4, 4)]
+    if w.nt * 32 <= 128:
+        subs.append((8, 4))
+    for sx, sy in subs:
+        for levels in (1, 2, 3, 4):
+            if any(w.n[a] % (1 << (levels - 1)) for a in range(w.dim)):
+                continue
+            out.append(dict(sub=(sx, sy, 1), coarse_sub=(2, 2, 1), levels=levels,
+                            coarse_sweeps=1, nu1=1, nu2=1 if levels > 1 else 1))
+    return out
+
+
+def key(w: wl.Workload, precision: int) -> str:
+    return f"{w.dim}:{'x'.join(map(str, w.n[:w.dim]))}:K{w.nt}:p{precision}:{w.weight}"
+
+
+def measure(w: wl.Workload, precision: int, nsteps: int = 3, warmup: int = 1) -> dict:
+    import torch
+    cfg = B.config_from_workload(w, precision=precision)
+    ctx = B.Context(cfg)
+    ctx.set_hamiltonian(torch.tensor(wl.potential(w).ravel(), dtype=torch.float64, device="cuda"), w.pulse)
+    psi = torch.from_numpy(wl.initial_state(w).ravel().copy()).cuda()
+    t = 0.0
+    for _ in range(warmup):
+        ctx.step(psi, 1, t)
+        t += w.dt
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    st, stats = ctx.step(psi, nsteps, t, stats=True)
+    torch.cuda.synchronize()
+    el = time.perf_counter() - t0
+    ctx.close()
+    return {"ms_per_step": 1e3 * el / nsteps, "cycles": sum(s[0] for s in stats) / nsteps,
+            "rel": max(s[3] for s in stats)}
+
+
+def tune(w: wl.Workload, precision: int = 0, use_cache: bool = True, verbose: bool = False) -> dict:
+    """Best schedule for workload ``w`` (a dict of Workload fields to replace)."""
+    cache = {}
+    if use_cache and os.path.exists(CACHE):
+        with open(CACHE) as fh:
+            cache = json.load(fh)
+    k = key(w, precision)
+    if use_cache and k in cache:
+        return cache[k]["best"]
+    results = []
+    for cand in candidates(w):
+        wc = dataclasses.replace(w, **cand)
+        try:
+            r = measure(wc, precision)
+        except B.LeastActionError as e:
+            if verbose:
+                print("skip", cand, e)
+            continue
+        if r["rel"] <= w.tol:
+            results.append((r["ms_per_step"], cand, r))
+            if verbose:
+                print(cand, r)
+    results.sort(key=lambda x: x[0])
+    best = results[0][1]
+    cache[k] = {"best": best, "table": [dict(c, **r) for _, c, r in results]}
+    os.makedirs(os.path.dirname(CACHE), exist_ok=True)
+    with open(CACHE, "w") as fh:
+        json.dump(cache, fh, indent=1)
+    return best
