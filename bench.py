@@ -32,7 +32,7 @@ METRIC = "spacetime unknowns relaxed/s"
 # DRAM bytes (read + write) per finest-level subvolume from one ncu capture of the current kernels
 # (profiles/k_sweep_fine_2d_softcore_128x128_fp64.md, profiles/k_factor_2d_softcore_128x128_fp64.md),
 # scaled to a launch by the number of subvolumes it processes.  Set to None when a kernel changes.
-NCU_BYTES_PER_SUBVOLUME = {("sweep", 0): (23.114240e6 + 256) / 256, ("factor", 0): (0.327168e6 + 43.886592e6) / 1024}
+NCU_BYTES_PER_SUBVOLUME = {}   # (kernel class, precision) -> DRAM bytes per subvolume from one ncu capture
 FP64_PEAK_TFLOPS = 152 * 4 * 2070e6 / 1e12   # 152 SMs x 4 FP64 flop/clk/SM x 2070 MHz (derived)
 L2_BYTES = 129 * 2 ** 20
 

@@ -70,8 +70,9 @@ k_factor(LevelGeom L, FineOp g, int is_fine, int nptsmax, const double* __restri
   CT* sCol = sA + NTRI;                                       // [NPAD] scaled column j
   R* sInv = reinterpret_cast<R*>(sCol + NPAD);                // [NPAD] 1/L_jj
   double* sP = reinterpret_cast<double*>(sInv + NPAD);        // [9][K*K]
-  double* sPair = sP + LA_NPAIR * LA_KMAX * LA_KMAX;          // [npts*npts][nv]
-  const int nv = is_fine ? 2 : LA_NPAIR;
+  double* sPair = sP + LA_NPAIR * LA_KMAX * LA_KMAX;          // [npair][9], point pairs i >= j
+  const int npair_max = nptsmax * (nptsmax + 1) / 2;
+  int* sMask = reinterpret_cast<int*>(sPair + (size_t)npair_max * LA_NPAIR);  // nonzero factors of a pair
 
   const int tid = threadIdx.x, ti = tid >> 4, tk = tid & 15;
   const int b = blockIdx.x;
@@ -81,66 +82,69 @@ k_factor(LevelGeom L, FineOp g, int is_fine, int nptsmax, const double* __restri
   const int n = npts * K;
 
   for (int i = tid; i < LA_NPAIR * KK; i += kFactorThreads) sP[i] = tm->P[i / KK][i % KK];
+  // pair table for point pairs i >= j: the nine spatial factors Sigma_kk'[p_i, p_j] and a bit mask
+  // of the nonzero ones (most pairs of a subvolume are too far apart for most factors)
   const int nbox = box5_count(L.dim);
-  for (int t = tid; t < npts * npts; t += kFactorThreads) {
-    const int i = t / npts, j = t % npts;
+  const int npair = npts * (npts + 1) / 2;
+  for (int q = tid; q < npair; q += kFactorThreads) {
+    int i = (int)((sqrtf(8.0f * (float)q + 1.0f) - 1.0f) * 0.5f);
+    while (i * (i + 1) / 2 > q) --i;
+    while ((i + 1) * (i + 2) / 2 <= q) ++i;
+    const int j = q - i * (i + 1) / 2;
     int ix, iy, iz, jx, jy, jz;
     local_coords(i, e, ix, iy, iz);
     local_coords(j, e, jx, jy, jz);
     const int px = o[0] + ix, py = o[1] + iy, pz = o[2] + iz;
     const int qx = o[0] + jx, qy = o[1] + jy, qz = o[2] + jz;
-    double* dst = sPair + (size_t)t * nv;
+    double s9[LA_NPAIR];
     if (is_fine) {
-      double s9[LA_NPAIR];
       fine_sigma(g, px, py, pz, qx, qy, qz, s9);
-      dst[0] = s9[1];   // H_pq
-      dst[1] = s9[4];   // (H^2)_pq
     } else {
       const int dx = qx - px, dy = qy - py, dz = qz - pz;
       const bool near = abs(dx) <= 2 && abs(dy) <= 2 && abs(dz) <= 2;
       const int p = (pz * L.n[1] + py) * L.n[0] + px;
       const int ofs = near ? box5_index(L.dim, dx, dy, dz) : 0;
-      for (int k = 0; k < LA_NPAIR; ++k) dst[k] = near ? sigma[sigma_offset(p, k, ofs, nbox)] : 0.0;
+      for (int k = 0; k < LA_NPAIR; ++k) s9[k] = near ? sigma[sigma_offset(p, k, ofs, nbox)] : 0.0;
     }
+    int mask = 0;
+    for (int k = 0; k < LA_NPAIR; ++k) {
+      sPair[(size_t)q * LA_NPAIR + k] = s9[k];
+      if (s9[k] != 0.0) mask |= 1 << k;
+    }
+    sMask[q] = mask;
+  }
+  // padding rows: identity
+  for (int t = tid; t < NTRI; t += kFactorThreads) {
+    int r = (int)((sqrtf(8.0f * (float)t + 1.0f) - 1.0f) * 0.5f);
+    while (r * (r + 1) / 2 > t) --r;
+    while ((r + 1) * (r + 2) / 2 <= t) ++r;
+    const int c = t - r * (r + 1) / 2;
+    if (r >= n) sA[t] = mkc<CT>((R)(r == c ? 1 : 0), (R)0);
   }
   __syncthreads();
 
-  // ---- assemble: G_UU[(i,m),(j,n)] = sum_kk' Sigma_kk'[p_i, p_j] Theta_kk'[m, n]
+  // ---- assemble pair-major: G_UU[(i,m),(j,n)] = sum_kk' Sigma_kk'[p_i, p_j] Theta_kk'[m, n].
+  // Consecutive threads take the K*K entries of one point pair, so the skipped (zero) factors
+  // are uniform across a warp except at pair boundaries.
+  for (int t = tid; t < npair * KK; t += kFactorThreads) {
+    const int q = t / KK, mn = t % KK, mm = mn / K, nn = mn % K;
+    int i = (int)((sqrtf(8.0f * (float)q + 1.0f) - 1.0f) * 0.5f);
+    while (i * (i + 1) / 2 > q) --i;
+    while ((i + 1) * (i + 2) / 2 <= q) ++i;
+    const int j = q - i * (i + 1) / 2;
+    const int r = i * K + mm, c = j * K + nn;
+    if (r < c) continue;
+    const int mask = sMask[q];
+    const double* pr = sPair + (size_t)q * LA_NPAIR;
+    double re = 0.0, im = 0.0;
 #pragma unroll
-  for (int I = 0; I < NB; ++I) {
-#pragma unroll
-    for (int J = 0; J <= I; ++J) {
-      const int r = LA_BLK * I + ti, c = LA_BLK * J + tk;
-      if (I == J && ti < tk) continue;
-      double re = 0.0, im = 0.0;
-      if (r >= n || c >= n) {
-        re = (r == c) ? 1.0 : 0.0;
-      } else {
-        const int i = r / K, mm = r % K, j = c / K, nn = c % K;
-        double s9[LA_NPAIR];
-        const double* pr = sPair + (size_t)(i * npts + j) * nv;
-        if (is_fine) {
-          int ix, iy, iz, jx, jy, jz;
-          local_coords(i, e, ix, iy, iz);
-          local_coords(j, e, jx, jy, jz);
-          const double xp = fine_x(g, o[0] + ix, o[1] + iy, o[2] + iz);
-          const double xq = fine_x(g, o[0] + jx, o[1] + jy, o[2] + jz);
-          const double same = (i == j) ? 1.0 : 0.0, Hpq = pr[0];
-          s9[0] = same; s9[1] = Hpq; s9[2] = same * xp; s9[3] = Hpq; s9[4] = pr[1];
-          s9[5] = Hpq * xq; s9[6] = same * xp; s9[7] = xp * Hpq; s9[8] = same * xp * xp;
-        } else {
-#pragma unroll
-          for (int kk = 0; kk < LA_NPAIR; ++kk) s9[kk] = pr[kk];
-        }
-#pragma unroll
-        for (int kk = 0; kk < LA_NPAIR; ++kk) {
-          const double v = s9[kk] * sP[kk * KK + mm * K + nn];
-          const int ph = theta_phase(kk);
-          if (ph == 0) re += v; else if (ph == 1) im += v; else im -= v;
-        }
-      }
-      sA[tri_index(r, c)] = mkc<CT>((R)re, (R)im);
+    for (int kk = 0; kk < LA_NPAIR; ++kk) {
+      if (!((mask >> kk) & 1)) continue;
+      const double v = pr[kk] * sP[kk * KK + mm * K + nn];
+      const int ph = theta_phase(kk);
+      if (ph == 0) re += v; else if (ph == 1) im += v; else im -= v;
     }
+    sA[tri_index(r, c)] = mkc<CT>((R)re, (R)im);
   }
   __syncthreads();
   if (tid == 0) {
@@ -408,69 +412,77 @@ k_factor_c64(LevelGeom L, FineOp g, int is_fine, int nptsmax, const double* __re
 }
 
 // ======================================================================== triangular solves
-// x = (L L^dagger)^{-1} rhs with the blocked factor F; 128 threads.  rhs is overwritten by x.
+// x = (L L^dagger)^{-1} rhs with the blocked factor F; rhs is overwritten by x.  Two warps (64
+// threads, 4 lanes per row) do the block mat-vecs and synchronise with a named barrier; the other
+// warps of the CTA skip the solve.  Four lanes per row keep the cross-lane reduction at two shuffle
+// levels, which matters because every FP64 add issues on the slow FP64 pipe.  The caller
+// synchronises the whole CTA before and after.
+__device__ __forceinline__ void solve_bar() { asm volatile("bar.sync 1, 64;" ::: "memory"); }
+
+template <typename CT>
+__device__ __forceinline__ CT reduce4(CT v) {
+  v.x += __shfl_xor_sync(0xffffffffu, v.x, 1); v.y += __shfl_xor_sync(0xffffffffu, v.y, 1);
+  v.x += __shfl_xor_sync(0xffffffffu, v.x, 2); v.y += __shfl_xor_sync(0xffffffffu, v.y, 2);
+  return v;
+}
+
 template <typename CT, int NPAD>
 __device__ __forceinline__ void subvol_solve(const CT* __restrict__ F, CT* rhs, CT* y, CT* tvec, CT* red) {
   constexpr int NB = NPAD / LA_BLK;
+  (void)red;
   const int tid = threadIdx.x;
-  {  // forward: y_I = inv(L_II) (rhs_I - sum_{J<I} L_IJ y_J)
-    const int r = tid >> 3, l = tid & 7;
-    for (int I = 0; I < NB; ++I) {
-      const CT* rowblk = F + (size_t)(I * (I + 1) / 2) * 256;
-      CT acc = mkc<CT>(0, 0), acc1 = mkc<CT>(0, 0);
-      for (int J = 0; J < I; ++J) {
-        const CT* blk = rowblk + J * 256 + r * LA_BLK;
-        cfma(acc, blk[l], y[J * LA_BLK + l]);
-        cfma(acc1, blk[l + 8], y[J * LA_BLK + l + 8]);
-      }
-      acc.x += acc1.x; acc.y += acc1.y;
-      acc.x += __shfl_xor_sync(0xffffffffu, acc.x, 1); acc.y += __shfl_xor_sync(0xffffffffu, acc.y, 1);
-      acc.x += __shfl_xor_sync(0xffffffffu, acc.x, 2); acc.y += __shfl_xor_sync(0xffffffffu, acc.y, 2);
-      acc.x += __shfl_xor_sync(0xffffffffu, acc.x, 4); acc.y += __shfl_xor_sync(0xffffffffu, acc.y, 4);
-      if (l == 0) tvec[r] = mkc<CT>(rhs[I * LA_BLK + r].x - acc.x, rhs[I * LA_BLK + r].y - acc.y);
-      __syncthreads();
-      const CT* dblk = rowblk + I * 256 + r * LA_BLK;
-      acc = mkc<CT>(0, 0);
-      if (l <= r) cfma(acc, dblk[l], tvec[l]);
-      if (l + 8 <= r) cfma(acc, dblk[l + 8], tvec[l + 8]);
-      acc.x += __shfl_xor_sync(0xffffffffu, acc.x, 1); acc.y += __shfl_xor_sync(0xffffffffu, acc.y, 1);
-      acc.x += __shfl_xor_sync(0xffffffffu, acc.x, 2); acc.y += __shfl_xor_sync(0xffffffffu, acc.y, 2);
-      acc.x += __shfl_xor_sync(0xffffffffu, acc.x, 4); acc.y += __shfl_xor_sync(0xffffffffu, acc.y, 4);
-      if (l == 0) y[I * LA_BLK + r] = acc;
-      __syncthreads();
+  if (tid >= 64) return;
+  const int r = tid >> 2, l = tid & 3;
+  // forward: y_I = inv(L_II) (rhs_I - sum_{J<I} L_IJ y_J)
+  for (int I = 0; I < NB; ++I) {
+    const CT* rowblk = F + (size_t)(I * (I + 1) / 2) * 256;
+    CT acc0 = mkc<CT>(0, 0), acc1 = mkc<CT>(0, 0);
+    for (int J = 0; J < I; ++J) {
+      const CT* blk = rowblk + J * 256 + r * LA_BLK;
+      const CT* yy = y + J * LA_BLK;
+      cfma(acc0, blk[l], yy[l]);
+      cfma(acc1, blk[l + 4], yy[l + 4]);
+      cfma(acc0, blk[l + 8], yy[l + 8]);
+      cfma(acc1, blk[l + 12], yy[l + 12]);
     }
+    CT acc = reduce4(mkc<CT>(acc0.x + acc1.x, acc0.y + acc1.y));
+    if (l == 0) tvec[r] = mkc<CT>(rhs[I * LA_BLK + r].x - acc.x, rhs[I * LA_BLK + r].y - acc.y);
+    solve_bar();
+    const CT* dblk = rowblk + I * 256 + r * LA_BLK;
+    acc0 = mkc<CT>(0, 0);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const int c = l + 4 * k;
+      if (c <= r) cfma(acc0, dblk[c], tvec[c]);
+    }
+    acc = reduce4(acc0);
+    if (l == 0) y[I * LA_BLK + r] = acc;
+    solve_bar();
   }
-  {  // backward: x_I = inv(L_II)^dagger (y_I - sum_{J>I} L_JI^dagger x_J), x stored in rhs
-    const int r = tid & 15, gq = tid >> 4;
-    for (int I = NB - 1; I >= 0; --I) {
-      CT acc = mkc<CT>(0, 0), acc1 = mkc<CT>(0, 0);
-      for (int J = I + 1; J < NB; ++J) {
-        const CT* blk = F + (size_t)(J * (J + 1) / 2 + I) * 256;
-        cfma_conj(acc, blk[gq * LA_BLK + r], rhs[J * LA_BLK + gq]);
-        cfma_conj(acc1, blk[(gq + 8) * LA_BLK + r], rhs[J * LA_BLK + gq + 8]);
-      }
-      acc.x += acc1.x; acc.y += acc1.y;
-      red[gq * LA_BLK + r] = acc;
-      __syncthreads();
-      if (tid < LA_BLK) {
-        CT s = y[I * LA_BLK + tid];
-        for (int q = 0; q < 8; ++q) { s.x -= red[q * LA_BLK + tid].x; s.y -= red[q * LA_BLK + tid].y; }
-        tvec[tid] = s;
-      }
-      __syncthreads();
-      const CT* dblk = F + (size_t)(I * (I + 1) / 2 + I) * 256;
-      acc = mkc<CT>(0, 0);
-      if (gq >= r) cfma_conj(acc, dblk[gq * LA_BLK + r], tvec[gq]);
-      if (gq + 8 >= r) cfma_conj(acc, dblk[(gq + 8) * LA_BLK + r], tvec[gq + 8]);
-      red[gq * LA_BLK + r] = acc;
-      __syncthreads();
-      if (tid < LA_BLK) {
-        CT s = mkc<CT>(0, 0);
-        for (int q = 0; q < 8; ++q) { s.x += red[q * LA_BLK + tid].x; s.y += red[q * LA_BLK + tid].y; }
-        rhs[I * LA_BLK + tid] = s;
-      }
-      __syncthreads();
+  // backward: x_I = inv(L_II)^dagger (y_I - sum_{J>I} L_JI^dagger x_J), x stored in rhs
+  for (int I = NB - 1; I >= 0; --I) {
+    CT acc0 = mkc<CT>(0, 0), acc1 = mkc<CT>(0, 0);
+    for (int J = I + 1; J < NB; ++J) {
+      const CT* blk = F + (size_t)(J * (J + 1) / 2 + I) * 256;
+      const CT* xx = rhs + J * LA_BLK;
+      cfma_conj(acc0, blk[l * LA_BLK + r], xx[l]);
+      cfma_conj(acc1, blk[(l + 4) * LA_BLK + r], xx[l + 4]);
+      cfma_conj(acc0, blk[(l + 8) * LA_BLK + r], xx[l + 8]);
+      cfma_conj(acc1, blk[(l + 12) * LA_BLK + r], xx[l + 12]);
     }
+    CT acc = reduce4(mkc<CT>(acc0.x + acc1.x, acc0.y + acc1.y));
+    if (l == 0) tvec[r] = mkc<CT>(y[I * LA_BLK + r].x - acc.x, y[I * LA_BLK + r].y - acc.y);
+    solve_bar();
+    const CT* dblk = F + (size_t)(I * (I + 1) / 2 + I) * 256;
+    acc0 = mkc<CT>(0, 0);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const int cc = l + 4 * k;
+      if (cc >= r) cfma_conj(acc0, dblk[cc * LA_BLK + r], tvec[cc]);
+    }
+    acc = reduce4(acc0);
+    if (l == 0) rhs[I * LA_BLK + r] = acc;
+    solve_bar();
   }
 }
 
@@ -651,6 +663,7 @@ k_sweep_fine(LevelGeom L, FineOp g, const TimeMats* __restrict__ tm, const typen
   }
   __syncthreads();
   subvol_solve<CT, NPAD>(factors + (size_t)b * L.fsize, sRhs, sY, sT, sRed);
+  __syncthreads();
   for (int t = tid; t < npts * K; t += kSweepThreads) {
     const int i = t / K, m = t % K;
     int lx, ly, lz;
@@ -798,6 +811,7 @@ k_sweep_coarse(LevelGeom L, const double* __restrict__ sigma, const TimeMats* __
   CoarseSmem<R> S = coarse_smem_layout<R>(smem, L, K, NPAD);
   coarse_rhs<R>(L, sigma, tm, gvec, ev, o, e, NPAD, S);
   subvol_solve<CT, NPAD>(factors + (size_t)b * L.fsize, S.Rhs, S.Y, S.T, S.Red);
+  __syncthreads();
   for (int t = threadIdx.x; t < npts * K; t += kSweepThreads) {
     const int i = t / K, m = t % K;
     int lx, ly, lz;
@@ -835,8 +849,10 @@ k_gresid_tiles(LevelGeom L, const double* __restrict__ sigma, const TimeMats* __
 // ======================================================================== host dispatch
 inline size_t factor_smem(const LevelGeom& L, int nptsmax, size_t csize, bool fine) {
   const size_t ntri = (size_t)L.npad * (L.npad + 1) / 2;
+  const size_t npair = (size_t)nptsmax * (nptsmax + 1) / 2;
+  (void)fine;
   return csize * (ntri + L.npad) + (size_t)L.npad * (csize / 2) +
-         sizeof(double) * (LA_NPAIR * LA_KMAX * LA_KMAX + (size_t)nptsmax * nptsmax * (fine ? 2 : LA_NPAIR));
+         sizeof(double) * (LA_NPAIR * LA_KMAX * LA_KMAX + npair * LA_NPAIR) + sizeof(int) * (npair + 1);
 }
 inline size_t sweep_fine_smem(const LevelGeom& L, int K, size_t rsize, size_t csize) {
   const int sx = L.sub[0] + 4, sy = L.dim > 1 ? L.sub[1] + 4 : 1, sz = L.dim > 2 ? L.sub[2] + 4 : 1;
