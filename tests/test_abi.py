@@ -58,3 +58,14 @@ def test_init_rejects_invalid_configs_without_touching_the_gpu():
     cfg.sub[0] = cfg.sub[1] = 8   # 64 points per subvolume > 32
     with pytest.raises(B.LeastActionError):
         B.Context(cfg)
+
+
+def test_allocation_failure_reports_enomem(monkeypatch):
+    """LA_FAIL_ALLOC refuses every device allocation: la_init returns LA_ENOMEM and frees what it holds."""
+    from paper_1111_4363_gb300 import binding as B
+    from paper_1111_4363_gb300 import workloads as wl
+    monkeypatch.setenv("LA_FAIL_ALLOC", "1")
+    cfg = B.config_from_workload(wl.softcore_2d(n=32, levels=3))
+    with pytest.raises(B.LeastActionError, match="LA_FAIL_ALLOC") as e:
+        B.Context(cfg)
+    assert e.value.status == B.LA_ENOMEM
