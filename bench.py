@@ -13,6 +13,7 @@ shard).  ``--impl reference`` times the CPU oracle on the same workload instead.
 from __future__ import annotations
 
 import argparse
+import dataclasses
 import json
 import os
 import statistics
@@ -119,6 +120,8 @@ def run_ours(args):
     from paper_1111_4363_gb300 import binding as B
 
     w = workload(args.workload)
+    if args.trial >= 0:
+        w = dataclasses.replace(w, trial=args.trial)
     cfg = B.config_from_workload(w, precision=args.precision)
     ctx = B.Context(cfg)
     V0 = torch.tensor(wl.potential(w).ravel(), dtype=torch.float64, device="cuda")
@@ -209,7 +212,7 @@ def run_ours(args):
            "scaling": "weak", "vs_baseline": None, "dtype": prec_tag, "data": "synthetic",
            "config": {"workload": w.name, "grid": list(w.shape), "K": w.nt, "subvolume": list(w.sub[:w.dim]),
                       "levels": w.levels, "cycle": f"V({w.nu1},{w.nu2})", "coarse_sweeps": w.coarse_sweeps,
-                      "tol_rel_action": w.tol, "precision": args.precision,
+                      "tol_rel_action": w.tol, "precision": args.precision, "trial": w.trial,
                       "parallelism": "replicas" if ws > 1 else "single",
                       "l2": "inputs smaller than L2; each step rewrites the 352 MB factor store (> L2)"},
            "cycles_per_step": cycles / args.steps, "fine_sweeps_per_step": sweeps / args.steps,
@@ -408,6 +411,8 @@ def main():
     ap.add_argument("--n3d", type=int, default=128)
     ap.add_argument("--precision", type=int, default=0, choices=[0, 1])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--trial", type=int, default=-1, choices=[-1, 0, 1, 2, 3],
+                    help="trial iterate of each step (extrapolation order + 1); -1: the workload's setting")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

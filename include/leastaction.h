@@ -74,6 +74,10 @@ typedef struct {
   int laser_axis;       /* axis of the dipole coupling E(t) x_axis */
   int ckpt_every;       /* > 0: la_step keeps psi every ckpt_every steps for la_backward; 0: no recording */
   int coarse_sub[3];    /* subvolume extent on the Galerkin levels (>= 2 on used axes); 0 = same as sub */
+  int trial;            /* trial function of each la_step step, which the relaxation corrects (Sec. IV,
+                           Eq. leastaction_correction): 0 = c = 0; 1..3 = extrapolation, polynomial of
+                           degree trial-1 in the step index, of the last `trial` converged coefficient
+                           vectors of the same propagation */
 } la_config;
 
 /* Laser field E(t) = sum_k amp[k] * env_k(t) * sin(omega[k] t), env_k = exp(-((t - t_center[k])/sigma[k])^2)
@@ -107,6 +111,12 @@ la_status la_set_hamiltonian(la_ctx* ctx, const double* V0, const la_pulse* puls
    least-action steps starting at time t0.  per_step (host, nullable) receives nsteps records.
    Each step: time matrices (Sec. IV Legendre overlaps, Gauss-Legendre quadrature of E(t)), subvolume
    factorisation on every level, V-cycles until N/N(0) <= tol, then psi(t0+dt) = phi(tau = 1).
+   N(0) = f^dagger W f is the action of c = 0 in every case.  With cfg.trial > 0 the relaxation of a
+   step starts from c extrapolated from the preceding steps' converged coefficients (1, 2 or 3 of
+   them: constant, linear, quadratic in the step index) when that trial has a smaller action than
+   c = 0, else from c = 0.  The history is kept across calls whose t0 continues the previous call,
+   and cleared at every checkpoint (ckpt_every > 0), by la_set_hamiltonian and by la_backward, so
+   the recomputation in la_backward repeats the forward iterates exactly.
    Returns LA_ENOTCONV if some step hit max_cycles (psi is still advanced). */
 la_status la_step(la_ctx* ctx, void* psi, int nsteps, double t0, la_step_stats* per_step);
 

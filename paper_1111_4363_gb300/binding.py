@@ -35,7 +35,7 @@ class la_config(C.Structure):
                 ("sub", C.c_int * 3), ("levels", C.c_int), ("nu1", C.c_int), ("nu2", C.c_int),
                 ("coarse_sweeps", C.c_int), ("max_cycles", C.c_int), ("tol", C.c_double), ("weight", C.c_int),
                 ("precision", C.c_int), ("laser_axis", C.c_int), ("ckpt_every", C.c_int),
-                ("coarse_sub", C.c_int * 3)]
+                ("coarse_sub", C.c_int * 3), ("trial", C.c_int)]
 
 
 class la_pulse(C.Structure):
@@ -133,6 +133,7 @@ def config_from_workload(w, precision: int = 0, **overrides) -> la_config:
     if getattr(w, "coarse_sub", None) is not None:
         for a in range(w.dim):
             cfg.coarse_sub[a] = w.coarse_sub[a]
+    cfg.trial = getattr(w, "trial", 0)
     for k, v in overrides.items():
         setattr(cfg, k, v)
     return cfg

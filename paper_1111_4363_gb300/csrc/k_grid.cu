@@ -1,5 +1,7 @@
 // Grid-wide kernels: per-step time matrices, right-hand side, action residual and residual
 // norm, normal residual, Galerkin-level residual, intergrid transfers, step advance.
+#include <algorithm>
+
 #include "la_internal.cuh"
 
 namespace la {
@@ -459,6 +461,23 @@ __global__ void k_scale_c128(long long n, double a, const double2* __restrict__ 
 }
 void launch_scale_c128(long long n, double a, const double2* x, double2* y, cudaStream_t s) {
   k_scale_c128<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, a, x, y);
+}
+// Trial coefficients c = a0 h0 + a1 h1 + a2 h2 (h1, h2 nullable), the extrapolation of the last
+// converged coefficient vectors h0 (newest), h1, h2 of a propagation.
+__global__ void k_trial(long long n, double a0, double a1, double a2, const double2* __restrict__ h0,
+                        const double2* __restrict__ h1, const double2* __restrict__ h2, double2* __restrict__ c) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const double2 v = h0[i];
+    double re = a0 * v.x, im = a0 * v.y;
+    if (h1) { const double2 u = h1[i]; re = fma(a1, u.x, re); im = fma(a1, u.y, im); }
+    if (h2) { const double2 u = h2[i]; re = fma(a2, u.x, re); im = fma(a2, u.y, im); }
+    c[i] = make_double2(re, im);
+  }
+}
+void launch_trial(long long n, const double* a, const double2* h0, const double2* h1, const double2* h2, double2* c,
+                  cudaStream_t s) {
+  const long long nb = std::min<long long>((n + 255) / 256, 152LL * 8);
+  k_trial<<<(unsigned)nb, 256, 0, s>>>(n, a[0], a[1], a[2], h0, h1, h2, c);
 }
 void launch_c128_to_c64(long long n, const double2* x, float2* y, cudaStream_t s) {
   k_c128_to_c64<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, x, y);

@@ -59,6 +59,10 @@ struct la_ctx {
   double* d_grad = nullptr;
   int seg_cap = 0;
   double last_N = 0.0, last_rel = 0.0;
+  // converged coefficients of the last steps of the current propagation (trial extrapolation)
+  double2* d_hist[3] = {};
+  int nhist = 0, hist_head = 0;     // valid vectors; slot of the next push
+  double hist_t_next = 0.0;         // start time of the step the history continues into
   std::vector<void*> allocs;
   // profiling
   bool prof = false;
@@ -281,6 +285,7 @@ extern "C" la_status la_init(const la_config* cfg, void* stream, la_ctx** out) {
   else if (k.precision < 0 || k.precision > 1) bad("precision must be 0 or 1");
   else if (k.laser_axis < 0 || k.laser_axis >= k.dim) bad("laser_axis must be a used axis");
   else if (k.ckpt_every < 0) bad("ckpt_every must be >= 0");
+  else if (k.trial < 0 || k.trial > 3) bad("trial must be 0..3");
   if (st == LA_OK) {
     for (int a = 0; a < 3 && st == LA_OK; ++a) {
       if (a < k.dim) {
@@ -391,6 +396,7 @@ extern "C" la_status la_init(const la_config* cfg, void* stream, la_ctx** out) {
   ALLOC(c->d_partials, sizeof(double) * c->nparts);
   ALLOC(c->d_N, sizeof(double) * 2);
   ALLOC(c->d_status, sizeof(int));
+  for (int j = 0; j < k.trial; ++j) ALLOC(c->d_hist[j], sizeof(double2) * (size_t)c->nunk0);
 #undef ALLOC
   c->fine.V0 = c->d_V0;
   c->use_graph = getenv("LA_NO_GRAPH") == nullptr;
@@ -519,6 +525,7 @@ extern "C" la_status la_set_hamiltonian(la_ctx* c, const double* V0, const la_pu
   }
   LA_CUDA(c, cudaStreamSynchronize(c->stream));
   c->have_ham = true;
+  c->nhist = 0;
   return LA_OK;
 }
 
@@ -649,15 +656,16 @@ static la_status vcycle(la_ctx* c, int l) {
   return sweep_level<R>(c, l, k.nu2);
 }
 
-// N of the current FP64 iterate (stores r~ = f~ - M~ c in d_r); synchronises.
-static la_status action_enqueue(la_ctx* c) {
+// N of the current FP64 iterate into h_N[slot] (stores r~ = f~ - M~ c in d_r); enqueue only.
+static la_status action_enqueue(la_ctx* c, int slot = 0) {
   launch_mresid<double>(c->fine, c->d_tm, c->d_f, c->d_c, c->d_r, nullptr, c->d_partials, c->nparts, c->stream);
   launch_norm_final(c->d_partials, c->nparts, c->nscale, c->d_N, c->stream);
   c->launches += 2;
   LA_CHECK_LAUNCH(c);
-  LA_CUDA(c, cudaMemcpyAsync(c->h_N, c->d_N, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  LA_CUDA(c, cudaMemcpyAsync(c->h_N + slot, c->d_N, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
   return LA_OK;
 }
+// N of the current FP64 iterate; synchronises.
 static la_status action_now(la_ctx* c, double* N) {
   LA_TRY(action_enqueue(c));
   LA_CUDA(c, cudaStreamSynchronize(c->stream));
@@ -754,15 +762,66 @@ static la_status setup_step(la_ctx* c, double t0) {
   return LA_OK;
 }
 
-// Relax the step's coefficients from c = 0.  ncycles > 0: exactly that many cycles.
-static la_status solve_current(la_ctx* c, int ncycles, la_step_stats* st) {
+// ------------------------------------------------------------------ trial iterate
+// The relaxation corrects a trial function (Sec. IV, Eq. leastaction_correction).  The trial of a
+// step is the polynomial in the step index through the last q converged coefficient vectors
+// (q = 1, 2, 3: constant, linear, quadratic), evaluated at the new step.
+static const double kTrialW[3][3] = {{1.0, 0.0, 0.0}, {2.0, -1.0, 0.0}, {3.0, -3.0, 1.0}};
+
+static la_status hist_push(la_ctx* c) {
+  const int T = c->cfg.trial;
+  if (T <= 0) return LA_OK;
+  LA_CUDA(c, cudaMemcpyAsync(c->d_hist[c->hist_head], c->d_c, sizeof(double2) * (size_t)c->nunk0,
+                             cudaMemcpyDeviceToDevice, c->stream));
+  c->hist_head = (c->hist_head + 1) % T;
+  c->nhist = std::min(c->nhist + 1, T);
+  return LA_OK;
+}
+
+// Enqueue the starting iterate of a step: N(0) into h_N[1]; with a history (and use_trial) the
+// extrapolated trial into d_c and its action into h_N[0].  d_r ends as the residual of d_c.
+static la_status seed_enqueue(la_ctx* c, bool use_trial, bool* tried) {
+  LA_CUDA(c, cudaMemsetAsync(c->d_c, 0, sizeof(double2) * (size_t)c->nunk0, c->stream));
+  LA_TRY(action_enqueue(c, 1));
+  *tried = false;
+  if (use_trial && c->cfg.trial > 0 && c->nhist > 0) {
+    const int T = c->cfg.trial, q = c->nhist;
+    const double2* h[3] = {nullptr, nullptr, nullptr};
+    for (int j = 0; j < q; ++j) h[j] = c->d_hist[((c->hist_head - 1 - j) % T + T) % T];
+    launch_trial(c->nunk0, kTrialW[q - 1], h[0], h[1], h[2], c->d_c, c->stream);
+    ++c->launches;
+    LA_CHECK_LAUNCH(c);
+    LA_TRY(action_enqueue(c, 0));
+    *tried = true;
+  }
+  return LA_OK;
+}
+
+// After the stream has synchronised: N0 = N(0); N = N of the starting iterate.  A trial whose
+// action is not below N(0) is replaced by c = 0.
+static la_status seed_finish(la_ctx* c, bool tried, double* N0, double* N) {
+  *N0 = c->h_N[1];
+  *N = *N0;
+  if (!tried) return LA_OK;
+  *N = c->h_N[0];
+  if (!(*N < *N0)) {
+    LA_CUDA(c, cudaMemsetAsync(c->d_c, 0, sizeof(double2) * (size_t)c->nunk0, c->stream));
+    LA_TRY(action_now(c, N));
+  }
+  return LA_OK;
+}
+
+// Relax the step's coefficients from c = 0, or from the trial when use_trial.  ncycles > 0:
+// exactly that many cycles.
+static la_status solve_current(la_ctx* c, int ncycles, la_step_stats* st, bool use_trial = false) {
   const la_config& k = c->cfg;
   if (k.precision == 0) LA_TRY(factor_all<double>(c));
   else LA_TRY(factor_all<float>(c));
-  LA_CUDA(c, cudaMemsetAsync(c->d_c, 0, sizeof(double2) * (size_t)c->nunk0, c->stream));
+  bool tried = false;
+  LA_TRY(seed_enqueue(c, use_trial, &tried));
+  LA_CUDA(c, cudaStreamSynchronize(c->stream));
   double N0 = 0.0, N = 0.0;
-  LA_TRY(action_now(c, &N0));
-  N = N0;
+  LA_TRY(seed_finish(c, tried, &N0, &N));
   int cyc = 0;
   const int maxc = ncycles > 0 ? ncycles : k.max_cycles;
   const bool check = ncycles <= 0 && k.tol > 0;
@@ -799,6 +858,8 @@ extern "C" la_status la_step(la_ctx* c, void* psi, int nsteps, double t0, la_ste
   LA_CUDA(c, cudaMemcpyAsync(c->d_psi, psi, bytes, dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->stream));
   la_status worst = LA_OK;
   const int C = c->cfg.ckpt_every;
+  // the trial history continues only a propagation that ended at t0
+  if (!(std::fabs(t0 - c->hist_t_next) <= 1e-9 * std::fabs(c->cfg.dt))) c->nhist = 0;
   if (C > 0 && nsteps > 0) {
     const int need = (nsteps + C - 1) / C;
     if (need > c->ckpt_cap) {
@@ -812,16 +873,20 @@ extern "C" la_status la_step(la_ctx* c, void* psi, int nsteps, double t0, la_ste
     c->have_rec = true;
   }
   for (int s = 0; s < nsteps; ++s) {
-    if (C > 0 && s % C == 0)
+    if (C > 0 && s % C == 0) {
       LA_CUDA(c, cudaMemcpyAsync(c->d_ckpt + (size_t)(s / C) * c->np0, c->d_psi, bytes, cudaMemcpyDeviceToDevice,
                                  c->stream));
+      c->nhist = 0;   // a segment's iterates depend only on its checkpoint (exact recomputation)
+    }
     LA_TRY(setup_step(c, t0 + s * c->cfg.dt));
-    la_status st = solve_current(c, 0, per_step ? per_step + s : nullptr);
+    la_status st = solve_current(c, 0, per_step ? per_step + s : nullptr, true);
     if (st == LA_ENOTCONV) worst = LA_ENOTCONV;
     else if (st != LA_OK) return st;
     launch_advance(c->np0, c->d_tm, c->d_c, c->d_psi, c->stream);
     ++c->launches;
     LA_CHECK_LAUNCH(c);
+    LA_TRY(hist_push(c));
+    c->hist_t_next = t0 + (s + 1) * c->cfg.dt;
   }
   prof_drain(c);
   LA_CUDA(c, cudaMemcpyAsync(psi, c->d_psi, bytes, dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->stream));
@@ -902,16 +967,18 @@ extern "C" la_status la_backward(la_ctx* c, const void* dJ_dpsiT, double* grad_a
     const int k0 = sgm * C, k1 = std::min(k0 + C, nsteps);
     // recompute the segment's states and converged coefficients from its checkpoint
     LA_CUDA(c, cudaMemcpyAsync(c->d_psi, c->d_ckpt + (size_t)sgm * c->np0, vb, cudaMemcpyDeviceToDevice, c->stream));
+    c->nhist = 0;
     for (int kk = k0; kk < k1; ++kk) {
       LA_CUDA(c, cudaMemcpyAsync(c->d_seg_psi + (size_t)(kk - k0) * c->np0, c->d_psi, vb, cudaMemcpyDeviceToDevice,
                                  c->stream));
       LA_TRY(setup_step(c, c->rec_t0 + kk * c->cfg.dt));
-      la_status st = solve_current(c, 0, nullptr);
+      la_status st = solve_current(c, 0, nullptr, true);
       if (st != LA_OK && st != LA_ENOTCONV) return st;
       LA_CUDA(c, cudaMemcpyAsync(c->d_seg_c + (size_t)(kk - k0) * c->nunk0, c->d_c, cb, cudaMemcpyDeviceToDevice,
                                  c->stream));
       launch_advance(c->np0, c->d_tm, c->d_c, c->d_psi, c->stream);
       ++c->launches;
+      LA_TRY(hist_push(c));
     }
     // backward through the segment
     for (int kk = k1 - 1; kk >= k0; --kk) {
@@ -931,6 +998,7 @@ extern "C" la_status la_backward(la_ctx* c, const void* dJ_dpsiT, double* grad_a
       LA_CHECK_LAUNCH(c);
     }
   }
+  c->nhist = 0;   // the history now belongs to the recomputation
   if (dJ_dpsi0) LA_TRY(store_any(c, dJ_dpsi0, c->d_lam, vb));
   if (grad_amp && c->htm.ncomp > 0)
     LA_CUDA(c, cudaMemcpyAsync(grad_amp, c->d_grad, sizeof(double) * c->htm.ncomp, cudaMemcpyDeviceToHost, c->stream));
@@ -954,6 +1022,7 @@ extern "C" la_status la_step_batch(la_ctx* const* ctxs, int nctx, void* const* p
   std::vector<char> dev(nctx);
   std::vector<double> N0(nctx), N(nctx);
   std::vector<int> cyc(nctx), active(nctx);
+  std::vector<char> tried(nctx);
   la_status worst = LA_OK;
   // every context works on its own internal stream for the whole call (forked from its stream)
   for (int i = 0; i < nctx; ++i) {
@@ -963,6 +1032,7 @@ extern "C" la_status la_step_batch(la_ctx* const* ctxs, int nctx, void* const* p
     LA_CUDA(c, cudaStreamWaitEvent(c->cap, c->ev_fork, 0));
     c->stream = c->cap;
     dev[i] = is_device_ptr(psis[i]);
+    if (!(std::fabs(t0s[i] - c->hist_t_next) <= 1e-9 * std::fabs(c->cfg.dt))) c->nhist = 0;
     LA_CUDA(c, cudaMemcpyAsync(c->d_psi, psis[i], sizeof(double2) * (size_t)c->np0,
                                dev[i] ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->stream));
   }
@@ -972,14 +1042,14 @@ extern "C" la_status la_step_batch(la_ctx* const* ctxs, int nctx, void* const* p
       la_ctx* c = ctxs[i];
       st = setup_step(c, t0s[i] + s * c->cfg.dt);
       if (st == LA_OK) st = c->cfg.precision == 0 ? factor_all<double>(c) : factor_all<float>(c);
-      if (st == LA_OK && cudaMemsetAsync(c->d_c, 0, sizeof(double2) * (size_t)c->nunk0, c->stream) != cudaSuccess)
-        st = fail(c, LA_ECUDA, "memset failed");
-      if (st == LA_OK) st = action_enqueue(c);
+      bool tr = false;
+      if (st == LA_OK) st = seed_enqueue(c, true, &tr);
+      tried[i] = tr;
     }
     for (int i = 0; i < nctx && st == LA_OK; ++i) {
-      st = cycle_complete(ctxs[i], &N0[i]);
-      --ctxs[i]->cycles_run;   // the initial action is not a cycle
-      N[i] = N0[i];
+      la_ctx* c = ctxs[i];
+      if (cudaStreamSynchronize(c->stream) != cudaSuccess) st = fail(c, LA_ECUDA, "synchronisation failed");
+      if (st == LA_OK) st = seed_finish(c, tried[i], &N0[i], &N[i]);
       cyc[i] = 0;
       active[i] = 1;
     }
@@ -1024,6 +1094,8 @@ extern "C" la_status la_step_batch(la_ctx* const* ctxs, int nctx, void* const* p
       if (c->cfg.tol > 0 && !(N[i] <= c->cfg.tol * N0[i])) worst = LA_ENOTCONV;
       launch_advance(c->np0, c->d_tm, c->d_c, c->d_psi, c->stream);
       ++c->launches;
+      st = hist_push(c);
+      c->hist_t_next = t0s[i] + (s + 1) * c->cfg.dt;
     }
   }
   // results back, streams restored and joined

@@ -205,6 +205,8 @@ void launch_advance(int np, const TimeMats* tm, const double2* c, double2* psi, 
 void launch_axpy_c64_to_c128(long long n, const float2* x, double2* y, cudaStream_t s);
 void launch_c128_to_c64(long long n, const double2* x, float2* y, cudaStream_t s);
 void launch_scale_c128(long long n, double a, const double2* x, double2* y, cudaStream_t s);
+void launch_trial(long long n, const double* a, const double2* h0, const double2* h1, const double2* h2, double2* c,
+                  cudaStream_t s);
 // Galerkin coarse stencils
 void launch_galerkin_from_fine(const FineOp& g, const LevelGeom& coarse, double* sigma_c, cudaStream_t s);
 void launch_galerkin_coarse(const LevelGeom& fine, const double* sigma_f, const LevelGeom& coarse, double* sigma_c,

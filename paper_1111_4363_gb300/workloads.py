@@ -62,6 +62,7 @@ class Workload:
     psi_kind: str = "gaussian"       # "displaced_noisy" | "gaussian"
     seed: int = 0
     coarse_sub: Optional[Tuple[int, int, int]] = None   # subvolume extent on Galerkin levels (None: sub)
+    trial: int = 0                 # la_step trial iterate: 0 = zero, 1..3 = extrapolation from 1..3 steps
 
     @property
     def shape(self) -> Tuple[int, ...]:

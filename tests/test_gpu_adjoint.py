@@ -44,9 +44,10 @@ def run_forward(w, precision, psi0, nsteps, ckpt):
     return ctx, psi
 
 
-@pytest.mark.parametrize("kind,precision", [("1d", 0), ("2d", 0), ("2d", 1), ("3d", 0)])
-def test_backward_matches_oracle_adjoint(kind, precision):
-    w = pulsed(kind)
+@pytest.mark.parametrize("kind,precision,trial", [("1d", 0, 0), ("2d", 0, 0), ("2d", 1, 0), ("3d", 0, 0),
+                                                 ("2d", 0, 3), ("3d", 1, 3)])
+def test_backward_matches_oracle_adjoint(kind, precision, trial):
+    w = dataclasses.replace(pulsed(kind), trial=trial)
     nsteps, ckpt = 5, 2          # segments of 2, 2, 1 steps
     prob = system.Problem.from_workload(w)
     psi0 = wl.initial_state(w).ravel()

@@ -28,11 +28,11 @@ def members():
     return [a, b, c]
 
 
-@pytest.mark.parametrize("precision", [0, 1])
-def test_batch_equals_individual_steps(precision):
+@pytest.mark.parametrize("precision,trial", [(0, 0), (1, 0), (0, 3), (1, 3)])
+def test_batch_equals_individual_steps(precision, trial):
     import torch
     from paper_1111_4363_gb300 import binding as B
-    ws = members()
+    ws = [dataclasses.replace(w, trial=trial) for w in members()]
     nsteps = 3
     alone = []
     for w in ws:
