@@ -1,11 +1,13 @@
 """Benchmark: spacetime unknowns relaxed per second of the least-action propagator on one GB300.
 
 A "step" is one least-action time step of the 2D soft-core workload (256 x 256 points, K = 6
-Legendre time functions, 4 x 4-point subvolumes, 4-level V(1,1) cycles, FP64, tolerance 1e-10 on
+Legendre time functions, 4 x 4-point subvolumes, 4-level V(1,2) cycles, FP64, tolerance 1e-10 on
 N/N(0)): time matrices, right-hand side, subvolume factorisation on every level, V-cycles to
-tolerance, step advance.  Metric = (finest-level unknowns) x (finest-level sweeps) / time.
+tolerance from the trial extrapolated from the last three steps, step advance.
+Metric = (finest-level unknowns) x (finest-level sweeps) / time.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--precision 0|1]
+                  [--workload 2d|2d-small|1d|batched|3d-adjoint] [--trial -1|0..3]
 
 N > 1 runs N independent replicas (one propagation per rank, no collective: the path does not
 shard).  ``--impl reference`` times the CPU oracle on the same workload instead.
@@ -33,16 +35,26 @@ METRIC = "spacetime unknowns relaxed/s"
 # DRAM bytes (read + write) per finest-level subvolume from one ncu capture of the current kernels
 # (profiles/k_sweep_fine_2d_softcore_128x128_fp64.md, profiles/k_factor_2d_softcore_128x128_fp64.md),
 # scaled to a launch by the number of subvolumes it processes.  Set to None when a kernel changes.
-NCU_BYTES_PER_SUBVOLUME = {}   # (kernel class, precision) -> DRAM bytes per subvolume from one ncu capture
+# (kernel class, precision) -> DRAM bytes (read + write) per finest-level subvolume, from one ncu capture of
+# the 2D 256x256 workload: the finest k_factor launch (4096 subvolumes) and one full k_sweep_fine sweep
+# (four colour launches, 4096 subvolumes)
+NCU_BYTES_PER_SUBVOLUME = {("factor", 0): (709120 + 307017216) / 4096,
+                           ("sweep", 0): (396126976 + 49786112) / 4096}
 FP64_PEAK_TFLOPS = 152 * 4 * 2070e6 / 1e12   # 152 SMs x 4 FP64 flop/clk/SM x 2070 MHz (derived)
+FP32_PEAK_TFLOPS = 152 * 256 * 2070e6 / 1e12  # 152 SMs x 128 FP32 lanes x 2 flop (FMA) x 2070 MHz (derived)
 L2_BYTES = 129 * 2 ** 20
+
+
+# production schedule of the 2D workload: 4-level V(1,2) cycles started from the quadratic trial
+# (2 cycles per step to 1e-10, against 5 for V(1,1) from c = 0); --trial 0 gives the plain start
+PRODUCTION_2D = dict(nu1=1, nu2=2, trial=3)
 
 
 def workload(name: str) -> wl.Workload:
     if name == "2d":
-        return wl.softcore_2d(n=256, levels=4, nsteps=200)
+        return dataclasses.replace(wl.softcore_2d(n=256, levels=4, nsteps=200), **PRODUCTION_2D)
     if name == "2d-small":          # the same problem on 128 x 128, for ncu captures of single kernels
-        return wl.softcore_2d(n=128, levels=4, nsteps=200)
+        return dataclasses.replace(wl.softcore_2d(n=128, levels=4, nsteps=200), **PRODUCTION_2D)
     if name == "1d":
         return wl.harmonic_1d()
     raise ValueError(name)
@@ -56,7 +68,7 @@ def dist_env():
 
 
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
+    """nvidia-smi clocks and throttle reasons sampled every 100 ms during the timed region."""
     QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
@@ -70,7 +82,7 @@ class ClockSampler:
     def start(self):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.QUERY}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
@@ -192,20 +204,23 @@ def run_ours(args):
         dom, flops, dms, cls = "k_factor (finest level)", prof["flops_factor"], fac_ms, "factor"
     else:
         dom, flops, dms, cls = "k_sweep_fine (one sweep, all colours)", prof["flops_sweep"], swp_ms_full, "sweep"
-    bps = NCU_BYTES_PER_SUBVOLUME.get((cls, args.precision)) if args.workload.startswith("2d") else None
+    bps = NCU_BYTES_PER_SUBVOLUME.get((cls, args.precision)) if args.workload == "2d" else None
     traffic = round(bps * nsub) if bps else None
     achieved = flops / (dms * 1e-3) / 1e12
     prec_tag = "f64" if args.precision == 0 else "c64 local solves + f64 refinement"
-    peak = FP64_PEAK_TFLOPS
+    if args.precision == 0:
+        peak = FP64_PEAK_TFLOPS
+        peak_note = "FP64 pipe: 152 SMs x 4 flop/clk x 2070 MHz (derived); probe measured 1.19 at 1995 MHz"
+    else:
+        peak = FP32_PEAK_TFLOPS
+        peak_note = "FP32 pipe (complex64 kernel): 152 SMs x 128 lanes x 2 flop x 2070 MHz (derived)"
     roofline = {"bound": "alu", "kernel": dom, "achieved": round(achieved, 4), "peak": round(peak, 4),
                 "unit": "TFLOP/s", "frac": round(achieved / peak, 4), "traffic": traffic,
-                "traffic_note": "DRAM bytes per launch unit from one ncu capture at 128x128, scaled by subvolumes",
-                "peak_note": "FP64 pipe: 152 SMs x 4 flop/clk x 2070 MHz (derived); probe measured 1.19 at 1995 MHz",
+                "traffic_note": "DRAM read+write bytes of this kernel per launch from one ncu capture of this workload",
+                "peak_note": peak_note,
                 "kernel_ms": {"factor_per_launch": round(fac_ms, 4), "sweep_full": round(swp_ms_full, 4),
                               "factor_share": round(prof["ms_factor"] / max(ms, 1e-9), 3),
                               "sweep_share": round(prof["ms_sweep"] / max(ms, 1e-9), 3)}}
-    if args.precision == 1:
-        roofline["peak_note"] += " (mixed mode: FP32 kernels measured against the FP64 peak for comparability)"
 
     out = {"metric": METRIC, "value": value, "unit": "unknowns/s", "n_gpus": ws, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
@@ -309,13 +324,13 @@ def run_batched(args):
     """512 independent 2D propagations of uneven size (64^2 .. 256^2, K = 4): la_step_batch vs stepping
     the same contexts one after another, at the same tolerance.  The schedule is autotuned on a
     128 x 128 member."""
-    import dataclasses
     import torch
     import __graft_entry__
     __graft_entry__.build()
     from paper_1111_4363_gb300 import autotune
     from paper_1111_4363_gb300 import binding as B
-    members = [wl.batched_2d(i) for i in range(args.batch)]
+    members = [dataclasses.replace(wl.batched_2d(i), trial=3 if args.trial < 0 else args.trial)
+               for i in range(args.batch)]
     rep = dataclasses.replace(members[0], n=(128, 128, 1))
     best = autotune.tune(rep, precision=args.precision)
     ws = [dataclasses.replace(m, **best) for m in members]
@@ -371,6 +386,7 @@ def run_3d_adjoint(args):
     from paper_1111_4363_gb300 import binding as B
     n = args.n3d
     w = wl.hydrogen_3d(n=n, nsteps=args.steps)
+    w = dataclasses.replace(w, trial=3 if args.trial < 0 else args.trial)
     cfg = B.config_from_workload(w, precision=args.precision, ckpt_every=20)
     ctx = B.Context(cfg)
     ctx.set_hamiltonian(torch.tensor(wl.potential(w).ravel(), dtype=torch.float64, device="cuda"), w.pulse)
@@ -392,7 +408,8 @@ def run_3d_adjoint(args):
            "steps": args.steps, "warmup": 0, "ms_per_step": 1e3 * el_f / args.steps, "higher_is_better": True,
            "dtype": "f64" if args.precision == 0 else "c64 local solves + f64 refinement", "data": "synthetic",
            "config": {"workload": w.name, "grid": list(w.shape), "K": w.nt, "subvolume": list(w.sub),
-                      "levels": w.levels, "pulse_components": w.pulse.ncomp, "ckpt_every": 20},
+                      "levels": w.levels, "cycle": f"V({w.nu1},{w.nu2})", "trial": w.trial,
+                      "pulse_components": w.pulse.ncomp, "ckpt_every": 20},
            "cycles_per_step": sum(s_[0] for s_ in stats) / args.steps,
            "backward_ms_per_step": 1e3 * el_b / args.steps,
            "dipole_T": float(hd * (x * psi.abs() ** 2).sum()), "grad_norm": float(np.linalg.norm(grad)),
@@ -403,7 +420,7 @@ def run_3d_adjoint(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=40)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="2d", choices=["2d", "2d-small", "1d", "batched", "3d-adjoint"])

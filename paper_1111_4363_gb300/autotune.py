@@ -1,4 +1,4 @@
-"""Autotuner for the relaxation schedule: subvolume shape, Galerkin-level subvolume shape, levels.
+"""Autotuner for the relaxation schedule: subvolume shape, levels, cycle shape V(nu1, nu2).
 
 Every candidate reaches the same tolerance on N/N(0) (the minimiser does not depend on the
 schedule), so candidates are ranked by measured time per least-action step on the GPU.  The
@@ -28,16 +28,19 @@ def candidates(w: wl.Workload):
         for levels in (1, 2, 3, 4):
             if any(w.n[a] % (1 << (levels - 1)) for a in range(w.dim)):
                 continue
-            out.append(dict(sub=(sx, sy, 1), coarse_sub=(2, 2, 1), levels=levels,
-                            coarse_sweeps=1, nu1=1, nu2=1 if levels > 1 else 1))
+            # one level: nu1 + nu2 sweeps between action evaluations
+            shapes = ((1, 1), (1, 2)) if levels > 1 else ((1, 0), (1, 1), (2, 1))
+            for nu1, nu2 in shapes:
+                out.append(dict(sub=(sx, sy, 1), coarse_sub=(2, 2, 1), levels=levels,
+                                coarse_sweeps=1, nu1=nu1, nu2=nu2))
     return out
 
 
 def key(w: wl.Workload, precision: int) -> str:
-    return f"{w.dim}:{'x'.join(map(str, w.n[:w.dim]))}:K{w.nt}:p{precision}:{w.weight}"
+    return f"{w.dim}:{'x'.join(map(str, w.n[:w.dim]))}:K{w.nt}:p{precision}:{w.weight}:t{w.trial}"
 
 
-def measure(w: wl.Workload, precision: int, nsteps: int = 3, warmup: int = 1) -> dict:
+def measure(w: wl.Workload, precision: int, nsteps: int = 3, warmup: int = 3) -> dict:
     import torch
     cfg = B.config_from_workload(w, precision=precision)
     ctx = B.Context(cfg)
