@@ -227,10 +227,12 @@ k_factor(LevelGeom L, FineOp g, int is_fine, int nptsmax, const double* __restri
 
 // ------------------------------------------------------------------------ complex64 variant
 // For complex64 the whole factor fits in registers: thread (ti, tk) keeps its tile-cyclic entries
-// (16 I + ti, 16 J + tk), J <= I, in registers with compile-time tile indices, so the trailing
-// update is pure FFMA plus one shared-memory read per tile row and column (the shared-memory
-// resident form is bound by shared-memory bandwidth in FP32).  Same two barriers per column and
-// the same pivot lookahead as above.
+// (16 I + ti, 16 J + tk), J <= I, in registers with compile-time tile indices.  Blocked
+// right-looking Cholesky: the 16 columns of a panel are eliminated one by one inside the panel's
+// block column only (two barriers per column, pivot lookahead), the finished panel goes to shared
+// memory k-major, and every trailing block then takes one rank-16 update from it (row reads are
+// broadcasts, column reads are consecutive), so the per-entry bookkeeping is paid once per 16
+// columns instead of once per column.
 template <int NPAD>
 __global__ void __launch_bounds__(kFactorThreads, 2)
 k_factor_c64(LevelGeom L, FineOp g, int is_fine, int nptsmax, const double* __restrict__ sigma,
@@ -240,8 +242,8 @@ k_factor_c64(LevelGeom L, FineOp g, int is_fine, int nptsmax, const double* __re
   constexpr int NT = NB * (NB + 1) / 2;
   extern __shared__ __align__(16) unsigned char smem[];
   const int K = tm->K, KK = K * K;
-  CT* sCol = reinterpret_cast<CT*>(smem);                      // [NPAD]
-  float* sInv = reinterpret_cast<float*>(sCol + NPAD);          // [NPAD]
+  CT* sPan = reinterpret_cast<CT*>(smem);                      // [LA_BLK][NPAD] finished panel, k-major
+  float* sInv = reinterpret_cast<float*>(sPan + LA_BLK * NPAD); // [NPAD]
   CT* sDiag = reinterpret_cast<CT*>(sInv + NPAD);               // [NB][256]
   float* sP = reinterpret_cast<float*>(sDiag + NB * 256);       // [9][K*K]
   float* sPair = sP + LA_NPAIR * LA_KMAX * LA_KMAX;             // [npts*npts][nv]
@@ -327,55 +329,80 @@ k_factor_c64(LevelGeom L, FineOp g, int is_fine, int nptsmax, const double* __re
   }
   __syncthreads();
 
-  for (int j = 0; j < NPAD; ++j) {
-    const int J0 = j >> 4, jj = j & 15;
-    // (A) owners of column j scale it and publish it
-    if (tk == jj) {
-      const float inv = sInv[j];
 #pragma unroll
-      for (int I = 0; I < NB; ++I)
+  for (int J0 = 0; J0 < NB; ++J0) {
+    const int c0 = LA_BLK * J0 + tk;   // this thread's column inside the panel
+    for (int jj = 0; jj < LA_BLK; ++jj) {
+      const int j = LA_BLK * J0 + jj;
+      // (A) owners of column j scale it and publish it
+      if (tk == jj) {
+        const float inv = sInv[j];
 #pragma unroll
-        for (int J = 0; J <= I; ++J)
-          if (J == J0 && LA_BLK * I + ti > j) {
-            CT& v = a[I * (I + 1) / 2 + J];
+        for (int I = J0; I < NB; ++I) {
+          const int r = LA_BLK * I + ti;
+          if (r > j) {
+            CT& v = a[I * (I + 1) / 2 + J0];
             v.x *= inv;
             v.y *= inv;
-            sCol[LA_BLK * I + ti] = v;
+            sPan[jj * NPAD + r] = v;
           }
-    }
-    __syncthreads();
-    // (B) trailing update; the owner of the next pivot finishes it and takes its rsqrt
-    const int j1 = j + 1;
-    CT cc[NB];
+        }
+      }
+      __syncthreads();
+      if (jj == LA_BLK - 1) break;   // the panel's last column changes nothing inside the panel
+      // (B) rank-1 update of the panel right of column j; the owner of entry (j+1, j+1) takes its rsqrt
+      if (c0 > j) {
+        const CT y = sPan[jj * NPAD + c0];
 #pragma unroll
-    for (int J = 0; J < NB; ++J) {
-      const int c = LA_BLK * J + tk;
-      cc[J] = (J >= J0 && c > j) ? sCol[c] : make_float2(0.f, 0.f);
-    }
-#pragma unroll
-    for (int I = 0; I < NB; ++I) {
-      if (I < J0) continue;
-      const int r = LA_BLK * I + ti;
-      const CT xr = (r > j) ? sCol[r] : make_float2(0.f, 0.f);
-#pragma unroll
-      for (int J = 0; J <= I; ++J) {
-        if (J < J0) continue;
-        const int c = LA_BLK * J + tk;
-        if (c <= j || c > r || r <= j) continue;
-        CT& v = a[I * (I + 1) / 2 + J];
-        const CT y = cc[J];
-        v.x = fmaf(-xr.x, y.x, v.x); v.x = fmaf(-xr.y, y.y, v.x);
-        v.y = fmaf(-xr.y, y.x, v.y); v.y = fmaf(xr.x, y.y, v.y);
-        if (r == j1 && c == j1) {
+        for (int I = J0; I < NB; ++I) {
+          const int r = LA_BLK * I + ti;
+          if (r >= c0) {
+            const CT xr = sPan[jj * NPAD + r];
+            CT& v = a[I * (I + 1) / 2 + J0];
+            v.x = fmaf(-xr.x, y.x, v.x); v.x = fmaf(-xr.y, y.y, v.x);
+            v.y = fmaf(-xr.y, y.x, v.y); v.y = fmaf(xr.x, y.y, v.y);
+          }
+        }
+        if (ti == jj + 1 && tk == jj + 1) {
+          CT& v = a[J0 * (J0 + 1) / 2 + J0];
           float d2 = v.x;
           if (!(d2 > 0.f)) { atomicOr(status, 1); d2 = 1.f; }
           const float inv = rsqrtf(d2);
           v = make_float2(d2 * inv, 0.f);
-          sInv[j1] = inv;
+          sInv[j + 1] = inv;
         }
       }
+      __syncthreads();
     }
-    __syncthreads();
+    if (J0 + 1 < NB) {
+      // rank-16 update of the trailing blocks (I, J), J0 < J <= I (upper halves of diagonal blocks
+      // are updated too and never read)
+      for (int k = 0; k < LA_BLK; ++k) {
+        CT xr[NB], yc[NB];
+#pragma unroll
+        for (int I = J0 + 1; I < NB; ++I) {
+          xr[I] = sPan[k * NPAD + LA_BLK * I + ti];
+          yc[I] = sPan[k * NPAD + LA_BLK * I + tk];
+        }
+#pragma unroll
+        for (int I = J0 + 1; I < NB; ++I)
+#pragma unroll
+          for (int J = J0 + 1; J <= I; ++J) {
+            CT& v = a[I * (I + 1) / 2 + J];
+            v.x = fmaf(-xr[I].x, yc[J].x, v.x); v.x = fmaf(-xr[I].y, yc[J].y, v.x);
+            v.y = fmaf(-xr[I].y, yc[J].x, v.y); v.y = fmaf(xr[I].x, yc[J].y, v.y);
+          }
+      }
+      if (tid == 0) {   // first pivot of the next panel
+        CT& v = a[(J0 + 1) * (J0 + 2) / 2 + J0 + 1];
+        float d2 = v.x;
+        if (!(d2 > 0.f)) { atomicOr(status, 1); d2 = 1.f; }
+        const float inv = rsqrtf(d2);
+        v = make_float2(d2 * inv, 0.f);
+        sInv[LA_BLK * (J0 + 1)] = inv;
+      }
+      __syncthreads();
+    }
   }
 
   float2* F = factors + (size_t)b * L.fsize;
@@ -869,7 +896,7 @@ template <int NPAD>
 cudaError_t launch_factor_c64_n(const LevelGeom& L, const FineOp* fine, const double* sigma, const TimeMats* tm,
                                 float2* factors, int* status, cudaStream_t s) {
   const int nptsmax = L.sub[0] * L.sub[1] * L.sub[2];
-  const size_t smem = sizeof(float2) * (NPAD + (size_t)(NPAD / LA_BLK) * 256) + sizeof(float) * NPAD +
+  const size_t smem = sizeof(float2) * ((size_t)LA_BLK * NPAD + (size_t)(NPAD / LA_BLK) * 256) + sizeof(float) * NPAD +
                       sizeof(float) * (LA_NPAIR * LA_KMAX * LA_KMAX + (size_t)nptsmax * nptsmax * (fine ? 2 : LA_NPAIR));
   auto kern = k_factor_c64<NPAD>;
   static bool attr_set = false;
