@@ -119,6 +119,59 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def hbm_peak():
+    """Measured copy bandwidth (GB/s) from MEASURED_PEAKS.json beside this file, else the fallback."""
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            return float(json.load(fh)["hbm_gbs"]), "of measured (MEASURED_PEAKS.json hbm_gbs)"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "of fallback (6.8 TB/s)"
+
+
+def dominant_roofline(prof, w, precision, ms_total, traffic_ok):
+    """Roofline of the dominant kernel class (the larger total device time of factor and sweep)."""
+    fac_ms = prof["ms_factor"] / max(prof["n_factor"], 1)
+    ncol = 1 << w.dim
+    swp_ms_full = prof["ms_sweep"] / max(prof["n_sweep"], 1) * ncol
+    nsub = 1
+    for a in range(w.dim):
+        nsub *= -(-w.n[a] // w.sub[a])
+    if prof["ms_factor"] >= prof["ms_sweep"]:
+        dom, flops, dms, cls = "k_factor (finest level)", prof["flops_factor"], fac_ms, "factor"
+    else:
+        dom, flops, dms, cls = "k_sweep_fine (one sweep, all colours)", prof["flops_sweep"], swp_ms_full, "sweep"
+    bps = NCU_BYTES_PER_SUBVOLUME.get((cls, precision)) if traffic_ok else None
+    traffic = round(bps * nsub) if bps else None
+    achieved = flops / (dms * 1e-3) / 1e12
+    if precision == 0:
+        peak = FP64_PEAK_TFLOPS
+        peak_note = "FP64 pipe: 152 SMs x 4 flop/clk x 2070 MHz (derived); probe measured 1.19 at 1995 MHz"
+    else:
+        peak = FP32_PEAK_TFLOPS
+        peak_note = "FP32 pipe (complex64 kernel): 152 SMs x 128 lanes x 2 flop x 2070 MHz (derived)"
+    return {"bound": "alu", "kernel": dom, "achieved": round(achieved, 4), "peak": round(peak, 4),
+            "unit": "TFLOP/s", "frac": round(achieved / peak, 4), "traffic": traffic,
+            "traffic_note": "DRAM read+write bytes of this kernel per launch from one ncu capture of this workload",
+            "peak_note": peak_note,
+            "kernel_ms": {"factor_per_launch": round(fac_ms, 4), "sweep_full": round(swp_ms_full, 4),
+                          "factor_share": round(prof["ms_factor"] / max(ms_total, 1e-9), 3),
+                          "sweep_share": round(prof["ms_sweep"] / max(ms_total, 1e-9), 3)}}
+
+
+def stencil_roofline(prof, precision):
+    """Finest-level action-residual stencil (k_mresid) against HBM: algorithmic bytes / event time."""
+    if not prof.get("n_resid"):
+        return None
+    peak, note = hbm_peak()
+    gbs = prof["bytes_resid"] / (prof["ms_resid"] * 1e-3) / 1e9
+    return {"bound": "hbm", "kernel": "k_mresid (finest-level action residual, S1)", "achieved": round(gbs, 1),
+            "peak": peak, "unit": "GB/s", "frac": round(gbs / peak, 4), "peak_note": note,
+            "launches": prof["n_resid"], "us_per_launch": round(1e3 * prof["ms_resid"] / prof["n_resid"], 2),
+            "note": ("FP64 launches are bound by the FP64 pipe, not by HBM" if precision == 0 else
+                     "complex64 V-cycle launches and FP64 action launches together")}
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -195,32 +248,8 @@ def run_ours(args):
     e2e_s = time.perf_counter() - t0
     e2e_value = nunk * e2e_sweeps / e2e_s * (ws if ws > 1 else 1)
 
-    # roofline of the dominant kernel (the larger total device time of the two classes)
-    fac_ms = prof["ms_factor"] / max(prof["n_factor"], 1)
-    ncol = 1 << w.dim
-    swp_ms_full = prof["ms_sweep"] / max(prof["n_sweep"], 1) * ncol
-    nsub = (w.n[0] // w.sub[0]) * (w.n[1] // w.sub[1] if w.dim > 1 else 1)
-    if prof["ms_factor"] >= prof["ms_sweep"]:
-        dom, flops, dms, cls = "k_factor (finest level)", prof["flops_factor"], fac_ms, "factor"
-    else:
-        dom, flops, dms, cls = "k_sweep_fine (one sweep, all colours)", prof["flops_sweep"], swp_ms_full, "sweep"
-    bps = NCU_BYTES_PER_SUBVOLUME.get((cls, args.precision)) if args.workload == "2d" else None
-    traffic = round(bps * nsub) if bps else None
-    achieved = flops / (dms * 1e-3) / 1e12
+    roofline = dominant_roofline(prof, w, args.precision, ms, traffic_ok=args.workload == "2d")
     prec_tag = "f64" if args.precision == 0 else "c64 local solves + f64 refinement"
-    if args.precision == 0:
-        peak = FP64_PEAK_TFLOPS
-        peak_note = "FP64 pipe: 152 SMs x 4 flop/clk x 2070 MHz (derived); probe measured 1.19 at 1995 MHz"
-    else:
-        peak = FP32_PEAK_TFLOPS
-        peak_note = "FP32 pipe (complex64 kernel): 152 SMs x 128 lanes x 2 flop x 2070 MHz (derived)"
-    roofline = {"bound": "alu", "kernel": dom, "achieved": round(achieved, 4), "peak": round(peak, 4),
-                "unit": "TFLOP/s", "frac": round(achieved / peak, 4), "traffic": traffic,
-                "traffic_note": "DRAM read+write bytes of this kernel per launch from one ncu capture of this workload",
-                "peak_note": peak_note,
-                "kernel_ms": {"factor_per_launch": round(fac_ms, 4), "sweep_full": round(swp_ms_full, 4),
-                              "factor_share": round(prof["ms_factor"] / max(ms, 1e-9), 3),
-                              "sweep_share": round(prof["ms_sweep"] / max(ms, 1e-9), 3)}}
 
     out = {"metric": METRIC, "value": value, "unit": "unknowns/s", "n_gpus": ws, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
@@ -234,7 +263,8 @@ def run_ours(args):
            "ms_per_time_step_to_tol": ms_max / args.steps,
            "e2e": {"value": e2e_value, "unit": "unknowns/s", "h2d_bytes_per_step": 16 * w.npoints,
                    "d2h_bytes_per_step": 16 * w.npoints, "steps": e2e_steps},
-           "gpu_launches": int(prof["launches"]), "roofline": roofline, "clocks": clk}
+           "gpu_launches": int(prof["launches"]), "roofline": roofline,
+           "stencil_roofline": stencil_roofline(prof, args.precision), "clocks": clk}
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(w)
     if rank == 0:
@@ -391,11 +421,14 @@ def run_3d_adjoint(args):
     ctx = B.Context(cfg)
     ctx.set_hamiltonian(torch.tensor(wl.potential(w).ravel(), dtype=torch.float64, device="cuda"), w.pulse)
     psi = torch.from_numpy(wl.initial_state(w).ravel()).cuda()
+    ctx.profile_enable(True)
     torch.cuda.synchronize()
     a = time.perf_counter()
     st, stats = ctx.step(psi, args.steps, 0.0, stats=True)
     torch.cuda.synchronize()
     el_f = time.perf_counter() - a
+    prof = ctx.profile_read()
+    ctx.profile_enable(False)
     x = torch.from_numpy(wl.laser_coordinate(w).ravel()).cuda()
     hd = float(np.prod(w.h[:3]))
     dJ = (hd * x * psi).contiguous()
@@ -412,6 +445,8 @@ def run_3d_adjoint(args):
                       "pulse_components": w.pulse.ncomp, "ckpt_every": 20},
            "cycles_per_step": sum(s_[0] for s_ in stats) / args.steps,
            "backward_ms_per_step": 1e3 * el_b / args.steps,
+           "roofline": dominant_roofline(prof, w, args.precision, 1e3 * el_f, traffic_ok=False),
+           "stencil_roofline": stencil_roofline(prof, args.precision),
            "dipole_T": float(hd * (x * psi.abs() ** 2).sum()), "grad_norm": float(np.linalg.norm(grad)),
            "grad_head": [float(g) for g in grad[:4]]}
     print(json.dumps(out))

@@ -168,11 +168,13 @@ la_status la_relax_colour(la_ctx* ctx, const void* psi0, double t0, int colour, 
    with b_n = P_n - (-1)^n P_0.  out is a host array of 4*K*K + 2*K doubles. */
 la_status la_time_matrices(la_ctx* ctx, double t0, double* out);
 
-/* Kernel timing of the two dominant kernel classes, for roofline reporting.  While enabled, the
-   library records CUDA events on its stream around every finest-level factorisation launch and
-   every finest-level colour-sweep launch, and counts all of its kernel launches.  Algorithmic
-   flops: factorisation (4/3) n^3 per subvolume (complex Cholesky of the n = |U| K unknowns);
-   sweep 8 n^2 per subvolume (the two triangular solves; the residual stencil is not counted). */
+/* Kernel timing for roofline reporting.  While enabled, the library records CUDA events on its
+   stream around every finest-level factorisation launch, every finest-level colour-sweep launch and
+   every finest-level action-residual stencil launch (S1: r = f - M c, inside the V-cycle and for
+   the action norm), and counts all of its kernel launches.  Algorithmic flops: factorisation
+   (4/3) n^3 per subvolume (complex Cholesky of the n = |U| K unknowns); sweep 8 n^2 per subvolume
+   (the two triangular solves; the residual stencil is not counted).  Algorithmic bytes of the
+   residual stencil: c in, r out, f in where present (K complex each per point) and V0 in. */
 typedef struct {
   long long launches;     /* kernels launched by the library since enabling */
   int n_factor;           /* finest-level factorisation launches */
@@ -181,6 +183,9 @@ typedef struct {
   int n_sweep;            /* finest-level colour-sweep launches */
   double ms_sweep;
   double flops_sweep;     /* algorithmic flops of one full sweep (all colours) */
+  int n_resid;            /* finest-level residual stencil launches */
+  double ms_resid;        /* their summed device time */
+  double bytes_resid;     /* their summed algorithmic bytes */
 } la_profile;
 /* enable != 0 resets the counters and starts recording; 0 stops.  Errors: LA_EINVAL. */
 la_status la_profile_enable(la_ctx* ctx, int enable);

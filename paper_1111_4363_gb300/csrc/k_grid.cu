@@ -81,28 +81,81 @@ __device__ __forceinline__ void pcoords(const FineOp& g, int p, int& x, int& y, 
   z = r / g.n[1];
 }
 
-// (H v)_p for a K-vector field v (point-major), Dirichlet zero outside the grid.
-template <typename CT, typename RR>
-__device__ __forceinline__ void apply_H(const FineOp& g, const CT* v, int K, int x, int y, int z, CT* out) {
-  const int p = (z * g.n[1] + y) * g.n[0] + x;
-  const RR dg = (RR)(g.dsum + g.V0[p]);
-  for (int m = 0; m < K; ++m) {
-    CT a = v[(long long)p * K + m];
-    out[m] = cmk<CT>(dg * a.x, dg * a.y);
-  }
-  const int nb[6][3] = {{1, 0, 0}, {-1, 0, 0}, {0, 1, 0}, {0, -1, 0}, {0, 0, 1}, {0, 0, -1}};
-  for (int t = 0; t < 2 * g.dim; ++t) {
-    int qx = x + nb[t][0], qy = y + nb[t][1], qz = z + nb[t][2];
-    if (qx < 0 || qy < 0 || qz < 0 || qx >= g.n[0] || qy >= g.n[1] || qz >= g.n[2]) continue;
-    const RR w = (RR)(-0.5 * g.ih2[t >> 1]);
-    const long long q = (long long)((qz * g.n[1] + qy) * g.n[0] + qx) * K;
-    for (int m = 0; m < K; ++m) {
-      CT a = v[q + m];
-      out[m].x += w * a.x;
-      out[m].y += w * a.y;
+// K complex values of point p from a point-major field into registers (16-byte loads where the
+// record allows: complex64 with even K pairs two values per load).
+template <typename CT, int K>
+__device__ __forceinline__ void load_k(const CT* __restrict__ v, long long p, CT (&out)[K]) {
+  const CT* src = v + p * K;
+  if constexpr (sizeof(CT) == 8 && K % 2 == 0) {
+    const float4* s4 = reinterpret_cast<const float4*>(src);
+#pragma unroll
+    for (int m = 0; m < K / 2; ++m) {
+      const float4 q = s4[m];
+      out[2 * m] = cmk<CT>(q.x, q.y);
+      out[2 * m + 1] = cmk<CT>(q.z, q.w);
     }
+  } else {
+#pragma unroll
+    for (int m = 0; m < K; ++m) out[m] = src[m];
   }
 }
+template <typename CT, int K>
+__device__ __forceinline__ void store_k(CT* __restrict__ v, long long p, const CT (&in)[K]) {
+  CT* dst = v + p * K;
+  if constexpr (sizeof(CT) == 8 && K % 2 == 0) {
+    float4* d4 = reinterpret_cast<float4*>(dst);
+#pragma unroll
+    for (int m = 0; m < K / 2; ++m) d4[m] = make_float4(in[2 * m].x, in[2 * m].y, in[2 * m + 1].x, in[2 * m + 1].y);
+  } else {
+#pragma unroll
+    for (int m = 0; m < K; ++m) dst[m] = in[m];
+  }
+}
+template <typename CT, typename RR, int K>
+__device__ __forceinline__ void axpy_k(RR w, const CT (&a)[K], CT (&acc)[K]) {
+#pragma unroll
+  for (int m = 0; m < K; ++m) { acc[m].x += w * a[m].x; acc[m].y += w * a[m].y; }
+}
+
+// (H v)_p for a K-vector field v (point-major), Dirichlet zero outside the grid; also returns v_p.
+// Neighbours in the order +x, -x, +y, -y, +z, -z.
+template <typename CT, typename RR, int K>
+__device__ __forceinline__ void apply_H(const FineOp& g, const CT* __restrict__ v, int p, int x, int y, int z,
+                                        CT (&vp)[K], CT (&out)[K]) {
+  const RR dg = (RR)(g.dsum + g.V0[p]);
+  load_k<CT, K>(v, p, vp);
+#pragma unroll
+  for (int m = 0; m < K; ++m) out[m] = cmk<CT>(dg * vp[m].x, dg * vp[m].y);
+  CT a[K];
+  const RR wx = (RR)(-0.5 * g.ih2[0]);
+  if (x + 1 < g.n[0]) { load_k<CT, K>(v, p + 1, a); axpy_k<CT, RR, K>(wx, a, out); }
+  if (x > 0) { load_k<CT, K>(v, p - 1, a); axpy_k<CT, RR, K>(wx, a, out); }
+  if (g.dim > 1) {
+    const RR wy = (RR)(-0.5 * g.ih2[1]);
+    const int sy = g.n[0];
+    if (y + 1 < g.n[1]) { load_k<CT, K>(v, p + sy, a); axpy_k<CT, RR, K>(wy, a, out); }
+    if (y > 0) { load_k<CT, K>(v, p - sy, a); axpy_k<CT, RR, K>(wy, a, out); }
+  }
+  if (g.dim > 2) {
+    const RR wz = (RR)(-0.5 * g.ih2[2]);
+    const int sz = g.n[0] * g.n[1];
+    if (z + 1 < g.n[2]) { load_k<CT, K>(v, p + sz, a); axpy_k<CT, RR, K>(wz, a, out); }
+    if (z > 0) { load_k<CT, K>(v, p - sz, a); axpy_k<CT, RR, K>(wz, a, out); }
+  }
+}
+
+#define LA_K_DISPATCH(K, CALL)        \
+  switch (K) {                        \
+    case 1: CALL(1); break;           \
+    case 2: CALL(2); break;           \
+    case 3: CALL(3); break;           \
+    case 4: CALL(4); break;           \
+    case 5: CALL(5); break;           \
+    case 6: CALL(6); break;           \
+    case 7: CALL(7); break;           \
+    case 8: CALL(8); break;           \
+    default: break;                   \
+  }
 
 // f~[p, m] = Ub0[m] (H psi0)_p + x_p Eb0[m] psi0_p (the psi0 P_0 part moved to the right-hand side).
 __global__ void k_rhs(FineOp g, const TimeMats* __restrict__ tm, const double2* __restrict__ psi0,
@@ -112,10 +165,10 @@ __global__ void k_rhs(FineOp g, const TimeMats* __restrict__ tm, const double2* 
   if (p >= np) return;
   int x, y, z;
   pcoords(g, p, x, y, z);
-  double2 hp[1];
-  apply_H<double2, double>(g, psi0, 1, x, y, z, hp);
+  double2 hp[1], pv[1];
+  apply_H<double2, double, 1>(g, psi0, p, x, y, z, pv, hp);
   const double xl = fine_x(g, x, y, z);
-  const double2 ps = psi0[p];
+  const double2 ps = pv[0];
   const int K = tm->K;
   for (int m = 0; m < K; ++m) {
     double a = tm->Ub0[m], b = xl * tm->Eb0[m];
@@ -132,16 +185,16 @@ int norm_blocks(int np) { return (np + 255) / 256; }
 
 // r = f~ - M~ c with (M~ c)_p = i Qb c_p - Ub (H c)_p - x_p Eb c_p; z = Wt r; partials of r^dagger Wt r.
 // One thread per point, 256 threads per block, no grid stride (fixed block-to-point map so the
-// norm reduction is deterministic).  f may be null (f = 0).
-template <typename CT>
+// norm reduction is deterministic).  f may be null (f = 0).  K is a template parameter so the
+// per-point K-vectors live in registers.
+template <typename CT, int K>
 __global__ void __launch_bounds__(256) k_mresid(FineOp g, const TimeMats* __restrict__ tm,
                                                 const CT* __restrict__ f, const CT* __restrict__ c,
                                                 CT* __restrict__ rout, CT* __restrict__ zout,
                                                 double* __restrict__ partials) {
   typedef typename CR<CT>::R RR;
-  __shared__ RR Qb[LA_KMAX * LA_KMAX], Ub[LA_KMAX * LA_KMAX], Eb[LA_KMAX * LA_KMAX], Wt[LA_KMAX * LA_KMAX];
+  __shared__ RR Qb[K * K], Ub[K * K], Eb[K * K], Wt[K * K];
   __shared__ double red[256];
-  const int K = tm->K;
   for (int i = threadIdx.x; i < K * K; i += blockDim.x) {
     Qb[i] = (RR)tm->Qb[i]; Ub[i] = (RR)tm->Ub[i]; Eb[i] = (RR)tm->Eb[i]; Wt[i] = (RR)tm->Wt[i];
   }
@@ -152,30 +205,39 @@ __global__ void __launch_bounds__(256) k_mresid(FineOp g, const TimeMats* __rest
   if (p < np) {
     int x, y, z;
     pcoords(g, p, x, y, z);
-    CT cp[LA_KMAX], hc[LA_KMAX], r[LA_KMAX];
-    for (int m = 0; m < K; ++m) cp[m] = c[(long long)p * K + m];
-    apply_H<CT, RR>(g, c, K, x, y, z, hc);
+    CT cp[K], hc[K], r[K];
+    apply_H<CT, RR, K>(g, c, p, x, y, z, cp, hc);
     const RR xl = (RR)fine_x(g, x, y, z);
+    if (f) load_k<CT, K>(f, p, r);
+    else {
+#pragma unroll
+      for (int m = 0; m < K; ++m) r[m] = cmk<CT>(0, 0);
+    }
+#pragma unroll
     for (int m = 0; m < K; ++m) {
       RR qr = 0, qi = 0, ur = 0, ui = 0, er = 0, ei = 0;
+#pragma unroll
       for (int n = 0; n < K; ++n) {
-        RR q = Qb[m * K + n], u = Ub[m * K + n], e = Eb[m * K + n];
+        const RR q = Qb[m * K + n], u = Ub[m * K + n], e = Eb[m * K + n];
         qr += q * cp[n].x; qi += q * cp[n].y;
         ur += u * hc[n].x; ui += u * hc[n].y;
         er += e * cp[n].x; ei += e * cp[n].y;
       }
       // i (qr + i qi) = -qi + i qr
-      CT fv = f ? f[(long long)p * K + m] : cmk<CT>(0, 0);
-      r[m].x = fv.x - (-qi - ur - xl * er);
-      r[m].y = fv.y - (qr - ui - xl * ei);
+      r[m].x = r[m].x - (-qi - ur - xl * er);
+      r[m].y = r[m].y - (qr - ui - xl * ei);
     }
+    CT zv[K];
+#pragma unroll
     for (int m = 0; m < K; ++m) {
       RR zr = 0, zi = 0;
+#pragma unroll
       for (int n = 0; n < K; ++n) { zr += Wt[m * K + n] * r[n].x; zi += Wt[m * K + n] * r[n].y; }
-      nsum += (double)r[m].x * (double)zr + (double)r[m].y * (double)zi;
-      if (zout) zout[(long long)p * K + m] = cmk<CT>(zr, zi);
-      if (rout) rout[(long long)p * K + m] = r[m];
+      zv[m] = cmk<CT>(zr, zi);
+      if (partials) nsum += (double)r[m].x * (double)zr + (double)r[m].y * (double)zi;
     }
+    if (zout) store_k<CT, K>(zout, p, zv);
+    if (rout) store_k<CT, K>(rout, p, r);
   }
   if (partials) {
     red[threadIdx.x] = nsum;
@@ -189,23 +251,25 @@ __global__ void __launch_bounds__(256) k_mresid(FineOp g, const TimeMats* __rest
 }
 
 template <typename R>
-void launch_mresid(const FineOp& g, const TimeMats* tm, const typename C2<R>::T* f, const typename C2<R>::T* c,
-                   typename C2<R>::T* r, typename C2<R>::T* z, double* partials, int nb, cudaStream_t s) {
-  k_mresid<typename C2<R>::T><<<nb, 256, 0, s>>>(g, tm, f, c, r, z, partials);
+void launch_mresid(const FineOp& g, const TimeMats* tm, int K, const typename C2<R>::T* f,
+                   const typename C2<R>::T* c, typename C2<R>::T* r, typename C2<R>::T* z, double* partials, int nb,
+                   cudaStream_t s) {
+#define LA_CALL(KK) k_mresid<typename C2<R>::T, KK><<<nb, 256, 0, s>>>(g, tm, f, c, r, z, partials)
+  LA_K_DISPATCH(K, LA_CALL)
+#undef LA_CALL
 }
-template void launch_mresid<double>(const FineOp&, const TimeMats*, const double2*, const double2*, double2*,
+template void launch_mresid<double>(const FineOp&, const TimeMats*, int, const double2*, const double2*, double2*,
                                     double2*, double*, int, cudaStream_t);
-template void launch_mresid<float>(const FineOp&, const TimeMats*, const float2*, const float2*, float2*, float2*,
-                                   double*, int, cudaStream_t);
+template void launch_mresid<float>(const FineOp&, const TimeMats*, int, const float2*, const float2*, float2*,
+                                   float2*, double*, int, cudaStream_t);
 
 // s = M~^dagger z: s_p = -i Qb^T z_p - Ub (H z)_p - x_p Eb z_p.
-template <typename CT>
+template <typename CT, int K>
 __global__ void __launch_bounds__(256) k_mnormal(FineOp g, const TimeMats* __restrict__ tm,
                                                  const CT* __restrict__ zin, CT* __restrict__ out,
                                                  const CT* __restrict__ yadd) {
   typedef typename CR<CT>::R RR;
-  __shared__ RR Qb[LA_KMAX * LA_KMAX], Ub[LA_KMAX * LA_KMAX], Eb[LA_KMAX * LA_KMAX];
-  const int K = tm->K;
+  __shared__ RR Qb[K * K], Ub[K * K], Eb[K * K];
   for (int i = threadIdx.x; i < K * K; i += blockDim.x) {
     Qb[i] = (RR)tm->Qb[i]; Ub[i] = (RR)tm->Ub[i]; Eb[i] = (RR)tm->Eb[i];
   }
@@ -215,38 +279,39 @@ __global__ void __launch_bounds__(256) k_mnormal(FineOp g, const TimeMats* __res
   if (p >= np) return;
   int x, y, z;
   pcoords(g, p, x, y, z);
-  CT zp[LA_KMAX], hz[LA_KMAX];
-  for (int m = 0; m < K; ++m) zp[m] = zin[(long long)p * K + m];
-  apply_H<CT, RR>(g, zin, K, x, y, z, hz);
+  CT zp[K], hz[K], v[K];
+  apply_H<CT, RR, K>(g, zin, p, x, y, z, zp, hz);
   const RR xl = (RR)fine_x(g, x, y, z);
+  if (yadd) load_k<CT, K>(yadd, p, v);
+#pragma unroll
   for (int m = 0; m < K; ++m) {
     RR qr = 0, qi = 0, ur = 0, ui = 0, er = 0, ei = 0;
+#pragma unroll
     for (int n = 0; n < K; ++n) {
-      RR q = Qb[n * K + m], u = Ub[m * K + n], e = Eb[m * K + n];
+      const RR q = Qb[n * K + m], u = Ub[m * K + n], e = Eb[m * K + n];
       qr += q * zp[n].x; qi += q * zp[n].y;
       ur += u * hz[n].x; ui += u * hz[n].y;
       er += e * zp[n].x; ei += e * zp[n].y;
     }
     // -i (qr + i qi) = qi - i qr
-    CT v = cmk<CT>(qi - ur - xl * er, -qr - ui - xl * ei);
-    if (yadd) {
-      const CT ya = yadd[(long long)p * K + m];
-      v.x += ya.x;
-      v.y += ya.y;
-    }
-    out[(long long)p * K + m] = v;
+    CT w = cmk<CT>(qi - ur - xl * er, -qr - ui - xl * ei);
+    if (yadd) { w.x += v[m].x; w.y += v[m].y; }
+    v[m] = w;
   }
+  store_k<CT, K>(out, p, v);
 }
 
 template <typename R>
-void launch_mnormal(const FineOp& g, const TimeMats* tm, const typename C2<R>::T* z, typename C2<R>::T* out,
+void launch_mnormal(const FineOp& g, const TimeMats* tm, int K, const typename C2<R>::T* z, typename C2<R>::T* out,
                     cudaStream_t s, const typename C2<R>::T* yadd) {
-  int np = g.n[0] * g.n[1] * g.n[2];
-  k_mnormal<typename C2<R>::T><<<(np + 255) / 256, 256, 0, s>>>(g, tm, z, out, yadd);
+  const int np = g.n[0] * g.n[1] * g.n[2];
+#define LA_CALL(KK) k_mnormal<typename C2<R>::T, KK><<<(np + 255) / 256, 256, 0, s>>>(g, tm, z, out, yadd)
+  LA_K_DISPATCH(K, LA_CALL)
+#undef LA_CALL
 }
-template void launch_mnormal<double>(const FineOp&, const TimeMats*, const double2*, double2*, cudaStream_t,
+template void launch_mnormal<double>(const FineOp&, const TimeMats*, int, const double2*, double2*, cudaStream_t,
                                      const double2*);
-template void launch_mnormal<float>(const FineOp&, const TimeMats*, const float2*, float2*, cudaStream_t,
+template void launch_mnormal<float>(const FineOp&, const TimeMats*, int, const float2*, float2*, cudaStream_t,
                                     const float2*);
 
 // ------------------------------------------------------------------ Galerkin-level residual
@@ -258,139 +323,97 @@ __device__ __forceinline__ void lcoords(const LevelGeom& L, int p, int& x, int& 
   z = r / L.n[1];
 }
 
-template <typename CT>
-__global__ void __launch_bounds__(128) k_gresid(LevelGeom L, const TimeMats* __restrict__ tm,
-                                                const double* __restrict__ sigma, const CT* __restrict__ gvec,
-                                                const CT* __restrict__ e, CT* __restrict__ out) {
-  typedef typename CR<CT>::R RR;
-  __shared__ RR P[LA_NPAIR][LA_KMAX * LA_KMAX];
-  const int K = tm->K;
-  for (int i = threadIdx.x; i < LA_NPAIR * K * K; i += blockDim.x) P[i / (K * K)][i % (K * K)] = (RR)tm->P[i / (K * K)][i % (K * K)];
-  __syncthreads();
-  const int p = blockIdx.x * blockDim.x + threadIdx.x;
-  if (p >= L.np) return;
-  int x, y, z;
-  lcoords(L, p, x, y, z);
-  const int nbox = box5_count(L.dim);
-  const int rz = L.dim > 2 ? 2 : 0, ry = L.dim > 1 ? 2 : 0;
-  CT acc[LA_KMAX];
-  for (int m = 0; m < K; ++m) acc[m] = cmk<CT>(0, 0);
-  for (int kk = 0; kk < LA_NPAIR; ++kk) {
-    CT u[LA_KMAX];
-    for (int m = 0; m < K; ++m) u[m] = cmk<CT>(0, 0);
-    for (int oz = -rz; oz <= rz; ++oz)
-      for (int oy = -ry; oy <= ry; ++oy)
-        for (int ox = -2; ox <= 2; ++ox) {
-          int qx = x + ox, qy = y + oy, qz = z + oz;
-          if (qx < 0 || qy < 0 || qz < 0 || qx >= L.n[0] || qy >= L.n[1] || qz >= L.n[2]) continue;
-          RR s = (RR)sigma[sigma_offset(p, kk, box5_index(L.dim, ox, oy, oz), nbox)];
-          if (s == (RR)0) continue;
-          const CT* eq = e + (long long)((qz * L.n[1] + qy) * L.n[0] + qx) * K;
-          for (int m = 0; m < K; ++m) { u[m].x += s * eq[m].x; u[m].y += s * eq[m].y; }
-        }
-    const int ph = theta_phase(kk);
-    for (int m = 0; m < K; ++m) {
-      RR vr = 0, vi = 0;
-      for (int n = 0; n < K; ++n) { RR pv = P[kk][m * K + n]; vr += pv * u[n].x; vi += pv * u[n].y; }
-      if (ph == 0) { acc[m].x += vr; acc[m].y += vi; }
-      else if (ph == 1) { acc[m].x -= vi; acc[m].y += vr; }   // i (vr + i vi)
-      else { acc[m].x += vi; acc[m].y -= vr; }                // -i (vr + i vi)
-    }
-  }
-  for (int m = 0; m < K; ++m) {
-    CT gv = gvec[(long long)p * K + m];
-    out[(long long)p * K + m] = cmk<CT>(gv.x - acc[m].x, gv.y - acc[m].y);
-  }
-}
-
-template <typename R>
-void launch_gresid(const LevelGeom& L, const TimeMats* tm, const double* sigma, const typename C2<R>::T* gvec,
-                   const typename C2<R>::T* e, typename C2<R>::T* out, cudaStream_t s) {
-  k_gresid<typename C2<R>::T><<<(L.np + 127) / 128, 128, 0, s>>>(L, tm, sigma, gvec, e, out);
-}
-template void launch_gresid<double>(const LevelGeom&, const TimeMats*, const double*, const double2*, const double2*,
-                                    double2*, cudaStream_t);
-template void launch_gresid<float>(const LevelGeom&, const TimeMats*, const double*, const float2*, const float2*,
-                                   float2*, cudaStream_t);
-
 // ------------------------------------------------------------------ transfers (Sec. III)
 // Cell-centred 2:1 interpolation per used axis: fine 2J <- 3/4 c_J + 1/4 c_{J-1},
 // fine 2J+1 <- 3/4 c_J + 1/4 c_{J+1}; restriction is the transpose.
-__device__ __forceinline__ int parents_1d(int a, int nc, bool used, int J[2], float w[2]) {
-  if (!used) { J[0] = a; w[0] = 1.f; return 1; }
-  int j0 = a >> 1;
-  int j1 = (a & 1) ? j0 + 1 : j0 - 1;
-  J[0] = j0; w[0] = 0.75f;
-  if (j1 >= 0 && j1 < nc) { J[1] = j1; w[1] = 0.25f; return 2; }
-  return 1;
+// Cell-centred 2:1 linear transfer weights along one axis.  Children of coarse J: fine 2J-1, 2J,
+// 2J+1, 2J+2 with weights 1/4, 3/4, 3/4, 1/4 (those inside the grid).  Parents of fine a: a/2
+// with 3/4 and the neighbour on a's side with 1/4 (if inside).  Unused axes map 1:1.
+__device__ __forceinline__ bool child_1d(int J, int t, int nf, bool used, int& a, float& w) {
+  if (!used) { a = J; w = 1.f; return t == 0; }
+  a = 2 * J - 1 + t;
+  w = (t == 1 || t == 2) ? 0.75f : 0.25f;
+  return a >= 0 && a < nf;
 }
-__device__ __forceinline__ int children_1d(int J, int nf, bool used, int a[4], float w[4]) {
-  if (!used) { a[0] = J; w[0] = 1.f; return 1; }
-  int cnt = 0;
-  const int cand[4] = {2 * J - 1, 2 * J, 2 * J + 1, 2 * J + 2};
-  const float wc[4] = {0.25f, 0.75f, 0.75f, 0.25f};
-  for (int t = 0; t < 4; ++t)
-    if (cand[t] >= 0 && cand[t] < nf) { a[cnt] = cand[t]; w[cnt] = wc[t]; ++cnt; }
-  return cnt;
+__device__ __forceinline__ bool parent_1d(int a, int t, int nc, bool used, int& J, float& w) {
+  if (!used) { J = a; w = 1.f; return t == 0; }
+  const int j0 = a >> 1;
+  if (t == 0) { J = j0; w = 0.75f; return true; }
+  J = (a & 1) ? j0 + 1 : j0 - 1;
+  w = 0.25f;
+  return J >= 0 && J < nc;
 }
 
-template <typename CT>
-__global__ void k_restrict(LevelGeom F, LevelGeom C, int K, const CT* __restrict__ sf, CT* __restrict__ gc) {
+template <typename CT, int K>
+__global__ void k_restrict(LevelGeom F, LevelGeom C, const CT* __restrict__ sf, CT* __restrict__ gc) {
   typedef typename CR<CT>::R RR;
   const int J = blockIdx.x * blockDim.x + threadIdx.x;
   if (J >= C.np) return;
   int jx, jy, jz;
   lcoords(C, J, jx, jy, jz);
-  int ax[4], ay[4], az[4];
-  float wx[4], wy[4], wz[4];
-  int nx = children_1d(jx, F.n[0], F.dim > 0, ax, wx);
-  int ny = children_1d(jy, F.n[1], F.dim > 1, ay, wy);
-  int nz = children_1d(jz, F.n[2], F.dim > 2, az, wz);
-  CT acc[LA_KMAX];
+  CT acc[K], a[K];
+#pragma unroll
   for (int m = 0; m < K; ++m) acc[m] = cmk<CT>(0, 0);
-  for (int iz = 0; iz < nz; ++iz)
-    for (int iy = 0; iy < ny; ++iy)
-      for (int ix = 0; ix < nx; ++ix) {
-        RR w = (RR)(wx[ix] * wy[iy] * wz[iz]);
-        const CT* s = sf + (long long)((az[iz] * F.n[1] + ay[iy]) * F.n[0] + ax[ix]) * K;
-        for (int m = 0; m < K; ++m) { acc[m].x += w * s[m].x; acc[m].y += w * s[m].y; }
+  for (int tz = 0; tz < 4; ++tz) {
+    int az; float wz;
+    if (!child_1d(jz, tz, F.n[2], F.dim > 2, az, wz)) continue;
+    for (int ty = 0; ty < 4; ++ty) {
+      int ay; float wy;
+      if (!child_1d(jy, ty, F.n[1], F.dim > 1, ay, wy)) continue;
+#pragma unroll
+      for (int tx = 0; tx < 4; ++tx) {
+        int ax; float wx;
+        if (!child_1d(jx, tx, F.n[0], F.dim > 0, ax, wx)) continue;
+        const RR w = (RR)(wx * wy * wz);
+        load_k<CT, K>(sf, (long long)(az * F.n[1] + ay) * F.n[0] + ax, a);
+        axpy_k<CT, RR, K>(w, a, acc);
       }
-  for (int m = 0; m < K; ++m) gc[(long long)J * K + m] = acc[m];
+    }
+  }
+  store_k<CT, K>(gc, J, acc);
 }
 
-template <typename CT>
-__global__ void k_prolong_add(LevelGeom F, LevelGeom C, int K, const CT* __restrict__ ec, CT* __restrict__ ef) {
+template <typename CT, int K>
+__global__ void k_prolong_add(LevelGeom F, LevelGeom C, const CT* __restrict__ ec, CT* __restrict__ ef) {
   typedef typename CR<CT>::R RR;
-  const int a = blockIdx.x * blockDim.x + threadIdx.x;
-  if (a >= F.np) return;
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= F.np) return;
   int x, y, z;
-  lcoords(F, a, x, y, z);
-  int Jx[2], Jy[2], Jz[2];
-  float wx[2], wy[2], wz[2];
-  int nx = parents_1d(x, C.n[0], F.dim > 0, Jx, wx);
-  int ny = parents_1d(y, C.n[1], F.dim > 1, Jy, wy);
-  int nz = parents_1d(z, C.n[2], F.dim > 2, Jz, wz);
-  CT acc[LA_KMAX];
-  for (int m = 0; m < K; ++m) acc[m] = ef[(long long)a * K + m];
-  for (int iz = 0; iz < nz; ++iz)
-    for (int iy = 0; iy < ny; ++iy)
-      for (int ix = 0; ix < nx; ++ix) {
-        RR w = (RR)(wx[ix] * wy[iy] * wz[iz]);
-        const CT* s = ec + (long long)((Jz[iz] * C.n[1] + Jy[iy]) * C.n[0] + Jx[ix]) * K;
-        for (int m = 0; m < K; ++m) { acc[m].x += w * s[m].x; acc[m].y += w * s[m].y; }
+  lcoords(F, p, x, y, z);
+  CT acc[K], a[K];
+  load_k<CT, K>(ef, p, acc);
+  for (int tz = 0; tz < 2; ++tz) {
+    int Jz; float wz;
+    if (!parent_1d(z, tz, C.n[2], F.dim > 2, Jz, wz)) continue;
+    for (int ty = 0; ty < 2; ++ty) {
+      int Jy; float wy;
+      if (!parent_1d(y, ty, C.n[1], F.dim > 1, Jy, wy)) continue;
+#pragma unroll
+      for (int tx = 0; tx < 2; ++tx) {
+        int Jx; float wx;
+        if (!parent_1d(x, tx, C.n[0], F.dim > 0, Jx, wx)) continue;
+        const RR w = (RR)(wx * wy * wz);
+        load_k<CT, K>(ec, (long long)(Jz * C.n[1] + Jy) * C.n[0] + Jx, a);
+        axpy_k<CT, RR, K>(w, a, acc);
       }
-  for (int m = 0; m < K; ++m) ef[(long long)a * K + m] = acc[m];
+    }
+  }
+  store_k<CT, K>(ef, p, acc);
 }
 
 template <typename R>
 void launch_restrict(const LevelGeom& F, const LevelGeom& C, int K, const typename C2<R>::T* sf,
                      typename C2<R>::T* gc, cudaStream_t s) {
-  k_restrict<typename C2<R>::T><<<(C.np + 127) / 128, 128, 0, s>>>(F, C, K, sf, gc);
+#define LA_CALL(KK) k_restrict<typename C2<R>::T, KK><<<(C.np + 127) / 128, 128, 0, s>>>(F, C, sf, gc)
+  LA_K_DISPATCH(K, LA_CALL)
+#undef LA_CALL
 }
 template <typename R>
 void launch_prolong_add(const LevelGeom& F, const LevelGeom& C, int K, const typename C2<R>::T* ec,
                         typename C2<R>::T* ef, cudaStream_t s) {
-  k_prolong_add<typename C2<R>::T><<<(F.np + 127) / 128, 128, 0, s>>>(F, C, K, ec, ef);
+#define LA_CALL(KK) k_prolong_add<typename C2<R>::T, KK><<<(F.np + 127) / 128, 128, 0, s>>>(F, C, ec, ef)
+  LA_K_DISPATCH(K, LA_CALL)
+#undef LA_CALL
 }
 template void launch_restrict<double>(const LevelGeom&, const LevelGeom&, int, const double2*, double2*, cudaStream_t);
 template void launch_restrict<float>(const LevelGeom&, const LevelGeom&, int, const float2*, float2*, cudaStream_t);

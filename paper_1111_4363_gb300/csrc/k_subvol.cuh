@@ -248,6 +248,7 @@ k_factor_c64(LevelGeom L, FineOp g, int is_fine, int nptsmax, const double* __re
   float* sP = reinterpret_cast<float*>(sDiag + NB * 256);       // [9][K*K]
   float* sPair = sP + LA_NPAIR * LA_KMAX * LA_KMAX;             // [npts*npts][nv]
   const int nv = is_fine ? 2 : LA_NPAIR;
+  float* sX = sPair + (size_t)nptsmax * nptsmax * nv;          // [npts] laser coordinate (finest level)
 
   const int tid = threadIdx.x, ti = tid >> 4, tk = tid & 15;
   const int b = blockIdx.x;
@@ -257,6 +258,12 @@ k_factor_c64(LevelGeom L, FineOp g, int is_fine, int nptsmax, const double* __re
   const int n = npts * K;
   for (int i = tid; i < LA_NPAIR * KK; i += kFactorThreads) sP[i] = (float)tm->P[i / KK][i % KK];
   for (int i = tid; i < NB * 256; i += kFactorThreads) sDiag[i] = make_float2(0.f, 0.f);
+  if (is_fine)
+    for (int i = tid; i < npts; i += kFactorThreads) {
+      int ix, iy, iz;
+      local_coords(i, e, ix, iy, iz);
+      sX[i] = (float)fine_x(g, o[0] + ix, o[1] + iy, o[2] + iz);
+    }
   const int nbox = box5_count(L.dim);
   for (int t = tid; t < npts * npts; t += kFactorThreads) {
     const int i = t / npts, j = t % npts;
@@ -297,12 +304,7 @@ k_factor_c64(LevelGeom L, FineOp g, int is_fine, int nptsmax, const double* __re
         float s9[LA_NPAIR];
         const float* pr = sPair + (size_t)(i * npts + j) * nv;
         if (is_fine) {
-          int ix, iy, iz, jx, jy, jz;
-          local_coords(i, e, ix, iy, iz);
-          local_coords(j, e, jx, jy, jz);
-          const int cxp = g.lax == 0 ? ix : (g.lax == 1 ? iy : iz), cxq = g.lax == 0 ? jx : (g.lax == 1 ? jy : jz);
-          const float xp = (float)g.x0[g.lax] + (float)(o[g.lax] + cxp) * (float)g.h[g.lax];
-          const float xq = (float)g.x0[g.lax] + (float)(o[g.lax] + cxq) * (float)g.h[g.lax];
+          const float xp = sX[i], xq = sX[j];
           const float same = (i == j) ? 1.f : 0.f, Hpq = pr[0];
           s9[0] = same; s9[1] = Hpq; s9[2] = same * xp; s9[3] = Hpq; s9[4] = pr[1];
           s9[5] = Hpq * xq; s9[6] = same * xp; s9[7] = xp * Hpq; s9[8] = same * xp * xp;
@@ -897,7 +899,8 @@ cudaError_t launch_factor_c64_n(const LevelGeom& L, const FineOp* fine, const do
                                 float2* factors, int* status, cudaStream_t s) {
   const int nptsmax = L.sub[0] * L.sub[1] * L.sub[2];
   const size_t smem = sizeof(float2) * ((size_t)LA_BLK * NPAD + (size_t)(NPAD / LA_BLK) * 256) + sizeof(float) * NPAD +
-                      sizeof(float) * (LA_NPAIR * LA_KMAX * LA_KMAX + (size_t)nptsmax * nptsmax * (fine ? 2 : LA_NPAIR));
+                      sizeof(float) * (LA_NPAIR * LA_KMAX * LA_KMAX + (size_t)nptsmax * nptsmax * (fine ? 2 : LA_NPAIR) +
+                                       nptsmax);
   auto kern = k_factor_c64<NPAD>;
   static bool attr_set = false;
   if (!attr_set) {

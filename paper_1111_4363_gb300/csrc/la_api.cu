@@ -68,15 +68,22 @@ struct la_ctx {
   bool prof = false;
   long long launches = 0;
   std::vector<cudaEvent_t> ev_pool;
-  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_factor, ev_sweep;
+  // a timed launch: kind 0 = finest colour sweep, 1 = action residual stencil (k_mresid)
+  struct ProfPair {
+    cudaEvent_t e0, e1;
+    int kind;
+    double bytes;
+  };
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_factor;
+  std::vector<ProfPair> ev_kern;
   size_t ev_next = 0;
-  double ms_factor = 0.0, ms_sweep = 0.0;
-  int n_factor = 0, n_sweep = 0;
+  double ms_factor = 0.0, ms_sweep = 0.0, ms_resid = 0.0, bytes_resid = 0.0;
+  int n_factor = 0, n_sweep = 0, n_resid = 0;
   double flops_factor = 0.0, flops_sweep = 0.0;
   // one captured cycle (V-cycle + action norm + read-back), replayed on an internal stream
   struct CycleGraph {
     cudaGraphExec_t exec = nullptr;
-    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> pairs;  // profiling event nodes
+    std::vector<ProfPair> pairs;  // profiling event nodes
     long long launches = 0;
   };
   CycleGraph cg[2];               // [0] plain, [1] with profiling events
@@ -84,7 +91,7 @@ struct la_ctx {
   bool use_graph = true;
   bool capturing = false;
   long long cycles_run = 0;
-  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> cap_pairs;
+  std::vector<ProfPair> cap_pairs;
   cudaStream_t cap = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   double* h_N = nullptr;          // pinned
@@ -98,21 +105,47 @@ static cudaEvent_t prof_event(la_ctx* c) {
   }
   return c->ev_pool[c->ev_next++];
 }
+// Adds one completed timed launch to the totals of its kind.
+static void prof_add(la_ctx* c, const la_ctx::ProfPair& p) {
+  float ms = 0.f;
+  if (cudaEventElapsedTime(&ms, p.e0, p.e1) != cudaSuccess) return;
+  if (p.kind == 0) { c->ms_sweep += ms; ++c->n_sweep; }
+  else { c->ms_resid += ms; ++c->n_resid; c->bytes_resid += p.bytes; }
+}
 // Drain recorded event pairs into the totals (synchronises).
 static void prof_drain(la_ctx* c) {
-  if (c->ev_factor.empty() && c->ev_sweep.empty()) return;
+  if (c->ev_factor.empty() && c->ev_kern.empty()) return;
   cudaStreamSynchronize(c->stream);
   for (auto& p : c->ev_factor) {
     float ms = 0.f;
     if (cudaEventElapsedTime(&ms, p.first, p.second) == cudaSuccess) { c->ms_factor += ms; ++c->n_factor; }
   }
-  for (auto& p : c->ev_sweep) {
-    float ms = 0.f;
-    if (cudaEventElapsedTime(&ms, p.first, p.second) == cudaSuccess) { c->ms_sweep += ms; ++c->n_sweep; }
-  }
+  for (auto& p : c->ev_kern) prof_add(c, p);
   c->ev_factor.clear();
-  c->ev_sweep.clear();
+  c->ev_kern.clear();
   c->ev_next = 0;
+}
+// Start event of a timed launch on the context's stream (an external event node while a cycle is
+// being captured; the graph keeps those events).  False when profiling is off or events fail.
+static bool prof_begin(la_ctx* c, cudaEvent_t* e0, cudaEvent_t* e1) {
+  *e0 = *e1 = nullptr;
+  if (!c->prof) return false;
+  if (c->capturing) {
+    if (cudaEventCreate(e0) != cudaSuccess) return false;
+    if (cudaEventCreate(e1) != cudaSuccess) { cudaEventDestroy(*e0); *e0 = nullptr; return false; }
+    cudaEventRecordWithFlags(*e0, c->stream, cudaEventRecordExternal);
+  } else {
+    *e0 = prof_event(c);
+    *e1 = *e0 ? prof_event(c) : nullptr;
+    if (!*e1) return false;
+    cudaEventRecord(*e0, c->stream);
+  }
+  return true;
+}
+static void prof_end(la_ctx* c, cudaEvent_t e0, cudaEvent_t e1, int kind, double bytes) {
+  if (c->capturing) cudaEventRecordWithFlags(e1, c->stream, cudaEventRecordExternal);
+  else cudaEventRecord(e1, c->stream);
+  (c->capturing ? c->cap_pairs : c->ev_kern).push_back({e0, e1, kind, bytes});
 }
 
 static la_status fail(la_ctx* c, la_status s, const char* fmt, ...) {
@@ -436,14 +469,20 @@ static void finest_flops(la_ctx* c) {
   c->flops_sweep = fs;
 }
 
+// Compulsory bytes of one k_mresid launch on the finest level: c in, r or z out, f in when present
+// (csize bytes per complex), V0 in (8 bytes per point); stencil neighbours are re-reads.
+static double resid_bytes(const la_ctx* c, size_t csize, bool with_f) {
+  return (double)c->np0 * ((double)csize * c->K * (with_f ? 3 : 2) + sizeof(double));
+}
+
 extern "C" la_status la_profile_enable(la_ctx* c, int enable) {
   if (!c) return LA_EINVAL;
   prof_drain(c);
   c->prof = enable != 0;
   if (c->prof) {
     c->launches = 0;
-    c->ms_factor = c->ms_sweep = 0.0;
-    c->n_factor = c->n_sweep = 0;
+    c->ms_factor = c->ms_sweep = c->ms_resid = c->bytes_resid = 0.0;
+    c->n_factor = c->n_sweep = c->n_resid = 0;
     finest_flops(c);
   }
   return LA_OK;
@@ -460,6 +499,9 @@ extern "C" la_status la_profile_read(la_ctx* c, la_profile* out) {
   out->n_sweep = c->n_sweep;
   out->ms_sweep = c->ms_sweep;
   out->flops_sweep = c->flops_sweep;
+  out->n_resid = c->n_resid;
+  out->ms_resid = c->ms_resid;
+  out->bytes_resid = c->bytes_resid;
   return LA_OK;
 }
 
@@ -469,7 +511,7 @@ extern "C" la_status la_finalize(la_ctx* c) {
   for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
   for (auto& g : c->cg) {
     if (g.exec) cudaGraphExecDestroy(g.exec);
-    for (auto& p : g.pairs) { cudaEventDestroy(p.first); cudaEventDestroy(p.second); }
+    for (auto& p : g.pairs) { cudaEventDestroy(p.e0); cudaEventDestroy(p.e1); }
   }
   if (c->ev_fork) cudaEventDestroy(c->ev_fork);
   if (c->ev_join) cudaEventDestroy(c->ev_join);
@@ -590,18 +632,7 @@ static la_status sweep_level(la_ctx* c, int l, int nsweeps) {
       cudaError_t e;
       if (colour_count(c->geo[l], col) > 0) ++c->launches;
       cudaEvent_t e0 = nullptr, e1 = nullptr;
-      if (c->prof && l == 0) {
-        if (c->capturing) {
-          if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) e0 = e1 = nullptr;
-        } else {
-          e0 = prof_event(c);
-          e1 = e0 ? prof_event(c) : nullptr;
-        }
-        if (e1) {
-          if (c->capturing) cudaEventRecordWithFlags(e0, c->stream, cudaEventRecordExternal);
-          else cudaEventRecord(e0, c->stream);
-        }
-      }
+      const bool timed = l == 0 && prof_begin(c, &e0, &e1);
       if (l == 0)
         e = launch_sweep_fine<R>(c->geo[0], c->fine, c->d_tm, c->K, c->adj ? nullptr : Fine<R>::f(c),
                                  c->adj ? (const CT*)c->adj_y : nullptr, Fine<R>::e(c), (const CT*)c->d_fac[0], col,
@@ -610,12 +641,8 @@ static la_status sweep_level(la_ctx* c, int l, int nsweeps) {
         e = launch_sweep_coarse<R>(c->geo[l], c->d_sigma[l], c->d_tm, c->K, (const CT*)c->d_g[l], (CT*)c->d_e[l],
                                    (const CT*)c->d_fac[l], col, c->stream);
       if (e != cudaSuccess) return fail(c, LA_ECUDA, "sweep level %d colour %d: %s", l, col, cudaGetErrorString(e));
-      if (e1) {
-        // inside a capture the records must be graph nodes (external), not capture-internal joins
-        if (c->capturing) cudaEventRecordWithFlags(e1, c->stream, cudaEventRecordExternal);
-        else cudaEventRecord(e1, c->stream);
-        (c->capturing ? c->cap_pairs : c->ev_sweep).push_back({e0, e1});
-      }
+      // inside a capture the records are graph nodes (external), not capture-internal joins
+      if (timed) prof_end(c, e0, e1, 0, 0.0);
     }
   return LA_OK;
 }
@@ -631,9 +658,12 @@ static la_status vcycle(la_ctx* c, int l) {
   if (l == 0) {
     // normal residual s = M~^dagger Wt (f - M~ e) on the finest level
     // (adjoint mode: s = y - G~ e)
-    launch_mresid<R>(c->fine, c->d_tm, c->adj ? nullptr : Fine<R>::f(c), Fine<R>::e(c), nullptr, Fine<R>::z(c),
+    cudaEvent_t e0, e1;
+    const bool timed = prof_begin(c, &e0, &e1);
+    launch_mresid<R>(c->fine, c->d_tm, c->K, c->adj ? nullptr : Fine<R>::f(c), Fine<R>::e(c), nullptr, Fine<R>::z(c),
                      nullptr, c->nparts, c->stream);
-    launch_mnormal<R>(c->fine, c->d_tm, Fine<R>::z(c), Fine<R>::s(c), c->stream,
+    if (timed) prof_end(c, e0, e1, 1, resid_bytes(c, sizeof(CT), !c->adj));
+    launch_mnormal<R>(c->fine, c->d_tm, c->K, Fine<R>::z(c), Fine<R>::s(c), c->stream,
                       c->adj ? (const CT*)c->adj_y : nullptr);
     c->launches += 2;
     sfine = Fine<R>::s(c);
@@ -658,7 +688,10 @@ static la_status vcycle(la_ctx* c, int l) {
 
 // N of the current FP64 iterate into h_N[slot] (stores r~ = f~ - M~ c in d_r); enqueue only.
 static la_status action_enqueue(la_ctx* c, int slot = 0) {
-  launch_mresid<double>(c->fine, c->d_tm, c->d_f, c->d_c, c->d_r, nullptr, c->d_partials, c->nparts, c->stream);
+  cudaEvent_t e0, e1;
+  const bool timed = prof_begin(c, &e0, &e1);
+  launch_mresid<double>(c->fine, c->d_tm, c->K, c->d_f, c->d_c, c->d_r, nullptr, c->d_partials, c->nparts, c->stream);
+  if (timed) prof_end(c, e0, e1, 1, resid_bytes(c, sizeof(double2), true));
   launch_norm_final(c->d_partials, c->nparts, c->nscale, c->d_N, c->stream);
   c->launches += 2;
   LA_CHECK_LAUNCH(c);
@@ -735,10 +768,7 @@ static la_status cycle_complete(la_ctx* c, double* N) {
     la_ctx::CycleGraph& g = *c->pending_graph;
     c->launches += g.launches;
     if (c->prof) {
-      for (auto& p : g.pairs) {
-        float ms = 0.f;
-        if (cudaEventElapsedTime(&ms, p.first, p.second) == cudaSuccess) { c->ms_sweep += ms; ++c->n_sweep; }
-      }
+      for (auto& p : g.pairs) prof_add(c, p);
     }
     c->pending_graph = nullptr;
   }
@@ -902,8 +932,8 @@ static la_status adjoint_solve(la_ctx* c, int* cycles) {
   const int nb = (int)std::min<long long>((n + 255) / 256, 4096);
   LA_CUDA(c, cudaMemsetAsync(c->d_c, 0, sizeof(double2) * (size_t)n, c->stream));
   auto rho_norm = [&](double* out) -> la_status {
-    launch_mresid<double>(c->fine, c->d_tm, nullptr, c->d_c, nullptr, c->d_z, nullptr, c->nparts, c->stream);
-    launch_mnormal<double>(c->fine, c->d_tm, c->d_z, c->d_rho, c->stream, c->d_y);
+    launch_mresid<double>(c->fine, c->d_tm, c->K, nullptr, c->d_c, nullptr, c->d_z, nullptr, c->nparts, c->stream);
+    launch_mnormal<double>(c->fine, c->d_tm, c->K, c->d_z, c->d_rho, c->stream, c->d_y);
     launch_norm2_partials(n, c->d_rho, c->d_partials, std::min(nb, c->nparts), c->stream);
     launch_norm_final(c->d_partials, std::min(nb, c->nparts), 1.0, c->d_N, c->stream);
     c->launches += 4;

@@ -98,9 +98,12 @@ __device__ inline double fine_H(const FineOp& g, int px, int py, int pz, int qx,
   if (dy) return -0.5 * g.ih2[1];
   return -0.5 * g.ih2[2];
 }
+// Selects instead of indexing the parameter arrays with g.lax: a runtime index into a by-value
+// kernel parameter forces a local-memory copy of the struct.
 __device__ inline double fine_x(const FineOp& g, int px, int py, int pz) {
-  int c = g.lax == 0 ? px : (g.lax == 1 ? py : pz);
-  return g.x0[g.lax] + c * g.h[g.lax];
+  if (g.lax == 0) return g.x0[0] + px * g.h[0];
+  if (g.lax == 1) return g.x0[1] + py * g.h[1];
+  return g.x0[2] + pz * g.h[2];
 }
 __device__ inline bool fine_in(const FineOp& g, int x, int y, int z) {
   return x >= 0 && y >= 0 && z >= 0 && x < g.n[0] && y < g.n[1] && z < g.n[2];
@@ -110,11 +113,14 @@ __device__ inline void fine_sigma(const FineOp& g, int px, int py, int pz, int q
   double Hpq = fine_H(g, px, py, pz, qx, qy, qz);
   // (H^2)_pq = sum over r in {p, p +- e_a} inside the grid of H_pr H_rq
   double H2 = 0.0;
-  const int off[7][3] = {{0, 0, 0}, {1, 0, 0}, {-1, 0, 0}, {0, 1, 0}, {0, -1, 0}, {0, 0, 1}, {0, 0, -1}};
   int nofs = 1 + 2 * g.dim;
 #pragma unroll 1
   for (int t = 0; t < nofs; ++t) {
-    int rx = px + off[t][0], ry = py + off[t][1], rz = pz + off[t][2];
+    // r = p, then p + e_0, p - e_0, p + e_1, ... (offsets computed, not tabulated: a runtime-indexed
+    // table would live in local memory)
+    const int ax = (t - 1) >> 1, sg = (t & 1) ? 1 : -1;
+    const int rx = px + (t > 0 && ax == 0 ? sg : 0), ry = py + (t > 0 && ax == 1 ? sg : 0),
+              rz = pz + (t > 0 && ax == 2 ? sg : 0);
     if (!fine_in(g, rx, ry, rz)) continue;
     int ex = abs(qx - rx), ey = abs(qy - ry), ez = abs(qz - rz);
     if (ex + ey + ez > 1) continue;
@@ -178,10 +184,10 @@ void launch_time_matrices(TimeMats* tm, double t0, cudaStream_t s);
 // grid kernels (FP64 unless noted)
 void launch_rhs(const FineOp& g, const TimeMats* tm, const double2* psi0, double2* f, cudaStream_t s);
 template <typename R>
-void launch_mresid(const FineOp& g, const TimeMats* tm, const typename C2<R>::T* f, const typename C2<R>::T* c,
+void launch_mresid(const FineOp& g, const TimeMats* tm, int K, const typename C2<R>::T* f, const typename C2<R>::T* c,
                    typename C2<R>::T* r, typename C2<R>::T* z, double* partials, int nblocks_norm, cudaStream_t s);
 template <typename R>
-void launch_mnormal(const FineOp& g, const TimeMats* tm, const typename C2<R>::T* z, typename C2<R>::T* out,
+void launch_mnormal(const FineOp& g, const TimeMats* tm, int K, const typename C2<R>::T* z, typename C2<R>::T* out,
                     cudaStream_t s, const typename C2<R>::T* yadd = nullptr);
 // adjoint
 void launch_bt_lambda(int np, const TimeMats* tm, double inv_hd, const double2* lam, double2* y, cudaStream_t s);
@@ -190,9 +196,6 @@ void launch_grad_contract(const FineOp& g, const TimeMats* tm, int K, double t0,
                           const double2* psi, const double2* c, double2* partials, double* grad, cudaStream_t s);
 void launch_lambda_update(const FineOp& g, const TimeMats* tm, double hd, const double2* zneg, double2* lam,
                           cudaStream_t s);
-template <typename R>
-void launch_gresid(const LevelGeom& L, const TimeMats* tm, const double* sigma, const typename C2<R>::T* gvec,
-                   const typename C2<R>::T* e, typename C2<R>::T* out, cudaStream_t s);
 template <typename R>
 void launch_restrict(const LevelGeom& fine, const LevelGeom& coarse, int K, const typename C2<R>::T* sf,
                      typename C2<R>::T* gc, cudaStream_t s);
