@@ -1,0 +1,54 @@
+"""bench.py's JSON helpers on synthetic profile counters (no GPU): roofline fields and arithmetic."""
+import importlib.util
+import os
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def bench():
+    spec = importlib.util.spec_from_file_location("bench_mod", os.path.join(ROOT, "bench.py"))
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    return mod
+
+
+def fake_profile(**kw):
+    p = dict(launches=100, n_factor=2, ms_factor=10.0, flops_factor=4.0e9, n_sweep=8, ms_sweep=2.0,
+             flops_sweep=3.0e8, n_resid=4, ms_resid=0.4, bytes_resid=8.0e7)
+    p.update(kw)
+    return p
+
+
+def test_dominant_roofline_picks_the_larger_class_and_divides_by_the_peak(bench):
+    w = bench.workload("2d")
+    r = bench.dominant_roofline(fake_profile(), w, 0, ms_total=20.0, traffic_ok=True)
+    assert r["kernel"].startswith("k_factor")
+    assert r["achieved"] == pytest.approx(4.0e9 / 5e-3 / 1e12, rel=1e-3)
+    assert r["frac"] == pytest.approx(r["achieved"] / bench.FP64_PEAK_TFLOPS, rel=1e-3)
+    assert r["bound"] == "alu" and r["unit"] == "TFLOP/s"
+    assert r["traffic"] == round(bench.NCU_BYTES_PER_SUBVOLUME[("factor", 0)] * 4096)
+    # sweep dominant: one full sweep = four colour launches
+    r = bench.dominant_roofline(fake_profile(ms_sweep=40.0), w, 1, ms_total=60.0, traffic_ok=False)
+    assert r["kernel"].startswith("k_sweep_fine")
+    assert r["achieved"] == pytest.approx(3.0e8 / 20e-3 / 1e12, rel=1e-3)
+    assert r["peak"] == pytest.approx(bench.FP32_PEAK_TFLOPS, rel=1e-4)
+    assert r["traffic"] is None
+
+
+def test_stencil_roofline_is_bytes_over_event_time_against_hbm(bench):
+    s = bench.stencil_roofline(fake_profile(), 0)
+    peak, note = bench.hbm_peak()
+    assert s["bound"] == "hbm" and s["unit"] == "GB/s" and s["peak"] == peak
+    assert s["achieved"] == pytest.approx(8.0e7 / 0.4e-3 / 1e9, rel=1e-3)
+    assert s["us_per_launch"] == pytest.approx(100.0)
+    assert bench.stencil_roofline(fake_profile(n_resid=0), 0) is None
+
+
+def test_workloads_named_by_the_bench(bench):
+    w = bench.workload("2d")
+    assert w.n[:2] == (256, 256) and w.nt == 6 and w.levels == 4 and w.sub[:2] == (4, 4)
+    assert (w.nu1, w.nu2, w.trial) == (1, 2, 3)
+    assert bench.workload("2d-small").n[:2] == (128, 128)
