@@ -132,8 +132,7 @@ def hbm_peak():
 def dominant_roofline(prof, w, precision, ms_total, traffic_ok):
     """Roofline of the dominant kernel class (the larger total device time of factor and sweep)."""
     fac_ms = prof["ms_factor"] / max(prof["n_factor"], 1)
-    ncol = 1 << w.dim
-    swp_ms_full = prof["ms_sweep"] / max(prof["n_sweep"], 1) * ncol
+    swp_ms_full = prof["ms_sweep"] / max(prof["n_sweep"], 1)   # one event pair per full sweep
     nsub = 1
     for a in range(w.dim):
         nsub *= -(-w.n[a] // w.sub[a])
@@ -419,7 +418,11 @@ def run_3d_adjoint(args):
     w = dataclasses.replace(w, trial=3 if args.trial < 0 else args.trial)
     cfg = B.config_from_workload(w, precision=args.precision, ckpt_every=20)
     ctx = B.Context(cfg)
-    ctx.set_hamiltonian(torch.tensor(wl.potential(w).ravel(), dtype=torch.float64, device="cuda"), w.pulse)
+    V0 = torch.tensor(wl.potential(w).ravel(), dtype=torch.float64, device="cuda")
+    torch.cuda.synchronize()
+    a = time.perf_counter()
+    ctx.set_hamiltonian(V0, w.pulse)    # builds the Galerkin stencils of every coarse level
+    setup_s = time.perf_counter() - a
     psi = torch.from_numpy(wl.initial_state(w).ravel()).cuda()
     ctx.profile_enable(True)
     torch.cuda.synchronize()
@@ -444,7 +447,7 @@ def run_3d_adjoint(args):
                       "levels": w.levels, "cycle": f"V({w.nu1},{w.nu2})", "trial": w.trial,
                       "pulse_components": w.pulse.ncomp, "ckpt_every": 20},
            "cycles_per_step": sum(s_[0] for s_ in stats) / args.steps,
-           "backward_ms_per_step": 1e3 * el_b / args.steps,
+           "backward_ms_per_step": 1e3 * el_b / args.steps, "set_hamiltonian_s": setup_s,
            "roofline": dominant_roofline(prof, w, args.precision, 1e3 * el_f, traffic_ok=False),
            "stencil_roofline": stencil_roofline(prof, args.precision),
            "dipole_T": float(hd * (x * psi.abs() ** 2).sum()), "grad_norm": float(np.linalg.norm(grad)),

@@ -169,9 +169,9 @@ la_status la_relax_colour(la_ctx* ctx, const void* psi0, double t0, int colour, 
 la_status la_time_matrices(la_ctx* ctx, double t0, double* out);
 
 /* Kernel timing for roofline reporting.  While enabled, the library records CUDA events on its
-   stream around every finest-level factorisation launch, every finest-level colour-sweep launch and
-   every finest-level action-residual stencil launch (S1: r = f - M c, inside the V-cycle and for
-   the action norm), and counts all of its kernel launches.  Algorithmic flops: factorisation
+   stream around every finest-level factorisation launch, every finest-level sweep (the launches of
+   all colours together) and every finest-level action-residual stencil launch (S1: r = f - M c,
+   inside the V-cycle and for the action norm), and counts all of its kernel launches.  Algorithmic flops: factorisation
    (4/3) n^3 per subvolume (complex Cholesky of the n = |U| K unknowns); sweep 8 n^2 per subvolume
    (the two triangular solves; the residual stencil is not counted).  Algorithmic bytes of the
    residual stencil: c in, r out, f in where present (K complex each per point) and V0 in. */
@@ -180,7 +180,7 @@ typedef struct {
   int n_factor;           /* finest-level factorisation launches */
   double ms_factor;       /* their summed device time */
   double flops_factor;    /* algorithmic flops per factorisation launch */
-  int n_sweep;            /* finest-level colour-sweep launches */
+  int n_sweep;            /* finest-level sweeps (all colours) */
   double ms_sweep;
   double flops_sweep;     /* algorithmic flops of one full sweep (all colours) */
   int n_resid;            /* finest-level residual stencil launches */

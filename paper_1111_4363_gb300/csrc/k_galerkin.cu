@@ -58,6 +58,8 @@ __global__ void k_galerkin(FineOp g, LevelGeom F, const double* __restrict__ sig
               for (int ibx = 0; ibx < nbx; ++ibx) {
                 const int dx = bx[ibx] - ax[iax], dy = by[iby] - ay[iay], dz = bz[ibz] - az[iaz];
                 if (abs(dx) > 2 || abs(dy) > 2 || abs(dz) > 2) continue;
+                // the finest-level factors (I, H, X products) vanish beyond Manhattan distance 2
+                if (FROM_FINE && abs(dx) + abs(dy) + abs(dz) > 2) continue;
                 const double w = wa * wbx[ibx] * wby[iby] * wbz[ibz];
                 if (FROM_FINE) {
                   double s[LA_NPAIR];

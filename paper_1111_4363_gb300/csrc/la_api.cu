@@ -627,12 +627,13 @@ template <typename R>
 static la_status sweep_level(la_ctx* c, int l, int nsweeps) {
   typedef typename C2<R>::T CT;
   const int ncol = 1 << c->dim;
-  for (int s = 0; s < nsweeps; ++s)
+  for (int s = 0; s < nsweeps; ++s) {
+    // one event pair around a whole finest-level sweep (all colours)
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    const bool timed = l == 0 && prof_begin(c, &e0, &e1);
     for (int col = 0; col < ncol; ++col) {
       cudaError_t e;
       if (colour_count(c->geo[l], col) > 0) ++c->launches;
-      cudaEvent_t e0 = nullptr, e1 = nullptr;
-      const bool timed = l == 0 && prof_begin(c, &e0, &e1);
       if (l == 0)
         e = launch_sweep_fine<R>(c->geo[0], c->fine, c->d_tm, c->K, c->adj ? nullptr : Fine<R>::f(c),
                                  c->adj ? (const CT*)c->adj_y : nullptr, Fine<R>::e(c), (const CT*)c->d_fac[0], col,
@@ -641,9 +642,10 @@ static la_status sweep_level(la_ctx* c, int l, int nsweeps) {
         e = launch_sweep_coarse<R>(c->geo[l], c->d_sigma[l], c->d_tm, c->K, (const CT*)c->d_g[l], (CT*)c->d_e[l],
                                    (const CT*)c->d_fac[l], col, c->stream);
       if (e != cudaSuccess) return fail(c, LA_ECUDA, "sweep level %d colour %d: %s", l, col, cudaGetErrorString(e));
-      // inside a capture the records are graph nodes (external), not capture-internal joins
-      if (timed) prof_end(c, e0, e1, 0, 0.0);
     }
+    // inside a capture the records are graph nodes (external), not capture-internal joins
+    if (timed) prof_end(c, e0, e1, 0, 0.0);
+  }
   return LA_OK;
 }
 

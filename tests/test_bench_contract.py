@@ -30,10 +30,10 @@ def test_dominant_roofline_picks_the_larger_class_and_divides_by_the_peak(bench)
     assert r["frac"] == pytest.approx(r["achieved"] / bench.FP64_PEAK_TFLOPS, rel=1e-3)
     assert r["bound"] == "alu" and r["unit"] == "TFLOP/s"
     assert r["traffic"] == round(bench.NCU_BYTES_PER_SUBVOLUME[("factor", 0)] * 4096)
-    # sweep dominant: one full sweep = four colour launches
+    # sweep dominant: the counters hold whole sweeps (all colours)
     r = bench.dominant_roofline(fake_profile(ms_sweep=40.0), w, 1, ms_total=60.0, traffic_ok=False)
     assert r["kernel"].startswith("k_sweep_fine")
-    assert r["achieved"] == pytest.approx(3.0e8 / 20e-3 / 1e12, rel=1e-3)
+    assert r["achieved"] == pytest.approx(3.0e8 / 5e-3 / 1e12, rel=1e-3)
     assert r["peak"] == pytest.approx(bench.FP32_PEAK_TFLOPS, rel=1e-4)
     assert r["traffic"] is None
 
