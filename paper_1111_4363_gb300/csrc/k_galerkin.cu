@@ -6,20 +6,22 @@
 
 namespace la {
 
-// children of coarse index J on one axis with interpolation weights (transpose of the
-// cell-centred linear interpolation): fine {2J-1, 2J, 2J+1, 2J+2} with {1/4, 3/4, 3/4, 1/4}.
-__device__ __forceinline__ int gal_children(int J, int nf, bool used, int a[4], double w[4]) {
-  if (!used) { a[0] = J; w[0] = 1.0; return 1; }
-  int cnt = 0;
-  const int cand[4] = {2 * J - 1, 2 * J, 2 * J + 1, 2 * J + 2};
-  const double wc[4] = {0.25, 0.75, 0.75, 0.25};
-  for (int t = 0; t < 4; ++t)
-    if (cand[t] >= 0 && cand[t] < nf) { a[cnt] = cand[t]; w[cnt] = wc[t]; ++cnt; }
-  return cnt;
+// Children of coarse index J on one axis (transpose of the cell-centred linear interpolation):
+// fine 2J-1 .. 2J+2 inside [0, nf) with weights 1/4, 3/4, 3/4, 1/4; an unused axis maps J to J.
+__device__ __forceinline__ void gal_range(int J, int nf, bool used, int& lo, int& hi) {
+  if (!used) { lo = hi = J; return; }
+  lo = max(2 * J - 1, 0);
+  hi = min(2 * J + 2, nf - 1);
+}
+__device__ __forceinline__ double gal_weight(int a, int J, bool used) {
+  return !used ? 1.0 : ((a == 2 * J || a == 2 * J + 1) ? 0.75 : 0.25);
 }
 
-// Shared driver: thread per (coarse point J, coarse offset o').  For each fine pair (a in
-// supp(J), b in supp(J+o')) with |a-b| <= 2 accumulate w_a w_b Sigma_f[a, b] (9 pairs).
+// Thread per (coarse point J, coarse offset o).  Sums w_a w_b Sigma_f[a, b] (9 pairs) over the fine
+// pairs a in supp(J), b in supp(J + o) that can be nonzero: |a - b| <= 2 per axis on a Galerkin
+// level (box stencils), and |a - b|_1 <= 2 on the finest level, where the factors are products of
+// I, H (7-point) and X.  The b ranges are intersected with those limits axis by axis, so only
+// contributing pairs are visited.
 template <bool FROM_FINE>
 __global__ void k_galerkin(FineOp g, LevelGeom F, const double* __restrict__ sigma_f, LevelGeom C,
                            double* __restrict__ sigma_c) {
@@ -33,45 +35,50 @@ __global__ void k_galerkin(FineOp g, LevelGeom F, const double* __restrict__ sig
   else { ox = o % 5 - 2; oy = (o / 5) % 5 - 2; oz = o / 25 - 2; }
   const int jx = J % C.n[0], jy = (J / C.n[0]) % C.n[1], jz = J / (C.n[0] * C.n[1]);
   const int kx = jx + ox, ky = jy + oy, kz = jz + oz;
+  const bool ux = C.dim > 0, uy = C.dim > 1, uz = C.dim > 2;
   double acc[LA_NPAIR];
+#pragma unroll
   for (int k = 0; k < LA_NPAIR; ++k) acc[k] = 0.0;
   if (kx >= 0 && ky >= 0 && kz >= 0 && kx < C.n[0] && ky < C.n[1] && kz < C.n[2]) {
-    int ax[4], ay[4], az[4], bx[4], by[4], bz[4];
-    double wax[4], way[4], waz[4], wbx[4], wby[4], wbz[4];
-    const int nax = gal_children(jx, F.n[0], C.dim > 0, ax, wax), nbx = gal_children(kx, F.n[0], C.dim > 0, bx, wbx);
-    const int nay = gal_children(jy, F.n[1], C.dim > 1, ay, way), nby = gal_children(ky, F.n[1], C.dim > 1, by, wby);
-    const int naz = gal_children(jz, F.n[2], C.dim > 2, az, waz), nbz = gal_children(kz, F.n[2], C.dim > 2, bz, wbz);
+    int alx, ahx, aly, ahy, alz, ahz, blx, bhx, bly, bhy, blz, bhz;
+    gal_range(jx, F.n[0], ux, alx, ahx); gal_range(kx, F.n[0], ux, blx, bhx);
+    gal_range(jy, F.n[1], uy, aly, ahy); gal_range(ky, F.n[1], uy, bly, bhy);
+    gal_range(jz, F.n[2], uz, alz, ahz); gal_range(kz, F.n[2], uz, blz, bhz);
     const int fnbox = box5_count(F.dim);
 #pragma unroll 1
-    for (int iaz = 0; iaz < naz; ++iaz)
+    for (int az = alz; az <= ahz; ++az)
 #pragma unroll 1
-      for (int iay = 0; iay < nay; ++iay)
+      for (int ay = aly; ay <= ahy; ++ay)
 #pragma unroll 1
-        for (int iax = 0; iax < nax; ++iax) {
-          const double wa = wax[iax] * way[iay] * waz[iaz];
-          const int pa = (az[iaz] * F.n[1] + ay[iay]) * F.n[0] + ax[iax];
+        for (int ax = alx; ax <= ahx; ++ax) {
+          const double wa = gal_weight(ax, jx, ux) * gal_weight(ay, jy, uy) * gal_weight(az, jz, uz);
+          const int pa = (az * F.n[1] + ay) * F.n[0] + ax;
 #pragma unroll 1
-          for (int ibz = 0; ibz < nbz; ++ibz)
+          for (int bz = max(blz, az - 2); bz <= min(bhz, az + 2); ++bz) {
+            const int rz = FROM_FINE ? 2 - abs(bz - az) : 2;
 #pragma unroll 1
-            for (int iby = 0; iby < nby; ++iby)
+            for (int by = max(bly, ay - rz); by <= min(bhy, ay + rz); ++by) {
+              const int ry = FROM_FINE ? rz - abs(by - ay) : 2;
+              const double wyz = wa * gal_weight(by, ky, uy) * gal_weight(bz, kz, uz);
 #pragma unroll 1
-              for (int ibx = 0; ibx < nbx; ++ibx) {
-                const int dx = bx[ibx] - ax[iax], dy = by[iby] - ay[iay], dz = bz[ibz] - az[iaz];
-                if (abs(dx) > 2 || abs(dy) > 2 || abs(dz) > 2) continue;
-                // the finest-level factors (I, H, X products) vanish beyond Manhattan distance 2
-                if (FROM_FINE && abs(dx) + abs(dy) + abs(dz) > 2) continue;
-                const double w = wa * wbx[ibx] * wby[iby] * wbz[ibz];
+              for (int bx = max(blx, ax - ry); bx <= min(bhx, ax + ry); ++bx) {
+                const double w = wyz * gal_weight(bx, kx, ux);
                 if (FROM_FINE) {
                   double s[LA_NPAIR];
-                  fine_sigma(g, ax[iax], ay[iay], az[iaz], bx[ibx], by[iby], bz[ibz], s);
+                  fine_sigma(g, ax, ay, az, bx, by, bz, s);
+#pragma unroll
                   for (int k = 0; k < LA_NPAIR; ++k) acc[k] += w * s[k];
                 } else {
-                  const int fo = box5_index(F.dim, dx, dy, dz);
+                  const int fo = box5_index(F.dim, bx - ax, by - ay, bz - az);
+#pragma unroll
                   for (int k = 0; k < LA_NPAIR; ++k) acc[k] += w * sigma_f[sigma_offset(pa, k, fo, fnbox)];
                 }
               }
+            }
+          }
         }
   }
+#pragma unroll
   for (int k = 0; k < LA_NPAIR; ++k) sigma_c[sigma_offset(J, k, o, nbox)] = acc[k];
 }
 
