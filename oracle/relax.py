@@ -56,6 +56,15 @@ def unknown_indices(points: np.ndarray, K: int) -> np.ndarray:
     return (points[:, None] * K + np.arange(K)[None, :]).ravel()
 
 
+def block_update(G, g, x, idx) -> np.ndarray:
+    """delta_U = G_UU^{-1} (g - G x)_U for one subvolume U (unknown indices idx): the exact
+    minimisation of N over U with the rest of x fixed (Sec. II)."""
+    G = G.tocsr()
+    s = g[idx] - G[idx] @ x
+    Guu = G[idx][:, idx].toarray()
+    return sla.cho_solve(sla.cho_factor(Guu, lower=True), s)
+
+
 class BlockRelaxation:
     """Exact coloured block Gauss-Seidel on a Hermitian positive-definite level operator G."""
 

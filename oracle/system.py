@@ -134,6 +134,42 @@ def assemble(prob: Problem, t0: float, psi0: np.ndarray, weight: str = "dual"):
     return M, f.astype(np.complex128), W
 
 
+def hamiltonian_row(prob: Problem, q: int):
+    """Column indices and values of row q of T + diag(V0) (the 3/5/7-point stencil, Dirichlet walls)."""
+    coord = np.unravel_index(q, prob.shape)
+    cols, vals = [q], [float(prob.V0[q])]
+    for a in range(prob.dim):
+        w = -0.5 / (prob.h[a] * prob.h[a])
+        vals[0] += -2.0 * w                       # -1/2 * (-2 / h^2)
+        for step in (-1, 1):
+            nb = list(coord)
+            nb[a] += step
+            if 0 <= nb[a] < prob.shape[a]:
+                cols.append(int(np.ravel_multi_index(tuple(nb), prob.shape)))
+                vals.append(w)
+    return np.array(cols, dtype=np.int64), np.array(vals)
+
+
+def residual_at(prob: Problem, t0: float, psi0: np.ndarray, c: np.ndarray, points) -> np.ndarray:
+    """Rows of r = f - M c at the listed points, shape (len(points), K), from the stencil form of the
+    same system as `assemble` (for grids too large to assemble):
+      (M c)[q,m] = h^d sum_n ( i Qb[m,n] c[q,n] - Ub[m,n] (H c)[q,n] - x_q Eb[m,n] c[q,n] ),
+      f[q,m]     = h^d ( Ub0[m] (H psi0)[q] + x_q Eb0[m] psi0[q] )."""
+    Ub, Qb, Ub0, Eb, Eb0 = time_matrices(prob, t0)
+    K, v = prob.K, prob.vol
+    C = np.asarray(c).reshape(-1, K)
+    out = np.empty((len(points), K), dtype=np.complex128)
+    for j, q in enumerate(points):
+        cols, vals = hamiltonian_row(prob, int(q))
+        Hc = vals @ C[cols]                       # (H c)[q, :]
+        Hpsi = vals @ psi0[cols]
+        xq = prob.xlaser[q]
+        f = v * (Ub0 * Hpsi + xq * Eb0 * psi0[q])
+        Mc = v * (1j * (Qb @ C[q]) - Ub @ Hc - xq * (Eb @ C[q]))
+        out[j] = f - Mc
+    return out
+
+
 def residual(M, f, c):
     """Action residual r = f - M c (Eq. actionresidual with the initial condition moved to f)."""
     return f - M @ c

@@ -48,3 +48,30 @@ def gpu_context(w: wl.Workload, precision=0, **overrides):
 def to_dev(x):
     import torch
     return torch.from_numpy(np.ascontiguousarray(x)).to("cuda")
+
+
+# extrapolation of the next step's coefficients from the last 1, 2, 3 converged ones (newest first)
+TRIAL_WEIGHTS = {1: [1.0], 2: [2.0, -1.0], 3: [3.0, -3.0, 1.0]}
+
+
+def oracle_trial_propagation(w, psi0, nsteps, trial, ncycles, t0=0.0):
+    """nsteps steps of exactly ncycles V-cycles each (oracle), every step started from the
+    extrapolated trial (or c = 0 where the trial's action is not below N(0))."""
+    from oracle import multigrid, system
+    from oracle.propagate import numpy_coarse_sub, numpy_sub
+    prob = system.Problem.from_workload(w)
+    psi = psi0.astype(np.complex128).copy()
+    hist = []
+    for s in range(nsteps):
+        M, f, W = system.assemble(prob, t0 + s * w.dt, psi, w.weight)
+        c0 = None
+        if trial > 0 and hist:
+            q = min(len(hist), trial)
+            cand = sum(a * h for a, h in zip(TRIAL_WEIGHTS[q], hist[::-1][:q]))
+            if system.action_norm(system.residual(M, f, cand), W) < system.action_norm(f, W):
+                c0 = cand
+        c, _, _, _ = multigrid.solve_step(M, f, W, prob.shape, prob.K, numpy_sub(w), w.levels, w.nu1, w.nu2,
+                                          w.coarse_sweeps, ncycles=ncycles, c0=c0, coarse_sub=numpy_coarse_sub(w))
+        hist.append(c)
+        psi = system.advance(psi, c, prob.K)
+    return psi

@@ -1,0 +1,201 @@
+"""Parity at the full configurations, in the launch configuration bench.py times (GB300 required).
+
+2D 256 x 256 x 6 (the bench's schedule: 4 levels, V(1,2), quadratic trial): the whole residual,
+whole colour passes and the first V-cycle element by element against the oracle, which assembles
+this size in seconds; converged steps checked by the oracle's own evaluation of the stopping
+rule.  3D 128^3 x 4: the residual at sampled points (the oracle evaluates rows one by one) and
+the adjoint gradient against central differences.  Batched 512 problems: sampled members
+against the same problems stepped alone.
+"""
+import dataclasses
+import importlib.util
+import os
+
+import numpy as np
+import pytest
+
+from oracle import multigrid, relax, system
+from oracle.propagate import numpy_coarse_sub, numpy_sub
+from paper_1111_4363_gb300 import workloads as wl
+from tests.helpers import gpu_context, oracle_trial_propagation, rel_l2
+
+pytestmark = pytest.mark.gpu
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+T0 = 0.3
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+
+
+@pytest.fixture(scope="module")
+def bench():
+    spec = importlib.util.spec_from_file_location("bench_mod", os.path.join(ROOT, "bench.py"))
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    return mod
+
+
+@pytest.fixture(scope="module")
+def w2d(bench):
+    return bench.workload("2d")
+
+
+@pytest.fixture(scope="module")
+def sys2d(w2d):
+    prob = system.Problem.from_workload(w2d)
+    psi0 = wl.initial_state(w2d).ravel()
+    M, f, W = system.assemble(prob, T0, psi0, w2d.weight)
+    G = (M.conj().T @ W @ M).tocsr()
+    g = M.conj().T @ (W @ f)
+    return prob, psi0, M, f, W, G, g
+
+
+def test_2d_residual_and_action(w2d, sys2d):
+    prob, psi0, M, f, W, G, g = sys2d
+    assert w2d.n[:2] == (256, 256) and w2d.nt == 6
+    ctx = gpu_context(w2d)
+    c = wl.random_state(M.shape[1], 7) * 0.05
+    r = np.zeros_like(c)
+    N = ctx.residual(psi0, T0, c, r)
+    r_ref = system.residual(M, f, c)
+    assert rel_l2(r, r_ref) < 1e-13
+    assert N == pytest.approx(system.action_norm(r_ref, W), rel=1e-12)
+
+
+@pytest.mark.parametrize("colour", [0, 3])
+def test_2d_colour_pass(w2d, sys2d, colour):
+    """Every subvolume of one colour (1024 of 4096) against the oracle's exact block minimisation."""
+    prob, psi0, M, f, W, G, g = sys2d
+    ctx = gpu_context(w2d)
+    c0 = wl.random_state(M.shape[1], 8 + colour) * 0.05
+    got = c0.copy()
+    ctx.relax_colour(psi0, T0, colour, got)
+    ref = c0.copy()
+    touched = np.zeros(M.shape[1], dtype=bool)
+    for col, pts in relax.subvolumes(prob.shape, numpy_sub(w2d)):
+        if col == colour:
+            idx = relax.unknown_indices(pts, prob.K)
+            ref[idx] += relax.block_update(G, g, c0, idx)
+            touched[idx] = True
+    assert touched.sum() == M.shape[1] // 4
+    assert rel_l2(got - c0, ref - c0) < 1e-10
+    assert rel_l2(got, ref) < 1e-11
+    assert np.array_equal(got[~touched], c0[~touched])
+
+
+def test_2d_first_vcycle(w2d, sys2d):
+    """One V(1,2) cycle of the bench schedule from c = 0: every coefficient against the oracle."""
+    prob, psi0, M, f, W, G, g = sys2d
+    ctx = gpu_context(w2d)
+    c_ref, hist, _, _ = multigrid.solve_step(M, f, W, prob.shape, prob.K, numpy_sub(w2d), w2d.levels, w2d.nu1,
+                                             w2d.nu2, w2d.coarse_sweeps, ncycles=1,
+                                             coarse_sub=numpy_coarse_sub(w2d))
+    c = np.zeros(M.shape[1], dtype=np.complex128)
+    st, (cycles, sweeps, N, rel) = ctx.solve_step(psi0, T0, c, ncycles=1)
+    assert (cycles, sweeps) == (1, w2d.nu1 + w2d.nu2)
+    assert rel_l2(c, c_ref) < 1e-11
+    assert N == pytest.approx(hist[-1], rel=1e-9)
+
+
+def test_2d_converged_steps_meet_the_stopping_rule(w2d, sys2d):
+    """FP64 and mixed precision to the bench tolerance and, refined to 1e-22, to each other: the oracle
+    evaluates N(c)/N(0) of the returned coefficients itself."""
+    prob, psi0, M, f, W, G, g = sys2d
+    N0 = system.action_norm(f, W)
+    out = {}
+    for precision in (0, 1):
+        for tol in (w2d.tol, 1e-22):
+            ctx = gpu_context(w2d, precision=precision, tol=tol, max_cycles=60)
+            c = np.zeros(M.shape[1], dtype=np.complex128)
+            st, (cycles, sweeps, N, rel) = ctx.solve_step(psi0, T0, c)
+            N_ref = system.action_norm(system.residual(M, f, c), W)
+            assert N_ref / N0 <= tol * (1 + 1e-6), (precision, tol, N_ref / N0)
+            if tol == w2d.tol:
+                assert N == pytest.approx(N_ref, rel=1e-6)
+            out[(precision, tol)] = c
+    # mixed precision refined to 1e-22 equals the FP64 result to 1e-9
+    assert rel_l2(out[(1, 1e-22)], out[(0, 1e-22)]) < 1e-9
+
+
+def test_2d_steps_with_the_trial(w2d):
+    """Two steps of la_step in the bench schedule with one cycle each (the second from the trial)."""
+    w = dataclasses.replace(w2d, tol=0.0, max_cycles=1)
+    psi0 = wl.initial_state(w).ravel()
+    ref = oracle_trial_propagation(w, psi0, 2, w.trial, 1)
+    ctx = gpu_context(w2d, tol=0.0, max_cycles=1)
+    psi = psi0.copy()
+    ctx.step(psi, 2, 0.0)
+    assert rel_l2(psi, ref) < 1e-11
+
+
+def test_3d_residual_at_sampled_points():
+    w = wl.hydrogen_3d(n=128, nsteps=20)
+    prob = system.Problem.from_workload(w)
+    psi0 = wl.initial_state(w).ravel()
+    ctx = gpu_context(dataclasses.replace(w, trial=3))
+    c = wl.random_state(w.nunknowns, 9) * 0.05
+    r = np.zeros_like(c)
+    ctx.residual(psi0, T0, c, r)
+    rng = np.random.default_rng(3)
+    n = prob.shape
+    corners = [np.ravel_multi_index((z, y, x), n) for z in (0, n[0] - 1) for y in (0, n[1] - 1) for x in (0, n[2] - 1)]
+    pts = np.unique(np.concatenate([corners, rng.integers(0, prob.npoints, 300)]))
+    ref = system.residual_at(prob, T0, psi0, c, pts)
+    got = r.reshape(-1, w.nt)[pts]
+    np.testing.assert_allclose(got, ref, rtol=0, atol=1e-13 * np.max(np.abs(ref)))
+
+
+def test_3d_adjoint_gradient_against_central_differences():
+    """128^3 with a 32-component pulse, mixed precision local solves, checkpoints every 2 steps."""
+    nsteps = 3
+    w = dataclasses.replace(wl.hydrogen_3d(n=128, nsteps=nsteps), trial=3)
+    prob = system.Problem.from_workload(w)
+    psi0 = wl.initial_state(w).ravel()
+
+    def forward(wk):
+        ctx = gpu_context(wk, precision=1, tol=1e-22, max_cycles=80, ckpt_every=2)
+        psi = psi0.copy()
+        ctx.step(psi, nsteps, 0.0)
+        return ctx, psi
+
+    ctx, psiT = forward(w)
+    dJ = prob.vol * prob.xlaser * psiT
+    g = ctx.backward(dJ, w.pulse.ncomp)
+    picks = np.argsort(-np.abs(g))[:2]
+    eps = 1e-4 * max(np.max(np.abs(w.pulse.amp)), 1e-3)
+    for j in picks:
+        vals = []
+        for sgn in (1, -1):
+            amp = list(w.pulse.amp)
+            amp[j] += sgn * eps
+            _, pT = forward(dataclasses.replace(w, pulse=dataclasses.replace(w.pulse, amp=amp)))
+            vals.append(system.dipole(prob, pT))
+        fd = (vals[0] - vals[1]) / (2 * eps)
+        assert g[j] == pytest.approx(fd, rel=1e-5), (j, g[j], fd)
+
+
+def test_batched_members_equal_their_single_runs(bench):
+    """All 512 problems in one la_step_batch call with the autotuned schedule; sampled members against
+    the same problems stepped alone."""
+    import torch
+    from paper_1111_4363_gb300 import autotune
+    from paper_1111_4363_gb300 import binding as B
+    members = [dataclasses.replace(wl.batched_2d(i), trial=3) for i in range(512)]
+    best = autotune.tune(dataclasses.replace(members[0], n=(128, 128, 1)), precision=0)
+    ws = [dataclasses.replace(m, **best) for m in members]
+    ctxs = [gpu_context(w) for w in ws]
+    psis = [torch.from_numpy(wl.initial_state(w).ravel().copy()).cuda() for w in ws]
+    nsteps = 2
+    stats = B.step_batch(ctxs, psis, nsteps, [0.0] * len(ws))
+    assert all(s[3] <= w.tol for w, st in zip(ws, stats) for s in st)
+    for i in (0, 1, 100, 255, 256, 511):
+        ctx = gpu_context(ws[i])
+        psi = torch.from_numpy(wl.initial_state(ws[i]).ravel().copy()).cuda()
+        ctx.step(psi, nsteps, 0.0)
+        assert rel_l2(psis[i].cpu().numpy(), psi.cpu().numpy()) < 1e-14, i

@@ -4,15 +4,10 @@ import dataclasses
 import numpy as np
 import pytest
 
-from oracle import multigrid, system
-from oracle.propagate import numpy_coarse_sub, numpy_sub
 from paper_1111_4363_gb300 import workloads as wl
-from tests.helpers import gpu_context, rel_l2, small_3d
+from tests.helpers import gpu_context, oracle_trial_propagation, rel_l2, small_3d
 
 pytestmark = pytest.mark.gpu
-
-# extrapolation of the next step's coefficients from the last 1, 2, 3 converged ones (newest first)
-WEIGHTS = {1: [1.0], 2: [2.0, -1.0], 3: [3.0, -3.0, 1.0]}
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -22,27 +17,6 @@ def _cuda():
         pytest.skip("no CUDA device")
     import __graft_entry__
     __graft_entry__.build()
-
-
-def oracle_trial_propagation(w, psi0, nsteps, trial, ncycles, t0=0.0):
-    """nsteps steps of exactly ncycles V-cycles each, every step started from the extrapolated trial
-    (or c = 0 where the trial's action is not below N(0))."""
-    prob = system.Problem.from_workload(w)
-    psi = psi0.astype(np.complex128).copy()
-    hist = []
-    for s in range(nsteps):
-        M, f, W = system.assemble(prob, t0 + s * w.dt, psi, w.weight)
-        c0 = None
-        if trial > 0 and hist:
-            q = min(len(hist), trial)
-            cand = sum(a * h for a, h in zip(WEIGHTS[q], hist[::-1][:q]))
-            if system.action_norm(system.residual(M, f, cand), W) < system.action_norm(f, W):
-                c0 = cand
-        c, _, _, _ = multigrid.solve_step(M, f, W, prob.shape, prob.K, numpy_sub(w), w.levels, w.nu1, w.nu2,
-                                          w.coarse_sweeps, ncycles=ncycles, c0=c0, coarse_sub=numpy_coarse_sub(w))
-        hist.append(c)
-        psi = system.advance(psi, c, prob.K)
-    return psi
 
 
 @pytest.mark.parametrize("name,trial", [("2d", 1), ("2d", 2), ("2d", 3), ("3d", 3)])

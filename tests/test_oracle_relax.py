@@ -72,6 +72,27 @@ def test_block_update_minimises_N_over_the_block():
         assert system.action_norm(system.residual(M, f, c + d), W) >= N * (1 - 1e-14)
 
 
+def test_single_block_update_is_the_blockwise_minimiser():
+    """relax.block_update on one subvolume: zero block gradient of N afterwards, and the same update
+    as the colour pass (same-colour blocks do not interact)."""
+    w, prob, M, f, W = small_2d(n=12, levels=1)
+    G = (M.conj().T @ W @ M).tocsr()
+    g = M.conj().T @ (W @ f)
+    R = relax.BlockRelaxation(G, prob.shape, (4, 4), prob.K)
+    c0 = wl.random_state(M.shape[1], 6) * 0.01
+    ref = c0.copy()
+    R.colour_pass(ref, g, 1)
+    for col, idx, _ in R.blocks:
+        if col != 1:
+            continue
+        d = relax.block_update(G, g, c0, idx)
+        np.testing.assert_allclose(d, (ref - c0)[idx], rtol=0, atol=1e-12 * np.max(np.abs(d)))
+        c = c0.copy()
+        c[idx] += d
+        grad = M.conj().T @ (W @ system.residual(M, f, c))
+        assert np.max(np.abs(grad[idx])) < 1e-10 * np.max(np.abs(g))
+
+
 def test_same_colour_updates_are_independent():
     # computing all same-colour corrections from one residual equals applying them one by one
     w, prob, M, f, W = small_2d(n=16, levels=1)

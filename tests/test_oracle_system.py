@@ -209,3 +209,30 @@ def test_dual_weight_is_test_basis_invariant():
     Ar = sp.kron(sp.identity(prob.npoints), A) @ r
     W2 = sp.kron(sp.identity(prob.npoints), np.linalg.inv(A @ Ub @ A.T)) / prob.vol
     assert system.action_norm(Ar, W2) == pytest.approx(system.action_norm(r, W), rel=1e-12)
+
+
+@pytest.mark.parametrize("kind", ["1d", "2d", "2d_ragged", "3d"])
+def test_pointwise_residual_matches_the_assembled_system(kind):
+    """residual_at (stencil rows, for grids too large to assemble) against the sparse assembly."""
+    import dataclasses
+    if kind == "1d":
+        w = wl.harmonic_1d()
+    elif kind == "2d":
+        w = wl.softcore_2d(n=16, levels=2)
+    elif kind == "2d_ragged":
+        w = dataclasses.replace(wl.softcore_2d(n=16, levels=1), n=(15, 11, 1))
+    else:
+        w = wl.hydrogen_3d(n=8, nsteps=3, ncomp=3, sub=2)
+    prob = system.Problem.from_workload(w)
+    psi0 = wl.initial_state(w).ravel()
+    t0 = 0.7
+    M, f, W = system.assemble(prob, t0, psi0)
+    c = wl.random_state(M.shape[1], 4) * 0.1
+    r = system.residual(M, f, c).reshape(-1, w.nt)
+    rng = np.random.default_rng(1)
+    pts = np.unique(np.concatenate([[0, prob.npoints - 1], rng.integers(0, prob.npoints, 40)]))
+    got = system.residual_at(prob, t0, psi0, c, pts)
+    np.testing.assert_allclose(got, r[pts], rtol=0, atol=1e-13 * np.max(np.abs(r)))
+    # c = 0 gives the right-hand side itself
+    np.testing.assert_allclose(system.residual_at(prob, t0, psi0, np.zeros_like(c), pts),
+                               f.reshape(-1, w.nt)[pts], rtol=0, atol=1e-14 * np.max(np.abs(f)))
