@@ -250,18 +250,318 @@ __global__ void __launch_bounds__(256) k_mresid(FineOp g, const TimeMats* __rest
   }
 }
 
+// ------------------------------------------------------------------ TMA-staged stencils (2D, 3D)
+// complex64 V-cycle residual and normal residual on grids of dimension 2 and 3, for even K.  A CTA
+// owns a kTX x kTY column tile and marches along z through a chunk of planes (chosen per launch so
+// that the CTAs fill whole waves of the resident slots).  Each plane of the tile
+// with a one-point halo in x and y is one TMA tensor load ({2K floats, x, y[, z]} box) into a
+// ring of kNST shared-memory stages, completed on an mbarrier per stage; coordinates outside the
+// grid read zeros, which is the Dirichlet wall in x, y and z.  Loads run kNST - 3 planes ahead of
+// the plane being computed, issued by one thread, so the bytes in flight do not depend on the
+// number of resident threads.
+constexpr int kTX = 32, kTY = 8, kNST = 5;
+constexpr int kPW = kTX + 2, kPH = kTY + 2, kPS = kPW * kPH;
+constexpr unsigned kTmaWaitLimit = 1u << 22;
+// stage stride in float2 units: one plane box, rounded up to 128 bytes so every stage is aligned
+__host__ __device__ constexpr int stage_f2(int K) { return ((kPS * K * 8 + 127) / 128) * 16; }
+
+__device__ __forceinline__ unsigned smem_addr(const void* p) {
+  return static_cast<unsigned>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void tma_plane(void* dst, const CUtensorMap* map, int dim, int x, int y, int z,
+                                          unsigned long long* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes) : "memory");
+  if (dim > 2)
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], [%6];"
+        ::"r"(smem_addr(dst)), "l"(map), "r"(0), "r"(x), "r"(y), "r"(z), "r"(smem_addr(bar)) : "memory");
+  else
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
+        ::"r"(smem_addr(dst)), "l"(map), "r"(0), "r"(x), "r"(y), "r"(smem_addr(bar)) : "memory");
+}
+// Polls the phase of an mbarrier at most `limit` times; true when it completed.
+__device__ __forceinline__ bool tma_wait(unsigned long long* bar, unsigned parity, unsigned limit) {
+  for (unsigned it = 0; it < limit; ++it) {
+    unsigned done;
+    asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+                 "selp.u32 %0, 1, 0, p;\n\t}"
+                 : "=r"(done) : "r"(smem_addr(bar)), "r"(parity) : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+
+// K complex values of a staged point, two per 16-byte shared-memory load (K even).  For K = 4
+// the records are 32 bytes apart, so lanes i and i + 4 of an 8-lane shared-memory wavefront would
+// hit the same banks; lanes with bit 2 set read the two halves in the opposite order, which makes
+// every wavefront touch each bank once (K = 6 records, 48 bytes apart, are conflict-free as is).
+template <int K>
+__device__ __forceinline__ void lds_k(const float2* src, float2 (&out)[K]) {
+  const float4* q = reinterpret_cast<const float4*>(src);
+  if constexpr (K == 4) {
+    const bool sw = (threadIdx.x >> 2) & 1;
+    const float4 a = q[sw ? 1 : 0], b = q[sw ? 0 : 1];
+    const float4 lo = sw ? b : a, hi = sw ? a : b;
+    out[0] = make_float2(lo.x, lo.y);
+    out[1] = make_float2(lo.z, lo.w);
+    out[2] = make_float2(hi.x, hi.y);
+    out[3] = make_float2(hi.z, hi.w);
+  } else {
+#pragma unroll
+    for (int m = 0; m < K / 2; ++m) {
+      const float4 v = q[m];
+      out[2 * m] = make_float2(v.x, v.y);
+      out[2 * m + 1] = make_float2(v.z, v.w);
+    }
+  }
+}
+
+// NORMAL = false: out = Wt (f - M~ v) (f nullable).  NORMAL = true: out = M~^dagger v (+ yadd).
+// Stage layout (as loaded): [y][x][K complex], point-major.
+template <int K, bool NORMAL>
+__global__ void __launch_bounds__(kTX * kTY, K <= 4 ? 4 : 2) k_stencil_tma(FineOp g, const __grid_constant__ CUtensorMap map,
+                                                               const TimeMats* __restrict__ tm,
+                                                               const float2* __restrict__ f, float2* __restrict__ out,
+                                                               const float2* __restrict__ yadd, int* status, int zc) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  constexpr unsigned kPlaneBytes = kPS * K * 8;
+  constexpr int kStage = stage_f2(K);
+  float2* stage = reinterpret_cast<float2*>(smem);                                  // [kNST][kPS][K] (padded)
+  unsigned long long* bar = reinterpret_cast<unsigned long long*>(smem + (size_t)kNST * kStage * 8);
+  float* Qb = reinterpret_cast<float*>(bar + kNST);
+  float* Ub = Qb + K * K;
+  float* Eb = Ub + K * K;
+  float* Wt = Eb + K * K;
+  const int tid = threadIdx.x, tx = tid % kTX, ty = tid / kTX;
+  const int x0 = blockIdx.x * kTX, y0 = blockIdx.y * kTY;
+  const int nz = g.dim > 2 ? g.n[2] : 1;
+  const int z0 = blockIdx.z * zc, z1 = min(z0 + zc, nz);
+  // planes j = 0 .. nplanes-1 hold z = zlo + j: z0-1 .. z1 in 3D, z = 0 alone in 2D
+  const int zlo = g.dim > 2 ? z0 - 1 : 0;
+  const int nplanes = g.dim > 2 ? z1 - z0 + 2 : 1;
+  for (int i = tid; i < K * K; i += blockDim.x) {
+    Qb[i] = (float)tm->Qb[i]; Ub[i] = (float)tm->Ub[i]; Eb[i] = (float)tm->Eb[i]; Wt[i] = (float)tm->Wt[i];
+  }
+  if (tid == 0) {
+    for (int s = 0; s < kNST; ++s)
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(bar + s)) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  int issued = 0;   // planes issued so far (meaningful in thread 0)
+  if (tid == 0)
+    for (; issued < min(kNST, nplanes); ++issued)
+      tma_plane(stage + (size_t)issued * kStage, &map, g.dim, x0 - 1, y0 - 1, zlo + issued, bar + issued, kPlaneBytes);
+  const bool in = x0 + tx < g.n[0] && y0 + ty < g.n[1];
+  const int x = x0 + tx, y = y0 + ty;
+  const int c0 = (ty + 1) * kPW + tx + 1;
+  const float wx = (float)(-0.5 * g.ih2[0]), wy = (float)(-0.5 * g.ih2[1]), wz = (float)(-0.5 * g.ih2[2]);
+  const long long col = (long long)y * g.n[0] + x, plane = (long long)g.n[0] * g.n[1];
+  // the point-wise inputs (f or yadd, and V0) are loaded before the plane wait, so their latency
+  // overlaps it
+  const float2* pin = NORMAL ? yadd : f;
+  bool ok = true;
+  // 3D: iteration z needs planes z-1, z, z+1 (indices jz-1, jz, jz+1 with jz = z - zlo); 2D: plane 0
+  for (int z = z0; z < z1; ++z) {
+    const int jz = z - zlo;
+    float2 add[K];
+    double v0 = 0.0;
+#pragma unroll
+    for (int m = 0; m < K; ++m) add[m] = make_float2(0.f, 0.f);
+    if (in) {
+      v0 = g.V0[(long long)z * plane + col];
+      if (pin) load_k<float2, K>(pin, (long long)z * plane + col, add);
+    }
+    const int jfirst = g.dim > 2 ? (z == z0 ? jz - 1 : jz + 1) : 0, jlast = g.dim > 2 ? jz + 1 : 0;
+    for (int j = jfirst; j <= jlast; ++j) ok = ok && tma_wait(bar + j % kNST, (j / kNST) & 1, kTmaWaitLimit);
+    if (__syncthreads_or(!ok)) {   // CTA-uniform: some thread gave up waiting
+      ok = false;
+      break;
+    }
+    if (in) {
+      const float2* Pz = stage + (size_t)(jz % kNST) * kStage;
+      const float2* own = Pz + (size_t)c0 * K;
+      const long long p = (long long)z * plane + col;
+      const float dg = (float)(g.dsum + v0);
+      float2 cur[K], hv[K], a[K];
+      lds_k<K>(own, cur);
+#pragma unroll
+      for (int m = 0; m < K; ++m) hv[m] = make_float2(dg * cur[m].x, dg * cur[m].y);
+      // +x, -x, +y, -y, +z, -z, as in apply_H
+      const float2* nb[6] = {own + K, own - K, own + kPW * K, own - kPW * K, nullptr, nullptr};
+      const float wts[6] = {wx, wx, wy, wy, wz, wz};
+      if (g.dim > 2) {
+        nb[4] = stage + (size_t)((jz + 1) % kNST) * kStage + (size_t)c0 * K;
+        nb[5] = stage + (size_t)((jz - 1) % kNST) * kStage + (size_t)c0 * K;
+      }
+#pragma unroll
+      for (int t = 0; t < 6; ++t) {
+        if (t >= 4 && g.dim < 3) break;
+        lds_k<K>(nb[t], a);
+#pragma unroll
+        for (int m = 0; m < K; ++m) { hv[m].x += wts[t] * a[m].x; hv[m].y += wts[t] * a[m].y; }
+      }
+      const float xl = (float)fine_x(g, x, y, z);
+      float2 res[K];
+#pragma unroll
+      for (int m = 0; m < K; ++m) res[m] = add[m];   // f (zero when absent) or yadd
+#pragma unroll
+      for (int m = 0; m < K; ++m) {
+        float qr = 0, qi = 0, ur = 0, ui = 0, er = 0, ei = 0;
+#pragma unroll
+        for (int n = 0; n < K; ++n) {
+          const float q = NORMAL ? Qb[n * K + m] : Qb[m * K + n], u = Ub[m * K + n], e = Eb[m * K + n];
+          qr += q * cur[n].x; qi += q * cur[n].y;
+          ur += u * hv[n].x; ui += u * hv[n].y;
+          er += e * cur[n].x; ei += e * cur[n].y;
+        }
+        if (!NORMAL) {
+          res[m].x = res[m].x - (-qi - ur - xl * er);   // r = f - (i Qb v - Ub H v - x Eb v)
+          res[m].y = res[m].y - (qr - ui - xl * ei);
+        } else {
+          float2 w = make_float2(qi - ur - xl * er, -qr - ui - xl * ei);   // -i Qb^T v - Ub H v - x Eb v
+          if (yadd) { w.x += res[m].x; w.y += res[m].y; }
+          res[m] = w;
+        }
+      }
+      if (!NORMAL) {
+        float2 zv[K];
+#pragma unroll
+        for (int m = 0; m < K; ++m) {
+          float zr = 0, zi = 0;
+#pragma unroll
+          for (int n = 0; n < K; ++n) { zr += Wt[m * K + n] * res[n].x; zi += Wt[m * K + n] * res[n].y; }
+          zv[m] = make_float2(zr, zi);
+        }
+        store_k<float2, K>(out, p, zv);
+      } else {
+        store_k<float2, K>(out, p, res);
+      }
+    }
+    // every thread is done with plane jz - 1: refill its stage with plane jz - 1 + kNST
+    __syncthreads();
+    const int jn = jz - 1 + kNST;
+    if (g.dim > 2 && tid == 0 && jz >= 1 && jn < nplanes) {
+      tma_plane(stage + (size_t)(jn % kNST) * kStage, &map, g.dim, x0 - 1, y0 - 1, zlo + jn, bar + jn % kNST,
+                kPlaneBytes);
+      issued = jn + 1;
+    }
+  }
+  if (!ok) {
+    // a plane did not arrive within the wait limit: flag it and give the copies in flight a last
+    // bounded chance to land before the CTA exits
+    if (tid == 0) {
+      if (status) atomicOr(status, 4);
+      for (int j = max(0, issued - kNST); j < issued; ++j) tma_wait(bar + j % kNST, (j / kNST) & 1, kTmaWaitLimit);
+    }
+  }
+}
+
+// Resident CTAs of a stencil kernel on the whole GPU (SMs x CTAs per SM), queried once.
+template <typename Kern>
+static int stencil_slots(Kern kern, size_t smem) {
+  int dev = 0, nsm = 0, per_sm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kTX * kTY, smem);
+  return std::max(1, nsm * per_sm);
+}
+// Planes per CTA: among 4..16, the chunk whose CTA count fills the resident slots best (the last
+// wave as full as possible), larger chunks on ties (fewer z-halo planes).
+static int stencil_zchunk(int nz, int ncol, int slots) {
+  if (nz <= 1) return 1;
+  int best = 16;
+  double best_eff = -1.0;
+  for (int zc = 16; zc >= 4; --zc) {
+    const long long ctas = (long long)ncol * ((nz + zc - 1) / zc);
+    const long long waves = (ctas + slots - 1) / slots;
+    const double eff = (double)ctas / (double)(waves * slots);
+    if (eff > best_eff + 1e-9) { best_eff = eff; best = zc; }
+  }
+  return best;
+}
+
+size_t stencil_tma_smem(int K) {
+  return (size_t)kNST * stage_f2(K) * 8 + kNST * sizeof(unsigned long long) + 4 * (size_t)K * K * sizeof(float);
+}
+
+// Tensor map of a complex64 point-major field for the TMA stencils: dims {2K floats, nx, ny[, nz]},
+// box {2K, kTX + 2, kTY + 2[, 1]}, zero fill outside.  False when the field does not qualify (odd K,
+// 1D grid) or the driver call fails; the per-point kernels are used then.
+bool encode_stencil_map(const FineOp& g, int K, const float2* field, CUtensorMap* map) {
+  if (g.dim < 2 || (K & 1) || !field) return false;
+  static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+  if (!encode) {
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess || !fn)
+      return false;
+    encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+  }
+  const cuuint32_t rank = g.dim + 1;
+  cuuint64_t dims[4] = {(cuuint64_t)(2 * K), (cuuint64_t)g.n[0], (cuuint64_t)g.n[1], (cuuint64_t)g.n[2]};
+  cuuint64_t strides[3] = {(cuuint64_t)8 * K, (cuuint64_t)8 * K * g.n[0], (cuuint64_t)8 * K * g.n[0] * g.n[1]};
+  cuuint32_t box[4] = {(cuuint32_t)(2 * K), (cuuint32_t)kPW, (cuuint32_t)kPH, 1};
+  cuuint32_t estr[4] = {1, 1, 1, 1};
+  const CUresult r = encode(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, rank, const_cast<float2*>(field), dims, strides, box,
+                            estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                            CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
+template <bool NORMAL>
+static bool launch_stencil_tma(const FineOp& g, const CUtensorMap* map, const TimeMats* tm, int K, const float2* f,
+                               float2* out, const float2* yadd, int* status, cudaStream_t s) {
+  if (!map || g.dim < 2 || (K & 1)) return false;
+  const int nz = g.dim > 2 ? g.n[2] : 1;
+  const size_t smem = stencil_tma_smem(K);
+#define LA_CALL(KK)                                                                                  \
+  {                                                                                                  \
+    static bool attr = false;                                                                        \
+    if (!attr) {                                                                                     \
+      if (cudaFuncSetAttribute(k_stencil_tma<KK, NORMAL>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                               (int)smem) != cudaSuccess)                                            \
+        return false;                                                                                \
+      attr = true;                                                                                   \
+    }                                                                                                \
+    static int slots = 0;                                                                            \
+    if (!slots) slots = stencil_slots(k_stencil_tma<KK, NORMAL>, smem);                              \
+    const int ncol = ((g.n[0] + kTX - 1) / kTX) * ((g.n[1] + kTY - 1) / kTY);                       \
+    const int zc = stencil_zchunk(nz, ncol, slots);                                                  \
+    const dim3 grid((g.n[0] + kTX - 1) / kTX, (g.n[1] + kTY - 1) / kTY, (nz + zc - 1) / zc);         \
+    k_stencil_tma<KK, NORMAL><<<grid, kTX * kTY, smem, s>>>(g, *map, tm, f, out, yadd, status, zc);  \
+  }
+  switch (K) {
+    case 2: LA_CALL(2); break;
+    case 4: LA_CALL(4); break;
+    case 6: LA_CALL(6); break;
+    case 8: LA_CALL(8); break;
+    default: return false;
+  }
+#undef LA_CALL
+  return true;
+}
+
 template <typename R>
 void launch_mresid(const FineOp& g, const TimeMats* tm, int K, const typename C2<R>::T* f,
                    const typename C2<R>::T* c, typename C2<R>::T* r, typename C2<R>::T* z, double* partials, int nb,
-                   cudaStream_t s) {
+                   cudaStream_t s, const CUtensorMap* cmap, int* status) {
+  if constexpr (sizeof(R) == 4) {
+    // the complex64 V-cycle residual (z out only) of a field with a tensor map takes the TMA kernel
+    if (!r && !partials && z && launch_stencil_tma<false>(g, cmap, tm, K, f, z, nullptr, status, s)) return;
+  } else {
+    (void)cmap; (void)status;
+  }
 #define LA_CALL(KK) k_mresid<typename C2<R>::T, KK><<<nb, 256, 0, s>>>(g, tm, f, c, r, z, partials)
   LA_K_DISPATCH(K, LA_CALL)
 #undef LA_CALL
 }
 template void launch_mresid<double>(const FineOp&, const TimeMats*, int, const double2*, const double2*, double2*,
-                                    double2*, double*, int, cudaStream_t);
+                                    double2*, double*, int, cudaStream_t, const CUtensorMap*, int*);
 template void launch_mresid<float>(const FineOp&, const TimeMats*, int, const float2*, const float2*, float2*,
-                                   float2*, double*, int, cudaStream_t);
+                                   float2*, double*, int, cudaStream_t, const CUtensorMap*, int*);
 
 // s = M~^dagger z: s_p = -i Qb^T z_p - Ub (H z)_p - x_p Eb z_p.
 template <typename CT, int K>
@@ -303,16 +603,21 @@ __global__ void __launch_bounds__(256) k_mnormal(FineOp g, const TimeMats* __res
 
 template <typename R>
 void launch_mnormal(const FineOp& g, const TimeMats* tm, int K, const typename C2<R>::T* z, typename C2<R>::T* out,
-                    cudaStream_t s, const typename C2<R>::T* yadd) {
+                    cudaStream_t s, const typename C2<R>::T* yadd, const CUtensorMap* zmap, int* status) {
+  if constexpr (sizeof(R) == 4) {
+    if (launch_stencil_tma<true>(g, zmap, tm, K, nullptr, out, yadd, status, s)) return;
+  } else {
+    (void)zmap; (void)status;
+  }
   const int np = g.n[0] * g.n[1] * g.n[2];
 #define LA_CALL(KK) k_mnormal<typename C2<R>::T, KK><<<(np + 255) / 256, 256, 0, s>>>(g, tm, z, out, yadd)
   LA_K_DISPATCH(K, LA_CALL)
 #undef LA_CALL
 }
 template void launch_mnormal<double>(const FineOp&, const TimeMats*, int, const double2*, double2*, cudaStream_t,
-                                     const double2*);
+                                     const double2*, const CUtensorMap*, int*);
 template void launch_mnormal<float>(const FineOp&, const TimeMats*, int, const float2*, float2*, cudaStream_t,
-                                    const float2*);
+                                    const float2*, const CUtensorMap*, int*);
 
 // ------------------------------------------------------------------ Galerkin-level residual
 // out_p = g_p - sum_{kk'} Theta_kk' sum_o Sigma[p][kk'][o] e_{p+o}  (coarse levels, all points)

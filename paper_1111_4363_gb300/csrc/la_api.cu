@@ -95,6 +95,9 @@ struct la_ctx {
   cudaStream_t cap = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   double* h_N = nullptr;          // pinned
+  // TMA tensor maps of the complex64 fields the finest-level stencils read (mixed precision, 2D/3D)
+  CUtensorMap map_e32, map_z32;
+  bool have_map_e32 = false, have_map_z32 = false;
 };
 
 static cudaEvent_t prof_event(la_ctx* c) {
@@ -433,6 +436,10 @@ extern "C" la_status la_init(const la_config* cfg, void* stream, la_ctx** out) {
 #undef ALLOC
   c->fine.V0 = c->d_V0;
   c->use_graph = getenv("LA_NO_GRAPH") == nullptr;
+  if (k.precision == 1) {
+    c->have_map_e32 = encode_stencil_map(c->fine, c->K, c->d_e32, &c->map_e32);
+    c->have_map_z32 = encode_stencil_map(c->fine, c->K, c->d_z32, &c->map_z32);
+  }
   if (cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking) != cudaSuccess ||
       cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) != cudaSuccess ||
@@ -649,6 +656,20 @@ static la_status sweep_level(la_ctx* c, int l, int nsweeps) {
   return LA_OK;
 }
 
+// Error for a nonzero device status word (bit 1: a subvolume matrix was not positive definite;
+// bit 4: a TMA-staged plane did not arrive within its wait limit).
+static la_status status_error(la_ctx* c, int status) {
+  if (status & 1) return fail(c, LA_ECUDA, "a subvolume matrix was not positive definite (status %d)", status);
+  return fail(c, LA_ECUDA, "a staged copy did not complete within its wait limit (status %d)", status);
+}
+
+// The TMA tensor map of a finest-level complex64 field, when one was encoded for it.
+static const CUtensorMap* stencil_map(const la_ctx* c, const void* field) {
+  if (c->have_map_e32 && field == c->d_e32) return &c->map_e32;
+  if (c->have_map_z32 && field == c->d_z32) return &c->map_z32;
+  return nullptr;
+}
+
 template <typename R>
 static la_status vcycle(la_ctx* c, int l) {
   typedef typename C2<R>::T CT;
@@ -663,10 +684,10 @@ static la_status vcycle(la_ctx* c, int l) {
     cudaEvent_t e0, e1;
     const bool timed = prof_begin(c, &e0, &e1);
     launch_mresid<R>(c->fine, c->d_tm, c->K, c->adj ? nullptr : Fine<R>::f(c), Fine<R>::e(c), nullptr, Fine<R>::z(c),
-                     nullptr, c->nparts, c->stream);
+                     nullptr, c->nparts, c->stream, stencil_map(c, Fine<R>::e(c)), c->d_status);
     if (timed) prof_end(c, e0, e1, 1, resid_bytes(c, sizeof(CT), !c->adj));
     launch_mnormal<R>(c->fine, c->d_tm, c->K, Fine<R>::z(c), Fine<R>::s(c), c->stream,
-                      c->adj ? (const CT*)c->adj_y : nullptr);
+                      c->adj ? (const CT*)c->adj_y : nullptr, stencil_map(c, Fine<R>::z(c)), c->d_status);
     c->launches += 2;
     sfine = Fine<R>::s(c);
   } else {
@@ -866,7 +887,7 @@ static la_status solve_current(la_ctx* c, int ncycles, la_step_stats* st, bool u
   LA_CUDA(c, cudaMemcpy(&status, c->d_status, sizeof(int), cudaMemcpyDeviceToHost));
   if (status) {
     cudaMemsetAsync(c->d_status, 0, sizeof(int), c->stream);
-    return fail(c, LA_ECUDA, "a subvolume matrix was not positive definite (status %d)", status);
+    return status_error(c, status);
   }
   c->last_N = N;
   c->last_rel = N0 > 0 ? N / N0 : 0.0;
@@ -1037,7 +1058,7 @@ extern "C" la_status la_backward(la_ctx* c, const void* dJ_dpsiT, double* grad_a
   LA_CUDA(c, cudaStreamSynchronize(c->stream));
   int status = 0;
   LA_CUDA(c, cudaMemcpy(&status, c->d_status, sizeof(int), cudaMemcpyDeviceToHost));
-  if (status) return fail(c, LA_ECUDA, "a subvolume matrix was not positive definite");
+  if (status) return status_error(c, status);
   return LA_OK;
 }
 
@@ -1110,7 +1131,7 @@ extern "C" la_status la_step_batch(la_ctx* const* ctxs, int nctx, void* const* p
       la_ctx* c = ctxs[i];
       int status = 0;
       if (cudaMemcpy(&status, c->d_status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess || status) {
-        st = fail(c, LA_ECUDA, "a subvolume matrix was not positive definite");
+        st = status_error(c, status);
         break;
       }
       c->last_N = N[i];
@@ -1215,7 +1236,7 @@ extern "C" la_status la_relax_colour(la_ctx* c, const void* psi0, double t0, int
   LA_CUDA(c, cudaStreamSynchronize(c->stream));
   int status = 0;
   LA_CUDA(c, cudaMemcpy(&status, c->d_status, sizeof(int), cudaMemcpyDeviceToHost));
-  if (status) return fail(c, LA_ECUDA, "a subvolume matrix was not positive definite");
+  if (status) return status_error(c, status);
   return LA_OK;
 }
 

@@ -10,6 +10,8 @@
 // factors Sigma^l_kk' = I^T Sigma^{l-1}_kk' I (Galerkin, Sec. III), stored as
 // radius-2 box stencils.
 #pragma once
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <stddef.h>
@@ -185,10 +187,14 @@ void launch_time_matrices(TimeMats* tm, double t0, cudaStream_t s);
 void launch_rhs(const FineOp& g, const TimeMats* tm, const double2* psi0, double2* f, cudaStream_t s);
 template <typename R>
 void launch_mresid(const FineOp& g, const TimeMats* tm, int K, const typename C2<R>::T* f, const typename C2<R>::T* c,
-                   typename C2<R>::T* r, typename C2<R>::T* z, double* partials, int nblocks_norm, cudaStream_t s);
+                   typename C2<R>::T* r, typename C2<R>::T* z, double* partials, int nblocks_norm, cudaStream_t s,
+                   const CUtensorMap* cmap = nullptr, int* status = nullptr);
 template <typename R>
 void launch_mnormal(const FineOp& g, const TimeMats* tm, int K, const typename C2<R>::T* z, typename C2<R>::T* out,
-                    cudaStream_t s, const typename C2<R>::T* yadd = nullptr);
+                    cudaStream_t s, const typename C2<R>::T* yadd = nullptr, const CUtensorMap* zmap = nullptr,
+                    int* status = nullptr);
+// Tensor map of a complex64 field for the TMA-staged stencils (false: field does not qualify).
+bool encode_stencil_map(const FineOp& g, int K, const float2* field, CUtensorMap* map);
 // adjoint
 void launch_bt_lambda(int np, const TimeMats* tm, double inv_hd, const double2* lam, double2* y, cudaStream_t s);
 void launch_norm2_partials(long long n, const double2* v, double* partials, int nblocks, cudaStream_t s);
