@@ -183,9 +183,12 @@ typedef struct {
   int n_sweep;            /* finest-level sweeps (all colours) */
   double ms_sweep;
   double flops_sweep;     /* algorithmic flops of one full sweep (all colours) */
-  int n_resid;            /* finest-level residual stencil launches */
+  int n_resid;            /* finest-level residual stencil launches in FP64 */
   double ms_resid;        /* their summed device time */
   double bytes_resid;     /* their summed algorithmic bytes */
+  int n_resid32;          /* the same for the complex64 residual stencil (mixed-precision V-cycle) */
+  double ms_resid32;
+  double bytes_resid32;
 } la_profile;
 /* enable != 0 resets the counters and starts recording; 0 stops.  Errors: LA_EINVAL. */
 la_status la_profile_enable(la_ctx* ctx, int enable);

@@ -51,7 +51,8 @@ class la_profile(C.Structure):
     _fields_ = [("launches", C.c_longlong), ("n_factor", C.c_int), ("ms_factor", C.c_double),
                 ("flops_factor", C.c_double), ("n_sweep", C.c_int), ("ms_sweep", C.c_double),
                 ("flops_sweep", C.c_double), ("n_resid", C.c_int), ("ms_resid", C.c_double),
-                ("bytes_resid", C.c_double)]
+                ("bytes_resid", C.c_double), ("n_resid32", C.c_int), ("ms_resid32", C.c_double),
+                ("bytes_resid32", C.c_double)]
 
 
 _lib = None

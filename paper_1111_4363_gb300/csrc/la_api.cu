@@ -68,7 +68,7 @@ struct la_ctx {
   bool prof = false;
   long long launches = 0;
   std::vector<cudaEvent_t> ev_pool;
-  // a timed launch: kind 0 = finest colour sweep, 1 = action residual stencil (k_mresid)
+  // a timed launch: kind 0 = finest sweep, 1 = FP64 residual stencil, 2 = complex64 residual stencil
   struct ProfPair {
     cudaEvent_t e0, e1;
     int kind;
@@ -77,8 +77,8 @@ struct la_ctx {
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_factor;
   std::vector<ProfPair> ev_kern;
   size_t ev_next = 0;
-  double ms_factor = 0.0, ms_sweep = 0.0, ms_resid = 0.0, bytes_resid = 0.0;
-  int n_factor = 0, n_sweep = 0, n_resid = 0;
+  double ms_factor = 0.0, ms_sweep = 0.0, ms_resid = 0.0, bytes_resid = 0.0, ms_resid32 = 0.0, bytes_resid32 = 0.0;
+  int n_factor = 0, n_sweep = 0, n_resid = 0, n_resid32 = 0;
   double flops_factor = 0.0, flops_sweep = 0.0;
   // one captured cycle (V-cycle + action norm + read-back), replayed on an internal stream
   struct CycleGraph {
@@ -113,7 +113,8 @@ static void prof_add(la_ctx* c, const la_ctx::ProfPair& p) {
   float ms = 0.f;
   if (cudaEventElapsedTime(&ms, p.e0, p.e1) != cudaSuccess) return;
   if (p.kind == 0) { c->ms_sweep += ms; ++c->n_sweep; }
-  else { c->ms_resid += ms; ++c->n_resid; c->bytes_resid += p.bytes; }
+  else if (p.kind == 1) { c->ms_resid += ms; ++c->n_resid; c->bytes_resid += p.bytes; }
+  else { c->ms_resid32 += ms; ++c->n_resid32; c->bytes_resid32 += p.bytes; }
 }
 // Drain recorded event pairs into the totals (synchronises).
 static void prof_drain(la_ctx* c) {
@@ -488,8 +489,8 @@ extern "C" la_status la_profile_enable(la_ctx* c, int enable) {
   c->prof = enable != 0;
   if (c->prof) {
     c->launches = 0;
-    c->ms_factor = c->ms_sweep = c->ms_resid = c->bytes_resid = 0.0;
-    c->n_factor = c->n_sweep = c->n_resid = 0;
+    c->ms_factor = c->ms_sweep = c->ms_resid = c->bytes_resid = c->ms_resid32 = c->bytes_resid32 = 0.0;
+    c->n_factor = c->n_sweep = c->n_resid = c->n_resid32 = 0;
     finest_flops(c);
   }
   return LA_OK;
@@ -509,6 +510,9 @@ extern "C" la_status la_profile_read(la_ctx* c, la_profile* out) {
   out->n_resid = c->n_resid;
   out->ms_resid = c->ms_resid;
   out->bytes_resid = c->bytes_resid;
+  out->n_resid32 = c->n_resid32;
+  out->ms_resid32 = c->ms_resid32;
+  out->bytes_resid32 = c->bytes_resid32;
   return LA_OK;
 }
 
@@ -685,7 +689,7 @@ static la_status vcycle(la_ctx* c, int l) {
     const bool timed = prof_begin(c, &e0, &e1);
     launch_mresid<R>(c->fine, c->d_tm, c->K, c->adj ? nullptr : Fine<R>::f(c), Fine<R>::e(c), nullptr, Fine<R>::z(c),
                      nullptr, c->nparts, c->stream, stencil_map(c, Fine<R>::e(c)), c->d_status);
-    if (timed) prof_end(c, e0, e1, 1, resid_bytes(c, sizeof(CT), !c->adj));
+    if (timed) prof_end(c, e0, e1, sizeof(R) == 8 ? 1 : 2, resid_bytes(c, sizeof(CT), !c->adj));
     launch_mnormal<R>(c->fine, c->d_tm, c->K, Fine<R>::z(c), Fine<R>::s(c), c->stream,
                       c->adj ? (const CT*)c->adj_y : nullptr, stencil_map(c, Fine<R>::z(c)), c->d_status);
     c->launches += 2;

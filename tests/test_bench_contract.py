@@ -17,7 +17,8 @@ def bench():
 
 def fake_profile(**kw):
     p = dict(launches=100, n_factor=2, ms_factor=10.0, flops_factor=4.0e9, n_sweep=8, ms_sweep=2.0,
-             flops_sweep=3.0e8, n_resid=4, ms_resid=0.4, bytes_resid=8.0e7)
+             flops_sweep=3.0e8, n_resid=4, ms_resid=0.4, bytes_resid=8.0e7, n_resid32=2, ms_resid32=0.1,
+             bytes_resid32=4.0e8)
     p.update(kw)
     return p
 
@@ -45,6 +46,9 @@ def test_stencil_roofline_is_bytes_over_event_time_against_hbm(bench):
     assert s["achieved"] == pytest.approx(8.0e7 / 0.4e-3 / 1e9, rel=1e-3)
     assert s["us_per_launch"] == pytest.approx(100.0)
     assert bench.stencil_roofline(fake_profile(n_resid=0), 0) is None
+    c = bench.stencil_roofline(fake_profile(), 1, c64=True)
+    assert c["achieved"] == pytest.approx(4.0e8 / 0.1e-3 / 1e9, rel=1e-3) and c["launches"] == 2
+    assert bench.stencil_roofline(fake_profile(n_resid32=0), 1, c64=True) is None
 
 
 def test_workloads_named_by_the_bench(bench):
