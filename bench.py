@@ -45,9 +45,10 @@ FP32_PEAK_TFLOPS = 152 * 256 * 2070e6 / 1e12  # 152 SMs x 128 FP32 lanes x 2 flo
 L2_BYTES = 129 * 2 ** 20
 
 
-# production schedule of the 2D workload: 4-level V(1,2) cycles started from the quadratic trial
-# (2 cycles per step to 1e-10, against 5 for V(1,1) from c = 0); --trial 0 gives the plain start
-PRODUCTION_2D = dict(nu1=1, nu2=2, trial=3)
+# production schedule of the 2D workload: 4-level cycles, V(1,2) on the finest level and one
+# pre-sweep on the Galerkin levels, started from the quadratic trial (2 cycles per step to 1e-10,
+# against 5 for V(1,1) from c = 0); --trial 0 gives the plain start
+PRODUCTION_2D = dict(nu1=1, nu2=2, coarse_nu=(1, 0), trial=3)
 
 
 def workload(name: str) -> wl.Workload:
@@ -117,6 +118,14 @@ class ClockSampler:
                     reasons.add(nm)
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
                 "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cycle_name(w) -> str:
+    """V(nu1,nu2) of the finest level, with the Galerkin levels' shape when it differs."""
+    s = f"V({w.nu1},{w.nu2})"
+    if getattr(w, "coarse_nu", None) is not None:
+        s += f", Galerkin levels ({w.coarse_nu[0]},{w.coarse_nu[1]})"
+    return s
 
 
 def hbm_peak():
@@ -258,7 +267,7 @@ def run_ours(args):
            "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": prec_tag, "data": "synthetic",
            "config": {"workload": w.name, "grid": list(w.shape), "K": w.nt, "subvolume": list(w.sub[:w.dim]),
-                      "levels": w.levels, "cycle": f"V({w.nu1},{w.nu2})", "coarse_sweeps": w.coarse_sweeps,
+                      "levels": w.levels, "cycle": cycle_name(w), "coarse_sweeps": w.coarse_sweeps,
                       "tol_rel_action": w.tol, "precision": args.precision, "trial": w.trial,
                       "parallelism": "replicas" if ws > 1 else "single",
                       "l2": "inputs smaller than L2; each step rewrites the 352 MB factor store (> L2)"},
@@ -281,7 +290,7 @@ def run_ours(args):
 def oracle_cycle_rate(w: wl.Workload, budget_s: float):
     """Time the CPU oracle on the workload: one step's setup, then V-cycles until ``budget_s`` is used."""
     from oracle import multigrid, system
-    from oracle.propagate import numpy_coarse_sub, numpy_sub
+    from oracle.propagate import numpy_coarse_nu, numpy_coarse_sub, numpy_sub
     prob = system.Problem.from_workload(w)
     psi0 = wl.initial_state(w).ravel()
     t_a = time.perf_counter()
@@ -289,7 +298,7 @@ def oracle_cycle_rate(w: wl.Workload, budget_s: float):
     G0 = (M.conj().T @ W @ M).tocsr()
     g0 = M.conj().T @ (W @ f)
     hier = multigrid.Hierarchy(G0, prob.shape, prob.K, numpy_sub(w), w.levels, w.nu1, w.nu2, w.coarse_sweeps,
-                                     numpy_coarse_sub(w))
+                                     numpy_coarse_sub(w), numpy_coarse_nu(w))
     setup_s = time.perf_counter() - t_a
     c = np.zeros(M.shape[1], dtype=np.complex128)
     ncyc = 0
@@ -323,7 +332,7 @@ def run_reference(args):
     cores = len(os.sched_getaffinity(0))
     # each step = one oracle V-cycle on the full workload after an untimed setup; bounded to a few minutes
     from oracle import multigrid, system
-    from oracle.propagate import numpy_coarse_sub, numpy_sub
+    from oracle.propagate import numpy_coarse_nu, numpy_coarse_sub, numpy_sub
     prob = system.Problem.from_workload(w)
     psi0 = wl.initial_state(w).ravel()
     t_a = time.perf_counter()
@@ -331,7 +340,7 @@ def run_reference(args):
     G0 = (M.conj().T @ W @ M).tocsr()
     g0 = M.conj().T @ (W @ f)
     hier = multigrid.Hierarchy(G0, prob.shape, prob.K, numpy_sub(w), w.levels, w.nu1, w.nu2, w.coarse_sweeps,
-                                     numpy_coarse_sub(w))
+                                     numpy_coarse_sub(w), numpy_coarse_nu(w))
     setup_s = time.perf_counter() - t_a
     c = np.zeros(M.shape[1], dtype=np.complex128)
     for _ in range(min(args.warmup, 1)):
@@ -449,7 +458,7 @@ def run_3d_adjoint(args):
            "steps": args.steps, "warmup": 0, "ms_per_step": 1e3 * el_f / args.steps, "higher_is_better": True,
            "dtype": "f64" if args.precision == 0 else "c64 local solves + f64 refinement", "data": "synthetic",
            "config": {"workload": w.name, "grid": list(w.shape), "K": w.nt, "subvolume": list(w.sub),
-                      "levels": w.levels, "cycle": f"V({w.nu1},{w.nu2})", "trial": w.trial,
+                      "levels": w.levels, "cycle": cycle_name(w), "trial": w.trial,
                       "pulse_components": w.pulse.ncomp, "ckpt_every": 20},
            "cycles_per_step": sum(s_[0] for s_ in stats) / args.steps,
            "backward_ms_per_step": 1e3 * el_b / args.steps, "set_hamiltonian_s": setup_s,

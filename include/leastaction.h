@@ -78,6 +78,9 @@ typedef struct {
                            Eq. leastaction_correction): 0 = c = 0; 1..3 = extrapolation, polynomial of
                            degree trial-1 in the step index, of the last `trial` converged coefficient
                            vectors of the same propagation */
+  int coarse_cycle;     /* 0: V(nu1, nu2) on every level but the coarsest; 1: V(coarse_nu1, coarse_nu2) on
+                           the Galerkin levels above the coarsest (the finest keeps nu1, nu2) */
+  int coarse_nu1, coarse_nu2;
 } la_config;
 
 /* Laser field E(t) = sum_k amp[k] * env_k(t) * sin(omega[k] t), env_k = exp(-((t - t_center[k])/sigma[k])^2)

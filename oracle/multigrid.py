@@ -10,8 +10,9 @@ correction minimises the residual norm N over the coarse space), I is
 cell-centred 2:1 linear interpolation per axis with zero Dirichlet ghosts
 (weights 3/4, 1/4), acting on space only (the K time functions are kept), and
 the coarsest level is relaxed ``coarse_sweeps`` times instead of a direct
-factorisation.  Cycle shape V(nu1, nu2); a single level means nu1 + nu2
-sweeps per cycle.
+factorisation.  Cycle shape V(nu1, nu2) on the finest level; the Galerkin levels
+above the coarsest use (nu1, nu2) too, or ``coarse_nu`` = (nu1c, nu2c) when
+given.  A single level means nu1 + nu2 sweeps per cycle.
 """
 from __future__ import annotations
 
@@ -44,9 +45,10 @@ def interpolation(coarse_shape, K: int) -> sp.csr_matrix:
 class Hierarchy:
     """Levels 0 (finest) .. L-1, each with its Galerkin operator and block relaxation."""
 
-    def __init__(self, G0, shape0, K, sub, levels, nu1=1, nu2=1, coarse_sweeps=2, coarse_sub=None):
+    def __init__(self, G0, shape0, K, sub, levels, nu1=1, nu2=1, coarse_sweeps=2, coarse_sub=None, coarse_nu=None):
         self.K, self.L = K, levels
         self.nu1, self.nu2, self.coarse_sweeps = nu1, nu2, coarse_sweeps
+        self.coarse_nu = (nu1, nu2) if coarse_nu is None else tuple(coarse_nu)
         self.shapes = [tuple(shape0)]
         self.G = [G0.tocsr()]
         self.I = []                    # I[l]: level l+1 -> level l
@@ -74,7 +76,8 @@ class Hierarchy:
             for _ in range(self.coarse_sweeps):
                 self.relax[l].sweep(x, g)
             return
-        for _ in range(self.nu1):
+        nu1, nu2 = (self.nu1, self.nu2) if l == 0 else self.coarse_nu
+        for _ in range(nu1):
             self.relax[l].sweep(x, g, hook)
         s = g - self.G[l] @ x
         gc = self.I[l].T @ s
@@ -83,7 +86,7 @@ class Hierarchy:
         x += self.I[l] @ xc
         if after_colour is not None and l == 0:
             after_colour(-1)           # -1 marks "after the coarse-grid correction"
-        for _ in range(self.nu2):
+        for _ in range(nu2):
             self.relax[l].sweep(x, g, hook)
 
     def fine_sweeps_per_cycle(self) -> int:
@@ -91,14 +94,14 @@ class Hierarchy:
 
 
 def solve_step(M, f, W, shape, K, sub, levels, nu1, nu2, coarse_sweeps, ncycles=None, tol=None,
-               max_cycles=200, after_colour=None, c0=None, coarse_sub=None):
+               max_cycles=200, after_colour=None, c0=None, coarse_sub=None, coarse_nu=None):
     """Relax from c0 (default 0) by V-cycles; returns (c, history of N, cycles run).
 
     Exactly ``ncycles`` cycles when given, else until N(c)/N(0) <= tol or ``max_cycles``.
     """
     G0 = (M.conj().T @ W @ M).tocsr()
     g0 = M.conj().T @ (W @ f)
-    hier = Hierarchy(G0, shape, K, sub, levels, nu1, nu2, coarse_sweeps, coarse_sub)
+    hier = Hierarchy(G0, shape, K, sub, levels, nu1, nu2, coarse_sweeps, coarse_sub, coarse_nu)
     c = np.zeros(M.shape[1], dtype=np.complex128) if c0 is None else c0.astype(np.complex128).copy()
     N0 = system.action_norm(f, W)
     hist = [system.action_norm(system.residual(M, f, c), W)]

@@ -19,6 +19,10 @@ def numpy_coarse_sub(w: wl.Workload):
     return None if w.coarse_sub is None else tuple(w.coarse_sub[a] for a in reversed(range(w.dim)))
 
 
+def numpy_coarse_nu(w: wl.Workload):
+    return None if getattr(w, "coarse_nu", None) is None else tuple(w.coarse_nu)
+
+
 def step_direct(prob: system.Problem, psi0: np.ndarray, t0: float):
     M, f, W = system.assemble(prob, t0, psi0)
     c = system.direct_solve(M, f)
@@ -30,7 +34,7 @@ def step_relax(prob: system.Problem, w: wl.Workload, psi0: np.ndarray, t0: float
     c, hist, cyc, _ = multigrid.solve_step(M, f, W, prob.shape, prob.K, numpy_sub(w), w.levels, w.nu1, w.nu2,
                                            w.coarse_sweeps, ncycles=ncycles,
                                            tol=w.tol if tol is None else tol, max_cycles=w.max_cycles,
-                                           coarse_sub=numpy_coarse_sub(w))
+                                           coarse_sub=numpy_coarse_sub(w), coarse_nu=numpy_coarse_nu(w))
     return system.advance(psi0, c, prob.K), c, hist, cyc
 
 

@@ -1,4 +1,5 @@
-"""Autotuner for the relaxation schedule: subvolume shape, levels, cycle shape V(nu1, nu2).
+"""Autotuner for the relaxation schedule: subvolume shape, levels, cycle shape V(nu1, nu2) and the
+Galerkin levels' cycle shape.
 
 Every candidate reaches the same tolerance on N/N(0) (the minimiser does not depend on the
 schedule), so candidates are ranked by measured time per least-action step on the GPU.  The
@@ -28,11 +29,14 @@ def candidates(w: wl.Workload):
         for levels in (1, 2, 3, 4):
             if any(w.n[a] % (1 << (levels - 1)) for a in range(w.dim)):
                 continue
-            # one level: nu1 + nu2 sweeps between action evaluations
-            shapes = ((1, 1), (1, 2)) if levels > 1 else ((1, 0), (1, 1), (2, 1))
-            for nu1, nu2 in shapes:
+            # one level: nu1 + nu2 sweeps between action evaluations; with three or more levels the
+            # Galerkin levels above the coarsest may take a lighter (1, 0) cycle
+            shapes = ((1, 1, None), (1, 2, None)) if levels > 1 else ((1, 0, None), (1, 1, None), (2, 1, None))
+            if levels > 2:
+                shapes += ((1, 2, (1, 0)),)
+            for nu1, nu2, cnu in shapes:
                 out.append(dict(sub=(sx, sy, 1), coarse_sub=(2, 2, 1), levels=levels,
-                                coarse_sweeps=1, nu1=nu1, nu2=nu2))
+                                coarse_sweeps=1, nu1=nu1, nu2=nu2, coarse_nu=cnu))
     return out
 
 

@@ -35,7 +35,8 @@ class la_config(C.Structure):
                 ("sub", C.c_int * 3), ("levels", C.c_int), ("nu1", C.c_int), ("nu2", C.c_int),
                 ("coarse_sweeps", C.c_int), ("max_cycles", C.c_int), ("tol", C.c_double), ("weight", C.c_int),
                 ("precision", C.c_int), ("laser_axis", C.c_int), ("ckpt_every", C.c_int),
-                ("coarse_sub", C.c_int * 3), ("trial", C.c_int)]
+                ("coarse_sub", C.c_int * 3), ("trial", C.c_int), ("coarse_cycle", C.c_int),
+                ("coarse_nu1", C.c_int), ("coarse_nu2", C.c_int)]
 
 
 class la_pulse(C.Structure):
@@ -136,6 +137,8 @@ def config_from_workload(w, precision: int = 0, **overrides) -> la_config:
         for a in range(w.dim):
             cfg.coarse_sub[a] = w.coarse_sub[a]
     cfg.trial = getattr(w, "trial", 0)
+    if getattr(w, "coarse_nu", None) is not None:
+        cfg.coarse_cycle, cfg.coarse_nu1, cfg.coarse_nu2 = 1, int(w.coarse_nu[0]), int(w.coarse_nu[1])
     for k, v in overrides.items():
         setattr(cfg, k, v)
     return cfg

@@ -323,6 +323,7 @@ extern "C" la_status la_init(const la_config* cfg, void* stream, la_ctx** out) {
   else if (k.laser_axis < 0 || k.laser_axis >= k.dim) bad("laser_axis must be a used axis");
   else if (k.ckpt_every < 0) bad("ckpt_every must be >= 0");
   else if (k.trial < 0 || k.trial > 3) bad("trial must be 0..3");
+  else if (k.coarse_cycle && (k.coarse_nu1 < 0 || k.coarse_nu2 < 0)) bad("coarse_nu1, coarse_nu2 must be >= 0");
   if (st == LA_OK) {
     for (int a = 0; a < 3 && st == LA_OK; ++a) {
       if (a < k.dim) {
@@ -680,7 +681,9 @@ static la_status vcycle(la_ctx* c, int l) {
   const la_config& k = c->cfg;
   if (c->L == 1) return sweep_level<R>(c, 0, k.nu1 + k.nu2);
   if (l == c->L - 1) return sweep_level<R>(c, l, k.coarse_sweeps);
-  LA_TRY(sweep_level<R>(c, l, k.nu1));
+  const int nu1 = (l > 0 && k.coarse_cycle) ? k.coarse_nu1 : k.nu1;
+  const int nu2 = (l > 0 && k.coarse_cycle) ? k.coarse_nu2 : k.nu2;
+  LA_TRY(sweep_level<R>(c, l, nu1));
   CT* sfine;
   if (l == 0) {
     // normal residual s = M~^dagger Wt (f - M~ e) on the finest level
@@ -710,7 +713,7 @@ static la_status vcycle(la_ctx* c, int l) {
   launch_prolong_add<R>(c->geo[l], c->geo[l + 1], c->K, (const CT*)c->d_e[l + 1], efine, c->stream);
   ++c->launches;
   LA_CHECK_LAUNCH(c);
-  return sweep_level<R>(c, l, k.nu2);
+  return sweep_level<R>(c, l, nu2);
 }
 
 // N of the current FP64 iterate into h_N[slot] (stores r~ = f~ - M~ c in d_r); enqueue only.

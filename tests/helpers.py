@@ -58,7 +58,7 @@ def oracle_trial_propagation(w, psi0, nsteps, trial, ncycles, t0=0.0):
     """nsteps steps of exactly ncycles V-cycles each (oracle), every step started from the
     extrapolated trial (or c = 0 where the trial's action is not below N(0))."""
     from oracle import multigrid, system
-    from oracle.propagate import numpy_coarse_sub, numpy_sub
+    from oracle.propagate import numpy_coarse_nu, numpy_coarse_sub, numpy_sub
     prob = system.Problem.from_workload(w)
     psi = psi0.astype(np.complex128).copy()
     hist = []
@@ -71,7 +71,8 @@ def oracle_trial_propagation(w, psi0, nsteps, trial, ncycles, t0=0.0):
             if system.action_norm(system.residual(M, f, cand), W) < system.action_norm(f, W):
                 c0 = cand
         c, _, _, _ = multigrid.solve_step(M, f, W, prob.shape, prob.K, numpy_sub(w), w.levels, w.nu1, w.nu2,
-                                          w.coarse_sweeps, ncycles=ncycles, c0=c0, coarse_sub=numpy_coarse_sub(w))
+                                          w.coarse_sweeps, ncycles=ncycles, c0=c0, coarse_sub=numpy_coarse_sub(w),
+                                          coarse_nu=numpy_coarse_nu(w))
         hist.append(c)
         psi = system.advance(psi, c, prob.K)
     return psi

@@ -15,7 +15,7 @@ import numpy as np
 import pytest
 
 from oracle import multigrid, relax, system
-from oracle.propagate import numpy_coarse_sub, numpy_sub
+from oracle.propagate import numpy_coarse_nu, numpy_coarse_sub, numpy_sub
 from paper_1111_4363_gb300 import workloads as wl
 from tests.helpers import gpu_context, oracle_trial_propagation, rel_l2
 
@@ -95,10 +95,10 @@ def test_2d_first_vcycle(w2d, sys2d):
     ctx = gpu_context(w2d)
     c_ref, hist, _, _ = multigrid.solve_step(M, f, W, prob.shape, prob.K, numpy_sub(w2d), w2d.levels, w2d.nu1,
                                              w2d.nu2, w2d.coarse_sweeps, ncycles=1,
-                                             coarse_sub=numpy_coarse_sub(w2d))
+                                             coarse_sub=numpy_coarse_sub(w2d), coarse_nu=numpy_coarse_nu(w2d))
     c = np.zeros(M.shape[1], dtype=np.complex128)
     st, (cycles, sweeps, N, rel) = ctx.solve_step(psi0, T0, c, ncycles=1)
-    assert (cycles, sweeps) == (1, w2d.nu1 + w2d.nu2)
+    assert (cycles, sweeps) == (1, w2d.nu1 + w2d.nu2) and w2d.coarse_nu is not None
     assert rel_l2(c, c_ref) < 1e-11
     assert N == pytest.approx(hist[-1], rel=1e-9)
 

@@ -1,9 +1,11 @@
 """CUDA path vs the CPU oracle, element by element, through the C ABI (GB300 required)."""
+import dataclasses
+
 import numpy as np
 import pytest
 
 from oracle import multigrid, relax, system, timebasis as tb
-from oracle.propagate import numpy_coarse_sub, numpy_sub
+from oracle.propagate import numpy_coarse_nu, numpy_coarse_sub, numpy_sub
 from paper_1111_4363_gb300 import workloads as wl
 from tests.helpers import gpu_context, oracle_system, ragged_2d, rel_l2, small_3d, to_dev, variant
 
@@ -87,17 +89,21 @@ def test_single_colour_pass(name):
         assert rel_l2(got, ref) < TOL64
 
 
-@pytest.mark.parametrize("name,ncycles", [("1d", 3), ("2d", 2), ("2d_ragged", 2), ("3d", 2)])
-def test_fixed_schedule_iterates(name, ncycles):
+@pytest.mark.parametrize("name,ncycles,coarse_nu", [("1d", 3, None), ("2d", 2, None), ("2d_ragged", 2, None),
+                                                  ("3d", 2, None), ("2d", 2, (1, 0)), ("3d", 2, (0, 1))])
+def test_fixed_schedule_iterates(name, ncycles, coarse_nu):
     """ncycles V-cycles (or sweeps) from c = 0 with the identical schedule: same iterate."""
     w = WORKLOADS[name]()
+    if coarse_nu is not None:   # a middle Galerkin level is needed: three levels
+        w = dataclasses.replace(w, nu2=2, levels=3, coarse_nu=coarse_nu,
+                                n=(8, 8, 8) if w.dim == 3 else w.n)
     ctx = gpu_context(w)
     psi0 = wl.initial_state(w).ravel()
     t0 = 0.1
     prob, M, f, W = oracle_system(w, psi0, t0)
     c_ref, hist, cyc, _ = multigrid.solve_step(M, f, W, prob.shape, prob.K, numpy_sub(w), w.levels, w.nu1, w.nu2,
                                                w.coarse_sweeps, ncycles=ncycles,
-                                               coarse_sub=numpy_coarse_sub(w))
+                                               coarse_sub=numpy_coarse_sub(w), coarse_nu=numpy_coarse_nu(w))
     c = np.zeros(M.shape[1], dtype=np.complex128)
     st, (cycles, sweeps, N, rel) = ctx.solve_step(psi0, t0, c, ncycles=ncycles)
     assert cycles == ncycles

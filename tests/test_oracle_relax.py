@@ -158,6 +158,21 @@ def test_2d_vcycle_converges_to_direct_solution():
     assert cyc <= 15
 
 
+def test_lighter_galerkin_cycle_converges_to_direct_solution():
+    """V(1,2) on the finest level with a (1,0) cycle on the Galerkin levels: the same minimiser, and
+    coarse_nu equal to (nu1, nu2) reproduces the uniform cycle exactly."""
+    w, prob, M, f, W = small_2d(n=32, levels=3)
+    cd = system.direct_solve(M, f)
+    c, hist, cyc, _ = multigrid.solve_step(M, f, W, prob.shape, prob.K, (4, 4), 3, 1, 2, 1, tol=1e-24,
+                                           max_cycles=60, coarse_sub=(2, 2), coarse_nu=(1, 0))
+    assert hist[-1] <= 1e-24 * hist[0]
+    assert np.linalg.norm(c - cd) < 1e-9 * np.linalg.norm(cd)
+    a, _, _, _ = multigrid.solve_step(M, f, W, prob.shape, prob.K, (4, 4), 3, 1, 2, 1, ncycles=2, coarse_sub=(2, 2))
+    b, _, _, _ = multigrid.solve_step(M, f, W, prob.shape, prob.K, (4, 4), 3, 1, 2, 1, ncycles=2, coarse_sub=(2, 2),
+                                      coarse_nu=(1, 2))
+    assert np.array_equal(a, b)
+
+
 def test_coarse_correction_is_galerkin_optimal():
     """With an exact coarse solve, c + I e_c minimises N over the coarse space (Eq. correction_fine)."""
     w, prob, M, f, W = small_2d(n=16, levels=2)
