@@ -49,6 +49,8 @@ L2_BYTES = 129 * 2 ** 20
 # pre-sweep on the Galerkin levels, started from the quadratic trial (2 cycles per step to 1e-10,
 # against 5 for V(1,1) from c = 0); --trial 0 gives the plain start
 PRODUCTION_2D = dict(nu1=1, nu2=2, coarse_nu=(1, 0), trial=3)
+# the same shape for the 3D workload (4 levels): 2 cycles per step instead of 3 for V(1,1)
+PRODUCTION_3D = dict(nu1=1, nu2=2, coarse_nu=(1, 0), trial=3)
 
 
 def workload(name: str) -> wl.Workload:
@@ -428,8 +430,9 @@ def run_3d_adjoint(args):
     __graft_entry__.build()
     from paper_1111_4363_gb300 import binding as B
     n = args.n3d
-    w = wl.hydrogen_3d(n=n, nsteps=args.steps)
-    w = dataclasses.replace(w, trial=3 if args.trial < 0 else args.trial)
+    w = dataclasses.replace(wl.hydrogen_3d(n=n, nsteps=args.steps), **PRODUCTION_3D)
+    if args.trial >= 0:
+        w = dataclasses.replace(w, trial=args.trial)
     cfg = B.config_from_workload(w, precision=args.precision, ckpt_every=20)
     ctx = B.Context(cfg)
     V0 = torch.tensor(wl.potential(w).ravel(), dtype=torch.float64, device="cuda")

@@ -134,11 +134,11 @@ def test_2d_steps_with_the_trial(w2d):
     assert rel_l2(psi, ref) < 1e-11
 
 
-def test_3d_residual_at_sampled_points():
-    w = wl.hydrogen_3d(n=128, nsteps=20)
+def test_3d_residual_at_sampled_points(bench):
+    w = dataclasses.replace(wl.hydrogen_3d(n=128, nsteps=20), **bench.PRODUCTION_3D)
     prob = system.Problem.from_workload(w)
     psi0 = wl.initial_state(w).ravel()
-    ctx = gpu_context(dataclasses.replace(w, trial=3))
+    ctx = gpu_context(w)
     c = wl.random_state(w.nunknowns, 9) * 0.05
     r = np.zeros_like(c)
     ctx.residual(psi0, T0, c, r)
@@ -151,10 +151,10 @@ def test_3d_residual_at_sampled_points():
     np.testing.assert_allclose(got, ref, rtol=0, atol=1e-13 * np.max(np.abs(ref)))
 
 
-def test_3d_adjoint_gradient_against_central_differences():
+def test_3d_adjoint_gradient_against_central_differences(bench):
     """128^3 with a 32-component pulse, mixed precision local solves, checkpoints every 2 steps."""
     nsteps = 3
-    w = dataclasses.replace(wl.hydrogen_3d(n=128, nsteps=nsteps), trial=3)
+    w = dataclasses.replace(wl.hydrogen_3d(n=128, nsteps=nsteps), **bench.PRODUCTION_3D)
     prob = system.Problem.from_workload(w)
     psi0 = wl.initial_state(w).ravel()
 
