@@ -143,7 +143,8 @@ la_status la_action(la_ctx* ctx, double* action, double* rel_action);
    the pulse amplitudes; dJ_dpsi0 (complex128[Np], host or device, nullable): dJ/dpsi_0^*.
    Per step, backwards (segments of ckpt_every steps are recomputed from their checkpoint):
    mu = M^{-dagger} B^T lambda is obtained by relaxing G z = B^T lambda with the step's factors
-   (G = M^dagger W M is Hermitian, so the adjoint is a second relaxation), mu = W M z;
+   (G = M^dagger W M is Hermitian, so the adjoint is a second relaxation; with cfg.trial > 0 it starts
+   from the extrapolation of the preceding backward steps' z when that has the smaller residual), mu = W M z;
    dJ/da_j += 2 Re mu^dagger (dF/da_j psi_k - dM/da_j c_k); lambda += F_k^T mu (Sec. I, stationarity
    and the initial-condition multipliers define M and F).  Errors: LA_ESTATE, LA_EINVAL, LA_ECUDA. */
 la_status la_backward(la_ctx* ctx, const void* dJ_dpsiT, double* grad_amp, void* dJ_dpsi0);

@@ -63,6 +63,9 @@ struct la_ctx {
   double2* d_hist[3] = {};
   int nhist = 0, hist_head = 0;     // valid vectors; slot of the next push
   double hist_t_next = 0.0;         // start time of the step the history continues into
+  // converged adjoint solutions z of the last backward steps (trial of the adjoint relaxation)
+  double2* d_ahist[3] = {};
+  int nahist = 0, ahist_head = 0;
   std::vector<void*> allocs;
   // profiling
   bool prof = false;
@@ -956,6 +959,9 @@ extern "C" la_status la_step(la_ctx* c, void* psi, int nsteps, double t0, la_ste
 
 // Relax G~ z = y~ (y~ in d_y) from z = 0 into d_c with the step's factors; on return d_z holds
 // Wt (0 - M~ z) = -mu of the final z.  Stops when |y~ - G~ z|^2 <= tol |y~|^2 or at max_cycles.
+// Relaxes from z = 0 or, with cfg.trial > 0 and an adjoint history, from the extrapolation of the
+// last converged adjoint solutions (in the backward step order) when that trial's residual is
+// below the one of z = 0; the stopping test stays relative to |y~|^2.
 static la_status adjoint_solve(la_ctx* c, int* cycles) {
   const la_config& k = c->cfg;
   const long long n = c->nunk0;
@@ -976,6 +982,23 @@ static la_status adjoint_solve(la_ctx* c, int* cycles) {
   double N0 = 0.0, N = 0.0;
   LA_TRY(rho_norm(&N0));
   N = N0;
+  const int T = k.trial;
+  if (T > 0 && c->nahist > 0) {
+    const int q = c->nahist;
+    const double2* h[3] = {nullptr, nullptr, nullptr};
+    for (int j = 0; j < q; ++j) h[j] = c->d_ahist[((c->ahist_head - 1 - j) % T + T) % T];
+    launch_trial(n, kTrialW[q - 1], h[0], h[1], h[2], c->d_c, c->stream);
+    ++c->launches;
+    LA_CHECK_LAUNCH(c);
+    double Nt = 0.0;
+    LA_TRY(rho_norm(&Nt));
+    if (Nt < N0) {
+      N = Nt;
+    } else {
+      LA_CUDA(c, cudaMemsetAsync(c->d_c, 0, sizeof(double2) * (size_t)n, c->stream));
+      LA_TRY(rho_norm(&N));
+    }
+  }
   int cyc = 0;
   while (cyc < k.max_cycles && N > k.tol * N0) {
     c->adj = true;
@@ -998,6 +1021,12 @@ static la_status adjoint_solve(la_ctx* c, int* cycles) {
     LA_TRY(rho_norm(&N));
   }
   if (cycles) *cycles = cyc;
+  if (T > 0) {   // history of converged adjoint solutions
+    LA_CUDA(c, cudaMemcpyAsync(c->d_ahist[c->ahist_head], c->d_c, sizeof(double2) * (size_t)n, cudaMemcpyDeviceToDevice,
+                               c->stream));
+    c->ahist_head = (c->ahist_head + 1) % T;
+    c->nahist = std::min(c->nahist + 1, T);
+  }
   return LA_OK;
 }
 
@@ -1020,6 +1049,13 @@ extern "C" la_status la_backward(la_ctx* c, const void* dJ_dpsiT, double* grad_a
     }
     c->seg_cap = C;
   }
+  for (int j = 0; j < c->cfg.trial; ++j)
+    if (!c->d_ahist[j]) {
+      void* p = nullptr;
+      LA_TRY(dalloc(c, &p, cb));
+      c->d_ahist[j] = (double2*)p;
+    }
+  c->nahist = 0;
   LA_TRY(load_any(c, c->d_lam, dJ_dpsiT, vb));
   LA_CUDA(c, cudaMemsetAsync(c->d_grad, 0, sizeof(double) * LA_NCOMP_MAX, c->stream));
   const int nseg = (nsteps + C - 1) / C;
