@@ -81,6 +81,10 @@ typedef struct {
   int coarse_cycle;     /* 0: V(nu1, nu2) on every level but the coarsest; 1: V(coarse_nu1, coarse_nu2) on
                            the Galerkin levels above the coarsest (the finest keeps nu1, nu2) */
   int coarse_nu1, coarse_nu2;
+  int cache_factors;    /* nonzero: la_backward keeps the subvolume factors of a recomputed segment
+                           (ckpt_every steps x all levels) in device memory and reuses them for the
+                           adjoint relaxation instead of factorising every step again; without the
+                           memory for it the factors are recomputed as usual */
 } la_config;
 
 /* Laser field E(t) = sum_k amp[k] * env_k(t) * sin(omega[k] t), env_k = exp(-((t - t_center[k])/sigma[k])^2)

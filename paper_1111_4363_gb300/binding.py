@@ -36,7 +36,7 @@ class la_config(C.Structure):
                 ("coarse_sweeps", C.c_int), ("max_cycles", C.c_int), ("tol", C.c_double), ("weight", C.c_int),
                 ("precision", C.c_int), ("laser_axis", C.c_int), ("ckpt_every", C.c_int),
                 ("coarse_sub", C.c_int * 3), ("trial", C.c_int), ("coarse_cycle", C.c_int),
-                ("coarse_nu1", C.c_int), ("coarse_nu2", C.c_int)]
+                ("coarse_nu1", C.c_int), ("coarse_nu2", C.c_int), ("cache_factors", C.c_int)]
 
 
 class la_pulse(C.Structure):

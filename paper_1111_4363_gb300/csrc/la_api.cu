@@ -63,6 +63,10 @@ struct la_ctx {
   double2* d_hist[3] = {};
   int nhist = 0, hist_head = 0;     // valid vectors; slot of the next push
   double hist_t_next = 0.0;         // start time of the step the history continues into
+  // factors of the steps of the segment being back-propagated (cfg.cache_factors)
+  void* d_fcache = nullptr;
+  size_t fcache_step = 0;           // bytes of one step's factors (all levels)
+  int fcache_cap = 0;               // steps the cache holds
   // converged adjoint solutions z of the last backward steps (trial of the adjoint relaxation)
   double2* d_ahist[3] = {};
   int nahist = 0, ahist_head = 0;
@@ -1056,6 +1060,39 @@ extern "C" la_status la_backward(la_ctx* c, const void* dJ_dpsiT, double* grad_a
       c->d_ahist[j] = (double2*)p;
     }
   c->nahist = 0;
+  // factor cache for one segment (cfg.cache_factors); allocation failure only disables it
+  size_t lvl_bytes[LA_MAX_LEVELS] = {};
+  bool cache = false;
+  if (c->cfg.cache_factors) {
+    size_t step = 0;
+    for (int l = 0; l < c->L; ++l) {
+      lvl_bytes[l] = csize(c) * (size_t)c->geo[l].nsub * c->geo[l].fsize;
+      step += lvl_bytes[l];
+    }
+    if (c->fcache_cap < C || c->fcache_step != step) {
+      if (c->d_fcache) {
+        cudaFree(c->d_fcache);
+        c->allocs.erase(std::remove(c->allocs.begin(), c->allocs.end(), c->d_fcache), c->allocs.end());
+        c->d_fcache = nullptr;
+        c->fcache_cap = 0;
+      }
+      void* p = nullptr;
+      if (cudaMalloc(&p, step * (size_t)C) == cudaSuccess) {
+        c->allocs.push_back(p);
+        c->d_fcache = p;
+        c->fcache_cap = C;
+        c->fcache_step = step;
+      } else {
+        cudaGetLastError();
+      }
+    }
+    cache = c->d_fcache != nullptr;
+  }
+  auto cache_slot = [&](int j, int l) -> unsigned char* {
+    size_t off = c->fcache_step * (size_t)j;
+    for (int m = 0; m < l; ++m) off += lvl_bytes[m];
+    return static_cast<unsigned char*>(c->d_fcache) + off;
+  };
   LA_TRY(load_any(c, c->d_lam, dJ_dpsiT, vb));
   LA_CUDA(c, cudaMemsetAsync(c->d_grad, 0, sizeof(double) * LA_NCOMP_MAX, c->stream));
   const int nseg = (nsteps + C - 1) / C;
@@ -1072,6 +1109,10 @@ extern "C" la_status la_backward(la_ctx* c, const void* dJ_dpsiT, double* grad_a
       if (st != LA_OK && st != LA_ENOTCONV) return st;
       LA_CUDA(c, cudaMemcpyAsync(c->d_seg_c + (size_t)(kk - k0) * c->nunk0, c->d_c, cb, cudaMemcpyDeviceToDevice,
                                  c->stream));
+      if (cache)
+        for (int l = 0; l < c->L; ++l)
+          LA_CUDA(c, cudaMemcpyAsync(cache_slot(kk - k0, l), c->d_fac[l], lvl_bytes[l], cudaMemcpyDeviceToDevice,
+                                     c->stream));
       launch_advance(c->np0, c->d_tm, c->d_c, c->d_psi, c->stream);
       ++c->launches;
       LA_TRY(hist_push(c));
@@ -1082,11 +1123,22 @@ extern "C" la_status la_backward(la_ctx* c, const void* dJ_dpsiT, double* grad_a
       LA_CUDA(c, cudaMemcpyAsync(c->d_psi, c->d_seg_psi + (size_t)(kk - k0) * c->np0, vb, cudaMemcpyDeviceToDevice,
                                  c->stream));
       LA_TRY(setup_step(c, tk));
-      if (c->cfg.precision == 0) LA_TRY(factor_all<double>(c));
-      else LA_TRY(factor_all<float>(c));
+      void* own[LA_MAX_LEVELS] = {};
+      if (cache) {
+        // the adjoint V-cycles are launched directly (no captured graph), so they can read the
+        // cached factors in place
+        for (int l = 0; l < c->L; ++l) { own[l] = c->d_fac[l]; c->d_fac[l] = cache_slot(kk - k0, l); }
+      } else if (c->cfg.precision == 0) {
+        LA_TRY(factor_all<double>(c));
+      } else {
+        LA_TRY(factor_all<float>(c));
+      }
       launch_bt_lambda(c->np0, c->d_tm, 1.0 / c->hd, c->d_lam, c->d_y, c->stream);
       ++c->launches;
-      LA_TRY(adjoint_solve(c, nullptr));
+      const la_status ast = adjoint_solve(c, nullptr);
+      if (cache)
+        for (int l = 0; l < c->L; ++l) c->d_fac[l] = own[l];
+      LA_TRY(ast);
       launch_grad_contract(c->fine, c->d_tm, K, tk, c->hd, c->d_z, c->d_psi, c->d_seg_c + (size_t)(kk - k0) * c->nunk0,
                            c->d_gpart, c->d_grad, c->stream);
       launch_lambda_update(c->fine, c->d_tm, c->hd, c->d_z, c->d_lam, c->stream);

@@ -110,3 +110,22 @@ def test_autograd_function_gradients():
     g_ref, lam_ref = adjoint.gradients(prob, psi0_np, nsteps)
     assert rel_l2(amp.grad.numpy(), g_ref) < 1e-8
     assert rel_l2(psi0.grad.cpu().numpy(), 2 * lam_ref) < 1e-8
+
+
+@pytest.mark.parametrize("kind,precision", [("2d", 0), ("3d", 1)])
+def test_factor_cache_gives_identical_gradients(kind, precision):
+    """cache_factors reuses the recomputed segment's factors in the adjoint relaxation: same numbers."""
+    w = dataclasses.replace(pulsed(kind), trial=3)
+    nsteps, ckpt = 5, 2
+    psi0 = wl.initial_state(w).ravel()
+    prob = system.Problem.from_workload(w)
+    out = []
+    for cache in (0, 1):
+        ctx = gpu_context(w, precision=precision, ckpt_every=ckpt, cache_factors=cache)
+        psi = psi0.copy()
+        ctx.step(psi, nsteps, 0.0)
+        _, dJ = adjoint.dipole_objective(prob, psi)
+        dpsi0 = np.zeros_like(psi0)
+        out.append((ctx.backward(dJ, w.pulse.ncomp, dpsi0), dpsi0))
+    assert np.array_equal(out[0][0], out[1][0])
+    assert np.array_equal(out[0][1], out[1][1])
