@@ -315,12 +315,17 @@ def oracle_cycle_rate(w: wl.Workload, budget_s: float):
     return setup_s, cyc_s, ncyc
 
 
+# The oracle is plain NumPy/SciPy: sparse products and 96 x 96 dense Cholesky solves, which run on one
+# thread (limiting BLAS to one thread does not change its time), so it uses one core of the host.
+ORACLE_THREADS = 1
+
+
 def cpu_baseline(w: wl.Workload):
-    cores = len(os.sched_getaffinity(0))
     setup_s, cyc_s, ncyc = oracle_cycle_rate(w, 8.0)
     sweeps = w.nu1 + w.nu2 if w.levels > 1 else w.nu1 + w.nu2
     value = w.nunknowns * sweeps / cyc_s
-    return {"value": value, "unit": "unknowns/s", "cores": cores, "kind": "oracle",
+    return {"value": value, "unit": "unknowns/s", "cores": ORACLE_THREADS, "kind": "oracle",
+            "host_cores": len(os.sched_getaffinity(0)),
             "sample": f"one time step of {w.name}: setup (assembly, Galerkin levels, {w.name} block Cholesky) "
                       f"{setup_s:.1f} s excluded, then {ncyc} V-cycles timed ({cyc_s:.2f} s each)",
             "setup_s": setup_s, "cycle_s": cyc_s}
@@ -331,7 +336,7 @@ def run_reference(args):
     if rank != 0:
         return
     w = workload(args.workload)
-    cores = len(os.sched_getaffinity(0))
+    cores = ORACLE_THREADS
     # each step = one oracle V-cycle on the full workload after an untimed setup; bounded to a few minutes
     from oracle import multigrid, system
     from oracle.propagate import numpy_coarse_nu, numpy_coarse_sub, numpy_sub
