@@ -1,0 +1,109 @@
+"""Edge and degenerate cases of the CUDA path against the oracle (GB300 required): every size class
+of the time basis (K = 1, 2, 5, 8, including the largest subvolume of 128 unknowns), odd K in mixed
+precision (per-point complex64 kernels instead of the TMA-staged ones), a grid that is one
+subvolume, no laser field, a ragged 3D grid, zero steps and a zero initial state."""
+import dataclasses
+
+import numpy as np
+import pytest
+
+from oracle import multigrid, system
+from oracle.propagate import numpy_coarse_nu, numpy_coarse_sub, numpy_sub
+from paper_1111_4363_gb300 import workloads as wl
+from tests.helpers import gpu_context, oracle_system, rel_l2, small_3d
+
+pytestmark = pytest.mark.gpu
+TOL64 = 1e-11
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+
+
+def fixed_cycles(w, ncycles, t0=0.2):
+    """ncycles cycles from c = 0 on the GPU and in the oracle with the identical schedule."""
+    psi0 = wl.initial_state(w).ravel()
+    prob, M, f, W = oracle_system(w, psi0, t0)
+    c_ref, hist, _, _ = multigrid.solve_step(M, f, W, prob.shape, prob.K, numpy_sub(w), w.levels, w.nu1, w.nu2,
+                                             w.coarse_sweeps, ncycles=ncycles, coarse_sub=numpy_coarse_sub(w),
+                                             coarse_nu=numpy_coarse_nu(w))
+    ctx = gpu_context(w)
+    c = np.zeros(M.shape[1], dtype=np.complex128)
+    st, (cycles, sweeps, N, rel) = ctx.solve_step(psi0, t0, c, ncycles=ncycles)
+    return c, c_ref, N, hist[-1]
+
+
+@pytest.mark.parametrize("K", [1, 2, 5, 8])
+def test_every_time_basis_size(K):
+    """4x4 subvolumes with K time functions: 16 (K=1) to 128 (K=8) unknowns per subvolume."""
+    w = dataclasses.replace(wl.softcore_2d(n=16, levels=2), nt=K)
+    c, c_ref, N, N_ref = fixed_cycles(w, 2)
+    assert rel_l2(c, c_ref) < TOL64
+    assert N == pytest.approx(N_ref, rel=1e-9)
+
+
+def test_largest_subvolume():
+    """8x4 points x 4 time functions = 128 unknowns, the largest one-CTA factorisation."""
+    w = dataclasses.replace(wl.softcore_2d(n=32, levels=2), nt=4, sub=(8, 4, 1))
+    c, c_ref, _, _ = fixed_cycles(w, 2)
+    assert rel_l2(c, c_ref) < TOL64
+
+
+@pytest.mark.parametrize("K", [3, 5])
+def test_mixed_precision_with_odd_K(K):
+    """Odd K has no tensor map (16-byte TMA rule), so the complex64 V-cycle takes the per-point
+    kernels; refined to 1e-22 it reaches the FP64 direct solution."""
+    w = dataclasses.replace(wl.softcore_2d(n=16, levels=2), nt=K)
+    psi0 = wl.initial_state(w).ravel()
+    prob, M, f, W = oracle_system(w, psi0, 0.0)
+    cd = system.direct_solve(M, f)
+    ctx = gpu_context(w, precision=1, tol=1e-22, max_cycles=80)
+    c = np.zeros(M.shape[1], dtype=np.complex128)
+    st, (cycles, sweeps, N, rel) = ctx.solve_step(psi0, 0.0, c)
+    assert rel <= 1e-22
+    assert rel_l2(c, cd) < 1e-9
+
+
+def test_grid_of_one_subvolume():
+    """4x4 grid, 4x4 subvolume, one level: only colour 0 has a subvolume."""
+    w = dataclasses.replace(wl.softcore_2d(n=16, levels=1), n=(4, 4, 1))
+    c, c_ref, _, _ = fixed_cycles(w, 3)
+    assert rel_l2(c, c_ref) < TOL64
+
+
+def test_no_laser_field():
+    w = dataclasses.replace(wl.softcore_2d(n=16, levels=2), pulse=None)
+    c, c_ref, _, _ = fixed_cycles(w, 2)
+    assert rel_l2(c, c_ref) < TOL64
+
+
+def test_ragged_3d_grid():
+    """10x6x7 points with 4x2x2 subvolumes: tails of 2 and 1 points, one level."""
+    w = dataclasses.replace(small_3d(levels=1), n=(10, 6, 7), sub=(4, 2, 2))
+    c, c_ref, _, _ = fixed_cycles(w, 2)
+    assert rel_l2(c, c_ref) < TOL64
+
+
+def test_zero_steps_leave_the_state_unchanged():
+    w = wl.softcore_2d(n=16, levels=2)
+    ctx = gpu_context(w)
+    psi0 = wl.initial_state(w).ravel()
+    psi = psi0.copy()
+    ctx.step(psi, 0, 0.0)
+    assert np.array_equal(psi, psi0)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_zero_initial_state_stays_zero(precision):
+    """psi0 = 0: f = 0, N(0) = 0, no cycle runs and the state stays exactly zero."""
+    w = dataclasses.replace(wl.softcore_2d(n=16, levels=2), trial=3)
+    ctx = gpu_context(w, precision=precision)
+    psi = np.zeros(w.npoints, dtype=np.complex128)
+    st, stats = ctx.step(psi, 3, 0.0, stats=True)
+    assert np.count_nonzero(psi) == 0
+    assert all(s[0] == 0 and s[3] == 0.0 for s in stats)
