@@ -544,8 +544,9 @@ k_sweep_fine(LevelGeom L, FineOp g, const TimeMats* __restrict__ tm, const typen
   R* sU = sQ + LA_KMAX * LA_KMAX;
   R* sW = sU + LA_KMAX * LA_KMAX;
   R* sE = sW + LA_KMAX * LA_KMAX;
-  R* sV = sE + LA_KMAX * LA_KMAX;                     // V0 on the footprint box [nbc_max]
-  CT* sC = reinterpret_cast<CT*>(sV + ((nbc_max + 3) & ~3));  // c on U+2  [nbc_max * K]
+  R* sV = sE + LA_KMAX * LA_KMAX;                     // dsum + V0 on the footprint box [nbc_max]
+  R* sX = sV + ((nbc_max + 3) & ~3);                  // laser coordinate on the footprint box [nbc_max]
+  CT* sC = reinterpret_cast<CT*>(sX + ((nbc_max + 3) & ~3));  // c on U+2  [nbc_max * K]
   CT* sA = sC + (size_t)nbc_max * K;                  // Hc, then z   [nbc_max * K]
   CT* sB = sA + (size_t)nbc_max * K;                  // r, then Hz   [nbc_max * K]
   CT* sRhs = sB + (size_t)nbc_max * K;                // [NPAD]
@@ -565,11 +566,18 @@ k_sweep_fine(LevelGeom L, FineOp g, const TimeMats* __restrict__ tm, const typen
     if (fine_in(g, gx, gy, gz)) v = c[(size_t)((gz * g.n[1] + gy) * g.n[0] + gx) * K + m];
     sC[t] = v;
   }
-  for (int i = tid; i < nbf; i += kSweepThreads) {
-    int lx, ly, lz;
-    local_coords(i, ef, lx, ly, lz);
-    const int gx = of_[0] + lx, gy = of_[1] + ly, gz = of_[2] + lz;
-    sV[i] = fine_in(g, gx, gy, gz) ? (R)(g.dsum + g.V0[(gz * g.n[1] + gy) * g.n[0] + gx]) : (R)0;
+  {
+    // per footprint point, in the kernel's own precision (a complex64 sweep issues no FP64 work here)
+    const R dsum = (R)g.dsum;
+    const R xo = (R)(g.lax == 0 ? g.x0[0] : (g.lax == 1 ? g.x0[1] : g.x0[2]));
+    const R xh = (R)(g.lax == 0 ? g.h[0] : (g.lax == 1 ? g.h[1] : g.h[2]));
+    for (int i = tid; i < nbf; i += kSweepThreads) {
+      int lx, ly, lz;
+      local_coords(i, ef, lx, ly, lz);
+      const int gx = of_[0] + lx, gy = of_[1] + ly, gz = of_[2] + lz;
+      sV[i] = fine_in(g, gx, gy, gz) ? dsum + (R)g.V0[(gz * g.n[1] + gy) * g.n[0] + gx] : (R)0;
+      sX[i] = xo + (R)(g.lax == 0 ? gx : (g.lax == 1 ? gy : gz)) * xh;
+    }
   }
   __syncthreads();
   // c-box index of footprint point (lx, ly, lz): (lx+1, ly+1, lz+1) on used axes
@@ -609,7 +617,7 @@ k_sweep_fine(LevelGeom L, FineOp g, const TimeMats* __restrict__ tm, const typen
     if (fine_in(g, gx, gy, gz)) {
       const int cx = L.dim > 0 ? lx + 1 : lx, cy = L.dim > 1 ? ly + 1 : ly, cz = L.dim > 2 ? lz + 1 : lz;
       const int ci = (cz * ec[1] + cy) * ec[0] + cx;
-      const R xl = (R)fine_x(g, gx, gy, gz);
+      const R xl = sX[i];
       R qr = 0, qi = 0, ur = 0, ui = 0, er = 0, ei = 0;
       for (int nn = 0; nn < K; ++nn) {
         const CT cv = sC[ci * K + nn], hv = sA[i * K + nn];
@@ -671,7 +679,7 @@ k_sweep_fine(LevelGeom L, FineOp g, const TimeMats* __restrict__ tm, const typen
       local_coords(i, e, lx, ly, lz);
       const int fx = L.dim > 0 ? lx + 1 : lx, fy = L.dim > 1 ? ly + 1 : ly, fz = L.dim > 2 ? lz + 1 : lz;
       const int fi = (fz * ef[1] + fy) * ef[0] + fx;
-      const R xl = (R)fine_x(g, o[0] + lx, o[1] + ly, o[2] + lz);
+      const R xl = sX[fi];
       R qr = 0, qi = 0, ur = 0, ui = 0, er = 0, ei = 0;
       for (int nn = 0; nn < K; ++nn) {
         const CT zv = sA[fi * K + nn], hv = sB[i * K + nn];
@@ -886,7 +894,7 @@ inline size_t factor_smem(const LevelGeom& L, int nptsmax, size_t csize, bool fi
 inline size_t sweep_fine_smem(const LevelGeom& L, int K, size_t rsize, size_t csize) {
   const int sx = L.sub[0] + 4, sy = L.dim > 1 ? L.sub[1] + 4 : 1, sz = L.dim > 2 ? L.sub[2] + 4 : 1;
   const size_t nbc = (size_t)sx * sy * sz;
-  return rsize * (4 * LA_KMAX * LA_KMAX + ((nbc + 3) & ~(size_t)3)) + csize * (3 * nbc * K + 2 * (size_t)L.npad + LA_BLK + 128);
+  return rsize * (4 * LA_KMAX * LA_KMAX + 2 * ((nbc + 3) & ~(size_t)3)) + csize * (3 * nbc * K + 2 * (size_t)L.npad + LA_BLK + 128);
 }
 inline size_t sweep_coarse_smem(const LevelGeom& L, int K, size_t rsize, size_t csize) {
   const size_t nptsmax = (size_t)L.sub[0] * L.sub[1] * L.sub[2];
