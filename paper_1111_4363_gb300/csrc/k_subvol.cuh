@@ -57,6 +57,11 @@ __device__ __forceinline__ void local_coords(int i, const int e[3], int& x, int&
 // (lookahead), so the pivot chain is off the critical path.
 __host__ __device__ constexpr int tri_index(int r, int c) { return r * (r + 1) / 2 + c; }
 
+// Small matrices leave most threads of a CTA idle in the later columns, so a CTA factorises
+// factor_mpc(NPAD) matrices together: each phase's work is split over the entries of all of them and
+// they share the two barriers per column.
+__host__ __device__ constexpr int factor_mpc(int npad) { return npad <= 32 ? 4 : (npad <= 64 ? 2 : 1); }
+
 template <typename R, int NPAD>
 __global__ void __launch_bounds__(kFactorThreads, 2)
 k_factor(LevelGeom L, FineOp g, int is_fine, int nptsmax, const double* __restrict__ sigma,
@@ -64,29 +69,49 @@ k_factor(LevelGeom L, FineOp g, int is_fine, int nptsmax, const double* __restri
   typedef typename C2<R>::T CT;
   constexpr int NTRI = NPAD * (NPAD + 1) / 2;
   constexpr int NB = NPAD / LA_BLK;
+  constexpr int MPC = factor_mpc(NPAD);
   extern __shared__ __align__(16) unsigned char smem[];
   const int K = tm->K, KK = K * K;
-  CT* sA = reinterpret_cast<CT*>(smem);                       // [NTRI] packed lower triangle
-  CT* sCol = sA + NTRI;                                       // [NPAD] scaled column j
-  R* sInv = reinterpret_cast<R*>(sCol + NPAD);                // [NPAD] 1/L_jj
-  double* sP = reinterpret_cast<double*>(sInv + NPAD);        // [9][K*K]
-  double* sPair = sP + LA_NPAIR * LA_KMAX * LA_KMAX;          // [npair][9], point pairs i >= j
   const int npair_max = nptsmax * (nptsmax + 1) / 2;
-  int* sMask = reinterpret_cast<int*>(sPair + (size_t)npair_max * LA_NPAIR);  // nonzero factors of a pair
+  CT* sA = reinterpret_cast<CT*>(smem);                       // [MPC][NTRI] packed lower triangles
+  CT* sCol = sA + MPC * NTRI;                                 // [MPC][NPAD] scaled column j
+  R* sInv = reinterpret_cast<R*>(sCol + MPC * NPAD);          // [MPC][NPAD] 1/L_jj
+  double* sP = reinterpret_cast<double*>(sInv + MPC * NPAD);  // [9][K*K]
+  double* sPair = sP + LA_NPAIR * LA_KMAX * LA_KMAX;          // [MPC][npair_max][9], point pairs i >= j
+  int* sMask = reinterpret_cast<int*>(sPair + (size_t)MPC * npair_max * LA_NPAIR);  // [MPC][npair_max]
 
   const int tid = threadIdx.x, ti = tid >> 4, tk = tid & 15;
-  const int b = blockIdx.x;
-  int o[3], e[3];
-  subvol_box(L, b, o, e);
-  const int npts = e[0] * e[1] * e[2];
-  const int n = npts * K;
+  // the CTA's matrices; slots past the last subvolume factorise an identity and store nothing
+  int bsv[MPC], nn_[MPC], npts_[MPC];
+  int o_[MPC][3], e_[MPC][3];
+#pragma unroll
+  for (int mi = 0; mi < MPC; ++mi) {
+    bsv[mi] = blockIdx.x * MPC + mi;
+    if (bsv[mi] < L.nsub) {
+      subvol_box(L, bsv[mi], o_[mi], e_[mi]);
+      npts_[mi] = e_[mi][0] * e_[mi][1] * e_[mi][2];
+    } else {
+      o_[mi][0] = o_[mi][1] = o_[mi][2] = 0;
+      e_[mi][0] = e_[mi][1] = e_[mi][2] = 1;
+      npts_[mi] = 0;
+    }
+    nn_[mi] = npts_[mi] * K;
+  }
 
   for (int i = tid; i < LA_NPAIR * KK; i += kFactorThreads) sP[i] = tm->P[i / KK][i % KK];
-  // pair table for point pairs i >= j: the nine spatial factors Sigma_kk'[p_i, p_j] and a bit mask
+  // pair tables for point pairs i >= j: the nine spatial factors Sigma_kk'[p_i, p_j] and a bit mask
   // of the nonzero ones (most pairs of a subvolume are too far apart for most factors)
   const int nbox = box5_count(L.dim);
-  const int npair = npts * (npts + 1) / 2;
-  for (int q = tid; q < npair; q += kFactorThreads) {
+  for (int t = tid; t < MPC * npair_max; t += kFactorThreads) {
+    const int mi = t / npair_max, q = t - mi * npair_max;
+    int npts = 0, o[3] = {0, 0, 0}, e[3] = {1, 1, 1};
+#pragma unroll
+    for (int u = 0; u < MPC; ++u)
+      if (u == mi) {
+        npts = npts_[u];
+        for (int a = 0; a < 3; ++a) { o[a] = o_[u][a]; e[a] = e_[u][a]; }
+      }
+    if (q >= npts * (npts + 1) / 2) continue;
     int i = (int)((sqrtf(8.0f * (float)q + 1.0f) - 1.0f) * 0.5f);
     while (i * (i + 1) / 2 > q) --i;
     while ((i + 1) * (i + 2) / 2 <= q) ++i;
@@ -107,18 +132,23 @@ k_factor(LevelGeom L, FineOp g, int is_fine, int nptsmax, const double* __restri
       for (int k = 0; k < LA_NPAIR; ++k) s9[k] = near ? sigma[sigma_offset(p, k, ofs, nbox)] : 0.0;
     }
     int mask = 0;
+    double* dst = sPair + ((size_t)mi * npair_max + q) * LA_NPAIR;
     for (int k = 0; k < LA_NPAIR; ++k) {
-      sPair[(size_t)q * LA_NPAIR + k] = s9[k];
+      dst[k] = s9[k];
       if (s9[k] != 0.0) mask |= 1 << k;
     }
-    sMask[q] = mask;
+    sMask[mi * npair_max + q] = mask;
   }
   // padding rows: identity
-  for (int t = tid; t < NTRI; t += kFactorThreads) {
-    int r = (int)((sqrtf(8.0f * (float)t + 1.0f) - 1.0f) * 0.5f);
-    while (r * (r + 1) / 2 > t) --r;
-    while ((r + 1) * (r + 2) / 2 <= t) ++r;
-    const int c = t - r * (r + 1) / 2;
+  for (int t = tid; t < MPC * NTRI; t += kFactorThreads) {
+    const int mi = t / NTRI, u = t - mi * NTRI;
+    int r = (int)((sqrtf(8.0f * (float)u + 1.0f) - 1.0f) * 0.5f);
+    while (r * (r + 1) / 2 > u) --r;
+    while ((r + 1) * (r + 2) / 2 <= u) ++r;
+    const int c = u - r * (r + 1) / 2;
+    int n = 0;
+#pragma unroll
+    for (int w = 0; w < MPC; ++w) if (w == mi) n = nn_[w];
     if (r >= n) sA[t] = mkc<CT>((R)(r == c ? 1 : 0), (R)0);
   }
   __syncthreads();
@@ -126,16 +156,21 @@ k_factor(LevelGeom L, FineOp g, int is_fine, int nptsmax, const double* __restri
   // ---- assemble pair-major: G_UU[(i,m),(j,n)] = sum_kk' Sigma_kk'[p_i, p_j] Theta_kk'[m, n].
   // Consecutive threads take the K*K entries of one point pair, so the skipped (zero) factors
   // are uniform across a warp except at pair boundaries.
-  for (int t = tid; t < npair * KK; t += kFactorThreads) {
-    const int q = t / KK, mn = t % KK, mm = mn / K, nn = mn % K;
+  for (int t = tid; t < MPC * npair_max * KK; t += kFactorThreads) {
+    const int mi = t / (npair_max * KK), tq = t - mi * npair_max * KK;
+    const int q = tq / KK, mn = tq % KK, mm = mn / K, nn = mn % K;
+    int npts = 0;
+#pragma unroll
+    for (int u = 0; u < MPC; ++u) if (u == mi) npts = npts_[u];
+    if (q >= npts * (npts + 1) / 2) continue;
     int i = (int)((sqrtf(8.0f * (float)q + 1.0f) - 1.0f) * 0.5f);
     while (i * (i + 1) / 2 > q) --i;
     while ((i + 1) * (i + 2) / 2 <= q) ++i;
     const int j = q - i * (i + 1) / 2;
     const int r = i * K + mm, c = j * K + nn;
     if (r < c) continue;
-    const int mask = sMask[q];
-    const double* pr = sPair + (size_t)q * LA_NPAIR;
+    const int mask = sMask[mi * npair_max + q];
+    const double* pr = sPair + ((size_t)mi * npair_max + q) * LA_NPAIR;
     double re = 0.0, im = 0.0;
 #pragma unroll
     for (int kk = 0; kk < LA_NPAIR; ++kk) {
@@ -144,45 +179,49 @@ k_factor(LevelGeom L, FineOp g, int is_fine, int nptsmax, const double* __restri
       const int ph = theta_phase(kk);
       if (ph == 0) re += v; else if (ph == 1) im += v; else im -= v;
     }
-    sA[tri_index(r, c)] = mkc<CT>((R)re, (R)im);
+    sA[mi * NTRI + tri_index(r, c)] = mkc<CT>((R)re, (R)im);
   }
   __syncthreads();
-  if (tid == 0) {
-    R d2 = sA[0].x;
+  if (tid < MPC) {
+    CT* A = sA + tid * NTRI;
+    R d2 = A[0].x;
     if (!(d2 > (R)0)) { atomicOr(status, 1); d2 = (R)1; }
     const R inv = rsqrt(d2);
-    sA[0] = mkc<CT>(d2 * inv, (R)0);
-    sInv[0] = inv;
+    A[0] = mkc<CT>(d2 * inv, (R)0);
+    sInv[tid * NPAD] = inv;
   }
   __syncthreads();
 
   // ---- right-looking Cholesky.  Work of each phase is spread linearly over exactly the active
-  // entries (consecutive threads take consecutive entries of a row), so every issued FP64
-  // instruction has all lanes busy except in the last warp of a phase.
+  // entries of all the CTA's matrices (consecutive threads take consecutive entries of a row), so
+  // every issued FP64 instruction has all lanes busy except in the last warp of a phase.
   for (int j = 0; j < NPAD; ++j) {
-    // (A) scale and publish column j: rows j+1 .. NPAD-1
+    // (A) scale and publish column j: rows j+1 .. NPAD-1 of every matrix
     {
-      const R inv = sInv[j];
-      for (int r = j + 1 + tid; r < NPAD; r += kFactorThreads) {
-        CT v = sA[tri_index(r, j)];
+      const int rows = NPAD - 1 - j;
+      for (int t = tid; t < MPC * rows; t += kFactorThreads) {
+        const int mi = t / rows, r = j + 1 + (t - mi * rows);
+        const R inv = sInv[mi * NPAD + j];
+        CT v = sA[mi * NTRI + tri_index(r, j)];
         v.x *= inv; v.y *= inv;
-        sA[tri_index(r, j)] = v;
-        sCol[r] = v;
+        sA[mi * NTRI + tri_index(r, j)] = v;
+        sCol[mi * NPAD + r] = v;
       }
     }
     __syncthreads();
-    // (B) trailing update of the entries (r, c), j < c <= r; entry e of the trailing triangle
-    // lies in row r = j + m with (m-1) m / 2 <= e < m (m+1) / 2.  e = 0 is the next pivot: its
-    // thread finishes it first and computes the reciprocal square root (lookahead).
+    // (B) trailing update of the entries (r, c), j < c <= r; entry e of a trailing triangle lies
+    // in row r = j + m with (m-1) m / 2 <= e < m (m+1) / 2.  e = 0 is the next pivot: its thread
+    // finishes it first and computes the reciprocal square root (lookahead).
     const int m1 = NPAD - 1 - j;
     const int T = m1 * (m1 + 1) / 2;
-    for (int e = tid; e < T; e += kFactorThreads) {
+    for (int t = tid; t < MPC * T; t += kFactorThreads) {
+      const int mi = t / T, e = t - mi * T;
       int m = (int)((1.0f + sqrtf(1.0f + 8.0f * (float)e)) * 0.5f);
       while ((m - 1) * m / 2 > e) --m;
       while (m * (m + 1) / 2 <= e) ++m;
       const int r = j + m, c = j + 1 + (e - (m - 1) * m / 2);
-      const CT xr = sCol[r], y = sCol[c];
-      CT a = sA[tri_index(r, c)];
+      const CT xr = sCol[mi * NPAD + r], y = sCol[mi * NPAD + c];
+      CT a = sA[mi * NTRI + tri_index(r, c)];
       a.x = fma(-xr.x, y.x, a.x); a.x = fma(-xr.y, y.y, a.x);
       a.y = fma(-xr.y, y.x, a.y); a.y = fma(xr.x, y.y, a.y);
       if (e == 0) {
@@ -190,38 +229,51 @@ k_factor(LevelGeom L, FineOp g, int is_fine, int nptsmax, const double* __restri
         if (!(d2 > (R)0)) { atomicOr(status, 1); d2 = (R)1; }
         const R inv = rsqrt(d2);
         a = mkc<CT>(d2 * inv, (R)0);
-        sInv[j + 1] = inv;
+        sInv[mi * NPAD + j + 1] = inv;
       }
-      sA[tri_index(r, c)] = a;
+      sA[mi * NTRI + tri_index(r, c)] = a;
     }
     __syncthreads();
   }
 
   // ---- store: off-diagonal blocks as they are, diagonal blocks inverted
-  CT* F = factors + (size_t)b * L.fsize;
 #pragma unroll
-  for (int I = 1; I < NB; ++I)
+  for (int mi = 0; mi < MPC; ++mi) {
+    if (bsv[mi] >= L.nsub) continue;
+    CT* F = factors + (size_t)bsv[mi] * L.fsize;
+    const CT* A = sA + mi * NTRI;
 #pragma unroll
-    for (int J = 0; J < I; ++J)
-      F[(size_t)(I * (I + 1) / 2 + J) * 256 + ti * LA_BLK + tk] = sA[tri_index(LA_BLK * I + ti, LA_BLK * J + tk)];
-  // inv(L_II): thread (I, column jj) solves L_II x = e_jj by forward substitution
-  if (tid < NB * LA_BLK) {
-    const int I = tid / LA_BLK, jj = tid % LA_BLK, base = LA_BLK * I;
-    CT x[LA_BLK];
+    for (int I = 1; I < NB; ++I)
 #pragma unroll
-    for (int i = 0; i < LA_BLK; ++i) {
-      CT acc = mkc<CT>(0, 0);
+      for (int J = 0; J < I; ++J)
+        F[(size_t)(I * (I + 1) / 2 + J) * 256 + ti * LA_BLK + tk] = A[tri_index(LA_BLK * I + ti, LA_BLK * J + tk)];
+  }
+  // inv(L_II): thread (matrix, I, column jj) solves L_II x = e_jj by forward substitution
+  if (tid < MPC * NB * LA_BLK) {
+    const int mi = tid / (NB * LA_BLK), rem = tid - mi * NB * LA_BLK;
+    const int I = rem / LA_BLK, jj = rem % LA_BLK, base = LA_BLK * I;
+    int bm = 0;
 #pragma unroll
-      for (int k = 0; k < i; ++k)
-        if (k >= jj) cfma(acc, sA[tri_index(base + i, base + k)], x[k]);
-      const R rinv = sInv[base + i];
-      if (i < jj) x[i] = mkc<CT>(0, 0);
-      else if (i == jj) x[i] = mkc<CT>(rinv, (R)0);
-      else x[i] = mkc<CT>(-acc.x * rinv, -acc.y * rinv);
+    for (int u = 0; u < MPC; ++u) if (u == mi) bm = bsv[u];
+    if (bm < L.nsub) {
+      const CT* A = sA + mi * NTRI;
+      const R* Inv = sInv + mi * NPAD;
+      CT x[LA_BLK];
+#pragma unroll
+      for (int i = 0; i < LA_BLK; ++i) {
+        CT acc = mkc<CT>(0, 0);
+#pragma unroll
+        for (int k = 0; k < i; ++k)
+          if (k >= jj) cfma(acc, A[tri_index(base + i, base + k)], x[k]);
+        const R rinv = Inv[base + i];
+        if (i < jj) x[i] = mkc<CT>(0, 0);
+        else if (i == jj) x[i] = mkc<CT>(rinv, (R)0);
+        else x[i] = mkc<CT>(-acc.x * rinv, -acc.y * rinv);
+      }
+      CT* D = factors + (size_t)bm * L.fsize + (size_t)(I * (I + 1) / 2 + I) * 256;
+#pragma unroll
+      for (int i = 0; i < LA_BLK; ++i) D[i * LA_BLK + jj] = x[i];
     }
-    CT* D = F + (size_t)(I * (I + 1) / 2 + I) * 256;
-#pragma unroll
-    for (int i = 0; i < LA_BLK; ++i) D[i * LA_BLK + jj] = x[i];
   }
 }
 
@@ -887,9 +939,10 @@ k_gresid_tiles(LevelGeom L, const double* __restrict__ sigma, const TimeMats* __
 inline size_t factor_smem(const LevelGeom& L, int nptsmax, size_t csize, bool fine) {
   const size_t ntri = (size_t)L.npad * (L.npad + 1) / 2;
   const size_t npair = (size_t)nptsmax * (nptsmax + 1) / 2;
+  const size_t mpc = (size_t)factor_mpc(L.npad);
   (void)fine;
-  return csize * (ntri + L.npad) + (size_t)L.npad * (csize / 2) +
-         sizeof(double) * (LA_NPAIR * LA_KMAX * LA_KMAX + npair * LA_NPAIR) + sizeof(int) * (npair + 1);
+  return mpc * (csize * (ntri + L.npad) + (size_t)L.npad * (csize / 2)) +
+         sizeof(double) * (LA_NPAIR * LA_KMAX * LA_KMAX + mpc * npair * LA_NPAIR) + sizeof(int) * (mpc * npair + 1);
 }
 inline size_t sweep_fine_smem(const LevelGeom& L, int K, size_t rsize, size_t csize) {
   const int sx = L.sub[0] + 4, sy = L.dim > 1 ? L.sub[1] + 4 : 1, sz = L.dim > 2 ? L.sub[2] + 4 : 1;
@@ -936,7 +989,8 @@ cudaError_t launch_factor_n(const LevelGeom& L, const FineOp* fine, const double
   }
   if (smem > 227 * 1024) return cudaErrorInvalidValue;
   FineOp g = fine ? *fine : FineOp{};
-  kern<<<L.nsub, kFactorThreads, smem, s>>>(L, g, fine ? 1 : 0, nptsmax, sigma, tm, factors, status);
+  constexpr int mpc = factor_mpc(NPAD);
+  kern<<<(L.nsub + mpc - 1) / mpc, kFactorThreads, smem, s>>>(L, g, fine ? 1 : 0, nptsmax, sigma, tm, factors, status);
   return cudaGetLastError();
 }
 template <typename R, int NPAD>
