@@ -60,7 +60,7 @@ __host__ __device__ constexpr int tri_index(int r, int c) { return r * (r + 1) /
 // Small matrices leave most threads of a CTA idle in the later columns, so a CTA factorises
 // factor_mpc(NPAD) matrices together: each phase's work is split over the entries of all of them and
 // they share the two barriers per column.
-__host__ __device__ constexpr int factor_mpc(int npad) { return npad <= 32 ? 4 : (npad <= 64 ? 2 : 1); }
+__host__ __device__ constexpr int factor_mpc(int npad) { return npad <= 32 ? 8 : (npad <= 64 ? 2 : 1); }
 
 template <typename R, int NPAD>
 __global__ void __launch_bounds__(kFactorThreads, 2)
