@@ -285,6 +285,10 @@ k_factor(LevelGeom L, FineOp g, int is_fine, int nptsmax, const double* __restri
 // memory k-major, and every trailing block then takes one rank-16 update from it (row reads are
 // broadcasts, column reads are consecutive), so the per-entry bookkeeping is paid once per 16
 // columns instead of once per column.
+// complex64 matrices per CTA: small ones share the column barriers (their per-thread register tiles
+// stay small: NT = 3 complex for NPAD 32, 6 for NPAD 48).
+__host__ __device__ constexpr int factor_c64_mpc(int npad) { return npad <= 32 ? 4 : (npad <= 48 ? 2 : 1); }
+
 template <int NPAD>
 __global__ void __launch_bounds__(kFactorThreads, 2)
 k_factor_c64(LevelGeom L, FineOp g, int is_fine, int nptsmax, const double* __restrict__ sigma,
@@ -292,94 +296,118 @@ k_factor_c64(LevelGeom L, FineOp g, int is_fine, int nptsmax, const double* __re
   typedef float2 CT;
   constexpr int NB = NPAD / LA_BLK;
   constexpr int NT = NB * (NB + 1) / 2;
+  constexpr int MPC = factor_c64_mpc(NPAD);
   extern __shared__ __align__(16) unsigned char smem[];
   const int K = tm->K, KK = K * K;
-  CT* sPan = reinterpret_cast<CT*>(smem);                      // [LA_BLK][NPAD] finished panel, k-major
-  float* sInv = reinterpret_cast<float*>(sPan + LA_BLK * NPAD); // [NPAD]
-  CT* sDiag = reinterpret_cast<CT*>(sInv + NPAD);               // [NB][256]
-  float* sP = reinterpret_cast<float*>(sDiag + NB * 256);       // [9][K*K]
-  float* sPair = sP + LA_NPAIR * LA_KMAX * LA_KMAX;             // [npts*npts][nv]
   const int nv = is_fine ? 2 : LA_NPAIR;
-  float* sX = sPair + (size_t)nptsmax * nptsmax * nv;          // [npts] laser coordinate (finest level)
+  const int pstride = nptsmax * nptsmax * nv;
+  CT* sPan = reinterpret_cast<CT*>(smem);                          // [MPC][LA_BLK][NPAD] finished panel, k-major
+  float* sInv = reinterpret_cast<float*>(sPan + MPC * LA_BLK * NPAD); // [MPC][NPAD]
+  CT* sDiag = reinterpret_cast<CT*>(sInv + MPC * NPAD);             // [MPC][NB][256]
+  float* sP = reinterpret_cast<float*>(sDiag + MPC * NB * 256);     // [9][K*K]
+  float* sPair = sP + LA_NPAIR * LA_KMAX * LA_KMAX;                 // [MPC][npts*npts][nv]
+  float* sX = sPair + (size_t)MPC * pstride;                        // [MPC][npts] laser coordinate (finest)
 
   const int tid = threadIdx.x, ti = tid >> 4, tk = tid & 15;
-  const int b = blockIdx.x;
-  int o[3], e[3];
-  subvol_box(L, b, o, e);
-  const int npts = e[0] * e[1] * e[2];
-  const int n = npts * K;
-  for (int i = tid; i < LA_NPAIR * KK; i += kFactorThreads) sP[i] = (float)tm->P[i / KK][i % KK];
-  for (int i = tid; i < NB * 256; i += kFactorThreads) sDiag[i] = make_float2(0.f, 0.f);
-  if (is_fine)
-    for (int i = tid; i < npts; i += kFactorThreads) {
-      int ix, iy, iz;
-      local_coords(i, e, ix, iy, iz);
-      sX[i] = (float)fine_x(g, o[0] + ix, o[1] + iy, o[2] + iz);
-    }
-  const int nbox = box5_count(L.dim);
-  for (int t = tid; t < npts * npts; t += kFactorThreads) {
-    const int i = t / npts, j = t % npts;
-    int ix, iy, iz, jx, jy, jz;
-    local_coords(i, e, ix, iy, iz);
-    local_coords(j, e, jx, jy, jz);
-    const int px = o[0] + ix, py = o[1] + iy, pz = o[2] + iz;
-    const int qx = o[0] + jx, qy = o[1] + jy, qz = o[2] + jz;
-    float* dst = sPair + (size_t)t * nv;
-    if (is_fine) {
-      double s9[LA_NPAIR];
-      fine_sigma(g, px, py, pz, qx, qy, qz, s9);
-      dst[0] = (float)s9[1];
-      dst[1] = (float)s9[4];
+  // the CTA's matrices; slots past the last subvolume factorise an identity and store nothing
+  int bsv[MPC], npts_[MPC], o_[MPC][3], e_[MPC][3];
+#pragma unroll
+  for (int mi = 0; mi < MPC; ++mi) {
+    bsv[mi] = blockIdx.x * MPC + mi;
+    if (bsv[mi] < L.nsub) {
+      subvol_box(L, bsv[mi], o_[mi], e_[mi]);
+      npts_[mi] = e_[mi][0] * e_[mi][1] * e_[mi][2];
     } else {
-      const int dx = qx - px, dy = qy - py, dz = qz - pz;
-      const bool near = abs(dx) <= 2 && abs(dy) <= 2 && abs(dz) <= 2;
-      const int p = (pz * L.n[1] + py) * L.n[0] + px;
-      const int ofs = near ? box5_index(L.dim, dx, dy, dz) : 0;
-      for (int k = 0; k < LA_NPAIR; ++k) dst[k] = near ? (float)sigma[sigma_offset(p, k, ofs, nbox)] : 0.f;
+      o_[mi][0] = o_[mi][1] = o_[mi][2] = 0;
+      e_[mi][0] = e_[mi][1] = e_[mi][2] = 1;
+      npts_[mi] = 0;
+    }
+  }
+  for (int i = tid; i < LA_NPAIR * KK; i += kFactorThreads) sP[i] = (float)tm->P[i / KK][i % KK];
+  for (int i = tid; i < MPC * NB * 256; i += kFactorThreads) sDiag[i] = make_float2(0.f, 0.f);
+  const int nbox = box5_count(L.dim);
+#pragma unroll
+  for (int mi = 0; mi < MPC; ++mi) {
+    const int npts = npts_[mi];
+    const int* o = o_[mi];
+    const int* e = e_[mi];
+    if (is_fine)
+      for (int i = tid; i < npts; i += kFactorThreads) {
+        int ix, iy, iz;
+        local_coords(i, e, ix, iy, iz);
+        sX[mi * nptsmax + i] = (float)fine_x(g, o[0] + ix, o[1] + iy, o[2] + iz);
+      }
+    for (int t = tid; t < npts * npts; t += kFactorThreads) {
+      const int i = t / npts, j = t % npts;
+      int ix, iy, iz, jx, jy, jz;
+      local_coords(i, e, ix, iy, iz);
+      local_coords(j, e, jx, jy, jz);
+      const int px = o[0] + ix, py = o[1] + iy, pz = o[2] + iz;
+      const int qx = o[0] + jx, qy = o[1] + jy, qz = o[2] + jz;
+      float* dst = sPair + (size_t)mi * pstride + (size_t)t * nv;
+      if (is_fine) {
+        double s9[LA_NPAIR];
+        fine_sigma(g, px, py, pz, qx, qy, qz, s9);
+        dst[0] = (float)s9[1];
+        dst[1] = (float)s9[4];
+      } else {
+        const int dx = qx - px, dy = qy - py, dz = qz - pz;
+        const bool near = abs(dx) <= 2 && abs(dy) <= 2 && abs(dz) <= 2;
+        const int p = (pz * L.n[1] + py) * L.n[0] + px;
+        const int ofs = near ? box5_index(L.dim, dx, dy, dz) : 0;
+        for (int k = 0; k < LA_NPAIR; ++k) dst[k] = near ? (float)sigma[sigma_offset(p, k, ofs, nbox)] : 0.f;
+      }
     }
   }
   __syncthreads();
 
-  CT a[NT];
+  CT a[MPC][NT];
 #pragma unroll
-  for (int I = 0; I < NB; ++I) {
+  for (int mi = 0; mi < MPC; ++mi) {
+    const int npts = npts_[mi], n = npts * K;
 #pragma unroll
-    for (int J = 0; J <= I; ++J) {
-      const int r = LA_BLK * I + ti, c = LA_BLK * J + tk;
-      // assembled in FP32: this factor only preconditions the FP64-refined iteration
-      float re = 0.f, im = 0.f;
-      if (I == J && ti < tk) {
-      } else if (r >= n || c >= n) {
-        re = (r == c) ? 1.f : 0.f;
-      } else {
-        const int i = r / K, mm = r % K, j = c / K, nn = c % K;
-        float s9[LA_NPAIR];
-        const float* pr = sPair + (size_t)(i * npts + j) * nv;
-        if (is_fine) {
-          const float xp = sX[i], xq = sX[j];
-          const float same = (i == j) ? 1.f : 0.f, Hpq = pr[0];
-          s9[0] = same; s9[1] = Hpq; s9[2] = same * xp; s9[3] = Hpq; s9[4] = pr[1];
-          s9[5] = Hpq * xq; s9[6] = same * xp; s9[7] = xp * Hpq; s9[8] = same * xp * xp;
+    for (int I = 0; I < NB; ++I) {
+#pragma unroll
+      for (int J = 0; J <= I; ++J) {
+        const int r = LA_BLK * I + ti, c = LA_BLK * J + tk;
+        // assembled in FP32: this factor only preconditions the FP64-refined iteration
+        float re = 0.f, im = 0.f;
+        if (I == J && ti < tk) {
+        } else if (r >= n || c >= n) {
+          re = (r == c) ? 1.f : 0.f;
         } else {
+          const int i = r / K, mm = r % K, j = c / K, nn = c % K;
+          float s9[LA_NPAIR];
+          const float* pr = sPair + (size_t)mi * pstride + (size_t)(i * npts + j) * nv;
+          if (is_fine) {
+            const float xp = sX[mi * nptsmax + i], xq = sX[mi * nptsmax + j];
+            const float same = (i == j) ? 1.f : 0.f, Hpq = pr[0];
+            s9[0] = same; s9[1] = Hpq; s9[2] = same * xp; s9[3] = Hpq; s9[4] = pr[1];
+            s9[5] = Hpq * xq; s9[6] = same * xp; s9[7] = xp * Hpq; s9[8] = same * xp * xp;
+          } else {
 #pragma unroll
-          for (int kk = 0; kk < LA_NPAIR; ++kk) s9[kk] = pr[kk];
-        }
+            for (int kk = 0; kk < LA_NPAIR; ++kk) s9[kk] = pr[kk];
+          }
 #pragma unroll
-        for (int kk = 0; kk < LA_NPAIR; ++kk) {
-          const float v = s9[kk] * sP[kk * KK + mm * K + nn];
-          const int ph = theta_phase(kk);
-          if (ph == 0) re += v; else if (ph == 1) im += v; else im -= v;
+          for (int kk = 0; kk < LA_NPAIR; ++kk) {
+            const float v = s9[kk] * sP[kk * KK + mm * K + nn];
+            const int ph = theta_phase(kk);
+            if (ph == 0) re += v; else if (ph == 1) im += v; else im -= v;
+          }
         }
+        a[mi][I * (I + 1) / 2 + J] = make_float2(re, im);
       }
-      a[I * (I + 1) / 2 + J] = make_float2(re, im);
     }
   }
   if (tid == 0) {
-    float d2 = a[0].x;
-    if (!(d2 > 0.f)) { atomicOr(status, 1); d2 = 1.f; }
-    const float inv = rsqrtf(d2);
-    a[0] = make_float2(d2 * inv, 0.f);
-    sInv[0] = inv;
+#pragma unroll
+    for (int mi = 0; mi < MPC; ++mi) {
+      float d2 = a[mi][0].x;
+      if (!(d2 > 0.f)) { atomicOr(status, 1); d2 = 1.f; }
+      const float inv = rsqrtf(d2);
+      a[mi][0] = make_float2(d2 * inv, 0.f);
+      sInv[mi * NPAD] = inv;
+    }
   }
   __syncthreads();
 
@@ -390,15 +418,19 @@ k_factor_c64(LevelGeom L, FineOp g, int is_fine, int nptsmax, const double* __re
       const int j = LA_BLK * J0 + jj;
       // (A) owners of column j scale it and publish it
       if (tk == jj) {
-        const float inv = sInv[j];
 #pragma unroll
-        for (int I = J0; I < NB; ++I) {
-          const int r = LA_BLK * I + ti;
-          if (r > j) {
-            CT& v = a[I * (I + 1) / 2 + J0];
-            v.x *= inv;
-            v.y *= inv;
-            sPan[jj * NPAD + r] = v;
+        for (int mi = 0; mi < MPC; ++mi) {
+          const float inv = sInv[mi * NPAD + j];
+          CT* pan = sPan + (size_t)mi * LA_BLK * NPAD;
+#pragma unroll
+          for (int I = J0; I < NB; ++I) {
+            const int r = LA_BLK * I + ti;
+            if (r > j) {
+              CT& v = a[mi][I * (I + 1) / 2 + J0];
+              v.x *= inv;
+              v.y *= inv;
+              pan[jj * NPAD + r] = v;
+            }
           }
         }
       }
@@ -406,24 +438,28 @@ k_factor_c64(LevelGeom L, FineOp g, int is_fine, int nptsmax, const double* __re
       if (jj == LA_BLK - 1) break;   // the panel's last column changes nothing inside the panel
       // (B) rank-1 update of the panel right of column j; the owner of entry (j+1, j+1) takes its rsqrt
       if (c0 > j) {
-        const CT y = sPan[jj * NPAD + c0];
 #pragma unroll
-        for (int I = J0; I < NB; ++I) {
-          const int r = LA_BLK * I + ti;
-          if (r >= c0) {
-            const CT xr = sPan[jj * NPAD + r];
-            CT& v = a[I * (I + 1) / 2 + J0];
-            v.x = fmaf(-xr.x, y.x, v.x); v.x = fmaf(-xr.y, y.y, v.x);
-            v.y = fmaf(-xr.y, y.x, v.y); v.y = fmaf(xr.x, y.y, v.y);
+        for (int mi = 0; mi < MPC; ++mi) {
+          const CT* pan = sPan + (size_t)mi * LA_BLK * NPAD;
+          const CT y = pan[jj * NPAD + c0];
+#pragma unroll
+          for (int I = J0; I < NB; ++I) {
+            const int r = LA_BLK * I + ti;
+            if (r >= c0) {
+              const CT xr = pan[jj * NPAD + r];
+              CT& v = a[mi][I * (I + 1) / 2 + J0];
+              v.x = fmaf(-xr.x, y.x, v.x); v.x = fmaf(-xr.y, y.y, v.x);
+              v.y = fmaf(-xr.y, y.x, v.y); v.y = fmaf(xr.x, y.y, v.y);
+            }
           }
-        }
-        if (ti == jj + 1 && tk == jj + 1) {
-          CT& v = a[J0 * (J0 + 1) / 2 + J0];
-          float d2 = v.x;
-          if (!(d2 > 0.f)) { atomicOr(status, 1); d2 = 1.f; }
-          const float inv = rsqrtf(d2);
-          v = make_float2(d2 * inv, 0.f);
-          sInv[j + 1] = inv;
+          if (ti == jj + 1 && tk == jj + 1) {
+            CT& v = a[mi][J0 * (J0 + 1) / 2 + J0];
+            float d2 = v.x;
+            if (!(d2 > 0.f)) { atomicOr(status, 1); d2 = 1.f; }
+            const float inv = rsqrtf(d2);
+            v = make_float2(d2 * inv, 0.f);
+            sInv[mi * NPAD + j + 1] = inv;
+          }
         }
       }
       __syncthreads();
@@ -431,64 +467,82 @@ k_factor_c64(LevelGeom L, FineOp g, int is_fine, int nptsmax, const double* __re
     if (J0 + 1 < NB) {
       // rank-16 update of the trailing blocks (I, J), J0 < J <= I (upper halves of diagonal blocks
       // are updated too and never read)
-      for (int k = 0; k < LA_BLK; ++k) {
-        CT xr[NB], yc[NB];
 #pragma unroll
-        for (int I = J0 + 1; I < NB; ++I) {
-          xr[I] = sPan[k * NPAD + LA_BLK * I + ti];
-          yc[I] = sPan[k * NPAD + LA_BLK * I + tk];
-        }
+      for (int mi = 0; mi < MPC; ++mi) {
+        const CT* pan = sPan + (size_t)mi * LA_BLK * NPAD;
+        for (int k = 0; k < LA_BLK; ++k) {
+          CT xr[NB], yc[NB];
 #pragma unroll
-        for (int I = J0 + 1; I < NB; ++I)
-#pragma unroll
-          for (int J = J0 + 1; J <= I; ++J) {
-            CT& v = a[I * (I + 1) / 2 + J];
-            v.x = fmaf(-xr[I].x, yc[J].x, v.x); v.x = fmaf(-xr[I].y, yc[J].y, v.x);
-            v.y = fmaf(-xr[I].y, yc[J].x, v.y); v.y = fmaf(xr[I].x, yc[J].y, v.y);
+          for (int I = J0 + 1; I < NB; ++I) {
+            xr[I] = pan[k * NPAD + LA_BLK * I + ti];
+            yc[I] = pan[k * NPAD + LA_BLK * I + tk];
           }
+#pragma unroll
+          for (int I = J0 + 1; I < NB; ++I)
+#pragma unroll
+            for (int J = J0 + 1; J <= I; ++J) {
+              CT& v = a[mi][I * (I + 1) / 2 + J];
+              v.x = fmaf(-xr[I].x, yc[J].x, v.x); v.x = fmaf(-xr[I].y, yc[J].y, v.x);
+              v.y = fmaf(-xr[I].y, yc[J].x, v.y); v.y = fmaf(xr[I].x, yc[J].y, v.y);
+            }
+        }
       }
       if (tid == 0) {   // first pivot of the next panel
-        CT& v = a[(J0 + 1) * (J0 + 2) / 2 + J0 + 1];
-        float d2 = v.x;
-        if (!(d2 > 0.f)) { atomicOr(status, 1); d2 = 1.f; }
-        const float inv = rsqrtf(d2);
-        v = make_float2(d2 * inv, 0.f);
-        sInv[LA_BLK * (J0 + 1)] = inv;
+#pragma unroll
+        for (int mi = 0; mi < MPC; ++mi) {
+          CT& v = a[mi][(J0 + 1) * (J0 + 2) / 2 + J0 + 1];
+          float d2 = v.x;
+          if (!(d2 > 0.f)) { atomicOr(status, 1); d2 = 1.f; }
+          const float inv = rsqrtf(d2);
+          v = make_float2(d2 * inv, 0.f);
+          sInv[mi * NPAD + LA_BLK * (J0 + 1)] = inv;
+        }
       }
       __syncthreads();
     }
   }
 
-  float2* F = factors + (size_t)b * L.fsize;
 #pragma unroll
-  for (int I = 0; I < NB; ++I)
+  for (int mi = 0; mi < MPC; ++mi) {
+    float2* F = factors + (size_t)bsv[mi] * L.fsize;
+    const bool store = bsv[mi] < L.nsub;
 #pragma unroll
-    for (int J = 0; J <= I; ++J) {
-      if (I == J) {
-        if (ti >= tk) sDiag[I * 256 + ti * LA_BLK + tk] = a[I * (I + 1) / 2 + J];
-      } else {
-        F[(size_t)(I * (I + 1) / 2 + J) * 256 + ti * LA_BLK + tk] = a[I * (I + 1) / 2 + J];
+    for (int I = 0; I < NB; ++I)
+#pragma unroll
+      for (int J = 0; J <= I; ++J) {
+        if (I == J) {
+          if (ti >= tk) sDiag[(mi * NB + I) * 256 + ti * LA_BLK + tk] = a[mi][I * (I + 1) / 2 + J];
+        } else if (store) {
+          F[(size_t)(I * (I + 1) / 2 + J) * 256 + ti * LA_BLK + tk] = a[mi][I * (I + 1) / 2 + J];
+        }
       }
-    }
+  }
   __syncthreads();
-  if (tid < NB * LA_BLK) {
-    const int I = tid / LA_BLK, jj = tid % LA_BLK, base = LA_BLK * I;
-    const CT* Ld = sDiag + I * 256;
-    CT x[LA_BLK];
+  if (tid < MPC * NB * LA_BLK) {
+    const int mi = tid / (NB * LA_BLK), rem = tid - mi * NB * LA_BLK;
+    const int I = rem / LA_BLK, jj = rem % LA_BLK, base = LA_BLK * I;
+    int bm = 0;
 #pragma unroll
-    for (int i = 0; i < LA_BLK; ++i) {
-      CT acc = make_float2(0.f, 0.f);
+    for (int u = 0; u < MPC; ++u) if (u == mi) bm = bsv[u];
+    if (bm < L.nsub) {
+      const CT* Ld = sDiag + (mi * NB + I) * 256;
+      const float* Inv = sInv + mi * NPAD;
+      CT x[LA_BLK];
 #pragma unroll
-      for (int k = 0; k < i; ++k)
-        if (k >= jj) cfma(acc, Ld[i * LA_BLK + k], x[k]);
-      const float rinv = sInv[base + i];
-      if (i < jj) x[i] = make_float2(0.f, 0.f);
-      else if (i == jj) x[i] = make_float2(rinv, 0.f);
-      else x[i] = make_float2(-acc.x * rinv, -acc.y * rinv);
+      for (int i = 0; i < LA_BLK; ++i) {
+        CT acc = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int k = 0; k < i; ++k)
+          if (k >= jj) cfma(acc, Ld[i * LA_BLK + k], x[k]);
+        const float rinv = Inv[base + i];
+        if (i < jj) x[i] = make_float2(0.f, 0.f);
+        else if (i == jj) x[i] = make_float2(rinv, 0.f);
+        else x[i] = make_float2(-acc.x * rinv, -acc.y * rinv);
+      }
+      float2* D = factors + (size_t)bm * L.fsize + (size_t)(I * (I + 1) / 2 + I) * 256;
+#pragma unroll
+      for (int i = 0; i < LA_BLK; ++i) D[i * LA_BLK + jj] = x[i];
     }
-    float2* D = F + (size_t)(I * (I + 1) / 2 + I) * 256;
-#pragma unroll
-    for (int i = 0; i < LA_BLK; ++i) D[i * LA_BLK + jj] = x[i];
   }
 }
 
@@ -959,9 +1013,10 @@ template <int NPAD>
 cudaError_t launch_factor_c64_n(const LevelGeom& L, const FineOp* fine, const double* sigma, const TimeMats* tm,
                                 float2* factors, int* status, cudaStream_t s) {
   const int nptsmax = L.sub[0] * L.sub[1] * L.sub[2];
-  const size_t smem = sizeof(float2) * ((size_t)LA_BLK * NPAD + (size_t)(NPAD / LA_BLK) * 256) + sizeof(float) * NPAD +
-                      sizeof(float) * (LA_NPAIR * LA_KMAX * LA_KMAX + (size_t)nptsmax * nptsmax * (fine ? 2 : LA_NPAIR) +
-                                       nptsmax);
+  constexpr int mpc = factor_c64_mpc(NPAD);
+  const size_t smem = mpc * (sizeof(float2) * ((size_t)LA_BLK * NPAD + (size_t)(NPAD / LA_BLK) * 256) + sizeof(float) * NPAD) +
+                      sizeof(float) * (LA_NPAIR * LA_KMAX * LA_KMAX +
+                                       mpc * ((size_t)nptsmax * nptsmax * (fine ? 2 : LA_NPAIR) + nptsmax));
   auto kern = k_factor_c64<NPAD>;
   static bool attr_set = false;
   if (!attr_set) {
@@ -971,7 +1026,7 @@ cudaError_t launch_factor_c64_n(const LevelGeom& L, const FineOp* fine, const do
   }
   if (smem > 227 * 1024) return cudaErrorInvalidValue;
   FineOp g = fine ? *fine : FineOp{};
-  kern<<<L.nsub, kFactorThreads, smem, s>>>(L, g, fine ? 1 : 0, nptsmax, sigma, tm, factors, status);
+  kern<<<(L.nsub + mpc - 1) / mpc, kFactorThreads, smem, s>>>(L, g, fine ? 1 : 0, nptsmax, sigma, tm, factors, status);
   return cudaGetLastError();
 }
 
