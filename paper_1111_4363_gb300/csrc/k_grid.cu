@@ -261,13 +261,9 @@ __global__ void __launch_bounds__(256) k_mresid(FineOp g, const TimeMats* __rest
 // number of resident threads.
 constexpr int kTX = 32, kTY = 8, kNST = 5;
 constexpr int kPW = kTX + 2, kPH = kTY + 2, kPS = kPW * kPH;
-constexpr unsigned kTmaWaitLimit = 1u << 22;
 // stage stride in float2 units: one plane box, rounded up to 128 bytes so every stage is aligned
 __host__ __device__ constexpr int stage_f2(int K) { return ((kPS * K * 8 + 127) / 128) * 16; }
 
-__device__ __forceinline__ unsigned smem_addr(const void* p) {
-  return static_cast<unsigned>(__cvta_generic_to_shared(p));
-}
 __device__ __forceinline__ void tma_plane(void* dst, const CUtensorMap* map, int dim, int x, int y, int z,
                                           unsigned long long* bar, unsigned bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes) : "memory");
@@ -279,17 +275,6 @@ __device__ __forceinline__ void tma_plane(void* dst, const CUtensorMap* map, int
     asm volatile(
         "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
         ::"r"(smem_addr(dst)), "l"(map), "r"(0), "r"(x), "r"(y), "r"(smem_addr(bar)) : "memory");
-}
-// Polls the phase of an mbarrier at most `limit` times; true when it completed.
-__device__ __forceinline__ bool tma_wait(unsigned long long* bar, unsigned parity, unsigned limit) {
-  for (unsigned it = 0; it < limit; ++it) {
-    unsigned done;
-    asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-                 "selp.u32 %0, 1, 0, p;\n\t}"
-                 : "=r"(done) : "r"(smem_addr(bar)), "r"(parity) : "memory");
-    if (done) return true;
-  }
-  return false;
 }
 
 // K complex values of a staged point, two per 16-byte shared-memory load (K even).  For K = 4
@@ -345,8 +330,8 @@ __global__ void __launch_bounds__(kTX * kTY, K <= 4 ? 4 : 2) k_stencil_tma(FineO
   }
   if (tid == 0) {
     for (int s = 0; s < kNST; ++s)
-      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(bar + s)) : "memory");
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+      mbar_init(bar + s, 1);
+    mbar_init_fence();
   }
   __syncthreads();
   int issued = 0;   // planes issued so far (meaningful in thread 0)
@@ -374,7 +359,7 @@ __global__ void __launch_bounds__(kTX * kTY, K <= 4 ? 4 : 2) k_stencil_tma(FineO
       if (pin) load_k<float2, K>(pin, (long long)z * plane + col, add);
     }
     const int jfirst = g.dim > 2 ? (z == z0 ? jz - 1 : jz + 1) : 0, jlast = g.dim > 2 ? jz + 1 : 0;
-    for (int j = jfirst; j <= jlast; ++j) ok = ok && tma_wait(bar + j % kNST, (j / kNST) & 1, kTmaWaitLimit);
+    for (int j = jfirst; j <= jlast; ++j) ok = ok && mbar_wait(bar + j % kNST, (j / kNST) & 1, kMbarWaitLimit);
     if (__syncthreads_or(!ok)) {   // CTA-uniform: some thread gave up waiting
       ok = false;
       break;
@@ -453,7 +438,7 @@ __global__ void __launch_bounds__(kTX * kTY, K <= 4 ? 4 : 2) k_stencil_tma(FineO
     // bounded chance to land before the CTA exits
     if (tid == 0) {
       if (status) atomicOr(status, 4);
-      for (int j = max(0, issued - kNST); j < issued; ++j) tma_wait(bar + j % kNST, (j / kNST) & 1, kTmaWaitLimit);
+      for (int j = max(0, issued - kNST); j < issued; ++j) mbar_wait(bar + j % kNST, (j / kNST) & 1, kMbarWaitLimit);
     }
   }
 }

@@ -10,16 +10,16 @@ cudaError_t launch_factor<float>(const LevelGeom& L, const FineOp* fine, const d
 }
 template <>
 cudaError_t launch_sweep_fine<float>(const LevelGeom& L, const FineOp& g, const TimeMats* tm, int K, const float2* f,
-                                      const float2* yx, float2* c, const float2* factors, int colour, cudaStream_t s) {
-#define LA_CALL(N) launch_sweep_fine_n<float, N>(L, g, tm, K, f, yx, c, factors, colour, s)
+                                      const float2* yx, float2* c, const float2* factors, int colour, int* status, cudaStream_t s) {
+#define LA_CALL(N) launch_sweep_fine_n<float, N>(L, g, tm, K, f, yx, c, factors, colour, status, s)
   LA_NPAD_DISPATCH(L.npad, LA_CALL)
 #undef LA_CALL
 }
 template <>
 cudaError_t launch_sweep_coarse<float>(const LevelGeom& L, const double* sigma, const TimeMats* tm, int K,
                                         const float2* gvec, float2* e, const float2* factors, int colour,
-                                        cudaStream_t s) {
-#define LA_CALL(N) launch_sweep_coarse_n<float, N>(L, sigma, tm, K, gvec, e, factors, colour, s)
+                                        int* status, cudaStream_t s) {
+#define LA_CALL(N) launch_sweep_coarse_n<float, N>(L, sigma, tm, K, gvec, e, factors, colour, status, s)
   LA_NPAD_DISPATCH(L.npad, LA_CALL)
 #undef LA_CALL
 }

@@ -10,16 +10,16 @@ cudaError_t launch_factor<double>(const LevelGeom& L, const FineOp* fine, const 
 }
 template <>
 cudaError_t launch_sweep_fine<double>(const LevelGeom& L, const FineOp& g, const TimeMats* tm, int K, const double2* f,
-                                      const double2* yx, double2* c, const double2* factors, int colour, cudaStream_t s) {
-#define LA_CALL(N) launch_sweep_fine_n<double, N>(L, g, tm, K, f, yx, c, factors, colour, s)
+                                      const double2* yx, double2* c, const double2* factors, int colour, int* status, cudaStream_t s) {
+#define LA_CALL(N) launch_sweep_fine_n<double, N>(L, g, tm, K, f, yx, c, factors, colour, status, s)
   LA_NPAD_DISPATCH(L.npad, LA_CALL)
 #undef LA_CALL
 }
 template <>
 cudaError_t launch_sweep_coarse<double>(const LevelGeom& L, const double* sigma, const TimeMats* tm, int K,
                                         const double2* gvec, double2* e, const double2* factors, int colour,
-                                        cudaStream_t s) {
-#define LA_CALL(N) launch_sweep_coarse_n<double, N>(L, sigma, tm, K, gvec, e, factors, colour, s)
+                                        int* status, cudaStream_t s) {
+#define LA_CALL(N) launch_sweep_coarse_n<double, N>(L, sigma, tm, K, gvec, e, factors, colour, status, s)
   LA_NPAD_DISPATCH(L.npad, LA_CALL)
 #undef LA_CALL
 }

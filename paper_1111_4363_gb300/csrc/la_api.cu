@@ -656,10 +656,10 @@ static la_status sweep_level(la_ctx* c, int l, int nsweeps) {
       if (l == 0)
         e = launch_sweep_fine<R>(c->geo[0], c->fine, c->d_tm, c->K, c->adj ? nullptr : Fine<R>::f(c),
                                  c->adj ? (const CT*)c->adj_y : nullptr, Fine<R>::e(c), (const CT*)c->d_fac[0], col,
-                                 c->stream);
+                                 c->d_status, c->stream);
       else
         e = launch_sweep_coarse<R>(c->geo[l], c->d_sigma[l], c->d_tm, c->K, (const CT*)c->d_g[l], (CT*)c->d_e[l],
-                                   (const CT*)c->d_fac[l], col, c->stream);
+                                   (const CT*)c->d_fac[l], col, c->d_status, c->stream);
       if (e != cudaSuccess) return fail(c, LA_ECUDA, "sweep level %d colour %d: %s", l, col, cudaGetErrorString(e));
     }
     // inside a capture the records are graph nodes (external), not capture-internal joins
@@ -1315,13 +1315,13 @@ extern "C" la_status la_relax_colour(la_ctx* c, const void* psi0, double t0, int
   if (c->cfg.precision == 0) {
     LA_TRY(factor_all<double>(c));
     e = launch_sweep_fine<double>(c->geo[0], c->fine, c->d_tm, c->K, c->d_f, nullptr, c->d_c,
-                                  (const double2*)c->d_fac[0], colour, c->stream);
+                                  (const double2*)c->d_fac[0], colour, c->d_status, c->stream);
   } else {
     LA_TRY(factor_all<float>(c));
     launch_c128_to_c64(c->nunk0, c->d_f, c->d_f32, c->stream);
     launch_c128_to_c64(c->nunk0, c->d_c, c->d_e32, c->stream);
     e = launch_sweep_fine<float>(c->geo[0], c->fine, c->d_tm, c->K, c->d_f32, nullptr, c->d_e32,
-                                 (const float2*)c->d_fac[0], colour, c->stream);
+                                 (const float2*)c->d_fac[0], colour, c->d_status, c->stream);
     LA_CUDA(c, cudaMemsetAsync(c->d_c, 0, sizeof(double2) * (size_t)c->nunk0, c->stream));
     launch_axpy_c64_to_c128(c->nunk0, c->d_e32, c->d_c, c->stream);
   }

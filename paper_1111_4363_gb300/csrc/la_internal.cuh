@@ -227,7 +227,7 @@ cudaError_t launch_factor(const LevelGeom& L, const FineOp* fine, const double* 
 template <typename R>
 cudaError_t launch_sweep_fine(const LevelGeom& L, const FineOp& g, const TimeMats* tm, int K,
                               const typename C2<R>::T* f, const typename C2<R>::T* yx, typename C2<R>::T* c,
-                              const typename C2<R>::T* factors, int colour, cudaStream_t s);
+                              const typename C2<R>::T* factors, int colour, int* status, cudaStream_t s);
 template <typename R>
 cudaError_t launch_gresid_tiles(const LevelGeom& L, const double* sigma, const TimeMats* tm, int K,
                                 const typename C2<R>::T* gvec, const typename C2<R>::T* e, typename C2<R>::T* out,
@@ -235,6 +235,40 @@ cudaError_t launch_gresid_tiles(const LevelGeom& L, const double* sigma, const T
 template <typename R>
 cudaError_t launch_sweep_coarse(const LevelGeom& L, const double* sigma, const TimeMats* tm, int K,
                                 const typename C2<R>::T* gvec, typename C2<R>::T* e,
-                                const typename C2<R>::T* factors, int colour, cudaStream_t s);
+                                const typename C2<R>::T* factors, int colour, int* status, cudaStream_t s);
+
+
+// ------------------------------------------------------------------ mbarrier and bulk copies
+// Every wait on an mbarrier polls a bounded number of times; a caller that gives up records a
+// status bit instead of spinning on.
+constexpr unsigned kMbarWaitLimit = 1u << 22;
+
+__device__ __forceinline__ unsigned smem_addr(const void* p) {
+  return static_cast<unsigned>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+// makes initialised mbarriers visible to the asynchronous (copy) proxy
+__device__ __forceinline__ void mbar_init_fence() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+// Polls the phase of an mbarrier at most `limit` times; true when it completed.
+__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity, unsigned limit) {
+  for (unsigned it = 0; it < limit; ++it) {
+    unsigned done;
+    asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+                 "selp.u32 %0, 1, 0, p;\n\t}"
+                 : "=r"(done) : "r"(smem_addr(bar)), "r"(parity) : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+// One contiguous global -> shared copy completed on `bar` (both addresses 16-byte aligned, bytes a
+// multiple of 16); the calling thread also posts the expected byte count.
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, unsigned bytes, unsigned long long* bar) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes) : "memory");
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+               ::"r"(smem_addr(dst)), "l"(__cvta_generic_to_global(src)), "r"(bytes), "r"(smem_addr(bar))
+               : "memory");
+}
 
 }  // namespace la
