@@ -4,6 +4,15 @@ Sec. II: the trial coefficients are improved by minimising, in each subvolume U,
 the residual norm N with the coefficients outside U held fixed; relaxations of
 subvolumes that do not interact are independent and may run in parallel.
 
+Two local problems are kept.  The default (least squares, below) is the norm
+argument of Sec. II.  The paper's own preconditioner form (Sec. II, last
+paragraphs) is the square Dirichlet problem: find delta_U with
+L_U delta_U = -L_U phi, delta = 0 on the boundary of U and at t0, i.e. in the
+discrete system the rows of U's test functions and the columns of U's unknowns,
+    M_UU delta_U = (f - M c)_U,
+which the paper notes need not decrease the action (the Lagrange multipliers of
+the boundary conditions make it a critical point, not a minimum).
+
 Local problem (reading of Sec. II, the norm argument; the paper's own square
 Dirichlet form is noted there to be non-monotone): with G = M^dagger W M the
 Hermitian positive-definite normal matrix and g = M^dagger W f,
@@ -105,6 +114,74 @@ def colouring_is_valid(G, shape, sub, K) -> bool:
         owner[unknown_indices(pts, K)] = b
         colour_of.append(colour)
     coo = G.tocoo()
+    nz = np.abs(coo.data) > 0
+    bi, bj = owner[coo.row[nz]], owner[coo.col[nz]]
+    cross = bi != bj
+    same = np.array(colour_of)[bi[cross]] == np.array(colour_of)[bj[cross]]
+    return not bool(np.any(same))
+
+
+# ----------------------------------------------------------------------------- square form
+def red_black_subvolumes(shape, sub):
+    """(colour, point indices) per subvolume with the two-colour checkerboard colouring
+    colour = (sum of block indices) mod 2.  M couples only edge neighbours (radius-1
+    stencil), so two same-colour subvolumes, which touch at most at corners, never
+    share a row of M."""
+    d = len(shape)
+    nb = block_counts(shape, sub)
+    strides = [int(np.prod(shape[a + 1:])) for a in range(d)]
+    out = []
+    for bidx in itertools.product(*[range(n) for n in nb]):
+        ranges = [range(bidx[a] * sub[a], min((bidx[a] + 1) * sub[a], shape[a])) for a in range(d)]
+        pts = sorted(sum(coord[a] * strides[a] for a in range(d)) for coord in itertools.product(*ranges))
+        out.append((int(sum(bidx)) % 2, np.array(pts, dtype=np.int64)))
+    return out
+
+
+def square_block_update(M, f, x, idx) -> np.ndarray:
+    """delta_U = M_UU^{-1} (f - M x)_U for one subvolume U (unknown indices idx): the square
+    Dirichlet form of the local problem (Sec. II); afterwards the residual rows of U vanish."""
+    M = M.tocsr()
+    r = f[idx] - M[idx] @ x
+    return np.linalg.solve(M[idx][:, idx].toarray(), r)
+
+
+class SquareRelaxation:
+    """Red-black block Gauss-Seidel on M c = f with the square local problem of Sec. II."""
+
+    def __init__(self, M, shape, sub, K):
+        self.M = M.tocsr()
+        self.K = K
+        self.ncolours = 2
+        self.blocks = []
+        for colour, pts in red_black_subvolumes(shape, sub):
+            idx = unknown_indices(pts, K)
+            self.blocks.append((colour, idx, sla.lu_factor(self.M[idx][:, idx].toarray())))
+
+    def colour_pass(self, x, f, colour, order=1):
+        r = f - self.M @ x
+        updates = [(idx, sla.lu_solve(fac, r[idx])) for col, idx, fac in self.blocks[::order] if col == colour]
+        for idx, d in updates:
+            x[idx] += d
+
+    def sweep(self, x, f, after_colour=None):
+        """One sweep = colour 0 then colour 1."""
+        for colour in range(2):
+            self.colour_pass(x, f, colour)
+            if after_colour is not None:
+                after_colour(colour)
+
+
+def red_black_is_valid(A, shape, sub, K) -> bool:
+    """True when no two distinct same-colour red-black subvolumes are coupled by A."""
+    A = A.tocsr()
+    blocks = red_black_subvolumes(shape, sub)
+    owner = np.full(A.shape[0], -1, dtype=np.int64)
+    colour_of = []
+    for b, (colour, pts) in enumerate(blocks):
+        owner[unknown_indices(pts, K)] = b
+        colour_of.append(colour)
+    coo = A.tocoo()
     nz = np.abs(coo.data) > 0
     bi, bj = owner[coo.row[nz]], owner[coo.col[nz]]
     cross = bi != bj
