@@ -85,6 +85,12 @@ typedef struct {
                            (ckpt_every steps x all levels) in device memory and reuses them for the
                            adjoint relaxation instead of factorising every step again; without the
                            memory for it the factors are recomputed as usual */
+  int local_form;       /* local problem of a subvolume U (Sec. II): 0 = least squares, minimise N over
+                           c_U (exact block Gauss-Seidel on M^dagger W M, 2^dim colours, never raises N;
+                           default); 1 = the paper's square Dirichlet form M_UU delta_U = (f - M c)_U,
+                           two-colour checkerboard, LU with partial pivoting; N may rise and the
+                           iteration may diverge.  1 requires precision 0, levels 1, sub >= 1 and at
+                           most 96 unknowns per subvolume; la_backward rejects it (LA_EINVAL) */
 } la_config;
 
 /* Laser field E(t) = sum_k amp[k] * env_k(t) * sin(omega[k] t), env_k = exp(-((t - t_center[k])/sigma[k])^2)

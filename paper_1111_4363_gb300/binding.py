@@ -17,6 +17,7 @@ LIB_PATH = os.path.join(HERE, "_build", "libleastaction.so")
 LA_OK, LA_EINVAL, LA_ENOMEM, LA_ECUDA, LA_ENOTCONV, LA_ESTATE = range(6)
 STATUS_NAMES = {0: "LA_OK", 1: "LA_EINVAL", 2: "LA_ENOMEM", 3: "LA_ECUDA", 4: "LA_ENOTCONV", 5: "LA_ESTATE"}
 WEIGHTS = {"dual": 0, "literal": 1, "identity": 2}
+LOCAL_FORMS = {"lsq": 0, "square": 1}
 
 EXPORTS = ["la_init", "la_set_hamiltonian", "la_step", "la_action", "la_solve_step", "la_residual",
            "la_relax_colour", "la_time_matrices", "la_backward", "la_step_batch", "la_profile_enable", "la_profile_read", "la_action_noalloc",
@@ -36,7 +37,8 @@ class la_config(C.Structure):
                 ("coarse_sweeps", C.c_int), ("max_cycles", C.c_int), ("tol", C.c_double), ("weight", C.c_int),
                 ("precision", C.c_int), ("laser_axis", C.c_int), ("ckpt_every", C.c_int),
                 ("coarse_sub", C.c_int * 3), ("trial", C.c_int), ("coarse_cycle", C.c_int),
-                ("coarse_nu1", C.c_int), ("coarse_nu2", C.c_int), ("cache_factors", C.c_int)]
+                ("coarse_nu1", C.c_int), ("coarse_nu2", C.c_int), ("cache_factors", C.c_int),
+                ("local_form", C.c_int)]
 
 
 class la_pulse(C.Structure):
@@ -139,6 +141,7 @@ def config_from_workload(w, precision: int = 0, **overrides) -> la_config:
     cfg.trial = getattr(w, "trial", 0)
     if getattr(w, "coarse_nu", None) is not None:
         cfg.coarse_cycle, cfg.coarse_nu1, cfg.coarse_nu2 = 1, int(w.coarse_nu[0]), int(w.coarse_nu[1])
+    cfg.local_form = LOCAL_FORMS[getattr(w, "local_form", "lsq")]
     for k, v in overrides.items():
         setattr(cfg, k, v)
     return cfg

@@ -42,6 +42,7 @@ struct la_ctx {
   double* d_partials = nullptr;
   double* d_N = nullptr;
   int* d_status = nullptr;
+  int* d_perm = nullptr;            // square local form: row permutation of every finest factor
   int nparts = 0;
   bool have_ham = false;
   bool have_step = false;
@@ -331,12 +332,16 @@ extern "C" la_status la_init(const la_config* cfg, void* stream, la_ctx** out) {
   else if (k.ckpt_every < 0) bad("ckpt_every must be >= 0");
   else if (k.trial < 0 || k.trial > 3) bad("trial must be 0..3");
   else if (k.coarse_cycle && (k.coarse_nu1 < 0 || k.coarse_nu2 < 0)) bad("coarse_nu1, coarse_nu2 must be >= 0");
+  else if (k.local_form < 0 || k.local_form > 1) bad("local_form must be 0 or 1");
+  else if (k.local_form == 1 && k.precision != 0) bad("the square local form runs in FP64 (precision 0)");
+  else if (k.local_form == 1 && k.levels != 1) bad("the square local form is single-level (levels 1)");
   if (st == LA_OK) {
     for (int a = 0; a < 3 && st == LA_OK; ++a) {
       if (a < k.dim) {
         if (k.n[a] < 1) bad("n must be >= 1 on used axes");
         else if (!(k.h[a] > 0)) bad("h must be positive on used axes");
-        else if (k.sub[a] < 2) bad("sub must be >= 2 on used axes (same-colour subvolumes must not interact)");
+        else if (k.sub[a] < (k.local_form == 1 ? 1 : 2))
+          bad("sub must be >= 2 on used axes (>= 1 in the square form): same-colour subvolumes must not interact");
         else if (k.coarse_sub[a] == 1 || k.coarse_sub[a] < 0) bad("coarse_sub must be 0 or >= 2 on used axes");
         else if (k.n[a] % (1 << (k.levels - 1))) bad("n must be divisible by 2^(levels-1) on used axes");
       } else if (k.n[a] != 1) bad("unused axes must have n = 1");
@@ -358,6 +363,11 @@ extern "C" la_status la_init(const la_config* cfg, void* stream, la_ctx** out) {
   if (subpts > LA_NPTS_MAX || round_npad(subpts * k.nt) < 0 || csubpts > LA_NPTS_MAX ||
       round_npad(csubpts * k.nt) < 0) {
     g_init_error = "invalid configuration: a subvolume may hold at most 32 points and 128 unknowns";
+    delete c;
+    return LA_EINVAL;
+  }
+  if (k.local_form == 1 && round_npad(subpts * k.nt) > 96) {
+    g_init_error = "invalid configuration: the square local form allows at most 96 unknowns per subvolume";
     delete c;
     return LA_EINVAL;
   }
@@ -394,7 +404,7 @@ extern "C" la_status la_init(const la_config* cfg, void* stream, la_ctx** out) {
     G.nsub = G.nb[0] * G.nb[1] * G.nb[2];
     G.npad = round_npad((l > 0 ? csubpts : subpts) * k.nt);
     G.nblk = G.npad / LA_BLK;
-    G.fsize = (long long)G.nblk * (G.nblk + 1) / 2 * LA_BLK * LA_BLK;
+    G.fsize = k.local_form == 1 ? (long long)G.npad * G.npad : (long long)G.nblk * (G.nblk + 1) / 2 * LA_BLK * LA_BLK;
   }
   if (!build_time_constants(c)) {
     g_init_error = "invalid configuration: singular time-basis Gram matrix";
@@ -441,6 +451,7 @@ extern "C" la_status la_init(const la_config* cfg, void* stream, la_ctx** out) {
   ALLOC(c->d_partials, sizeof(double) * c->nparts);
   ALLOC(c->d_N, sizeof(double) * 2);
   ALLOC(c->d_status, sizeof(int));
+  if (k.local_form == 1) ALLOC(c->d_perm, sizeof(int) * (size_t)c->geo[0].nsub * c->geo[0].npad);
   for (int j = 0; j < k.trial; ++j) ALLOC(c->d_hist[j], sizeof(double2) * (size_t)c->nunk0);
 #undef ALLOC
   c->fine.V0 = c->d_V0;
@@ -478,7 +489,8 @@ static void finest_flops(la_ctx* c) {
         int e[3], bb[3] = {bx, by, bz};
         for (int a = 0; a < 3; ++a) e[a] = std::min(G.sub[a], G.n[a] - bb[a] * G.sub[a]);
         const double n = (double)e[0] * e[1] * e[2] * c->K;
-        ff += 4.0 / 3.0 * n * n * n;
+        // Cholesky (4/3 n^3) and two triangular solves (8 n^2); the square form's LU takes 8/3 n^3
+        ff += (c->cfg.local_form == 1 ? 8.0 : 4.0) / 3.0 * n * n * n;
         fs += 8.0 * n * n;
       }
   c->flops_factor = ff;
@@ -626,8 +638,11 @@ static la_status factor_all(la_ctx* c) {
   for (int l = 0; l < (side ? 1 : c->L); ++l) {
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (c->prof && l == 0 && (e0 = prof_event(c)) && (e1 = prof_event(c))) cudaEventRecord(e0, c->stream);
-    cudaError_t e = launch_factor<R>(c->geo[l], l == 0 ? &c->fine : nullptr, c->d_sigma[l], c->d_tm,
-                                     (CT*)c->d_fac[l], c->d_status, c->stream);
+    cudaError_t e = c->cfg.local_form == 1
+                        ? launch_factor_square(c->geo[0], c->fine, c->d_tm, (double2*)c->d_fac[0], c->d_perm,
+                                               c->d_status, c->stream)
+                        : launch_factor<R>(c->geo[l], l == 0 ? &c->fine : nullptr, c->d_sigma[l], c->d_tm,
+                                           (CT*)c->d_fac[l], c->d_status, c->stream);
     if (e != cudaSuccess) return fail(c, LA_ECUDA, "factor level %d: %s", l, cudaGetErrorString(e));
     ++c->launches;
     if (e1) {
@@ -645,15 +660,19 @@ static la_status factor_all(la_ctx* c) {
 template <typename R>
 static la_status sweep_level(la_ctx* c, int l, int nsweeps) {
   typedef typename C2<R>::T CT;
-  const int ncol = 1 << c->dim;
+  const bool square = c->cfg.local_form == 1;
+  const int ncol = square ? 2 : 1 << c->dim;
   for (int s = 0; s < nsweeps; ++s) {
     // one event pair around a whole finest-level sweep (all colours)
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     const bool timed = l == 0 && prof_begin(c, &e0, &e1);
     for (int col = 0; col < ncol; ++col) {
       cudaError_t e;
-      if (colour_count(c->geo[l], col) > 0) ++c->launches;
-      if (l == 0)
+      if (square || colour_count(c->geo[l], col) > 0) ++c->launches;
+      if (square)
+        e = launch_sweep_square(c->geo[0], c->fine, c->d_tm, c->K, c->d_f, c->d_c, (const double2*)c->d_fac[0],
+                                c->d_perm, col, c->stream);
+      else if (l == 0)
         e = launch_sweep_fine<R>(c->geo[0], c->fine, c->d_tm, c->K, c->adj ? nullptr : Fine<R>::f(c),
                                  c->adj ? (const CT*)c->adj_y : nullptr, Fine<R>::e(c), (const CT*)c->d_fac[0], col,
                                  c->d_status, c->stream);
@@ -671,7 +690,8 @@ static la_status sweep_level(la_ctx* c, int l, int nsweeps) {
 // Error for a nonzero device status word (bit 1: a subvolume matrix was not positive definite;
 // bit 4: a TMA-staged plane did not arrive within its wait limit).
 static la_status status_error(la_ctx* c, int status) {
-  if (status & 1) return fail(c, LA_ECUDA, "a subvolume matrix was not positive definite (status %d)", status);
+  if (status & 1)
+    return fail(c, LA_ECUDA, "a subvolume matrix was singular or not positive definite (status %d)", status);
   return fail(c, LA_ECUDA, "a staged copy did not complete within its wait limit (status %d)", status);
 }
 
@@ -1036,6 +1056,8 @@ static la_status adjoint_solve(la_ctx* c, int* cycles) {
 
 extern "C" la_status la_backward(la_ctx* c, const void* dJ_dpsiT, double* grad_amp, void* dJ_dpsi0) {
   if (!c || !dJ_dpsiT) return c ? fail(c, LA_EINVAL, "null dJ/dpsi_T") : LA_EINVAL;
+  if (c->cfg.local_form == 1)
+    return fail(c, LA_EINVAL, "la_backward relaxes the adjoint with the least-squares factors (local_form 0)");
   if (!c->have_rec || c->rec_nsteps < 1)
     return fail(c, LA_ESTATE, "la_backward needs a preceding la_step with ckpt_every > 0");
   const int C = c->cfg.ckpt_every, nsteps = c->rec_nsteps, K = c->K;
@@ -1306,13 +1328,18 @@ extern "C" la_status la_residual(la_ctx* c, const void* psi0, double t0, const v
 
 extern "C" la_status la_relax_colour(la_ctx* c, const void* psi0, double t0, int colour, void* cio) {
   if (!c || !psi0 || !cio) return c ? fail(c, LA_EINVAL, "invalid argument") : LA_EINVAL;
-  if (colour < 0 || colour >= (1 << c->dim)) return fail(c, LA_EINVAL, "colour out of range");
+  if (colour < 0 || colour >= (c->cfg.local_form == 1 ? 2 : (1 << c->dim)))
+    return fail(c, LA_EINVAL, "colour out of range");
   if (!c->have_ham) return fail(c, LA_ESTATE, "la_set_hamiltonian must be called first");
   LA_TRY(load_any(c, c->d_psi, psi0, sizeof(double2) * (size_t)c->np0));
   LA_TRY(load_any(c, c->d_c, cio, sizeof(double2) * (size_t)c->nunk0));
   LA_TRY(setup_step(c, t0));
   cudaError_t e;
-  if (c->cfg.precision == 0) {
+  if (c->cfg.local_form == 1) {
+    LA_TRY(factor_all<double>(c));
+    e = launch_sweep_square(c->geo[0], c->fine, c->d_tm, c->K, c->d_f, c->d_c, (const double2*)c->d_fac[0],
+                            c->d_perm, colour, c->stream);
+  } else if (c->cfg.precision == 0) {
     LA_TRY(factor_all<double>(c));
     e = launch_sweep_fine<double>(c->geo[0], c->fine, c->d_tm, c->K, c->d_f, nullptr, c->d_c,
                                   (const double2*)c->d_fac[0], colour, c->d_status, c->stream);

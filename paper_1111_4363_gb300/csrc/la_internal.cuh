@@ -232,6 +232,11 @@ template <typename R>
 cudaError_t launch_gresid_tiles(const LevelGeom& L, const double* sigma, const TimeMats* tm, int K,
                                 const typename C2<R>::T* gvec, const typename C2<R>::T* e, typename C2<R>::T* out,
                                 cudaStream_t s);
+// square local form (finest level, FP64): LU factors with row permutations, red-black sweeps
+cudaError_t launch_factor_square(const LevelGeom& L, const FineOp& g, const TimeMats* tm, double2* lu, int* perm,
+                                 int* status, cudaStream_t s);
+cudaError_t launch_sweep_square(const LevelGeom& L, const FineOp& g, const TimeMats* tm, int K, const double2* f,
+                                double2* c, const double2* lu, const int* perm, int colour, cudaStream_t s);
 template <typename R>
 cudaError_t launch_sweep_coarse(const LevelGeom& L, const double* sigma, const TimeMats* tm, int K,
                                 const typename C2<R>::T* gvec, typename C2<R>::T* e,

@@ -64,6 +64,7 @@ class Workload:
     coarse_sub: Optional[Tuple[int, int, int]] = None   # subvolume extent on Galerkin levels (None: sub)
     trial: int = 0                 # la_step trial iterate: 0 = zero, 1..3 = extrapolation from 1..3 steps
     coarse_nu: Optional[Tuple[int, int]] = None   # (nu1, nu2) on Galerkin levels above the coarsest (None: nu1, nu2)
+    local_form: str = "lsq"        # subvolume problem: "lsq" (least squares) | "square" (Dirichlet form, red-black)
 
     @property
     def shape(self) -> Tuple[int, ...]:
