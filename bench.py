@@ -60,7 +60,42 @@ def workload(name: str) -> wl.Workload:
         return dataclasses.replace(wl.softcore_2d(n=128, levels=4, nsteps=200), **PRODUCTION_2D)
     if name == "1d":
         return wl.harmonic_1d()
+    if name == "2d-square":         # the paper's square local form (Sec. II), single level, red-black
+        return dataclasses.replace(wl.softcore_2d(n=256, levels=1, nsteps=200), local_form="square", nu1=1, nu2=1,
+                                   trial=3)
     raise ValueError(name)
+
+
+def action_trajectory(B, torch, w, dt, local_form, nsweeps):
+    """N(c)/N(0) after each of nsweeps single sweeps of the first step from c = 0 (single level, one
+    sweep per cycle), for the given local form and time step."""
+    v = dataclasses.replace(w, dt=dt, levels=1, nu1=1, nu2=0, local_form=local_form, trial=0, coarse_nu=None)
+    ctx = B.Context(B.config_from_workload(v))
+    ctx.set_hamiltonian(torch.tensor(wl.potential(v).ravel(), dtype=torch.float64, device="cuda"), v.pulse)
+    psi0 = torch.from_numpy(wl.initial_state(v).ravel()).cuda()
+    c = torch.zeros(v.nunknowns, dtype=torch.complex128, device="cuda")
+    out = []
+    for s in range(1, nsweeps + 1):
+        st, (cycles, sweeps, N, rel) = ctx.solve_step(psi0, 0.0, c, ncycles=s)
+        out.append(rel)
+    ctx.close()
+    return out
+
+
+def square_form_report(B, torch, w):
+    """Action per sweep of the square form against the least-squares form at the workload's kappa and
+    at kappa = 2.5 (dt = 0.2 on h = 0.2): Sec. II notes the square form need not decrease the action."""
+    rep = {}
+    for dt in (w.dt, 0.2):
+        kappa = dt / (2 * w.h[0] ** 2)
+        sq = action_trajectory(B, torch, w, dt, "square", 8)
+        ls = action_trajectory(B, torch, w, dt, "lsq", 8)
+        rep[f"kappa_{kappa:g}"] = {
+            "square_rel_action_per_sweep": [float(f"{x:.3e}") for x in sq],
+            "square_monotone": all(b <= a for a, b in zip([1.0] + sq, sq)),
+            "least_squares_rel_action_per_sweep": [float(f"{x:.3e}") for x in ls],
+            "least_squares_monotone": all(b <= a for a, b in zip([1.0] + ls, ls))}
+    return rep
 
 
 def dist_env():
@@ -263,6 +298,9 @@ def run_ours(args):
     e2e_value = nunk * e2e_sweeps / e2e_s * (ws if ws > 1 else 1)
 
     roofline = dominant_roofline(prof, w, args.precision, ms, traffic_ok=args.workload == "2d")
+    if getattr(w, "local_form", "lsq") == "square":
+        roofline["kernel"] = roofline["kernel"].replace("k_factor", "k_factor_square").replace("k_sweep_fine",
+                                                                                               "k_sweep_square")
     prec_tag = "f64" if args.precision == 0 else "c64 local solves + f64 refinement"
 
     out = {"metric": METRIC, "value": value, "unit": "unknowns/s", "n_gpus": ws, "steps": args.steps,
@@ -271,6 +309,7 @@ def run_ours(args):
            "config": {"workload": w.name, "grid": list(w.shape), "K": w.nt, "subvolume": list(w.sub[:w.dim]),
                       "levels": w.levels, "cycle": cycle_name(w), "coarse_sweeps": w.coarse_sweeps,
                       "tol_rel_action": w.tol, "precision": args.precision, "trial": w.trial,
+                      "local_form": getattr(w, "local_form", "lsq"),
                       "parallelism": "replicas" if ws > 1 else "single",
                       "l2": "inputs smaller than L2; each step rewrites the 352 MB factor store (> L2)"},
            "cycles_per_step": cycles / args.steps, "fine_sweeps_per_step": sweeps / args.steps,
@@ -280,8 +319,10 @@ def run_ours(args):
            "gpu_launches": int(prof["launches"]), "roofline": roofline,
            "stencil_roofline": stencil_roofline(prof, args.precision),
            "stencil_roofline_c64": stencil_roofline(prof, args.precision, c64=True), "clocks": clk}
-    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline and getattr(w, "local_form", "lsq") == "lsq":
         out["cpu_baseline"] = cpu_baseline(w)
+    if rank == 0 and getattr(w, "local_form", "lsq") == "square":
+        out["square_form"] = square_form_report(B, torch, w)
     if rank == 0:
         print(json.dumps(out))
     ctx.close()
@@ -486,7 +527,8 @@ def main():
     ap.add_argument("--steps", type=int, default=40)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="2d", choices=["2d", "2d-small", "1d", "batched", "3d-adjoint"])
+    ap.add_argument("--workload", default="2d",
+                    choices=["2d", "2d-small", "1d", "2d-square", "batched", "3d-adjoint"])
     ap.add_argument("--batch", type=int, default=512)
     ap.add_argument("--n3d", type=int, default=128)
     ap.add_argument("--precision", type=int, default=0, choices=[0, 1])
