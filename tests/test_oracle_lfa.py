@@ -1,0 +1,106 @@
+"""Pins for the oracle's Legendre-element convergence maps (Secs. IV-V: element matrices,
+constrained relaxation, continuity projection, the plane-wave experiment)."""
+import numpy as np
+import pytest
+
+from oracle import legendre_elements as le
+from oracle import lfa
+
+
+@pytest.mark.parametrize("nx,nt", [(3, 3), (4, 5), (6, 6)])
+def test_element_matrices_closed_forms(nx, nt):
+    """Sec. IV: O and U from the orthogonality relation, Q_nm = 2 for n > m with n - m odd, and the
+    kinetic element in the closed form of Eq. Tmatelt (row = test function)."""
+    O, U, Qt, K = lfa.element_matrices(nx, nt)
+    assert np.allclose(O, np.diag(2.0 / (2 * np.arange(nx) + 1)), atol=1e-14)
+    assert np.allclose(U, np.diag(2.0 / (2 * np.arange(nt) + 1)), atol=1e-14)
+    for m in range(nt):
+        for n in range(nt):
+            ref = 2.0 if (n > m and (n - m) % 2 == 1) else 0.0
+            assert abs(Qt[m, n] - ref) < 1e-13
+    for j in range(nx):
+        for i in range(nx):
+            ref = (j * (j + 1) - i * (i + 1)) / 2.0 if (i > j and (i - j) % 2 == 0) else 0.0
+            assert abs(K[j, i] - ref) < 1e-12
+
+
+@pytest.mark.parametrize("nx,nt", [(3, 3), (4, 4), (5, 3), (6, 6)])
+def test_constraint_ranks(nx, nt):
+    """Initial-time and end values meet at an element's two bottom corners (and, for two elements,
+    at the bottom of the shared boundary), so Nx + 2 Nt conditions have rank Nx + 2 Nt - 2; for
+    two elements 2 Nx + 3 Nt conditions have rank 2 Nx + 3 Nt - 3."""
+    assert np.linalg.matrix_rank(lfa.constraints(nx, nt, 1)) == nx + 2 * nt - 2
+    assert np.linalg.matrix_rank(lfa.constraints(nx, nt, 2)) == 2 * nx + 3 * nt - 3
+
+
+def test_unconstrained_relaxation_is_the_exact_solve():
+    """Without any condition the correction solves A delta = r exactly: the relaxed residual is 0."""
+    A = lfa.element_operator(4, 4, 1.0, 0.5)
+    C = lfa.project(4, 4, 1, lfa.plane_wave_overlaps(4, 4, 1, 1.3, -0.7))
+    C1 = lfa.relax(A, np.zeros((0, 16)), C)
+    assert np.linalg.norm(A @ C1) < 1e-12 * np.linalg.norm(A @ C)
+
+
+@pytest.mark.parametrize("nel", [1, 2])
+def test_null_space_solution_equals_the_bordered_system(nel):
+    """The Lagrange-multiplier system [A B^T; B 0] solved by least squares (minimum norm, which
+    copes with the repeated corner conditions) gives the same correction."""
+    nx, nt = 4, 3
+    A1 = lfa.element_operator(nx, nt, 0.1, -1.0)
+    A = A1 if nel == 1 else np.kron(np.eye(2), A1)
+    B = lfa.constraints(nx, nt, nel)
+    C = lfa.project(nx, nt, nel, lfa.plane_wave_overlaps(nx, nt, nel, 2.1, 0.4))
+    r = -A @ C
+    nc = B.shape[0]
+    kkt = np.block([[A, B.T.astype(complex)], [B.astype(complex), np.zeros((nc, nc))]])
+    sol = np.linalg.lstsq(kkt, np.concatenate([r, np.zeros(nc)]), rcond=None)[0]
+    assert np.linalg.norm(C + sol[:len(C)] - lfa.relax(A, B, C)) < 1e-11 * np.linalg.norm(C)
+
+
+@pytest.mark.parametrize("method", ["one", "two", "transfer"])
+def test_relaxation_keeps_initial_and_boundary_values(method):
+    nx, nt = 5, 4
+    nel = 1 if method == "one" else 2
+    C = lfa.project(nx, nt, nel, lfa.plane_wave_overlaps(nx, nt, nel, -1.7, 2.2))
+    C1 = lfa.relax_method(method, nx, nt, 1.0, 1.0, C)
+    B = lfa.constraints(nx, nt, nel)
+    assert np.linalg.norm(B @ (C1 - C)) < 1e-12 * np.linalg.norm(C)
+    assert np.linalg.norm(C1 - C) > 1e-3 * np.linalg.norm(C)
+
+
+def test_continuous_projection():
+    """Two elements: the projected trial is continuous at x = 0; a constant is reproduced exactly,
+    and the projection of a plane wave converges to it as Nx grows."""
+    B = lfa.constraints(4, 3, 2, left=False, right=False, initial=False)
+    C = lfa.project(4, 3, 2, lfa.plane_wave_overlaps(4, 3, 2, 2.5, 1.0))
+    assert np.linalg.norm(B @ C) < 1e-13 * np.linalg.norm(C)
+    C0 = lfa.project(4, 3, 2, lfa.plane_wave_overlaps(4, 3, 2, 0.0, 0.0))
+    ref = np.zeros(24)
+    ref[0] = ref[12] = 1.0
+    assert np.allclose(C0, ref, atol=1e-13)
+    # value at x = 0.5 (right child y' = 0), t = 0: sum_i C[i, n] P_i(0) P_n(0)
+    errs = []
+    for nx in (4, 6, 8):
+        C = lfa.project(nx, 8, 2, lfa.plane_wave_overlaps(nx, 8, 2, 2.5, 1.0))
+        Pi = le.legendre_P(nx - 1, np.array([0.0]))[:, 0]
+        Pn = le.legendre_P(7, np.array([0.0]))[:, 0]
+        v = Pi @ C[nx * 8:].reshape(nx, 8) @ Pn
+        errs.append(abs(v - np.exp(1j * 2.5 * 0.5)))
+    assert errs[2] < errs[1] < errs[0] and errs[2] < 1e-5
+
+
+def test_maps_follow_sec_v():
+    """Sec. V, qualitatively: a larger basis converges faster and shrinks the region where the
+    residual norm grows (ratio > 1); relaxing the two elements through the parent-element transfer
+    converges about as fast as relaxing both at once, and faster than one element alone."""
+    ks = np.linspace(-6, 6, 9)
+    ws = np.linspace(-6, 6, 9)
+    small, _ = lfa.ratio_map("one", 3, 3, 1.0, 0.0, ks, ws)
+    large, _ = lfa.ratio_map("one", 6, 6, 1.0, 0.0, ks, ws)
+    assert np.median(large) < np.median(small) - 0.5
+    assert np.mean(large > 0) < np.mean(small > 0)
+    one, _ = lfa.ratio_map("one", 5, 5, 1.0, 0.0, ks, ws)
+    two, _ = lfa.ratio_map("two", 5, 5, 1.0, 0.0, ks, ws)
+    tr, _ = lfa.ratio_map("transfer", 5, 5, 1.0, 0.0, ks, ws)
+    assert abs(np.median(tr) - np.median(two)) < 0.5
+    assert np.median(tr) < np.median(one)
