@@ -225,6 +225,34 @@ la_status la_profile_read(la_ctx* ctx, la_profile* out);
 la_status la_action_noalloc(const la_config* cfg, const double* V0, const la_pulse* pulse, const void* psi0,
                             double t0, const void* c, double* action, void* cuda_stream);
 
+/* Convergence maps of one relaxation step in the paper's Legendre-element basis (Secs. IV-V, the
+   plane-wave experiment).  An element is the box y, tau in [-1, 1] with Legendre functions P_i(y),
+   i < nx, and P_n(tau), n < nt, obeying the dimensionless least-action rows of
+   Eq. leastaction_dimensionless with (kappa, nu).  The trial function exp(i (k x + w t)) on
+   x, t in [-1, 1] is projected onto one element (method 0) or onto two elements [-1, 0], [0, 1]
+   continuously at x = 0 (methods 1, 2), and relaxed once: method 0 relaxes the element, method 1
+   both elements at once, method 2 corrects on the parent element through the Legendre transfers
+   (Eqs. residual_rough, correction_fine) and then relaxes each element alone.  A relaxation solves
+   the correction rows (Eq. leastaction_correction) with the correction held at zero at t0, at the
+   ends of the relaxed volume and continuous inside it, the conditions entering through Lagrange
+   multipliers. */
+typedef struct {
+  int method;           /* 0, 1 or 2 as above */
+  int nx, nt;           /* Legendre functions per element in space and in time, 2..8 */
+  double kappa, nu;     /* parameters of the dimensionless rows */
+} la_lfa_case;
+
+/* For every case c and grid point (w[a], k[b]):
+     out[((c * 2 + 0) * nw + a) * nk + b] = log10(N_after / N_before),  N = r^H (O x U) r (Eq. residnorm)
+     out[((c * 2 + 1) * nw + a) * nk + b] = log10(|S_after| / |S_before|),  S = the element action
+   cases: host array of ncases; k, w: host arrays of nk wavenumbers and nw frequencies; out: device or
+   host array of ncases * 2 * nw * nk doubles.  Per case the relaxation step, a linear map, is built on
+   the host (dense algebra on at most 128 coefficients) and the maps are evaluated on the GPU on
+   cuda_stream; synchronises before returning.  Errors: LA_EINVAL (bad case or grid, or a singular
+   relaxation system; message in la_last_error(NULL)), LA_ENOMEM, LA_ECUDA. */
+la_status la_lfa_maps(const la_lfa_case* cases, int ncases, const double* k, int nk, const double* w, int nw,
+                      void* out, void* cuda_stream);
+
 la_status la_finalize(la_ctx* ctx);
 const char* la_last_error(const la_ctx* ctx);
 const char* la_version(void);

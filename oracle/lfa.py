@@ -95,12 +95,21 @@ def null_space(B, tol=1e-12):
     return vh[rank:].conj().T
 
 
-def relax(A, B, C):
+def constrained_solve(A, B, r, solver="null"):
+    """delta with A delta + B^T lambda = r, B delta = 0.  solver "null": on the null space of B;
+    "bordered": least squares (minimum norm) on the bordered system [A B^T; B 0], a second
+    backward-stable route used to gauge how much rounding the problem itself amplifies."""
+    if solver == "null":
+        Z = null_space(B)
+        return Z @ np.linalg.solve(Z.T @ A @ Z, Z.T @ r)
+    nc = B.shape[0]
+    kkt = np.block([[A, B.T.astype(complex)], [B.astype(complex), np.zeros((nc, nc))]])
+    return np.linalg.lstsq(kkt, np.concatenate([r, np.zeros(nc)]), rcond=None)[0][:A.shape[0]]
+
+
+def relax(A, B, C, solver="null"):
     """C + delta for the constrained correction problem with residual r = -A C."""
-    Z = null_space(B)
-    r = -A @ C
-    z = np.linalg.solve(Z.T @ A @ Z, Z.T @ r)
-    return C + Z @ z
+    return C + constrained_solve(A, B, -A @ C, solver)
 
 
 def plane_wave_overlaps(nx, nt, nel, k, w, nquad=48):
@@ -133,33 +142,31 @@ def measures(A, W, C):
     return float(np.real(r.conj() @ (W @ r))), complex(C.conj() @ (A @ C))
 
 
-def relax_method(method, nx, nt, kappa, nu, C):
+def relax_method(method, nx, nt, kappa, nu, C, solver="null"):
     """One relaxation of the trial coefficients C by the given method."""
     A1 = element_operator(nx, nt, kappa, nu)
     if method == "one":
-        return relax(A1, constraints(nx, nt, 1), C)
+        return relax(A1, constraints(nx, nt, 1), C, solver)
     A2 = np.kron(np.eye(2), A1)
     if method == "two":
-        return relax(A2, constraints(nx, nt, 2), C)
+        return relax(A2, constraints(nx, nt, 2), C, solver)
     assert method == "transfer"
     # coarse correction on the parent element (spatial transfers; the time basis is shared)
     I = np.kron(le.interpolation(nx - 1), np.eye(nt))        # child coefficients of parent functions
     P = np.kron(le.projection(nx - 1), np.eye(nt))
     r = -A2 @ C
     Ac = P @ A2 @ I
-    Z = null_space(constraints(nx, nt, 1))
-    zc = np.linalg.solve(Z.T @ Ac @ Z, Z.T @ (P @ r))
-    C = C + I @ (Z @ zc)
+    C = C + I @ constrained_solve(Ac, constraints(nx, nt, 1), P @ r, solver)
     # then each child element on its own (delta = 0 on both of its ends)
     n = nx * nt
     B1 = constraints(nx, nt, 1)
     out = C.copy()
     for e in range(2):
-        out[e * n:(e + 1) * n] = relax(A1, B1, C[e * n:(e + 1) * n])
+        out[e * n:(e + 1) * n] = relax(A1, B1, C[e * n:(e + 1) * n], solver)
     return out
 
 
-def ratio_map(method, nx, nt, kappa, nu, ks, ws):
+def ratio_map(method, nx, nt, kappa, nu, ks, ws, solver="null"):
     """log10 N_after / N_before and log10 |S_after| / |S_before| on the (w, k) grid [len(ws), len(ks)]."""
     nel = 1 if method == "one" else 2
     A1 = element_operator(nx, nt, kappa, nu)
@@ -171,7 +178,7 @@ def ratio_map(method, nx, nt, kappa, nu, ks, ws):
         for b, k in enumerate(ks):
             C = project(nx, nt, nel, plane_wave_overlaps(nx, nt, nel, k, w))
             N0, S0 = measures(A, W, C)
-            N1, S1 = measures(A, W, relax_method(method, nx, nt, kappa, nu, C))
+            N1, S1 = measures(A, W, relax_method(method, nx, nt, kappa, nu, C, solver))
             lrN[a, b] = np.log10(N1 / N0)
             lrS[a, b] = np.log10(abs(S1) / abs(S0))
     return lrN, lrS

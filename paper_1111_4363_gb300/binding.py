@@ -21,6 +21,7 @@ LOCAL_FORMS = {"lsq": 0, "square": 1}
 
 EXPORTS = ["la_init", "la_set_hamiltonian", "la_step", "la_action", "la_solve_step", "la_residual",
            "la_relax_colour", "la_time_matrices", "la_backward", "la_step_batch", "la_profile_enable", "la_profile_read", "la_action_noalloc",
+           "la_lfa_maps",
            "la_finalize", "la_last_error", "la_version"]
 NOALLOC_MAX_POINTS = 1 << 22
 
@@ -158,6 +159,31 @@ def _pulse_struct(pulse):
             setattr(p, name, a.ctypes.data_as(C.POINTER(C.c_double)))
         p.ncomp = pulse.ncomp
     return p, keep
+
+
+class la_lfa_case(C.Structure):
+    _fields_ = [("method", C.c_int), ("nx", C.c_int), ("nt", C.c_int), ("kappa", C.c_double), ("nu", C.c_double)]
+
+
+LFA_METHODS = {"one": 0, "two": 1, "transfer": 2}
+
+
+def lfa_maps(cases, k, w, out=None, stream=None) -> np.ndarray:
+    """la_lfa_maps: cases = [(method, nx, nt, kappa, nu)], method a name of LFA_METHODS; returns (or fills
+    ``out``, host or device, shaped [ncases, 2, len(w), len(k)]) log10 ratios after / before of N and |S|."""
+    L = lib()
+    arr = (la_lfa_case * len(cases))()
+    for c, (method, nx, nt, kappa, nu) in enumerate(cases):
+        arr[c] = la_lfa_case(LFA_METHODS[method], nx, nt, kappa, nu)
+    k = np.ascontiguousarray(k, dtype=np.float64)
+    w = np.ascontiguousarray(w, dtype=np.float64)
+    if out is None:
+        out = np.zeros((len(cases), 2, len(w), len(k)))
+    st = L.la_lfa_maps(arr, len(cases), k.ctypes.data_as(C.POINTER(C.c_double)), len(k),
+                       w.ctypes.data_as(C.POINTER(C.c_double)), len(w), _ptr(out), _stream_handle(stream))
+    if st != LA_OK:
+        raise LeastActionError(st, L.la_last_error(None).decode())
+    return out
 
 
 def action_noalloc(cfg: la_config, V0, pulse, psi0, t0: float, c, stream=None) -> float:

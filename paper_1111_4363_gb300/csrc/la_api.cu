@@ -305,6 +305,7 @@ bool time_constants_for(const la_config& cfg, TimeMats& out) {
   return true;
 }
 void set_thread_error(const char* msg) { g_init_error = msg ? msg : "unknown error"; }
+void gauss_legendre_rule(int q, double* x, double* w) { gauss_legendre(q, x, w); }
 }  // namespace la
 
 extern "C" la_status la_init(const la_config* cfg, void* stream, la_ctx** out) {
