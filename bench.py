@@ -521,6 +521,72 @@ def run_3d_adjoint(args):
     print(json.dumps(out))
 
 
+LFA_SIZES = (3, 4, 6, 8)
+LFA_KAPPA_NU = [(0.0, 0.0), (0.1, 0.0), (1.0, 0.0), (10.0, 0.0), (0.0, 1.0), (0.0, -1.0), (1.0, 1.0), (1.0, -1.0)]
+
+
+def run_lfa(args):
+    """The paper's plane-wave experiment (Sec. V) in its Legendre-element basis: log10 ratios of the
+    residual norm and of |S| after one relaxation, for the 8 (kappa, nu) pairs of the paper's figures,
+    Nx = Nt in LFA_SIZES, one element, two elements at once and two through the parent-element transfer,
+    on a 256 x 256 (w, k) grid over [-8, 8]^2 (no point at k = w = 0, where N or S of the trial vanishes
+    for nu = 0).  value: relaxation evaluations (case x grid point) per second of la_lfa_maps with the maps
+    left on the device."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1111_4363_gb300 import binding as B
+    ng = 256
+    ks = np.linspace(-8.0, 8.0, ng)
+    ws = np.linspace(-8.0, 8.0, ng)
+    methods = ("one", "two", "transfer")
+    cases = [(m, s_, s_, kappa, nu) for m in methods for s_ in LFA_SIZES for kappa, nu in LFA_KAPPA_NU]
+    out = torch.empty((len(cases), 2, ng, ng), dtype=torch.float64, device="cuda")
+    for _ in range(max(args.warmup, 1)):
+        B.lfa_maps(cases, ks, ws, out=out)
+    torch.cuda.synchronize()
+    reps = max(1, min(args.steps, 5))
+    a = time.perf_counter()
+    for _ in range(reps):
+        B.lfa_maps(cases, ks, ws, out=out)
+    torch.cuda.synchronize()
+    el = (time.perf_counter() - a) / reps
+    host = np.empty((len(cases), 2, ng, ng))
+    a = time.perf_counter()
+    B.lfa_maps(cases, ks, ws, out=host)
+    el_e2e = time.perf_counter() - a
+    maps = out.cpu().numpy()
+    summary = {}
+    for m in methods:
+        for s_ in LFA_SIZES:
+            idx = [c for c, cs in enumerate(cases) if cs[0] == m and cs[1] == s_]
+            N = maps[idx, 0]
+            summary[f"{m}_{s_}x{s_}"] = {
+                "median_log10_N_ratio": round(float(np.median(N)), 3),
+                "fraction_N_ratio_above_1": round(float(np.mean(N > 0)), 4),
+                "median_log10_S_ratio": round(float(np.median(maps[idx, 1])), 3),
+                "fraction_N_ratio_above_1_per_pair": [round(float(np.mean(maps[c, 0] > 0)), 4) for c in idx]}
+    evals = len(cases) * ng * ng
+    res = {"metric": "relaxation evaluations/s", "value": evals / el, "unit": "evaluations/s", "n_gpus": 1,
+           "steps": reps, "warmup": max(args.warmup, 1), "ms_per_step": 1e3 * el, "higher_is_better": True,
+           "dtype": "f64", "data": "synthetic",
+           "config": {"workload": "legendre_element_maps", "grid": [ng, ng], "k_range": [-8, 8],
+                      "w_range": [-8, 8], "sizes": list(LFA_SIZES), "methods": list(methods),
+                      "kappa_nu": LFA_KAPPA_NU, "cases": len(cases)},
+           "e2e": {"value": evals / el_e2e, "unit": "evaluations/s", "h2d_bytes_per_step": 16 * ng,
+                   "d2h_bytes_per_step": 8 * evals * 2},
+           "summary": summary}
+    if not args.no_cpu_baseline:
+        from oracle import lfa
+        sub = np.linspace(-8.0, 8.0, 6)
+        a = time.perf_counter()
+        lfa.ratio_map("two", 6, 6, 1.0, 0.0, sub, sub)
+        dt_o = time.perf_counter() - a
+        res["cpu_baseline"] = {"value": sub.size ** 2 / dt_o, "unit": "evaluations/s", "cores": 1,
+                               "kind": "oracle", "sample": "two elements, Nx = Nt = 6, kappa 1, nu 0, 6 x 6 points"}
+    print(json.dumps(res))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -528,7 +594,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="2d",
-                    choices=["2d", "2d-small", "1d", "2d-square", "batched", "3d-adjoint"])
+                    choices=["2d", "2d-small", "1d", "2d-square", "batched", "3d-adjoint", "lfa"])
     ap.add_argument("--batch", type=int, default=512)
     ap.add_argument("--n3d", type=int, default=128)
     ap.add_argument("--precision", type=int, default=0, choices=[0, 1])
@@ -542,6 +608,8 @@ def main():
         run_batched(args)
     elif args.workload == "3d-adjoint":
         run_3d_adjoint(args)
+    elif args.workload == "lfa":
+        run_lfa(args)
     else:
         run_ours(args)
 
