@@ -285,15 +285,22 @@ k_factor(LevelGeom L, FineOp g, int is_fine, int nptsmax, const double* __restri
 // memory k-major, and every trailing block then takes one rank-16 update from it (row reads are
 // broadcasts, column reads are consecutive), so the per-entry bookkeeping is paid once per 16
 // columns instead of once per column.
-// complex64 matrices per CTA: small ones share the column barriers (their per-thread register tiles
-// stay small: NT = 3 complex for NPAD 32, 6 for NPAD 48).
+// Matrices per CTA of the blocked factorisation: small ones share the column barriers (their
+// per-thread register tiles stay small: NT = 3 complex for NPAD 32, 6 for NPAD 48).
 __host__ __device__ constexpr int factor_c64_mpc(int npad) { return npad <= 32 ? 4 : (npad <= 48 ? 2 : 1); }
 
-template <int NPAD>
-__global__ void __launch_bounds__(kFactorThreads, 2)
-k_factor_c64(LevelGeom L, FineOp g, int is_fine, int nptsmax, const double* __restrict__ sigma,
-             const TimeMats* __restrict__ tm, float2* __restrict__ factors, int* __restrict__ status) {
-  typedef float2 CT;
+__device__ __forceinline__ float rsq(float x) { return rsqrtf(x); }
+__device__ __forceinline__ double rsq(double x) { return rsqrt(x); }
+
+// The blocked factorisation, written for a precision R; the mixed path runs it in complex64 (two
+// CTAs per SM).  In complex128 its register tiles allow one CTA per SM, and measured slower than the
+// shared-memory factorisation above (NPAD 96 at 256 x 256: 9.4 ms against 5.7 ms), so the FP64
+// path does not use it.
+template <typename R, int NPAD>
+__global__ void __launch_bounds__(kFactorThreads, sizeof(R) == 4 ? 2 : 1)
+k_factor_blk(LevelGeom L, FineOp g, int is_fine, int nptsmax, const double* __restrict__ sigma,
+             const TimeMats* __restrict__ tm, typename C2<R>::T* __restrict__ factors, int* __restrict__ status) {
+  typedef typename C2<R>::T CT;
   constexpr int NB = NPAD / LA_BLK;
   constexpr int NT = NB * (NB + 1) / 2;
   constexpr int MPC = factor_c64_mpc(NPAD);
@@ -302,11 +309,11 @@ k_factor_c64(LevelGeom L, FineOp g, int is_fine, int nptsmax, const double* __re
   const int nv = is_fine ? 2 : LA_NPAIR;
   const int pstride = nptsmax * nptsmax * nv;
   CT* sPan = reinterpret_cast<CT*>(smem);                          // [MPC][LA_BLK][NPAD] finished panel, k-major
-  float* sInv = reinterpret_cast<float*>(sPan + MPC * LA_BLK * NPAD); // [MPC][NPAD]
+  R* sInv = reinterpret_cast<R*>(sPan + MPC * LA_BLK * NPAD);     // [MPC][NPAD]
   CT* sDiag = reinterpret_cast<CT*>(sInv + MPC * NPAD);             // [MPC][NB][256]
-  float* sP = reinterpret_cast<float*>(sDiag + MPC * NB * 256);     // [9][K*K]
-  float* sPair = sP + LA_NPAIR * LA_KMAX * LA_KMAX;                 // [MPC][npts*npts][nv]
-  float* sX = sPair + (size_t)MPC * pstride;                        // [MPC][npts] laser coordinate (finest)
+  R* sP = reinterpret_cast<R*>(sDiag + MPC * NB * 256);             // [9][K*K]
+  R* sPair = sP + LA_NPAIR * LA_KMAX * LA_KMAX;                     // [MPC][npts*npts][nv]
+  R* sX = sPair + (size_t)MPC * pstride;                            // [MPC][npts] laser coordinate (finest)
 
   const int tid = threadIdx.x, ti = tid >> 4, tk = tid & 15;
   // the CTA's matrices; slots past the last subvolume factorise an identity and store nothing
@@ -323,8 +330,8 @@ k_factor_c64(LevelGeom L, FineOp g, int is_fine, int nptsmax, const double* __re
       npts_[mi] = 0;
     }
   }
-  for (int i = tid; i < LA_NPAIR * KK; i += kFactorThreads) sP[i] = (float)tm->P[i / KK][i % KK];
-  for (int i = tid; i < MPC * NB * 256; i += kFactorThreads) sDiag[i] = make_float2(0.f, 0.f);
+  for (int i = tid; i < LA_NPAIR * KK; i += kFactorThreads) sP[i] = (R)tm->P[i / KK][i % KK];
+  for (int i = tid; i < MPC * NB * 256; i += kFactorThreads) sDiag[i] = mkc<CT>(0, 0);
   const int nbox = box5_count(L.dim);
 #pragma unroll
   for (int mi = 0; mi < MPC; ++mi) {
@@ -335,7 +342,7 @@ k_factor_c64(LevelGeom L, FineOp g, int is_fine, int nptsmax, const double* __re
       for (int i = tid; i < npts; i += kFactorThreads) {
         int ix, iy, iz;
         local_coords(i, e, ix, iy, iz);
-        sX[mi * nptsmax + i] = (float)fine_x(g, o[0] + ix, o[1] + iy, o[2] + iz);
+        sX[mi * nptsmax + i] = (R)fine_x(g, o[0] + ix, o[1] + iy, o[2] + iz);
       }
     for (int t = tid; t < npts * npts; t += kFactorThreads) {
       const int i = t / npts, j = t % npts;
@@ -344,18 +351,18 @@ k_factor_c64(LevelGeom L, FineOp g, int is_fine, int nptsmax, const double* __re
       local_coords(j, e, jx, jy, jz);
       const int px = o[0] + ix, py = o[1] + iy, pz = o[2] + iz;
       const int qx = o[0] + jx, qy = o[1] + jy, qz = o[2] + jz;
-      float* dst = sPair + (size_t)mi * pstride + (size_t)t * nv;
+      R* dst = sPair + (size_t)mi * pstride + (size_t)t * nv;
       if (is_fine) {
         double s9[LA_NPAIR];
         fine_sigma(g, px, py, pz, qx, qy, qz, s9);
-        dst[0] = (float)s9[1];
-        dst[1] = (float)s9[4];
+        dst[0] = (R)s9[1];
+        dst[1] = (R)s9[4];
       } else {
         const int dx = qx - px, dy = qy - py, dz = qz - pz;
         const bool near = abs(dx) <= 2 && abs(dy) <= 2 && abs(dz) <= 2;
         const int p = (pz * L.n[1] + py) * L.n[0] + px;
         const int ofs = near ? box5_index(L.dim, dx, dy, dz) : 0;
-        for (int k = 0; k < LA_NPAIR; ++k) dst[k] = near ? (float)sigma[sigma_offset(p, k, ofs, nbox)] : 0.f;
+        for (int k = 0; k < LA_NPAIR; ++k) dst[k] = near ? (R)sigma[sigma_offset(p, k, ofs, nbox)] : (R)0;
       }
     }
   }
@@ -370,18 +377,18 @@ k_factor_c64(LevelGeom L, FineOp g, int is_fine, int nptsmax, const double* __re
 #pragma unroll
       for (int J = 0; J <= I; ++J) {
         const int r = LA_BLK * I + ti, c = LA_BLK * J + tk;
-        // assembled in FP32: this factor only preconditions the FP64-refined iteration
-        float re = 0.f, im = 0.f;
+        // assembled in R (complex64: this factor only preconditions the FP64-refined iteration)
+        R re = 0, im = 0;
         if (I == J && ti < tk) {
         } else if (r >= n || c >= n) {
-          re = (r == c) ? 1.f : 0.f;
+          re = (r == c) ? (R)1 : (R)0;
         } else {
           const int i = r / K, mm = r % K, j = c / K, nn = c % K;
-          float s9[LA_NPAIR];
-          const float* pr = sPair + (size_t)mi * pstride + (size_t)(i * npts + j) * nv;
+          R s9[LA_NPAIR];
+          const R* pr = sPair + (size_t)mi * pstride + (size_t)(i * npts + j) * nv;
           if (is_fine) {
-            const float xp = sX[mi * nptsmax + i], xq = sX[mi * nptsmax + j];
-            const float same = (i == j) ? 1.f : 0.f, Hpq = pr[0];
+            const R xp = sX[mi * nptsmax + i], xq = sX[mi * nptsmax + j];
+            const R same = (i == j) ? (R)1 : (R)0, Hpq = pr[0];
             s9[0] = same; s9[1] = Hpq; s9[2] = same * xp; s9[3] = Hpq; s9[4] = pr[1];
             s9[5] = Hpq * xq; s9[6] = same * xp; s9[7] = xp * Hpq; s9[8] = same * xp * xp;
           } else {
@@ -390,22 +397,22 @@ k_factor_c64(LevelGeom L, FineOp g, int is_fine, int nptsmax, const double* __re
           }
 #pragma unroll
           for (int kk = 0; kk < LA_NPAIR; ++kk) {
-            const float v = s9[kk] * sP[kk * KK + mm * K + nn];
+            const R v = s9[kk] * sP[kk * KK + mm * K + nn];
             const int ph = theta_phase(kk);
             if (ph == 0) re += v; else if (ph == 1) im += v; else im -= v;
           }
         }
-        a[mi][I * (I + 1) / 2 + J] = make_float2(re, im);
+        a[mi][I * (I + 1) / 2 + J] = mkc<CT>(re, im);
       }
     }
   }
   if (tid == 0) {
 #pragma unroll
     for (int mi = 0; mi < MPC; ++mi) {
-      float d2 = a[mi][0].x;
-      if (!(d2 > 0.f)) { atomicOr(status, 1); d2 = 1.f; }
-      const float inv = rsqrtf(d2);
-      a[mi][0] = make_float2(d2 * inv, 0.f);
+      R d2 = a[mi][0].x;
+      if (!(d2 > (R)0)) { atomicOr(status, 1); d2 = (R)1; }
+      const R inv = rsq(d2);
+      a[mi][0] = mkc<CT>(d2 * inv, 0);
       sInv[mi * NPAD] = inv;
     }
   }
@@ -420,7 +427,7 @@ k_factor_c64(LevelGeom L, FineOp g, int is_fine, int nptsmax, const double* __re
       if (tk == jj) {
 #pragma unroll
         for (int mi = 0; mi < MPC; ++mi) {
-          const float inv = sInv[mi * NPAD + j];
+          const R inv = sInv[mi * NPAD + j];
           CT* pan = sPan + (size_t)mi * LA_BLK * NPAD;
 #pragma unroll
           for (int I = J0; I < NB; ++I) {
@@ -448,16 +455,16 @@ k_factor_c64(LevelGeom L, FineOp g, int is_fine, int nptsmax, const double* __re
             if (r >= c0) {
               const CT xr = pan[jj * NPAD + r];
               CT& v = a[mi][I * (I + 1) / 2 + J0];
-              v.x = fmaf(-xr.x, y.x, v.x); v.x = fmaf(-xr.y, y.y, v.x);
-              v.y = fmaf(-xr.y, y.x, v.y); v.y = fmaf(xr.x, y.y, v.y);
+              v.x = fma(-xr.x, y.x, v.x); v.x = fma(-xr.y, y.y, v.x);
+              v.y = fma(-xr.y, y.x, v.y); v.y = fma(xr.x, y.y, v.y);
             }
           }
           if (ti == jj + 1 && tk == jj + 1) {
             CT& v = a[mi][J0 * (J0 + 1) / 2 + J0];
-            float d2 = v.x;
-            if (!(d2 > 0.f)) { atomicOr(status, 1); d2 = 1.f; }
-            const float inv = rsqrtf(d2);
-            v = make_float2(d2 * inv, 0.f);
+            R d2 = v.x;
+            if (!(d2 > (R)0)) { atomicOr(status, 1); d2 = (R)1; }
+            const R inv = rsq(d2);
+            v = mkc<CT>(d2 * inv, 0);
             sInv[mi * NPAD + j + 1] = inv;
           }
         }
@@ -482,8 +489,8 @@ k_factor_c64(LevelGeom L, FineOp g, int is_fine, int nptsmax, const double* __re
 #pragma unroll
             for (int J = J0 + 1; J <= I; ++J) {
               CT& v = a[mi][I * (I + 1) / 2 + J];
-              v.x = fmaf(-xr[I].x, yc[J].x, v.x); v.x = fmaf(-xr[I].y, yc[J].y, v.x);
-              v.y = fmaf(-xr[I].y, yc[J].x, v.y); v.y = fmaf(xr[I].x, yc[J].y, v.y);
+              v.x = fma(-xr[I].x, yc[J].x, v.x); v.x = fma(-xr[I].y, yc[J].y, v.x);
+              v.y = fma(-xr[I].y, yc[J].x, v.y); v.y = fma(xr[I].x, yc[J].y, v.y);
             }
         }
       }
@@ -491,10 +498,10 @@ k_factor_c64(LevelGeom L, FineOp g, int is_fine, int nptsmax, const double* __re
 #pragma unroll
         for (int mi = 0; mi < MPC; ++mi) {
           CT& v = a[mi][(J0 + 1) * (J0 + 2) / 2 + J0 + 1];
-          float d2 = v.x;
-          if (!(d2 > 0.f)) { atomicOr(status, 1); d2 = 1.f; }
-          const float inv = rsqrtf(d2);
-          v = make_float2(d2 * inv, 0.f);
+          R d2 = v.x;
+          if (!(d2 > (R)0)) { atomicOr(status, 1); d2 = (R)1; }
+          const R inv = rsq(d2);
+          v = mkc<CT>(d2 * inv, 0);
           sInv[mi * NPAD + LA_BLK * (J0 + 1)] = inv;
         }
       }
@@ -504,7 +511,7 @@ k_factor_c64(LevelGeom L, FineOp g, int is_fine, int nptsmax, const double* __re
 
 #pragma unroll
   for (int mi = 0; mi < MPC; ++mi) {
-    float2* F = factors + (size_t)bsv[mi] * L.fsize;
+    CT* F = factors + (size_t)bsv[mi] * L.fsize;
     const bool store = bsv[mi] < L.nsub;
 #pragma unroll
     for (int I = 0; I < NB; ++I)
@@ -526,20 +533,20 @@ k_factor_c64(LevelGeom L, FineOp g, int is_fine, int nptsmax, const double* __re
     for (int u = 0; u < MPC; ++u) if (u == mi) bm = bsv[u];
     if (bm < L.nsub) {
       const CT* Ld = sDiag + (mi * NB + I) * 256;
-      const float* Inv = sInv + mi * NPAD;
+      const R* Inv = sInv + mi * NPAD;
       CT x[LA_BLK];
 #pragma unroll
       for (int i = 0; i < LA_BLK; ++i) {
-        CT acc = make_float2(0.f, 0.f);
+        CT acc = mkc<CT>(0, 0);
 #pragma unroll
         for (int k = 0; k < i; ++k)
           if (k >= jj) cfma(acc, Ld[i * LA_BLK + k], x[k]);
-        const float rinv = Inv[base + i];
-        if (i < jj) x[i] = make_float2(0.f, 0.f);
-        else if (i == jj) x[i] = make_float2(rinv, 0.f);
-        else x[i] = make_float2(-acc.x * rinv, -acc.y * rinv);
+        const R rinv = Inv[base + i];
+        if (i < jj) x[i] = mkc<CT>(0, 0);
+        else if (i == jj) x[i] = mkc<CT>(rinv, 0);
+        else x[i] = mkc<CT>(-acc.x * rinv, -acc.y * rinv);
       }
-      float2* D = factors + (size_t)bm * L.fsize + (size_t)(I * (I + 1) / 2 + I) * 256;
+      CT* D = factors + (size_t)bm * L.fsize + (size_t)(I * (I + 1) / 2 + I) * 256;
 #pragma unroll
       for (int i = 0; i < LA_BLK; ++i) D[i * LA_BLK + jj] = x[i];
     }
@@ -1131,15 +1138,16 @@ inline size_t sweep_coarse_smem(const LevelGeom& L, int K, size_t rsize, size_t 
          csize * (coarse_box_count(L) * K + nptsmax * LA_NPAIR * K + 2 * (size_t)L.npad + LA_BLK + 128);
 }
 
-template <int NPAD>
-cudaError_t launch_factor_c64_n(const LevelGeom& L, const FineOp* fine, const double* sigma, const TimeMats* tm,
-                                float2* factors, int* status, cudaStream_t s) {
+template <typename R, int NPAD>
+cudaError_t launch_factor_blk_n(const LevelGeom& L, const FineOp* fine, const double* sigma, const TimeMats* tm,
+                                typename C2<R>::T* factors, int* status, cudaStream_t s) {
+  typedef typename C2<R>::T CT;
   const int nptsmax = L.sub[0] * L.sub[1] * L.sub[2];
   constexpr int mpc = factor_c64_mpc(NPAD);
-  const size_t smem = mpc * (sizeof(float2) * ((size_t)LA_BLK * NPAD + (size_t)(NPAD / LA_BLK) * 256) + sizeof(float) * NPAD) +
-                      sizeof(float) * (LA_NPAIR * LA_KMAX * LA_KMAX +
-                                       mpc * ((size_t)nptsmax * nptsmax * (fine ? 2 : LA_NPAIR) + nptsmax));
-  auto kern = k_factor_c64<NPAD>;
+  const size_t smem = mpc * (sizeof(CT) * ((size_t)LA_BLK * NPAD + (size_t)(NPAD / LA_BLK) * 256) + sizeof(R) * NPAD) +
+                      sizeof(R) * (LA_NPAIR * LA_KMAX * LA_KMAX +
+                                   mpc * ((size_t)nptsmax * nptsmax * (fine ? 2 : LA_NPAIR) + nptsmax));
+  auto kern = k_factor_blk<R, NPAD>;
   static bool attr_set = false;
   if (!attr_set) {
     cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);

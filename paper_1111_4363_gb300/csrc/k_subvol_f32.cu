@@ -4,7 +4,7 @@ namespace la {
 template <>
 cudaError_t launch_factor<float>(const LevelGeom& L, const FineOp* fine, const double* sigma, const TimeMats* tm,
                                   float2* factors, int* status, cudaStream_t s) {
-#define LA_CALL(N) launch_factor_c64_n<N>(L, fine, sigma, tm, factors, status, s)
+#define LA_CALL(N) launch_factor_blk_n<float, N>(L, fine, sigma, tm, factors, status, s)
   LA_NPAD_DISPATCH(L.npad, LA_CALL)
 #undef LA_CALL
 }
