@@ -23,6 +23,7 @@
 #include <complex>
 #include <cstring>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "../../include/leastaction.h"
@@ -460,16 +461,38 @@ extern "C" la_status la_lfa_maps(const la_lfa_case* cases, int ncases, const dou
   cudaGetLastError();
   double qy[kLfaQuad], qw[kLfaQuad];
   gauss_legendre_rule(kLfaQuad, qy, qw);
-  // device buffers: grid, rule, overlaps, forms, contracted forms, maps (when out is on the host)
-  size_t gmax = 0;
+  // the cases' step matrices, built on host threads (independent dense algebra per case)
   std::vector<CaseForms> forms(ncases);
-  for (int c = 0; c < ncases; ++c) {
-    std::string why;
-    if (!build_case(cases[c], forms[c], why)) {
-      set_thread_error(("la_lfa_maps: case " + std::to_string(c) + ": " + why).c_str());
+  std::vector<std::string> why(ncases);
+  std::vector<char> ok(ncases, 0);
+  {
+    const int nth = std::max(1, std::min(ncases, std::min(32, (int)std::thread::hardware_concurrency())));
+    std::vector<std::thread> pool;
+    for (int t = 0; t < nth; ++t)
+      pool.emplace_back([&, t]() {
+        for (int c = t; c < ncases; c += nth) ok[c] = build_case(cases[c], forms[c], why[c]) ? 1 : 0;
+      });
+    for (auto& th : pool) th.join();
+  }
+  for (int c = 0; c < ncases; ++c)
+    if (!ok[c]) {
+      set_thread_error(("la_lfa_maps: case " + std::to_string(c) + ": " + why[c]).c_str());
       return LA_EINVAL;
     }
-    gmax = std::max(gmax, forms[c].G.size());
+  // all cases' matrices and weights in one upload (offsets in elements, 256-byte aligned)
+  std::vector<size_t> goff(ncases), woff(ncases);
+  size_t gtot = 0, wtot = 0;
+  for (int c = 0; c < ncases; ++c) {
+    goff[c] = gtot;
+    gtot += (forms[c].G.size() + 15) & ~(size_t)15;
+    woff[c] = wtot;
+    wtot += (forms[c].W.size() + 31) & ~(size_t)31;
+  }
+  std::vector<double2> Gall(gtot);
+  std::vector<double> Wall(wtot);
+  for (int c = 0; c < ncases; ++c) {
+    std::copy(forms[c].G.begin(), forms[c].G.end(), Gall.begin() + goff[c]);
+    std::copy(forms[c].W.begin(), forms[c].W.end(), Wall.begin() + woff[c]);
   }
   void* buf = nullptr;
   // every sub-array starts on a 256-byte boundary (double2 accesses need 16-byte alignment)
@@ -478,8 +501,8 @@ extern "C" la_status la_lfa_maps(const la_lfa_case* cases, int ncases, const dou
   const size_t off_qw = up(off_qy + kLfaQuad * sizeof(double)), off_a = up(off_qw + kLfaQuad * sizeof(double));
   const size_t off_b = up(off_a + (size_t)nk * kLfaMaxP * sizeof(double2));
   const size_t off_g = up(off_b + (size_t)nw * 8 * sizeof(double2));
-  const size_t off_wt = up(off_g + gmax * sizeof(double2));
-  const size_t off_h = up(off_wt + 128 * sizeof(double));
+  const size_t off_wt = up(off_g + gtot * sizeof(double2));
+  const size_t off_h = up(off_wt + wtot * sizeof(double));
   const size_t off_o = up(off_h + (size_t)nw * 4 * 128 * kLfaMaxP * sizeof(double2));
   const size_t total = off_o + (out_dev ? 0 : map_doubles * ncases * sizeof(double));
   if (cudaMalloc(&buf, total) != cudaSuccess) {
@@ -492,29 +515,35 @@ extern "C" la_status la_lfa_maps(const la_lfa_case* cases, int ncases, const dou
   if (e == cudaSuccess) e = cudaMemcpyAsync(B + off_w, w, nw * sizeof(double), cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess) e = cudaMemcpyAsync(B + off_qy, qy, sizeof(qy), cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess) e = cudaMemcpyAsync(B + off_qw, qw, sizeof(qw), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(B + off_g, Gall.data(), gtot * sizeof(double2), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(B + off_wt, Wall.data(), wtot * sizeof(double), cudaMemcpyHostToDevice, s);
   double* maps = out_dev ? static_cast<double*>(out) : reinterpret_cast<double*>(B + off_o);
+  double2* a = reinterpret_cast<double2*>(B + off_a);
+  double2* b = reinterpret_cast<double2*>(B + off_b);
+  double2* H = reinterpret_cast<double2*>(B + off_h);
+  // the overlap tables and the contracted matrices are reused case after case in stream order
+  int tab_nel = 0, tab_nx = 0, tab_nt = 0;
   for (int c = 0; c < ncases && e == cudaSuccess; ++c) {
     const CaseForms& F = forms[c];
     const int np = F.nel * F.nx;
-    double2* a = reinterpret_cast<double2*>(B + off_a);
-    double2* b = reinterpret_cast<double2*>(B + off_b);
-    double2* G = reinterpret_cast<double2*>(B + off_g);
-    double2* H = reinterpret_cast<double2*>(B + off_h);
-    double* Wt = reinterpret_cast<double*>(B + off_wt);
-    // the host forms stay alive until the stream has consumed them: synchronise per case
-    e = cudaMemcpyAsync(G, F.G.data(), F.G.size() * sizeof(double2), cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(Wt, F.W.data(), F.W.size() * sizeof(double), cudaMemcpyHostToDevice, s);
-    if (e != cudaSuccess) break;
-    k_lfa_overlaps<<<(nk + nw + 127) / 128, 128, 0, s>>>(reinterpret_cast<double*>(B + off_k), nk,
-                                                         reinterpret_cast<double*>(B + off_w), nw,
-                                                         reinterpret_cast<double*>(B + off_qy),
-                                                         reinterpret_cast<double*>(B + off_qw), F.nel, F.nx, F.nt, a, b);
+    const double2* G = reinterpret_cast<const double2*>(B + off_g) + goff[c];
+    const double* Wt = reinterpret_cast<const double*>(B + off_wt) + woff[c];
+    if (F.nel != tab_nel || F.nx != tab_nx || F.nt != tab_nt) {
+      k_lfa_overlaps<<<(nk + nw + 127) / 128, 128, 0, s>>>(reinterpret_cast<double*>(B + off_k), nk,
+                                                           reinterpret_cast<double*>(B + off_w), nw,
+                                                           reinterpret_cast<double*>(B + off_qy),
+                                                           reinterpret_cast<double*>(B + off_qw), F.nel, F.nx, F.nt,
+                                                           a, b);
+      tab_nel = F.nel;
+      tab_nx = F.nx;
+      tab_nt = F.nt;
+    }
     k_lfa_time<<<nw, 256, 0, s>>>(G, b, F.n, np, F.nt, H);
     const size_t smem = (size_t)4 * F.n * np * sizeof(double2) + F.n * sizeof(double);
     k_lfa_eval<<<dim3((nk + 127) / 128, nw), 128, smem, s>>>(H, Wt, a, nk, nw, F.n, np,
                                                             maps + (size_t)c * map_doubles);
     e = cudaGetLastError();
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   }
   if (e == cudaSuccess && !out_dev)
     e = cudaMemcpyAsync(out, maps, map_doubles * ncases * sizeof(double), cudaMemcpyDeviceToHost, s);
