@@ -62,14 +62,13 @@ __host__ __device__ constexpr int tri_index(int r, int c) { return r * (r + 1) /
 // they share the two barriers per column.
 __host__ __device__ constexpr int factor_mpc(int npad) { return npad <= 32 ? 8 : (npad <= 64 ? 2 : 1); }
 
-template <typename R, int NPAD>
+template <typename R, int NPAD, int MPC>
 __global__ void __launch_bounds__(kFactorThreads, 2)
 k_factor(LevelGeom L, FineOp g, int is_fine, int nptsmax, const double* __restrict__ sigma,
          const TimeMats* __restrict__ tm, typename C2<R>::T* __restrict__ factors, int* __restrict__ status) {
   typedef typename C2<R>::T CT;
   constexpr int NTRI = NPAD * (NPAD + 1) / 2;
   constexpr int NB = NPAD / LA_BLK;
-  constexpr int MPC = factor_mpc(NPAD);
   extern __shared__ __align__(16) unsigned char smem[];
   const int K = tm->K, KK = K * K;
   const int npair_max = nptsmax * (nptsmax + 1) / 2;
@@ -296,14 +295,13 @@ __device__ __forceinline__ double rsq(double x) { return rsqrt(x); }
 // CTAs per SM).  In complex128 its register tiles allow one CTA per SM, and measured slower than the
 // shared-memory factorisation above (NPAD 96 at 256 x 256: 9.4 ms against 5.7 ms), so the FP64
 // path does not use it.
-template <typename R, int NPAD>
+template <typename R, int NPAD, int MPC>
 __global__ void __launch_bounds__(kFactorThreads, sizeof(R) == 4 ? 2 : 1)
 k_factor_blk(LevelGeom L, FineOp g, int is_fine, int nptsmax, const double* __restrict__ sigma,
              const TimeMats* __restrict__ tm, typename C2<R>::T* __restrict__ factors, int* __restrict__ status) {
   typedef typename C2<R>::T CT;
   constexpr int NB = NPAD / LA_BLK;
   constexpr int NT = NB * (NB + 1) / 2;
-  constexpr int MPC = factor_c64_mpc(NPAD);
   extern __shared__ __align__(16) unsigned char smem[];
   const int K = tm->K, KK = K * K;
   const int nv = is_fine ? 2 : LA_NPAIR;
@@ -1119,11 +1117,17 @@ k_gresid_tiles(LevelGeom L, const double* __restrict__ sigma, const TimeMats* __
 }
 
 // ======================================================================== host dispatch
-inline size_t factor_smem(const LevelGeom& L, int nptsmax, size_t csize, bool fine) {
+// Several matrices per CTA only on levels of at least 512 subvolumes; a level with fewer (a small
+// grid such as the 1D workload's 8) runs one matrix per CTA, so that its few matrices are
+// factorised side by side instead of one after another in a single CTA.  (Per context: the
+// batched workload's grids of 512 and more subvolumes, running concurrently, keep the grouping.)
+constexpr int kFactorMultiMin = 512;
+inline int factor_grid_mpc(const LevelGeom& L, int mpc) { return L.nsub >= kFactorMultiMin ? mpc : 1; }
+
+inline size_t factor_smem(const LevelGeom& L, int nptsmax, size_t csize, int mpc_) {
   const size_t ntri = (size_t)L.npad * (L.npad + 1) / 2;
   const size_t npair = (size_t)nptsmax * (nptsmax + 1) / 2;
-  const size_t mpc = (size_t)factor_mpc(L.npad);
-  (void)fine;
+  const size_t mpc = (size_t)mpc_;
   return mpc * (csize * (ntri + L.npad) + (size_t)L.npad * (csize / 2)) +
          sizeof(double) * (LA_NPAIR * LA_KMAX * LA_KMAX + mpc * npair * LA_NPAIR) + sizeof(int) * (mpc * npair + 1);
 }
@@ -1138,16 +1142,15 @@ inline size_t sweep_coarse_smem(const LevelGeom& L, int K, size_t rsize, size_t 
          csize * (coarse_box_count(L) * K + nptsmax * LA_NPAIR * K + 2 * (size_t)L.npad + LA_BLK + 128);
 }
 
-template <typename R, int NPAD>
-cudaError_t launch_factor_blk_n(const LevelGeom& L, const FineOp* fine, const double* sigma, const TimeMats* tm,
+template <typename R, int NPAD, int mpc>
+cudaError_t launch_factor_blk_m(const LevelGeom& L, const FineOp* fine, const double* sigma, const TimeMats* tm,
                                 typename C2<R>::T* factors, int* status, cudaStream_t s) {
   typedef typename C2<R>::T CT;
   const int nptsmax = L.sub[0] * L.sub[1] * L.sub[2];
-  constexpr int mpc = factor_c64_mpc(NPAD);
   const size_t smem = mpc * (sizeof(CT) * ((size_t)LA_BLK * NPAD + (size_t)(NPAD / LA_BLK) * 256) + sizeof(R) * NPAD) +
                       sizeof(R) * (LA_NPAIR * LA_KMAX * LA_KMAX +
                                    mpc * ((size_t)nptsmax * nptsmax * (fine ? 2 : LA_NPAIR) + nptsmax));
-  auto kern = k_factor_blk<R, NPAD>;
+  auto kern = k_factor_blk<R, NPAD, mpc>;
   static bool attr_set = false;
   if (!attr_set) {
     cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
@@ -1161,11 +1164,20 @@ cudaError_t launch_factor_blk_n(const LevelGeom& L, const FineOp* fine, const do
 }
 
 template <typename R, int NPAD>
-cudaError_t launch_factor_n(const LevelGeom& L, const FineOp* fine, const double* sigma, const TimeMats* tm,
+cudaError_t launch_factor_blk_n(const LevelGeom& L, const FineOp* fine, const double* sigma, const TimeMats* tm,
+                                typename C2<R>::T* factors, int* status, cudaStream_t s) {
+  constexpr int mpc = factor_c64_mpc(NPAD);
+  if (mpc > 1 && factor_grid_mpc(L, mpc) == 1)
+    return launch_factor_blk_m<R, NPAD, 1>(L, fine, sigma, tm, factors, status, s);
+  return launch_factor_blk_m<R, NPAD, mpc>(L, fine, sigma, tm, factors, status, s);
+}
+
+template <typename R, int NPAD, int mpc>
+cudaError_t launch_factor_m(const LevelGeom& L, const FineOp* fine, const double* sigma, const TimeMats* tm,
                             typename C2<R>::T* factors, int* status, cudaStream_t s) {
   const int nptsmax = L.sub[0] * L.sub[1] * L.sub[2];
-  const size_t smem = factor_smem(L, nptsmax, sizeof(typename C2<R>::T), fine != nullptr);
-  auto kern = k_factor<R, NPAD>;
+  const size_t smem = factor_smem(L, nptsmax, sizeof(typename C2<R>::T), mpc);
+  auto kern = k_factor<R, NPAD, mpc>;
   static bool attr_set = false;
   if (!attr_set) {
     cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
@@ -1174,9 +1186,16 @@ cudaError_t launch_factor_n(const LevelGeom& L, const FineOp* fine, const double
   }
   if (smem > 227 * 1024) return cudaErrorInvalidValue;
   FineOp g = fine ? *fine : FineOp{};
-  constexpr int mpc = factor_mpc(NPAD);
   kern<<<(L.nsub + mpc - 1) / mpc, kFactorThreads, smem, s>>>(L, g, fine ? 1 : 0, nptsmax, sigma, tm, factors, status);
   return cudaGetLastError();
+}
+template <typename R, int NPAD>
+cudaError_t launch_factor_n(const LevelGeom& L, const FineOp* fine, const double* sigma, const TimeMats* tm,
+                            typename C2<R>::T* factors, int* status, cudaStream_t s) {
+  constexpr int mpc = factor_mpc(NPAD);
+  if (mpc > 1 && factor_grid_mpc(L, mpc) == 1)
+    return launch_factor_m<R, NPAD, 1>(L, fine, sigma, tm, factors, status, s);
+  return launch_factor_m<R, NPAD, mpc>(L, fine, sigma, tm, factors, status, s);
 }
 template <typename R, int NPAD>
 cudaError_t launch_sweep_fine_n(const LevelGeom& L, const FineOp& g, const TimeMats* tm, int K,
