@@ -766,6 +766,23 @@ k_sweep_fine(LevelGeom L, FineOp g, const TimeMats* __restrict__ tm, const typen
   const int nbc = ec[0] * ec[1] * ec[2], nbf = ef[0] * ef[1] * ef[2], npts = e[0] * e[1] * e[2];
   const int sx = L.sub[0] + 4, sy = L.dim > 1 ? L.sub[1] + 4 : 1, sz = L.dim > 2 ? L.sub[2] + 4 : 1;
   const int nbc_max = sx * sy * sz;
+  // index maps item t -> (point i, time function m) and point -> (x, y, z) by multiply-shift
+  // division: the level's divisors for a full subvolume, this CTA's own for a ragged one
+  const bool full = e[0] == L.sub[0] && e[1] == L.sub[1] && e[2] == L.sub[2];
+  const FastDiv dK = L.fd_K;
+  const FastDiv dc0 = full ? L.fd_c[0] : make_fastdiv(ec[0]), dc1 = full ? L.fd_c[1] : make_fastdiv(ec[1]);
+  const FastDiv df0 = full ? L.fd_f[0] : make_fastdiv(ef[0]), df1 = full ? L.fd_f[1] : make_fastdiv(ef[1]);
+  const FastDiv du0 = full ? L.fd_u[0] : make_fastdiv(e[0]), du1 = full ? L.fd_u[1] : make_fastdiv(e[1]);
+  auto item = [&](int t, int& i, int& m) {
+    i = fdiv(t, dK);
+    m = t - i * K;
+  };
+  auto coords = [](int i, const FastDiv& d0, const FastDiv& d1, int& x, int& y, int& z) {
+    const int r = fdiv(i, d0);
+    x = i - r * d0.d;
+    z = fdiv(r, d1);
+    y = r - z * d1.d;
+  };
 
   R* sQ = reinterpret_cast<R*>(smem);
   R* sU = sQ + LA_KMAX * LA_KMAX;
@@ -787,9 +804,10 @@ k_sweep_fine(LevelGeom L, FineOp g, const TimeMats* __restrict__ tm, const typen
     sQ[i] = (R)tm->Qb[i]; sU[i] = (R)tm->Ub[i]; sW[i] = (R)tm->Wt[i]; sE[i] = (R)tm->Eb[i];
   }
   for (int t = tid; t < nbc * K; t += kSweepThreads) {
-    const int i = t / K, m = t % K;
+    int i, m;
+    item(t, i, m);
     int lx, ly, lz;
-    local_coords(i, ec, lx, ly, lz);
+    coords(i, dc0, dc1, lx, ly, lz);
     const int gx = oc[0] + lx, gy = oc[1] + ly, gz = oc[2] + lz;
     CT v = mkc<CT>(0, 0);
     if (fine_in(g, gx, gy, gz)) v = c[(size_t)((gz * g.n[1] + gy) * g.n[0] + gx) * K + m];
@@ -802,7 +820,7 @@ k_sweep_fine(LevelGeom L, FineOp g, const TimeMats* __restrict__ tm, const typen
     const R xh = (R)(g.lax == 0 ? g.h[0] : (g.lax == 1 ? g.h[1] : g.h[2]));
     for (int i = tid; i < nbf; i += kSweepThreads) {
       int lx, ly, lz;
-      local_coords(i, ef, lx, ly, lz);
+      coords(i, df0, df1, lx, ly, lz);
       const int gx = of_[0] + lx, gy = of_[1] + ly, gz = of_[2] + lz;
       sV[i] = fine_in(g, gx, gy, gz) ? dsum + (R)g.V0[(gz * g.n[1] + gy) * g.n[0] + gx] : (R)0;
       sX[i] = xo + (R)(g.lax == 0 ? gx : (g.lax == 1 ? gy : gz)) * xh;
@@ -814,9 +832,10 @@ k_sweep_fine(LevelGeom L, FineOp g, const TimeMats* __restrict__ tm, const typen
   const R wx = (R)(-0.5 * g.ih2[0]), wy = (R)(-0.5 * g.ih2[1]), wz = (R)(-0.5 * g.ih2[2]);
   // stage 1: Hc on the footprint
   for (int t = tid; t < nbf * K; t += kSweepThreads) {
-    const int i = t / K, m = t % K;
+    int i, m;
+    item(t, i, m);
     int lx, ly, lz;
-    local_coords(i, ef, lx, ly, lz);
+    coords(i, df0, df1, lx, ly, lz);
     const int cx = L.dim > 0 ? lx + 1 : lx, cy = L.dim > 1 ? ly + 1 : ly, cz = L.dim > 2 ? lz + 1 : lz;
     const int ci = (cz * ec[1] + cy) * ec[0] + cx;
     const CT v = sC[ci * K + m];
@@ -838,9 +857,10 @@ k_sweep_fine(LevelGeom L, FineOp g, const TimeMats* __restrict__ tm, const typen
   __syncthreads();
   // stage 2: r = f - (i Qb c - Ub Hc - x Eb c) on the footprint (0 outside the grid)
   for (int t = tid; t < nbf * K; t += kSweepThreads) {
-    const int i = t / K, m = t % K;
+    int i, m;
+    item(t, i, m);
     int lx, ly, lz;
-    local_coords(i, ef, lx, ly, lz);
+    coords(i, df0, df1, lx, ly, lz);
     const int gx = of_[0] + lx, gy = of_[1] + ly, gz = of_[2] + lz;
     CT r = mkc<CT>(0, 0);
     if (fine_in(g, gx, gy, gz)) {
@@ -864,7 +884,8 @@ k_sweep_fine(LevelGeom L, FineOp g, const TimeMats* __restrict__ tm, const typen
   __syncthreads();
   // stage 3: z = Wt r
   for (int t = tid; t < nbf * K; t += kSweepThreads) {
-    const int i = t / K, m = t % K;
+    int i, m;
+    item(t, i, m);
     R zr = 0, zi = 0;
     for (int nn = 0; nn < K; ++nn) {
       const R w = sW[m * K + nn];
@@ -877,9 +898,10 @@ k_sweep_fine(LevelGeom L, FineOp g, const TimeMats* __restrict__ tm, const typen
   // stage 4: Hz on U (footprint index of U point = local + 1 on used axes)
   const int dfy = L.dim > 1 ? ef[0] : 0, dfz = L.dim > 2 ? ef[0] * ef[1] : 0;
   for (int t = tid; t < npts * K; t += kSweepThreads) {
-    const int i = t / K, m = t % K;
+    int i, m;
+    item(t, i, m);
     int lx, ly, lz;
-    local_coords(i, e, lx, ly, lz);
+    coords(i, du0, du1, lx, ly, lz);
     const int fx = L.dim > 0 ? lx + 1 : lx, fy = L.dim > 1 ? ly + 1 : ly, fz = L.dim > 2 ? lz + 1 : lz;
     const int fi = (fz * ef[1] + fy) * ef[0] + fx;
     const CT v = sA[fi * K + m];
@@ -903,9 +925,10 @@ k_sweep_fine(LevelGeom L, FineOp g, const TimeMats* __restrict__ tm, const typen
   for (int t = tid; t < NPAD; t += kSweepThreads) {
     CT out = mkc<CT>(0, 0);
     if (t < npts * K) {
-      const int i = t / K, m = t % K;
+      int i, m;
+      item(t, i, m);
       int lx, ly, lz;
-      local_coords(i, e, lx, ly, lz);
+      coords(i, du0, du1, lx, ly, lz);
       const int fx = L.dim > 0 ? lx + 1 : lx, fy = L.dim > 1 ? ly + 1 : ly, fz = L.dim > 2 ? lz + 1 : lz;
       const int fi = (fz * ef[1] + fy) * ef[0] + fx;
       const R xl = sX[fi];
@@ -935,9 +958,10 @@ k_sweep_fine(LevelGeom L, FineOp g, const TimeMats* __restrict__ tm, const typen
   __syncthreads();
   if (kStage && *reinterpret_cast<volatile int*>(sStage + 8)) return;
   for (int t = tid; t < npts * K; t += kSweepThreads) {
-    const int i = t / K, m = t % K;
+    int i, m;
+    item(t, i, m);
     int lx, ly, lz;
-    local_coords(i, e, lx, ly, lz);
+    coords(i, du0, du1, lx, ly, lz);
     const size_t gi = (size_t)(((o[2] + lz) * g.n[1] + (o[1] + ly)) * g.n[0] + (o[0] + lx)) * K + m;
     CT v = c[gi];
     v.x += sRhs[t].x;

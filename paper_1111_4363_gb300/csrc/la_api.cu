@@ -406,6 +406,13 @@ extern "C" la_status la_init(const la_config* cfg, void* stream, la_ctx** out) {
     G.npad = round_npad((l > 0 ? csubpts : subpts) * k.nt);
     G.nblk = G.npad / LA_BLK;
     G.fsize = k.local_form == 1 ? (long long)G.npad * G.npad : (long long)G.nblk * (G.nblk + 1) / 2 * LA_BLK * LA_BLK;
+    G.fd_K = make_fastdiv(k.nt);
+    for (int a = 0; a < 2; ++a) {
+      const bool used = a < k.dim;
+      G.fd_c[a] = make_fastdiv(used ? G.sub[a] + 4 : 1);
+      G.fd_f[a] = make_fastdiv(used ? G.sub[a] + 2 : 1);
+      G.fd_u[a] = make_fastdiv(G.sub[a]);
+    }
   }
   if (!build_time_constants(c)) {
     g_init_error = "invalid configuration: singular time-basis Gram matrix";

@@ -57,6 +57,27 @@ __host__ __device__ inline int theta_phase(int kk) {  // 0: real +1, 1: +i, 2: -
 }
 
 // Geometry of one multigrid level.
+// Division by a divisor fixed for a launch or a CTA: floor(x / d) = (x m) >> s for 0 <= x < 2^31, with
+// s = 31 + ceil(log2 d) and m = floor(2^s / d) + 1 < 2^32 (Granlund and Montgomery, "Division by
+// invariant integers using multiplication", PLDI 1994): one wide multiply and a shift instead of
+// the instruction sequence of an integer division.
+struct FastDiv {
+  int d;
+  unsigned m, s;
+};
+__host__ __device__ inline FastDiv make_fastdiv(int d) {
+  unsigned l = 0;
+  while ((1u << l) < (unsigned)d) ++l;
+  FastDiv f;
+  f.d = d;
+  f.s = 31 + l;
+  f.m = (unsigned)((1ull << f.s) / (unsigned long long)d + 1ull);
+  return f;
+}
+__host__ __device__ __forceinline__ int fdiv(int x, const FastDiv& f) {
+  return (int)(((unsigned long long)(unsigned)x * f.m) >> f.s);
+}
+
 struct LevelGeom {
   int dim;
   int n[3];        // points per axis (unused axes 1)
@@ -67,6 +88,9 @@ struct LevelGeom {
   int npad;        // padded unknowns per subvolume, multiple of LA_BLK
   int nblk;        // npad / LA_BLK
   long long fsize; // complex entries per subvolume factor: nblk(nblk+1)/2 * LA_BLK^2
+  // divisors of the finest-level sweep's index maps for a full (not ragged) subvolume: K, and the
+  // x and y extents of U + 2 (c box), U + 1 (footprint) and U (1 on unused axes)
+  FastDiv fd_K, fd_c[2], fd_f[2], fd_u[2];
 };
 
 // Finest-level spatial operator: H = -1/2 Laplacian + V0, X = x along laser_axis.
