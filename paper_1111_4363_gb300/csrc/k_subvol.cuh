@@ -1004,6 +1004,31 @@ __device__ inline CoarseSmem<R> coarse_smem_layout(unsigned char* smem, const Le
   return m;
 }
 
+// Multiply-shift index maps of one subvolume: item -> (point, time function), point -> (x, y, z) in U
+// and in U + 2 (the level's divisors for a full subvolume, the CTA's own for a ragged one).
+struct SubvolDiv {
+  FastDiv K, c0, c1, u0, u1;
+  __device__ SubvolDiv(const LevelGeom& L, const int e[3]) {
+    const bool full = e[0] == L.sub[0] && e[1] == L.sub[1] && e[2] == L.sub[2];
+    K = L.fd_K;
+    c0 = full ? L.fd_c[0] : make_fastdiv(e[0] + 4);
+    c1 = full ? L.fd_c[1] : make_fastdiv(L.dim > 1 ? e[1] + 4 : 1);
+    u0 = full ? L.fd_u[0] : make_fastdiv(e[0]);
+    u1 = full ? L.fd_u[1] : make_fastdiv(e[1]);
+  }
+  __device__ __forceinline__ void item(int t, int& i, int& m) const {
+    i = fdiv(t, K);
+    m = t - i * K.d;
+  }
+  __device__ __forceinline__ static void coords(int i, const FastDiv& d0, const FastDiv& d1, int& x, int& y,
+                                                int& z) {
+    const int r = fdiv(i, d0);
+    x = i - r * d0.d;
+    z = fdiv(r, d1);
+    y = r - z * d1.d;
+  }
+};
+
 // Fills S.Rhs[0..npad) with (g - G e) on the subvolume with origin o and extent e (0 in padding).
 template <typename R>
 __device__ inline void coarse_rhs(const LevelGeom& L, const double* __restrict__ sigma,
@@ -1020,11 +1045,13 @@ __device__ inline void coarse_rhs(const LevelGeom& L, const double* __restrict__
   }
   const int nbc = ec[0] * ec[1] * ec[2], npts = e[0] * e[1] * e[2];
   const int nbox = box5_count(L.dim);
+  const SubvolDiv dv(L, e);
   for (int i = tid; i < LA_NPAIR * KK; i += nthr) S.P[i] = (R)tm->P[i / KK][i % KK];
   for (int t = tid; t < nbc * K; t += nthr) {
-    const int i = t / K, m = t % K;
+    int i, m;
+    dv.item(t, i, m);
     int lx, ly, lz;
-    local_coords(i, ec, lx, ly, lz);
+    SubvolDiv::coords(i, dv.c0, dv.c1, lx, ly, lz);
     const int gx = oc[0] + lx, gy = oc[1] + ly, gz = oc[2] + lz;
     CT v = mkc<CT>(0, 0);
     if (gx >= 0 && gy >= 0 && gz >= 0 && gx < L.n[0] && gy < L.n[1] && gz < L.n[2])
@@ -1033,9 +1060,9 @@ __device__ inline void coarse_rhs(const LevelGeom& L, const double* __restrict__
   }
   const int per_pt = LA_NPAIR * nbox;
   for (int t = tid; t < npts * per_pt; t += nthr) {
-    const int i = t / per_pt, w = t % per_pt;
+    const int i = fdiv(t, L.fd_pair), w = t - i * per_pt;
     int lx, ly, lz;
-    local_coords(i, e, lx, ly, lz);
+    SubvolDiv::coords(i, dv.u0, dv.u1, lx, ly, lz);
     const int p = ((o[2] + lz) * L.n[1] + (o[1] + ly)) * L.n[0] + (o[0] + lx);
     S.Sg[t] = (R)sigma[(size_t)p * per_pt + w];
   }
@@ -1043,9 +1070,11 @@ __device__ inline void coarse_rhs(const LevelGeom& L, const double* __restrict__
   // u[i][kk][n] = sum_o Sigma_kk[p_i][o] e[p_i + o][n]
   const int ry = L.dim > 1 ? 2 : 0, rz = L.dim > 2 ? 2 : 0;
   for (int t = tid; t < npts * LA_NPAIR * K; t += nthr) {
-    const int n = t % K, ikk = t / K, i = ikk / LA_NPAIR;
+    int ikk, n;
+    dv.item(t, ikk, n);
+    const int i = ikk / LA_NPAIR;
     int lx, ly, lz;
-    local_coords(i, e, lx, ly, lz);
+    SubvolDiv::coords(i, dv.u0, dv.u1, lx, ly, lz);
     const int cx = lx + 2, cy = L.dim > 1 ? ly + 2 : ly, cz = L.dim > 2 ? lz + 2 : lz;
     const R* sg = S.Sg + (size_t)ikk * nbox;
     R ur0 = 0, ui0 = 0, ur1 = 0, ui1 = 0;
@@ -1068,9 +1097,10 @@ __device__ inline void coarse_rhs(const LevelGeom& L, const double* __restrict__
   for (int t = tid; t < npad; t += nthr) {
     CT out = mkc<CT>(0, 0);
     if (t < npts * K) {
-      const int i = t / K, m = t % K;
+      int i, m;
+      dv.item(t, i, m);
       int lx, ly, lz;
-      local_coords(i, e, lx, ly, lz);
+      SubvolDiv::coords(i, dv.u0, dv.u1, lx, ly, lz);
       const int p = ((o[2] + lz) * L.n[1] + (o[1] + ly)) * L.n[0] + (o[0] + lx);
       out = gvec[(size_t)p * K + m];
 #pragma unroll
@@ -1106,10 +1136,12 @@ k_sweep_coarse(LevelGeom L, const double* __restrict__ sigma, const TimeMats* __
   coarse_rhs<R>(L, sigma, tm, gvec, ev, o, e, NPAD, S);
   subvol_solve<CT, NPAD>(factors + (size_t)b * L.fsize, S.Rhs, S.Y, S.T, S.Red);
   __syncthreads();
+  const SubvolDiv dv(L, e);
   for (int t = threadIdx.x; t < npts * K; t += kSweepThreads) {
-    const int i = t / K, m = t % K;
+    int i, m;
+    dv.item(t, i, m);
     int lx, ly, lz;
-    local_coords(i, e, lx, ly, lz);
+    SubvolDiv::coords(i, dv.u0, dv.u1, lx, ly, lz);
     const size_t gi = (size_t)(((o[2] + lz) * L.n[1] + (o[1] + ly)) * L.n[0] + (o[0] + lx)) * K + m;
     CT v = ev[gi];
     v.x += S.Rhs[t].x;
@@ -1132,10 +1164,12 @@ k_gresid_tiles(LevelGeom L, const double* __restrict__ sigma, const TimeMats* __
   const int npts = e[0] * e[1] * e[2];
   CoarseSmem<R> S = coarse_smem_layout<R>(smem, L, K, npad);
   coarse_rhs<R>(L, sigma, tm, gvec, ev, o, e, npad, S);
+  const SubvolDiv dv(L, e);
   for (int t = threadIdx.x; t < npts * K; t += kSweepThreads) {
-    const int i = t / K, m = t % K;
+    int i, m;
+    dv.item(t, i, m);
     int lx, ly, lz;
-    local_coords(i, e, lx, ly, lz);
+    SubvolDiv::coords(i, dv.u0, dv.u1, lx, ly, lz);
     out[(size_t)(((o[2] + lz) * L.n[1] + (o[1] + ly)) * L.n[0] + (o[0] + lx)) * K + m] = S.Rhs[t];
   }
 }

@@ -413,6 +413,7 @@ extern "C" la_status la_init(const la_config* cfg, void* stream, la_ctx** out) {
       G.fd_f[a] = make_fastdiv(used ? G.sub[a] + 2 : 1);
       G.fd_u[a] = make_fastdiv(G.sub[a]);
     }
+    G.fd_pair = make_fastdiv(LA_NPAIR * box5_count(k.dim));
   }
   if (!build_time_constants(c)) {
     g_init_error = "invalid configuration: singular time-basis Gram matrix";

@@ -91,6 +91,7 @@ struct LevelGeom {
   // divisors of the finest-level sweep's index maps for a full (not ragged) subvolume: K, and the
   // x and y extents of U + 2 (c box), U + 1 (footprint) and U (1 on unused axes)
   FastDiv fd_K, fd_c[2], fd_f[2], fd_u[2];
+  FastDiv fd_pair;   // Galerkin levels: stencil values per point, 9 pairs x the radius-2 box
 };
 
 // Finest-level spatial operator: H = -1/2 Laplacian + V0, X = x along laser_axis.
