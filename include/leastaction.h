@@ -253,6 +253,12 @@ typedef struct {
 la_status la_lfa_maps(const la_lfa_case* cases, int ncases, const double* k, int nk, const double* w, int nw,
                       void* out, void* cuda_stream);
 
+/* Self-test of the bounded waits (no context): one CTA waits on an mbarrier that nothing completes,
+   polling at most `polls` times as the TMA-staged kernels do, and on giving up sets bit 4 of a status
+   word, which is written to *status_out (host).  The wait ends by itself; the device stays usable.
+   Synchronises cuda_stream.  Errors: LA_EINVAL (polls < 1 or null status_out), LA_ENOMEM, LA_ECUDA. */
+la_status la_wait_selftest(int polls, int* status_out, void* cuda_stream);
+
 la_status la_finalize(la_ctx* ctx);
 const char* la_last_error(const la_ctx* ctx);
 const char* la_version(void);

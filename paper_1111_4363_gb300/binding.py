@@ -21,7 +21,7 @@ LOCAL_FORMS = {"lsq": 0, "square": 1}
 
 EXPORTS = ["la_init", "la_set_hamiltonian", "la_step", "la_action", "la_solve_step", "la_residual",
            "la_relax_colour", "la_time_matrices", "la_backward", "la_step_batch", "la_profile_enable", "la_profile_read", "la_action_noalloc",
-           "la_lfa_maps",
+           "la_lfa_maps", "la_wait_selftest",
            "la_finalize", "la_last_error", "la_version"]
 NOALLOC_MAX_POINTS = 1 << 22
 
@@ -184,6 +184,16 @@ def lfa_maps(cases, k, w, out=None, stream=None) -> np.ndarray:
     if st != LA_OK:
         raise LeastActionError(st, L.la_last_error(None).decode())
     return out
+
+
+def wait_selftest(polls: int, stream=None) -> int:
+    """la_wait_selftest: the status word after one bounded wait on an mbarrier nothing completes."""
+    L = lib()
+    st = C.c_int(0)
+    rc = L.la_wait_selftest(int(polls), C.byref(st), _stream_handle(stream))
+    if rc != LA_OK:
+        raise LeastActionError(rc, "la_wait_selftest failed")
+    return st.value
 
 
 def action_noalloc(cfg: la_config, V0, pulse, psi0, t0: float, c, stream=None) -> float:

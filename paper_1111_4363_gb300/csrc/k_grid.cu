@@ -2,6 +2,7 @@
 // norm, normal residual, Galerkin-level residual, intergrid transfers, step advance.
 #include <algorithm>
 
+#include "../../include/leastaction.h"
 #include "la_internal.cuh"
 
 namespace la {
@@ -796,4 +797,38 @@ void launch_c128_to_c64(long long n, const double2* x, float2* y, cudaStream_t s
   k_c128_to_c64<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, x, y);
 }
 
+
+// ------------------------------------------------------------------ bounded-wait self-test
+// One CTA waits on an mbarrier that nothing completes, with the poll loop the staged kernels use,
+// and on giving up sets bit 4 of the status word as they do.
+__global__ void k_wait_selftest(unsigned polls, int* status) {
+  __shared__ __align__(8) unsigned long long bar;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    mbar_init_fence();
+  }
+  __syncthreads();
+  const bool ok = mbar_wait(&bar, 0, polls);
+  if (__syncthreads_or(!ok) && threadIdx.x == 0) atomicOr(status, 4);
+}
+
 }  // namespace la
+
+extern "C" la_status la_wait_selftest(int polls, int* status_out, void* cuda_stream) {
+  if (polls < 1 || !status_out) return LA_EINVAL;
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  int* d = nullptr;
+  if (cudaMalloc(&d, sizeof(int)) != cudaSuccess) {
+    cudaGetLastError();
+    return LA_ENOMEM;
+  }
+  cudaError_t e = cudaMemsetAsync(d, 0, sizeof(int), s);
+  if (e == cudaSuccess) {
+    la::k_wait_selftest<<<1, 32, 0, s>>>((unsigned)polls, d);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaMemcpyAsync(status_out, d, sizeof(int), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  cudaFree(d);
+  return e == cudaSuccess ? LA_OK : LA_ECUDA;
+}
