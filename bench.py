@@ -188,6 +188,28 @@ def dominant_roofline(prof, w, precision, ms_total, traffic_ok):
         dom, flops, dms, cls = "k_sweep_fine (one sweep, all colours)", prof["flops_sweep"], swp_ms_full, "sweep"
     bps = NCU_BYTES_PER_SUBVOLUME.get((cls, precision)) if traffic_ok else None
     traffic = round(bps * nsub) if bps else None
+    kms = {"factor_per_launch": round(fac_ms, 4), "sweep_full": round(swp_ms_full, 4),
+           "factor_share": round(prof["ms_factor"] / max(ms_total, 1e-9), 3),
+           "sweep_share": round(prof["ms_sweep"] / max(ms_total, 1e-9), 3)}
+    if precision == 1 and cls == "sweep":
+        # the complex64 sweep streams the factor store: HBM roofline on its compulsory bytes, every
+        # factor once plus c read and written, f read (8 B per complex64) and V0 read per point
+        pts = 1
+        for a in range(w.dim):
+            pts *= w.sub[a]
+        npad = next(s_ for s_ in (16, 32, 48, 64, 96, 128) if pts * w.nt <= s_)
+        nb = npad // 16
+        fbytes = nb * (nb + 1) // 2 * 256 * 8
+        nunk = w.nunknowns
+        algo = nsub * fbytes + nunk * 8 * 3 + w.npoints * 8
+        gbs = algo / (dms * 1e-3) / 1e9
+        peak, note = hbm_peak()
+        return {"bound": "hbm", "kernel": dom, "achieved": round(gbs, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(gbs / peak, 4), "traffic": traffic, "algorithmic_bytes": algo,
+                "traffic_note": "DRAM read+write bytes of this kernel per launch from one ncu capture of this workload",
+                "peak_note": note, "note": "latency-bound: few CTAs per SM (each holds a 43 KB factor in shared "
+                                           "memory for NPAD 96) and a dependent chain per CTA",
+                "kernel_ms": kms}
     achieved = flops / (dms * 1e-3) / 1e12
     if precision == 0:
         peak = FP64_PEAK_TFLOPS
@@ -198,10 +220,7 @@ def dominant_roofline(prof, w, precision, ms_total, traffic_ok):
     return {"bound": "alu", "kernel": dom, "achieved": round(achieved, 4), "peak": round(peak, 4),
             "unit": "TFLOP/s", "frac": round(achieved / peak, 4), "traffic": traffic,
             "traffic_note": "DRAM read+write bytes of this kernel per launch from one ncu capture of this workload",
-            "peak_note": peak_note,
-            "kernel_ms": {"factor_per_launch": round(fac_ms, 4), "sweep_full": round(swp_ms_full, 4),
-                          "factor_share": round(prof["ms_factor"] / max(ms_total, 1e-9), 3),
-                          "sweep_share": round(prof["ms_sweep"] / max(ms_total, 1e-9), 3)}}
+            "peak_note": peak_note, "kernel_ms": kms}
 
 
 def stencil_roofline(prof, precision, c64=False):

@@ -31,12 +31,19 @@ def test_dominant_roofline_picks_the_larger_class_and_divides_by_the_peak(bench)
     assert r["frac"] == pytest.approx(r["achieved"] / bench.FP64_PEAK_TFLOPS, rel=1e-3)
     assert r["bound"] == "alu" and r["unit"] == "TFLOP/s"
     assert r["traffic"] == round(bench.NCU_BYTES_PER_SUBVOLUME[("factor", 0)] * 4096)
-    # sweep dominant: the counters hold whole sweeps (all colours)
-    r = bench.dominant_roofline(fake_profile(ms_sweep=40.0), w, 1, ms_total=60.0, traffic_ok=False)
+    # sweep dominant: the counters hold whole sweeps (all colours); FP64 against the FP64 pipe
+    r = bench.dominant_roofline(fake_profile(ms_sweep=40.0), w, 0, ms_total=60.0, traffic_ok=False)
     assert r["kernel"].startswith("k_sweep_fine")
     assert r["achieved"] == pytest.approx(3.0e8 / 5e-3 / 1e12, rel=1e-3)
-    assert r["peak"] == pytest.approx(bench.FP32_PEAK_TFLOPS, rel=1e-4)
+    assert r["peak"] == pytest.approx(bench.FP64_PEAK_TFLOPS, rel=1e-4)
     assert r["traffic"] is None
+    # the complex64 sweep against HBM: every factor once (4096 x 21 blocks x 256 x 8 B at NPAD 96),
+    # c in and out and f (8 B per unknown each), V0 (8 B per point)
+    r = bench.dominant_roofline(fake_profile(ms_sweep=40.0), w, 1, ms_total=60.0, traffic_ok=False)
+    algo = 4096 * 21 * 256 * 8 + 256 * 256 * 6 * 24 + 256 * 256 * 8
+    assert r["bound"] == "hbm" and r["unit"] == "GB/s" and r["algorithmic_bytes"] == algo
+    assert r["achieved"] == pytest.approx(algo / 5e-3 / 1e9, rel=1e-3)
+    assert r["frac"] == pytest.approx(r["achieved"] / bench.hbm_peak()[0], rel=1e-3)
 
 
 def test_stencil_roofline_is_bytes_over_event_time_against_hbm(bench):
