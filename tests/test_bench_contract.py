@@ -43,7 +43,7 @@ def test_dominant_roofline_picks_the_larger_class_and_divides_by_the_peak(bench)
     algo = 4096 * 21 * 256 * 8 + 256 * 256 * 6 * 24 + 256 * 256 * 8
     assert r["bound"] == "hbm" and r["unit"] == "GB/s" and r["algorithmic_bytes"] == algo
     assert r["achieved"] == pytest.approx(algo / 5e-3 / 1e9, rel=1e-3)
-    assert r["frac"] == pytest.approx(r["achieved"] / bench.hbm_peak()[0], rel=1e-3)
+    assert r["frac"] == pytest.approx(r["achieved"] / bench.hbm_peak()[0], abs=1e-4)
 
 
 def test_stencil_roofline_is_bytes_over_event_time_against_hbm(bench):
