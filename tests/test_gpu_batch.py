@@ -59,3 +59,26 @@ def test_batch_rejects_repeated_context():
     psi = torch.from_numpy(wl.initial_state(w).ravel().copy()).cuda()
     with pytest.raises(B.LeastActionError):
         B.step_batch([ctx, ctx], [psi, psi.clone()], 1)
+
+
+def test_batch_with_square_local_form():
+    """Contexts of both local forms in one batch (the square form single-level, red-black)."""
+    import torch
+    from paper_1111_4363_gb300 import binding as B
+    a, b, c = members()
+    ws = [dataclasses.replace(a, levels=1, local_form="square", trial=3), b,
+          dataclasses.replace(c, local_form="square")]
+    nsteps = 3
+    alone = []
+    for w in ws:
+        ctx = gpu_context(w)
+        psi = torch.from_numpy(wl.initial_state(w).ravel().copy()).cuda()
+        st, stats = ctx.step(psi, nsteps, 0.2, stats=True)
+        alone.append((psi.cpu().numpy(), stats))
+    ctxs = [gpu_context(w) for w in ws]
+    psis = [torch.from_numpy(wl.initial_state(w).ravel().copy()).cuda() for w in ws]
+    stats = B.step_batch(ctxs, psis, nsteps, [0.2] * 3)
+    for i, (psi_ref, st_ref) in enumerate(alone):
+        assert rel_l2(psis[i].cpu().numpy(), psi_ref) < 1e-14, i
+        assert [s[0] for s in stats[i]] == [s[0] for s in st_ref]
+        assert all(s[3] <= ws[i].tol for s in stats[i])
