@@ -89,6 +89,30 @@ def test_2d_colour_pass(w2d, sys2d, colour):
     assert np.array_equal(got[~touched], c0[~touched])
 
 
+@pytest.mark.parametrize("colour", [0, 1])
+def test_2d_square_colour_pass(bench, w2d, sys2d, colour):
+    """The bench's square-form workload (256 x 256 x 6, 4 x 4 subvolumes, red-black): every subvolume
+    of one colour (2048 of 4096) against the oracle's square block update; the relaxed blocks'
+    residual rows vanish."""
+    prob, psi0, M, f, W, G, g = sys2d
+    wsq = bench.workload("2d-square")
+    assert wsq.local_form == "square" and system.Problem.from_workload(wsq).shape == prob.shape
+    assert (wsq.dt, wsq.nt, wsq.h) == (w2d.dt, w2d.nt, w2d.h)
+    ctx = gpu_context(wsq)
+    c0 = wl.random_state(M.shape[1], 21 + colour) * 0.05
+    got = c0.copy()
+    ctx.relax_colour(psi0, T0, colour, got)
+    R = relax.SquareRelaxation(M, prob.shape, numpy_sub(wsq), prob.K)
+    ref = c0.copy()
+    R.colour_pass(ref, f, colour)
+    rows = np.concatenate([idx for col, idx, _ in R.blocks if col == colour])
+    assert len(rows) == M.shape[1] // 2
+    assert rel_l2(got - c0, ref - c0) < 1e-10
+    assert rel_l2(got, ref) < 1e-11
+    r = system.residual(M, f, got)
+    assert np.max(np.abs(r[rows])) <= 1e-11 * np.max(np.abs(f))
+
+
 def test_2d_first_vcycle(w2d, sys2d):
     """One V(1,2) cycle of the bench schedule from c = 0: every coefficient against the oracle."""
     prob, psi0, M, f, W, G, g = sys2d

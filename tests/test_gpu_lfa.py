@@ -45,13 +45,13 @@ def test_maps_match_the_oracle(method, nx, nt):
 
 
 def test_device_output_and_full_grid_samples():
-    """The full map set the bench computes (8 (kappa, nu) pairs x 3 methods x 4 basis sizes on a 128 x
-    128 grid, which avoids k = w = 0 where N or S of the trial vanishes for nu = 0), into a device
-    array; sampled points against the oracle."""
+    """The full map set the bench computes (8 (kappa, nu) pairs x 3 methods x 4 basis sizes on its
+    256 x 256 grid, which avoids k = w = 0 where N or S of the trial vanishes for nu = 0), into a
+    device array; sampled points against the oracle."""
     import torch
     from paper_1111_4363_gb300 import binding as B
-    ks = np.linspace(-8.0, 8.0, 128)
-    ws = np.linspace(-8.0, 8.0, 128)
+    ks = np.linspace(-8.0, 8.0, 256)
+    ws = np.linspace(-8.0, 8.0, 256)
     cases = [(m, s, s, kappa, nu) for m in ("one", "two", "transfer") for s in (3, 4, 6, 8)
              for kappa, nu in lfa.KAPPA_NU]
     out = torch.zeros((len(cases), 2, len(ws), len(ks)), dtype=torch.float64, device="cuda")
