@@ -51,7 +51,8 @@ k_factor_square(LevelGeom L, FineOp g, const TimeMats* __restrict__ tm, double2*
                 int* __restrict__ perm, int* __restrict__ status) {
   extern __shared__ __align__(16) unsigned char smem[];
   double2* A = reinterpret_cast<double2*>(smem);                  // [NPAD][NPAD]
-  double* sQ = reinterpret_cast<double*>(A + NPAD * NPAD);         // [K][K]
+  double2* sInvP = A + NPAD * NPAD;                                // reciprocal of the current pivot
+  double* sQ = reinterpret_cast<double*>(sInvP + 1);               // [K][K]
   double* sU = sQ + LA_KMAX * LA_KMAX;
   double* sE = sU + LA_KMAX * LA_KMAX;
   int* sPerm = reinterpret_cast<int*>(sE + LA_KMAX * LA_KMAX);     // [NPAD]
@@ -107,6 +108,11 @@ k_factor_square(LevelGeom L, FineOp g, const TimeMats* __restrict__ tm, double2*
         if (!(best > 0.0)) { atomicOr(status, 1); bi = k; }
         *sPiv = bi;
         const int t = sPerm[k]; sPerm[k] = sPerm[bi]; sPerm[bi] = t;
+        // one complex reciprocal per column, shared (an FP64 division per thread would cost as
+        // much as the column's rank-1 update)
+        const double2 d = A[bi * NPAD + k];
+        const double sq = d.x * d.x + d.y * d.y;
+        *sInvP = sq > 0.0 ? make_double2(d.x / sq, -d.y / sq) : make_double2(1.0, 0.0);
       }
     }
     __syncthreads();
@@ -118,12 +124,7 @@ k_factor_square(LevelGeom L, FineOp g, const TimeMats* __restrict__ tm, double2*
         A[p * NPAD + j] = t;
       }
     __syncthreads();
-    double2 inv;
-    {
-      const double2 d = A[k * NPAD + k];
-      const double s = d.x * d.x + d.y * d.y;
-      inv = s > 0.0 ? make_double2(d.x / s, -d.y / s) : make_double2(1.0, 0.0);
-    }
+    const double2 inv = *sInvP;
     for (int i = k + 1 + tid; i < NPAD; i += kSqFactorThreads) A[i * NPAD + k] = cmul(A[i * NPAD + k], inv);
     __syncthreads();
     for (int i = k + 1 + ty; i < NPAD; i += kSqFactorThreads / 16) {
@@ -288,7 +289,7 @@ k_sweep_square(LevelGeom L, FineOp g, const TimeMats* __restrict__ tm, const dou
 template <int NPAD>
 cudaError_t factor_square_n(const LevelGeom& L, const FineOp& g, const TimeMats* tm, double2* lu, int* perm,
                             int* status, cudaStream_t s) {
-  const size_t smem = sizeof(double2) * NPAD * NPAD + sizeof(double) * 3 * LA_KMAX * LA_KMAX +
+  const size_t smem = sizeof(double2) * (NPAD * NPAD + 1) + sizeof(double) * 3 * LA_KMAX * LA_KMAX +
                       sizeof(int) * (NPAD + 1);
   if (smem > 227 * 1024) return cudaErrorInvalidValue;
   static bool attr_set = false;
