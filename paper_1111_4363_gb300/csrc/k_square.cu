@@ -245,33 +245,46 @@ k_sweep_square(LevelGeom L, FineOp g, const TimeMats* __restrict__ tm, const dou
   const bool own = tid < NPAD;
   double2 y = sY[pr];          // y = P r
   __syncthreads();
-  // forward: unit lower L, column k updates the rows below it
-  for (int k0 = 0; k0 < NPAD; k0 += kSqPrefetch) {
+  // Only the warps that own rows take part, and each step's barrier (id 1) counts just the warps
+  // that still have work in it: in the forward pass warp w is done after column 32 w + 31, in the
+  // backward pass before column 32 w.  (A predicated update in finished warps would still occupy the
+  // FP64 pipe.)  Id 2 separates the two passes.
+  constexpr int NWo = (NPAD + 31) / 32;
+  const int w = tid >> 5;
+  if (w < NWo) {
+    // forward: unit lower L, column k updates the rows below it
+    for (int k0 = 0; k0 < NPAD; k0 += kSqPrefetch) {
+      if (k0 >= 32 * (w + 1)) break;
+      const unsigned cnt = 32u * (unsigned)(NWo - (k0 >> 5));
 #pragma unroll
-    for (int u = 0; u < kSqPrefetch; ++u) {
-      const int k = k0 + u;
-      const double2 lk = pf[u];
-      if (k + kSqPrefetch < NPAD) pf[u] = F[(k + kSqPrefetch) * NPAD + row];
-      if (tid == k) sY[k] = y;
-      __syncthreads();
-      if (own && tid > k) cfms(y, lk, sY[k]);
-    }
-  }
-  // backward: columns of U from the last; x_k = y_k / U_kk
-#pragma unroll
-  for (int u = 0; u < kSqPrefetch; ++u) pf[u] = F[(NPAD - 1 - u) * NPAD + row];
-  for (int k0 = NPAD - 1; k0 >= 0; k0 -= kSqPrefetch) {
-#pragma unroll
-    for (int u = 0; u < kSqPrefetch; ++u) {
-      const int k = k0 - u;
-      const double2 uk = pf[u];
-      if (k - kSqPrefetch >= 0) pf[u] = F[(k - kSqPrefetch) * NPAD + row];
-      if (tid == k) {
-        y = cmul(y, uk);     // uk = 1 / U_kk on the diagonal
-        sY[k] = y;
+      for (int u = 0; u < kSqPrefetch; ++u) {
+        const int k = k0 + u;
+        const double2 lk = pf[u];
+        if (k + kSqPrefetch < NPAD) pf[u] = F[(k + kSqPrefetch) * NPAD + row];
+        if (tid == k) sY[k] = y;
+        asm volatile("bar.sync 1, %0;" ::"r"(cnt) : "memory");
+        if (own && tid > k) cfms(y, lk, sY[k]);
       }
-      __syncthreads();
-      if (own && tid < k) cfms(y, uk, sY[k]);
+    }
+    asm volatile("bar.sync 2, %0;" ::"r"(32u * NWo) : "memory");
+    // backward: columns of U from the last; x_k = y_k / U_kk
+#pragma unroll
+    for (int u = 0; u < kSqPrefetch; ++u) pf[u] = F[(NPAD - 1 - u) * NPAD + row];
+    for (int k0 = NPAD - 1; k0 >= 0; k0 -= kSqPrefetch) {
+      if (k0 < 32 * w) break;
+      const unsigned cnt = 32u * (unsigned)((k0 >> 5) + 1);
+#pragma unroll
+      for (int u = 0; u < kSqPrefetch; ++u) {
+        const int k = k0 - u;
+        const double2 uk = pf[u];
+        if (k - kSqPrefetch >= 0) pf[u] = F[(k - kSqPrefetch) * NPAD + row];
+        if (tid == k) {
+          y = cmul(y, uk);     // uk = 1 / U_kk on the diagonal
+          sY[k] = y;
+        }
+        asm volatile("bar.sync 1, %0;" ::"r"(cnt) : "memory");
+        if (own && tid < k) cfms(y, uk, sY[k]);
+      }
     }
   }
   if (own && tid < n) {
