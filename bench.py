@@ -38,8 +38,8 @@ METRIC = "spacetime unknowns relaxed/s"
 # (kernel class, precision) -> DRAM bytes (read + write) per finest-level subvolume, from one ncu capture of
 # the 2D 256x256 workload: the finest k_factor launch (4096 subvolumes) and one full k_sweep_fine sweep
 # (four colour launches, 4096 subvolumes)
-NCU_BYTES_PER_SUBVOLUME = {("factor", 0): (789504 + 286813184) / 4096,
-                           ("sweep", 0): (393767424 + 4342528) / 4096}
+NCU_BYTES_PER_SUBVOLUME = {("factor", 0): (867072 + 287257600) / 4096,
+                           ("sweep", 0): (391391488 + 2344192) / 4096}
 FP64_PEAK_TFLOPS = 152 * 4 * 2070e6 / 1e12   # 152 SMs x 4 FP64 flop/clk/SM x 2070 MHz (derived)
 FP32_PEAK_TFLOPS = 152 * 256 * 2070e6 / 1e12  # 152 SMs x 128 FP32 lanes x 2 flop (FMA) x 2070 MHz (derived)
 L2_BYTES = 129 * 2 ** 20
