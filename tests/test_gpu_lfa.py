@@ -26,7 +26,7 @@ def tolerances(method, nx, nt, kappa, nu, ks, ws):
 
 
 @pytest.mark.parametrize("method", ["one", "two", "transfer"])
-@pytest.mark.parametrize("nx,nt", [(3, 3), (4, 5), (6, 6), (8, 8)])
+@pytest.mark.parametrize("nx,nt", [(2, 2), (3, 3), (4, 5), (6, 6), (8, 8)])
 def test_maps_match_the_oracle(method, nx, nt):
     from paper_1111_4363_gb300 import binding as B
     ks = np.array([-7.5, -2.0, 0.3, 1.0, 4.4])
@@ -42,6 +42,8 @@ def test_maps_match_the_oracle(method, nx, nt):
         if max(np.max(tolN), np.max(tolS)) < 1e-5:
             well += 1
     assert well >= 5       # most cases are checked to tight bounds
+    if (nx, nt) == (2, 2) and method == "one":
+        assert np.all(np.abs(got) < 1e-12)   # no free parameter: the trial is unchanged
 
 
 def test_device_output_and_full_grid_samples():

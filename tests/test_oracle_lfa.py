@@ -104,3 +104,12 @@ def test_maps_follow_sec_v():
     tr, _ = lfa.ratio_map("transfer", 5, 5, 1.0, 0.0, ks, ws)
     assert abs(np.median(tr) - np.median(two)) < 0.5
     assert np.median(tr) < np.median(one)
+
+
+def test_two_by_two_element_has_no_free_parameter():
+    """Nx = Nt = 2: the four conditions of one element have rank 4 = Nx Nt, so a relaxation cannot
+    change the trial (log ratio 0); two elements keep 8 - 7 = 1 free parameter."""
+    assert lfa.null_space(lfa.constraints(2, 2, 1)).shape[1] == 0
+    assert lfa.null_space(lfa.constraints(2, 2, 2)).shape[1] == 1
+    N, S = lfa.ratio_map("one", 2, 2, 1.0, 0.5, np.array([1.3, -2.0]), np.array([0.4]))
+    assert np.all(N == 0.0) and np.all(S == 0.0)
