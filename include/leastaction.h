@@ -171,8 +171,9 @@ la_status la_residual(la_ctx* ctx, const void* psi0, double t0, const void* c, v
                       double* action);
 
 /* One relaxation pass of a single colour on the finest level (Sec. II): every subvolume of
-   that colour is replaced by the minimiser of N over its coefficients, the others fixed.
-   c (complex128[Np*K]) is read and overwritten.  colour in [0, 2^dim). */
+   that colour is replaced by the minimiser of N over its coefficients, the others fixed
+   (local_form 1: by the solution of its square Dirichlet problem).  c (complex128[Np*K]) is read
+   and overwritten.  colour in [0, 2^dim) (local_form 1: the two checkerboard colours 0, 1). */
 la_status la_relax_colour(la_ctx* ctx, const void* psi0, double t0, int colour, void* c);
 
 /* Per-step time matrices at t0 (row-major K x K unless noted), for inspection:
