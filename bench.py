@@ -105,6 +105,22 @@ def dist_env():
     return ws, rank, local
 
 
+def reduce_over_ranks(ms: float, sweeps: float, ws: int):
+    """Whole-job figures of N replicas: the slowest rank's timed region and the sweeps of all ranks
+    (each rank relaxes its own copy of the workload; the only exchange is this timing reduction)."""
+    if ws <= 1:
+        return ms, sweeps
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    tt = torch.tensor([ms, float(sweeps)], dtype=torch.float64, device=dev)
+    mx = tt.clone()
+    dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+    sm_ = tt.clone()
+    dist.all_reduce(sm_, op=dist.ReduceOp.SUM)
+    return float(mx[0]), float(sm_[1])
+
+
 class ClockSampler:
     """nvidia-smi clocks and throttle reasons sampled every 100 ms during the timed region."""
     QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -291,15 +307,7 @@ def run_ours(args):
     clk = clocks.stop()
     prof = ctx.profile_read()
     ctx.profile_enable(False)
-    ms_max = ms
-    sweeps_all = sweeps
-    if ws > 1:
-        tt = torch.tensor([ms, float(sweeps)], dtype=torch.float64, device="cuda")
-        mx = tt.clone()
-        dist.all_reduce(mx, op=dist.ReduceOp.MAX)
-        sm_ = tt.clone()
-        dist.all_reduce(sm_, op=dist.ReduceOp.SUM)
-        ms_max, sweeps_all = float(mx[0]), float(sm_[1])
+    ms_max, sweeps_all = reduce_over_ranks(ms, sweeps, ws)
     value = nunk * sweeps_all / (ms_max * 1e-3)
 
     # end to end through the public call with host buffers: pinned psi copied in and out every step
