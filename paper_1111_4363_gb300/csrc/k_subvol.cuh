@@ -296,7 +296,7 @@ __device__ __forceinline__ double rsq(double x) { return rsqrt(x); }
 // shared-memory factorisation above (NPAD 96 at 256 x 256: 9.4 ms against 5.7 ms), so the FP64
 // path does not use it.
 template <typename R, int NPAD, int MPC>
-__global__ void __launch_bounds__(kFactorThreads, sizeof(R) == 4 ? 2 : 1)
+__global__ void __launch_bounds__(kFactorThreads, sizeof(R) == 4 ? (NPAD <= 96 ? 3 : 2) : 1)
 k_factor_blk(LevelGeom L, FineOp g, int is_fine, int nptsmax, const double* __restrict__ sigma,
              const TimeMats* __restrict__ tm, typename C2<R>::T* __restrict__ factors, int* __restrict__ status) {
   typedef typename C2<R>::T CT;
