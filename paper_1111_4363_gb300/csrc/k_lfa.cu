@@ -248,13 +248,13 @@ void transfers(int nx, int nt, Mat& I, Mat& P) {
       }
 }
 
-struct CaseForms {
+struct CaseMats {
   int nel, nx, nt, n;
-  std::vector<double2> G;   // [4][n][n]: M0 .. M3
+  std::vector<double2> G;   // [4][n][n]: the step matrices M0 .. M3
   std::vector<double> W;    // [n]: the diagonal weight O (x) U per element
 };
 
-bool build_case(const la_lfa_case& cs, CaseForms& out, std::string& why) {
+bool build_case(const la_lfa_case& cs, CaseMats& out, std::string& why) {
   const int nx = cs.nx, nt = cs.nt;
   const int nel = cs.method == 0 ? 1 : 2, n = nel * nx * nt;
   const Mat A1 = element_operator(nx, nt, cs.kappa, cs.nu);
@@ -308,7 +308,7 @@ bool build_case(const la_lfa_case& cs, CaseForms& out, std::string& why) {
       }
   }
   const Mat RPi = mul(R, Pi);
-  const Mat forms[4] = {mul(A, Pi), mul(A, RPi), Pi, RPi};
+  const Mat mats[4] = {mul(A, Pi), mul(A, RPi), Pi, RPi};
   out.nel = nel;
   out.nx = nx;
   out.nt = nt;
@@ -318,7 +318,7 @@ bool build_case(const la_lfa_case& cs, CaseForms& out, std::string& why) {
   out.G.resize((size_t)4 * n * n);
   for (int f = 0; f < 4; ++f)
     for (size_t t = 0; t < (size_t)n * n; ++t)
-      out.G[(size_t)f * n * n + t] = make_double2(forms[f].v[t].real(), forms[f].v[t].imag());
+      out.G[(size_t)f * n * n + t] = make_double2(mats[f].v[t].real(), mats[f].v[t].imag());
   return true;
 }
 
@@ -462,7 +462,7 @@ extern "C" la_status la_lfa_maps(const la_lfa_case* cases, int ncases, const dou
   double qy[kLfaQuad], qw[kLfaQuad];
   gauss_legendre_rule(kLfaQuad, qy, qw);
   // the cases' step matrices, built on host threads (independent dense algebra per case)
-  std::vector<CaseForms> forms(ncases);
+  std::vector<CaseMats> mats(ncases);
   std::vector<std::string> why(ncases);
   std::vector<char> ok(ncases, 0);
   {
@@ -470,7 +470,7 @@ extern "C" la_status la_lfa_maps(const la_lfa_case* cases, int ncases, const dou
     std::vector<std::thread> pool;
     for (int t = 0; t < nth; ++t)
       pool.emplace_back([&, t]() {
-        for (int c = t; c < ncases; c += nth) ok[c] = build_case(cases[c], forms[c], why[c]) ? 1 : 0;
+        for (int c = t; c < ncases; c += nth) ok[c] = build_case(cases[c], mats[c], why[c]) ? 1 : 0;
       });
     for (auto& th : pool) th.join();
   }
@@ -484,15 +484,15 @@ extern "C" la_status la_lfa_maps(const la_lfa_case* cases, int ncases, const dou
   size_t gtot = 0, wtot = 0;
   for (int c = 0; c < ncases; ++c) {
     goff[c] = gtot;
-    gtot += (forms[c].G.size() + 15) & ~(size_t)15;
+    gtot += (mats[c].G.size() + 15) & ~(size_t)15;
     woff[c] = wtot;
-    wtot += (forms[c].W.size() + 31) & ~(size_t)31;
+    wtot += (mats[c].W.size() + 31) & ~(size_t)31;
   }
   std::vector<double2> Gall(gtot);
   std::vector<double> Wall(wtot);
   for (int c = 0; c < ncases; ++c) {
-    std::copy(forms[c].G.begin(), forms[c].G.end(), Gall.begin() + goff[c]);
-    std::copy(forms[c].W.begin(), forms[c].W.end(), Wall.begin() + woff[c]);
+    std::copy(mats[c].G.begin(), mats[c].G.end(), Gall.begin() + goff[c]);
+    std::copy(mats[c].W.begin(), mats[c].W.end(), Wall.begin() + woff[c]);
   }
   void* buf = nullptr;
   // every sub-array starts on a 256-byte boundary (double2 accesses need 16-byte alignment)
@@ -525,7 +525,7 @@ extern "C" la_status la_lfa_maps(const la_lfa_case* cases, int ncases, const dou
   // the overlap tables and the contracted matrices are reused case after case in stream order
   int tab_nel = 0, tab_nx = 0, tab_nt = 0;
   for (int c = 0; c < ncases && e == cudaSuccess; ++c) {
-    const CaseForms& F = forms[c];
+    const CaseMats& F = mats[c];
     const int np = F.nel * F.nx;
     const double2* G = reinterpret_cast<const double2*>(B + off_g) + goff[c];
     const double* Wt = reinterpret_cast<const double*>(B + off_wt) + woff[c];
