@@ -390,7 +390,7 @@ ORACLE_THREADS = 1
 
 def cpu_baseline(w: wl.Workload):
     setup_s, cyc_s, ncyc = oracle_cycle_rate(w, 8.0)
-    sweeps = w.nu1 + w.nu2 if w.levels > 1 else w.nu1 + w.nu2
+    sweeps = w.nu1 + w.nu2
     value = w.nunknowns * sweeps / cyc_s
     return {"value": value, "unit": "unknowns/s", "cores": ORACLE_THREADS, "kind": "oracle",
             "host_cores": len(os.sched_getaffinity(0)),
