@@ -1,5 +1,7 @@
 """Pins for the oracle's Legendre-element convergence maps (Secs. IV-V: element matrices,
 constrained relaxation, continuity projection, the plane-wave experiment)."""
+import os
+
 import numpy as np
 import pytest
 
@@ -113,3 +115,72 @@ def test_two_by_two_element_has_no_free_parameter():
     assert lfa.null_space(lfa.constraints(2, 2, 2)).shape[1] == 1
     N, S = lfa.ratio_map("one", 2, 2, 1.0, 0.5, np.array([1.3, -2.0]), np.array([0.4]))
     assert np.all(N == 0.0) and np.all(S == 0.0)
+
+
+def _sec5_facts():
+    facts = {"kappa_nu": [], "counts": {}, "cost": {}}
+    path = os.path.join(os.path.dirname(__file__), "golden", "sec5_plane_wave_experiment.txt")
+    for line in open(path):
+        f = line.split()
+        if not f or f[0].startswith("#"):
+            continue
+        if f[0] == "kappa_nu":
+            facts["kappa_nu"].append((float(f[1]), float(f[2])))
+        elif f[0] == "counts":
+            facts["counts"][f[1]] = (int(f[2]), int(f[3]), int(f[5]), int(f[7]))
+        elif f[0] == "cost":
+            facts["cost"][f[1]] = float(f[2])
+    return facts
+
+
+def test_sec5_printed_parameters_counts_and_costs(monkeypatch):
+    """Sec. V as printed: the eight (kappa, nu) pairs of the figures; at Nx = Nt = 3 one element has
+    9 free parameters and 9 constraint equations, two elements 18 and 12 (the 15 conditions of two
+    elements, initial values per element included, have rank 12); the transfer method solves three
+    systems of one element's size, 1.5 times the cost of relaxing each element separately, against
+    4 times for both at once."""
+    facts = _sec5_facts()
+    assert lfa.KAPPA_NU == facts["kappa_nu"]
+    nx, nt, params, ncons = facts["counts"]["one"]
+    assert nx * nt == params
+    assert lfa.constraints(nx, nt, 1).shape[0] == ncons
+    nx, nt, params, ncons = facts["counts"]["two"]
+    assert 2 * nx * nt == params
+    assert np.linalg.matrix_rank(lfa.constraints(nx, nt, 2)) == ncons
+
+    sizes = []
+    solve = lfa.constrained_solve
+
+    def counting(A, B, r, solver="null"):
+        sizes.append(A.shape[0])
+        return solve(A, B, r, solver)
+
+    monkeypatch.setattr(lfa, "constrained_solve", counting)
+    n = 4 * 4
+    C = lfa.project(4, 4, 2, lfa.plane_wave_overlaps(4, 4, 2, 1.0, -0.5))
+    cost = {}
+    for method in ("two", "transfer"):
+        sizes.clear()
+        lfa.relax_method(method, 4, 4, 1.0, 0.0, C)
+        cost[method] = sum(s ** 3 for s in sizes) / (2 * n ** 3)
+    assert sizes == [n, n, n]
+    assert cost == facts["cost"]
+
+
+def test_slow_convergence_only_near_the_dispersion_curve():
+    """Sec. V: with a large basis the residual norm falls nearly everywhere and grows only near the
+    curve where the plane wave solves the equation (so the trial is already close to the minimum
+    action wavefunction); for the dimensionless rows A that is -w = kappa k^2 + nu.  A small basis
+    instead fails to converge over much of the plane."""
+    ks = np.linspace(-3.0, 3.0, 7)
+    ws = np.linspace(-5.0, 5.0, 11)
+    W, K = np.meshgrid(ws, ks, indexing="ij")
+    grows = {3: [0, 0], 8: [0, 0]}          # points where N grows: near the curve, away from it
+    for nb in grows:
+        for kappa, nu in lfa.KAPPA_NU:
+            lrN, _ = lfa.ratio_map("one", nb, nb, kappa, nu, ks, ws)
+            near = np.abs(W + kappa * K ** 2 + nu) <= 0.5
+            grows[nb][0] += int(np.sum((lrN > 0) & near))
+            grows[nb][1] += int(np.sum((lrN > 0) & ~near))
+    assert grows[8][0] > 0 and grows[8][1] == 0
+    assert grows[3][1] > 50
