@@ -191,13 +191,40 @@ def hbm_peak():
         return 6800.0, "of fallback (6.8 TB/s)"
 
 
+def finest_factor_store(w, precision):
+    """(subvolumes, bytes per subvolume factor) of the finest level, in the library's layout: packed
+    lower-triangular 16 x 16 blocks of the padded size (least squares), or the dense padded LU
+    (square local form); complex128 entries in FP64, complex64 in the mixed path."""
+    nsub, pts = 1, 1
+    for a in range(w.dim):
+        nsub *= -(-w.n[a] // w.sub[a])
+        pts *= w.sub[a]
+    npad = next(s_ for s_ in (16, 32, 48, 64, 96, 128) if pts * w.nt <= s_)
+    entry = 16 if precision == 0 else 8
+    if getattr(w, "local_form", "lsq") == "square":
+        return nsub, npad * npad * entry
+    nb = npad // 16
+    return nsub, nb * (nb + 1) // 2 * 256 * entry
+
+
+def l2_note(w, precision):
+    """How the timed steps stand to the L2: either the factor store that every sweep streams (rewritten
+    each step) is larger than L2, or the whole working set fits and nothing is flushed."""
+    nsub, per = finest_factor_store(w, precision)
+    store, vec = nsub * per, w.nunknowns * 16
+    if store > L2_BYTES:
+        return (f"inputs ({vec / 1e6:.3g} MB per coefficient vector) {'larger' if vec > L2_BYTES else 'smaller'} "
+                f"than L2; each step rewrites the {store / 1e6:.0f} MB finest-level factor store (> L2), "
+                f"which every sweep streams")
+    return (f"working set (coefficient vectors {vec / 1e6:.3g} MB, factors {store / 1e6:.3g} MB) fits in "
+            f"L2; not flushed between steps")
+
+
 def dominant_roofline(prof, w, precision, ms_total, traffic_ok):
     """Roofline of the dominant kernel class (the larger total device time of factor and sweep)."""
     fac_ms = prof["ms_factor"] / max(prof["n_factor"], 1)
     swp_ms_full = prof["ms_sweep"] / max(prof["n_sweep"], 1)   # one event pair per full sweep
-    nsub = 1
-    for a in range(w.dim):
-        nsub *= -(-w.n[a] // w.sub[a])
+    nsub, fbytes = finest_factor_store(w, precision)
     if prof["ms_factor"] >= prof["ms_sweep"]:
         dom, flops, dms, cls = "k_factor (finest level)", prof["flops_factor"], fac_ms, "factor"
     else:
@@ -210,12 +237,6 @@ def dominant_roofline(prof, w, precision, ms_total, traffic_ok):
     if precision == 1 and cls == "sweep":
         # the complex64 sweep streams the factor store: HBM roofline on its compulsory bytes, every
         # factor once plus c read and written, f read (8 B per complex64) and V0 read per point
-        pts = 1
-        for a in range(w.dim):
-            pts *= w.sub[a]
-        npad = next(s_ for s_ in (16, 32, 48, 64, 96, 128) if pts * w.nt <= s_)
-        nb = npad // 16
-        fbytes = nb * (nb + 1) // 2 * 256 * 8
         nunk = w.nunknowns
         algo = nsub * fbytes + nunk * 8 * 3 + w.npoints * 8
         gbs = algo / (dms * 1e-3) / 1e9
@@ -338,7 +359,7 @@ def run_ours(args):
                       "tol_rel_action": w.tol, "precision": args.precision, "trial": w.trial,
                       "local_form": getattr(w, "local_form", "lsq"),
                       "parallelism": "replicas" if ws > 1 else "single",
-                      "l2": "inputs smaller than L2; each step rewrites the 352 MB factor store (> L2)"},
+                      "l2": l2_note(w, args.precision)},
            "cycles_per_step": cycles / args.steps, "fine_sweeps_per_step": sweeps / args.steps,
            "ms_per_time_step_to_tol": ms_max / args.steps,
            "e2e": {"value": e2e_value, "unit": "unknowns/s", "h2d_bytes_per_step": 16 * w.npoints,
@@ -537,7 +558,8 @@ def run_3d_adjoint(args):
            "dtype": "f64" if args.precision == 0 else "c64 local solves + f64 refinement", "data": "synthetic",
            "config": {"workload": w.name, "grid": list(w.shape), "K": w.nt, "subvolume": list(w.sub),
                       "levels": w.levels, "cycle": cycle_name(w), "trial": w.trial,
-                      "pulse_components": w.pulse.ncomp, "ckpt_every": 20, "cache_factors": True},
+                      "pulse_components": w.pulse.ncomp, "ckpt_every": 20, "cache_factors": True,
+                      "l2": l2_note(w, args.precision)},
            "cycles_per_step": sum(s_[0] for s_ in stats) / args.steps,
            "backward_ms_per_step": 1e3 * el_b / args.steps, "set_hamiltonian_s": setup_s,
            "roofline": dominant_roofline(prof, w, args.precision, 1e3 * el_f, traffic_ok=False),

@@ -63,3 +63,15 @@ def test_workloads_named_by_the_bench(bench):
     assert w.n[:2] == (256, 256) and w.nt == 6 and w.levels == 4 and w.sub[:2] == (4, 4)
     assert (w.nu1, w.nu2, w.trial) == (1, 2, 3)
     assert bench.workload("2d-small").n[:2] == (128, 128)
+
+
+def test_factor_store_and_l2_note(bench):
+    """The factor store the finest sweeps stream: 4096 subvolumes of 21 packed 16 x 16 blocks
+    (86 KB complex128, 43 KB complex64) at 256^2 x 6, larger than L2; the dense LU of the square
+    form is 96^2 entries; the 1D workload fits in L2 and the line says it is not flushed."""
+    w = bench.workload("2d")
+    assert bench.finest_factor_store(w, 0) == (4096, 21 * 256 * 16)
+    assert bench.finest_factor_store(w, 1) == (4096, 21 * 256 * 8)
+    assert bench.finest_factor_store(bench.workload("2d-square"), 0) == (4096, 96 * 96 * 16)
+    assert "352 MB" in bench.l2_note(w, 0) and "(> L2)" in bench.l2_note(w, 0)
+    assert "fits in L2" in bench.l2_note(bench.workload("1d"), 0)
