@@ -167,7 +167,7 @@ __device__ inline void fine_sigma(const FineOp& g, int px, int py, int pz, int q
 }
 
 // Subvolume b (lexicographic, x fastest) of a level -> origin and extent.
-__device__ inline void subvol_box(const LevelGeom& L, int b, int o[3], int e[3]) {
+__host__ __device__ inline void subvol_box(const LevelGeom& L, int b, int o[3], int e[3]) {
   int bx = b % L.nb[0];
   int rest = b / L.nb[0];
   int by = rest % L.nb[1];
@@ -180,7 +180,7 @@ __device__ inline void subvol_box(const LevelGeom& L, int b, int o[3], int e[3])
   }
 }
 // j-th subvolume of colour `colour` -> subvolume index.  colour bit a = parity of block index on axis a.
-__device__ inline int colour_subvol(const LevelGeom& L, int colour, int j) {
+__host__ __device__ inline int colour_subvol(const LevelGeom& L, int colour, int j) {
   int cb[3] = {colour & 1, (colour >> 1) & 1, (colour >> 2) & 1};
   int cnt[3];
   for (int a = 0; a < 3; ++a) cnt[a] = (L.nb[a] - cb[a] + 1) / 2;
