@@ -260,8 +260,15 @@ la_status la_lfa_maps(const la_lfa_case* cases, int ncases, const double* k, int
    Synchronises cuda_stream.  Errors: LA_EINVAL (polls < 1 or null status_out), LA_ENOMEM, LA_ECUDA. */
 la_status la_wait_selftest(int polls, int* status_out, void* cuda_stream);
 
+/* Waits for the context's stream, then releases everything the context owns (device workspace,
+   factor store, checkpoints, captured graphs, events, pinned read-back buffer) and the context
+   itself; ctx is invalid afterwards.  Caller-owned buffers are untouched.  Errors: LA_EINVAL (null). */
 la_status la_finalize(la_ctx* ctx);
+/* Message of the last error of ctx; with ctx = NULL, of the last call on this host thread that had no
+   context (la_init, la_action_noalloc, la_lfa_maps).  The string stays valid until
+   the next call that records an error on the same context or thread. */
 const char* la_last_error(const la_ctx* ctx);
+/* Library name, version and target architecture (static string). */
 const char* la_version(void);
 
 #ifdef __cplusplus
