@@ -33,7 +33,10 @@
  *
  * Errors: every call returns la_status; no exception crosses the ABI; the text
  * of the last error of a context is available from la_last_error.  After
- * LA_ECUDA the context should be finalised.
+ * LA_ECUDA or LA_ETIMEOUT the context should be finalised.  Calls that run the
+ * relaxation (la_step, la_step_batch, la_solve_step, la_relax_colour, la_backward)
+ * return LA_ECUDA when a subvolume matrix was singular or not positive definite
+ * and LA_ETIMEOUT when a staged copy did not arrive within its bounded wait.
  */
 #ifndef LEASTACTION_H_
 #define LEASTACTION_H_
@@ -48,7 +51,9 @@ typedef enum {
   LA_ENOMEM = 2,    /* device allocation failed */
   LA_ECUDA = 3,     /* CUDA runtime error */
   LA_ENOTCONV = 4,  /* max_cycles reached before rel <= tol (the state is still advanced) */
-  LA_ESTATE = 5     /* call out of order (e.g. la_step before la_set_hamiltonian) */
+  LA_ESTATE = 5,    /* call out of order (e.g. la_step before la_set_hamiltonian) */
+  LA_ETIMEOUT = 6   /* a kernel's bounded wait for a staged copy gave up (the kernel returned; the
+                       device stays usable, the step's result is not valid) */
 } la_status;
 
 typedef struct la_ctx la_ctx;
@@ -255,8 +260,9 @@ la_status la_lfa_maps(const la_lfa_case* cases, int ncases, const double* k, int
                       void* out, void* cuda_stream);
 
 /* Self-test of the bounded waits (no context): one CTA waits on an mbarrier that nothing completes,
-   polling at most `polls` times as the TMA-staged kernels do, and on giving up sets bit 4 of a status
-   word, which is written to *status_out (host).  The wait ends by itself; the device stays usable.
+   polling at most `polls` times as the TMA-staged kernels do, and on giving up sets flag 4 (the value
+   4) of a status word, which is written to *status_out (host).  The wait ends by itself; the device
+   stays usable.
    Synchronises cuda_stream.  Errors: LA_EINVAL (polls < 1 or null status_out), LA_ENOMEM, LA_ECUDA. */
 la_status la_wait_selftest(int polls, int* status_out, void* cuda_stream);
 

@@ -14,8 +14,9 @@ import numpy as np
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "_build", "libleastaction.so")
 
-LA_OK, LA_EINVAL, LA_ENOMEM, LA_ECUDA, LA_ENOTCONV, LA_ESTATE = range(6)
-STATUS_NAMES = {0: "LA_OK", 1: "LA_EINVAL", 2: "LA_ENOMEM", 3: "LA_ECUDA", 4: "LA_ENOTCONV", 5: "LA_ESTATE"}
+LA_OK, LA_EINVAL, LA_ENOMEM, LA_ECUDA, LA_ENOTCONV, LA_ESTATE, LA_ETIMEOUT = range(7)
+STATUS_NAMES = {0: "LA_OK", 1: "LA_EINVAL", 2: "LA_ENOMEM", 3: "LA_ECUDA", 4: "LA_ENOTCONV", 5: "LA_ESTATE",
+                6: "LA_ETIMEOUT"}
 WEIGHTS = {"dual": 0, "literal": 1, "identity": 2}
 LOCAL_FORMS = {"lsq": 0, "square": 1}
 

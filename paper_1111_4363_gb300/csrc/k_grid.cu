@@ -800,7 +800,7 @@ void launch_c128_to_c64(long long n, const double2* x, float2* y, cudaStream_t s
 
 // ------------------------------------------------------------------ bounded-wait self-test
 // One CTA waits on an mbarrier that nothing completes, with the poll loop the staged kernels use,
-// and on giving up sets bit 4 of the status word as they do.
+// and on giving up sets flag 4 of the status word as they do.
 __global__ void k_wait_selftest(unsigned polls, int* status) {
   __shared__ __align__(8) unsigned long long bar;
   if (threadIdx.x == 0) {

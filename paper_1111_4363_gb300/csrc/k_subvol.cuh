@@ -724,7 +724,7 @@ __device__ __forceinline__ void stage_begin(unsigned char* area, const CT* src, 
   }
 }
 // Warp 0 waits (bounded) for the staged factor and solves from shared memory; on a timeout it
-// records status bit 4 and raises the CTA's failure flag instead.  The caller synchronises the
+// records status flag 4 and raises the CTA's failure flag instead.  The caller synchronises the
 // CTA afterwards and skips its update when the flag is set.
 template <typename CT, int NPAD>
 __device__ __forceinline__ void staged_solve(unsigned char* area, CT* rhs, CT* y, CT* tvec, int* status) {

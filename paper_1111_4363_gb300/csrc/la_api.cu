@@ -696,12 +696,12 @@ static la_status sweep_level(la_ctx* c, int l, int nsweeps) {
   return LA_OK;
 }
 
-// Error for a nonzero device status word (bit 1: a subvolume matrix was not positive definite;
-// bit 4: a TMA-staged plane did not arrive within its wait limit).
+// Error for a nonzero device status word (flag 1: a subvolume matrix was not positive definite;
+// flag 4: a staged copy did not arrive within its wait limit).
 static la_status status_error(la_ctx* c, int status) {
   if (status & 1)
     return fail(c, LA_ECUDA, "a subvolume matrix was singular or not positive definite (status %d)", status);
-  return fail(c, LA_ECUDA, "a staged copy did not complete within its wait limit (status %d)", status);
+  return fail(c, LA_ETIMEOUT, "a staged copy did not complete within its wait limit (status %d)", status);
 }
 
 // The TMA tensor map of a finest-level complex64 field, when one was encoded for it.

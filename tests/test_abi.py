@@ -35,6 +35,15 @@ def test_library_exports_every_declared_symbol():
     assert set(binding.EXPORTS) <= set(declared_functions())
 
 
+def test_binding_status_codes_match_the_header():
+    text = open(os.path.join(ROOT, "include", "leastaction.h")).read()
+    codes = {int(v): k for k, v in re.findall(r"\b(LA_[A-Z]+) = (\d+)", text)}
+    from paper_1111_4363_gb300 import binding as B
+    assert codes == B.STATUS_NAMES
+    for value, name in codes.items():
+        assert getattr(B, name) == value
+
+
 def test_init_rejects_invalid_configs_without_touching_the_gpu():
     from paper_1111_4363_gb300 import binding as B
     from paper_1111_4363_gb300 import workloads as wl
