@@ -184,3 +184,44 @@ def test_slow_convergence_only_near_the_dispersion_curve():
             grows[nb][1] += int(np.sum((lrN > 0) & ~near))
     assert grows[8][0] > 0 and grows[8][1] == 0
     assert grows[3][1] > 50
+
+
+def _physical_rows(nx, nt, width, duration, V):
+    """Rows of one element x in [x0, x0 + width], t in [0, duration] in physical units, by quadrature:
+    int int P_j(y) P_m(tau) (i d/dt + 1/2 d^2/dx^2 - V) P_i(y) P_n(tau) dx dt, y and tau the element's
+    Legendre variables (derivatives through the chain rule, x = x0 + width (y + 1)/2)."""
+    from numpy.polynomial import legendre as L
+    q, wq = L.leggauss(nx + nt + 4)
+    e = np.eye(max(nx, nt))
+    P = lambda k, d=0: L.legval(q, L.legder(e[k], d) if d else e[k])
+    sx, st = 2.0 / width, 2.0 / duration
+    jx, jt = width / 2.0 * wq, duration / 2.0 * wq
+    A = np.zeros((nx * nt, nx * nt), dtype=complex)
+    for j in range(nx):
+        for m in range(nt):
+            for i in range(nx):
+                for n in range(nt):
+                    ox = jx @ (P(j) * P(i))
+                    ut = jt @ (P(m) * P(n))
+                    dt_ = jt @ (P(m) * st * P(n, 1))
+                    dxx = jx @ (P(j) * sx ** 2 * P(i, 2))
+                    A[j * nt + m, i * nt + n] = 1j * ox * dt_ + 0.5 * dxx * ut - V * ox * ut
+    return A
+
+
+@pytest.mark.parametrize("width,duration,V", [(2.0, 2.0, 0.0), (0.3, 0.05, -1.7), (1.1, 0.4, 2.5)])
+def test_dimensionless_rows_and_their_scaling(width, duration, V):
+    """Eq. leastaction_dimensionless from the physical rows: divided by the element's half-width, they
+    are i O Qt - 2 kappa K U - nu O U with kappa = p_max^2 dt / 2 and nu = V dt, p_max = 1/dx, where
+    dx and dt are the element's half-extents (the Jacobians of its Legendre variables).  Hence
+    (Sec. IV) doubling the element maps kappa to kappa/4 with nu unchanged, and halving the step maps
+    (kappa, nu) to (kappa/2, nu/2)."""
+    nx, nt = 4, 3
+    hx, ht = width / 2.0, duration / 2.0
+    kappa, nu = (1.0 / hx) ** 2 * ht / 2.0, V * ht
+    A = _physical_rows(nx, nt, width, duration, V) / hx
+    assert np.allclose(A, lfa.element_operator(nx, nt, kappa, nu), atol=1e-11 * np.abs(A).max())
+    A2 = _physical_rows(nx, nt, 2 * width, duration, V) / (2 * hx)
+    assert np.allclose(A2, lfa.element_operator(nx, nt, kappa / 4, nu), atol=1e-11 * np.abs(A2).max())
+    Ah = _physical_rows(nx, nt, width, duration / 2, V) / hx
+    assert np.allclose(Ah, lfa.element_operator(nx, nt, kappa / 2, nu / 2), atol=1e-11 * np.abs(Ah).max())
