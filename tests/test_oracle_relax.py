@@ -288,3 +288,21 @@ def test_stale_local_factors_keep_the_contraction():
     fresh, stale = hists
     assert len(fresh) == len(stale) <= 4
     assert np.all(np.abs(stale / fresh - 1) < 0.05)
+
+
+def test_trial_weights_extrapolate_polynomials_exactly():
+    """The trial of a step (the polynomial of degree q - 1 in the step index through the last q
+    converged coefficient vectors, evaluated one step on) reproduces every polynomial of degree below
+    q and no higher one: the weights used by the oracle's replay of the trial schedule."""
+    from tests.helpers import TRIAL_WEIGHTS
+    rng = np.random.default_rng(3)
+    for q, a in TRIAL_WEIGHTS.items():
+        for deg in range(q + 1):
+            coef = rng.standard_normal(deg + 1)
+            p = lambda s: np.polyval(coef, s)
+            n = 7.0
+            pred = sum(ai * p(n - 1 - i) for i, ai in enumerate(a))
+            if deg < q:
+                assert abs(pred - p(n)) < 1e-9 * max(1.0, abs(p(n)))
+            else:
+                assert abs(pred - p(n)) > 1e-6
