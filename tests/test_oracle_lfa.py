@@ -225,3 +225,21 @@ def test_dimensionless_rows_and_their_scaling(width, duration, V):
     assert np.allclose(A2, lfa.element_operator(nx, nt, kappa / 4, nu), atol=1e-11 * np.abs(A2).max())
     Ah = _physical_rows(nx, nt, width, duration / 2, V) / hx
     assert np.allclose(Ah, lfa.element_operator(nx, nt, kappa / 2, nu / 2), atol=1e-11 * np.abs(Ah).max())
+
+
+@pytest.mark.parametrize("nel", [1, 2])
+def test_plane_wave_overlaps_closed_form(nel):
+    """int_{-1}^{1} exp(i a y) P_n(y) dy = 2 i^n j_n(a) (spherical Bessel function): the trial's
+    overlaps with one element, and with the children x = (y - 1)/2, (y + 1)/2 of two elements
+    (a = k/2 and the phase exp(-+ i k/2))."""
+    from scipy.special import spherical_jn
+    nx, nt, k, w = 5, 4, 3.7, -2.2
+    got = lfa.plane_wave_overlaps(nx, nt, nel, k, w).reshape(nel, nx, nt)
+    bt = np.array([2 * 1j ** n * spherical_jn(n, w) for n in range(nt)])
+    for e in range(nel):
+        if nel == 1:
+            ax = np.array([2 * 1j ** i * spherical_jn(i, k) for i in range(nx)])
+        else:
+            shift = -0.5 if e == 0 else 0.5
+            ax = np.exp(1j * k * shift) * np.array([2 * 1j ** i * spherical_jn(i, k / 2) for i in range(nx)])
+        assert np.allclose(got[e], np.outer(ax, bt), atol=1e-13)
