@@ -3,9 +3,10 @@
 A plain, slow, FP64 NumPy/SciPy restatement of what the method computes, written
 from the paper (Walters, "An efficient parallel method for relaxing to the
 minimum action wavefunction").  Only the tests, ``__graft_entry__.smoke()`` and
-the benchmark's CPU legs (``cpu_baseline`` and ``--impl reference``) may import it.  It shares no code with the
-CUDA path; the only common module is ``paper_1111_4363_gb300.workloads`` (the
-seeded synthetic inputs, which hold none of the method's arithmetic).
+the benchmark's CPU legs (``cpu_baseline`` and ``--impl reference``) may import
+it.  It shares no code with the CUDA path; the only common module is
+``paper_1111_4363_gb300.workloads`` (the seeded synthetic inputs, which hold none
+of the method's arithmetic).
 
 Modules
 -------
