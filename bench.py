@@ -220,6 +220,16 @@ def l2_note(w, precision):
             f"L2; not flushed between steps")
 
 
+def workload_config(w, precision, ws):
+    """The "config" object of a bench line; the reference arm prints the same one."""
+    return {"workload": w.name, "grid": list(w.shape), "K": w.nt, "subvolume": list(w.sub[:w.dim]),
+            "levels": w.levels, "cycle": cycle_name(w), "coarse_sweeps": w.coarse_sweeps,
+            "tol_rel_action": w.tol, "precision": precision, "trial": w.trial,
+            "local_form": getattr(w, "local_form", "lsq"),
+            "parallelism": "replicas" if ws > 1 else "single",
+            "l2": l2_note(w, precision)}
+
+
 def dominant_roofline(prof, w, precision, ms_total, traffic_ok):
     """Roofline of the dominant kernel class (the larger total device time of factor and sweep)."""
     fac_ms = prof["ms_factor"] / max(prof["n_factor"], 1)
@@ -354,12 +364,7 @@ def run_ours(args):
     out = {"metric": METRIC, "value": value, "unit": "unknowns/s", "n_gpus": ws, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": prec_tag, "data": "synthetic",
-           "config": {"workload": w.name, "grid": list(w.shape), "K": w.nt, "subvolume": list(w.sub[:w.dim]),
-                      "levels": w.levels, "cycle": cycle_name(w), "coarse_sweeps": w.coarse_sweeps,
-                      "tol_rel_action": w.tol, "precision": args.precision, "trial": w.trial,
-                      "local_form": getattr(w, "local_form", "lsq"),
-                      "parallelism": "replicas" if ws > 1 else "single",
-                      "l2": l2_note(w, args.precision)},
+           "config": workload_config(w, args.precision, ws),
            "cycles_per_step": cycles / args.steps, "fine_sweeps_per_step": sweeps / args.steps,
            "ms_per_time_step_to_tol": ms_max / args.steps,
            "e2e": {"value": e2e_value, "unit": "unknowns/s", "h2d_bytes_per_step": 16 * w.npoints,
@@ -452,7 +457,9 @@ def run_reference(args):
     out = {"impl": "reference", "metric": METRIC, "value": value, "unit": "unknowns/s", "n_gpus": ws,
            "steps": steps, "warmup": args.warmup, "ms_per_step": el / steps * 1e3, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-           "config": {"workload": w.name, "grid": list(w.shape), "K": w.nt, "levels": w.levels},
+           "config": workload_config(w, 0, ws),
+           "reference_step": f"one oracle V-cycle ({sweeps} finest-level sweeps) of the workload on the host, "
+                             f"from the same schedule; host memory, no L2 flush",
            "cpu_baseline": {"value": value, "unit": "unknowns/s", "cores": cores, "kind": "oracle",
                             "sample": f"{steps} V-cycles of {w.name} after an untimed setup of {setup_s:.1f} s"},
            "e2e": {"value": value, "unit": "unknowns/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}

@@ -75,3 +75,23 @@ def test_factor_store_and_l2_note(bench):
     assert bench.finest_factor_store(bench.workload("2d-square"), 0) == (4096, 96 * 96 * 16)
     assert "352 MB" in bench.l2_note(w, 0) and "(> L2)" in bench.l2_note(w, 0)
     assert "fits in L2" in bench.l2_note(bench.workload("1d"), 0)
+
+
+def test_reference_arm_line(bench):
+    """`--impl reference` (the CPU oracle, run here on the 1D workload) prints one JSON line with the
+    contract's keys and the same config object as the GPU arm."""
+    import json
+    import subprocess
+    import sys
+    out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--workload", "1d",
+                          "--steps", "2", "--warmup", "1"], capture_output=True, text=True, timeout=300, cwd=ROOT)
+    assert out.returncode == 0, out.stderr
+    lines = [ln for ln in out.stdout.splitlines() if ln.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["metric"] == bench.METRIC and d["unit"] == "unknowns/s"
+    assert d["value"] > 0 and d["higher_is_better"] is True and d["n_gpus"] == 1
+    assert d["config"] == bench.workload_config(bench.workload("1d"), 0, 1)
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
+    assert d["cpu_baseline"]["value"] == d["value"]
+    assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
