@@ -5,7 +5,7 @@ Every candidate reaches the same tolerance on N/N(0) (the minimiser does not dep
 schedule), so candidates are ranked by measured time per least-action step on the GPU.  The
 colouring is not a free parameter: same-colour subvolumes must not interact through the radius-2
 normal operator, which leaves the 2^d block-parity classes (a checkerboard is invalid).  Results
-are cached in JSON next to the built library, keyed by grid, K, precision and weight.
+are cached in JSON next to the built library, keyed by grid, K, precision, weight and trial.
 """
 from __future__ import annotations
 
@@ -72,7 +72,8 @@ def tune(w: wl.Workload, precision: int = 0, use_cache: bool = True, verbose: bo
             cache = json.load(fh)
     k = key(w, precision)
     if use_cache and k in cache:
-        return cache[k]["best"]
+        # JSON holds the tuple-valued fields (subvolume shapes) as lists
+        return {f: tuple(v) if isinstance(v, list) else v for f, v in cache[k]["best"].items()}
     results = []
     for cand in candidates(w):
         wc = dataclasses.replace(w, **cand)
@@ -86,6 +87,8 @@ def tune(w: wl.Workload, precision: int = 0, use_cache: bool = True, verbose: bo
             results.append((r["ms_per_step"], cand, r))
             if verbose:
                 print(cand, r)
+    if not results:
+        raise RuntimeError(f"autotune: no candidate schedule reached N/N(0) <= {w.tol} for {k}")
     results.sort(key=lambda x: x[0])
     best = results[0][1]
     cache[k] = {"best": best, "table": [dict(c, **r) for _, c, r in results]}

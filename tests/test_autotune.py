@@ -31,3 +31,42 @@ def test_cache_key_separates_precision_and_trial():
     w = wl.batched_2d(0)
     keys = {autotune.key(dataclasses.replace(w, trial=t), p) for t in (0, 3) for p in (0, 1)}
     assert len(keys) == 4
+
+
+def test_tune_ranks_by_time_among_converged_candidates_and_caches(monkeypatch, tmp_path):
+    """tune() on the CPU with the GPU measurement replaced: the fastest candidate that reached the
+    tolerance wins, candidates that did not converge or were rejected by la_init are skipped, the
+    table is cached and a second call reads the cache without measuring."""
+    from paper_1111_4363_gb300 import autotune
+    from paper_1111_4363_gb300 import binding as B
+    monkeypatch.setattr(autotune, "CACHE", str(tmp_path / "autotune.json"))
+    w = dataclasses.replace(wl.batched_2d(0), n=(128, 128, 1), trial=3)
+    cands = autotune.candidates(w)
+    calls = []
+
+    def fake_measure(wc, precision):
+        i = len(calls)
+        calls.append(wc)
+        if i == 0:
+            raise B.LeastActionError(B.LA_EINVAL, "rejected")
+        rel = 1.0 if i == 1 else w.tol / 2          # candidate 1 is the fastest but does not converge
+        return {"ms_per_step": 0.5 if i == 1 else 10.0 + (i * 7919) % 13, "cycles": 2.0, "rel": rel}
+
+    monkeypatch.setattr(autotune, "measure", fake_measure)
+    best = autotune.tune(w, 0)
+    assert len(calls) == len(cands)
+    times = {i: 10.0 + (i * 7919) % 13 for i in range(2, len(cands))}
+    fastest = min(times, key=lambda i: (times[i], i))
+    assert best == cands[fastest]
+    monkeypatch.setattr(autotune, "measure", lambda *a: pytest.fail("measured despite the cache"))
+    assert autotune.tune(w, 0) == best
+    table = __import__("json").load(open(autotune.CACHE))[autotune.key(w, 0)]["table"]
+    assert len(table) == len(cands) - 2
+
+
+def test_tune_reports_when_nothing_converges(monkeypatch, tmp_path):
+    from paper_1111_4363_gb300 import autotune
+    monkeypatch.setattr(autotune, "CACHE", str(tmp_path / "autotune.json"))
+    monkeypatch.setattr(autotune, "measure", lambda wc, p: {"ms_per_step": 1.0, "cycles": 9.0, "rel": 1.0})
+    with pytest.raises(RuntimeError, match="no candidate"):
+        autotune.tune(dataclasses.replace(wl.batched_2d(0), n=(64, 64, 1)), 0)
