@@ -135,7 +135,8 @@ la_status la_set_hamiltonian(la_ctx* ctx, const double* V0, const la_pulse* puls
    c = 0, else from c = 0.  The history is kept across calls whose t0 continues the previous call,
    and cleared at every checkpoint (ckpt_every > 0), by la_set_hamiltonian and by la_backward, so
    the recomputation in la_backward repeats the forward iterates exactly.
-   Returns LA_ENOTCONV if some step hit max_cycles (psi is still advanced). */
+   Returns LA_ENOTCONV if some step hit max_cycles or its action became non-finite (psi is still
+   advanced). */
 la_status la_step(la_ctx* ctx, void* psi, int nsteps, double t0, la_step_stats* per_step);
 
 /* Many independent propagations stepped together (each context its own grid, potential, pulse and

@@ -923,6 +923,7 @@ static la_status solve_current(la_ctx* c, int ncycles, la_step_stats* st, bool u
   const bool check = ncycles <= 0 && k.tol > 0;
   while (cyc < maxc) {
     if (check && N <= k.tol * N0) break;
+    if (!std::isfinite(N)) break;   // canary: a non-finite action ends the relaxation
     LA_TRY(run_cycle(c, &N));
     ++cyc;
   }
@@ -942,6 +943,7 @@ static la_status solve_current(la_ctx* c, int ncycles, la_step_stats* st, bool u
     st->action = N;
     st->rel_action = c->last_rel;
   }
+  if (!std::isfinite(N)) return fail(c, LA_ENOTCONV, "the action is not finite after %d cycles", cyc);
   if (check && !(N <= k.tol * N0)) return fail(c, LA_ENOTCONV, "not converged after %d cycles (rel %.3e)", cyc, c->last_rel);
   return LA_OK;
 }
@@ -1053,6 +1055,7 @@ static la_status adjoint_solve(la_ctx* c, int* cycles) {
     ++cyc;
     LA_TRY(rho_norm(&N));
   }
+  if (!std::isfinite(N)) return fail(c, LA_ENOTCONV, "the adjoint residual norm is not finite after %d cycles", cyc);
   if (cycles) *cycles = cyc;
   if (T > 0) {   // history of converged adjoint solutions
     LA_CUDA(c, cudaMemcpyAsync(c->d_ahist[c->ahist_head], c->d_c, sizeof(double2) * (size_t)n, cudaMemcpyDeviceToDevice,
@@ -1240,7 +1243,7 @@ extern "C" la_status la_step_batch(la_ctx* const* ctxs, int nctx, void* const* p
         la_ctx* c = ctxs[i];
         const bool check = c->cfg.tol > 0;
         if (!active[i]) continue;
-        if ((check && N[i] <= c->cfg.tol * N0[i]) || cyc[i] >= c->cfg.max_cycles) {
+        if ((check && N[i] <= c->cfg.tol * N0[i]) || cyc[i] >= c->cfg.max_cycles || !std::isfinite(N[i])) {
           active[i] = 0;
           continue;
         }
