@@ -1,7 +1,6 @@
 """la_step_batch: independent propagations stepped together equal the same propagations stepped alone."""
 import dataclasses
 
-import numpy as np
 import pytest
 
 from paper_1111_4363_gb300 import workloads as wl

@@ -4,7 +4,7 @@ import dataclasses
 import numpy as np
 import pytest
 
-from oracle import multigrid, relax, system, timebasis as tb
+from oracle import multigrid, relax, system
 from oracle.propagate import numpy_coarse_nu, numpy_coarse_sub, numpy_sub
 from paper_1111_4363_gb300 import workloads as wl
 from tests.helpers import gpu_context, oracle_system, ragged_2d, rel_l2, small_3d, to_dev, variant

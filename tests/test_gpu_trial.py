@@ -1,7 +1,6 @@
 """la_step with an extrapolated trial iterate (cfg.trial > 0) vs the oracle replaying the same schedule."""
 import dataclasses
 
-import numpy as np
 import pytest
 
 from paper_1111_4363_gb300 import workloads as wl

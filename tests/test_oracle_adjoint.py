@@ -1,5 +1,4 @@
 """Pins for the oracle's discrete adjoint: central finite differences of the forward map."""
-import copy
 
 import numpy as np
 import pytest

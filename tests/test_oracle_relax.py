@@ -4,7 +4,7 @@ import pytest
 import scipy.sparse as sp
 
 from oracle import legendre_elements as le
-from oracle import multigrid, propagate, relax, system
+from oracle import multigrid, relax, system
 from paper_1111_4363_gb300 import workloads as wl
 
 

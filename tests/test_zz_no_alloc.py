@@ -6,7 +6,6 @@ keeps its scratch in a static device array.  It must agree with the context-base
 two calls in a row (the second call reuses the array the first one left behind).  This file is
 collected last on purpose.
 """
-import numpy as np
 import pytest
 
 from paper_1111_4363_gb300 import workloads as wl
