@@ -146,7 +146,7 @@ la_status la_step(la_ctx* ctx, void* psi, int nsteps, double t0, la_step_stats* 
    cycle per unconverged context, then one synchronisation per context -- until every context reached
    its tolerance, so the small per-context launches of different problems run concurrently.
    stats (host, nullable): nctx * nsteps records, context-major.  Returns LA_ENOTCONV if some step of
-   some context hit max_cycles.  Errors: LA_EINVAL (null or repeated context), LA_ESTATE, LA_ECUDA. */
+   some context hit max_cycles or its action became non-finite (whatever that context's tol).  Errors: LA_EINVAL (null or repeated context), LA_ESTATE, LA_ECUDA. */
 la_status la_step_batch(la_ctx* const* ctxs, int nctx, void* const* psis, int nsteps, const double* t0s,
                         la_step_stats* stats);
 
@@ -221,12 +221,16 @@ la_status la_profile_read(la_ctx* ctx, la_profile* out);
    device memory through its own pool, or a process whose device memory budget is already spent).
    Computes N = r^dagger W r of trial coefficients c (complex128[Np*K]) for initial state psi0
    (complex128[Np]) at time t0, exactly as la_residual does, but with no context and no allocation:
-   V0, psi0 and c must be device pointers; *action is a host double.  Scratch (per-step time
-   matrices, per-block partial sums, the result) lives in one static device array of about 140 KB
-   that every GPU loading the library keeps until exit; grids of more than LA_NOALLOC_MAX_POINTS
-   points are rejected with LA_EINVAL.  All calls share that array and overwrite it completely, so
-   calls that overlap on the GPU race and must be serialised by the caller.  The first call on a
-   device looks up the array's address with that device current; make it before any stream capture.
+   V0, psi0 and c must be device (or managed) pointers, else LA_EINVAL; *action is a host double.
+   Scratch (per-step time matrices, per-block partial sums, the result) lives in one static device
+   array of about 140 KB that every GPU loading the library keeps until exit; grids of more than
+   LA_NOALLOC_MAX_POINTS points are rejected with LA_EINVAL.  All calls share that array and
+   overwrite it completely, so calls that overlap on the GPU race and must be serialised by the
+   caller.  The first call in a CUDA context (normally a device's primary context) looks up the
+   array's address with that device current and keeps it for that context; make it before any
+   stream capture.  Under lazy module loading (the CUDA default) that first call may also load the
+   library's module, which takes device memory for its code and the array: a process that must not
+   allocate at all sets CUDA_MODULE_LOADING=EAGER or makes one call early.
    Synchronises cuda_stream.  Errors: LA_EINVAL (message in la_last_error(NULL)), LA_ECUDA. */
 #define LA_NOALLOC_MAX_POINTS (1 << 22)
 la_status la_action_noalloc(const la_config* cfg, const double* V0, const la_pulse* pulse, const void* psi0,

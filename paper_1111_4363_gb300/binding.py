@@ -309,6 +309,10 @@ class Context:
         self._check(self._lib.la_profile_read(self.handle, C.byref(p)))
         return {k: getattr(p, k) for k, _ in la_profile._fields_}
 
+    def last_error(self) -> str:
+        """la_last_error of this context."""
+        return self._lib.la_last_error(self.handle).decode()
+
     def close(self):
         if getattr(self, "handle", None):
             self._lib.la_finalize(self.handle)

@@ -1273,7 +1273,14 @@ extern "C" la_status la_step_batch(la_ctx* const* ctxs, int nctx, void* const* p
         r.action = N[i];
         r.rel_action = c->last_rel;
       }
-      if (c->cfg.tol > 0 && !(N[i] <= c->cfg.tol * N0[i])) worst = LA_ENOTCONV;
+      // canary as in la_step: a non-finite action fails the member whatever its tolerance
+      if (!std::isfinite(N[i])) {
+        fail(c, LA_ENOTCONV, "the action is not finite after %d cycles", cyc[i]);
+        worst = LA_ENOTCONV;
+      } else if (c->cfg.tol > 0 && !(N[i] <= c->cfg.tol * N0[i])) {
+        fail(c, LA_ENOTCONV, "not converged after %d cycles (rel %.3e)", cyc[i], c->last_rel);
+        worst = LA_ENOTCONV;
+      }
       launch_advance(c->np0, c->d_tm, c->d_c, c->d_psi, c->stream);
       ++c->launches;
       st = hist_push(c);

@@ -8,12 +8,19 @@
 //
 // Limits and sharing rules:
 //   * at most LA_NOALLOC_MAX_POINTS grid points; larger grids are rejected with LA_EINVAL;
+//   * V0, psi0 and c must be device (or managed) memory; host pointers are rejected with LA_EINVAL;
 //   * every GPU that loads this library holds the array (about 140 KB) until the process exits;
 //   * all calls share the array: each call overwrites it completely before reading it, so no state
 //     leaks between calls, but calls that overlap on the GPU (different streams or host threads)
 //     race on it and must be serialised by the caller;
-//   * the first call on a device looks up the array's device address (cudaGetSymbolAddress) with
-//     that device current; make that first call before any stream capture.
+//   * set-up: the first call in a CUDA context (normally the primary context of a device) looks up
+//     the array's device address (cudaGetSymbolAddress) with that device current and keeps it for
+//     that context; make that first call before any stream capture.  The address is keyed by the
+//     context's unique id, so a context created later on the same device (after cudaDeviceReset,
+//     or a caller-created context) gets its own lookup instead of a stale address;
+//   * under lazy module loading (the CUDA default) the first call in a context may load this
+//     library's module, which takes device memory for its code and this array; a process that must
+//     not allocate at all sets CUDA_MODULE_LOADING=EAGER or makes one call early.
 #include <mutex>
 #include <string>
 
@@ -39,24 +46,86 @@ constexpr size_t kScratchBytes = kTmBytes + sizeof(double) * (kMaxBlocks + 32);
 __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 
 std::mutex g_mu;
-void* g_addr[64] = {};
+// (context id, scratch address) of the contexts seen so far; a small ring, newest overwriting oldest
+constexpr int kCacheSlots = 64;
+struct CacheSlot {
+  unsigned long long id;
+  void* addr;
+};
+CacheSlot g_cache[kCacheSlots] = {};
+int g_cache_next = 0;
 
+typedef CUresult (*PfnCtxGetCurrent)(CUcontext*);
+typedef CUresult (*PfnCtxGetId)(CUcontext, unsigned long long*);
+
+// Unique id of the CUDA context current on this thread (0 when none is current or the driver
+// entry points are unavailable).
+unsigned long long current_context_id() {
+  static PfnCtxGetCurrent get_cur = nullptr;
+  static PfnCtxGetId get_id = nullptr;
+  static bool looked_up = false;
+  if (!looked_up) {
+    void* f1 = nullptr;
+    void* f2 = nullptr;
+    cudaDriverEntryPointQueryResult q1, q2;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f1, 12000, cudaEnableDefault, &q1) == cudaSuccess &&
+        q1 == cudaDriverEntryPointSuccess)
+      get_cur = reinterpret_cast<PfnCtxGetCurrent>(f1);
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f2, 12000, cudaEnableDefault, &q2) == cudaSuccess &&
+        q2 == cudaDriverEntryPointSuccess)
+      get_id = reinterpret_cast<PfnCtxGetId>(f2);
+    cudaGetLastError();
+    looked_up = true;
+  }
+  if (!get_cur || !get_id) return 0;
+  CUcontext cu = nullptr;
+  if (get_cur(&cu) != CUDA_SUCCESS || !cu) return 0;
+  unsigned long long id = 0;
+  if (get_id(cu, &id) != CUDA_SUCCESS) return 0;
+  return id;
+}
+
+// Device address of the scratch array in the current context: looked up once per context (with
+// the device current) and cached by the context's id.
 la_status scratch_for_current_device(void** out) {
   int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess || dev < 0 || dev >= 64) return LA_ECUDA;
-  std::lock_guard<std::mutex> lk(g_mu);
-  if (!g_addr[dev]) {
-    void* p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-    if (e != cudaSuccess || !p) {
-      set_thread_error(cudaGetErrorString(e));
-      return LA_ECUDA;
-    }
-    g_addr[dev] = p;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    cudaGetLastError();
+    set_thread_error("la_action_noalloc: no CUDA device");
+    return LA_ECUDA;
   }
-  *out = g_addr[dev];
+  std::lock_guard<std::mutex> lk(g_mu);
+  unsigned long long id = current_context_id();
+  if (id != 0)
+    for (int i = 0; i < kCacheSlots; ++i)
+      if (g_cache[i].id == id) {
+        *out = g_cache[i].addr;
+        return LA_OK;
+      }
+  void* p = nullptr;
+  cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+  if (e != cudaSuccess || !p) {
+    cudaGetLastError();
+    set_thread_error(e != cudaSuccess ? cudaGetErrorString(e) : "la_action_noalloc: null scratch address");
+    return LA_ECUDA;
+  }
+  // the lookup makes the device's primary context current when none was
+  if (id == 0) id = current_context_id();
+  if (id != 0) {
+    g_cache[g_cache_next] = CacheSlot{id, p};
+    g_cache_next = (g_cache_next + 1) % kCacheSlots;
+  }
+  *out = p;
   return LA_OK;
+}
+
+bool on_device(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
 // Variant of the residual kernel that forms f~ from psi0 on the fly instead of reading a stored
@@ -160,6 +229,12 @@ extern "C" la_status la_action_noalloc(const la_config* cfg, const double* V0, c
       return LA_EINVAL;
     }
     g.n[a] = a < k.dim ? k.n[a] : 1;
+    // each factor is checked before the product grows: three axes of up to 2^31 points would
+    // overflow even a 64-bit count
+    if (g.n[a] > kMaxPoints || np * g.n[a] > kMaxPoints) {
+      set_thread_error("la_action_noalloc: the grid exceeds LA_NOALLOC_MAX_POINTS points");
+      return LA_EINVAL;
+    }
     g.h[a] = a < k.dim ? k.h[a] : 1.0;
     g.ih2[a] = a < k.dim ? 1.0 / (k.h[a] * k.h[a]) : 0.0;
     g.x0[a] = -0.5 * (g.n[a] - 1) * g.h[a];
@@ -169,8 +244,8 @@ extern "C" la_status la_action_noalloc(const la_config* cfg, const double* V0, c
     }
     np *= g.n[a];
   }
-  if (np > kMaxPoints) {
-    set_thread_error("la_action_noalloc: the grid exceeds LA_NOALLOC_MAX_POINTS points");
+  if (!on_device(V0) || !on_device(psi0) || !on_device(c)) {
+    set_thread_error("la_action_noalloc: V0, psi0 and c must be device pointers");
     return LA_EINVAL;
   }
   const int nc = pulse ? pulse->ncomp : 0;

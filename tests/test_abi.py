@@ -80,3 +80,25 @@ def test_allocation_failure_reports_enomem(monkeypatch):
     with pytest.raises(B.LeastActionError, match="LA_FAIL_ALLOC") as e:
         B.Context(cfg)
     assert e.value.status == B.LA_ENOMEM
+
+
+def test_noalloc_rejects_oversized_grids_and_host_pointers_without_the_gpu():
+    """la_action_noalloc checks every axis before it multiplies them (three axes of 2^31 - 1 points
+    would overflow a 64-bit count), and rejects host buffers; both before any device work."""
+    import numpy as np
+    from paper_1111_4363_gb300 import binding as B
+    from paper_1111_4363_gb300 import workloads as wl
+    w = wl.hydrogen_3d(n=8, nsteps=4, ncomp=4, sub=2)
+    host = np.zeros(8, dtype=np.complex128)
+    for ext in [(2 ** 31 - 1,) * 3, (2 ** 22 + 1, 1, 1), (2048, 2048, 2)]:
+        cfg = B.config_from_workload(w)
+        for a in range(3):
+            cfg.n[a] = ext[a]
+        with pytest.raises(B.LeastActionError, match="LA_NOALLOC_MAX_POINTS") as e:
+            B.action_noalloc(cfg, host.real.copy(), w.pulse, host, 0.0, host)
+        assert e.value.status == B.LA_EINVAL
+    cfg = B.config_from_workload(w)
+    with pytest.raises(B.LeastActionError, match="device pointers") as e:
+        B.action_noalloc(cfg, np.zeros(w.npoints), w.pulse, np.zeros(w.npoints, np.complex128), 0.0,
+                         np.zeros(w.nunknowns, np.complex128))
+    assert e.value.status == B.LA_EINVAL

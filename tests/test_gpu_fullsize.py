@@ -142,6 +142,13 @@ def test_2d_converged_steps_meet_the_stopping_rule(w2d, sys2d):
             assert N_ref / N0 <= tol * (1 + 1e-6), (precision, tol, N_ref / N0)
             if tol == w2d.tol:
                 assert N == pytest.approx(N_ref, rel=1e-6)
+                # the same iterates measured with the paper's printed weight O x U (Eq. residnorm as
+                # printed) and with W = I: the stopping rule holds in those norms too
+                for name in ("literal", "identity"):
+                    _, _, Wx = system.assemble(prob, T0, psi0, name)
+                    rel_x = system.action_norm(system.residual(M, f, c), Wx) / system.action_norm(f, Wx)
+                    print(f"\n256^2 precision {precision}: N/N(0) dual {N_ref / N0:.3e}, {name} {rel_x:.3e}")
+                    assert rel_x <= tol, (precision, name, rel_x)
             out[(precision, tol)] = c
     # mixed precision refined to 1e-22 equals the FP64 result to 1e-9
     assert rel_l2(out[(1, 1e-22)], out[(0, 1e-22)]) < 1e-9

@@ -83,3 +83,65 @@ def test_quadrature_converged_for_pulses():
 def test_end_values():
     # phi(t0+dt) weights b_n(1) = 1 - (-1)^n: 2 for odd n, 0 for even n
     np.testing.assert_array_equal(tb.end_values(5), [2, 0, 2, 0, 2])
+
+
+def test_pulse_field_by_value():
+    """E(t) where its value is known without the formula: each envelope is 1 at its centre and
+    e^-1 one width sigma away on either side (exp(-((t - tc)/sigma)^2), not exp(-(t - tc)^2/(2 sigma^2))),
+    sigma = 0 leaves the bare sin(omega t) of the absolute time t, and components add."""
+    import math
+    from paper_1111_4363_gb300 import workloads as wl
+    amp, om, tc, sg = 0.3, 0.7, 5.0, 2.0
+    one = wl.Pulse(amp=[amp], omega=[om], t_center=[tc], sigma=[sg])
+    e = tb.pulse_field(one, np.array([tc, tc + sg, tc - sg, tc + 2 * sg]))
+    np.testing.assert_allclose(e[0], amp * math.sin(om * tc), rtol=1e-15)
+    np.testing.assert_allclose(e[1], amp * math.exp(-1.0) * math.sin(om * (tc + sg)), rtol=1e-14)
+    np.testing.assert_allclose(e[2], amp * math.exp(-1.0) * math.sin(om * (tc - sg)), rtol=1e-14)
+    np.testing.assert_allclose(e[3], amp * math.exp(-4.0) * math.sin(om * (tc + 2 * sg)), rtol=1e-14)
+    bare = wl.Pulse(amp=[amp], omega=[om], t_center=[tc], sigma=[0.0])
+    t = np.array([0.0, 0.4, 3.1, 17.25])
+    np.testing.assert_allclose(tb.pulse_field(bare, t), amp * np.sin(om * t), rtol=1e-15, atol=1e-17)
+    # the 2D workload's field 0.05 sin(0.057 t): zero at t = 0, 0.05 at the first crest t = pi/(2 0.057)
+    w2 = wl.softcore_2d(n=32, levels=1)
+    crest = math.pi / (2 * 0.057)
+    np.testing.assert_allclose(tb.pulse_field(w2.pulse, np.array([0.0, crest])), [0.0, 0.05], atol=1e-16)
+    two = wl.Pulse(amp=[amp, -0.2], omega=[om, 1.3], t_center=[tc, 1.0], sigma=[sg, 0.0])
+    t = np.linspace(-3.0, 9.0, 13)
+    np.testing.assert_allclose(tb.pulse_field(two, t), tb.pulse_field(one, t) - 0.2 * np.sin(1.3 * t), atol=1e-16)
+    # the unit-amplitude component fields: E = sum_k amp_k E_k, and each E_k is 1 x its sine at its centre
+    w3 = wl.hydrogen_3d(n=8, nsteps=400)
+    t = np.linspace(0.0, 20.0, 41)
+    parts = sum(a * tb.pulse_component_field(w3.pulse, k, t) for k, a in enumerate(w3.pulse.amp))
+    np.testing.assert_allclose(parts, tb.pulse_field(w3.pulse, t), atol=1e-16)
+    for k in (0, 7, 31):
+        c = w3.pulse.t_center[k]
+        np.testing.assert_allclose(tb.pulse_component_field(w3.pulse, k, np.array([c]))[0],
+                                   math.sin(w3.pulse.omega[k] * c), rtol=1e-15, atol=1e-17)
+
+
+@pytest.mark.parametrize("t0", [0.0, 4.35])
+def test_field_matrices_against_adaptive_quadrature(t0):
+    """Eb and Eb0 of one Gaussian-enveloped component against scipy's adaptive quadrature of
+    (dt/2) int b_m b_n E(t(tau)) dtau with t(tau) = t0 + (tau + 1) dt/2, the b_n from scipy's own
+    Legendre polynomials: pins the step's time variable as well as the envelope."""
+    import math
+    from scipy import integrate, special
+    from paper_1111_4363_gb300 import workloads as wl
+    K, dt = 4, 0.6
+    p = wl.Pulse(amp=[0.8], omega=[1.1], t_center=[t0 + 0.2], sigma=[0.35])
+    Eb, Eb0 = tb.field_matrices(K, dt, t0, lambda t: tb.pulse_field(p, t))
+
+    def b(n, tau):
+        return special.eval_legendre(n, tau) - (-1.0) ** n
+
+    def field(tau):
+        t = t0 + 0.5 * (tau + 1.0) * dt
+        return 0.8 * math.exp(-((t - (t0 + 0.2)) / 0.35) ** 2) * math.sin(1.1 * t)
+
+    for m in range(1, K + 1):
+        ref0 = 0.5 * dt * integrate.quad(lambda x: b(m, x) * field(x), -1, 1, epsabs=1e-15, epsrel=1e-13)[0]
+        assert Eb0[m - 1] == pytest.approx(ref0, rel=1e-10, abs=1e-15)
+        for n in range(1, K + 1):
+            ref = 0.5 * dt * integrate.quad(lambda x: b(m, x) * b(n, x) * field(x), -1, 1,
+                                            epsabs=1e-15, epsrel=1e-13)[0]
+            assert Eb[m - 1, n - 1] == pytest.approx(ref, rel=1e-10, abs=1e-15), (m, n)
