@@ -551,6 +551,243 @@ k_factor_blk(LevelGeom L, FineOp g, int is_fine, int nptsmax, const double* __re
   }
 }
 
+// ======================================================================== wide subvolumes
+// Finest-level subvolumes of up to 256 unknowns (4 x 4 x 4 points x K = 4 in 3D, 8 x 8 x 4 in 2D).
+// Their factor (136 blocks: 557 KB complex128, 279 KB complex64) fits in no CTA's shared memory, so
+// one 256-thread CTA per subvolume factorises left-looking by 16-column block columns directly in
+// the factor store: block column J is assembled in registers, updated with the finished block
+// columns 0..J-1 read back from global memory (recently written by the same CTA, so mostly L2
+// hits), its diagonal block is factorised in shared memory, the blocks below it are divided by it,
+// and the column is stored.  Entries of G_UU come from closed forms of H and H^2 on the grid, so no
+// table of point pairs is needed.
+constexpr int kWidePtsMax = 64;   // grid points of a wide subvolume
+
+// Shared-memory layout of the wide factorisation (bytes), for the padded size npad.
+__host__ __device__ constexpr size_t wide_factor_smem(int npad, size_t csize, size_t rsize) {
+  return csize * ((size_t)(npad - LA_BLK) * LA_BLK    // block row J, transposed [k][c]
+                  + (size_t)npad * LA_BLK             // the block column's rows 16 J .. npad-1
+                  + 256)                              // inv(L_JJ)^dagger, [k][c]
+         + rsize * (LA_NPAIR * LA_KMAX * LA_KMAX + 3 * kWidePtsMax + LA_BLK) + sizeof(int) * kWidePtsMax;
+}
+
+// H_pq and (H^2)_pq of the finest-level operator H = -1/2 Laplacian + V0 for grid points p, q of one
+// subvolume: D = dsum + V0 on the diagonal, -w_a = -1/(2 h_a^2) between neighbours along axis a,
+// and H^2 by the paths of length two inside the grid (Dirichlet walls: the diagonal of H^2 counts
+// only in-grid neighbours, nb2 = sum_a w_a^2 over them).
+template <typename R>
+__device__ __forceinline__ void wide_h_h2(int dx, int dy, int dz, R Dp, R Dq, R nb2p, R wx, R wy, R wz, R& H,
+                                          R& H2) {
+  const int ax = abs(dx), ay = abs(dy), az = abs(dz), a1 = ax + ay + az;
+  H = 0;
+  H2 = 0;
+  if (a1 == 0) {
+    H = Dp;
+    H2 = Dp * Dp + nb2p;
+  } else if (a1 == 1) {
+    const R w = ax ? wx : (ay ? wy : wz);
+    H = -w;
+    H2 = -w * (Dp + Dq);
+  } else if (a1 == 2) {
+    if (ax == 2) H2 = wx * wx;
+    else if (ay == 2) H2 = wy * wy;
+    else if (az == 2) H2 = wz * wz;
+    else H2 = 2 * (ax ? wx : wy) * (az ? wz : wy);
+  }
+}
+
+// Assembles G_UU[r, c] (r, c < npad; identity outside the n true unknowns).  Point data in shared
+// memory: sD (dsum + V0), sX (laser coordinate), sN (in-grid neighbour weight nb2), sXYZ (packed
+// local coordinates); sP the nine K x K products P_kk' = R_k^T Wt R_k' (Theta = phase x P).
+template <typename R>
+__device__ __forceinline__ typename C2<R>::T wide_entry(int r, int c, int n, const FastDiv& dK, const R* sP, int K,
+                                                     const R* sD, const R* sX, const R* sN, const int* sXYZ, R wx,
+                                                     R wy, R wz) {
+  typedef typename C2<R>::T CT;
+  if (r >= n || c >= n) return mkc<CT>((R)(r == c ? 1 : 0), (R)0);
+  const int i = fdiv(r, dK), m = r - i * K, j = fdiv(c, dK), nn = c - j * K;
+  const int pi = sXYZ[i], pj = sXYZ[j];
+  const int dx = (pj & 255) - (pi & 255), dy = ((pj >> 8) & 255) - ((pi >> 8) & 255), dz = (pj >> 16) - (pi >> 16);
+  R H, H2;
+  wide_h_h2<R>(dx, dy, dz, sD[i], sD[j], sN[i], wx, wy, wz, H, H2);
+  const int KK = K * K, mn = m * K + nn;
+  const R xp = sX[i], xq = sX[j];
+  // pairs (k, k') in the order (0,0) (0,1) (0,2) (1,0) (1,1) (1,2) (2,0) (2,1) (2,2) of (I, H, X);
+  // phases: (0,1), (0,2) +i; (1,0), (2,0) -i; others real
+  R re = H2 * sP[4 * KK + mn] + H * (xq * sP[5 * KK + mn] + xp * sP[7 * KK + mn]);
+  R im = H * (sP[1 * KK + mn] - sP[3 * KK + mn]);
+  if (i == j) {
+    re += sP[mn] + xp * xp * sP[8 * KK + mn];
+    im += xp * (sP[2 * KK + mn] - sP[6 * KK + mn]);
+  }
+  return mkc<CT>(re, im);
+}
+
+// Block column J, rows 16 J + row of this thread (columns c0 .. c0 + CPT - 1): assemble, subtract
+// sum_{k < 16 J} L[r][k] conj(L[16 J + c][k]) (row r of the finished blocks (I, 0..J-1) from global
+// memory, the block row J transposed in shared memory), and write the result to sPan.
+template <typename R, int CPT>
+__device__ __forceinline__ void wide_column_update(int J, int row, int c0, int n, const FastDiv& dK, int K,
+                                                   const typename C2<R>::T* __restrict__ F, const R* sP, const R* sD,
+                                                   const R* sX, const R* sN, const int* sXYZ, R wx, R wy, R wz,
+                                                   const typename C2<R>::T* sRow, typename C2<R>::T* sPan) {
+  typedef typename C2<R>::T CT;
+  const int r = LA_BLK * J + row, I = r >> 4;
+  CT acc[CPT];
+#pragma unroll
+  for (int q = 0; q < CPT; ++q) acc[q] = wide_entry<R>(r, LA_BLK * J + c0 + q, n, dK, sP, K, sD, sX, sN, sXYZ, wx, wy, wz);
+  for (int Kb = 0; Kb < J; ++Kb) {
+    const CT* src = F + (size_t)tri_index(I, Kb) * 256 + (r & 15) * LA_BLK;
+    CT v[LA_BLK];
+#pragma unroll
+    for (int kk = 0; kk < LA_BLK; ++kk) v[kk] = src[kk];
+    const CT* rowk = sRow + (size_t)Kb * LA_BLK * LA_BLK + c0;
+#pragma unroll
+    for (int kk = 0; kk < LA_BLK; ++kk) {
+#pragma unroll
+      for (int q = 0; q < CPT; ++q) {
+        const CT y = rowk[kk * LA_BLK + q];
+        // acc -= v conj(y)
+        acc[q].x = fma(-v[kk].x, y.x, acc[q].x); acc[q].x = fma(-v[kk].y, y.y, acc[q].x);
+        acc[q].y = fma(-v[kk].y, y.x, acc[q].y); acc[q].y = fma(v[kk].x, y.y, acc[q].y);
+      }
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < CPT; ++q) sPan[row * LA_BLK + c0 + q] = acc[q];
+}
+
+template <typename R, int NPAD>
+__global__ void __launch_bounds__(kFactorThreads, sizeof(R) == 4 ? 2 : 1)
+k_factor_wide(LevelGeom L, FineOp g, const TimeMats* __restrict__ tm, typename C2<R>::T* __restrict__ factors,
+              int* __restrict__ status) {
+  typedef typename C2<R>::T CT;
+  constexpr int NB = NPAD / LA_BLK;
+  extern __shared__ __align__(16) unsigned char smem[];
+  CT* sRow = reinterpret_cast<CT*>(smem);                       // [NPAD-16][16]: sRow[k][c] = L[16 J + c][k]
+  CT* sPan = sRow + (size_t)(NPAD - LA_BLK) * LA_BLK;          // [NPAD][16]: rows 16 J + row of block column J
+  CT* sInvT = sPan + (size_t)NPAD * LA_BLK;                    // [16][16]: sInvT[k][c] = conj(inv(L_JJ)[c][k])
+  R* sP = reinterpret_cast<R*>(sInvT + 256);                   // [9][K*K]
+  R* sD = sP + LA_NPAIR * LA_KMAX * LA_KMAX;                   // [64] dsum + V0
+  R* sX = sD + kWidePtsMax;                                    // [64] laser coordinate
+  R* sN = sX + kWidePtsMax;                                    // [64] in-grid neighbour weight of H^2's diagonal
+  R* sPiv = sN + kWidePtsMax;                                  // [16] 1/L_jj of the diagonal block
+  int* sXYZ = reinterpret_cast<int*>(sPiv + LA_BLK);          // [64] packed local coordinates
+
+  const int tid = threadIdx.x;
+  const int K = tm->K, KK = K * K;
+  const int b = blockIdx.x;
+  int o[3], e[3];
+  subvol_box(L, b, o, e);
+  const int npts = e[0] * e[1] * e[2], n = npts * K;
+  CT* F = factors + (size_t)b * L.fsize;
+  for (int i = tid; i < LA_NPAIR * KK; i += kFactorThreads) sP[i] = (R)tm->P[i / KK][i % KK];
+  const R wx = (R)(0.5 * g.ih2[0]), wy = (R)(0.5 * g.ih2[1]), wz = (R)(0.5 * g.ih2[2]);
+  for (int i = tid; i < npts; i += kFactorThreads) {
+    int lx, ly, lz;
+    local_coords(i, e, lx, ly, lz);
+    const int px = o[0] + lx, py = o[1] + ly, pz = o[2] + lz;
+    sD[i] = (R)(g.dsum + g.V0[(pz * g.n[1] + py) * g.n[0] + px]);
+    sX[i] = (R)fine_x(g, px, py, pz);
+    // unused axes have n = 1 and w = 0
+    const int cx = (px > 0 ? 1 : 0) + (px + 1 < g.n[0] ? 1 : 0), cy = (py > 0 ? 1 : 0) + (py + 1 < g.n[1] ? 1 : 0),
+              cz = (pz > 0 ? 1 : 0) + (pz + 1 < g.n[2] ? 1 : 0);
+    sN[i] = wx * wx * (R)cx + wy * wy * (R)cy + wz * wz * (R)cz;
+    sXYZ[i] = lx | (ly << 8) | (lz << 16);
+  }
+  __syncthreads();
+  const FastDiv dK = L.fd_K;
+  const int ti = tid >> 4, tk = tid & 15;
+
+  for (int J = 0; J < NB; ++J) {
+    // block row J (blocks (J, 0..J-1)) transposed into shared memory
+    for (int t = tid; t < J * 256; t += kFactorThreads) {
+      const int Kb = t >> 8, w = t & 255, c = w >> 4, kk = w & 15;
+      sRow[(Kb * LA_BLK + kk) * LA_BLK + c] = F[(size_t)tri_index(J, Kb) * 256 + w];
+    }
+    __syncthreads();
+    // assemble and update the block column: rows 16 J .. NPAD-1, tpr threads per row
+    const int RJ = NPAD - LA_BLK * J;
+    int tpr = 1;
+    while (tpr < LA_BLK && 2 * tpr * RJ <= kFactorThreads) tpr *= 2;
+    const int row = tid / tpr, c0 = (tid % tpr) * (LA_BLK / tpr);
+    if (row < RJ) {
+      switch (tpr) {
+#define LA_WIDE_CASE(TPR)                                                                                        \
+  case TPR:                                                                                                      \
+    wide_column_update<R, LA_BLK / TPR>(J, row, c0, n, dK, K, F, sP, sD, sX, sN, sXYZ, wx, wy, wz, sRow, sPan); \
+    break;
+        LA_WIDE_CASE(1)
+        LA_WIDE_CASE(2)
+        LA_WIDE_CASE(4)
+        LA_WIDE_CASE(8)
+        LA_WIDE_CASE(16)
+#undef LA_WIDE_CASE
+      }
+    }
+    __syncthreads();
+    // Cholesky of the diagonal block (rows 0..15 of sPan, lower triangle), thread (ti, tk) = entry
+    for (int j = 0; j < LA_BLK; ++j) {
+      R d2 = sPan[j * LA_BLK + j].x;
+      if (!(d2 > (R)0)) {
+        if (tid == 0) atomicOr(status, 1);
+        d2 = (R)1;
+      }
+      const R inv = rsq(d2);
+      CT nv = sPan[ti * LA_BLK + tk];
+      bool wr = false;
+      if (tk == j && ti >= j) {
+        nv = ti == j ? mkc<CT>(d2 * inv, (R)0) : mkc<CT>(nv.x * inv, nv.y * inv);
+        wr = true;
+      } else if (tk > j && ti >= tk) {
+        const CT a = sPan[ti * LA_BLK + j], bb = sPan[tk * LA_BLK + j];
+        const R s = inv * inv;
+        // nv -= a conj(bb) / d2
+        nv.x -= s * (a.x * bb.x + a.y * bb.y);
+        nv.y -= s * (a.y * bb.x - a.x * bb.y);
+        wr = true;
+      }
+      if (tid == 0) sPiv[j] = inv;
+      __syncthreads();
+      if (wr) sPan[ti * LA_BLK + tk] = nv;
+      __syncthreads();
+    }
+    // inv(L_JJ) column tk by forward substitution (16 threads), stored as sInvT[k][c] = conj(inv[c][k])
+    if (tid < LA_BLK) {
+      const int jj = tid;
+      CT x[LA_BLK];
+#pragma unroll
+      for (int i = 0; i < LA_BLK; ++i) {
+        CT acc = mkc<CT>(0, 0);
+#pragma unroll
+        for (int k = 0; k < i; ++k)
+          if (k >= jj) cfma(acc, sPan[i * LA_BLK + k], x[k]);
+        const R rinv = sPiv[i];
+        if (i < jj) x[i] = mkc<CT>(0, 0);
+        else if (i == jj) x[i] = mkc<CT>(rinv, (R)0);
+        else x[i] = mkc<CT>(-acc.x * rinv, -acc.y * rinv);
+      }
+      // x = column jj of inv(L_JJ): inv[i][jj] = x[i]; sInvT[k][c] = conj(inv[c][k]) -> k = jj, c = i
+#pragma unroll
+      for (int i = 0; i < LA_BLK; ++i) {
+        sInvT[jj * LA_BLK + i] = mkc<CT>(x[i].x, -x[i].y);
+        F[(size_t)tri_index(J, J) * 256 + i * LA_BLK + jj] = x[i];
+      }
+    }
+    __syncthreads();
+    // blocks below: L_IJ = A_IJ inv(L_JJ)^dagger, L[r][c] = sum_{k <= c} A[r][k] conj(inv[c][k])
+    for (int t = tid; t < (RJ - LA_BLK) * LA_BLK; t += kFactorThreads) {
+      const int rr = LA_BLK + (t >> 4), c = t & 15;
+      const CT* a = sPan + rr * LA_BLK;
+      CT s = mkc<CT>(0, 0);
+#pragma unroll
+      for (int k = 0; k < LA_BLK; ++k)
+        if (k <= c) cfma(s, a[k], sInvT[k * LA_BLK + c]);
+      F[(size_t)tri_index(J + (rr >> 4), J) * 256 + (rr & 15) * LA_BLK + c] = s;
+    }
+    __syncthreads();
+  }
+}
+
 // ======================================================================== triangular solves
 // x = (L L^dagger)^{-1} rhs with the blocked factor F; rhs is overwritten by x.  Two warps (64
 // threads, 4 lanes per row) do the block mat-vecs and synchronise with a named barrier; the other
@@ -1230,6 +1467,25 @@ cudaError_t launch_factor_blk_n(const LevelGeom& L, const FineOp* fine, const do
   return launch_factor_blk_m<R, NPAD, mpc>(L, fine, sigma, tm, factors, status, s);
 }
 
+// Wide subvolumes (more than LA_NPAD_MAX unknowns) exist on the finest level only.
+template <typename R, int NPAD>
+cudaError_t launch_factor_wide_n(const LevelGeom& L, const FineOp* fine, const TimeMats* tm,
+                                 typename C2<R>::T* factors, int* status, cudaStream_t s) {
+  typedef typename C2<R>::T CT;
+  if (!fine) return cudaErrorInvalidValue;
+  const size_t smem = wide_factor_smem(NPAD, sizeof(CT), sizeof(R));
+  auto kern = k_factor_wide<R, NPAD>;
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+    if (err != cudaSuccess) return err;
+    attr_set = true;
+  }
+  if (smem > 227 * 1024) return cudaErrorInvalidValue;
+  kern<<<L.nsub, kFactorThreads, smem, s>>>(L, *fine, tm, factors, status);
+  return cudaGetLastError();
+}
+
 template <typename R, int NPAD, int mpc>
 cudaError_t launch_factor_m(const LevelGeom& L, const FineOp* fine, const double* sigma, const TimeMats* tm,
                             typename C2<R>::T* factors, int* status, cudaStream_t s) {
@@ -1312,6 +1568,14 @@ cudaError_t launch_gresid_tiles_r(const LevelGeom& L, const double* sigma, const
   kern<<<L.nsub, kSweepThreads, smem, s>>>(L, sigma, tm, gvec, e, out, L.npad);
   return cudaGetLastError();
 }
+
+// finest-level sweeps and factorisations also take the wide sizes
+#define LA_NPAD_DISPATCH_WIDE(NPADV, CALL) \
+  switch (NPADV) {                    \
+    case 192: return CALL(192);       \
+    case 256: return CALL(256);       \
+    default: break;                   \
+  }
 
 #define LA_NPAD_DISPATCH(NPADV, CALL) \
   switch (NPADV) {                    \

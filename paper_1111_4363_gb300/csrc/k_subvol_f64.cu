@@ -5,6 +5,11 @@ template <>
 cudaError_t launch_factor<double>(const LevelGeom& L, const FineOp* fine, const double* sigma, const TimeMats* tm,
                                   double2* factors, int* status, cudaStream_t s) {
 #define LA_CALL(N) launch_factor_n<double, N>(L, fine, sigma, tm, factors, status, s)
+  {
+#define LA_WCALL(N) launch_factor_wide_n<double, N>(L, fine, tm, factors, status, s)
+    LA_NPAD_DISPATCH_WIDE(L.npad, LA_WCALL)
+#undef LA_WCALL
+  }
   LA_NPAD_DISPATCH(L.npad, LA_CALL)
 #undef LA_CALL
 }
@@ -12,6 +17,7 @@ template <>
 cudaError_t launch_sweep_fine<double>(const LevelGeom& L, const FineOp& g, const TimeMats* tm, int K, const double2* f,
                                       const double2* yx, double2* c, const double2* factors, int colour, int* status, cudaStream_t s) {
 #define LA_CALL(N) launch_sweep_fine_n<double, N>(L, g, tm, K, f, yx, c, factors, colour, status, s)
+  LA_NPAD_DISPATCH_WIDE(L.npad, LA_CALL)
   LA_NPAD_DISPATCH(L.npad, LA_CALL)
 #undef LA_CALL
 }

@@ -278,7 +278,7 @@ static bool build_time_constants(la_ctx* c) {
 }
 
 static int round_npad(int n) {
-  const int sizes[6] = {16, 32, 48, 64, 96, 128};
+  const int sizes[8] = {16, 32, 48, 64, 96, 128, 192, 256};
   for (int s : sizes)
     if (n <= s) return s;
   return -1;
@@ -361,9 +361,17 @@ extern "C" la_status la_init(const la_config* cfg, void* stream, la_ctx** out) {
     subpts *= k.sub[a];
     csubpts *= k.coarse_sub[a] > 0 ? k.coarse_sub[a] : k.sub[a];
   }
-  if (subpts > LA_NPTS_MAX || round_npad(subpts * k.nt) < 0 || csubpts > LA_NPTS_MAX ||
-      round_npad(csubpts * k.nt) < 0) {
-    g_init_error = "invalid configuration: a subvolume may hold at most 32 points and 128 unknowns";
+  // finest level: up to 64 points and 256 unknowns (more than 128 unknowns: factorised in global
+  // memory); Galerkin levels: up to 32 points and 128 unknowns (factorised in shared memory)
+  if (subpts > LA_NPTS_WIDE || round_npad(subpts * k.nt) < 0) {
+    g_init_error = "invalid configuration: a finest-level subvolume may hold at most 64 points and 256 unknowns";
+    delete c;
+    return LA_EINVAL;
+  }
+  if (k.levels > 1 && (csubpts > LA_NPTS_MAX || round_npad(csubpts * k.nt) < 0 ||
+                       round_npad(csubpts * k.nt) > LA_NPAD_MAX)) {
+    g_init_error = "invalid configuration: a Galerkin-level subvolume may hold at most 32 points and 128 unknowns "
+                   "(set coarse_sub)";
     delete c;
     return LA_EINVAL;
   }

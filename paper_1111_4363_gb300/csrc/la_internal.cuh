@@ -19,8 +19,10 @@
 #define LA_KMAX 8          // largest K (free time functions per point)
 #define LA_NPAIR 9         // (k, k') pairs of the Kronecker normal operator
 #define LA_BLK 16          // block size of the subvolume factor layout
-#define LA_NPAD_MAX 128    // largest padded subvolume size (unknowns)
-#define LA_NPTS_MAX 32     // largest number of grid points in one subvolume
+#define LA_NPAD_MAX 128    // largest padded subvolume size (unknowns) factorised by one CTA in shared memory
+#define LA_NPTS_MAX 32     // largest number of grid points in such a subvolume
+#define LA_NPAD_WIDE 256   // largest padded size of a finest-level subvolume (factorised in global memory)
+#define LA_NPTS_WIDE 64    // largest number of grid points in a finest-level subvolume
 #define LA_NQ_MAX 32       // largest number of Gauss nodes per step
 #define LA_NCOMP_MAX 64    // largest number of pulse components
 

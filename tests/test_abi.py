@@ -66,8 +66,16 @@ def test_init_rejects_invalid_configs_without_touching_the_gpu():
     with pytest.raises(B.LeastActionError, match="divisible"):
         B.Context(cfg)
     cfg = B.config_from_workload(w)
-    cfg.sub[0] = cfg.sub[1] = 8   # 64 points per subvolume > 32
-    with pytest.raises(B.LeastActionError):
+    cfg.sub[0] = cfg.sub[1] = 8   # 64 points x K = 6 = 384 unknowns > 256
+    with pytest.raises(B.LeastActionError, match="at most 64 points and 256 unknowns"):
+        B.Context(cfg)
+    w3 = wl.hydrogen_3d(n=16, nsteps=4, ncomp=4, sub=4)
+    cfg = B.config_from_workload(w3)   # 4x4x4 finest subvolumes, Galerkin levels of the same size
+    with pytest.raises(B.LeastActionError, match="Galerkin-level subvolume"):
+        B.Context(cfg)
+    cfg = B.config_from_workload(w3, levels=1)
+    cfg.sub[0] = 5                     # 5x4x4 = 80 points
+    with pytest.raises(B.LeastActionError, match="at most 64 points"):
         B.Context(cfg)
 
 
