@@ -60,6 +60,10 @@ def workload(name: str) -> wl.Workload:
         return dataclasses.replace(wl.softcore_2d(n=128, levels=4, nsteps=200), **PRODUCTION_2D)
     if name == "1d":
         return wl.harmonic_1d()
+    if name == "3d":                # the 3D workload's forward propagation: 128^3, K = 4, 4x4x4 subvolumes
+        return dataclasses.replace(wl.hydrogen_3d(n=128, nsteps=400), **PRODUCTION_3D)
+    if name == "3d-small":          # the same problem on 32^3, for ncu captures of single kernels
+        return dataclasses.replace(wl.hydrogen_3d(n=32, nsteps=400), **PRODUCTION_3D)
     if name == "2d-square":         # the paper's square local form (Sec. II), single level, red-black
         return dataclasses.replace(wl.softcore_2d(n=256, levels=1, nsteps=200), local_form="square", nu1=1, nu2=1,
                                    trial=3)
@@ -199,7 +203,7 @@ def finest_factor_store(w, precision):
     for a in range(w.dim):
         nsub *= -(-w.n[a] // w.sub[a])
         pts *= w.sub[a]
-    npad = next(s_ for s_ in (16, 32, 48, 64, 96, 128) if pts * w.nt <= s_)
+    npad = next(s_ for s_ in (16, 32, 48, 64, 96, 128, 192, 256) if pts * w.nt <= s_)
     entry = 16 if precision == 0 else 8
     if getattr(w, "local_form", "lsq") == "square":
         return nsub, npad * npad * entry
@@ -653,7 +657,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="2d",
-                    choices=["2d", "2d-small", "1d", "2d-square", "batched", "3d-adjoint", "lfa"])
+                    choices=["2d", "2d-small", "1d", "2d-square", "3d", "3d-small", "batched", "3d-adjoint", "lfa"])
     ap.add_argument("--batch", type=int, default=512)
     ap.add_argument("--n3d", type=int, default=128)
     ap.add_argument("--precision", type=int, default=0, choices=[0, 1])

@@ -178,8 +178,9 @@ def batched_2d(index: int) -> Workload:
                     psi_kind="gaussian", seed=index)
 
 
-def hydrogen_3d(n: int = 128, nsteps: int = 400, ncomp: int = 32, sub: int = 2) -> Workload:
-    """3D, n^3 points, h = 0.3, V = -1/sqrt(r^2+0.64), 32-component Gaussian-enveloped pulse on x, K = 4."""
+def hydrogen_3d(n: int = 128, nsteps: int = 400, ncomp: int = 32, sub: int = 4) -> Workload:
+    """3D, n^3 points, h = 0.3, V = -1/sqrt(r^2+0.64), 32-component Gaussian-enveloped pulse on x, K = 4;
+    sub^3-point finest subvolumes (4^3 x 4 = 256 unknowns), 2^3-point subvolumes on the Galerkin levels."""
     rng = np.random.default_rng(0)
     T = nsteps * 0.05
     amp = list(rng.normal(0.0, 0.02, size=ncomp))
@@ -190,4 +191,4 @@ def hydrogen_3d(n: int = 128, nsteps: int = 400, ncomp: int = 32, sub: int = 2) 
                     sub=(sub, sub, sub), levels=4, nu1=1, nu2=1, coarse_sweeps=2, max_cycles=60, tol=1e-10,
                     nsteps=nsteps, potential="softcore", softcore_a=0.64,
                     pulse=Pulse(amp=amp, omega=om, t_center=tc, sigma=sig, axis=0),
-                    psi_kind="centred", seed=0)
+                    psi_kind="centred", seed=0, coarse_sub=(2, 2, 2))
