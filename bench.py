@@ -1,16 +1,21 @@
 """Benchmark: spacetime unknowns relaxed per second of the least-action propagator on one GB300.
 
-A "step" is one least-action time step of the 2D soft-core workload (256 x 256 points, K = 6
-Legendre time functions, 4 x 4-point subvolumes, 4-level V(1,2) cycles, FP64, tolerance 1e-10 on
-N/N(0)): time matrices, right-hand side, subvolume factorisation on every level, V-cycles to
-tolerance from the trial extrapolated from the last three steps, step advance.
-Metric = (finest-level unknowns) x (finest-level sweeps) / time.
+Default line: the 3D workload's forward propagation (128^3 points, K = 4 Legendre time functions,
+4 x 4 x 4-point subvolumes of 256 unknowns, 4-level V(1,2) cycles with a (1,0) Galerkin cycle, FP64
+residual, action and refinement with complex64 local solves, tolerance 1e-10 on N/N(0)).  A "step"
+is one least-action time step: time matrices, right-hand side, subvolume factorisation on every
+level, V-cycles to tolerance from the trial extrapolated from the last three steps, step advance.
+Metric = (finest-level unknowns) x (finest-level sweeps) / time.  The same JSON line carries clocked
+sub-records: the same 3D problem in plain FP64, the 2D workload's whole 200-step propagation in FP64
+and in mixed precision, and the 512-grid batch in FP64 and mixed precision, each with its speed-up
+at the same tolerance, plus the FMA peaks of this GPU measured in the run.
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--precision 0|1]
-                  [--workload 2d|2d-small|1d|batched|3d-adjoint] [--trial -1|0..3]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--precision -1|0|1]
+                  [--workload 3d|3d-small|2d|2d-small|1d|2d-square|batched|3d-adjoint|lfa]
+                  [--trial -1|0..3] [--headline-only]
 
 N > 1 runs N independent replicas (one propagation per rank, no collective: the path does not
-shard).  ``--impl reference`` times the CPU oracle on the same workload instead.
+shard).  ``--impl reference`` times the CPU oracle on a bounded sample of the same workload instead.
 """
 from __future__ import annotations
 
@@ -234,20 +239,31 @@ def workload_config(w, precision, ws):
             "l2": l2_note(w, precision)}
 
 
-def dominant_roofline(prof, w, precision, ms_total, traffic_ok):
-    """Roofline of the dominant kernel class (the larger total device time of factor and sweep)."""
+def default_precision(name: str) -> int:
+    """The arithmetic a workload is specified in: the 3D workload runs FP64 with complex64 local solves."""
+    return 1 if name in ("3d", "3d-small") else 0
+
+
+def dominant_roofline(prof, w, precision, ms_total, traffic_ok, peaks=None):
+    """Roofline of the dominant kernel class (the larger total device time of factor and sweep).
+    peaks: (FP64, FP32) TFLOP/s measured in this run by la_fma_peaks, else the derived figures."""
     fac_ms = prof["ms_factor"] / max(prof["n_factor"], 1)
     swp_ms_full = prof["ms_sweep"] / max(prof["n_sweep"], 1)   # one event pair per full sweep
     nsub, fbytes = finest_factor_store(w, precision)
+    wide = fbytes // (16 if precision == 0 else 8) > 136 * 128   # more than 128 unknowns: global-memory factor
+    fac_name = "k_factor_wide" if wide else ("k_factor" if precision == 0 else "k_factor_blk")
     if prof["ms_factor"] >= prof["ms_sweep"]:
-        dom, flops, dms, cls = "k_factor (finest level)", prof["flops_factor"], fac_ms, "factor"
+        dom, flops, dms, cls = f"{fac_name} (finest level)", prof["flops_factor"], fac_ms, "factor"
     else:
         dom, flops, dms, cls = "k_sweep_fine (one sweep, all colours)", prof["flops_sweep"], swp_ms_full, "sweep"
-    bps = NCU_BYTES_PER_SUBVOLUME.get((cls, precision)) if traffic_ok else None
+    bps = NCU_BYTES_PER_SUBVOLUME.get((cls + ("_wide" if wide else ""), precision)) if traffic_ok else None
     traffic = round(bps * nsub) if bps else None
     kms = {"factor_per_launch": round(fac_ms, 4), "sweep_full": round(swp_ms_full, 4),
            "factor_share": round(prof["ms_factor"] / max(ms_total, 1e-9), 3),
            "sweep_share": round(prof["ms_sweep"] / max(ms_total, 1e-9), 3)}
+    tnote = ("DRAM read+write bytes of this kernel per launch, from one ncu capture of the same kernel on the "
+             "32^3 case scaled by the subvolumes a launch processes" if wide else
+             "DRAM read+write bytes of this kernel per launch from one ncu capture of this workload")
     if precision == 1 and cls == "sweep":
         # the complex64 sweep streams the factor store: HBM roofline on its compulsory bytes, every
         # factor once plus c read and written, f read (8 B per complex64) and V0 read per point
@@ -257,21 +273,21 @@ def dominant_roofline(prof, w, precision, ms_total, traffic_ok):
         peak, note = hbm_peak()
         return {"bound": "hbm", "kernel": dom, "achieved": round(gbs, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(gbs / peak, 4), "traffic": traffic, "algorithmic_bytes": algo,
-                "traffic_note": "DRAM read+write bytes of this kernel per launch from one ncu capture of this workload",
-                "peak_note": note, "note": "latency-bound: few CTAs per SM (each holds a 43 KB factor in shared "
-                                           "memory for NPAD 96) and a dependent chain per CTA",
-                "kernel_ms": kms}
+                "traffic_note": tnote, "peak_note": note, "kernel_ms": kms}
     achieved = flops / (dms * 1e-3) / 1e12
-    if precision == 0:
+    if peaks is not None:
+        peak = peaks[0] if precision == 0 else peaks[1]
+        peak_note = (f"{'FP64' if precision == 0 else 'FP32'} FMA pipe of measured (la_fma_peaks in this run: "
+                     f"{peaks[2]} SMs)")
+    elif precision == 0:
         peak = FP64_PEAK_TFLOPS
-        peak_note = "FP64 pipe: 152 SMs x 4 flop/clk x 2070 MHz (derived); probe measured 1.19 at 1995 MHz"
+        peak_note = "FP64 pipe: 152 SMs x 4 flop/clk x 2070 MHz (derived)"
     else:
         peak = FP32_PEAK_TFLOPS
         peak_note = "FP32 pipe (complex64 kernel): 152 SMs x 128 lanes x 2 flop x 2070 MHz (derived)"
     return {"bound": "alu", "kernel": dom, "achieved": round(achieved, 4), "peak": round(peak, 4),
             "unit": "TFLOP/s", "frac": round(achieved / peak, 4), "traffic": traffic,
-            "traffic_note": "DRAM read+write bytes of this kernel per launch from one ncu capture of this workload",
-            "peak_note": peak_note, "kernel_ms": kms}
+            "algorithmic_flops": flops, "traffic_note": tnote, "peak_note": peak_note, "kernel_ms": kms}
 
 
 def stencil_roofline(prof, precision, c64=False):
@@ -291,6 +307,155 @@ def stencil_roofline(prof, precision, c64=False):
                      "algorithmic bytes: f, c, V0 in and z out per point")}
 
 
+def make_context(B, torch, w, precision, **overrides):
+    ctx = B.Context(B.config_from_workload(w, precision=precision, **overrides))
+    ctx.set_hamiltonian(torch.tensor(wl.potential(w).ravel(), dtype=torch.float64, device="cuda"), w.pulse)
+    return ctx
+
+
+def timed_steps(torch, ctx, psi, w, t, steps, snapshots=()):
+    """`steps` least-action steps from time t, timed with CUDA events on the current stream (one la_step
+    call per step, so that per-step statistics and snapshots are available).  Returns
+    (ms, per-step stats, t after, {step index: psi copy})."""
+    stream = torch.cuda.current_stream()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    stats, snaps = [], {}
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    for k in range(steps):
+        st, s1 = ctx.step(psi, 1, t, stats=True)
+        stats.append(s1[0])
+        t += w.dt
+        if k + 1 in snapshots:
+            snaps[k + 1] = psi.clone()
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    return ev0.elapsed_time(ev1), stats, t, snaps
+
+
+def rel_l2(a, b) -> float:
+    import torch
+    return float(torch.linalg.vector_norm(a - b) / torch.linalg.vector_norm(b))
+
+
+def subrecord_fp64_same_config(B, torch, w, psi_mixed, steps_mixed, ms_mixed):
+    """The headline problem in plain FP64: time per step, and the mixed path's speed-up at the same
+    tolerance, with the two propagations' states compared after the same steps from psi0."""
+    ctx = make_context(B, torch, w, 0)
+    psi = torch.from_numpy(wl.initial_state(w).ravel()).cuda()
+    warm = 2
+    t = 0.0
+    for _ in range(warm):
+        ctx.step(psi, 1, t)
+        t += w.dt
+    steps = 3
+    clk = ClockSampler(0)
+    clk.start()
+    ms, stats, t, _ = timed_steps(torch, ctx, psi, w, t, steps)
+    clocks = clk.stop()
+    ctx.close()
+    ms_step = ms / steps
+    diff = rel_l2(psi_mixed, psi) if psi_mixed is not None and steps_mixed == warm + steps else None
+    return {"what": f"{w.name} in FP64 throughout (complex128 factors and V-cycles)", "steps": steps,
+            "warmup": warm, "ms_per_step": ms_step, "cycles_per_step": sum(s[0] for s in stats) / steps,
+            "max_rel_action": max(s[3] for s in stats),
+            "value": w.nunknowns * sum(s[1] for s in stats) / (ms * 1e-3), "unit": "unknowns/s",
+            "mixed_speedup_at_same_tolerance": ms_step / ms_mixed,
+            "psi_rel_l2_mixed_vs_fp64_after_5_steps": diff, "clocks": clocks}
+
+
+def subrecord_2d_propagation(B, torch):
+    """The 2D workload's whole 200-step propagation from t = 0 in FP64 and in mixed precision (each
+    after 3 warm-up steps on the same context), with the mixed path's speed-up at the same tolerance
+    and the two final states compared."""
+    w = workload("2d")
+    out, final = {}, {}
+    for precision in (0, 1):
+        ctx = make_context(B, torch, w, precision)
+        psi0 = torch.from_numpy(wl.initial_state(w).ravel()).cuda()
+        psi = psi0.clone()
+        t = 0.0
+        for _ in range(3):
+            ctx.step(psi, 1, t)
+            t += w.dt
+        psi.copy_(psi0)   # t0 = 0 again: the trial history restarts with the propagation
+        clk = ClockSampler(0)
+        clk.start()
+        ms, stats, _, _ = timed_steps(torch, ctx, psi, w, 0.0, w.nsteps)
+        clocks = clk.stop()
+        ctx.close()
+        final[precision] = psi
+        cyc = [s[0] for s in stats]
+        out["fp64" if precision == 0 else "mixed"] = {
+            "steps": w.nsteps, "ms_total": ms, "ms_per_step": ms / w.nsteps,
+            "value": w.nunknowns * sum(s[1] for s in stats) / (ms * 1e-3), "unit": "unknowns/s",
+            "cycles_per_step_mean": sum(cyc) / len(cyc), "cycles_per_step_max": max(cyc),
+            "max_rel_action": max(s[3] for s in stats), "clocks": clocks}
+    out["mixed_speedup_at_same_tolerance"] = out["fp64"]["ms_total"] / out["mixed"]["ms_total"]
+    out["final_psi_rel_l2_mixed_vs_fp64"] = rel_l2(final[1], final[0])
+    out["what"] = (f"{w.name}: {w.nsteps} steps from t = 0 (the field 0.05 sin(0.057 t) grows from 0 to "
+                   f"{0.05 * abs(np.sin(0.057 * w.nsteps * w.dt)):.3f}), tolerance {w.tol} every step")
+    return out
+
+
+def batched_members(n, precision_trial=3):
+    return [dataclasses.replace(wl.batched_2d(i), trial=precision_trial) for i in range(n)]
+
+
+def batched_measure(B, torch, ws, precision, steps, warmup):
+    """la_step_batch over all members against the same contexts stepped one after another."""
+    ctxs = [make_context(B, torch, w, precision) for w in ws]
+    psis = [torch.from_numpy(wl.initial_state(w).ravel()).cuda() for w in ws]
+    t0s = [0.0] * len(ws)
+    if warmup:
+        B.step_batch(ctxs, psis, warmup, t0s)
+    t0s = [warmup * w.dt for w in ws]
+    torch.cuda.synchronize()
+    clk = ClockSampler(0)
+    clk.start()
+    a = time.perf_counter()
+    stats = B.step_batch(ctxs, psis, steps, t0s)
+    torch.cuda.synchronize()
+    el = time.perf_counter() - a
+    clocks = clk.stop()
+    work = sum(w.nunknowns * sum(s[1] for s in st) for w, st in zip(ws, stats))
+    t1s = [t + steps * w.dt for t, w in zip(t0s, ws)]
+    torch.cuda.synchronize()
+    a = time.perf_counter()
+    work_seq = 0
+    for ctx, psi, w, t in zip(ctxs, psis, ws, t1s):
+        st, sts = ctx.step(psi, steps, t, stats=True)
+        work_seq += w.nunknowns * sum(x[1] for x in sts)
+    torch.cuda.synchronize()
+    el_seq = time.perf_counter() - a
+    for c in ctxs:
+        c.close()
+    return {"value": work / el, "ms_per_step": 1e3 * el / steps, "unit": "unknowns/s",
+            "sequential": {"value": work_seq / el_seq, "ms_per_step": 1e3 * el_seq / steps},
+            "speedup_vs_sequential": (work / el) / (work_seq / el_seq),
+            "max_rel_action": max(s[3] for st in stats for s in st),
+            "cycles_per_step_mean": sum(s[0] for st in stats for s in st) / max(1, sum(len(st) for st in stats)),
+            "clocks": clocks}
+
+
+def subrecord_batched(B, torch, nbatch=512, steps=3, warmup=1):
+    """The batched workload (512 seeded grids of 64^2 .. 256^2, K = 4) in FP64 and in mixed precision,
+    schedule autotuned on a 128^2 member."""
+    from paper_1111_4363_gb300 import autotune
+    members = batched_members(nbatch)
+    rep = dataclasses.replace(members[0], n=(128, 128, 1))
+    out = {"members": nbatch, "unknowns_total": sum(w.nunknowns for w in members), "steps": steps,
+           "warmup": warmup}
+    for precision in (0, 1):
+        best = autotune.tune(rep, precision=precision)
+        ws = [dataclasses.replace(m, **best) for m in members]
+        r = batched_measure(B, torch, ws, precision, steps, warmup)
+        r["autotuned"] = {k: list(v) if isinstance(v, tuple) else v for k, v in best.items()}
+        out["fp64" if precision == 0 else "mixed"] = r
+    out["mixed_speedup_over_fp64_batched"] = out["fp64"]["ms_per_step"] / out["mixed"]["ms_per_step"]
+    return out
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -303,19 +468,19 @@ def run_ours(args):
     __graft_entry__.build()
     from paper_1111_4363_gb300 import binding as B
 
+    precision = args.precision if args.precision >= 0 else default_precision(args.workload)
     w = workload(args.workload)
     if args.trial >= 0:
         w = dataclasses.replace(w, trial=args.trial)
-    cfg = B.config_from_workload(w, precision=args.precision)
-    ctx = B.Context(cfg)
-    V0 = torch.tensor(wl.potential(w).ravel(), dtype=torch.float64, device="cuda")
-    ctx.set_hamiltonian(V0, w.pulse)
+    peaks = B.fma_peaks()
+    ctx = make_context(B, torch, w, precision)
     psi0 = torch.from_numpy(wl.initial_state(w).ravel()).cuda()
     psi = psi0.clone()
     nunk = w.nunknowns
     # warm-up steps (untimed); the propagation continues from where warm-up ended
     t = 0.0
-    for _ in range(args.warmup):
+    snap_mixed = None
+    for k in range(args.warmup):
         ctx.step(psi, 1, t)
         t += w.dt
     torch.cuda.synchronize()
@@ -324,24 +489,17 @@ def run_ours(args):
     clocks.start()
     if ws > 1:
         dist.barrier()
-    torch.cuda.synchronize()
-    stream = torch.cuda.current_stream()
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    ev0.record(stream)
-    sweeps, cycles = 0, 0
-    for _ in range(args.steps):
-        st, stats = ctx.step(psi, 1, t, stats=True)
-        sweeps += stats[0][1]
-        cycles += stats[0][0]
-        t += w.dt
-    ev1.record(stream)
-    torch.cuda.synchronize()
+    want = (5 - args.warmup,) if 0 < 5 - args.warmup <= args.steps else ()
+    ms, stats, t, snaps = timed_steps(torch, ctx, psi, w, t, args.steps, snapshots=want)
+    if want:
+        snap_mixed = snaps[want[0]]
     if ws > 1:
         dist.barrier()
-    ms = ev0.elapsed_time(ev1)
     clk = clocks.stop()
     prof = ctx.profile_read()
     ctx.profile_enable(False)
+    sweeps = sum(s[1] for s in stats)
+    cycles = [s[0] for s in stats]
     ms_max, sweeps_all = reduce_over_ranks(ms, sweeps, ws)
     value = nunk * sweeps_all / (ms_max * 1e-3)
 
@@ -353,36 +511,48 @@ def run_ours(args):
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
-        st, stats = ctx.step(psi_host, 1, t, stats=True)
-        e2e_sweeps += stats[0][1]
+        st, s1 = ctx.step(psi_host, 1, t, stats=True)
+        e2e_sweeps += s1[0][1]
         t += w.dt
     e2e_s = time.perf_counter() - t0
     e2e_value = nunk * e2e_sweeps / e2e_s * (ws if ws > 1 else 1)
+    ctx.close()
 
-    roofline = dominant_roofline(prof, w, args.precision, ms, traffic_ok=args.workload == "2d")
+    roofline = dominant_roofline(prof, w, precision, ms, traffic_ok=args.workload in ("2d", "3d"), peaks=peaks)
     if getattr(w, "local_form", "lsq") == "square":
         roofline["kernel"] = roofline["kernel"].replace("k_factor", "k_factor_square").replace("k_sweep_fine",
                                                                                                "k_sweep_square")
-    prec_tag = "f64" if args.precision == 0 else "c64 local solves + f64 refinement"
+    prec_tag = "f64" if precision == 0 else "c64 local solves + f64 refinement"
 
     out = {"metric": METRIC, "value": value, "unit": "unknowns/s", "n_gpus": ws, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": prec_tag, "data": "synthetic",
-           "config": workload_config(w, args.precision, ws),
-           "cycles_per_step": cycles / args.steps, "fine_sweeps_per_step": sweeps / args.steps,
+           "config": workload_config(w, precision, ws),
+           "cycles_per_step": sum(cycles) / args.steps, "cycles_per_step_max": max(cycles),
+           "fine_sweeps_per_step": sweeps / args.steps, "max_rel_action": max(s[3] for s in stats),
            "ms_per_time_step_to_tol": ms_max / args.steps,
            "e2e": {"value": e2e_value, "unit": "unknowns/s", "h2d_bytes_per_step": 16 * w.npoints,
                    "d2h_bytes_per_step": 16 * w.npoints, "steps": e2e_steps},
            "gpu_launches": int(prof["launches"]), "roofline": roofline,
-           "stencil_roofline": stencil_roofline(prof, args.precision),
-           "stencil_roofline_c64": stencil_roofline(prof, args.precision, c64=True), "clocks": clk}
+           "stencil_roofline": stencil_roofline(prof, precision),
+           "stencil_roofline_c64": stencil_roofline(prof, precision, c64=True), "clocks": clk,
+           "peaks": {"fp64_tflops": round(peaks[0], 4), "fp32_tflops": round(peaks[1], 3), "sm_count": peaks[2],
+                     "how": "la_fma_peaks: 8 independent FMA chains per thread, 8 CTAs of 256 threads per SM, "
+                            "CUDA events, in this run"}}
+    extras = rank == 0 and ws == 1 and not args.headline_only
+    if extras and args.workload == "3d" and precision == 1:
+        out["fp64_same_config"] = subrecord_fp64_same_config(B, torch, w, snap_mixed,
+                                                             args.warmup + (want[0] if want else 0),
+                                                             ms_max / args.steps)
+    if extras and args.workload == "3d":
+        out["config_2d_200_steps"] = subrecord_2d_propagation(B, torch)
+        out["config_batched_512"] = subrecord_batched(B, torch)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline and getattr(w, "local_form", "lsq") == "lsq":
         out["cpu_baseline"] = cpu_baseline(w)
     if rank == 0 and getattr(w, "local_form", "lsq") == "square":
         out["square_form"] = square_form_report(B, torch, w)
     if rank == 0:
         print(json.dumps(out))
-    ctx.close()
     if ws > 1:
         dist.destroy_process_group()
 
@@ -418,13 +588,25 @@ def oracle_cycle_rate(w: wl.Workload, budget_s: float):
 ORACLE_THREADS = 1
 
 
+def oracle_sample(w: wl.Workload):
+    """The workload itself when the oracle handles it in seconds, else the same problem on a 32^3 grid
+    (3D): the oracle's time per unknown and sweep does not depend on the grid size (measured 2.9e5 and
+    2.7e5 unknowns relaxed/s at 16^3 and 32^3), so the rate extrapolates to the full grid."""
+    if w.dim == 3 and w.npoints > 32 ** 3:
+        return dataclasses.replace(w, n=(32, 32, 32)), True
+    return w, False
+
+
 def cpu_baseline(w: wl.Workload):
-    setup_s, cyc_s, ncyc = oracle_cycle_rate(w, 8.0)
-    sweeps = w.nu1 + w.nu2
-    value = w.nunknowns * sweeps / cyc_s
+    ws_, extrap = oracle_sample(w)
+    setup_s, cyc_s, ncyc = oracle_cycle_rate(ws_, 8.0)
+    sweeps = ws_.nu1 + ws_.nu2
+    value = ws_.nunknowns * sweeps / cyc_s
+    where = (f"the same problem on {'x'.join(map(str, ws_.shape))} points, per unknown extrapolated to "
+             f"{'x'.join(map(str, w.shape))}") if extrap else f"{w.name}"
     return {"value": value, "unit": "unknowns/s", "cores": ORACLE_THREADS, "kind": "oracle",
-            "host_cores": len(os.sched_getaffinity(0)),
-            "sample": f"one time step of {w.name}: setup (assembly, Galerkin levels, {w.name} block Cholesky) "
+            "host_cores": len(os.sched_getaffinity(0)), "extrapolated": extrap,
+            "sample": f"one time step of {where}: setup (assembly, Galerkin levels, block Cholesky) "
                       f"{setup_s:.1f} s excluded, then {ncyc} V-cycles timed ({cyc_s:.2f} s each)",
             "setup_s": setup_s, "cycle_s": cyc_s}
 
@@ -433,9 +615,12 @@ def run_reference(args):
     ws, rank, local = dist_env()
     if rank != 0:
         return
-    w = workload(args.workload)
+    w_full = workload(args.workload)
+    precision = args.precision if args.precision >= 0 else default_precision(args.workload)
+    w, extrap = oracle_sample(w_full)
     cores = ORACLE_THREADS
-    # each step = one oracle V-cycle on the full workload after an untimed setup; bounded to a few minutes
+    # each step = one oracle V-cycle on the workload (a 32^3 sample of the 3D one) after an untimed
+    # setup; bounded to a few minutes
     from oracle import multigrid, system
     from oracle.propagate import numpy_coarse_nu, numpy_coarse_sub, numpy_sub
     prob = system.Problem.from_workload(w)
@@ -449,7 +634,7 @@ def run_reference(args):
     setup_s = time.perf_counter() - t_a
     c = np.zeros(M.shape[1], dtype=np.complex128)
     # the requested counts, capped so that the run stays within a few minutes (about 1-2 s per
-    # V-cycle of the 256^2 workload on one host core)
+    # V-cycle of the 256^2 workload or of the 32^3 sample on one host core)
     warm = max(0, min(args.warmup, 5))
     for _ in range(warm):
         hier.vcycle(0, c, g0)
@@ -464,11 +649,15 @@ def run_reference(args):
     out = {"impl": "reference", "metric": METRIC, "value": value, "unit": "unknowns/s", "n_gpus": ws,
            "steps": steps, "warmup": warm, "ms_per_step": el / steps * 1e3, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-           "config": workload_config(w, 0, ws),
-           "reference_step": f"one oracle V-cycle ({sweeps} finest-level sweeps) of the workload on the host, "
-                             f"from the same schedule; host memory, no L2 flush",
+           "config": workload_config(w_full, precision, ws),
+           "reference_step": (f"one oracle V-cycle ({sweeps} finest-level sweeps, FP64) of "
+                              + (f"the same problem on {'x'.join(map(str, w.shape))} points (rate per unknown "
+                                 f"extrapolated to the full grid)" if extrap else "the workload")
+                              + " on the host, from the same schedule; host memory, no L2 flush"),
            "cpu_baseline": {"value": value, "unit": "unknowns/s", "cores": cores, "kind": "oracle",
-                            "sample": f"{steps} V-cycles of {w.name} after an untimed setup of {setup_s:.1f} s"},
+                            "extrapolated": extrap,
+                            "sample": f"{steps} V-cycles of {w.name} on {'x'.join(map(str, w.shape))} points "
+                                      f"after an untimed setup of {setup_s:.1f} s"},
            "e2e": {"value": value, "unit": "unknowns/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out))
 
@@ -482,14 +671,15 @@ def run_batched(args):
     __graft_entry__.build()
     from paper_1111_4363_gb300 import autotune
     from paper_1111_4363_gb300 import binding as B
+    precision = precision if precision >= 0 else 0
     members = [dataclasses.replace(wl.batched_2d(i), trial=3 if args.trial < 0 else args.trial)
                for i in range(args.batch)]
     rep = dataclasses.replace(members[0], n=(128, 128, 1))
-    best = autotune.tune(rep, precision=args.precision)
+    best = autotune.tune(rep, precision=precision)
     ws = [dataclasses.replace(m, **best) for m in members]
     ctxs, psis = [], []
     for w in ws:
-        ctx = B.Context(B.config_from_workload(w, precision=args.precision))
+        ctx = B.Context(B.config_from_workload(w, precision=precision))
         ctx.set_hamiltonian(torch.tensor(wl.potential(w).ravel(), dtype=torch.float64, device="cuda"), w.pulse)
         ctxs.append(ctx)
         psis.append(torch.from_numpy(wl.initial_state(w).ravel()).cuda())
@@ -519,11 +709,11 @@ def run_batched(args):
     value_seq = work_seq / el_seq
     out = {"metric": METRIC, "value": value, "unit": "unknowns/s", "n_gpus": 1, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps, "higher_is_better": True,
-           "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.precision == 0 else "c64 local solves + f64 refinement",
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64" if precision == 0 else "c64 local solves + f64 refinement",
            "data": "synthetic",
            "config": {"workload": f"2d_batched_{args.batch}_K4", "members": args.batch,
                       "grids": "seeded n in {64, 80, ..., 256}", "unknowns_total": sum(w.nunknowns for w in ws),
-                      "autotuned": best, "tol_rel_action": ws[0].tol, "precision": args.precision},
+                      "autotuned": best, "tol_rel_action": ws[0].tol, "precision": precision},
            "sequential": {"value": value_seq, "ms_per_step": 1e3 * el_seq / args.steps},
            "speedup_vs_sequential": value / value_seq,
            "max_rel_action": max(s[3] for st in stats for s in st), "clocks": clk}
@@ -531,19 +721,20 @@ def run_batched(args):
 
 
 def run_3d_adjoint(args):
-    """3D hydrogen in a 32-component pulse (128^3, K = 4, 2x2x2 subvolumes): forward propagation with
+    """3D hydrogen in a 32-component pulse (128^3, K = 4, 4x4x4 subvolumes): forward propagation with
     checkpoints every 20 steps, then the gradient of the final dipole w.r.t. the 32 amplitudes."""
     import torch
     import __graft_entry__
     __graft_entry__.build()
     from paper_1111_4363_gb300 import binding as B
+    precision = precision if precision >= 0 else 1
     n = args.n3d
     w = dataclasses.replace(wl.hydrogen_3d(n=n, nsteps=args.steps), **PRODUCTION_3D)
     if args.trial >= 0:
         w = dataclasses.replace(w, trial=args.trial)
     # checkpoints every 20 steps; the backward pass keeps a recomputed segment's factors on the
     # device (20 steps x all levels: ~74 GB FP64, ~37 GB complex64) instead of factorising again
-    cfg = B.config_from_workload(w, precision=args.precision, ckpt_every=20, cache_factors=1)
+    cfg = B.config_from_workload(w, precision=precision, ckpt_every=20, cache_factors=1)
     ctx = B.Context(cfg)
     V0 = torch.tensor(wl.potential(w).ravel(), dtype=torch.float64, device="cuda")
     torch.cuda.synchronize()
@@ -553,34 +744,40 @@ def run_3d_adjoint(args):
     psi = torch.from_numpy(wl.initial_state(w).ravel()).cuda()
     ctx.profile_enable(True)
     torch.cuda.synchronize()
+    clk_f = ClockSampler(0)
+    clk_f.start()
     a = time.perf_counter()
     st, stats = ctx.step(psi, args.steps, 0.0, stats=True)
     torch.cuda.synchronize()
     el_f = time.perf_counter() - a
+    clocks_f = clk_f.stop()
     prof = ctx.profile_read()
     ctx.profile_enable(False)
     x = torch.from_numpy(wl.laser_coordinate(w).ravel()).cuda()
     hd = float(np.prod(w.h[:3]))
     dJ = (hd * x * psi).contiguous()
+    clk_b = ClockSampler(0)
+    clk_b.start()
     a = time.perf_counter()
     grad = ctx.backward(dJ, w.pulse.ncomp)
     torch.cuda.synchronize()
     el_b = time.perf_counter() - a
+    clocks_b = clk_b.stop()
     sweeps = sum(s_[1] for s_ in stats)
     out = {"metric": METRIC, "value": w.nunknowns * sweeps / el_f, "unit": "unknowns/s", "n_gpus": 1,
            "steps": args.steps, "warmup": 0, "ms_per_step": 1e3 * el_f / args.steps, "higher_is_better": True,
-           "dtype": "f64" if args.precision == 0 else "c64 local solves + f64 refinement", "data": "synthetic",
+           "dtype": "f64" if precision == 0 else "c64 local solves + f64 refinement", "data": "synthetic",
            "config": {"workload": w.name, "grid": list(w.shape), "K": w.nt, "subvolume": list(w.sub),
                       "levels": w.levels, "cycle": cycle_name(w), "trial": w.trial,
                       "pulse_components": w.pulse.ncomp, "ckpt_every": 20, "cache_factors": True,
-                      "l2": l2_note(w, args.precision)},
+                      "l2": l2_note(w, precision)},
            "cycles_per_step": sum(s_[0] for s_ in stats) / args.steps,
            "backward_ms_per_step": 1e3 * el_b / args.steps, "set_hamiltonian_s": setup_s,
-           "roofline": dominant_roofline(prof, w, args.precision, 1e3 * el_f, traffic_ok=False),
-           "stencil_roofline": stencil_roofline(prof, args.precision),
-           "stencil_roofline_c64": stencil_roofline(prof, args.precision, c64=True),
+           "roofline": dominant_roofline(prof, w, precision, 1e3 * el_f, traffic_ok=False),
+           "stencil_roofline": stencil_roofline(prof, precision),
+           "stencil_roofline_c64": stencil_roofline(prof, precision, c64=True),
            "dipole_T": float(hd * (x * psi.abs() ** 2).sum()), "grad_norm": float(np.linalg.norm(grad)),
-           "grad_head": [float(g) for g in grad[:4]]}
+           "grad_head": [float(g) for g in grad[:4]], "clocks": clocks_f, "clocks_backward": clocks_b}
     print(json.dumps(out))
 
 
@@ -609,11 +806,14 @@ def run_lfa(args):
         B.lfa_maps(cases, ks, ws, out=out)
     torch.cuda.synchronize()
     reps = max(1, min(args.steps, 5))
+    clk = ClockSampler(0)
+    clk.start()
     a = time.perf_counter()
     for _ in range(reps):
         B.lfa_maps(cases, ks, ws, out=out)
     torch.cuda.synchronize()
     el = (time.perf_counter() - a) / reps
+    clocks = clk.stop()
     host = np.empty((len(cases), 2, ng, ng))
     a = time.perf_counter()
     B.lfa_maps(cases, ks, ws, out=host)
@@ -638,7 +838,7 @@ def run_lfa(args):
                       "kappa_nu": LFA_KAPPA_NU, "cases": len(cases)},
            "e2e": {"value": evals / el_e2e, "unit": "evaluations/s", "h2d_bytes_per_step": 16 * ng,
                    "d2h_bytes_per_step": 8 * evals * 2},
-           "summary": summary}
+           "summary": summary, "clocks": clocks}
     if not args.no_cpu_baseline:
         from oracle import lfa
         sub = np.linspace(-8.0, 8.0, 6)
@@ -653,14 +853,18 @@ def run_lfa(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=40)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="2d",
-                    choices=["2d", "2d-small", "1d", "2d-square", "3d", "3d-small", "batched", "3d-adjoint", "lfa"])
+    ap.add_argument("--workload", default="3d",
+                    choices=["3d", "3d-small", "2d", "2d-small", "1d", "2d-square", "batched", "3d-adjoint", "lfa"])
     ap.add_argument("--batch", type=int, default=512)
     ap.add_argument("--n3d", type=int, default=128)
-    ap.add_argument("--precision", type=int, default=0, choices=[0, 1])
+    ap.add_argument("--precision", type=int, default=-1, choices=[-1, 0, 1],
+                    help="0 FP64, 1 complex64 local solves with FP64 refinement; -1: the workload's own "
+                         "(1 for the 3D workload, 0 otherwise)")
+    ap.add_argument("--headline-only", action="store_true",
+                    help="only the headline measurement (no sub-records), e.g. under ncu")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--trial", type=int, default=-1, choices=[-1, 0, 1, 2, 3],
                     help="trial iterate of each step (extrapolation order + 1); -1: the workload's setting")

@@ -22,7 +22,7 @@ LOCAL_FORMS = {"lsq": 0, "square": 1}
 
 EXPORTS = ["la_init", "la_set_hamiltonian", "la_step", "la_action", "la_solve_step", "la_residual",
            "la_relax_colour", "la_time_matrices", "la_backward", "la_step_batch", "la_profile_enable", "la_profile_read", "la_action_noalloc",
-           "la_lfa_maps", "la_wait_selftest",
+           "la_lfa_maps", "la_wait_selftest", "la_fma_peaks",
            "la_finalize", "la_last_error", "la_version"]
 NOALLOC_MAX_POINTS = 1 << 22
 
@@ -84,6 +84,7 @@ def lib() -> C.CDLL:
         L.la_profile_enable.argtypes = [vp, i]
         L.la_profile_read.argtypes = [vp, C.POINTER(la_profile)]
         L.la_action_noalloc.argtypes = [C.POINTER(la_config), vp, C.POINTER(la_pulse), vp, d, vp, C.POINTER(d), vp]
+        L.la_fma_peaks.argtypes = [C.POINTER(d), C.POINTER(d), C.POINTER(C.c_int), vp]
         L.la_finalize.argtypes = [vp]
         L.la_last_error.argtypes = [vp]
         L.la_last_error.restype = C.c_char_p
@@ -195,6 +196,16 @@ def wait_selftest(polls: int, stream=None) -> int:
     if rc != LA_OK:
         raise LeastActionError(rc, "la_wait_selftest failed")
     return st.value
+
+
+def fma_peaks(stream=None):
+    """la_fma_peaks: measured (FP64 TFLOP/s, FP32 TFLOP/s, SM count) of the current device."""
+    L = lib()
+    a, b, n = C.c_double(), C.c_double(), C.c_int()
+    rc = L.la_fma_peaks(C.byref(a), C.byref(b), C.byref(n), _stream_handle(stream))
+    if rc != LA_OK:
+        raise LeastActionError(rc, "la_fma_peaks failed")
+    return a.value, b.value, n.value
 
 
 def action_noalloc(cfg: la_config, V0, pulse, psi0, t0: float, c, stream=None) -> float:

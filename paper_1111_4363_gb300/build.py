@@ -11,7 +11,7 @@ CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libleastaction.so")
 SOURCES = ["la_api.cu", "la_noalloc.cu", "k_grid.cu", "k_galerkin.cu", "k_adjoint.cu", "k_subvol_f64.cu",
-           "k_subvol_f32.cu", "k_square.cu", "k_lfa.cu"]
+           "k_subvol_f32.cu", "k_square.cu", "k_lfa.cu", "k_probe.cu"]
 HEADERS = ["la_internal.cuh", "k_subvol.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC"]

@@ -1,0 +1,75 @@
+// Measured FMA throughput of this GPU: the denominators of the FP64- and FP32-pipe rooflines.
+//
+// Every thread runs kChains independent FMA chains for `iters` iterations, so the pipe, not the
+// dependent-FMA latency, is the limit; the grid fills every SM several times over.  The result is
+// written to memory only when the chains cancel to a value that cannot occur, so the compiler keeps
+// the work and the store costs nothing.
+#include <cuda_runtime.h>
+
+#include "../../include/leastaction.h"
+
+namespace {
+
+constexpr int kChains = 8;
+constexpr int kThreads = 256;
+
+template <typename R>
+__global__ void __launch_bounds__(kThreads) k_fma_probe(int iters, R a, R b, R* sink) {
+  R x[kChains];
+#pragma unroll
+  for (int c = 0; c < kChains; ++c) x[c] = (R)(threadIdx.x + c) * (R)1e-3;
+  for (int i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int c = 0; c < kChains; ++c) x[c] = fma(x[c], a, b);
+  }
+  R s = 0;
+#pragma unroll
+  for (int c = 0; c < kChains; ++c) s += x[c];
+  if (s == (R)-12345.678) sink[blockIdx.x] = s;
+}
+
+template <typename R>
+cudaError_t time_probe(int blocks, int iters, cudaStream_t s, double* tflops) {
+  R* sink = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaError_t err = cudaEventCreate(&e0);
+  if (err == cudaSuccess) err = cudaEventCreate(&e1);
+  if (err == cudaSuccess) {
+    // warm-up launch (clocks up, code loaded), then the timed one
+    k_fma_probe<R><<<blocks, kThreads, 0, s>>>(iters / 4, (R)0.999, (R)1e-4, sink);
+    cudaEventRecord(e0, s);
+    k_fma_probe<R><<<blocks, kThreads, 0, s>>>(iters, (R)0.999, (R)1e-4, sink);
+    cudaEventRecord(e1, s);
+    err = cudaEventSynchronize(e1);
+  }
+  if (err == cudaSuccess) err = cudaGetLastError();
+  float ms = 0.0f;
+  if (err == cudaSuccess) err = cudaEventElapsedTime(&ms, e0, e1);
+  if (err == cudaSuccess)
+    *tflops = 2.0 * kChains * (double)iters * blocks * kThreads / (ms * 1e-3) / 1e12;
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  return err;
+}
+
+}  // namespace
+
+extern "C" la_status la_fma_peaks(double* fp64_tflops, double* fp32_tflops, int* sm_count, void* cuda_stream) {
+  if (!fp64_tflops || !fp32_tflops || !sm_count) return LA_EINVAL;
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) !=
+                                                cudaSuccess) {
+    cudaGetLastError();
+    return LA_ECUDA;
+  }
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  const int blocks = sms * 8;
+  // about 20 ms each at the expected rates (FP64 ~1.2 TFLOP/s, FP32 ~75 TFLOP/s)
+  if (time_probe<double>(blocks, 1 << 11, s, fp64_tflops) != cudaSuccess ||
+      time_probe<float>(blocks, 1 << 17, s, fp32_tflops) != cudaSuccess) {
+    cudaGetLastError();
+    return LA_ECUDA;
+  }
+  *sm_count = sms;
+  return LA_OK;
+}

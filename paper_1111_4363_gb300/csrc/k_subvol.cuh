@@ -932,6 +932,154 @@ __device__ __forceinline__ void subvol_solve_warp(const CT* F, CT* rhs, CT* y, C
   }
 }
 
+// Triangular solves with a wide factor (more than eight block rows) by all 128 threads of the
+// sweep's CTA: every load of a step (one block row forward, one block column backward) is issued
+// together, and in complex64 the next step's blocks are loaded while the current step computes, so
+// the 2 NB dependent steps wait on memory about once each instead of once per block.  Forward, thread
+// (r, q) = (t / 8, t % 8) takes entries (r, 2q) and (r, 2q + 1) of each block of the row (coalesced
+// 16-byte pairs); backward, thread (r, q) = (t % 16, t / 16) takes entries (2q, r) and (2q + 1, r) of
+// each block of the column (two coalesced rows per warp).  x = (L L^dagger)^{-1} rhs; rhs is
+// overwritten by x.  Called by all threads of the CTA, between barriers.
+template <typename CT> struct CPair;
+template <> struct CPair<float2> {
+  float4 v;
+  __device__ __forceinline__ void load(const float2* p) { v = __ldg(reinterpret_cast<const float4*>(p)); }
+  __device__ __forceinline__ float2 a() const { return make_float2(v.x, v.y); }
+  __device__ __forceinline__ float2 b() const { return make_float2(v.z, v.w); }
+};
+template <> struct CPair<double2> {
+  double2 a_, b_;
+  __device__ __forceinline__ void load(const double2* p) { a_ = __ldg(p); b_ = __ldg(p + 1); }
+  __device__ __forceinline__ double2 a() const { return a_; }
+  __device__ __forceinline__ double2 b() const { return b_; }
+};
+// the two complex entries (2q, r) and (2q + 1, r) of a block (a column pair, stride 16)
+template <typename CT>
+__device__ __forceinline__ CPair<CT> load_colpair(const CT* blk, int q, int r);
+template <>
+__device__ __forceinline__ CPair<float2> load_colpair<float2>(const float2* blk, int q, int r) {
+  CPair<float2> p;
+  const float2 x = __ldg(blk + (2 * q) * LA_BLK + r), y = __ldg(blk + (2 * q + 1) * LA_BLK + r);
+  p.v = make_float4(x.x, x.y, y.x, y.y);
+  return p;
+}
+template <>
+__device__ __forceinline__ CPair<double2> load_colpair<double2>(const double2* blk, int q, int r) {
+  CPair<double2> p;
+  p.a_ = __ldg(blk + (2 * q) * LA_BLK + r);
+  p.b_ = __ldg(blk + (2 * q + 1) * LA_BLK + r);
+  return p;
+}
+
+template <typename CT>
+__device__ __forceinline__ CT reduce_xor(CT v, int m) {
+  v.x += __shfl_xor_sync(0xffffffffu, v.x, m);
+  v.y += __shfl_xor_sync(0xffffffffu, v.y, m);
+  return v;
+}
+
+template <typename CT, int NPAD>
+__device__ __forceinline__ void subvol_solve_wide(const CT* __restrict__ F, CT* rhs, CT* y, CT* tvec, CT* part) {
+  constexpr int NB = NPAD / LA_BLK;
+  constexpr bool kPrefetch = sizeof(CT) == 8;   // complex64: next step's blocks in flight during this one
+  const int t = threadIdx.x;
+  {
+    const int r = t >> 3, q = t & 7;
+    CPair<CT> cur[NB];
+    cur[0].load(F + r * LA_BLK + 2 * q);
+#pragma unroll
+    for (int I = 0; I < NB; ++I) {
+      CPair<CT> nxt[NB];
+      if (kPrefetch && I + 1 < NB) {
+#pragma unroll
+        for (int J = 0; J <= I + 1; ++J) nxt[J].load(F + (size_t)tri_index(I + 1, J) * 256 + r * LA_BLK + 2 * q);
+      }
+      if (!kPrefetch && I > 0) {
+#pragma unroll
+        for (int J = 0; J <= I; ++J) cur[J].load(F + (size_t)tri_index(I, J) * 256 + r * LA_BLK + 2 * q);
+      }
+      CT acc0 = mkc<CT>(0, 0), acc1 = mkc<CT>(0, 0);
+#pragma unroll
+      for (int J = 0; J < I; ++J) {
+        cfma(acc0, cur[J].a(), y[J * LA_BLK + 2 * q]);
+        cfma(acc1, cur[J].b(), y[J * LA_BLK + 2 * q + 1]);
+      }
+      CT acc = mkc<CT>(acc0.x + acc1.x, acc0.y + acc1.y);
+      acc = reduce_xor(acc, 1);
+      acc = reduce_xor(acc, 2);
+      acc = reduce_xor(acc, 4);
+      if (q == 0) tvec[r] = mkc<CT>(rhs[I * LA_BLK + r].x - acc.x, rhs[I * LA_BLK + r].y - acc.y);
+      __syncthreads();
+      CT d = mkc<CT>(0, 0);
+      cfma(d, cur[I].a(), tvec[2 * q]);
+      cfma(d, cur[I].b(), tvec[2 * q + 1]);
+      d = reduce_xor(d, 1);
+      d = reduce_xor(d, 2);
+      d = reduce_xor(d, 4);
+      if (q == 0) y[I * LA_BLK + r] = d;
+      __syncthreads();
+      if (kPrefetch) {
+#pragma unroll
+        for (int J = 0; J < NB; ++J) cur[J] = nxt[J];
+      }
+    }
+  }
+  {
+    const int r = t & 15, q = t >> 4, w = t >> 5;
+    CPair<CT> cur[NB];
+    // step I uses blocks (J, I), J = I .. NB-1 ((I, I): the inverted diagonal block)
+    if (kPrefetch) {
+#pragma unroll
+      for (int J = NB - 1; J < NB; ++J) cur[J] = load_colpair<CT>(F + (size_t)tri_index(J, NB - 1) * 256, q, r);
+    }
+#pragma unroll
+    for (int I = NB - 1; I >= 0; --I) {
+      CPair<CT> nxt[NB];
+      if (kPrefetch && I > 0) {
+#pragma unroll
+        for (int J = I - 1; J < NB; ++J) nxt[J] = load_colpair<CT>(F + (size_t)tri_index(J, I - 1) * 256, q, r);
+      }
+      if (!kPrefetch) {
+#pragma unroll
+        for (int J = I; J < NB; ++J) cur[J] = load_colpair<CT>(F + (size_t)tri_index(J, I) * 256, q, r);
+      }
+      CT acc0 = mkc<CT>(0, 0), acc1 = mkc<CT>(0, 0);
+#pragma unroll
+      for (int J = I + 1; J < NB; ++J) {
+        cfma_conj(acc0, cur[J].a(), rhs[J * LA_BLK + 2 * q]);
+        cfma_conj(acc1, cur[J].b(), rhs[J * LA_BLK + 2 * q + 1]);
+      }
+      CT acc = reduce_xor(mkc<CT>(acc0.x + acc1.x, acc0.y + acc1.y), 16);
+      if ((t & 16) == 0) part[w * LA_BLK + r] = acc;
+      __syncthreads();
+      if (t < LA_BLK) {
+        CT s = part[r];
+#pragma unroll
+        for (int u = 1; u < 4; ++u) { s.x += part[u * LA_BLK + r].x; s.y += part[u * LA_BLK + r].y; }
+        tvec[r] = mkc<CT>(y[I * LA_BLK + r].x - s.x, y[I * LA_BLK + r].y - s.y);
+      }
+      __syncthreads();
+      CT d = mkc<CT>(0, 0);
+      cfma_conj(d, cur[I].a(), tvec[2 * q]);
+      cfma_conj(d, cur[I].b(), tvec[2 * q + 1]);
+      d = reduce_xor(d, 16);
+      if ((t & 16) == 0) part[w * LA_BLK + r] = d;
+      __syncthreads();
+      if (t < LA_BLK) {
+        CT s = part[r];
+#pragma unroll
+        for (int u = 1; u < 4; ++u) { s.x += part[u * LA_BLK + r].x; s.y += part[u * LA_BLK + r].y; }
+        rhs[I * LA_BLK + r] = s;
+      }
+      __syncthreads();
+      if (kPrefetch) {
+#pragma unroll
+        for (int J = 0; J < NB; ++J) cur[J] = nxt[J];
+      }
+    }
+  }
+}
+
 // complex64 finest-level sweeps with long factors (three or more block rows, up to 48 KB) copy the
 // subvolume's factor into shared memory with one bulk copy issued when the CTA starts: the copy
 // overlaps the residual stages and the 2 NB dependent steps of the triangular solves read no
@@ -1190,6 +1338,8 @@ k_sweep_fine(LevelGeom L, FineOp g, const TimeMats* __restrict__ tm, const typen
   __syncthreads();
   if (kStage)
     staged_solve<CT, NPAD>(sStage, sRhs, sY, sT, status);
+  else if (NPAD > LA_NPAD_MAX)
+    subvol_solve_wide<CT, NPAD>(factors + (size_t)b * L.fsize, sRhs, sY, sT, sRed);
   else
     subvol_solve<CT, NPAD>(factors + (size_t)b * L.fsize, sRhs, sY, sT, sRed);
   __syncthreads();

@@ -96,3 +96,26 @@ def test_reference_arm_line(bench):
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
     assert d["cpu_baseline"]["value"] == d["value"]
     assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
+
+
+def test_default_line_is_the_3d_workload(bench):
+    """No flags: the 3D workload (128^3, K = 4, 4x4x4 subvolumes of 256 unknowns, 2x2x2 on the Galerkin
+    levels, 4 levels) in its own arithmetic (FP64 with complex64 local solves); its factor store is
+    32768 subvolumes of 136 packed blocks; the oracle times a 32^3 sample of it."""
+    w = bench.workload("3d")
+    assert w.n == (128, 128, 128) and w.nt == 4 and w.sub == (4, 4, 4) and w.coarse_sub == (2, 2, 2)
+    assert w.levels == 4 and (w.nu1, w.nu2, w.coarse_nu, w.trial) == (1, 2, (1, 0), 3)
+    assert bench.default_precision("3d") == 1 and bench.default_precision("2d") == 0
+    assert bench.finest_factor_store(w, 1) == (32768, 136 * 256 * 8)
+    sample, extrap = bench.oracle_sample(w)
+    assert extrap and sample.n == (32, 32, 32) and sample.sub == w.sub and sample.nt == w.nt
+    assert bench.oracle_sample(bench.workload("2d")) == (bench.workload("2d"), False)
+
+
+def test_wide_factor_roofline_against_the_measured_peak(bench):
+    """The wide complex64 factorisation dominates: alu-bound against the FP32 peak measured in the run."""
+    w = bench.workload("3d")
+    r = bench.dominant_roofline(fake_profile(), w, 1, ms_total=20.0, traffic_ok=False, peaks=(1.2, 75.0, 152))
+    assert r["kernel"].startswith("k_factor_wide") and r["bound"] == "alu"
+    assert r["peak"] == pytest.approx(75.0) and "measured" in r["peak_note"] and "152 SMs" in r["peak_note"]
+    assert r["frac"] == pytest.approx(4.0e9 / 5e-3 / 1e12 / 75.0, abs=1e-4)
