@@ -537,7 +537,7 @@ def run_ours(args):
            "stencil_roofline": stencil_roofline(prof, precision),
            "stencil_roofline_c64": stencil_roofline(prof, precision, c64=True), "clocks": clk,
            "peaks": {"fp64_tflops": round(peaks[0], 4), "fp32_tflops": round(peaks[1], 3), "sm_count": peaks[2],
-                     "how": "la_fma_peaks: 8 independent FMA chains per thread, 8 CTAs of 256 threads per SM, "
+                     "how": "la_fma_peaks: 8 independent FMA chains per thread, one full wave of 256-thread CTAs on every SM, "
                             "CUDA events, in this run"}}
     extras = rank == 0 and ws == 1 and not args.headline_only
     if extras and args.workload == "3d" and precision == 1:

@@ -217,8 +217,8 @@ la_status la_profile_enable(la_ctx* ctx, int enable);
 la_status la_profile_read(la_ctx* ctx, la_profile* out);
 
 /* Measured FMA throughput of the current device (no paper counterpart: the denominators of the FP64- and
-   FP32-pipe rooflines that the benchmark reports).  Each thread of a grid of 8 CTAs per SM runs 8
-   independent fused multiply-add chains, one launch per precision after a shorter warm-up launch, timed
+   FP32-pipe rooflines that the benchmark reports).  Each thread of one full wave of resident CTAs (256
+   threads each) on every SM runs 8 independent fused multiply-add chains, one launch per precision after a shorter warm-up launch, timed
    with CUDA events on cuda_stream (about 20 ms each); flops count 2 per FMA.  Outputs are host pointers:
    fp64_tflops, fp32_tflops (TFLOP/s) and sm_count (the device's multiprocessors).  Synchronises
    cuda_stream.  Errors: LA_EINVAL (null pointer), LA_ECUDA. */

@@ -1,7 +1,7 @@
 // Measured FMA throughput of this GPU: the denominators of the FP64- and FP32-pipe rooflines.
 //
 // Every thread runs kChains independent FMA chains for `iters` iterations, so the pipe, not the
-// dependent-FMA latency, is the limit; the grid fills every SM several times over.  The result is
+// dependent-FMA latency, is the limit; the grid is one full wave of resident CTAs on every SM.  The result is
 // written to memory only when the chains cancel to a value that cannot occur, so the compiler keeps
 // the work and the store costs nothing.
 #include <cuda_runtime.h>
@@ -28,11 +28,17 @@ __global__ void __launch_bounds__(kThreads) k_fma_probe(int iters, R a, R b, R* 
   if (s == (R)-12345.678) sink[blockIdx.x] = s;
 }
 
+// One full wave: as many CTAs as fit on all SMs at once, so that no SM runs a tail of extra CTAs.
 template <typename R>
-cudaError_t time_probe(int blocks, int iters, cudaStream_t s, double* tflops) {
+cudaError_t time_probe(int sms, int iters, cudaStream_t s, double* tflops) {
   R* sink = nullptr;
+  int per_sm = 0;
+  cudaError_t err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fma_probe<R>, kThreads, 0);
+  if (err != cudaSuccess) return err;
+  if (per_sm < 1) return cudaErrorInvalidConfiguration;
+  const int blocks = sms * per_sm;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
-  cudaError_t err = cudaEventCreate(&e0);
+  err = cudaEventCreate(&e0);
   if (err == cudaSuccess) err = cudaEventCreate(&e1);
   if (err == cudaSuccess) {
     // warm-up launch (clocks up, code loaded), then the timed one
@@ -63,10 +69,9 @@ extern "C" la_status la_fma_peaks(double* fp64_tflops, double* fp32_tflops, int*
     return LA_ECUDA;
   }
   cudaStream_t s = (cudaStream_t)cuda_stream;
-  const int blocks = sms * 8;
-  // about 20 ms each at the expected rates (FP64 ~1.2 TFLOP/s, FP32 ~75 TFLOP/s)
-  if (time_probe<double>(blocks, 1 << 11, s, fp64_tflops) != cudaSuccess ||
-      time_probe<float>(blocks, 1 << 17, s, fp32_tflops) != cudaSuccess) {
+  // about 10-20 ms each at the expected rates (FP64 ~1.2 TFLOP/s, FP32 ~75 TFLOP/s)
+  if (time_probe<double>(sms, 1 << 11, s, fp64_tflops) != cudaSuccess ||
+      time_probe<float>(sms, 1 << 17, s, fp32_tflops) != cudaSuccess) {
     cudaGetLastError();
     return LA_ECUDA;
   }

@@ -562,11 +562,43 @@ k_factor_blk(LevelGeom L, FineOp g, int is_fine, int nptsmax, const double* __re
 // table of point pairs is needed.
 constexpr int kWidePtsMax = 64;   // grid points of a wide subvolume
 
+// Two consecutive complex entries (16-byte aligned), as one vector load where the type allows.
+template <typename CT> struct CPair;
+template <> struct CPair<float2> {
+  float4 v;
+  __device__ __forceinline__ void load(const float2* p) { v = __ldg(reinterpret_cast<const float4*>(p)); }
+  __device__ __forceinline__ float2 a() const { return make_float2(v.x, v.y); }
+  __device__ __forceinline__ float2 b() const { return make_float2(v.z, v.w); }
+};
+template <> struct CPair<double2> {
+  double2 a_, b_;
+  __device__ __forceinline__ void load(const double2* p) { a_ = __ldg(p); b_ = __ldg(p + 1); }
+  __device__ __forceinline__ double2 a() const { return a_; }
+  __device__ __forceinline__ double2 b() const { return b_; }
+};
+// the same pair from shared memory
+__device__ __forceinline__ CPair<float2> lds_pair(const float2* p) {
+  CPair<float2> r;
+  r.v = *reinterpret_cast<const float4*>(p);
+  return r;
+}
+__device__ __forceinline__ CPair<double2> lds_pair(const double2* p) {
+  CPair<double2> r;
+  r.a_ = p[0];
+  r.b_ = p[1];
+  return r;
+}
+
 // Shared-memory layout of the wide factorisation (bytes), for the padded size npad.
+// Rows of the two shared-memory panels are padded so that the transposed stores of the block row and the
+// column-wise accesses of the diagonal block spread over the banks: 17 entries for the block column,
+// 18 for the block row (whose rows the update reads as 16-byte pairs, so they start 16-byte aligned).
+constexpr int kWideStride = LA_BLK + 1;
+constexpr int kRowStride = LA_BLK + 2;
 __host__ __device__ constexpr size_t wide_factor_smem(int npad, size_t csize, size_t rsize) {
-  return csize * ((size_t)(npad - LA_BLK) * LA_BLK    // block row J, transposed [k][c]
-                  + (size_t)npad * LA_BLK             // the block column's rows 16 J .. npad-1
-                  + 256)                              // inv(L_JJ)^dagger, [k][c]
+  return csize * ((size_t)(npad - LA_BLK) * kRowStride     // block row J, transposed [k][c]
+                  + (size_t)npad * kWideStride             // the block column's rows 16 J .. npad-1
+                  + 256)                                   // inv(L_JJ)^dagger, [k][c]
          + rsize * (LA_NPAIR * LA_KMAX * LA_KMAX + 3 * kWidePtsMax + LA_BLK) + sizeof(int) * kWidePtsMax;
 }
 
@@ -640,32 +672,42 @@ __device__ __forceinline__ void wide_column_update(int J, int row, int c0, int n
     CT v[LA_BLK];
 #pragma unroll
     for (int kk = 0; kk < LA_BLK; ++kk) v[kk] = src[kk];
-    const CT* rowk = sRow + (size_t)Kb * LA_BLK * LA_BLK + c0;
+    const CT* rowk = sRow + (size_t)Kb * LA_BLK * kRowStride + c0;
 #pragma unroll
     for (int kk = 0; kk < LA_BLK; ++kk) {
 #pragma unroll
-      for (int q = 0; q < CPT; ++q) {
-        const CT y = rowk[kk * LA_BLK + q];
-        // acc -= v conj(y)
-        acc[q].x = fma(-v[kk].x, y.x, acc[q].x); acc[q].x = fma(-v[kk].y, y.y, acc[q].x);
-        acc[q].y = fma(-v[kk].y, y.x, acc[q].y); acc[q].y = fma(v[kk].x, y.y, acc[q].y);
+      for (int q = 0; q < CPT; q += (CPT > 1 ? 2 : 1)) {
+        CT y[2];
+        if (CPT > 1) {
+          const CPair<CT> yp = lds_pair(rowk + kk * kRowStride + q);
+          y[0] = yp.a();
+          y[1] = yp.b();
+        } else {
+          y[0] = rowk[kk * kRowStride + q];
+        }
+#pragma unroll
+        for (int u = 0; u < (CPT > 1 ? 2 : 1); ++u) {
+          // acc -= v conj(y)
+          acc[q + u].x = fma(-v[kk].x, y[u].x, acc[q + u].x); acc[q + u].x = fma(-v[kk].y, y[u].y, acc[q + u].x);
+          acc[q + u].y = fma(-v[kk].y, y[u].x, acc[q + u].y); acc[q + u].y = fma(v[kk].x, y[u].y, acc[q + u].y);
+        }
       }
     }
   }
 #pragma unroll
-  for (int q = 0; q < CPT; ++q) sPan[row * LA_BLK + c0 + q] = acc[q];
+  for (int q = 0; q < CPT; ++q) sPan[row * kWideStride + c0 + q] = acc[q];
 }
 
 template <typename R, int NPAD>
-__global__ void __launch_bounds__(kFactorThreads, sizeof(R) == 4 ? 2 : 1)
+__global__ void __launch_bounds__(kFactorThreads, sizeof(R) == 4 ? 3 : 1)
 k_factor_wide(LevelGeom L, FineOp g, const TimeMats* __restrict__ tm, typename C2<R>::T* __restrict__ factors,
               int* __restrict__ status) {
   typedef typename C2<R>::T CT;
   constexpr int NB = NPAD / LA_BLK;
   extern __shared__ __align__(16) unsigned char smem[];
-  CT* sRow = reinterpret_cast<CT*>(smem);                       // [NPAD-16][16]: sRow[k][c] = L[16 J + c][k]
-  CT* sPan = sRow + (size_t)(NPAD - LA_BLK) * LA_BLK;          // [NPAD][16]: rows 16 J + row of block column J
-  CT* sInvT = sPan + (size_t)NPAD * LA_BLK;                    // [16][16]: sInvT[k][c] = conj(inv(L_JJ)[c][k])
+  CT* sRow = reinterpret_cast<CT*>(smem);                       // [NPAD-16][18]: sRow[k][c] = L[16 J + c][k]
+  CT* sPan = sRow + (size_t)(NPAD - LA_BLK) * kRowStride;      // [NPAD][17]: rows 16 J + row of block column J
+  CT* sInvT = sPan + (size_t)NPAD * kWideStride;               // [16][16]: sInvT[k][c] = conj(inv(L_JJ)[c][k])
   R* sP = reinterpret_cast<R*>(sInvT + 256);                   // [9][K*K]
   R* sD = sP + LA_NPAIR * LA_KMAX * LA_KMAX;                   // [64] dsum + V0
   R* sX = sD + kWidePtsMax;                                    // [64] laser coordinate
@@ -696,13 +738,11 @@ k_factor_wide(LevelGeom L, FineOp g, const TimeMats* __restrict__ tm, typename C
   }
   __syncthreads();
   const FastDiv dK = L.fd_K;
-  const int ti = tid >> 4, tk = tid & 15;
-
   for (int J = 0; J < NB; ++J) {
     // block row J (blocks (J, 0..J-1)) transposed into shared memory
     for (int t = tid; t < J * 256; t += kFactorThreads) {
       const int Kb = t >> 8, w = t & 255, c = w >> 4, kk = w & 15;
-      sRow[(Kb * LA_BLK + kk) * LA_BLK + c] = F[(size_t)tri_index(J, Kb) * 256 + w];
+      sRow[(Kb * LA_BLK + kk) * kRowStride + c] = F[(size_t)tri_index(J, Kb) * 256 + w];
     }
     __syncthreads();
     // assemble and update the block column: rows 16 J .. NPAD-1, tpr threads per row
@@ -725,59 +765,68 @@ k_factor_wide(LevelGeom L, FineOp g, const TimeMats* __restrict__ tm, typename C
       }
     }
     __syncthreads();
-    // Cholesky of the diagonal block (rows 0..15 of sPan, lower triangle), thread (ti, tk) = entry
-    for (int j = 0; j < LA_BLK; ++j) {
-      R d2 = sPan[j * LA_BLK + j].x;
-      if (!(d2 > (R)0)) {
-        if (tid == 0) atomicOr(status, 1);
-        d2 = (R)1;
+    // Cholesky of the diagonal block (rows 0..15 of sPan, lower triangle) and its inverse, by warp 0
+    // alone (steps ordered by __syncwarp); the other warps wait at the barrier that follows
+    if (tid < 32) {
+      const int lane = tid;
+      for (int j = 0; j < LA_BLK; ++j) {
+        R d2 = sPan[j * kWideStride + j].x;
+        if (!(d2 > (R)0)) {
+          if (lane == 0) atomicOr(status, 1);
+          d2 = (R)1;
+        }
+        const R inv = rsq(d2);
+        // column j: L[i][j] = A[i][j] / sqrt(d2), i > j; L[j][j] = sqrt(d2)
+        if (lane == j) {
+          sPan[j * kWideStride + j] = mkc<CT>(d2 * inv, (R)0);
+          sPiv[j] = inv;
+        } else if (lane > j && lane < LA_BLK) {
+          CT v = sPan[lane * kWideStride + j];
+          sPan[lane * kWideStride + j] = mkc<CT>(v.x * inv, v.y * inv);
+        }
+        __syncwarp();
+        // trailing entries (i, k), j < k <= i: A[i][k] -= L[i][j] conj(L[k][j])
+        const int m = LA_BLK - 1 - j, T = m * (m + 1) / 2;
+        for (int e = lane; e < T; e += 32) {
+          int a_ = (int)((sqrtf(8.0f * (float)e + 1.0f) - 1.0f) * 0.5f);
+          while (a_ * (a_ + 1) / 2 > e) --a_;
+          while ((a_ + 1) * (a_ + 2) / 2 <= e) ++a_;
+          const int i = j + 1 + a_, k = j + 1 + (e - a_ * (a_ + 1) / 2);
+          const CT li = sPan[i * kWideStride + j], lk = sPan[k * kWideStride + j];
+          CT v = sPan[i * kWideStride + k];
+          v.x -= li.x * lk.x + li.y * lk.y;
+          v.y -= li.y * lk.x - li.x * lk.y;
+          sPan[i * kWideStride + k] = v;
+        }
+        __syncwarp();
       }
-      const R inv = rsq(d2);
-      CT nv = sPan[ti * LA_BLK + tk];
-      bool wr = false;
-      if (tk == j && ti >= j) {
-        nv = ti == j ? mkc<CT>(d2 * inv, (R)0) : mkc<CT>(nv.x * inv, nv.y * inv);
-        wr = true;
-      } else if (tk > j && ti >= tk) {
-        const CT a = sPan[ti * LA_BLK + j], bb = sPan[tk * LA_BLK + j];
-        const R s = inv * inv;
-        // nv -= a conj(bb) / d2
-        nv.x -= s * (a.x * bb.x + a.y * bb.y);
-        nv.y -= s * (a.y * bb.x - a.x * bb.y);
-        wr = true;
-      }
-      if (tid == 0) sPiv[j] = inv;
-      __syncthreads();
-      if (wr) sPan[ti * LA_BLK + tk] = nv;
-      __syncthreads();
-    }
-    // inv(L_JJ) column tk by forward substitution (16 threads), stored as sInvT[k][c] = conj(inv[c][k])
-    if (tid < LA_BLK) {
-      const int jj = tid;
-      CT x[LA_BLK];
+      // inv(L_JJ) column lane by forward substitution (16 lanes), stored as sInvT[k][c] = conj(inv[c][k])
+      if (lane < LA_BLK) {
+        const int jj = lane;
+        CT x[LA_BLK];
 #pragma unroll
-      for (int i = 0; i < LA_BLK; ++i) {
-        CT acc = mkc<CT>(0, 0);
+        for (int i = 0; i < LA_BLK; ++i) {
+          CT acc = mkc<CT>(0, 0);
 #pragma unroll
-        for (int k = 0; k < i; ++k)
-          if (k >= jj) cfma(acc, sPan[i * LA_BLK + k], x[k]);
-        const R rinv = sPiv[i];
-        if (i < jj) x[i] = mkc<CT>(0, 0);
-        else if (i == jj) x[i] = mkc<CT>(rinv, (R)0);
-        else x[i] = mkc<CT>(-acc.x * rinv, -acc.y * rinv);
-      }
-      // x = column jj of inv(L_JJ): inv[i][jj] = x[i]; sInvT[k][c] = conj(inv[c][k]) -> k = jj, c = i
+          for (int k = 0; k < i; ++k)
+            if (k >= jj) cfma(acc, sPan[i * kWideStride + k], x[k]);
+          const R rinv = sPiv[i];
+          if (i < jj) x[i] = mkc<CT>(0, 0);
+          else if (i == jj) x[i] = mkc<CT>(rinv, (R)0);
+          else x[i] = mkc<CT>(-acc.x * rinv, -acc.y * rinv);
+        }
 #pragma unroll
-      for (int i = 0; i < LA_BLK; ++i) {
-        sInvT[jj * LA_BLK + i] = mkc<CT>(x[i].x, -x[i].y);
-        F[(size_t)tri_index(J, J) * 256 + i * LA_BLK + jj] = x[i];
+        for (int i = 0; i < LA_BLK; ++i) {
+          sInvT[jj * LA_BLK + i] = mkc<CT>(x[i].x, -x[i].y);
+          F[(size_t)tri_index(J, J) * 256 + i * LA_BLK + jj] = x[i];
+        }
       }
     }
     __syncthreads();
     // blocks below: L_IJ = A_IJ inv(L_JJ)^dagger, L[r][c] = sum_{k <= c} A[r][k] conj(inv[c][k])
     for (int t = tid; t < (RJ - LA_BLK) * LA_BLK; t += kFactorThreads) {
       const int rr = LA_BLK + (t >> 4), c = t & 15;
-      const CT* a = sPan + rr * LA_BLK;
+      const CT* a = sPan + rr * kWideStride;
       CT s = mkc<CT>(0, 0);
 #pragma unroll
       for (int k = 0; k < LA_BLK; ++k)
@@ -940,19 +989,6 @@ __device__ __forceinline__ void subvol_solve_warp(const CT* F, CT* rhs, CT* y, C
 // 16-byte pairs); backward, thread (r, q) = (t % 16, t / 16) takes entries (2q, r) and (2q + 1, r) of
 // each block of the column (two coalesced rows per warp).  x = (L L^dagger)^{-1} rhs; rhs is
 // overwritten by x.  Called by all threads of the CTA, between barriers.
-template <typename CT> struct CPair;
-template <> struct CPair<float2> {
-  float4 v;
-  __device__ __forceinline__ void load(const float2* p) { v = __ldg(reinterpret_cast<const float4*>(p)); }
-  __device__ __forceinline__ float2 a() const { return make_float2(v.x, v.y); }
-  __device__ __forceinline__ float2 b() const { return make_float2(v.z, v.w); }
-};
-template <> struct CPair<double2> {
-  double2 a_, b_;
-  __device__ __forceinline__ void load(const double2* p) { a_ = __ldg(p); b_ = __ldg(p + 1); }
-  __device__ __forceinline__ double2 a() const { return a_; }
-  __device__ __forceinline__ double2 b() const { return b_; }
-};
 // the two complex entries (2q, r) and (2q + 1, r) of a block (a column pair, stride 16)
 template <typename CT>
 __device__ __forceinline__ CPair<CT> load_colpair(const CT* blk, int q, int r);
@@ -1151,6 +1187,7 @@ k_sweep_fine(LevelGeom L, FineOp g, const TimeMats* __restrict__ tm, const typen
   const int nbc = ec[0] * ec[1] * ec[2], nbf = ef[0] * ef[1] * ef[2], npts = e[0] * e[1] * e[2];
   const int sx = L.sub[0] + 4, sy = L.dim > 1 ? L.sub[1] + 4 : 1, sz = L.dim > 2 ? L.sub[2] + 4 : 1;
   const int nbc_max = sx * sy * sz;
+  const int nbf_max = (L.sub[0] + 2) * (L.dim > 1 ? L.sub[1] + 2 : 1) * (L.dim > 2 ? L.sub[2] + 2 : 1);
   // index maps item t -> (point i, time function m) and point -> (x, y, z) by multiply-shift
   // division: the level's divisors for a full subvolume, this CTA's own for a ragged one
   const bool full = e[0] == L.sub[0] && e[1] == L.sub[1] && e[2] == L.sub[2];
@@ -1173,12 +1210,12 @@ k_sweep_fine(LevelGeom L, FineOp g, const TimeMats* __restrict__ tm, const typen
   R* sU = sQ + LA_KMAX * LA_KMAX;
   R* sW = sU + LA_KMAX * LA_KMAX;
   R* sE = sW + LA_KMAX * LA_KMAX;
-  R* sV = sE + LA_KMAX * LA_KMAX;                     // dsum + V0 on the footprint box [nbc_max]
-  R* sX = sV + ((nbc_max + 3) & ~3);                  // laser coordinate on the footprint box [nbc_max]
-  CT* sC = reinterpret_cast<CT*>(sX + ((nbc_max + 3) & ~3));  // c on U+2  [nbc_max * K]
-  CT* sA = sC + (size_t)nbc_max * K;                  // Hc, then z   [nbc_max * K]
-  CT* sB = sA + (size_t)nbc_max * K;                  // r, then Hz   [nbc_max * K]
-  CT* sRhs = sB + (size_t)nbc_max * K;                // [NPAD]
+  R* sV = sE + LA_KMAX * LA_KMAX;                     // dsum + V0 on the footprint F = U + 1 [nbf_max]
+  R* sX = sV + ((nbf_max + 3) & ~3);                  // laser coordinate on the footprint [nbf_max]
+  CT* sC = reinterpret_cast<CT*>(sX + ((nbf_max + 3) & ~3));  // c on U+2  [nbc_max * K]
+  CT* sA = sC + (size_t)nbc_max * K;                  // Hc, then z, on the footprint   [nbf_max * K]
+  CT* sB = sA + (size_t)nbf_max * K;                  // r, then Hz, on the footprint   [nbf_max * K]
+  CT* sRhs = sB + (size_t)nbf_max * K;                // [NPAD]
   CT* sY = sRhs + NPAD;                               // [NPAD]
   CT* sT = sY + NPAD;                                 // [16]
   CT* sRed = sT + LA_BLK;                             // [128]
@@ -1579,7 +1616,9 @@ inline size_t factor_smem(const LevelGeom& L, int nptsmax, size_t csize, int mpc
 inline size_t sweep_fine_smem(const LevelGeom& L, int K, size_t rsize, size_t csize) {
   const int sx = L.sub[0] + 4, sy = L.dim > 1 ? L.sub[1] + 4 : 1, sz = L.dim > 2 ? L.sub[2] + 4 : 1;
   const size_t nbc = (size_t)sx * sy * sz;
-  return rsize * (4 * LA_KMAX * LA_KMAX + 2 * ((nbc + 3) & ~(size_t)3)) + csize * (3 * nbc * K + 2 * (size_t)L.npad + LA_BLK + 128);
+  const size_t nbf = (size_t)(L.sub[0] + 2) * (L.dim > 1 ? L.sub[1] + 2 : 1) * (L.dim > 2 ? L.sub[2] + 2 : 1);
+  return rsize * (4 * LA_KMAX * LA_KMAX + 2 * ((nbf + 3) & ~(size_t)3)) +
+         csize * (nbc * K + 2 * nbf * K + 2 * (size_t)L.npad + LA_BLK + 128);
 }
 inline size_t sweep_coarse_smem(const LevelGeom& L, int K, size_t rsize, size_t csize) {
   const size_t nptsmax = (size_t)L.sub[0] * L.sub[1] * L.sub[2];

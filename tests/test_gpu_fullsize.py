@@ -182,15 +182,19 @@ def test_3d_residual_at_sampled_points(bench):
     np.testing.assert_allclose(got, ref, rtol=0, atol=1e-13 * np.max(np.abs(ref)))
 
 
-def test_3d_adjoint_gradient_against_central_differences(bench):
-    """128^3 with a 32-component pulse, mixed precision local solves, checkpoints every 2 steps."""
-    nsteps = 3
+@pytest.mark.parametrize("precision", [0, 1])
+def test_3d_adjoint_gradient_against_central_differences(bench, precision):
+    """128^3 with the 32-component pulse and the configuration's 4x4x4 x 4 subvolumes (256 unknowns),
+    FP64 and complex64 local solves, 4 steps with checkpoints every 2: the adjoint gradient of the final
+    dipole for the two largest components against central differences of the GPU forward, 1e-6."""
+    nsteps = 4
     w = dataclasses.replace(wl.hydrogen_3d(n=128, nsteps=nsteps), **bench.PRODUCTION_3D)
+    assert w.sub == (4, 4, 4) and w.nt == 4
     prob = system.Problem.from_workload(w)
     psi0 = wl.initial_state(w).ravel()
 
     def forward(wk):
-        ctx = gpu_context(wk, precision=1, tol=1e-22, max_cycles=80, ckpt_every=2)
+        ctx = gpu_context(wk, precision=precision, tol=1e-22, max_cycles=80, ckpt_every=2)
         psi = psi0.copy()
         ctx.step(psi, nsteps, 0.0)
         return ctx, psi
@@ -198,17 +202,21 @@ def test_3d_adjoint_gradient_against_central_differences(bench):
     ctx, psiT = forward(w)
     dJ = prob.vol * prob.xlaser * psiT
     g = ctx.backward(dJ, w.pulse.ncomp)
+    ctx.close()
     picks = np.argsort(-np.abs(g))[:2]
-    eps = 1e-4 * max(np.max(np.abs(w.pulse.amp)), 1e-3)
+    # J is close to linear in the amplitudes (weak field), so a step of 1e-3 of the largest amplitude
+    # keeps the truncation error far below the 1e-12-relative rounding of the converged forward steps
+    eps = 1e-3 * max(np.max(np.abs(w.pulse.amp)), 1e-3)
     for j in picks:
         vals = []
         for sgn in (1, -1):
             amp = list(w.pulse.amp)
             amp[j] += sgn * eps
-            _, pT = forward(dataclasses.replace(w, pulse=dataclasses.replace(w.pulse, amp=amp)))
+            cj, pT = forward(dataclasses.replace(w, pulse=dataclasses.replace(w.pulse, amp=amp)))
+            cj.close()
             vals.append(system.dipole(prob, pT))
         fd = (vals[0] - vals[1]) / (2 * eps)
-        assert g[j] == pytest.approx(fd, rel=1e-5), (j, g[j], fd)
+        assert g[j] == pytest.approx(fd, rel=1e-6), (j, g[j], fd)
 
 
 def test_batched_members_equal_their_single_runs(bench):
