@@ -671,7 +671,7 @@ def run_batched(args):
     __graft_entry__.build()
     from paper_1111_4363_gb300 import autotune
     from paper_1111_4363_gb300 import binding as B
-    precision = precision if precision >= 0 else 0
+    precision = args.precision if args.precision >= 0 else 0
     members = [dataclasses.replace(wl.batched_2d(i), trial=3 if args.trial < 0 else args.trial)
                for i in range(args.batch)]
     rep = dataclasses.replace(members[0], n=(128, 128, 1))
@@ -727,7 +727,7 @@ def run_3d_adjoint(args):
     import __graft_entry__
     __graft_entry__.build()
     from paper_1111_4363_gb300 import binding as B
-    precision = precision if precision >= 0 else 1
+    precision = args.precision if args.precision >= 0 else 1
     n = args.n3d
     w = dataclasses.replace(wl.hydrogen_3d(n=n, nsteps=args.steps), **PRODUCTION_3D)
     if args.trial >= 0:

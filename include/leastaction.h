@@ -96,6 +96,10 @@ typedef struct {
                            two-colour checkerboard, LU with partial pivoting; N may rise and the
                            iteration may diverge.  1 requires precision 0, levels 1, sub >= 1 and at
                            most 96 unknowns per subvolume; la_backward rejects it (LA_EINVAL) */
+  int factor_group;     /* CTA packing of the shared-memory subvolume factorisations (up to 128 unknowns):
+                           0 = several small matrices per CTA on levels of 512 or more subvolumes (8 up to
+                           32 unknowns, 2 up to 64; complex64: 4 up to 32, 2 up to 48), chosen by size;
+                           1 = one matrix per CTA on every level */
 } la_config;
 
 /* Laser field E(t) = sum_k amp[k] * env_k(t) * sin(omega[k] t), env_k = exp(-((t - t_center[k])/sigma[k])^2)
@@ -141,12 +145,16 @@ la_status la_step(la_ctx* ctx, void* psi, int nsteps, double t0, la_step_stats* 
 
 /* Many independent propagations stepped together (each context its own grid, potential, pulse and
    configuration).  psis[i] (complex128[Np_i], host or device) is advanced by nsteps steps from time
-   t0s[i].  Every context works on its own internal stream for the whole call; per time step all
-   contexts' factorisations are enqueued, then relaxation cycles are issued in rounds -- one captured
-   cycle per unconverged context, then one synchronisation per context -- until every context reached
-   its tolerance, so the small per-context launches of different problems run concurrently.
+   t0s[i].  Every context works on its own internal stream for the whole call, and every step of every
+   context is enqueued without waiting for the GPU: time matrices, factorisations, the starting iterate
+   (the extrapolated trial when its action is below N(0), else c = 0, decided on the device), one launch
+   of the context's relaxation graph -- a conditional loop that runs V-cycles until the action computed on
+   the device meets the stopping rule (N/N(0) <= tol, max_cycles, or a non-finite action) -- and the step
+   advance.  The contexts' streams run concurrently and the host synchronises once, after the last step.
    stats (host, nullable): nctx * nsteps records, context-major.  Returns LA_ENOTCONV if some step of
-   some context hit max_cycles or its action became non-finite (whatever that context's tol).  Errors: LA_EINVAL (null or repeated context), LA_ESTATE, LA_ECUDA. */
+   some context hit max_cycles or its action became non-finite (whatever that context's tol).
+   Errors: LA_EINVAL (null or repeated context), LA_ESTATE, LA_ENOMEM, LA_ECUDA (also a subvolume matrix
+   that was not positive definite in any step, reported after the call's last step). */
 la_status la_step_batch(la_ctx* const* ctxs, int nctx, void* const* psis, int nsteps, const double* t0s,
                         la_step_stats* stats);
 

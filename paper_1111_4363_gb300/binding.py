@@ -40,7 +40,7 @@ class la_config(C.Structure):
                 ("precision", C.c_int), ("laser_axis", C.c_int), ("ckpt_every", C.c_int),
                 ("coarse_sub", C.c_int * 3), ("trial", C.c_int), ("coarse_cycle", C.c_int),
                 ("coarse_nu1", C.c_int), ("coarse_nu2", C.c_int), ("cache_factors", C.c_int),
-                ("local_form", C.c_int)]
+                ("local_form", C.c_int), ("factor_group", C.c_int)]
 
 
 class la_pulse(C.Structure):
@@ -145,6 +145,7 @@ def config_from_workload(w, precision: int = 0, **overrides) -> la_config:
     if getattr(w, "coarse_nu", None) is not None:
         cfg.coarse_cycle, cfg.coarse_nu1, cfg.coarse_nu2 = 1, int(w.coarse_nu[0]), int(w.coarse_nu[1])
     cfg.local_form = LOCAL_FORMS[getattr(w, "local_form", "lsq")]
+    cfg.factor_group = int(getattr(w, "factor_group", 0))
     for k, v in overrides.items():
         setattr(cfg, k, v)
     return cfg

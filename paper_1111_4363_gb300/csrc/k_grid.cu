@@ -730,6 +730,55 @@ void launch_norm_final(const double* partials, int n, double scale, double* out,
   k_norm_final<<<1, 256, 0, s>>>(partials, n, scale, out);
 }
 
+// ---------------------------------------------------------------- device-side relaxation loop
+// Trial or zero start of a step's relaxation, decided on the device: the extrapolated trial is kept when
+// its action is below N(0), else c = 0 and r = f (the residual of c = 0).
+__global__ void k_seed_select(long long n, const double* __restrict__ Nslot, int tried, LoopState* st,
+                              double2* __restrict__ c, double2* __restrict__ r, const double2* __restrict__ f) {
+  const double Nt = Nslot[0], N0 = Nslot[1];
+  const bool keep = tried && Nt < N0;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    st->N0 = N0;
+    st->N = keep ? Nt : N0;
+    st->cyc = 0;
+  }
+  if (keep || !tried) return;   // without a trial c is already 0 and r = f
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    c[i] = make_double2(0.0, 0.0);
+    r[i] = f[i];
+  }
+}
+void launch_seed_select(long long n, const double* Nslot, int tried, LoopState* st, double2* c, double2* r,
+                        const double2* f, cudaStream_t s) {
+  const long long nb = std::min<long long>((n + 255) / 256, 4096);
+  k_seed_select<<<(int)nb, 256, 0, s>>>(n, Nslot, tried, st, c, r, f);
+}
+
+// The loop's condition (one thread): after a cycle, take its action and count it; continue while the
+// action is finite, fewer than max_cycles have run and (with a tolerance) N > tol N(0).
+__global__ void k_loop_cond(LoopState* st, const double* __restrict__ Nnew, double tol, int max_cycles, int check,
+                            int first, cudaGraphConditionalHandle h) {
+  if (!first) {
+    st->N = Nnew[0];
+    st->cyc += 1;
+  }
+  const double N = st->N;
+  const bool go = isfinite(N) && st->cyc < max_cycles && !(check && N <= tol * st->N0);
+  cudaGraphSetConditional(h, go ? 1u : 0u);
+}
+void launch_loop_cond(LoopState* st, const double* Nnew, double tol, int max_cycles, int check, int first,
+                      cudaGraphConditionalHandle h, cudaStream_t s) {
+  k_loop_cond<<<1, 1, 0, s>>>(st, Nnew, tol, max_cycles, check, first, h);
+}
+
+__global__ void k_loop_record(const LoopState* st, LoopRecord* rec) {
+  rec->N0 = st->N0;
+  rec->N = st->N;
+  rec->cycles = st->cyc;
+  rec->pad = 0;
+}
+void launch_loop_record(const LoopState* st, LoopRecord* rec, cudaStream_t s) { k_loop_record<<<1, 1, 0, s>>>(st, rec); }
+
 // psi(t0+dt)_p = psi0_p + sum_n b_n(+1) c_pn
 __global__ void k_advance(int np, const TimeMats* __restrict__ tm, const double2* __restrict__ c,
                           double2* __restrict__ psi) {

@@ -1604,7 +1604,9 @@ k_gresid_tiles(LevelGeom L, const double* __restrict__ sigma, const TimeMats* __
 // factorised side by side instead of one after another in a single CTA.  (Per context: the
 // batched workload's grids of 512 and more subvolumes, running concurrently, keep the grouping.)
 constexpr int kFactorMultiMin = 512;
-inline int factor_grid_mpc(const LevelGeom& L, int mpc) { return L.nsub >= kFactorMultiMin ? mpc : 1; }
+inline int factor_grid_mpc(const LevelGeom& L, int mpc) {
+  return (L.nsub >= kFactorMultiMin && !L.one_per_cta) ? mpc : 1;
+}
 
 inline size_t factor_smem(const LevelGeom& L, int nptsmax, size_t csize, int mpc_) {
   const size_t ntri = (size_t)L.npad * (L.npad + 1) / 2;

@@ -103,6 +103,13 @@ struct la_ctx {
   cudaStream_t cap = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   double* h_N = nullptr;          // pinned
+  // device-side relaxation loop (la_step_batch): one graph per context whose conditional WHILE node runs
+  // cycles until the device-computed action meets the stopping rule; no host synchronisation per cycle
+  cudaGraphExec_t loop_exec = nullptr;
+  LoopState* d_lstate = nullptr;
+  LoopRecord* d_lrec = nullptr;     // one record per step of the current batch call
+  int lrec_cap = 0;
+  bool device_norm = false;         // action evaluations stay on the device (no read-back)
   // TMA tensor maps of the complex64 fields the finest-level stencils read (mixed precision, 2D/3D)
   CUtensorMap map_e32, map_z32;
   bool have_map_e32 = false, have_map_z32 = false;
@@ -336,6 +343,7 @@ extern "C" la_status la_init(const la_config* cfg, void* stream, la_ctx** out) {
   else if (k.local_form < 0 || k.local_form > 1) bad("local_form must be 0 or 1");
   else if (k.local_form == 1 && k.precision != 0) bad("the square local form runs in FP64 (precision 0)");
   else if (k.local_form == 1 && k.levels != 1) bad("the square local form is single-level (levels 1)");
+  else if (k.factor_group < 0 || k.factor_group > 1) bad("factor_group must be 0 or 1");
   if (st == LA_OK) {
     for (int a = 0; a < 3 && st == LA_OK; ++a) {
       if (a < k.dim) {
@@ -422,6 +430,7 @@ extern "C" la_status la_init(const la_config* cfg, void* stream, la_ctx** out) {
       G.fd_u[a] = make_fastdiv(G.sub[a]);
     }
     G.fd_pair = make_fastdiv(LA_NPAIR * box5_count(k.dim));
+    G.one_per_cta = k.factor_group == 1 ? 1 : 0;
   }
   if (!build_time_constants(c)) {
     g_init_error = "invalid configuration: singular time-basis Gram matrix";
@@ -557,6 +566,8 @@ extern "C" la_status la_finalize(la_ctx* c) {
   if (!c) return LA_EINVAL;
   cudaStreamSynchronize(c->stream);
   for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
+  if (c->cap) cudaStreamSynchronize(c->cap);
+  if (c->loop_exec) cudaGraphExecDestroy(c->loop_exec);
   for (auto& g : c->cg) {
     if (g.exec) cudaGraphExecDestroy(g.exec);
     for (auto& p : g.pairs) { cudaEventDestroy(p.e0); cudaEventDestroy(p.e1); }
@@ -766,10 +777,11 @@ static la_status action_enqueue(la_ctx* c, int slot = 0) {
   const bool timed = prof_begin(c, &e0, &e1);
   launch_mresid<double>(c->fine, c->d_tm, c->K, c->d_f, c->d_c, c->d_r, nullptr, c->d_partials, c->nparts, c->stream);
   if (timed) prof_end(c, e0, e1, 1, resid_bytes(c, sizeof(double2), true));
-  launch_norm_final(c->d_partials, c->nparts, c->nscale, c->d_N, c->stream);
+  launch_norm_final(c->d_partials, c->nparts, c->nscale, c->d_N + slot, c->stream);
   c->launches += 2;
   LA_CHECK_LAUNCH(c);
-  LA_CUDA(c, cudaMemcpyAsync(c->h_N + slot, c->d_N, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  if (!c->device_norm)
+    LA_CUDA(c, cudaMemcpyAsync(c->h_N + slot, c->d_N + slot, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
   return LA_OK;
 }
 // N of the current FP64 iterate; synchronises.
@@ -1199,6 +1211,76 @@ extern "C" la_status la_backward(la_ctx* c, const void* dJ_dpsiT, double* grad_a
   return LA_OK;
 }
 
+// ------------------------------------------------------------------ device-side relaxation loop
+// One graph per context: a kernel sets the loop condition from the starting iterate's action, then a
+// conditional WHILE node repeats { cycle (V-cycle and action norm, on the device only), condition }.
+// Launched once per step on the context's stream, it relaxes to the stopping rule without any host
+// synchronisation; the step's cycles, N and N(0) are recorded on the device.
+static la_status build_loop_graph(la_ctx* c) {
+  if (c->loop_exec) return LA_OK;
+  if (!c->d_lstate) {
+    void* p = nullptr;
+    LA_TRY(dalloc(c, &p, sizeof(LoopState)));
+    c->d_lstate = (LoopState*)p;
+  }
+  const la_config& k = c->cfg;
+  const int check = k.tol > 0 ? 1 : 0;
+  cudaGraph_t g = nullptr;
+  LA_CUDA(c, cudaGraphCreate(&g, 0));
+  cudaGraphConditionalHandle h;
+  cudaError_t e = cudaGraphConditionalHandleCreate(&h, g, 0, 0);
+  cudaStream_t user = c->stream;
+  const long long l0 = c->launches;
+  cudaGraphNode_t head = nullptr, wnode = nullptr;
+  cudaGraph_t out = nullptr;
+  la_status st = LA_OK;
+  if (e == cudaSuccess) e = cudaStreamBeginCaptureToGraph(c->cap, g, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) {
+    launch_loop_cond(c->d_lstate, c->d_N, k.tol, k.max_cycles, check, 1, h, c->cap);
+    e = cudaStreamEndCapture(c->cap, &out);
+  }
+  size_t nn = 1;
+  if (e == cudaSuccess) e = cudaGraphGetNodes(g, &head, &nn);
+  cudaGraphNodeParams cp = {};
+  if (e == cudaSuccess) {
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = h;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    e = cudaGraphAddNode(&wnode, g, &head, nullptr, 1, &cp);
+  }
+  if (e == cudaSuccess) {
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    e = cudaStreamBeginCaptureToGraph(c->cap, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+      // a conditional body holds kernels, memsets and copies only: no profiling events
+      const bool prof = c->prof;
+      c->prof = false;
+      c->stream = c->cap;
+      c->capturing = true;
+      c->device_norm = true;
+      st = cycle_body(c);
+      if (st == LA_OK) launch_loop_cond(c->d_lstate, c->d_N, k.tol, k.max_cycles, check, 0, h, c->cap);
+      cudaError_t ee = cudaStreamEndCapture(c->cap, &out);
+      c->stream = user;
+      c->capturing = false;
+      c->device_norm = false;
+      c->prof = prof;
+      if (e == cudaSuccess) e = ee;
+    }
+  }
+  c->launches = l0;
+  if (st == LA_OK && e == cudaSuccess) e = cudaGraphInstantiate(&c->loop_exec, g, 0);
+  cudaGraphDestroy(g);
+  if (st != LA_OK) return st;
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    c->loop_exec = nullptr;
+    return fail(c, LA_ECUDA, "relaxation loop graph: %s", cudaGetErrorString(e));
+  }
+  return LA_OK;
+}
+
 extern "C" la_status la_step_batch(la_ctx* const* ctxs, int nctx, void* const* psis, int nsteps, const double* t0s,
                                    la_step_stats* stats) {
   if (!ctxs || !psis || !t0s || nctx < 1 || nsteps < 0) return LA_EINVAL;
@@ -1210,11 +1292,21 @@ extern "C" la_status la_step_batch(la_ctx* const* ctxs, int nctx, void* const* p
   }
   std::vector<cudaStream_t> user(nctx);
   std::vector<char> dev(nctx);
-  std::vector<double> N0(nctx), N(nctx);
-  std::vector<int> cyc(nctx), active(nctx);
-  std::vector<char> tried(nctx);
-  la_status worst = LA_OK;
+  la_status st = LA_OK;
   // every context works on its own internal stream for the whole call (forked from its stream)
+  for (int i = 0; i < nctx && st == LA_OK; ++i) {
+    la_ctx* c = ctxs[i];
+    st = build_loop_graph(c);
+    if (st == LA_OK && nsteps > c->lrec_cap) {
+      void* p = nullptr;
+      st = dalloc(c, &p, sizeof(LoopRecord) * (size_t)nsteps);
+      if (st == LA_OK) {
+        c->d_lrec = (LoopRecord*)p;
+        c->lrec_cap = nsteps;
+      }
+    }
+  }
+  if (st != LA_OK) return st;
   for (int i = 0; i < nctx; ++i) {
     la_ctx* c = ctxs[i];
     user[i] = c->stream;
@@ -1226,78 +1318,43 @@ extern "C" la_status la_step_batch(la_ctx* const* ctxs, int nctx, void* const* p
     LA_CUDA(c, cudaMemcpyAsync(c->d_psi, psis[i], sizeof(double2) * (size_t)c->np0,
                                dev[i] ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->stream));
   }
-  la_status st = LA_OK;
+  // Every step of every context is enqueued without waiting: time matrices, factorisation, the starting
+  // iterate (trial or zero, decided on the device), the relaxation loop graph, the step record and the
+  // advance.  The contexts' streams run concurrently; the host synchronises once, at the end.
   for (int s = 0; s < nsteps && st == LA_OK; ++s) {
     for (int i = 0; i < nctx && st == LA_OK; ++i) {
       la_ctx* c = ctxs[i];
       st = setup_step(c, t0s[i] + s * c->cfg.dt);
       if (st == LA_OK) st = c->cfg.precision == 0 ? factor_all<double>(c) : factor_all<float>(c);
-      bool tr = false;
-      if (st == LA_OK) st = seed_enqueue(c, true, &tr);
-      tried[i] = tr;
-    }
-    for (int i = 0; i < nctx && st == LA_OK; ++i) {
-      la_ctx* c = ctxs[i];
-      if (cudaStreamSynchronize(c->stream) != cudaSuccess) st = fail(c, LA_ECUDA, "synchronisation failed");
-      if (st == LA_OK) st = seed_finish(c, tried[i], &N0[i], &N[i]);
-      cyc[i] = 0;
-      active[i] = 1;
-    }
-    // relaxation rounds: one cycle per unconverged context, then one synchronisation per context
-    bool any = true;
-    while (any && st == LA_OK) {
-      any = false;
-      for (int i = 0; i < nctx && st == LA_OK; ++i) {
-        la_ctx* c = ctxs[i];
-        const bool check = c->cfg.tol > 0;
-        if (!active[i]) continue;
-        if ((check && N[i] <= c->cfg.tol * N0[i]) || cyc[i] >= c->cfg.max_cycles || !std::isfinite(N[i])) {
-          active[i] = 0;
-          continue;
-        }
-        st = cycle_issue(c);
-        any = true;
+      bool tried = false;
+      if (st == LA_OK) {
+        c->device_norm = true;
+        st = seed_enqueue(c, true, &tried);
+        c->device_norm = false;
       }
-      for (int i = 0; i < nctx && st == LA_OK; ++i) {
-        if (!active[i]) continue;
-        st = cycle_complete(ctxs[i], &N[i]);
-        ++cyc[i];
+      if (st == LA_OK) {
+        launch_seed_select(c->nunk0, c->d_N, tried ? 1 : 0, c->d_lstate, c->d_c, c->d_r, c->d_f, c->stream);
+        const cudaError_t e = cudaGraphLaunch(c->loop_exec, c->stream);
+        if (e != cudaSuccess) st = fail(c, LA_ECUDA, "relaxation loop launch: %s", cudaGetErrorString(e));
       }
-    }
-    for (int i = 0; i < nctx && st == LA_OK; ++i) {
-      la_ctx* c = ctxs[i];
-      int status = 0;
-      if (cudaMemcpy(&status, c->d_status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess || status) {
-        st = status_error(c, status);
-        break;
+      if (st == LA_OK) {
+        launch_loop_record(c->d_lstate, c->d_lrec + s, c->stream);
+        launch_advance(c->np0, c->d_tm, c->d_c, c->d_psi, c->stream);
+        c->launches += 3;
+        const cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) st = fail(c, LA_ECUDA, "batch step: %s", cudaGetErrorString(e));
       }
-      c->last_N = N[i];
-      c->last_rel = N0[i] > 0 ? N[i] / N0[i] : 0.0;
-      c->have_step = true;
-      if (stats) {
-        la_step_stats& r = stats[(size_t)i * nsteps + s];
-        r.cycles = cyc[i];
-        r.fine_sweeps = cyc[i] * (c->cfg.nu1 + c->cfg.nu2);
-        r.action = N[i];
-        r.rel_action = c->last_rel;
-      }
-      // canary as in la_step: a non-finite action fails the member whatever its tolerance
-      if (!std::isfinite(N[i])) {
-        fail(c, LA_ENOTCONV, "the action is not finite after %d cycles", cyc[i]);
-        worst = LA_ENOTCONV;
-      } else if (c->cfg.tol > 0 && !(N[i] <= c->cfg.tol * N0[i])) {
-        fail(c, LA_ENOTCONV, "not converged after %d cycles (rel %.3e)", cyc[i], c->last_rel);
-        worst = LA_ENOTCONV;
-      }
-      launch_advance(c->np0, c->d_tm, c->d_c, c->d_psi, c->stream);
-      ++c->launches;
-      st = hist_push(c);
+      if (st == LA_OK) st = hist_push(c);
       c->hist_t_next = t0s[i] + (s + 1) * c->cfg.dt;
     }
   }
   // results back, streams restored and joined
+  std::vector<std::vector<LoopRecord>> rec(nctx);
   for (int i = 0; i < nctx; ++i) {
     la_ctx* c = ctxs[i];
+    rec[i].resize((size_t)std::max(nsteps, 1));
+    if (st == LA_OK && nsteps > 0)
+      cudaMemcpyAsync(rec[i].data(), c->d_lrec, sizeof(LoopRecord) * (size_t)nsteps, cudaMemcpyDeviceToHost, c->stream);
     if (st == LA_OK)
       cudaMemcpyAsync(psis[i], c->d_psi, sizeof(double2) * (size_t)c->np0,
                       dev[i] ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->stream);
@@ -1309,7 +1366,38 @@ extern "C" la_status la_step_batch(la_ctx* const* ctxs, int nctx, void* const* p
     if (cudaStreamSynchronize(ctxs[i]->stream) != cudaSuccess && st == LA_OK)
       st = fail(ctxs[i], LA_ECUDA, "synchronisation failed");
   }
-  return st != LA_OK ? st : worst;
+  if (st != LA_OK) return st;
+  la_status worst = LA_OK;
+  for (int i = 0; i < nctx; ++i) {
+    la_ctx* c = ctxs[i];
+    int status = 0;
+    if (cudaMemcpy(&status, c->d_status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess || status) {
+      cudaMemset(c->d_status, 0, sizeof(int));
+      return status_error(c, status);
+    }
+    for (int s = 0; s < nsteps; ++s) {
+      const LoopRecord& r = rec[i][s];
+      c->last_N = r.N;
+      c->last_rel = r.N0 > 0 ? r.N / r.N0 : 0.0;
+      c->have_step = true;
+      if (stats) {
+        la_step_stats& o = stats[(size_t)i * nsteps + s];
+        o.cycles = r.cycles;
+        o.fine_sweeps = r.cycles * (c->cfg.nu1 + c->cfg.nu2);
+        o.action = r.N;
+        o.rel_action = c->last_rel;
+      }
+      // canary as in la_step: a non-finite action fails the member whatever its tolerance
+      if (!std::isfinite(r.N)) {
+        fail(c, LA_ENOTCONV, "the action is not finite after %d cycles (step %d)", r.cycles, s);
+        worst = LA_ENOTCONV;
+      } else if (c->cfg.tol > 0 && !(r.N <= c->cfg.tol * r.N0)) {
+        fail(c, LA_ENOTCONV, "not converged after %d cycles (step %d, rel %.3e)", r.cycles, s, c->last_rel);
+        worst = LA_ENOTCONV;
+      }
+    }
+  }
+  return worst;
 }
 
 extern "C" la_status la_action(la_ctx* c, double* N, double* rel) {

@@ -94,6 +94,7 @@ struct LevelGeom {
   // x and y extents of U + 2 (c box), U + 1 (footprint) and U (1 on unused axes)
   FastDiv fd_K, fd_c[2], fd_f[2], fd_u[2];
   FastDiv fd_pair;   // Galerkin levels: stencil values per point, 9 pairs x the radius-2 box
+  int one_per_cta;   // factorise one subvolume matrix per CTA (no packing of small matrices)
 };
 
 // Finest-level spatial operator: H = -1/2 Laplacian + V0, X = x along laser_axis.
@@ -243,6 +244,26 @@ void launch_c128_to_c64(long long n, const double2* x, float2* y, cudaStream_t s
 void launch_scale_c128(long long n, double a, const double2* x, double2* y, cudaStream_t s);
 void launch_trial(long long n, const double* a, const double2* h0, const double2* h1, const double2* h2, double2* c,
                   cudaStream_t s);
+// device-side relaxation loop of one context (la_step_batch): state and per-step record
+struct LoopState {
+  double N0;   // N(0) = f^dagger W f of the step
+  double N;    // N of the current iterate
+  int cyc;     // cycles run in the step
+  int pad;
+};
+struct LoopRecord {
+  double N0, N;
+  int cycles, pad;
+};
+// keep the trial (c from the extrapolation) when its action Nslot[0] is below N(0) = Nslot[1], else c = 0
+// and r = f; initialises the loop state
+void launch_seed_select(long long n, const double* Nslot, int tried, LoopState* st, double2* c, double2* r,
+                        const double2* f, cudaStream_t s);
+// sets the loop's condition: first = 1 before the first cycle, else after a cycle (N from Nnew[0], cycle
+// counted); continue while N is finite, below max_cycles and (when check) above tol N(0)
+void launch_loop_cond(LoopState* st, const double* Nnew, double tol, int max_cycles, int check, int first,
+                      cudaGraphConditionalHandle h, cudaStream_t s);
+void launch_loop_record(const LoopState* st, LoopRecord* rec, cudaStream_t s);
 // Galerkin coarse stencils
 void launch_galerkin_from_fine(const FineOp& g, const LevelGeom& coarse, double* sigma_c, cudaStream_t s);
 void launch_galerkin_coarse(const LevelGeom& fine, const double* sigma_f, const LevelGeom& coarse, double* sigma_c,

@@ -65,6 +65,7 @@ class Workload:
     trial: int = 0                 # la_step trial iterate: 0 = zero, 1..3 = extrapolation from 1..3 steps
     coarse_nu: Optional[Tuple[int, int]] = None   # (nu1, nu2) on Galerkin levels above the coarsest (None: nu1, nu2)
     local_form: str = "lsq"        # subvolume problem: "lsq" (least squares) | "square" (Dirichlet form, red-black)
+    factor_group: int = 0          # CTA packing of the small-subvolume factorisations: 0 by size, 1 one per CTA
 
     @property
     def shape(self) -> Tuple[int, ...]:

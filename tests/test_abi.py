@@ -52,7 +52,8 @@ def test_init_rejects_invalid_configs_without_touching_the_gpu():
     bad = [dict(dim=4), dict(nt=0), dict(nt=9), dict(dt=0.0), dict(levels=0), dict(max_cycles=0),
            dict(weight=3), dict(precision=2), dict(laser_axis=2), dict(nu1=0, nu2=0), dict(trial=4),
            dict(trial=-1), dict(coarse_cycle=1, coarse_nu1=-1), dict(local_form=2), dict(local_form=-1),
-           dict(local_form=1, precision=1), dict(local_form=1, levels=2), dict(local_form=1, levels=1, nt=8)]
+           dict(local_form=1, precision=1), dict(local_form=1, levels=2), dict(local_form=1, levels=1, nt=8),
+           dict(factor_group=2), dict(factor_group=-1)]
     for kw in bad:
         cfg = B.config_from_workload(w, **kw)
         with pytest.raises(B.LeastActionError) as e:

@@ -19,6 +19,9 @@ def test_every_candidate_passes_validation(monkeypatch, n):
     assert len(cands) >= 20
     shapes = {(c["levels"] > 1, c["nu1"], c["nu2"]) for c in cands}
     assert (True, 1, 2) in shapes and (False, 1, 0) in shapes
+    # K = 4 reaches the 8 x 8 subvolume (256 unknowns); every candidate also with one matrix per CTA
+    assert any(c["sub"][:2] == (8, 8) for c in cands)
+    cands = cands + [dict(c, factor_group=1) for c in cands[:3]]
     for cand in cands:
         cfg = B.config_from_workload(dataclasses.replace(w, **cand))
         with pytest.raises(B.LeastActionError) as e:
@@ -47,6 +50,8 @@ def test_tune_ranks_by_time_among_converged_candidates_and_caches(monkeypatch, t
     def fake_measure(wc, precision):
         i = len(calls)
         calls.append(wc)
+        if wc.factor_group == 1:                    # packing pass: the second of the three is faster still
+            return {"ms_per_step": 9.0 if i == len(cands) + 1 else 100.0, "cycles": 2.0, "rel": w.tol / 2}
         if i == 0:
             raise B.LeastActionError(B.LA_EINVAL, "rejected")
         rel = 1.0 if i == 1 else w.tol / 2          # candidate 1 is the fastest but does not converge
@@ -54,14 +59,15 @@ def test_tune_ranks_by_time_among_converged_candidates_and_caches(monkeypatch, t
 
     monkeypatch.setattr(autotune, "measure", fake_measure)
     best = autotune.tune(w, 0)
-    assert len(calls) == len(cands)
+    assert len(calls) == len(cands) + 3
     times = {i: 10.0 + (i * 7919) % 13 for i in range(2, len(cands))}
-    fastest = min(times, key=lambda i: (times[i], i))
-    assert best == cands[fastest]
+    ranked = sorted(times, key=lambda i: (times[i], i))
+    assert best == dict(cands[ranked[1]], factor_group=1)
+    assert [c.factor_group for c in calls[len(cands):]] == [1, 1, 1]
     monkeypatch.setattr(autotune, "measure", lambda *a: pytest.fail("measured despite the cache"))
     assert autotune.tune(w, 0) == best
     table = __import__("json").load(open(autotune.CACHE))[autotune.key(w, 0)]["table"]
-    assert len(table) == len(cands) - 2
+    assert len(table) == len(cands) - 2 + 3
 
 
 def test_tune_reports_when_nothing_converges(monkeypatch, tmp_path):
