@@ -912,75 +912,6 @@ __device__ __forceinline__ void subvol_solve(const CT* __restrict__ F, CT* rhs, 
   }
 }
 
-// The same solve by one warp with F in shared memory.  Lane (r, h) = (lane % 16, lane / 16) owns
-// row r of a 16-row block and half of the products; the two lanes of a row combine with one
-// shuffle, and __syncwarp orders the steps.  Each half-warp touches 16 different 8-byte bank pairs
-// per load: in the forward pass (rows of L_IJ) lane (r, h) takes columns (2k + h + r) mod 16, in
-// the backward pass (columns of L_JI, conjugated) it takes rows 2k + h of column r.
-template <typename CT, int NPAD>
-__device__ __forceinline__ void subvol_solve_warp(const CT* F, CT* rhs, CT* y, CT* tvec) {
-  constexpr int NB = NPAD / LA_BLK;
-  const int lane = threadIdx.x & 31, r = lane & 15, h = lane >> 4;
-#pragma unroll
-  for (int I = 0; I < NB; ++I) {
-    CT acc = mkc<CT>(0, 0);
-#pragma unroll
-    for (int J = 0; J < I; ++J) {
-      const CT* row = F + (size_t)tri_index(I, J) * 256 + r * LA_BLK;
-      const CT* yy = y + J * LA_BLK;
-#pragma unroll
-      for (int k = 0; k < LA_BLK / 2; ++k) {
-        const int cc = (2 * k + h + r) & (LA_BLK - 1);
-        cfma(acc, row[cc], yy[cc]);
-      }
-    }
-    acc.x += __shfl_xor_sync(0xffffffffu, acc.x, 16);
-    acc.y += __shfl_xor_sync(0xffffffffu, acc.y, 16);
-    if (h == 0) tvec[r] = mkc<CT>(rhs[I * LA_BLK + r].x - acc.x, rhs[I * LA_BLK + r].y - acc.y);
-    __syncwarp();
-    const CT* drow = F + (size_t)tri_index(I, I) * 256 + r * LA_BLK;
-    acc = mkc<CT>(0, 0);
-#pragma unroll
-    for (int k = 0; k < LA_BLK / 2; ++k) {
-      const int cc = (2 * k + h + r) & (LA_BLK - 1);
-      if (cc <= r) cfma(acc, drow[cc], tvec[cc]);
-    }
-    acc.x += __shfl_xor_sync(0xffffffffu, acc.x, 16);
-    acc.y += __shfl_xor_sync(0xffffffffu, acc.y, 16);
-    if (h == 0) y[I * LA_BLK + r] = acc;
-    __syncwarp();
-  }
-#pragma unroll
-  for (int I = NB - 1; I >= 0; --I) {
-    CT acc = mkc<CT>(0, 0);
-#pragma unroll
-    for (int J = I + 1; J < NB; ++J) {
-      const CT* blk = F + (size_t)tri_index(J, I) * 256 + r;
-      const CT* xx = rhs + J * LA_BLK;
-#pragma unroll
-      for (int k = 0; k < LA_BLK / 2; ++k) {
-        const int rr = 2 * k + h;
-        cfma_conj(acc, blk[rr * LA_BLK], xx[rr]);
-      }
-    }
-    acc.x += __shfl_xor_sync(0xffffffffu, acc.x, 16);
-    acc.y += __shfl_xor_sync(0xffffffffu, acc.y, 16);
-    if (h == 0) tvec[r] = mkc<CT>(y[I * LA_BLK + r].x - acc.x, y[I * LA_BLK + r].y - acc.y);
-    __syncwarp();
-    const CT* dcol = F + (size_t)tri_index(I, I) * 256 + r;
-    acc = mkc<CT>(0, 0);
-#pragma unroll
-    for (int k = 0; k < LA_BLK / 2; ++k) {
-      const int rr = 2 * k + h;
-      if (rr >= r) cfma_conj(acc, dcol[rr * LA_BLK], tvec[rr]);
-    }
-    acc.x += __shfl_xor_sync(0xffffffffu, acc.x, 16);
-    acc.y += __shfl_xor_sync(0xffffffffu, acc.y, 16);
-    if (h == 0) rhs[I * LA_BLK + r] = acc;
-    __syncwarp();
-  }
-}
-
 // Triangular solves with a wide factor (more than eight block rows) by all 128 threads of the
 // sweep's CTA: every load of a step (one block row forward, one block column backward) is issued
 // together, and in complex64 the next step's blocks are loaded while the current step computes, so
@@ -1116,50 +1047,16 @@ __device__ __forceinline__ void subvol_solve_wide(const CT* __restrict__ F, CT* 
   }
 }
 
-// complex64 finest-level sweeps with long factors (three or more block rows, up to 48 KB) copy the
-// subvolume's factor into shared memory with one bulk copy issued when the CTA starts: the copy
-// overlaps the residual stages and the 2 NB dependent steps of the triangular solves read no
-// global memory.  Shorter factors keep the two-warp solve from global memory, where the extra
-// shared memory would cost more resident CTAs than the short solve chain loses; FP64 sweeps are
-// bound by the FP64 pipe.
+// Bytes of one subvolume factor record (packed lower-triangular 16 x 16 blocks).
 __host__ __device__ constexpr size_t factor_bytes(int npad, size_t csize) {
   return (size_t)(npad / LA_BLK) * (npad / LA_BLK + 1) / 2 * 256 * csize;
 }
+// The 128-thread solve (every step's blocks loaded together, the next step's in flight) serves every
+// complex64 factor and the wide FP64 ones; shorter FP64 factors keep the two-warp solve, whose
+// two-level reductions issue fewer adds on the slow FP64 pipe.
 template <typename R, int NPAD>
-__host__ __device__ constexpr bool stage_factor() {
-  return sizeof(R) == 4 && NPAD >= 48 && factor_bytes(NPAD, 2 * sizeof(R)) <= 48 * 1024;
-}
-// The staging area follows `base` bytes of a sweep's other shared arrays: the mbarrier and a
-// failure flag (128 bytes, 128-aligned), then the factor.
-__host__ __device__ constexpr size_t stage_offset(size_t base) { return (base + 127) & ~(size_t)127; }
-
-// Starts the bulk copy of one factor into the staging area (thread 0 only).
-template <typename CT>
-__device__ __forceinline__ void stage_begin(unsigned char* area, const CT* src, unsigned bytes) {
-  unsigned long long* bar = reinterpret_cast<unsigned long long*>(area);
-  if (threadIdx.x == 0) {
-    mbar_init(bar, 1);
-    mbar_init_fence();
-    *reinterpret_cast<int*>(area + 8) = 0;
-    bulk_load(area + 128, src, bytes, bar);
-  }
-}
-// Warp 0 waits (bounded) for the staged factor and solves from shared memory; on a timeout it
-// records status flag 4 and raises the CTA's failure flag instead.  The caller synchronises the
-// CTA afterwards and skips its update when the flag is set.
-template <typename CT, int NPAD>
-__device__ __forceinline__ void staged_solve(unsigned char* area, CT* rhs, CT* y, CT* tvec, int* status) {
-  if (threadIdx.x >= 32) return;
-  unsigned long long* bar = reinterpret_cast<unsigned long long*>(area);
-  bool ok = mbar_wait(bar, 0, kMbarWaitLimit);
-  // a lane that gave up while another saw the phase complete polls again (it completes at once)
-  if (!ok && __any_sync(0xffffffffu, ok)) ok = mbar_wait(bar, 0, kMbarWaitLimit);
-  if (__all_sync(0xffffffffu, ok)) {
-    subvol_solve_warp<CT, NPAD>(reinterpret_cast<const CT*>(area + 128), rhs, y, tvec);
-  } else if (threadIdx.x == 0) {
-    if (status) atomicOr(status, 4);
-    *reinterpret_cast<int*>(area + 8) = 1;
-  }
+__host__ __device__ constexpr bool use_wide_solve() {
+  return sizeof(R) == 4 || NPAD > LA_NPAD_MAX;
 }
 
 // ======================================================================== finest-level sweep
@@ -1171,8 +1068,8 @@ k_sweep_fine(LevelGeom L, FineOp g, const TimeMats* __restrict__ tm, const typen
              const typename C2<R>::T* __restrict__ yx, typename C2<R>::T* __restrict__ c,
              const typename C2<R>::T* __restrict__ factors, int colour, int* __restrict__ status) {
   typedef typename C2<R>::T CT;
-  constexpr bool kStage = stage_factor<R, NPAD>();
   extern __shared__ __align__(16) unsigned char smem[];
+  (void)status;   // no bounded wait in this kernel
   const int K = tm->K, KK = K * K;
   const int tid = threadIdx.x;
   const int b = colour_subvol(L, colour, blockIdx.x);
@@ -1219,8 +1116,6 @@ k_sweep_fine(LevelGeom L, FineOp g, const TimeMats* __restrict__ tm, const typen
   CT* sY = sRhs + NPAD;                               // [NPAD]
   CT* sT = sY + NPAD;                                 // [16]
   CT* sRed = sT + LA_BLK;                             // [128]
-  unsigned char* sStage = smem + stage_offset(reinterpret_cast<unsigned char*>(sRed + 128) - smem);
-  if (kStage) stage_begin(sStage, factors + (size_t)b * L.fsize, (unsigned)factor_bytes(NPAD, sizeof(CT)));
 
   for (int i = tid; i < KK; i += kSweepThreads) {
     sQ[i] = (R)tm->Qb[i]; sU[i] = (R)tm->Ub[i]; sW[i] = (R)tm->Wt[i]; sE[i] = (R)tm->Eb[i];
@@ -1373,14 +1268,11 @@ k_sweep_fine(LevelGeom L, FineOp g, const TimeMats* __restrict__ tm, const typen
     sRhs[t] = out;
   }
   __syncthreads();
-  if (kStage)
-    staged_solve<CT, NPAD>(sStage, sRhs, sY, sT, status);
-  else if (NPAD > LA_NPAD_MAX)
+  if (use_wide_solve<R, NPAD>())
     subvol_solve_wide<CT, NPAD>(factors + (size_t)b * L.fsize, sRhs, sY, sT, sRed);
   else
     subvol_solve<CT, NPAD>(factors + (size_t)b * L.fsize, sRhs, sY, sT, sRed);
   __syncthreads();
-  if (kStage && *reinterpret_cast<volatile int*>(sStage + 8)) return;
   for (int t = tid; t < npts * K; t += kSweepThreads) {
     int i, m;
     item(t, i, m);
@@ -1708,11 +1600,7 @@ cudaError_t launch_sweep_fine_n(const LevelGeom& L, const FineOp& g, const TimeM
                                 const typename C2<R>::T* factors, int colour, int* status, cudaStream_t s) {
   const int nblocks = colour_count(L, colour);
   if (nblocks == 0) return cudaSuccess;
-  size_t smem = sweep_fine_smem(L, K, sizeof(R), sizeof(typename C2<R>::T));
-  if (stage_factor<R, NPAD>()) {
-    if (reinterpret_cast<uintptr_t>(factors) & 15) return cudaErrorMisalignedAddress;
-    smem = stage_offset(smem) + 128 + factor_bytes(NPAD, sizeof(typename C2<R>::T));
-  }
+  const size_t smem = sweep_fine_smem(L, K, sizeof(R), sizeof(typename C2<R>::T));
   auto kern = k_sweep_fine<R, NPAD>;
   static bool attr_set = false;
   if (!attr_set) {
