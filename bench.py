@@ -312,6 +312,22 @@ def stencil_roofline(prof, precision, c64=False):
                      "algorithmic bytes: f, c, V0 in and z out per point")}
 
 
+def transfer_roofline(prof):
+    """The finest-level transfers (Sec. III: restriction of the normal residual to level 1, prolongation
+    of level 1's correction added to the finest one) against HBM: algorithmic bytes / event time."""
+    if not prof.get("n_restrict"):
+        return None
+    peak, note = hbm_peak()
+    out = {"bound": "hbm", "peak": peak, "unit": "GB/s", "peak_note": note}
+    for name, n, ms, by in (("restrict", "n_restrict", "ms_restrict", "bytes_restrict"),
+                            ("prolong_add", "n_prolong", "ms_prolong", "bytes_prolong")):
+        if prof.get(n):
+            gbs = prof[by] / (prof[ms] * 1e-3) / 1e9
+            out[name] = {"kernel": f"k_{name}", "achieved": round(gbs, 1), "frac": round(gbs / peak, 4),
+                         "launches": prof[n], "us_per_launch": round(1e3 * prof[ms] / prof[n], 2)}
+    return out
+
+
 def make_context(B, torch, w, precision, **overrides):
     ctx = B.Context(B.config_from_workload(w, precision=precision, **overrides))
     ctx.set_hamiltonian(torch.tensor(wl.potential(w).ravel(), dtype=torch.float64, device="cuda"), w.pulse)
@@ -540,7 +556,8 @@ def run_ours(args):
                    "d2h_bytes_per_step": 16 * w.npoints, "steps": e2e_steps},
            "gpu_launches": int(prof["launches"]), "roofline": roofline,
            "stencil_roofline": stencil_roofline(prof, precision),
-           "stencil_roofline_c64": stencil_roofline(prof, precision, c64=True), "clocks": clk,
+           "stencil_roofline_c64": stencil_roofline(prof, precision, c64=True),
+           "transfer_roofline": transfer_roofline(prof), "clocks": clk,
            "peaks": {"fp64_tflops": round(peaks[0], 4), "fp32_tflops": round(peaks[1], 3), "sm_count": peaks[2],
                      "how": "la_fma_peaks: 8 independent FMA chains per thread, one full wave of 256-thread CTAs on every SM, "
                             "CUDA events, in this run"}}

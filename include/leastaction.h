@@ -199,8 +199,9 @@ la_status la_time_matrices(la_ctx* ctx, double t0, double* out);
 
 /* Kernel timing for roofline reporting.  While enabled, the library records CUDA events on its
    stream around every finest-level factorisation launch, every finest-level sweep (the launches of
-   all colours together) and every finest-level action-residual stencil launch (S1: r = f - M c,
-   inside the V-cycle and for the action norm), and counts all of its kernel launches.  Algorithmic flops: factorisation
+   all colours together), every finest-level action-residual stencil launch (S1: r = f - M c,
+   inside the V-cycle and for the action norm) and every finest-level restriction and prolongation,
+   and counts all of its kernel launches.  Algorithmic flops: factorisation
    (4/3) n^3 per subvolume (complex Cholesky of the n = |U| K unknowns); sweep 8 n^2 per subvolume
    (the two triangular solves; the residual stencil is not counted).  Algorithmic bytes of the
    residual stencil: c in, r out, f in where present (K complex each per point) and V0 in. */
@@ -218,6 +219,12 @@ typedef struct {
   int n_resid32;          /* the same for the complex64 residual stencil (mixed-precision V-cycle) */
   double ms_resid32;
   double bytes_resid32;
+  int n_restrict;         /* finest-level restriction launches (Sec. III, residual to level 1) */
+  double ms_restrict;
+  double bytes_restrict;  /* algorithmic bytes: the fine normal residual in, level 1's right-hand side out */
+  int n_prolong;          /* level 1 -> finest prolongation-and-correction launches (Eq. correction_fine) */
+  double ms_prolong;
+  double bytes_prolong;   /* algorithmic bytes: level 1's correction in, the fine correction read and written */
 } la_profile;
 /* enable != 0 resets the counters and starts recording; 0 stops.  Errors: LA_EINVAL. */
 la_status la_profile_enable(la_ctx* ctx, int enable);

@@ -57,7 +57,9 @@ class la_profile(C.Structure):
                 ("flops_factor", C.c_double), ("n_sweep", C.c_int), ("ms_sweep", C.c_double),
                 ("flops_sweep", C.c_double), ("n_resid", C.c_int), ("ms_resid", C.c_double),
                 ("bytes_resid", C.c_double), ("n_resid32", C.c_int), ("ms_resid32", C.c_double),
-                ("bytes_resid32", C.c_double)]
+                ("bytes_resid32", C.c_double), ("n_restrict", C.c_int), ("ms_restrict", C.c_double),
+                ("bytes_restrict", C.c_double), ("n_prolong", C.c_int), ("ms_prolong", C.c_double),
+                ("bytes_prolong", C.c_double)]
 
 
 _lib = None

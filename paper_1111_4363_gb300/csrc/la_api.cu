@@ -86,7 +86,8 @@ struct la_ctx {
   std::vector<ProfPair> ev_kern;
   size_t ev_next = 0;
   double ms_factor = 0.0, ms_sweep = 0.0, ms_resid = 0.0, bytes_resid = 0.0, ms_resid32 = 0.0, bytes_resid32 = 0.0;
-  int n_factor = 0, n_sweep = 0, n_resid = 0, n_resid32 = 0;
+  double ms_restrict = 0.0, bytes_restrict = 0.0, ms_prolong = 0.0, bytes_prolong = 0.0;
+  int n_factor = 0, n_sweep = 0, n_resid = 0, n_resid32 = 0, n_restrict = 0, n_prolong = 0;
   double flops_factor = 0.0, flops_sweep = 0.0;
   // one captured cycle (V-cycle + action norm + read-back), replayed on an internal stream
   struct CycleGraph {
@@ -129,7 +130,9 @@ static void prof_add(la_ctx* c, const la_ctx::ProfPair& p) {
   if (cudaEventElapsedTime(&ms, p.e0, p.e1) != cudaSuccess) return;
   if (p.kind == 0) { c->ms_sweep += ms; ++c->n_sweep; }
   else if (p.kind == 1) { c->ms_resid += ms; ++c->n_resid; c->bytes_resid += p.bytes; }
-  else { c->ms_resid32 += ms; ++c->n_resid32; c->bytes_resid32 += p.bytes; }
+  else if (p.kind == 2) { c->ms_resid32 += ms; ++c->n_resid32; c->bytes_resid32 += p.bytes; }
+  else if (p.kind == 3) { c->ms_restrict += ms; ++c->n_restrict; c->bytes_restrict += p.bytes; }
+  else { c->ms_prolong += ms; ++c->n_prolong; c->bytes_prolong += p.bytes; }
 }
 // Drain recorded event pairs into the totals (synchronises).
 static void prof_drain(la_ctx* c) {
@@ -536,7 +539,8 @@ extern "C" la_status la_profile_enable(la_ctx* c, int enable) {
   if (c->prof) {
     c->launches = 0;
     c->ms_factor = c->ms_sweep = c->ms_resid = c->bytes_resid = c->ms_resid32 = c->bytes_resid32 = 0.0;
-    c->n_factor = c->n_sweep = c->n_resid = c->n_resid32 = 0;
+    c->ms_restrict = c->bytes_restrict = c->ms_prolong = c->bytes_prolong = 0.0;
+    c->n_factor = c->n_sweep = c->n_resid = c->n_resid32 = c->n_restrict = c->n_prolong = 0;
     finest_flops(c);
   }
   return LA_OK;
@@ -559,6 +563,12 @@ extern "C" la_status la_profile_read(la_ctx* c, la_profile* out) {
   out->n_resid32 = c->n_resid32;
   out->ms_resid32 = c->ms_resid32;
   out->bytes_resid32 = c->bytes_resid32;
+  out->n_restrict = c->n_restrict;
+  out->ms_restrict = c->ms_restrict;
+  out->bytes_restrict = c->bytes_restrict;
+  out->n_prolong = c->n_prolong;
+  out->ms_prolong = c->ms_prolong;
+  out->bytes_prolong = c->bytes_prolong;
   return LA_OK;
 }
 
@@ -759,13 +769,27 @@ static la_status vcycle(la_ctx* c, int l) {
     ++c->launches;
     sfine = (CT*)c->d_sl[l];
   }
-  launch_restrict<R>(c->geo[l], c->geo[l + 1], c->K, sfine, (CT*)c->d_g[l + 1], c->stream);
+  {
+    // finest-level transfer timed for the roofline: s (fine) in, g (level 1) out
+    cudaEvent_t e0, e1;
+    const bool timed = l == 0 && prof_begin(c, &e0, &e1);
+    launch_restrict<R>(c->geo[l], c->geo[l + 1], c->K, sfine, (CT*)c->d_g[l + 1], c->stream);
+    if (timed)
+      prof_end(c, e0, e1, 3, (double)sizeof(CT) * c->K * ((double)c->geo[0].np + (double)c->geo[1].np));
+  }
   ++c->launches;
   LA_CHECK_LAUNCH(c);
   LA_CUDA(c, cudaMemsetAsync(c->d_e[l + 1], 0, sizeof(CT) * (size_t)c->geo[l + 1].np * c->K, c->stream));
   LA_TRY(vcycle<R>(c, l + 1));
   CT* efine = l == 0 ? Fine<R>::e(c) : (CT*)c->d_e[l];
-  launch_prolong_add<R>(c->geo[l], c->geo[l + 1], c->K, (const CT*)c->d_e[l + 1], efine, c->stream);
+  {
+    // e (level 1) in, the fine correction read and written
+    cudaEvent_t e0, e1;
+    const bool timed = l == 0 && prof_begin(c, &e0, &e1);
+    launch_prolong_add<R>(c->geo[l], c->geo[l + 1], c->K, (const CT*)c->d_e[l + 1], efine, c->stream);
+    if (timed)
+      prof_end(c, e0, e1, 4, (double)sizeof(CT) * c->K * (2.0 * c->geo[0].np + (double)c->geo[1].np));
+  }
   ++c->launches;
   LA_CHECK_LAUNCH(c);
   return sweep_level<R>(c, l, nu2);

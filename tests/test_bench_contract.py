@@ -119,3 +119,14 @@ def test_wide_factor_roofline_against_the_measured_peak(bench):
     assert r["kernel"].startswith("k_factor_wide") and r["bound"] == "alu"
     assert r["peak"] == pytest.approx(75.0) and "measured" in r["peak_note"] and "152 SMs" in r["peak_note"]
     assert r["frac"] == pytest.approx(4.0e9 / 5e-3 / 1e12 / 75.0, abs=1e-4)
+
+
+def test_transfer_roofline_is_bytes_over_event_time(bench):
+    p = fake_profile(n_restrict=4, ms_restrict=0.2, bytes_restrict=6.0e8, n_prolong=4, ms_prolong=0.4,
+                     bytes_prolong=1.0e9)
+    t = bench.transfer_roofline(p)
+    peak, _ = bench.hbm_peak()
+    assert t["bound"] == "hbm" and t["peak"] == peak
+    assert t["restrict"]["achieved"] == pytest.approx(6.0e8 / 0.2e-3 / 1e9, rel=1e-3)
+    assert t["prolong_add"]["us_per_launch"] == pytest.approx(100.0)
+    assert bench.transfer_roofline(fake_profile(n_restrict=0)) is None
