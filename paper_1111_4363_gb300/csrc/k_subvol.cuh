@@ -590,14 +590,18 @@ __device__ __forceinline__ CPair<double2> lds_pair(const double2* p) {
 }
 
 // Shared-memory layout of the wide factorisation (bytes), for the padded size npad.
-// Rows of the two shared-memory panels are padded so that the transposed stores of the block row and the
-// column-wise accesses of the diagonal block spread over the banks: 17 entries for the block column,
-// 18 for the block row (whose rows the update reads as 16-byte pairs, so they start 16-byte aligned).
+// The block column's rows are padded to 17 entries so that the diagonal block's column-wise accesses
+// spread over the banks.  The transposed block row keeps rows of 16 entries, read as 16-byte pairs whose
+// position in a row is XOR-swizzled by the row index (pair p of row k at p ^ (k mod 8)), so that its
+// transposed stores spread over the banks too.
 constexpr int kWideStride = LA_BLK + 1;
-constexpr int kRowStride = LA_BLK + 2;
+__host__ __device__ __forceinline__ int wide_row_idx(int k, int c) {
+  return k * LA_BLK + ((((c >> 1) ^ (k & 7))) << 1) + (c & 1);
+}
 __host__ __device__ constexpr size_t wide_factor_smem(int npad, size_t csize, size_t rsize) {
-  return csize * ((size_t)(npad - LA_BLK) * kRowStride     // block row J, transposed [k][c]
-                  + (size_t)npad * kWideStride             // the block column's rows 16 J .. npad-1
+  return csize * ((size_t)(npad - LA_BLK) * LA_BLK         // block row J+1, transposed (then the block (J+1, J))
+                  + (size_t)npad * kWideStride             // the block column's rows at their absolute index
+                  + LA_BLK * kWideStride                   // inv(L_JJ) being built
                   + 256)                                   // inv(L_JJ)^dagger, [k][c]
          + rsize * (LA_NPAIR * LA_KMAX * LA_KMAX + 3 * kWidePtsMax + LA_BLK) + sizeof(int) * kWidePtsMax;
 }
@@ -657,33 +661,36 @@ __device__ __forceinline__ typename C2<R>::T wide_entry(int r, int c, int n, con
 // Block column J, rows 16 J + row of this thread (columns c0 .. c0 + CPT - 1): assemble, subtract
 // sum_{k < 16 J} L[r][k] conj(L[16 J + c][k]) (row r of the finished blocks (I, 0..J-1) from global
 // memory, the block row J transposed in shared memory), and write the result to sPan.
+// Rows 16 J' + q of block column J' assembled and updated with the finished block columns Kb < kb_end:
+// acc[c] = G[r][16 J' + c0 + c] - sum_{k < 16 kb_end} L[r][k] conj(L[16 J' + c0 + c][k]), the finished rows
+// read back from the factor store, the block row J' transposed in sRow.
 template <typename R, int CPT>
-__device__ __forceinline__ void wide_column_update(int J, int row, int c0, int n, const FastDiv& dK, int K,
-                                                   const typename C2<R>::T* __restrict__ F, const R* sP, const R* sD,
-                                                   const R* sX, const R* sN, const int* sXYZ, R wx, R wy, R wz,
-                                                   const typename C2<R>::T* sRow, typename C2<R>::T* sPan) {
+__device__ __forceinline__ void wide_partial_update(int Jc, int kb_end, int r, int c0, int n, const FastDiv& dK, int K,
+                                                    const typename C2<R>::T* __restrict__ F, const R* sP, const R* sD,
+                                                    const R* sX, const R* sN, const int* sXYZ, R wx, R wy, R wz,
+                                                    const typename C2<R>::T* sRow, typename C2<R>::T* acc) {
   typedef typename C2<R>::T CT;
-  const int r = LA_BLK * J + row, I = r >> 4;
-  CT acc[CPT];
+  const int I = r >> 4;
 #pragma unroll
-  for (int q = 0; q < CPT; ++q) acc[q] = wide_entry<R>(r, LA_BLK * J + c0 + q, n, dK, sP, K, sD, sX, sN, sXYZ, wx, wy, wz);
-  for (int Kb = 0; Kb < J; ++Kb) {
-    const CT* src = F + (size_t)tri_index(I, Kb) * 256 + (r & 15) * LA_BLK;
-    CT v[LA_BLK];
+  for (int q = 0; q < CPT; ++q) acc[q] = wide_entry<R>(r, LA_BLK * Jc + c0 + q, n, dK, sP, K, sD, sX, sN, sXYZ, wx, wy, wz);
+  for (int h = 0; h < 2 * kb_end; ++h) {   // half a finished block row (8 columns k) at a time
+    const int Kb = h >> 1, k0 = (h & 1) * (LA_BLK / 2);
+    const CT* src = F + (size_t)tri_index(I, Kb) * 256 + (r & 15) * LA_BLK + k0;
+    CT v[LA_BLK / 2];
 #pragma unroll
-    for (int kk = 0; kk < LA_BLK; ++kk) v[kk] = src[kk];
-    const CT* rowk = sRow + (size_t)Kb * LA_BLK * kRowStride + c0;
+    for (int kk = 0; kk < LA_BLK / 2; ++kk) v[kk] = src[kk];
+    const CT* rowk = sRow + (size_t)Kb * LA_BLK * LA_BLK + k0 * LA_BLK;
 #pragma unroll
-    for (int kk = 0; kk < LA_BLK; ++kk) {
+    for (int kk = 0; kk < LA_BLK / 2; ++kk) {
 #pragma unroll
       for (int q = 0; q < CPT; q += (CPT > 1 ? 2 : 1)) {
         CT y[2];
         if (CPT > 1) {
-          const CPair<CT> yp = lds_pair(rowk + kk * kRowStride + q);
+          const CPair<CT> yp = lds_pair(rowk + wide_row_idx(kk, c0 + q));
           y[0] = yp.a();
           y[1] = yp.b();
         } else {
-          y[0] = rowk[kk * kRowStride + q];
+          y[0] = rowk[wide_row_idx(kk, c0 + q)];
         }
 #pragma unroll
         for (int u = 0; u < (CPT > 1 ? 2 : 1); ++u) {
@@ -694,26 +701,188 @@ __device__ __forceinline__ void wide_column_update(int J, int row, int c0, int n
       }
     }
   }
+}
+
+// Shared state of the wide factorisation.
+template <typename R>
+struct WideSmem {
+  typedef typename C2<R>::T CT;
+  CT* sRow;   // [NPAD-16][16]: block row J' transposed, sRow[wide_row_idx(k, c)] = L[16 J' + c][k]
+  CT* sPan;   // [NPAD][17]: rows of the current block column at their absolute row index
+  CT* sBT;    // [16][17]: sBT[k][c] = L[16 (J+1) + c][16 J + k] (the block (J+1, J)); in sRow's space
+  CT* sInvT;  // [16][16]: sInvT[k][c] = conj(inv(L_JJ)[c][k])
+  CT* sXi;    // [16][17]: inv(L_JJ) being built
+  R *sP, *sD, *sX, *sN, *sPiv;
+  int* sXYZ;
+};
+
+// Cholesky of the diagonal block of column J (rows 16 J .. 16 J + 15 of sPan) and its inverse in one
+// sweep of 16 steps, by one warp.  Lane (i, h) = (lane % 16, lane / 16) updates row i's trailing entries of
+// one column parity h and keeps the entries of parity h of row i of X = inv(L_JJ) in registers: X starts
+// as the identity, and step j divides row j by L[j][j] and subtracts L[i][j] times it from the rows i > j
+// (row j of X is final after step j), so the inverse costs no second chain of dependent steps.
+template <typename R>
+__device__ __forceinline__ void wide_diag(int J, const WideSmem<R>& S, typename C2<R>::T* F, int* status) {
+  typedef typename C2<R>::T CT;
+  const int lane = threadIdx.x & 31, ri = lane & 15, half = lane >> 4;
+  CT* D = S.sPan + (size_t)LA_BLK * J * kWideStride;   // the diagonal block's rows
+  CT x[LA_BLK / 2];                                     // X[ri][2 u + half]
 #pragma unroll
-  for (int q = 0; q < CPT; ++q) sPan[row * kWideStride + c0 + q] = acc[q];
+  for (int u = 0; u < LA_BLK / 2; ++u) x[u] = mkc<CT>((R)(2 * u + half == ri ? 1 : 0), (R)0);
+  for (int j = 0; j < LA_BLK; ++j) {
+    R d2 = D[j * kWideStride + j].x;
+    if (!(d2 > (R)0)) {
+      if (lane == 0) atomicOr(status, 1);
+      d2 = (R)1;
+    }
+    const R inv = rsq(d2);
+    CT lij = mkc<CT>(0, 0);
+    if (ri > j) {
+      const CT v = D[ri * kWideStride + j];
+      lij = mkc<CT>(v.x * inv, v.y * inv);
+    }
+    __syncwarp();
+    if (ri > j && half == 0) D[ri * kWideStride + j] = lij;
+    if (lane == j) D[j * kWideStride + j] = mkc<CT>(d2 * inv, (R)0);
+    // X: row j /= L[j][j] (its lanes), then rows i > j -= L[i][j] X[j]; X[j][c] comes from lane (j, h)
+#pragma unroll
+    for (int u = 0; u < LA_BLK / 2; ++u) {
+      if (ri == j) x[u] = mkc<CT>(x[u].x * inv, x[u].y * inv);
+      CT xj;
+      xj.x = __shfl_sync(0xffffffffu, x[u].x, j + 16 * half);
+      xj.y = __shfl_sync(0xffffffffu, x[u].y, j + 16 * half);
+      if (ri > j) {   // x -= L[i][j] X[j]
+        x[u].x -= lij.x * xj.x - lij.y * xj.y;
+        x[u].y -= lij.x * xj.y + lij.y * xj.x;
+      }
+    }
+    __syncwarp();
+    // trailing entries (i, k), j < k <= i: A[i][k] -= L[i][j] conj(L[k][j])
+    if (ri > j) {
+      for (int k = j + 1 + half; k <= ri; k += 2) {
+        const CT lk = D[k * kWideStride + j];
+        CT v = D[ri * kWideStride + k];
+        v.x -= lij.x * lk.x + lij.y * lk.y;
+        v.y -= lij.y * lk.x - lij.x * lk.y;
+        D[ri * kWideStride + k] = v;
+      }
+    }
+    __syncwarp();
+  }
+  // the inverse as the stored diagonal block (row ri, columns 2 u + half), and sInvT[k][c] = conj(X[c][k])
+#pragma unroll
+  for (int u = 0; u < LA_BLK / 2; ++u) {
+    const int c = 2 * u + half;
+    if (lane < 32) {
+      F[(size_t)tri_index(J, J) * 256 + ri * LA_BLK + c] = x[u];
+      S.sInvT[c * LA_BLK + ri] = mkc<CT>(x[u].x, -x[u].y);
+    }
+  }
+}
+
+// Named barrier of warps 1..7 (the lookahead update's threads).
+__device__ __forceinline__ void wide_bar() { asm volatile("bar.sync 1, 224;" ::: "memory"); }
+
+// One block column J with lookahead: warp 0 factorises J's diagonal block while warps 1..7 assemble block
+// column J+1 and update it with the finished block columns 0..J-1; then all threads divide J's rows below
+// by L_JJ, and warps 1..7 add block column J's contribution to J+1 from shared memory.
+template <typename R, int NPAD, int CPT>
+__device__ __forceinline__ void wide_column_step(int J, int n, const FastDiv& dK, int K, typename C2<R>::T* F,
+                                                 const WideSmem<R>& S, R wx, R wy, R wz, int* status) {
+  typedef typename C2<R>::T CT;
+  constexpr int NB = NPAD / LA_BLK;
+  constexpr int TPR = LA_BLK / CPT;
+  const int tid = threadIdx.x;
+  const bool next = J + 1 < NB;
+  const int RJ1 = NPAD - LA_BLK * (J + 1);            // rows of block column J+1
+  // warps 1..7 own rows q' = t' / TPR of block column J+1 (t' = tid - 32); rows beyond 224 / TPR
+  // (block column 1 of a 256-unknown matrix has 240) fall to warp 0 after its diagonal work
+  const int tl = tid - 32;
+  const int q_own = tid >= 32 ? tl / TPR : 224 / TPR + (tid & 31);
+  const int c0 = tid >= 32 ? (tl % TPR) * CPT : 0;
+  const bool own = next && q_own < RJ1 && (tid >= 32 || (TPR == 1 && (tid & 31) < LA_BLK));
+  const int r_own = LA_BLK * (J + 1) + q_own;
+  CT acc[CPT];
+  if (tid < 32) {
+    wide_diag<R>(J, S, F, status);
+  } else if (next) {
+    // block row J+1's finished blocks (J+1, Kb < J), transposed
+    for (int t = tl; t < J * 256; t += 224) {
+      const int Kb = t >> 8, w = t & 255, c = w >> 4, kk = w & 15;
+      S.sRow[wide_row_idx(Kb * LA_BLK + kk, c)] = F[(size_t)tri_index(J + 1, Kb) * 256 + w];
+    }
+    wide_bar();
+    if (own)
+      wide_partial_update<R, CPT>(J + 1, J, r_own, c0, n, dK, K, F, S.sP, S.sD, S.sX, S.sN, S.sXYZ, wx, wy, wz, S.sRow,
+                                  acc);
+  }
+  __syncthreads();
+  if (tid < 32 && own)   // warp 0's rows of block column 1 (no finished column before it)
+    wide_partial_update<R, CPT>(J + 1, 0, r_own, c0, n, dK, K, F, S.sP, S.sD, S.sX, S.sN, S.sXYZ, wx, wy, wz, S.sRow,
+                                acc);
+  // rows below the diagonal block: L[r][c] = sum_{k <= c} A[r][k] conj(inv(L_JJ)[c][k]), one entry per
+  // thread; the 16 entries of a row are in one warp, which reads them all before writing them back
+  const int RJ = NPAD - LA_BLK * J;
+  const int total = (RJ - LA_BLK) * LA_BLK;
+  const int iters = (total + kFactorThreads - 1) / kFactorThreads;
+  for (int m = 0; m < iters; ++m) {
+    const int e = tid + m * kFactorThreads;
+    const bool act = e < total;
+    const int rr = LA_BLK * (J + 1) + (act ? e >> 4 : 0), c = e & 15;
+    CT s = mkc<CT>(0, 0);
+    if (act) {
+      const CT* a = S.sPan + (size_t)rr * kWideStride;
+#pragma unroll
+      for (int k = 0; k < LA_BLK; ++k)
+        if (k <= c) cfma(s, a[k], S.sInvT[k * LA_BLK + c]);
+      F[(size_t)tri_index(rr >> 4, J) * 256 + (rr & 15) * LA_BLK + c] = s;
+      if ((rr >> 4) == J + 1) S.sBT[c * kWideStride + (rr & 15)] = s;
+    }
+    __syncwarp();
+    if (act) S.sPan[(size_t)rr * kWideStride + c] = s;
+  }
+  __syncthreads();
+  if (own) {
+    // block column J's contribution: acc[c] -= sum_k L[r][16 J + k] conj(L[16 (J+1) + c][16 J + k])
+    const CT* a = S.sPan + (size_t)r_own * kWideStride;
+#pragma unroll
+    for (int k = 0; k < LA_BLK; ++k) {
+      const CT lr = a[k];
+#pragma unroll
+      for (int q = 0; q < CPT; ++q) {
+        const CT y = S.sBT[k * kWideStride + c0 + q];
+        acc[q].x = fma(-lr.x, y.x, acc[q].x); acc[q].x = fma(-lr.y, y.y, acc[q].x);
+        acc[q].y = fma(-lr.y, y.x, acc[q].y); acc[q].y = fma(lr.x, y.y, acc[q].y);
+      }
+    }
+  }
+  __syncwarp();
+  if (own) {
+#pragma unroll
+    for (int q = 0; q < CPT; ++q) S.sPan[(size_t)r_own * kWideStride + c0 + q] = acc[q];
+  }
+  __syncthreads();
 }
 
 template <typename R, int NPAD>
-__global__ void __launch_bounds__(kFactorThreads, sizeof(R) == 4 ? 3 : 1)
+__global__ void __launch_bounds__(kFactorThreads, sizeof(R) == 4 ? 2 : 1)
 k_factor_wide(LevelGeom L, FineOp g, const TimeMats* __restrict__ tm, typename C2<R>::T* __restrict__ factors,
               int* __restrict__ status) {
   typedef typename C2<R>::T CT;
   constexpr int NB = NPAD / LA_BLK;
   extern __shared__ __align__(16) unsigned char smem[];
-  CT* sRow = reinterpret_cast<CT*>(smem);                       // [NPAD-16][18]: sRow[k][c] = L[16 J + c][k]
-  CT* sPan = sRow + (size_t)(NPAD - LA_BLK) * kRowStride;      // [NPAD][17]: rows 16 J + row of block column J
-  CT* sInvT = sPan + (size_t)NPAD * kWideStride;               // [16][16]: sInvT[k][c] = conj(inv(L_JJ)[c][k])
-  R* sP = reinterpret_cast<R*>(sInvT + 256);                   // [9][K*K]
-  R* sD = sP + LA_NPAIR * LA_KMAX * LA_KMAX;                   // [64] dsum + V0
-  R* sX = sD + kWidePtsMax;                                    // [64] laser coordinate
-  R* sN = sX + kWidePtsMax;                                    // [64] in-grid neighbour weight of H^2's diagonal
-  R* sPiv = sN + kWidePtsMax;                                  // [16] 1/L_jj of the diagonal block
-  int* sXYZ = reinterpret_cast<int*>(sPiv + LA_BLK);          // [64] packed local coordinates
+  WideSmem<R> S;
+  S.sRow = reinterpret_cast<CT*>(smem);
+  S.sBT = S.sRow;   // written after the lookahead update has read sRow, read before sRow is refilled
+  S.sPan = S.sRow + (size_t)(NPAD - LA_BLK) * LA_BLK;
+  S.sXi = S.sPan + (size_t)NPAD * kWideStride;
+  S.sInvT = S.sXi + LA_BLK * kWideStride;
+  S.sP = reinterpret_cast<R*>(S.sInvT + 256);
+  S.sD = S.sP + LA_NPAIR * LA_KMAX * LA_KMAX;
+  S.sX = S.sD + kWidePtsMax;
+  S.sN = S.sX + kWidePtsMax;
+  S.sPiv = S.sN + kWidePtsMax;
+  S.sXYZ = reinterpret_cast<int*>(S.sPiv + LA_BLK);
 
   const int tid = threadIdx.x;
   const int K = tm->K, KK = K * K;
@@ -722,118 +891,42 @@ k_factor_wide(LevelGeom L, FineOp g, const TimeMats* __restrict__ tm, typename C
   subvol_box(L, b, o, e);
   const int npts = e[0] * e[1] * e[2], n = npts * K;
   CT* F = factors + (size_t)b * L.fsize;
-  for (int i = tid; i < LA_NPAIR * KK; i += kFactorThreads) sP[i] = (R)tm->P[i / KK][i % KK];
+  for (int i = tid; i < LA_NPAIR * KK; i += kFactorThreads) S.sP[i] = (R)tm->P[i / KK][i % KK];
   const R wx = (R)(0.5 * g.ih2[0]), wy = (R)(0.5 * g.ih2[1]), wz = (R)(0.5 * g.ih2[2]);
   for (int i = tid; i < npts; i += kFactorThreads) {
     int lx, ly, lz;
     local_coords(i, e, lx, ly, lz);
     const int px = o[0] + lx, py = o[1] + ly, pz = o[2] + lz;
-    sD[i] = (R)(g.dsum + g.V0[(pz * g.n[1] + py) * g.n[0] + px]);
-    sX[i] = (R)fine_x(g, px, py, pz);
+    S.sD[i] = (R)(g.dsum + g.V0[(pz * g.n[1] + py) * g.n[0] + px]);
+    S.sX[i] = (R)fine_x(g, px, py, pz);
     // unused axes have n = 1 and w = 0
     const int cx = (px > 0 ? 1 : 0) + (px + 1 < g.n[0] ? 1 : 0), cy = (py > 0 ? 1 : 0) + (py + 1 < g.n[1] ? 1 : 0),
               cz = (pz > 0 ? 1 : 0) + (pz + 1 < g.n[2] ? 1 : 0);
-    sN[i] = wx * wx * (R)cx + wy * wy * (R)cy + wz * wz * (R)cz;
-    sXYZ[i] = lx | (ly << 8) | (lz << 16);
+    S.sN[i] = wx * wx * (R)cx + wy * wy * (R)cy + wz * wz * (R)cz;
+    S.sXYZ[i] = lx | (ly << 8) | (lz << 16);
   }
   __syncthreads();
   const FastDiv dK = L.fd_K;
+  // block column 0: assembled only, one row per thread
+  if (tid < NPAD) {
+    CT a0[LA_BLK];
+#pragma unroll
+    for (int q = 0; q < LA_BLK; ++q) a0[q] = wide_entry<R>(tid, q, n, dK, S.sP, K, S.sD, S.sX, S.sN, S.sXYZ, wx, wy, wz);
+#pragma unroll
+    for (int q = 0; q < LA_BLK; ++q) S.sPan[(size_t)tid * kWideStride + q] = a0[q];
+  }
+  __syncthreads();
   for (int J = 0; J < NB; ++J) {
-    // block row J (blocks (J, 0..J-1)) transposed into shared memory
-    for (int t = tid; t < J * 256; t += kFactorThreads) {
-      const int Kb = t >> 8, w = t & 255, c = w >> 4, kk = w & 15;
-      sRow[(Kb * LA_BLK + kk) * kRowStride + c] = F[(size_t)tri_index(J, Kb) * 256 + w];
-    }
-    __syncthreads();
-    // assemble and update the block column: rows 16 J .. NPAD-1, tpr threads per row
-    const int RJ = NPAD - LA_BLK * J;
+    // threads per row of block column J+1 over the 224 lookahead threads
+    const int RJ1 = NPAD - LA_BLK * (J + 1);
     int tpr = 1;
-    while (tpr < LA_BLK && 2 * tpr * RJ <= kFactorThreads) tpr *= 2;
-    const int row = tid / tpr, c0 = (tid % tpr) * (LA_BLK / tpr);
-    if (row < RJ) {
-      switch (tpr) {
-#define LA_WIDE_CASE(TPR)                                                                                        \
-  case TPR:                                                                                                      \
-    wide_column_update<R, LA_BLK / TPR>(J, row, c0, n, dK, K, F, sP, sD, sX, sN, sXYZ, wx, wy, wz, sRow, sPan); \
-    break;
-        LA_WIDE_CASE(1)
-        LA_WIDE_CASE(2)
-        LA_WIDE_CASE(4)
-        LA_WIDE_CASE(8)
-        LA_WIDE_CASE(16)
-#undef LA_WIDE_CASE
-      }
+    while (tpr < 8 && 2 * tpr * RJ1 <= 224) tpr *= 2;
+    switch (tpr) {
+      case 1: wide_column_step<R, NPAD, 16>(J, n, dK, K, F, S, wx, wy, wz, status); break;
+      case 2: wide_column_step<R, NPAD, 8>(J, n, dK, K, F, S, wx, wy, wz, status); break;
+      case 4: wide_column_step<R, NPAD, 4>(J, n, dK, K, F, S, wx, wy, wz, status); break;
+      default: wide_column_step<R, NPAD, 2>(J, n, dK, K, F, S, wx, wy, wz, status); break;
     }
-    __syncthreads();
-    // Cholesky of the diagonal block (rows 0..15 of sPan, lower triangle) and its inverse, by warp 0
-    // alone (steps ordered by __syncwarp); the other warps wait at the barrier that follows
-    if (tid < 32) {
-      const int lane = tid;
-      for (int j = 0; j < LA_BLK; ++j) {
-        R d2 = sPan[j * kWideStride + j].x;
-        if (!(d2 > (R)0)) {
-          if (lane == 0) atomicOr(status, 1);
-          d2 = (R)1;
-        }
-        const R inv = rsq(d2);
-        // column j: L[i][j] = A[i][j] / sqrt(d2), i > j; L[j][j] = sqrt(d2)
-        if (lane == j) {
-          sPan[j * kWideStride + j] = mkc<CT>(d2 * inv, (R)0);
-          sPiv[j] = inv;
-        } else if (lane > j && lane < LA_BLK) {
-          CT v = sPan[lane * kWideStride + j];
-          sPan[lane * kWideStride + j] = mkc<CT>(v.x * inv, v.y * inv);
-        }
-        __syncwarp();
-        // trailing entries (i, k), j < k <= i: A[i][k] -= L[i][j] conj(L[k][j])
-        const int m = LA_BLK - 1 - j, T = m * (m + 1) / 2;
-        for (int e = lane; e < T; e += 32) {
-          int a_ = (int)((sqrtf(8.0f * (float)e + 1.0f) - 1.0f) * 0.5f);
-          while (a_ * (a_ + 1) / 2 > e) --a_;
-          while ((a_ + 1) * (a_ + 2) / 2 <= e) ++a_;
-          const int i = j + 1 + a_, k = j + 1 + (e - a_ * (a_ + 1) / 2);
-          const CT li = sPan[i * kWideStride + j], lk = sPan[k * kWideStride + j];
-          CT v = sPan[i * kWideStride + k];
-          v.x -= li.x * lk.x + li.y * lk.y;
-          v.y -= li.y * lk.x - li.x * lk.y;
-          sPan[i * kWideStride + k] = v;
-        }
-        __syncwarp();
-      }
-      // inv(L_JJ) column lane by forward substitution (16 lanes), stored as sInvT[k][c] = conj(inv[c][k])
-      if (lane < LA_BLK) {
-        const int jj = lane;
-        CT x[LA_BLK];
-#pragma unroll
-        for (int i = 0; i < LA_BLK; ++i) {
-          CT acc = mkc<CT>(0, 0);
-#pragma unroll
-          for (int k = 0; k < i; ++k)
-            if (k >= jj) cfma(acc, sPan[i * kWideStride + k], x[k]);
-          const R rinv = sPiv[i];
-          if (i < jj) x[i] = mkc<CT>(0, 0);
-          else if (i == jj) x[i] = mkc<CT>(rinv, (R)0);
-          else x[i] = mkc<CT>(-acc.x * rinv, -acc.y * rinv);
-        }
-#pragma unroll
-        for (int i = 0; i < LA_BLK; ++i) {
-          sInvT[jj * LA_BLK + i] = mkc<CT>(x[i].x, -x[i].y);
-          F[(size_t)tri_index(J, J) * 256 + i * LA_BLK + jj] = x[i];
-        }
-      }
-    }
-    __syncthreads();
-    // blocks below: L_IJ = A_IJ inv(L_JJ)^dagger, L[r][c] = sum_{k <= c} A[r][k] conj(inv[c][k])
-    for (int t = tid; t < (RJ - LA_BLK) * LA_BLK; t += kFactorThreads) {
-      const int rr = LA_BLK + (t >> 4), c = t & 15;
-      const CT* a = sPan + rr * kWideStride;
-      CT s = mkc<CT>(0, 0);
-#pragma unroll
-      for (int k = 0; k < LA_BLK; ++k)
-        if (k <= c) cfma(s, a[k], sInvT[k * LA_BLK + c]);
-      F[(size_t)tri_index(J + (rr >> 4), J) * 256 + (rr & 15) * LA_BLK + c] = s;
-    }
-    __syncthreads();
   }
 }
 
