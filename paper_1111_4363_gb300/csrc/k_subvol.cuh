@@ -590,16 +590,13 @@ __device__ __forceinline__ CPair<double2> lds_pair(const double2* p) {
 }
 
 // Shared-memory layout of the wide factorisation (bytes), for the padded size npad.
-// The block column's rows are padded to 17 entries so that the diagonal block's column-wise accesses
-// spread over the banks.  The transposed block row keeps rows of 16 entries, read as 16-byte pairs whose
-// position in a row is XOR-swizzled by the row index (pair p of row k at p ^ (k mod 8)), so that its
-// transposed stores spread over the banks too.
+// Rows of the two shared-memory panels are padded so that the transposed stores of the block row and the
+// column-wise accesses of the diagonal block spread over the banks: 17 entries for the block column,
+// 18 for the block row (whose rows the update reads as 16-byte pairs, so they start 16-byte aligned).
 constexpr int kWideStride = LA_BLK + 1;
-__host__ __device__ __forceinline__ int wide_row_idx(int k, int c) {
-  return k * LA_BLK + ((((c >> 1) ^ (k & 7))) << 1) + (c & 1);
-}
+constexpr int kRowStride = LA_BLK + 2;
 __host__ __device__ constexpr size_t wide_factor_smem(int npad, size_t csize, size_t rsize) {
-  return csize * ((size_t)(npad - LA_BLK) * LA_BLK         // block row J+1, transposed (then the block (J+1, J))
+  return csize * ((size_t)(npad - LA_BLK) * kRowStride     // block row J+1, transposed (then the block (J+1, J))
                   + (size_t)npad * kWideStride             // the block column's rows at their absolute index
                   + LA_BLK * kWideStride                   // inv(L_JJ) being built
                   + 256)                                   // inv(L_JJ)^dagger, [k][c]
@@ -679,18 +676,18 @@ __device__ __forceinline__ void wide_partial_update(int Jc, int kb_end, int r, i
     CT v[LA_BLK / 2];
 #pragma unroll
     for (int kk = 0; kk < LA_BLK / 2; ++kk) v[kk] = src[kk];
-    const CT* rowk = sRow + (size_t)Kb * LA_BLK * LA_BLK + k0 * LA_BLK;
+    const CT* rowk = sRow + ((size_t)Kb * LA_BLK + k0) * kRowStride + c0;
 #pragma unroll
     for (int kk = 0; kk < LA_BLK / 2; ++kk) {
 #pragma unroll
       for (int q = 0; q < CPT; q += (CPT > 1 ? 2 : 1)) {
         CT y[2];
         if (CPT > 1) {
-          const CPair<CT> yp = lds_pair(rowk + wide_row_idx(kk, c0 + q));
+          const CPair<CT> yp = lds_pair(rowk + kk * kRowStride + q);
           y[0] = yp.a();
           y[1] = yp.b();
         } else {
-          y[0] = rowk[wide_row_idx(kk, c0 + q)];
+          y[0] = rowk[kk * kRowStride + q];
         }
 #pragma unroll
         for (int u = 0; u < (CPT > 1 ? 2 : 1); ++u) {
@@ -707,7 +704,7 @@ __device__ __forceinline__ void wide_partial_update(int Jc, int kb_end, int r, i
 template <typename R>
 struct WideSmem {
   typedef typename C2<R>::T CT;
-  CT* sRow;   // [NPAD-16][16]: block row J' transposed, sRow[wide_row_idx(k, c)] = L[16 J' + c][k]
+  CT* sRow;   // [NPAD-16][18]: block row J' transposed, sRow[k][c] = L[16 J' + c][k]
   CT* sPan;   // [NPAD][17]: rows of the current block column at their absolute row index
   CT* sBT;    // [16][17]: sBT[k][c] = L[16 (J+1) + c][16 J + k] (the block (J+1, J)); in sRow's space
   CT* sInvT;  // [16][16]: sInvT[k][c] = conj(inv(L_JJ)[c][k])
@@ -809,7 +806,7 @@ __device__ __forceinline__ void wide_column_step(int J, int n, const FastDiv& dK
     // block row J+1's finished blocks (J+1, Kb < J), transposed
     for (int t = tl; t < J * 256; t += 224) {
       const int Kb = t >> 8, w = t & 255, c = w >> 4, kk = w & 15;
-      S.sRow[wide_row_idx(Kb * LA_BLK + kk, c)] = F[(size_t)tri_index(J + 1, Kb) * 256 + w];
+      S.sRow[(Kb * LA_BLK + kk) * kRowStride + c] = F[(size_t)tri_index(J + 1, Kb) * 256 + w];
     }
     wide_bar();
     if (own)
@@ -820,28 +817,41 @@ __device__ __forceinline__ void wide_column_step(int J, int n, const FastDiv& dK
   if (tid < 32 && own)   // warp 0's rows of block column 1 (no finished column before it)
     wide_partial_update<R, CPT>(J + 1, 0, r_own, c0, n, dK, K, F, S.sP, S.sD, S.sX, S.sN, S.sXYZ, wx, wy, wz, S.sRow,
                                 acc);
-  // rows below the diagonal block: L[r][c] = sum_{k <= c} A[r][k] conj(inv(L_JJ)[c][k]), one entry per
-  // thread; the 16 entries of a row are in one warp, which reads them all before writing them back
-  const int RJ = NPAD - LA_BLK * J;
-  const int total = (RJ - LA_BLK) * LA_BLK;
-  const int iters = (total + kFactorThreads - 1) / kFactorThreads;
-  for (int m = 0; m < iters; ++m) {
-    const int e = tid + m * kFactorThreads;
-    const bool act = e < total;
-    const int rr = LA_BLK * (J + 1) + (act ? e >> 4 : 0), c = e & 15;
-    CT s = mkc<CT>(0, 0);
-    if (act) {
-      const CT* a = S.sPan + (size_t)rr * kWideStride;
+  // rows below the diagonal block, one row per thread: L[r][c] = sum_{k <= c} A[r][k] conj(inv(L_JJ)[c][k])
+  // (the row's entries in registers, sInvT's rows read as 16-byte pairs), written to the factor store and
+  // back to the row in place; the rows of the block (J+1, J) also go to sBT for the update below
+  for (int q = tid; q < RJ1; q += kFactorThreads) {
+    const int rr = LA_BLK * (J + 1) + q;
+    CT* row = S.sPan + (size_t)rr * kWideStride;
+    CT a[LA_BLK], l[LA_BLK];
 #pragma unroll
-      for (int k = 0; k < LA_BLK; ++k)
-        if (k <= c) cfma(s, a[k], S.sInvT[k * LA_BLK + c]);
-      F[(size_t)tri_index(rr >> 4, J) * 256 + (rr & 15) * LA_BLK + c] = s;
-      if ((rr >> 4) == J + 1) S.sBT[c * kWideStride + (rr & 15)] = s;
+    for (int k = 0; k < LA_BLK; ++k) {
+      a[k] = row[k];
+      l[k] = mkc<CT>(0, 0);
     }
-    __syncwarp();
-    if (act) S.sPan[(size_t)rr * kWideStride + c] = s;
+#pragma unroll
+    for (int k = 0; k < LA_BLK; ++k) {
+#pragma unroll
+      for (int c = k - (k & 1); c < LA_BLK; c += 2) {   // inv is lower triangular: only c >= k contribute
+        const CPair<CT> ip = lds_pair(S.sInvT + k * LA_BLK + c);
+        cfma(l[c], a[k], ip.a());
+        cfma(l[c + 1], a[k], ip.b());
+      }
+    }
+#pragma unroll
+    for (int c = 0; c < LA_BLK; ++c) row[c] = l[c];
+    if ((rr >> 4) == J + 1) {
+#pragma unroll
+      for (int c = 0; c < LA_BLK; ++c) S.sBT[c * kWideStride + (rr & 15)] = l[c];
+    }
   }
   __syncthreads();
+  // the divided rows to the factor store, consecutive threads on consecutive entries
+  for (int e = tid; e < RJ1 * LA_BLK; e += kFactorThreads) {
+    const int rr = LA_BLK * (J + 1) + (e >> 4), c = e & 15;
+    F[(size_t)tri_index(rr >> 4, J) * 256 + (rr & 15) * LA_BLK + c] = S.sPan[(size_t)rr * kWideStride + c];
+  }
+  __syncthreads();   // the rows are overwritten below with block column J+1
   if (own) {
     // block column J's contribution: acc[c] -= sum_k L[r][16 J + k] conj(L[16 (J+1) + c][16 J + k])
     const CT* a = S.sPan + (size_t)r_own * kWideStride;
@@ -874,7 +884,7 @@ k_factor_wide(LevelGeom L, FineOp g, const TimeMats* __restrict__ tm, typename C
   WideSmem<R> S;
   S.sRow = reinterpret_cast<CT*>(smem);
   S.sBT = S.sRow;   // written after the lookahead update has read sRow, read before sRow is refilled
-  S.sPan = S.sRow + (size_t)(NPAD - LA_BLK) * LA_BLK;
+  S.sPan = S.sRow + (size_t)(NPAD - LA_BLK) * kRowStride;
   S.sXi = S.sPan + (size_t)NPAD * kWideStride;
   S.sInvT = S.sXi + LA_BLK * kWideStride;
   S.sP = reinterpret_cast<R*>(S.sInvT + 256);
