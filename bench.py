@@ -48,7 +48,7 @@ NCU_BYTES_PER_SUBVOLUME = {("factor", 0): (867072 + 287257600) / 4096,
                            # 3D 32^3 (512 subvolumes of 256 unknowns per launch, 64 per colour launch),
                            # complex64: profiles/k_factor_wide_3d_hydrogen_32x32x32_mixed.md and
                            # profiles/k_sweep_fine_wide_3d_hydrogen_32x32x32_mixed.md
-                           ("factor_wide", 1): (450304 + 84511744) / 512,
+                           ("factor_wide", 1): (623872 + 83455744) / 512,
                            ("sweep_wide", 1): 19529984 / 64}
 FP64_PEAK_TFLOPS = 152 * 4 * 2070e6 / 1e12   # 152 SMs x 4 FP64 flop/clk/SM x 2070 MHz (derived)
 FP32_PEAK_TFLOPS = 152 * 256 * 2070e6 / 1e12  # 152 SMs x 128 FP32 lanes x 2 flop (FMA) x 2070 MHz (derived)
