@@ -664,6 +664,61 @@ __global__ void k_restrict(LevelGeom F, LevelGeom C, const CT* __restrict__ sf, 
   store_k<CT, K>(gc, J, acc);
 }
 
+// Restriction I^T on 2D and 3D levels, one CTA per tile of kRx x kRy x kRz coarse points: the fine points the
+// tile's children cover (2 kR + 2 per used axis, zero outside the grid) are loaded into shared memory with
+// consecutive threads on consecutive complex entries, then each (coarse point, time function) sums its
+// 4 x 4 (x 4) children there, in the same order and with the same weights as k_restrict.
+constexpr int kRx = 8, kRy = 4, kRz = 2;
+template <typename CT, int K>
+__global__ void __launch_bounds__(256) k_restrict_tile(LevelGeom F, LevelGeom C, const CT* __restrict__ sf,
+                                                       CT* __restrict__ gc) {
+  typedef typename CR<CT>::R RR;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  CT* box = reinterpret_cast<CT*>(smem_raw);
+  const bool uy = F.dim > 1, uz = F.dim > 2;
+  const int tx = kRx, ty = uy ? kRy : 1, tz = uz ? kRz : 1;
+  const int jx0 = blockIdx.x * tx, jy0 = blockIdx.y * ty, jz0 = blockIdx.z * tz;
+  const int bx = 2 * tx + 2, by = uy ? 2 * ty + 2 : 1, bz = uz ? 2 * tz + 2 : 1;
+  const int ox = 2 * jx0 - 1, oy = uy ? 2 * jy0 - 1 : 0, oz = uz ? 2 * jz0 - 1 : 0;
+  const int nbox = bx * by * bz * K;
+  for (int t = threadIdx.x; t < nbox; t += blockDim.x) {
+    const int m = t % K, pnt = t / K;
+    const int lx = pnt % bx, rest = pnt / bx, ly = rest % by, lz = rest / by;
+    const int gx = ox + lx, gy = oy + ly, gz = oz + lz;
+    CT v = cmk<CT>(0, 0);
+    if (gx >= 0 && gy >= 0 && gz >= 0 && gx < F.n[0] && gy < F.n[1] && gz < F.n[2])
+      v = sf[((long long)(gz * F.n[1] + gy) * F.n[0] + gx) * K + m];
+    box[t] = v;
+  }
+  __syncthreads();
+  const int nitems = tx * ty * tz * K;
+  for (int t = threadIdx.x; t < nitems; t += blockDim.x) {
+    const int m = t % K, c = t / K;
+    const int cx = c % tx, rest = c / tx, cy = rest % ty, cz = rest / ty;
+    const int jx = jx0 + cx, jy = jy0 + cy, jz = jz0 + cz;
+    if (jx >= C.n[0] || jy >= C.n[1] || jz >= C.n[2]) continue;
+    CT acc = cmk<CT>(0, 0);
+    for (int qz = 0; qz < 4; ++qz) {
+      int az; float wz;
+      if (!child_1d(jz, qz, F.n[2], uz, az, wz)) continue;
+      for (int qy = 0; qy < 4; ++qy) {
+        int ay; float wy;
+        if (!child_1d(jy, qy, F.n[1], uy, ay, wy)) continue;
+#pragma unroll
+        for (int qx = 0; qx < 4; ++qx) {
+          int ax; float wx;
+          if (!child_1d(jx, qx, F.n[0], true, ax, wx)) continue;
+          const RR w = (RR)(wx * wy * wz);
+          const CT a = box[(((az - oz) * by + (ay - oy)) * bx + (ax - ox)) * K + m];
+          acc.x += w * a.x;
+          acc.y += w * a.y;
+        }
+      }
+    }
+    gc[((long long)(jz * C.n[1] + jy) * C.n[0] + jx) * K + m] = acc;
+  }
+}
+
 template <typename CT, int K>
 __global__ void k_prolong_add(LevelGeom F, LevelGeom C, const CT* __restrict__ ec, CT* __restrict__ ef) {
   typedef typename CR<CT>::R RR;
@@ -695,6 +750,33 @@ __global__ void k_prolong_add(LevelGeom F, LevelGeom C, const CT* __restrict__ e
 template <typename R>
 void launch_restrict(const LevelGeom& F, const LevelGeom& C, int K, const typename C2<R>::T* sf,
                      typename C2<R>::T* gc, cudaStream_t s) {
+  typedef typename C2<R>::T CT;
+  if (F.dim >= 2) {
+    const int ty = kRy, tz = F.dim > 2 ? kRz : 1;
+    const dim3 grid((C.n[0] + kRx - 1) / kRx, (C.n[1] + ty - 1) / ty, (C.n[2] + tz - 1) / tz);
+    const size_t smem = sizeof(CT) * (size_t)(2 * kRx + 2) * (2 * ty + 2) * (F.dim > 2 ? 2 * tz + 2 : 1) * K;
+#define LA_CALL(KK)                                                                                        \
+  do {                                                                                                     \
+    static bool attr = false;                                                                              \
+    if (!attr) {                                                                                           \
+      cudaFuncSetAttribute(k_restrict_tile<CT, KK>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024); \
+      attr = true;                                                                                         \
+    }                                                                                                      \
+    k_restrict_tile<CT, KK><<<grid, 256, smem, s>>>(F, C, sf, gc);                                         \
+  } while (0)
+    switch (K) {
+      case 1: LA_CALL(1); break;
+      case 2: LA_CALL(2); break;
+      case 3: LA_CALL(3); break;
+      case 4: LA_CALL(4); break;
+      case 5: LA_CALL(5); break;
+      case 6: LA_CALL(6); break;
+      case 7: LA_CALL(7); break;
+      default: LA_CALL(8); break;
+    }
+#undef LA_CALL
+    return;
+  }
 #define LA_CALL(KK) k_restrict<typename C2<R>::T, KK><<<(C.np + 127) / 128, 128, 0, s>>>(F, C, sf, gc)
   LA_K_DISPATCH(K, LA_CALL)
 #undef LA_CALL
