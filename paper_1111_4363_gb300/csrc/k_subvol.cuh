@@ -558,8 +558,8 @@ k_factor_blk(LevelGeom L, FineOp g, int is_fine, int nptsmax, const double* __re
 // the factor store: block column J is assembled in registers, updated with the finished block
 // columns 0..J-1 read back from global memory (recently written by the same CTA, so mostly L2
 // hits), its diagonal block is factorised in shared memory, the blocks below it are divided by it,
-// and the column is stored.  Entries of G_UU come from closed forms of H and H^2 on the grid, so no
-// table of point pairs is needed.
+// and the column is stored.  Entries of G_UU come from closed forms of H and H^2 on the grid, built
+// once per subvolume into a shared-memory table of (H, H^2) over its point pairs.
 constexpr int kWidePtsMax = 64;   // grid points of a wide subvolume
 
 // Two consecutive complex entries (16-byte aligned), as one vector load where the type allows.
@@ -589,6 +589,43 @@ __device__ __forceinline__ CPair<double2> lds_pair(const double2* p) {
   return r;
 }
 
+// L2 eviction-priority policies and the loads that carry them.  The sweep reads each factor block
+// twice, forward then backward; a launch's forward-read blocks outgrow L2 before the backward pass
+// reaches them unless the single-use streams (the backward reads themselves, c and f) give way first.
+__device__ __forceinline__ unsigned long long l2_evict_first() {
+  unsigned long long p;
+  asm("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+__device__ __forceinline__ unsigned long long l2_evict_last() {
+  unsigned long long p;
+  asm("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+__device__ __forceinline__ float4 ldg_policy(const float4* p, unsigned long long pol) {
+  float4 v;
+  asm("ld.global.nc.L2::cache_hint.v4.f32 {%0, %1, %2, %3}, [%4], %5;"
+      : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+      : "l"(p), "l"(pol));
+  return v;
+}
+__device__ __forceinline__ float2 ldg_policy(const float2* p, unsigned long long pol) {
+  float2 v;
+  asm("ld.global.nc.L2::cache_hint.v2.f32 {%0, %1}, [%2], %3;" : "=f"(v.x), "=f"(v.y) : "l"(p), "l"(pol));
+  return v;
+}
+// coherent loads (the array is written by the same launch elsewhere) with a policy
+__device__ __forceinline__ float2 ld_policy(const float2* p, unsigned long long pol) {
+  float2 v;
+  asm volatile("ld.global.L2::cache_hint.v2.f32 {%0, %1}, [%2], %3;" : "=f"(v.x), "=f"(v.y) : "l"(p), "l"(pol));
+  return v;
+}
+__device__ __forceinline__ double2 ld_policy(const double2* p, unsigned long long pol) {
+  double2 v;
+  asm volatile("ld.global.L2::cache_hint.v2.f64 {%0, %1}, [%2], %3;" : "=d"(v.x), "=d"(v.y) : "l"(p), "l"(pol));
+  return v;
+}
+
 // Shared-memory layout of the wide factorisation (bytes), for the padded size npad.
 // Rows of the two shared-memory panels are padded so that the transposed stores of the block row and the
 // column-wise accesses of the diagonal block spread over the banks: 17 entries for the block column,
@@ -600,7 +637,9 @@ __host__ __device__ constexpr size_t wide_factor_smem(int npad, size_t csize, si
                   + (size_t)npad * kWideStride             // the block column's rows at their absolute index
                   + LA_BLK * kWideStride                   // inv(L_JJ) being built
                   + 256)                                   // inv(L_JJ)^dagger, [k][c]
-         + rsize * (LA_NPAIR * LA_KMAX * LA_KMAX + 3 * kWidePtsMax + LA_BLK) + sizeof(int) * kWidePtsMax;
+         + rsize * (LA_NPAIR * LA_KMAX * LA_KMAX + 3 * kWidePtsMax + LA_BLK) + sizeof(int) * kWidePtsMax
+         + csize * (size_t)kWidePtsMax * kWidePtsMax    // (H, H^2) of every point pair
+         + rsize * 2 * LA_KMAX * LA_KMAX;               // P_HI - P_IH and P_XI - P_IX
 }
 
 // H_pq and (H^2)_pq of the finest-level operator H = -1/2 Laplacian + V0 for grid points p, q of one
@@ -628,29 +667,48 @@ __device__ __forceinline__ void wide_h_h2(int dx, int dy, int dz, R Dp, R Dq, R 
   }
 }
 
-// Assembles G_UU[r, c] (r, c < npad; identity outside the n true unknowns).  Point data in shared
-// memory: sD (dsum + V0), sX (laser coordinate), sN (in-grid neighbour weight nb2), sXYZ (packed
-// local coordinates); sP the nine K x K products P_kk' = R_k^T Wt R_k' (Theta = phase x P).
+// Shared-memory tables of the wide assembly: sHH[i * kWidePtsMax + j] = (H_ij, (H^2)_ij) for the
+// subvolume's points, sP the nine K x K products P_kk' = R_k^T Wt R_k' (Theta = phase x P) in the pair
+// order (0,0) (0,1) (0,2) (1,0) (1,1) (1,2) (2,0) (2,1) (2,2) of (I, H, X), sPd = (P_01 - P_10, P_02 - P_20)
+// (phases: (0,1), (0,2) +i; (1,0), (2,0) -i; the others real), sX the laser coordinate of each point.
 template <typename R>
-__device__ __forceinline__ typename C2<R>::T wide_entry(int r, int c, int n, const FastDiv& dK, const R* sP, int K,
-                                                     const R* sD, const R* sX, const R* sN, const int* sXYZ, R wx,
-                                                     R wy, R wz) {
+struct WideTables {
   typedef typename C2<R>::T CT;
-  if (r >= n || c >= n) return mkc<CT>((R)(r == c ? 1 : 0), (R)0);
-  const int i = fdiv(r, dK), m = r - i * K, j = fdiv(c, dK), nn = c - j * K;
-  const int pi = sXYZ[i], pj = sXYZ[j];
-  const int dx = (pj & 255) - (pi & 255), dy = ((pj >> 8) & 255) - ((pi >> 8) & 255), dz = (pj >> 16) - (pi >> 16);
-  R H, H2;
-  wide_h_h2<R>(dx, dy, dz, sD[i], sD[j], sN[i], wx, wy, wz, H, H2);
-  const int KK = K * K, mn = m * K + nn;
-  const R xp = sX[i], xq = sX[j];
-  // pairs (k, k') in the order (0,0) (0,1) (0,2) (1,0) (1,1) (1,2) (2,0) (2,1) (2,2) of (I, H, X);
-  // phases: (0,1), (0,2) +i; (1,0), (2,0) -i; others real
-  R re = H2 * sP[4 * KK + mn] + H * (xq * sP[5 * KK + mn] + xp * sP[7 * KK + mn]);
-  R im = H * (sP[1 * KK + mn] - sP[3 * KK + mn]);
-  if (i == j) {
-    re += sP[mn] + xp * xp * sP[8 * KK + mn];
-    im += xp * (sP[2 * KK + mn] - sP[6 * KK + mn]);
+  const CT* sHH;
+  const R *sP, *sPd, *sX;
+};
+// The point and time function of one row of G_UU, decoded once per row.
+template <typename R>
+struct WideRow {
+  int r, i, m;
+  R xp;
+};
+template <typename R>
+__device__ __forceinline__ WideRow<R> wide_row(int r, const FastDiv& dK, int K, const R* sX) {
+  WideRow<R> w;
+  w.r = r;
+  w.i = fdiv(r, dK);
+  w.m = r - w.i * K;
+  w.xp = sX[w.i < kWidePtsMax ? w.i : 0];
+  return w;
+}
+
+// Assembles G_UU[r, c] (r, c < npad; identity outside the n true unknowns).
+template <typename R>
+__device__ __forceinline__ typename C2<R>::T wide_entry(const WideRow<R>& w, int c, int n, const FastDiv& dK, int K,
+                                                     const WideTables<R>& T) {
+  typedef typename C2<R>::T CT;
+  if (w.r >= n || c >= n) return mkc<CT>((R)(w.r == c ? 1 : 0), (R)0);
+  const int j = fdiv(c, dK), nn = c - j * K;
+  const CT hh = T.sHH[w.i * kWidePtsMax + j];
+  const R H = hh.x, H2 = hh.y;
+  const int KK = K * K, mn = w.m * K + nn;
+  const R xp = w.xp, xq = T.sX[j];
+  R re = H2 * T.sP[4 * KK + mn] + H * (xq * T.sP[5 * KK + mn] + xp * T.sP[7 * KK + mn]);
+  R im = H * T.sPd[mn];
+  if (w.i == j) {
+    re += T.sP[mn] + xp * xp * T.sP[8 * KK + mn];
+    im += xp * T.sPd[KK + mn];
   }
   return mkc<CT>(re, im);
 }
@@ -663,13 +721,13 @@ __device__ __forceinline__ typename C2<R>::T wide_entry(int r, int c, int n, con
 // read back from the factor store, the block row J' transposed in sRow.
 template <typename R, int CPT>
 __device__ __forceinline__ void wide_partial_update(int Jc, int kb_end, int r, int c0, int n, const FastDiv& dK, int K,
-                                                    const typename C2<R>::T* __restrict__ F, const R* sP, const R* sD,
-                                                    const R* sX, const R* sN, const int* sXYZ, R wx, R wy, R wz,
+                                                    const typename C2<R>::T* __restrict__ F, const WideTables<R>& T,
                                                     const typename C2<R>::T* sRow, typename C2<R>::T* acc) {
   typedef typename C2<R>::T CT;
   const int I = r >> 4;
+  const WideRow<R> w = wide_row<R>(r, dK, K, T.sX);
 #pragma unroll
-  for (int q = 0; q < CPT; ++q) acc[q] = wide_entry<R>(r, LA_BLK * Jc + c0 + q, n, dK, sP, K, sD, sX, sN, sXYZ, wx, wy, wz);
+  for (int q = 0; q < CPT; ++q) acc[q] = wide_entry<R>(w, LA_BLK * Jc + c0 + q, n, dK, K, T);
   for (int h = 0; h < 2 * kb_end; ++h) {   // half a finished block row (8 columns k) at a time
     const int Kb = h >> 1, k0 = (h & 1) * (LA_BLK / 2);
     const CT* src = F + (size_t)tri_index(I, Kb) * 256 + (r & 15) * LA_BLK + k0;
@@ -709,8 +767,10 @@ struct WideSmem {
   CT* sBT;    // [16][17]: sBT[k][c] = L[16 (J+1) + c][16 J + k] (the block (J+1, J)); in sRow's space
   CT* sInvT;  // [16][16]: sInvT[k][c] = conj(inv(L_JJ)[c][k])
   CT* sXi;    // [16][17]: inv(L_JJ) being built
-  R *sP, *sD, *sX, *sN, *sPiv;
+  CT* sHH;    // [64][64]: (H, H^2) of the point pairs
+  R *sP, *sPd, *sD, *sX, *sN, *sPiv;
   int* sXYZ;
+  __device__ WideTables<R> tables() const { return WideTables<R>{sHH, sP, sPd, sX}; }
 };
 
 // Cholesky of the diagonal block of column J (rows 16 J .. 16 J + 15 of sPan) and its inverse in one
@@ -785,7 +845,7 @@ __device__ __forceinline__ void wide_bar() { asm volatile("bar.sync 1, 224;" :::
 // by L_JJ, and warps 1..7 add block column J's contribution to J+1 from shared memory.
 template <typename R, int NPAD, int CPT>
 __device__ __forceinline__ void wide_column_step(int J, int n, const FastDiv& dK, int K, typename C2<R>::T* F,
-                                                 const WideSmem<R>& S, R wx, R wy, R wz, int* status) {
+                                                 const WideSmem<R>& S, int* status) {
   typedef typename C2<R>::T CT;
   constexpr int NB = NPAD / LA_BLK;
   constexpr int TPR = LA_BLK / CPT;
@@ -809,14 +869,11 @@ __device__ __forceinline__ void wide_column_step(int J, int n, const FastDiv& dK
       S.sRow[(Kb * LA_BLK + kk) * kRowStride + c] = F[(size_t)tri_index(J + 1, Kb) * 256 + w];
     }
     wide_bar();
-    if (own)
-      wide_partial_update<R, CPT>(J + 1, J, r_own, c0, n, dK, K, F, S.sP, S.sD, S.sX, S.sN, S.sXYZ, wx, wy, wz, S.sRow,
-                                  acc);
+    if (own) wide_partial_update<R, CPT>(J + 1, J, r_own, c0, n, dK, K, F, S.tables(), S.sRow, acc);
   }
   __syncthreads();
   if (tid < 32 && own)   // warp 0's rows of block column 1 (no finished column before it)
-    wide_partial_update<R, CPT>(J + 1, 0, r_own, c0, n, dK, K, F, S.sP, S.sD, S.sX, S.sN, S.sXYZ, wx, wy, wz, S.sRow,
-                                acc);
+    wide_partial_update<R, CPT>(J + 1, 0, r_own, c0, n, dK, K, F, S.tables(), S.sRow, acc);
   // rows below the diagonal block, one row per thread: L[r][c] = sum_{k <= c} A[r][k] conj(inv(L_JJ)[c][k])
   // (the row's entries in registers, sInvT's rows read as 16-byte pairs), written to the factor store and
   // back to the row in place; the rows of the block (J+1, J) also go to sBT for the update below
@@ -893,6 +950,8 @@ k_factor_wide(LevelGeom L, FineOp g, const TimeMats* __restrict__ tm, typename C
   S.sN = S.sX + kWidePtsMax;
   S.sPiv = S.sN + kWidePtsMax;
   S.sXYZ = reinterpret_cast<int*>(S.sPiv + LA_BLK);
+  S.sHH = reinterpret_cast<CT*>(S.sXYZ + kWidePtsMax);
+  S.sPd = reinterpret_cast<R*>(S.sHH + kWidePtsMax * kWidePtsMax);
 
   const int tid = threadIdx.x;
   const int K = tm->K, KK = K * K;
@@ -916,12 +975,27 @@ k_factor_wide(LevelGeom L, FineOp g, const TimeMats* __restrict__ tm, typename C
     S.sXYZ[i] = lx | (ly << 8) | (lz << 16);
   }
   __syncthreads();
+  for (int p = tid; p < npts * npts; p += kFactorThreads) {
+    const int i = p / npts, j = p - i * npts;
+    const int pi = S.sXYZ[i], pj = S.sXYZ[j];
+    const int dx = (pj & 255) - (pi & 255), dy = ((pj >> 8) & 255) - ((pi >> 8) & 255), dz = (pj >> 16) - (pi >> 16);
+    R H, H2;
+    wide_h_h2<R>(dx, dy, dz, S.sD[i], S.sD[j], S.sN[i], wx, wy, wz, H, H2);
+    S.sHH[i * kWidePtsMax + j] = mkc<CT>(H, H2);
+  }
+  for (int i = tid; i < KK; i += kFactorThreads) {
+    S.sPd[i] = S.sP[1 * KK + i] - S.sP[3 * KK + i];
+    S.sPd[KK + i] = S.sP[2 * KK + i] - S.sP[6 * KK + i];
+  }
+  __syncthreads();
   const FastDiv dK = L.fd_K;
+  const WideTables<R> T = S.tables();
   // block column 0: assembled only, one row per thread
   if (tid < NPAD) {
     CT a0[LA_BLK];
+    const WideRow<R> w = wide_row<R>(tid, dK, K, S.sX);
 #pragma unroll
-    for (int q = 0; q < LA_BLK; ++q) a0[q] = wide_entry<R>(tid, q, n, dK, S.sP, K, S.sD, S.sX, S.sN, S.sXYZ, wx, wy, wz);
+    for (int q = 0; q < LA_BLK; ++q) a0[q] = wide_entry<R>(w, q, n, dK, K, T);
 #pragma unroll
     for (int q = 0; q < LA_BLK; ++q) S.sPan[(size_t)tid * kWideStride + q] = a0[q];
   }
@@ -932,10 +1006,10 @@ k_factor_wide(LevelGeom L, FineOp g, const TimeMats* __restrict__ tm, typename C
     int tpr = 1;
     while (tpr < 8 && 2 * tpr * RJ1 <= 224) tpr *= 2;
     switch (tpr) {
-      case 1: wide_column_step<R, NPAD, 16>(J, n, dK, K, F, S, wx, wy, wz, status); break;
-      case 2: wide_column_step<R, NPAD, 8>(J, n, dK, K, F, S, wx, wy, wz, status); break;
-      case 4: wide_column_step<R, NPAD, 4>(J, n, dK, K, F, S, wx, wy, wz, status); break;
-      default: wide_column_step<R, NPAD, 2>(J, n, dK, K, F, S, wx, wy, wz, status); break;
+      case 1: wide_column_step<R, NPAD, 16>(J, n, dK, K, F, S, status); break;
+      case 2: wide_column_step<R, NPAD, 8>(J, n, dK, K, F, S, status); break;
+      case 4: wide_column_step<R, NPAD, 4>(J, n, dK, K, F, S, status); break;
+      default: wide_column_step<R, NPAD, 2>(J, n, dK, K, F, S, status); break;
     }
   }
 }
@@ -1025,16 +1099,16 @@ __device__ __forceinline__ void subvol_solve(const CT* __restrict__ F, CT* rhs, 
 // overwritten by x.  Called by all threads of the CTA, between barriers.
 // the two complex entries (2q, r) and (2q + 1, r) of a block (a column pair, stride 16)
 template <typename CT>
-__device__ __forceinline__ CPair<CT> load_colpair(const CT* blk, int q, int r);
+__device__ __forceinline__ CPair<CT> load_colpair(const CT* blk, int q, int r, unsigned long long pol);
 template <>
-__device__ __forceinline__ CPair<float2> load_colpair<float2>(const float2* blk, int q, int r) {
+__device__ __forceinline__ CPair<float2> load_colpair<float2>(const float2* blk, int q, int r, unsigned long long pol) {
   CPair<float2> p;
-  const float2 x = __ldg(blk + (2 * q) * LA_BLK + r), y = __ldg(blk + (2 * q + 1) * LA_BLK + r);
+  const float2 x = ldg_policy(blk + (2 * q) * LA_BLK + r, pol), y = ldg_policy(blk + (2 * q + 1) * LA_BLK + r, pol);
   p.v = make_float4(x.x, x.y, y.x, y.y);
   return p;
 }
 template <>
-__device__ __forceinline__ CPair<double2> load_colpair<double2>(const double2* blk, int q, int r) {
+__device__ __forceinline__ CPair<double2> load_colpair<double2>(const double2* blk, int q, int r, unsigned long long) {
   CPair<double2> p;
   p.a_ = __ldg(blk + (2 * q) * LA_BLK + r);
   p.b_ = __ldg(blk + (2 * q + 1) * LA_BLK + r);
@@ -1048,25 +1122,36 @@ __device__ __forceinline__ CT reduce_xor(CT v, int m) {
   return v;
 }
 
+// forward block loads of the solve: complex64 with the keep-for-the-backward-pass policy
+template <typename CT>
+__device__ __forceinline__ void load_fwd(CPair<CT>& p, const CT* a, unsigned long long pol) {
+  p.load(a);
+}
+template <>
+__device__ __forceinline__ void load_fwd<float2>(CPair<float2>& p, const float2* a, unsigned long long pol) {
+  p.v = ldg_policy(reinterpret_cast<const float4*>(a), pol);
+}
+
 template <typename CT, int NPAD>
 __device__ __forceinline__ void subvol_solve_wide(const CT* __restrict__ F, CT* rhs, CT* y, CT* tvec, CT* part) {
   constexpr int NB = NPAD / LA_BLK;
   constexpr bool kPrefetch = sizeof(CT) == 8;   // complex64: next step's blocks in flight during this one
   const int t = threadIdx.x;
+  const unsigned long long keep = l2_evict_last(), last_use = l2_evict_first();
   {
     const int r = t >> 3, q = t & 7;
     CPair<CT> cur[NB];
-    cur[0].load(F + r * LA_BLK + 2 * q);
+    load_fwd(cur[0], F + r * LA_BLK + 2 * q, keep);
 #pragma unroll
     for (int I = 0; I < NB; ++I) {
       CPair<CT> nxt[NB];
       if (kPrefetch && I + 1 < NB) {
 #pragma unroll
-        for (int J = 0; J <= I + 1; ++J) nxt[J].load(F + (size_t)tri_index(I + 1, J) * 256 + r * LA_BLK + 2 * q);
+        for (int J = 0; J <= I + 1; ++J) load_fwd(nxt[J], F + (size_t)tri_index(I + 1, J) * 256 + r * LA_BLK + 2 * q, keep);
       }
       if (!kPrefetch && I > 0) {
 #pragma unroll
-        for (int J = 0; J <= I; ++J) cur[J].load(F + (size_t)tri_index(I, J) * 256 + r * LA_BLK + 2 * q);
+        for (int J = 0; J <= I; ++J) load_fwd(cur[J], F + (size_t)tri_index(I, J) * 256 + r * LA_BLK + 2 * q, keep);
       }
       CT acc0 = mkc<CT>(0, 0), acc1 = mkc<CT>(0, 0);
 #pragma unroll
@@ -1100,18 +1185,18 @@ __device__ __forceinline__ void subvol_solve_wide(const CT* __restrict__ F, CT* 
     // step I uses blocks (J, I), J = I .. NB-1 ((I, I): the inverted diagonal block)
     if (kPrefetch) {
 #pragma unroll
-      for (int J = NB - 1; J < NB; ++J) cur[J] = load_colpair<CT>(F + (size_t)tri_index(J, NB - 1) * 256, q, r);
+      for (int J = NB - 1; J < NB; ++J) cur[J] = load_colpair<CT>(F + (size_t)tri_index(J, NB - 1) * 256, q, r, last_use);
     }
 #pragma unroll
     for (int I = NB - 1; I >= 0; --I) {
       CPair<CT> nxt[NB];
       if (kPrefetch && I > 0) {
 #pragma unroll
-        for (int J = I - 1; J < NB; ++J) nxt[J] = load_colpair<CT>(F + (size_t)tri_index(J, I - 1) * 256, q, r);
+        for (int J = I - 1; J < NB; ++J) nxt[J] = load_colpair<CT>(F + (size_t)tri_index(J, I - 1) * 256, q, r, last_use);
       }
       if (!kPrefetch) {
 #pragma unroll
-        for (int J = I; J < NB; ++J) cur[J] = load_colpair<CT>(F + (size_t)tri_index(J, I) * 256, q, r);
+        for (int J = I; J < NB; ++J) cur[J] = load_colpair<CT>(F + (size_t)tri_index(J, I) * 256, q, r, last_use);
       }
       CT acc0 = mkc<CT>(0, 0), acc1 = mkc<CT>(0, 0);
 #pragma unroll
@@ -1223,6 +1308,7 @@ k_sweep_fine(LevelGeom L, FineOp g, const TimeMats* __restrict__ tm, const typen
   for (int i = tid; i < KK; i += kSweepThreads) {
     sQ[i] = (R)tm->Qb[i]; sU[i] = (R)tm->Ub[i]; sW[i] = (R)tm->Wt[i]; sE[i] = (R)tm->Eb[i];
   }
+  const unsigned long long stream = l2_evict_first();   // c and f: read once per launch
   for (int t = tid; t < nbc * K; t += kSweepThreads) {
     int i, m;
     item(t, i, m);
@@ -1230,7 +1316,7 @@ k_sweep_fine(LevelGeom L, FineOp g, const TimeMats* __restrict__ tm, const typen
     coords(i, dc0, dc1, lx, ly, lz);
     const int gx = oc[0] + lx, gy = oc[1] + ly, gz = oc[2] + lz;
     CT v = mkc<CT>(0, 0);
-    if (fine_in(g, gx, gy, gz)) v = c[(size_t)((gz * g.n[1] + gy) * g.n[0] + gx) * K + m];
+    if (fine_in(g, gx, gy, gz)) v = ld_policy(c + (size_t)((gz * g.n[1] + gy) * g.n[0] + gx) * K + m, stream);
     sC[t] = v;
   }
   {
@@ -1295,7 +1381,7 @@ k_sweep_fine(LevelGeom L, FineOp g, const TimeMats* __restrict__ tm, const typen
         ur = fma(u, hv.x, ur); ui = fma(u, hv.y, ui);
         er = fma(ee, cv.x, er); ei = fma(ee, cv.y, ei);
       }
-      const CT fv = f ? f[(size_t)((gz * g.n[1] + gy) * g.n[0] + gx) * K + m] : mkc<CT>(0, 0);
+      const CT fv = f ? ld_policy(f + (size_t)((gz * g.n[1] + gy) * g.n[0] + gx) * K + m, stream) : mkc<CT>(0, 0);
       r.x = fv.x - (-qi - ur - xl * er);
       r.y = fv.y - (qr - ui - xl * ei);
     }
