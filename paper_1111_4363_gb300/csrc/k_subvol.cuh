@@ -626,6 +626,16 @@ __device__ __forceinline__ double2 ld_policy(const double2* p, unsigned long lon
   return v;
 }
 
+__device__ __forceinline__ void cp_async_elem(float2* sdst, const float2* gsrc) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"((unsigned)__cvta_generic_to_shared(sdst)), "l"(gsrc)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_elem(double2* sdst, const double2* gsrc) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((unsigned)__cvta_generic_to_shared(sdst)), "l"(gsrc)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
 // Shared-memory layout of the wide factorisation (bytes), for the padded size npad.
 // Rows of the two shared-memory panels are padded so that the transposed stores of the block row and the
 // column-wise accesses of the diagonal block spread over the banks: 17 entries for the block column,
@@ -866,8 +876,9 @@ __device__ __forceinline__ void wide_column_step(int J, int n, const FastDiv& dK
     // block row J+1's finished blocks (J+1, Kb < J), transposed
     for (int t = tl; t < J * 256; t += 224) {
       const int Kb = t >> 8, w = t & 255, c = w >> 4, kk = w & 15;
-      S.sRow[(Kb * LA_BLK + kk) * kRowStride + c] = F[(size_t)tri_index(J + 1, Kb) * 256 + w];
+      cp_async_elem(S.sRow + (Kb * LA_BLK + kk) * kRowStride + c, F + (size_t)tri_index(J + 1, Kb) * 256 + w);
     }
+    cp_async_wait_all();
     wide_bar();
     if (own) wide_partial_update<R, CPT>(J + 1, J, r_own, c0, n, dK, K, F, S.tables(), S.sRow, acc);
   }
