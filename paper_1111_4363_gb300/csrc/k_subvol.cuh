@@ -626,6 +626,8 @@ __device__ __forceinline__ double2 ld_policy(const double2* p, unsigned long lon
   return v;
 }
 
+// Asynchronous copy (cp.async) of one complex element global -> shared; cp_async_wait_all waits for the
+// calling thread's copies.
 __device__ __forceinline__ void cp_async_elem(float2* sdst, const float2* gsrc) {
   asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"((unsigned)__cvta_generic_to_shared(sdst)), "l"(gsrc)
                : "memory");
@@ -873,7 +875,7 @@ __device__ __forceinline__ void wide_column_step(int J, int n, const FastDiv& dK
   if (tid < 32) {
     wide_diag<R>(J, S, F, status);
   } else if (next) {
-    // block row J+1's finished blocks (J+1, Kb < J), transposed
+    // block row J+1's finished blocks (J+1, Kb < J), transposed, every copy in flight at once
     for (int t = tl; t < J * 256; t += 224) {
       const int Kb = t >> 8, w = t & 255, c = w >> 4, kk = w & 15;
       cp_async_elem(S.sRow + (Kb * LA_BLK + kk) * kRowStride + c, F + (size_t)tri_index(J + 1, Kb) * 256 + w);
