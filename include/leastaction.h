@@ -203,8 +203,11 @@ la_status la_time_matrices(la_ctx* ctx, double t0, double* out);
    inside the V-cycle and for the action norm) and every finest-level restriction and prolongation,
    and counts all of its kernel launches.  Algorithmic flops: factorisation
    (4/3) n^3 per subvolume (complex Cholesky of the n = |U| K unknowns); sweep 8 n^2 per subvolume
-   (the two triangular solves; the residual stencil is not counted).  Algorithmic bytes of the
-   residual stencil: c in, r out, f in where present (K complex each per point) and V0 in. */
+   (the two triangular solves; the residual stencil is not counted).  Where the finest-level factor
+   has 16 x 16 blocks that vanish identically (subvolumes of more than 128 unknowns: G_UU couples only
+   points at most two grid steps apart, and the factor keeps that envelope), both counts cover only the
+   blocks of the band: the block-banded Cholesky and the solves over the band's blocks.  Algorithmic
+   bytes of the residual stencil: c in, r out, f in where present (K complex each per point) and V0 in. */
 typedef struct {
   long long launches;     /* kernels launched by the library since enabling */
   int n_factor;           /* finest-level factorisation launches */

@@ -567,12 +567,14 @@ template <typename CT> struct CPair;
 template <> struct CPair<float2> {
   float4 v;
   __device__ __forceinline__ void load(const float2* p) { v = __ldg(reinterpret_cast<const float4*>(p)); }
+  __device__ __forceinline__ void load_zero() { v = make_float4(0.f, 0.f, 0.f, 0.f); }
   __device__ __forceinline__ float2 a() const { return make_float2(v.x, v.y); }
   __device__ __forceinline__ float2 b() const { return make_float2(v.z, v.w); }
 };
 template <> struct CPair<double2> {
   double2 a_, b_;
   __device__ __forceinline__ void load(const double2* p) { a_ = __ldg(p); b_ = __ldg(p + 1); }
+  __device__ __forceinline__ void load_zero() { a_ = make_double2(0.0, 0.0); b_ = a_; }
   __device__ __forceinline__ double2 a() const { return a_; }
   __device__ __forceinline__ double2 b() const { return b_; }
 };
@@ -732,15 +734,18 @@ __device__ __forceinline__ typename C2<R>::T wide_entry(const WideRow<R>& w, int
 // acc[c] = G[r][16 J' + c0 + c] - sum_{k < 16 kb_end} L[r][k] conj(L[16 J' + c0 + c][k]), the finished rows
 // read back from the factor store, the block row J' transposed in sRow.
 template <typename R, int CPT>
-__device__ __forceinline__ void wide_partial_update(int Jc, int kb_end, int r, int c0, int n, const FastDiv& dK, int K,
-                                                    const typename C2<R>::T* __restrict__ F, const WideTables<R>& T,
-                                                    const typename C2<R>::T* sRow, typename C2<R>::T* acc) {
+__device__ __forceinline__ void wide_partial_update(int Jc, int kb_end, int band, int r, int c0, int n,
+                                                    const FastDiv& dK, int K, const typename C2<R>::T* __restrict__ F,
+                                                    const WideTables<R>& T, const typename C2<R>::T* sRow,
+                                                    typename C2<R>::T* acc) {
   typedef typename C2<R>::T CT;
   const int I = r >> 4;
   const WideRow<R> w = wide_row<R>(r, dK, K, T.sX);
 #pragma unroll
   for (int q = 0; q < CPT; ++q) acc[q] = wide_entry<R>(w, LA_BLK * Jc + c0 + q, n, dK, K, T);
-  for (int h = 0; h < 2 * kb_end; ++h) {   // half a finished block row (8 columns k) at a time
+  // the blocks (I, Kb) with I - Kb > band are zero: the sum starts at Kb = I - band
+  const int kb_begin = I - band > 0 ? I - band : 0;
+  for (int h = 2 * kb_begin; h < 2 * kb_end; ++h) {   // half a finished block row (8 columns k) at a time
     const int Kb = h >> 1, k0 = (h & 1) * (LA_BLK / 2);
     const CT* src = F + (size_t)tri_index(I, Kb) * 256 + (r & 15) * LA_BLK + k0;
     CT v[LA_BLK / 2];
@@ -856,8 +861,8 @@ __device__ __forceinline__ void wide_bar() { asm volatile("bar.sync 1, 224;" :::
 // column J+1 and update it with the finished block columns 0..J-1; then all threads divide J's rows below
 // by L_JJ, and warps 1..7 add block column J's contribution to J+1 from shared memory.
 template <typename R, int NPAD, int CPT>
-__device__ __forceinline__ void wide_column_step(int J, int n, const FastDiv& dK, int K, typename C2<R>::T* F,
-                                                 const WideSmem<R>& S, int* status) {
+__device__ __forceinline__ void wide_column_step(int J, int band, int n, const FastDiv& dK, int K,
+                                                 typename C2<R>::T* F, const WideSmem<R>& S, int* status) {
   typedef typename C2<R>::T CT;
   constexpr int NB = NPAD / LA_BLK;
   constexpr int TPR = LA_BLK / CPT;
@@ -875,18 +880,19 @@ __device__ __forceinline__ void wide_column_step(int J, int n, const FastDiv& dK
   if (tid < 32) {
     wide_diag<R>(J, S, F, status);
   } else if (next) {
-    // block row J+1's finished blocks (J+1, Kb < J), transposed, every copy in flight at once
-    for (int t = tl; t < J * 256; t += 224) {
+    // block row J+1's finished blocks (J+1, Kb < J) inside the band, transposed, every copy in flight at once
+    const int kb0 = J + 1 - band > 0 ? J + 1 - band : 0;
+    for (int t = kb0 * 256 + tl; t < J * 256; t += 224) {
       const int Kb = t >> 8, w = t & 255, c = w >> 4, kk = w & 15;
       cp_async_elem(S.sRow + (Kb * LA_BLK + kk) * kRowStride + c, F + (size_t)tri_index(J + 1, Kb) * 256 + w);
     }
     cp_async_wait_all();
     wide_bar();
-    if (own) wide_partial_update<R, CPT>(J + 1, J, r_own, c0, n, dK, K, F, S.tables(), S.sRow, acc);
+    if (own) wide_partial_update<R, CPT>(J + 1, J, band, r_own, c0, n, dK, K, F, S.tables(), S.sRow, acc);
   }
   __syncthreads();
   if (tid < 32 && own)   // warp 0's rows of block column 1 (no finished column before it)
-    wide_partial_update<R, CPT>(J + 1, 0, r_own, c0, n, dK, K, F, S.tables(), S.sRow, acc);
+    wide_partial_update<R, CPT>(J + 1, 0, band, r_own, c0, n, dK, K, F, S.tables(), S.sRow, acc);
   // rows below the diagonal block, one row per thread: L[r][c] = sum_{k <= c} A[r][k] conj(inv(L_JJ)[c][k])
   // (the row's entries in registers, sInvT's rows read as 16-byte pairs), written to the factor store and
   // back to the row in place; the rows of the block (J+1, J) also go to sBT for the update below
@@ -1019,10 +1025,10 @@ k_factor_wide(LevelGeom L, FineOp g, const TimeMats* __restrict__ tm, typename C
     int tpr = 1;
     while (tpr < 8 && 2 * tpr * RJ1 <= 224) tpr *= 2;
     switch (tpr) {
-      case 1: wide_column_step<R, NPAD, 16>(J, n, dK, K, F, S, status); break;
-      case 2: wide_column_step<R, NPAD, 8>(J, n, dK, K, F, S, status); break;
-      case 4: wide_column_step<R, NPAD, 4>(J, n, dK, K, F, S, status); break;
-      default: wide_column_step<R, NPAD, 2>(J, n, dK, K, F, S, status); break;
+      case 1: wide_column_step<R, NPAD, 16>(J, L.band, n, dK, K, F, S, status); break;
+      case 2: wide_column_step<R, NPAD, 8>(J, L.band, n, dK, K, F, S, status); break;
+      case 4: wide_column_step<R, NPAD, 4>(J, L.band, n, dK, K, F, S, status); break;
+      default: wide_column_step<R, NPAD, 2>(J, L.band, n, dK, K, F, S, status); break;
     }
   }
 }
@@ -1144,9 +1150,22 @@ template <>
 __device__ __forceinline__ void load_fwd<float2>(CPair<float2>& p, const float2* a, unsigned long long pol) {
   p.v = ldg_policy(reinterpret_cast<const float4*>(a), pol);
 }
+template <typename CT>
+__device__ __forceinline__ CPair<CT> zero_pair() {
+  CPair<CT> p;
+  p.load_zero();
+  return p;
+}
+// a block entry pair inside the band, else the zero it is known to be
+template <typename CT>
+__device__ __forceinline__ void load_fwd_band(CPair<CT>& p, const CT* a, bool in_band, unsigned long long pol) {
+  if (in_band) load_fwd(p, a, pol);
+  else p.load_zero();
+}
 
 template <typename CT, int NPAD>
-__device__ __forceinline__ void subvol_solve_wide(const CT* __restrict__ F, CT* rhs, CT* y, CT* tvec, CT* part) {
+__device__ __forceinline__ void subvol_solve_wide(const CT* __restrict__ F, int band, CT* rhs, CT* y, CT* tvec,
+                                                  CT* part) {
   constexpr int NB = NPAD / LA_BLK;
   constexpr bool kPrefetch = sizeof(CT) == 8;   // complex64: next step's blocks in flight during this one
   const int t = threadIdx.x;
@@ -1158,13 +1177,16 @@ __device__ __forceinline__ void subvol_solve_wide(const CT* __restrict__ F, CT* 
 #pragma unroll
     for (int I = 0; I < NB; ++I) {
       CPair<CT> nxt[NB];
+      // blocks (I, J) with I - J > band are exact zeros: set, not loaded
       if (kPrefetch && I + 1 < NB) {
 #pragma unroll
-        for (int J = 0; J <= I + 1; ++J) load_fwd(nxt[J], F + (size_t)tri_index(I + 1, J) * 256 + r * LA_BLK + 2 * q, keep);
+        for (int J = 0; J <= I + 1; ++J)
+          load_fwd_band(nxt[J], F + (size_t)tri_index(I + 1, J) * 256 + r * LA_BLK + 2 * q, J >= I + 1 - band, keep);
       }
       if (!kPrefetch && I > 0) {
 #pragma unroll
-        for (int J = 0; J <= I; ++J) load_fwd(cur[J], F + (size_t)tri_index(I, J) * 256 + r * LA_BLK + 2 * q, keep);
+        for (int J = 0; J <= I; ++J)
+          load_fwd_band(cur[J], F + (size_t)tri_index(I, J) * 256 + r * LA_BLK + 2 * q, J >= I - band, keep);
       }
       CT acc0 = mkc<CT>(0, 0), acc1 = mkc<CT>(0, 0);
 #pragma unroll
@@ -1205,11 +1227,14 @@ __device__ __forceinline__ void subvol_solve_wide(const CT* __restrict__ F, CT* 
       CPair<CT> nxt[NB];
       if (kPrefetch && I > 0) {
 #pragma unroll
-        for (int J = I - 1; J < NB; ++J) nxt[J] = load_colpair<CT>(F + (size_t)tri_index(J, I - 1) * 256, q, r, last_use);
+        for (int J = I - 1; J < NB; ++J)
+          nxt[J] = J <= I - 1 + band ? load_colpair<CT>(F + (size_t)tri_index(J, I - 1) * 256, q, r, last_use)
+                                     : zero_pair<CT>();
       }
       if (!kPrefetch) {
 #pragma unroll
-        for (int J = I; J < NB; ++J) cur[J] = load_colpair<CT>(F + (size_t)tri_index(J, I) * 256, q, r, last_use);
+        for (int J = I; J < NB; ++J)
+          cur[J] = J <= I + band ? load_colpair<CT>(F + (size_t)tri_index(J, I) * 256, q, r, last_use) : zero_pair<CT>();
       }
       CT acc0 = mkc<CT>(0, 0), acc1 = mkc<CT>(0, 0);
 #pragma unroll
@@ -1471,7 +1496,7 @@ k_sweep_fine(LevelGeom L, FineOp g, const TimeMats* __restrict__ tm, const typen
   }
   __syncthreads();
   if (use_wide_solve<R, NPAD>())
-    subvol_solve_wide<CT, NPAD>(factors + (size_t)b * L.fsize, sRhs, sY, sT, sRed);
+    subvol_solve_wide<CT, NPAD>(factors + (size_t)b * L.fsize, L.band, sRhs, sY, sT, sRed);
   else
     subvol_solve<CT, NPAD>(factors + (size_t)b * L.fsize, sRhs, sY, sT, sRed);
   __syncthreads();

@@ -287,6 +287,26 @@ static bool build_time_constants(la_ctx* c) {
   return true;
 }
 
+// Block bandwidth of a finest-level subvolume factor (see LevelGeom::band).  G_UU couples two unknowns
+// only when their points are at most two grid steps apart (Manhattan), which in the subvolume's x-fastest
+// point order means point indices at most d_max apart; the Cholesky factor keeps that envelope.  Block
+// (I, J) holds the points floor(16 I / K) .. and .. floor((16 J + 15) / K), so it is zero when the
+// nearest two are more than d_max apart; the band is the largest I - J of a block that may be nonzero.
+static int fine_band_blocks(int dim, const int sub[3], int K, int nblk) {
+  int maxd = 0;
+  for (int dz = -2; dz <= 2; ++dz)
+    for (int dy = -2; dy <= 2; ++dy)
+      for (int dx = -2; dx <= 2; ++dx) {
+        if (abs(dx) + abs(dy) + abs(dz) > 2 || (dim < 2 && dy != 0) || (dim < 3 && dz != 0)) continue;
+        maxd = std::max(maxd, abs(dx + sub[0] * dy + sub[0] * sub[1] * dz));
+      }
+  int band = 0;
+  for (int d = 1; d < nblk; ++d)
+    for (int J = 0; J + d < nblk; ++J)
+      if ((LA_BLK * (J + d)) / K - (LA_BLK * J + LA_BLK - 1) / K <= maxd) band = d;
+  return band;
+}
+
 static int round_npad(int n) {
   const int sizes[8] = {16, 32, 48, 64, 96, 128, 192, 256};
   for (int s : sizes)
@@ -434,6 +454,8 @@ extern "C" la_status la_init(const la_config* cfg, void* stream, la_ctx** out) {
     }
     G.fd_pair = make_fastdiv(LA_NPAIR * box5_count(k.dim));
     G.one_per_cta = k.factor_group == 1 ? 1 : 0;
+    G.band = (l == 0 && k.local_form == 0 && G.npad > LA_NPAD_MAX) ? fine_band_blocks(k.dim, G.sub, k.nt, G.nblk)
+                                                                  : G.nblk - 1;
   }
   if (!build_time_constants(c)) {
     g_init_error = "invalid configuration: singular time-basis Gram matrix";
@@ -508,9 +530,30 @@ extern "C" la_status la_init(const la_config* cfg, void* stream, la_ctx** out) {
   return LA_OK;
 }
 
+// Real flops (8 per complex multiply-add) of the block-banded factorisation of an n-unknown subvolume
+// whose 16 x 16 blocks (I, J) with I - J > band are zero: block (I, J) of the band is updated with the
+// block columns Kb = max(0, I - band) .. J - 1 (only the lower half of a diagonal block counts), divided by
+// the diagonal block's triangular inverse, and every diagonal block is factorised and inverted (16^3 / 3).
+// Without a band this is the dense Cholesky's 4/3 n^3 up to terms of order 16 n^2.
+static double banded_factor_flops(double n, int band) {
+  const int nb = (int)((n + LA_BLK - 1) / LA_BLK);
+  const double b3 = (double)LA_BLK * LA_BLK * LA_BLK;
+  double macs = 0.0;
+  for (int J = 0; J < nb; ++J) {
+    for (int I = J; I < nb && I - J <= band; ++I) {
+      const int nk = J - std::max(0, I - band);
+      if (nk > 0) macs += (I == J ? b3 * (LA_BLK + 1) / (2.0 * LA_BLK) : b3) * nk;
+      if (I > J) macs += (double)LA_BLK * LA_BLK * (LA_BLK + 1) / 2.0;
+    }
+    macs += b3 / 3.0;
+  }
+  return 8.0 * macs;
+}
+
 // algorithmic flops of the finest-level factorisation and of one full sweep
 static void finest_flops(la_ctx* c) {
   const LevelGeom& G = c->geo[0];
+  const bool banded = G.band < G.nblk - 1;
   double ff = 0.0, fs = 0.0;
   for (int bz = 0; bz < G.nb[2]; ++bz)
     for (int by = 0; by < G.nb[1]; ++by)
@@ -518,9 +561,19 @@ static void finest_flops(la_ctx* c) {
         int e[3], bb[3] = {bx, by, bz};
         for (int a = 0; a < 3; ++a) e[a] = std::min(G.sub[a], G.n[a] - bb[a] * G.sub[a]);
         const double n = (double)e[0] * e[1] * e[2] * c->K;
-        // Cholesky (4/3 n^3) and two triangular solves (8 n^2); the square form's LU takes 8/3 n^3
-        ff += (c->cfg.local_form == 1 ? 8.0 : 4.0) / 3.0 * n * n * n;
-        fs += 8.0 * n * n;
+        if (banded) {
+          // the factor's nonzero blocks only: the banded factorisation, and two triangular solves over
+          // the blocks of the band (8 flops per complex entry and solve)
+          ff += banded_factor_flops(n, G.band);
+          const int nb = (int)((n + LA_BLK - 1) / LA_BLK);
+          double nz = 0.0;
+          for (int I = 0; I < nb; ++I) nz += std::min(I, G.band) + 1;
+          fs += 2.0 * 8.0 * LA_BLK * LA_BLK * nz * (n * n) / ((double)nb * nb * LA_BLK * LA_BLK);
+        } else {
+          // Cholesky (4/3 n^3) and two triangular solves (8 n^2); the square form's LU takes 8/3 n^3
+          ff += (c->cfg.local_form == 1 ? 8.0 : 4.0) / 3.0 * n * n * n;
+          fs += 8.0 * n * n;
+        }
       }
   c->flops_factor = ff;
   c->flops_sweep = fs;

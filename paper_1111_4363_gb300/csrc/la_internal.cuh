@@ -95,6 +95,11 @@ struct LevelGeom {
   FastDiv fd_K, fd_c[2], fd_f[2], fd_u[2];
   FastDiv fd_pair;   // Galerkin levels: stencil values per point, 9 pairs x the radius-2 box
   int one_per_cta;   // factorise one subvolume matrix per CTA (no packing of small matrices)
+  // block bandwidth of the local factor: blocks (I, K) with I - K > band are exactly zero.  The
+  // finest-level operator couples points at most two grid steps apart (H^2), so G_UU and its Cholesky
+  // factor (no fill outside the envelope) vanish beyond the largest index distance of such a pair; the
+  // wide (global-memory) factorisation and solves skip those blocks.  nblk - 1 where nothing is skipped.
+  int band;
 };
 
 // Finest-level spatial operator: H = -1/2 Laplacian + V0, X = x along laser_axis.
