@@ -561,6 +561,9 @@ k_factor_blk(LevelGeom L, FineOp g, int is_fine, int nptsmax, const double* __re
 // and the column is stored.  Entries of G_UU come from closed forms of H and H^2 on the grid, built
 // once per subvolume into a shared-memory table of (H, H^2) over its point pairs.
 constexpr int kWidePtsMax = 64;   // grid points of a wide subvolume
+// row stride of the (H, H^2) pair table: odd, so that the rows of one column a warp reads spread over
+// the banks
+constexpr int kHHStride = kWidePtsMax + 1;
 
 // Two consecutive complex entries (16-byte aligned), as one vector load where the type allows.
 template <typename CT> struct CPair;
@@ -652,7 +655,7 @@ __host__ __device__ constexpr size_t wide_factor_smem(int npad, size_t csize, si
                   + LA_BLK * kWideStride                   // inv(L_JJ) being built
                   + 256)                                   // inv(L_JJ)^dagger, [k][c]
          + rsize * (LA_NPAIR * LA_KMAX * LA_KMAX + 3 * kWidePtsMax + LA_BLK) + sizeof(int) * kWidePtsMax
-         + csize * (size_t)kWidePtsMax * kWidePtsMax    // (H, H^2) of every point pair
+         + csize * (size_t)kWidePtsMax * kHHStride      // (H, H^2) of every point pair
          + rsize * 2 * LA_KMAX * LA_KMAX;               // P_HI - P_IH and P_XI - P_IX
 }
 
@@ -681,7 +684,7 @@ __device__ __forceinline__ void wide_h_h2(int dx, int dy, int dz, R Dp, R Dq, R 
   }
 }
 
-// Shared-memory tables of the wide assembly: sHH[i * kWidePtsMax + j] = (H_ij, (H^2)_ij) for the
+// Shared-memory tables of the wide assembly: sHH[i * kHHStride + j] = (H_ij, (H^2)_ij) for the
 // subvolume's points, sP the nine K x K products P_kk' = R_k^T Wt R_k' (Theta = phase x P) in the pair
 // order (0,0) (0,1) (0,2) (1,0) (1,1) (1,2) (2,0) (2,1) (2,2) of (I, H, X), sPd = (P_01 - P_10, P_02 - P_20)
 // (phases: (0,1), (0,2) +i; (1,0), (2,0) -i; the others real), sX the laser coordinate of each point.
@@ -714,7 +717,7 @@ __device__ __forceinline__ typename C2<R>::T wide_entry(const WideRow<R>& w, int
   typedef typename C2<R>::T CT;
   if (w.r >= n || c >= n) return mkc<CT>((R)(w.r == c ? 1 : 0), (R)0);
   const int j = fdiv(c, dK), nn = c - j * K;
-  const CT hh = T.sHH[w.i * kWidePtsMax + j];
+  const CT hh = T.sHH[w.i * kHHStride + j];
   const R H = hh.x, H2 = hh.y;
   const int KK = K * K, mn = w.m * K + nn;
   const R xp = w.xp, xq = T.sX[j];
@@ -784,7 +787,7 @@ struct WideSmem {
   CT* sBT;    // [16][17]: sBT[k][c] = L[16 (J+1) + c][16 J + k] (the block (J+1, J)); in sRow's space
   CT* sInvT;  // [16][16]: sInvT[k][c] = conj(inv(L_JJ)[c][k])
   CT* sXi;    // [16][17]: inv(L_JJ) being built
-  CT* sHH;    // [64][64]: (H, H^2) of the point pairs
+  CT* sHH;    // [64][65]: (H, H^2) of the point pairs
   R *sP, *sPd, *sD, *sX, *sN, *sPiv;
   int* sXYZ;
   __device__ WideTables<R> tables() const { return WideTables<R>{sHH, sP, sPd, sX}; }
@@ -970,7 +973,7 @@ k_factor_wide(LevelGeom L, FineOp g, const TimeMats* __restrict__ tm, typename C
   S.sPiv = S.sN + kWidePtsMax;
   S.sXYZ = reinterpret_cast<int*>(S.sPiv + LA_BLK);
   S.sHH = reinterpret_cast<CT*>(S.sXYZ + kWidePtsMax);
-  S.sPd = reinterpret_cast<R*>(S.sHH + kWidePtsMax * kWidePtsMax);
+  S.sPd = reinterpret_cast<R*>(S.sHH + kWidePtsMax * kHHStride);
 
   const int tid = threadIdx.x;
   const int K = tm->K, KK = K * K;
@@ -1000,7 +1003,7 @@ k_factor_wide(LevelGeom L, FineOp g, const TimeMats* __restrict__ tm, typename C
     const int dx = (pj & 255) - (pi & 255), dy = ((pj >> 8) & 255) - ((pi >> 8) & 255), dz = (pj >> 16) - (pi >> 16);
     R H, H2;
     wide_h_h2<R>(dx, dy, dz, S.sD[i], S.sD[j], S.sN[i], wx, wy, wz, H, H2);
-    S.sHH[i * kWidePtsMax + j] = mkc<CT>(H, H2);
+    S.sHH[i * kHHStride + j] = mkc<CT>(H, H2);
   }
   for (int i = tid; i < KK; i += kFactorThreads) {
     S.sPd[i] = S.sP[1 * KK + i] - S.sP[3 * KK + i];
