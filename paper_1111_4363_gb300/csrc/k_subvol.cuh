@@ -743,6 +743,11 @@ __device__ __forceinline__ void wide_partial_update(int Jc, int kb_end, int band
                                                     typename C2<R>::T* acc) {
   typedef typename C2<R>::T CT;
   const int I = r >> 4;
+  if (I - Jc > band) {   // a block beyond the band: zero, nothing to assemble or update
+#pragma unroll
+    for (int q = 0; q < CPT; ++q) acc[q] = mkc<CT>(0, 0);
+    return;
+  }
   const WideRow<R> w = wide_row<R>(r, dK, K, T.sX);
 #pragma unroll
   for (int q = 0; q < CPT; ++q) acc[q] = wide_entry<R>(w, LA_BLK * Jc + c0 + q, n, dK, K, T);
@@ -899,7 +904,8 @@ __device__ __forceinline__ void wide_column_step(int J, int band, int n, const F
   // rows below the diagonal block, one row per thread: L[r][c] = sum_{k <= c} A[r][k] conj(inv(L_JJ)[c][k])
   // (the row's entries in registers, sInvT's rows read as 16-byte pairs), written to the factor store and
   // back to the row in place; the rows of the block (J+1, J) also go to sBT for the update below
-  for (int q = tid; q < RJ1; q += kFactorThreads) {
+  // (rows beyond the band hold exact zeros, which stay zeros)
+  for (int q = tid; q < RJ1 && q < LA_BLK * band; q += kFactorThreads) {
     const int rr = LA_BLK * (J + 1) + q;
     CT* row = S.sPan + (size_t)rr * kWideStride;
     CT a[LA_BLK], l[LA_BLK];
@@ -931,8 +937,9 @@ __device__ __forceinline__ void wide_column_step(int J, int band, int n, const F
     F[(size_t)tri_index(rr >> 4, J) * 256 + (rr & 15) * LA_BLK + c] = S.sPan[(size_t)rr * kWideStride + c];
   }
   __syncthreads();   // the rows are overwritten below with block column J+1
-  if (own) {
+  if (own && (r_own >> 4) - J <= band) {
     // block column J's contribution: acc[c] -= sum_k L[r][16 J + k] conj(L[16 (J+1) + c][16 J + k])
+    // (zero for rows whose block (I, J) is beyond the band)
     const CT* a = S.sPan + (size_t)r_own * kWideStride;
 #pragma unroll
     for (int k = 0; k < LA_BLK; ++k) {

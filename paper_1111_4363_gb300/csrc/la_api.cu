@@ -304,7 +304,7 @@ static int fine_band_blocks(int dim, const int sub[3], int K, int nblk) {
   for (int d = 1; d < nblk; ++d)
     for (int J = 0; J + d < nblk; ++J)
       if ((LA_BLK * (J + d)) / K - (LA_BLK * J + LA_BLK - 1) / K <= maxd) band = d;
-  return band;
+  return std::min(std::max(band, 1), nblk - 1);   // at least the first subdiagonal (a wider band is exact too)
 }
 
 static int round_npad(int n) {
