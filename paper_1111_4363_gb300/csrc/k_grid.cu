@@ -927,6 +927,15 @@ void launch_trial(long long n, const double* a, const double2* h0, const double2
 void launch_c128_to_c64(long long n, const double2* x, float2* y, cudaStream_t s) {
   k_c128_to_c64<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, x, y);
 }
+// y = (float) x, element by element (grid-stride)
+__global__ void k_f64_to_f32(long long n, const double* __restrict__ x, float* __restrict__ y) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    y[i] = (float)x[i];
+}
+void launch_f64_to_f32(long long n, const double* x, float* y, cudaStream_t s) {
+  const long long nb = std::min<long long>((n + 255) / 256, 152LL * 8);
+  k_f64_to_f32<<<(unsigned)(nb > 0 ? nb : 1), 256, 0, s>>>(n, x, y);
+}
 
 
 // ------------------------------------------------------------------ bounded-wait self-test

@@ -64,7 +64,7 @@ __host__ __device__ constexpr int factor_mpc(int npad) { return npad <= 32 ? 8 :
 
 template <typename R, int NPAD, int MPC>
 __global__ void __launch_bounds__(kFactorThreads, 2)
-k_factor(LevelGeom L, FineOp g, int is_fine, int nptsmax, const double* __restrict__ sigma,
+k_factor(LevelGeom L, FineOp g, int is_fine, int nptsmax, const R* __restrict__ sigma,
          const TimeMats* __restrict__ tm, typename C2<R>::T* __restrict__ factors, int* __restrict__ status) {
   typedef typename C2<R>::T CT;
   constexpr int NTRI = NPAD * (NPAD + 1) / 2;
@@ -297,7 +297,7 @@ __device__ __forceinline__ double rsq(double x) { return rsqrt(x); }
 // path does not use it.
 template <typename R, int NPAD, int MPC>
 __global__ void __launch_bounds__(kFactorThreads, sizeof(R) == 4 ? (NPAD <= 96 ? 3 : 2) : 1)
-k_factor_blk(LevelGeom L, FineOp g, int is_fine, int nptsmax, const double* __restrict__ sigma,
+k_factor_blk(LevelGeom L, FineOp g, int is_fine, int nptsmax, const R* __restrict__ sigma,
              const TimeMats* __restrict__ tm, typename C2<R>::T* __restrict__ factors, int* __restrict__ status) {
   typedef typename C2<R>::T CT;
   constexpr int NB = NPAD / LA_BLK;
@@ -1584,7 +1584,7 @@ struct SubvolDiv {
 
 // Fills S.Rhs[0..npad) with (g - G e) on the subvolume with origin o and extent e (0 in padding).
 template <typename R>
-__device__ inline void coarse_rhs(const LevelGeom& L, const double* __restrict__ sigma,
+__device__ inline void coarse_rhs(const LevelGeom& L, const R* __restrict__ sigma,
                                   const TimeMats* __restrict__ tm, const typename C2<R>::T* __restrict__ gvec,
                                   const typename C2<R>::T* __restrict__ ev, const int o[3], const int e[3], int npad,
                                   const CoarseSmem<R>& S) {
@@ -1675,7 +1675,7 @@ __device__ inline void coarse_rhs(const LevelGeom& L, const double* __restrict__
 
 template <typename R, int NPAD>
 __global__ void __launch_bounds__(kSweepThreads)
-k_sweep_coarse(LevelGeom L, const double* __restrict__ sigma, const TimeMats* __restrict__ tm,
+k_sweep_coarse(LevelGeom L, const R* __restrict__ sigma, const TimeMats* __restrict__ tm,
                const typename C2<R>::T* __restrict__ gvec, typename C2<R>::T* __restrict__ ev,
                const typename C2<R>::T* __restrict__ factors, int colour, int* __restrict__ status) {
   typedef typename C2<R>::T CT;
@@ -1706,7 +1706,7 @@ k_sweep_coarse(LevelGeom L, const double* __restrict__ sigma, const TimeMats* __
 // s = g - G e on every point of a Galerkin level, one CTA per subvolume (all colours at once).
 template <typename R>
 __global__ void __launch_bounds__(kSweepThreads)
-k_gresid_tiles(LevelGeom L, const double* __restrict__ sigma, const TimeMats* __restrict__ tm,
+k_gresid_tiles(LevelGeom L, const R* __restrict__ sigma, const TimeMats* __restrict__ tm,
                const typename C2<R>::T* __restrict__ gvec, const typename C2<R>::T* __restrict__ ev,
                typename C2<R>::T* __restrict__ out, int npad) {
   typedef typename C2<R>::T CT;
@@ -1758,7 +1758,7 @@ inline size_t sweep_coarse_smem(const LevelGeom& L, int K, size_t rsize, size_t 
 }
 
 template <typename R, int NPAD, int mpc>
-cudaError_t launch_factor_blk_m(const LevelGeom& L, const FineOp* fine, const double* sigma, const TimeMats* tm,
+cudaError_t launch_factor_blk_m(const LevelGeom& L, const FineOp* fine, const R* sigma, const TimeMats* tm,
                                 typename C2<R>::T* factors, int* status, cudaStream_t s) {
   typedef typename C2<R>::T CT;
   const int nptsmax = L.sub[0] * L.sub[1] * L.sub[2];
@@ -1779,7 +1779,7 @@ cudaError_t launch_factor_blk_m(const LevelGeom& L, const FineOp* fine, const do
 }
 
 template <typename R, int NPAD>
-cudaError_t launch_factor_blk_n(const LevelGeom& L, const FineOp* fine, const double* sigma, const TimeMats* tm,
+cudaError_t launch_factor_blk_n(const LevelGeom& L, const FineOp* fine, const R* sigma, const TimeMats* tm,
                                 typename C2<R>::T* factors, int* status, cudaStream_t s) {
   constexpr int mpc = factor_c64_mpc(NPAD);
   if (mpc > 1 && factor_grid_mpc(L, mpc) == 1)
@@ -1807,7 +1807,7 @@ cudaError_t launch_factor_wide_n(const LevelGeom& L, const FineOp* fine, const T
 }
 
 template <typename R, int NPAD, int mpc>
-cudaError_t launch_factor_m(const LevelGeom& L, const FineOp* fine, const double* sigma, const TimeMats* tm,
+cudaError_t launch_factor_m(const LevelGeom& L, const FineOp* fine, const R* sigma, const TimeMats* tm,
                             typename C2<R>::T* factors, int* status, cudaStream_t s) {
   const int nptsmax = L.sub[0] * L.sub[1] * L.sub[2];
   const size_t smem = factor_smem(L, nptsmax, sizeof(typename C2<R>::T), mpc);
@@ -1824,7 +1824,7 @@ cudaError_t launch_factor_m(const LevelGeom& L, const FineOp* fine, const double
   return cudaGetLastError();
 }
 template <typename R, int NPAD>
-cudaError_t launch_factor_n(const LevelGeom& L, const FineOp* fine, const double* sigma, const TimeMats* tm,
+cudaError_t launch_factor_n(const LevelGeom& L, const FineOp* fine, const R* sigma, const TimeMats* tm,
                             typename C2<R>::T* factors, int* status, cudaStream_t s) {
   constexpr int mpc = factor_mpc(NPAD);
   if (mpc > 1 && factor_grid_mpc(L, mpc) == 1)
@@ -1850,7 +1850,7 @@ cudaError_t launch_sweep_fine_n(const LevelGeom& L, const FineOp& g, const TimeM
   return cudaGetLastError();
 }
 template <typename R, int NPAD>
-cudaError_t launch_sweep_coarse_n(const LevelGeom& L, const double* sigma, const TimeMats* tm, int K,
+cudaError_t launch_sweep_coarse_n(const LevelGeom& L, const R* sigma, const TimeMats* tm, int K,
                                   const typename C2<R>::T* gvec, typename C2<R>::T* e,
                                   const typename C2<R>::T* factors, int colour, int* status, cudaStream_t s) {
   const int nblocks = colour_count(L, colour);
@@ -1869,7 +1869,7 @@ cudaError_t launch_sweep_coarse_n(const LevelGeom& L, const double* sigma, const
 }
 
 template <typename R>
-cudaError_t launch_gresid_tiles_r(const LevelGeom& L, const double* sigma, const TimeMats* tm, int K,
+cudaError_t launch_gresid_tiles_r(const LevelGeom& L, const R* sigma, const TimeMats* tm, int K,
                                   const typename C2<R>::T* gvec, const typename C2<R>::T* e, typename C2<R>::T* out,
                                   cudaStream_t s) {
   const size_t smem = sweep_coarse_smem(L, K, sizeof(R), sizeof(typename C2<R>::T));

@@ -2,7 +2,7 @@
 #include "k_subvol.cuh"
 namespace la {
 template <>
-cudaError_t launch_factor<float>(const LevelGeom& L, const FineOp* fine, const double* sigma, const TimeMats* tm,
+cudaError_t launch_factor<float>(const LevelGeom& L, const FineOp* fine, const float* sigma, const TimeMats* tm,
                                   float2* factors, int* status, cudaStream_t s) {
 #define LA_CALL(N) launch_factor_blk_n<float, N>(L, fine, sigma, tm, factors, status, s)
   {
@@ -22,7 +22,7 @@ cudaError_t launch_sweep_fine<float>(const LevelGeom& L, const FineOp& g, const 
 #undef LA_CALL
 }
 template <>
-cudaError_t launch_sweep_coarse<float>(const LevelGeom& L, const double* sigma, const TimeMats* tm, int K,
+cudaError_t launch_sweep_coarse<float>(const LevelGeom& L, const float* sigma, const TimeMats* tm, int K,
                                         const float2* gvec, float2* e, const float2* factors, int colour,
                                         int* status, cudaStream_t s) {
 #define LA_CALL(N) launch_sweep_coarse_n<float, N>(L, sigma, tm, K, gvec, e, factors, colour, status, s)
@@ -30,7 +30,7 @@ cudaError_t launch_sweep_coarse<float>(const LevelGeom& L, const double* sigma, 
 #undef LA_CALL
 }
 template <>
-cudaError_t launch_gresid_tiles<float>(const LevelGeom& L, const double* sigma, const TimeMats* tm, int K,
+cudaError_t launch_gresid_tiles<float>(const LevelGeom& L, const float* sigma, const TimeMats* tm, int K,
                                      const float2* gvec, const float2* e, float2* out, cudaStream_t s) {
   return launch_gresid_tiles_r<float>(L, sigma, tm, K, gvec, e, out, s);
 }

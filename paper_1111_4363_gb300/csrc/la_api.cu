@@ -39,6 +39,8 @@ struct la_ctx {
   void* d_sl[LA_MAX_LEVELS] = {};
   void* d_fac[LA_MAX_LEVELS] = {};
   double* d_sigma[LA_MAX_LEVELS] = {};
+  // complex64 path: the Galerkin stencils rounded to float once, as its kernels use them
+  float* d_sigma32[LA_MAX_LEVELS] = {};
   double* d_partials = nullptr;
   double* d_N = nullptr;
   int* d_status = nullptr;
@@ -496,6 +498,7 @@ extern "C" la_status la_init(const la_config* cfg, void* stream, la_ctx** out) {
       ALLOC(c->d_g[l], vb);
       ALLOC(c->d_sl[l], vb);
       ALLOC(c->d_sigma[l], sizeof(double) * (size_t)G.np * LA_NPAIR * box5_count(k.dim));
+      if (k.precision == 1) ALLOC(c->d_sigma32[l], sizeof(float) * (size_t)G.np * LA_NPAIR * box5_count(k.dim));
     }
   }
   c->nparts = norm_blocks(c->np0);
@@ -687,6 +690,15 @@ extern "C" la_status la_set_hamiltonian(la_ctx* c, const double* V0, const la_pu
     else launch_galerkin_coarse(c->geo[l - 1], c->d_sigma[l - 1], c->geo[l], c->d_sigma[l], c->stream);
     LA_CHECK_LAUNCH(c);
   }
+  // the complex64 kernels read the stencils as float: round them once here, which halves the bytes
+  // every Galerkin-level sweep, residual and factorisation streams and changes no result
+  if (c->cfg.precision == 1) {
+    for (int l = 1; l < c->L; ++l) {
+      launch_f64_to_f32((long long)c->geo[l].np * LA_NPAIR * box5_count(c->dim), c->d_sigma[l], c->d_sigma32[l],
+                        c->stream);
+      LA_CHECK_LAUNCH(c);
+    }
+  }
   LA_CUDA(c, cudaStreamSynchronize(c->stream));
   c->have_ham = true;
   c->nhist = 0;
@@ -710,6 +722,11 @@ template <> struct Fine<float> {
   static float2* s(la_ctx* c) { return c->d_s32; }
 };
 
+// The Galerkin stencils of level l in the precision R of the path that reads them.
+template <typename R> static const R* sigma_of(const la_ctx* c, int l);
+template <> const double* sigma_of<double>(const la_ctx* c, int l) { return c->d_sigma[l]; }
+template <> const float* sigma_of<float>(const la_ctx* c, int l) { return c->d_sigma32[l]; }
+
 template <typename R>
 static la_status factor_all(la_ctx* c) {
   typedef typename C2<R>::T CT;
@@ -720,7 +737,7 @@ static la_status factor_all(la_ctx* c) {
     LA_CUDA(c, cudaEventRecord(c->ev_fork, c->stream));
     LA_CUDA(c, cudaStreamWaitEvent(c->cap, c->ev_fork, 0));
     for (int l = 1; l < c->L; ++l) {
-      cudaError_t e = launch_factor<R>(c->geo[l], nullptr, c->d_sigma[l], c->d_tm, (CT*)c->d_fac[l], c->d_status,
+      cudaError_t e = launch_factor<R>(c->geo[l], nullptr, sigma_of<R>(c, l), c->d_tm, (CT*)c->d_fac[l], c->d_status,
                                        c->cap);
       if (e != cudaSuccess) return fail(c, LA_ECUDA, "factor level %d: %s", l, cudaGetErrorString(e));
       ++c->launches;
@@ -732,7 +749,7 @@ static la_status factor_all(la_ctx* c) {
     cudaError_t e = c->cfg.local_form == 1
                         ? launch_factor_square(c->geo[0], c->fine, c->d_tm, (double2*)c->d_fac[0], c->d_perm,
                                                c->d_status, c->stream)
-                        : launch_factor<R>(c->geo[l], l == 0 ? &c->fine : nullptr, c->d_sigma[l], c->d_tm,
+                        : launch_factor<R>(c->geo[l], l == 0 ? &c->fine : nullptr, sigma_of<R>(c, l), c->d_tm,
                                            (CT*)c->d_fac[l], c->d_status, c->stream);
     if (e != cudaSuccess) return fail(c, LA_ECUDA, "factor level %d: %s", l, cudaGetErrorString(e));
     ++c->launches;
@@ -768,7 +785,7 @@ static la_status sweep_level(la_ctx* c, int l, int nsweeps) {
                                  c->adj ? (const CT*)c->adj_y : nullptr, Fine<R>::e(c), (const CT*)c->d_fac[0], col,
                                  c->d_status, c->stream);
       else
-        e = launch_sweep_coarse<R>(c->geo[l], c->d_sigma[l], c->d_tm, c->K, (const CT*)c->d_g[l], (CT*)c->d_e[l],
+        e = launch_sweep_coarse<R>(c->geo[l], sigma_of<R>(c, l), c->d_tm, c->K, (const CT*)c->d_g[l], (CT*)c->d_e[l],
                                    (const CT*)c->d_fac[l], col, c->d_status, c->stream);
       if (e != cudaSuccess) return fail(c, LA_ECUDA, "sweep level %d colour %d: %s", l, col, cudaGetErrorString(e));
     }
@@ -816,7 +833,7 @@ static la_status vcycle(la_ctx* c, int l) {
     c->launches += 2;
     sfine = Fine<R>::s(c);
   } else {
-    cudaError_t ge = launch_gresid_tiles<R>(c->geo[l], c->d_sigma[l], c->d_tm, c->K, (const CT*)c->d_g[l],
+    cudaError_t ge = launch_gresid_tiles<R>(c->geo[l], sigma_of<R>(c, l), c->d_tm, c->K, (const CT*)c->d_g[l],
                                             (const CT*)c->d_e[l], (CT*)c->d_sl[l], c->stream);
     if (ge != cudaSuccess) return fail(c, LA_ECUDA, "coarse residual level %d: %s", l, cudaGetErrorString(ge));
     ++c->launches;

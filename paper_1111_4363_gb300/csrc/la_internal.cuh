@@ -246,6 +246,7 @@ int norm_blocks(int np);
 void launch_advance(int np, const TimeMats* tm, const double2* c, double2* psi, cudaStream_t s);
 void launch_axpy_c64_to_c128(long long n, const float2* x, double2* y, cudaStream_t s);
 void launch_c128_to_c64(long long n, const double2* x, float2* y, cudaStream_t s);
+void launch_f64_to_f32(long long n, const double* x, float* y, cudaStream_t s);
 void launch_scale_c128(long long n, double a, const double2* x, double2* y, cudaStream_t s);
 void launch_trial(long long n, const double* a, const double2* h0, const double2* h1, const double2* h2, double2* c,
                   cudaStream_t s);
@@ -275,14 +276,14 @@ void launch_galerkin_coarse(const LevelGeom& fine, const double* sigma_f, const 
                             cudaStream_t s);
 // subvolume factorisation and sweeps (dispatch over the padded subvolume size)
 template <typename R>
-cudaError_t launch_factor(const LevelGeom& L, const FineOp* fine, const double* sigma, const TimeMats* tm,
+cudaError_t launch_factor(const LevelGeom& L, const FineOp* fine, const R* sigma, const TimeMats* tm,
                           typename C2<R>::T* factors, int* status, cudaStream_t s);
 template <typename R>
 cudaError_t launch_sweep_fine(const LevelGeom& L, const FineOp& g, const TimeMats* tm, int K,
                               const typename C2<R>::T* f, const typename C2<R>::T* yx, typename C2<R>::T* c,
                               const typename C2<R>::T* factors, int colour, int* status, cudaStream_t s);
 template <typename R>
-cudaError_t launch_gresid_tiles(const LevelGeom& L, const double* sigma, const TimeMats* tm, int K,
+cudaError_t launch_gresid_tiles(const LevelGeom& L, const R* sigma, const TimeMats* tm, int K,
                                 const typename C2<R>::T* gvec, const typename C2<R>::T* e, typename C2<R>::T* out,
                                 cudaStream_t s);
 // square local form (finest level, FP64): LU factors with row permutations, red-black sweeps
@@ -291,7 +292,7 @@ cudaError_t launch_factor_square(const LevelGeom& L, const FineOp& g, const Time
 cudaError_t launch_sweep_square(const LevelGeom& L, const FineOp& g, const TimeMats* tm, int K, const double2* f,
                                 double2* c, const double2* lu, const int* perm, int colour, cudaStream_t s);
 template <typename R>
-cudaError_t launch_sweep_coarse(const LevelGeom& L, const double* sigma, const TimeMats* tm, int K,
+cudaError_t launch_sweep_coarse(const LevelGeom& L, const R* sigma, const TimeMats* tm, int K,
                                 const typename C2<R>::T* gvec, typename C2<R>::T* e,
                                 const typename C2<R>::T* factors, int colour, int* status, cudaStream_t s);
 
