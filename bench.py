@@ -37,19 +37,17 @@ import numpy as np  # noqa: E402
 from paper_1111_4363_gb300 import workloads as wl  # noqa: E402
 
 METRIC = "spacetime unknowns relaxed/s"
-# DRAM bytes (read + write) per finest-level subvolume from one ncu capture of the current kernels
-# (profiles/k_sweep_fine_2d_softcore_128x128_fp64.md, profiles/k_factor_2d_softcore_128x128_fp64.md),
-# scaled to a launch by the number of subvolumes it processes.  Set to None when a kernel changes.
-# (kernel class, precision) -> DRAM bytes (read + write) per finest-level subvolume, from one ncu capture of
-# the 2D 256x256 workload: the finest k_factor launch (4096 subvolumes) and one full k_sweep_fine sweep
-# (four colour launches, 4096 subvolumes)
+# (kernel class, precision) -> DRAM bytes (read + write) per finest-level subvolume of the current kernels,
+# from one-pass ncu captures of full-size launches, scaled to a launch by the subvolumes it processes
+# (set to None when a kernel changes):
+# - 2D 256x256 FP64: the finest k_factor launch (4096 subvolumes) and one full k_sweep_fine sweep (four
+#   colour launches), profiles/dram_2d_softcore_256x256_fp64.md
+# - 3D 128^3 complex64: one k_factor_wide launch (32768 subvolumes of 256 unknowns) and one full wide
+#   sweep (eight colour launches of 4096), profiles/dram_3d_hydrogen_128x128x128_mixed.md
 NCU_BYTES_PER_SUBVOLUME = {("factor", 0): (867072 + 287257600) / 4096,
-                           ("sweep", 0): (391391488 + 2344192) / 4096,
-                           # 3D 32^3 (512 subvolumes of 256 unknowns per launch, 64 per colour launch),
-                           # complex64: profiles/k_factor_wide_3d_hydrogen_32x32x32_mixed.md and
-                           # profiles/k_sweep_fine_wide_3d_hydrogen_32x32x32_mixed.md
-                           ("factor_wide", 1): (623872 + 83455744) / 512,
-                           ("sweep_wide", 1): 19529984 / 64}
+                           ("sweep", 0): (390778880 + 216064) / 4096,
+                           ("factor_wide", 1): (34818816 + 9068101376) / 32768,
+                           ("sweep_wide", 1): (10943546368 + 56069376) / 32768}
 FP64_PEAK_TFLOPS = 152 * 4 * 2070e6 / 1e12   # 152 SMs x 4 FP64 flop/clk/SM x 2070 MHz (derived)
 FP32_PEAK_TFLOPS = 152 * 256 * 2070e6 / 1e12  # 152 SMs x 128 FP32 lanes x 2 flop (FMA) x 2070 MHz (derived)
 L2_BYTES = 129 * 2 ** 20
@@ -266,8 +264,9 @@ def dominant_roofline(prof, w, precision, ms_total, traffic_ok, peaks=None):
     kms = {"factor_per_launch": round(fac_ms, 4), "sweep_full": round(swp_ms_full, 4),
            "factor_share": round(prof["ms_factor"] / max(ms_total, 1e-9), 3),
            "sweep_share": round(prof["ms_sweep"] / max(ms_total, 1e-9), 3)}
-    tnote = ("DRAM read+write bytes of this kernel per launch, from one ncu capture of the same kernel on the "
-             "32^3 case scaled by the subvolumes a launch processes" if wide else
+    tnote = ("DRAM read+write bytes of this kernel per launch: one ncu capture of the same kernel at 128^3 (a "
+             "factorisation launch; a full sweep of eight colour launches), per subvolume times the subvolumes "
+             "of a launch" if wide else
              "DRAM read+write bytes of this kernel per launch from one ncu capture of this workload")
     if precision == 1 and cls == "sweep":
         # the complex64 sweep streams the factor store: HBM roofline on its compulsory bytes, every
