@@ -642,6 +642,26 @@ __device__ __forceinline__ void cp_async_elem(double2* sdst, const double2* gsrc
                : "memory");
 }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+// the same with zero fill (nothing read) where valid is false
+__device__ __forceinline__ void cp_async_elem_zf(float2* sdst, const float2* gsrc, bool valid) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"((unsigned)__cvta_generic_to_shared(sdst)),
+               "l"(gsrc), "r"(valid ? 8 : 0)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_elem_zf(double2* sdst, const double2* gsrc, bool valid) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"((unsigned)__cvta_generic_to_shared(sdst)),
+               "l"(gsrc), "r"(valid ? 16 : 0)
+               : "memory");
+}
+// one real value
+__device__ __forceinline__ void cp_async_real(float* sdst, const float* gsrc) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"((unsigned)__cvta_generic_to_shared(sdst)), "l"(gsrc)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_real(double* sdst, const double* gsrc) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"((unsigned)__cvta_generic_to_shared(sdst)), "l"(gsrc)
+               : "memory");
+}
 
 // Shared-memory layout of the wide factorisation (bytes), for the padded size npad.
 // Rows of the two shared-memory panels are padded so that the transposed stores of the block row and the
@@ -1600,16 +1620,16 @@ __device__ inline void coarse_rhs(const LevelGeom& L, const R* __restrict__ sigm
   const int nbox = box5_count(L.dim);
   const SubvolDiv dv(L, e);
   for (int i = tid; i < LA_NPAIR * KK; i += nthr) S.P[i] = (R)tm->P[i / KK][i % KK];
+  // e on U + 2 (zero outside the grid) and the stencils of U's points reach shared memory by cp.async,
+  // every copy of a thread in flight at once instead of one dependent load per loop trip
   for (int t = tid; t < nbc * K; t += nthr) {
     int i, m;
     dv.item(t, i, m);
     int lx, ly, lz;
     SubvolDiv::coords(i, dv.c0, dv.c1, lx, ly, lz);
     const int gx = oc[0] + lx, gy = oc[1] + ly, gz = oc[2] + lz;
-    CT v = mkc<CT>(0, 0);
-    if (gx >= 0 && gy >= 0 && gz >= 0 && gx < L.n[0] && gy < L.n[1] && gz < L.n[2])
-      v = ev[(size_t)((gz * L.n[1] + gy) * L.n[0] + gx) * K + m];
-    S.E[t] = v;
+    const bool in = gx >= 0 && gy >= 0 && gz >= 0 && gx < L.n[0] && gy < L.n[1] && gz < L.n[2];
+    cp_async_elem_zf(S.E + t, in ? ev + (size_t)((gz * L.n[1] + gy) * L.n[0] + gx) * K + m : ev, in);
   }
   const int per_pt = LA_NPAIR * nbox;
   for (int t = tid; t < npts * per_pt; t += nthr) {
@@ -1617,8 +1637,9 @@ __device__ inline void coarse_rhs(const LevelGeom& L, const R* __restrict__ sigm
     int lx, ly, lz;
     SubvolDiv::coords(i, dv.u0, dv.u1, lx, ly, lz);
     const int p = ((o[2] + lz) * L.n[1] + (o[1] + ly)) * L.n[0] + (o[0] + lx);
-    S.Sg[t] = (R)sigma[(size_t)p * per_pt + w];
+    cp_async_real(S.Sg + t, sigma + (size_t)p * per_pt + w);
   }
+  cp_async_wait_all();
   __syncthreads();
   // u[i][kk][n] = sum_o Sigma_kk[p_i][o] e[p_i + o][n]
   const int ry = L.dim > 1 ? 2 : 0, rz = L.dim > 2 ? 2 : 0;
