@@ -206,27 +206,30 @@ __global__ void __launch_bounds__(256) k_mresid(FineOp g, const TimeMats* __rest
   if (p < np) {
     int x, y, z;
     pcoords(g, p, x, y, z);
-    CT cp[K], hc[K], r[K];
-    apply_H<CT, RR, K>(g, c, p, x, y, z, cp, hc);
-    const RR xl = (RR)fine_x(g, x, y, z);
+    CT r[K];
     if (f) load_k<CT, K>(f, p, r);
     else {
 #pragma unroll
       for (int m = 0; m < K; ++m) r[m] = cmk<CT>(0, 0);
     }
+    if (c) {   // c absent: c = 0 and r = f, with no stencil to apply
+      CT cp[K], hc[K];
+      apply_H<CT, RR, K>(g, c, p, x, y, z, cp, hc);
+      const RR xl = (RR)fine_x(g, x, y, z);
 #pragma unroll
-    for (int m = 0; m < K; ++m) {
-      RR qr = 0, qi = 0, ur = 0, ui = 0, er = 0, ei = 0;
+      for (int m = 0; m < K; ++m) {
+        RR qr = 0, qi = 0, ur = 0, ui = 0, er = 0, ei = 0;
 #pragma unroll
-      for (int n = 0; n < K; ++n) {
-        const RR q = Qb[m * K + n], u = Ub[m * K + n], e = Eb[m * K + n];
-        qr += q * cp[n].x; qi += q * cp[n].y;
-        ur += u * hc[n].x; ui += u * hc[n].y;
-        er += e * cp[n].x; ei += e * cp[n].y;
+        for (int n = 0; n < K; ++n) {
+          const RR q = Qb[m * K + n], u = Ub[m * K + n], e = Eb[m * K + n];
+          qr += q * cp[n].x; qi += q * cp[n].y;
+          ur += u * hc[n].x; ui += u * hc[n].y;
+          er += e * cp[n].x; ei += e * cp[n].y;
+        }
+        // i (qr + i qi) = -qi + i qr
+        r[m].x = r[m].x - (-qi - ur - xl * er);
+        r[m].y = r[m].y - (qr - ui - xl * ei);
       }
-      // i (qr + i qi) = -qi + i qr
-      r[m].x = r[m].x - (-qi - ur - xl * er);
-      r[m].y = r[m].y - (qr - ui - xl * ei);
     }
     CT zv[K];
 #pragma unroll

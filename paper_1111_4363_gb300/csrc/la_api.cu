@@ -865,11 +865,13 @@ static la_status vcycle(la_ctx* c, int l) {
   return sweep_level<R>(c, l, nu2);
 }
 
-// N of the current FP64 iterate into h_N[slot] (stores r~ = f~ - M~ c in d_r); enqueue only.
-static la_status action_enqueue(la_ctx* c, int slot = 0) {
+// N of the current FP64 iterate into h_N[slot] (stores r~ = f~ - M~ c in d_r); enqueue only.  zero_c:
+// the iterate is known to be c = 0, so r~ = f~ and no stencil is applied.
+static la_status action_enqueue(la_ctx* c, int slot = 0, bool zero_c = false) {
   cudaEvent_t e0, e1;
-  const bool timed = prof_begin(c, &e0, &e1);
-  launch_mresid<double>(c->fine, c->d_tm, c->K, c->d_f, c->d_c, c->d_r, nullptr, c->d_partials, c->nparts, c->stream);
+  const bool timed = !zero_c && prof_begin(c, &e0, &e1);   // the stencil launches carry the roofline
+  launch_mresid<double>(c->fine, c->d_tm, c->K, c->d_f, zero_c ? nullptr : c->d_c, c->d_r, nullptr, c->d_partials,
+                        c->nparts, c->stream);
   if (timed) prof_end(c, e0, e1, 1, resid_bytes(c, sizeof(double2), true));
   launch_norm_final(c->d_partials, c->nparts, c->nscale, c->d_N + slot, c->stream);
   c->launches += 2;
@@ -992,7 +994,7 @@ static la_status hist_push(la_ctx* c) {
 // extrapolated trial into d_c and its action into h_N[0].  d_r ends as the residual of d_c.
 static la_status seed_enqueue(la_ctx* c, bool use_trial, bool* tried) {
   LA_CUDA(c, cudaMemsetAsync(c->d_c, 0, sizeof(double2) * (size_t)c->nunk0, c->stream));
-  LA_TRY(action_enqueue(c, 1));
+  LA_TRY(action_enqueue(c, 1, true));
   *tried = false;
   if (use_trial && c->cfg.trial > 0 && c->nhist > 0) {
     const int T = c->cfg.trial, q = c->nhist;
