@@ -756,14 +756,12 @@ __device__ __forceinline__ typename C2<R>::T wide_entry(const WideRow<R>& w, int
 // Rows 16 J' + q of block column J' assembled and updated with the finished block columns Kb < kb_end:
 // acc[c] = G[r][16 J' + c0 + c] - sum_{k < 16 kb_end} L[r][k] conj(L[16 J' + c0 + c][k]), the finished rows
 // read back from the factor store, the block row J' transposed in sRow.
+// acc[c] = G[r][16 Jc + c0 + c], c < CPT (zero for a block beyond the band).
 template <typename R, int CPT>
-__device__ __forceinline__ void wide_partial_update(int Jc, int kb_end, int band, int r, int c0, int n,
-                                                    const FastDiv& dK, int K, const typename C2<R>::T* __restrict__ F,
-                                                    const WideTables<R>& T, const typename C2<R>::T* sRow,
-                                                    typename C2<R>::T* acc) {
+__device__ __forceinline__ void wide_assemble(int Jc, int band, int r, int c0, int n, const FastDiv& dK, int K,
+                                              const WideTables<R>& T, typename C2<R>::T* acc) {
   typedef typename C2<R>::T CT;
-  const int I = r >> 4;
-  if (I - Jc > band) {   // a block beyond the band: zero, nothing to assemble or update
+  if ((r >> 4) - Jc > band) {
 #pragma unroll
     for (int q = 0; q < CPT; ++q) acc[q] = mkc<CT>(0, 0);
     return;
@@ -771,6 +769,16 @@ __device__ __forceinline__ void wide_partial_update(int Jc, int kb_end, int band
   const WideRow<R> w = wide_row<R>(r, dK, K, T.sX);
 #pragma unroll
   for (int q = 0; q < CPT; ++q) acc[q] = wide_entry<R>(w, LA_BLK * Jc + c0 + q, n, dK, K, T);
+}
+
+// acc (the assembled entries) -= sum over the finished block columns Kb < kb_end inside the band.
+template <typename R, int CPT>
+__device__ __forceinline__ void wide_partial_update(int Jc, int kb_end, int band, int r, int c0,
+                                                    const typename C2<R>::T* __restrict__ F,
+                                                    const typename C2<R>::T* sRow, typename C2<R>::T* acc) {
+  typedef typename C2<R>::T CT;
+  const int I = r >> 4;
+  if (I - Jc > band) return;   // a block beyond the band: zero, nothing to update
   // the blocks (I, Kb) with I - Kb > band are zero: the sum starts at Kb = I - band
   const int kb_begin = I - band > 0 ? I - band : 0;
   for (int h = 2 * kb_begin; h < 2 * kb_end; ++h) {   // half a finished block row (8 columns k) at a time
@@ -914,13 +922,15 @@ __device__ __forceinline__ void wide_column_step(int J, int band, int n, const F
       const int Kb = t >> 8, w = t & 255, c = w >> 4, kk = w & 15;
       cp_async_elem(S.sRow + (Kb * LA_BLK + kk) * kRowStride + c, F + (size_t)tri_index(J + 1, Kb) * 256 + w);
     }
+    // the entries of G are assembled while the copies are in flight
+    if (own) wide_assemble<R, CPT>(J + 1, band, r_own, c0, n, dK, K, S.tables(), acc);
     cp_async_wait_all();
     wide_bar();
-    if (own) wide_partial_update<R, CPT>(J + 1, J, band, r_own, c0, n, dK, K, F, S.tables(), S.sRow, acc);
+    if (own) wide_partial_update<R, CPT>(J + 1, J, band, r_own, c0, F, S.sRow, acc);
   }
   __syncthreads();
   if (tid < 32 && own)   // warp 0's rows of block column 1 (no finished column before it)
-    wide_partial_update<R, CPT>(J + 1, 0, band, r_own, c0, n, dK, K, F, S.tables(), S.sRow, acc);
+    wide_assemble<R, CPT>(J + 1, band, r_own, c0, n, dK, K, S.tables(), acc);
   // rows below the diagonal block, one row per thread: L[r][c] = sum_{k <= c} A[r][k] conj(inv(L_JJ)[c][k])
   // (the row's entries in registers, sInvT's rows read as 16-byte pairs), written to the factor store and
   // back to the row in place; the rows of the block (J+1, J) also go to sBT for the update below
