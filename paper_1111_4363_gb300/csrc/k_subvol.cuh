@@ -672,7 +672,6 @@ constexpr int kRowStride = LA_BLK + 2;
 __host__ __device__ constexpr size_t wide_factor_smem(int npad, size_t csize, size_t rsize) {
   return csize * ((size_t)(npad - LA_BLK) * kRowStride     // block row J+1, transposed (then the block (J+1, J))
                   + (size_t)npad * kWideStride             // the block column's rows at their absolute index
-                  + LA_BLK * kWideStride                   // inv(L_JJ) being built
                   + 256)                                   // inv(L_JJ)^dagger, [k][c]
          + rsize * (LA_NPAIR * LA_KMAX * LA_KMAX + 3 * kWidePtsMax + LA_BLK) + sizeof(int) * kWidePtsMax
          + csize * (size_t)kWidePtsMax * kHHStride      // (H, H^2) of every point pair
@@ -819,7 +818,6 @@ struct WideSmem {
   CT* sPan;   // [NPAD][17]: rows of the current block column at their absolute row index
   CT* sBT;    // [16][17]: sBT[k][c] = L[16 (J+1) + c][16 J + k] (the block (J+1, J)); in sRow's space
   CT* sInvT;  // [16][16]: sInvT[k][c] = conj(inv(L_JJ)[c][k])
-  CT* sXi;    // [16][17]: inv(L_JJ) being built
   CT* sHH;    // [64][65]: (H, H^2) of the point pairs
   R *sP, *sPd, *sD, *sX, *sN, *sPiv;
   int* sXYZ;
@@ -1001,8 +999,7 @@ k_factor_wide(LevelGeom L, FineOp g, const TimeMats* __restrict__ tm, typename C
   S.sRow = reinterpret_cast<CT*>(smem);
   S.sBT = S.sRow;   // written after the lookahead update has read sRow, read before sRow is refilled
   S.sPan = S.sRow + (size_t)(NPAD - LA_BLK) * kRowStride;
-  S.sXi = S.sPan + (size_t)NPAD * kWideStride;
-  S.sInvT = S.sXi + LA_BLK * kWideStride;
+  S.sInvT = S.sPan + (size_t)NPAD * kWideStride;
   S.sP = reinterpret_cast<R*>(S.sInvT + 256);
   S.sD = S.sP + LA_NPAIR * LA_KMAX * LA_KMAX;
   S.sX = S.sD + kWidePtsMax;
