@@ -46,7 +46,7 @@ METRIC = "spacetime unknowns relaxed/s"
 #   sweep (eight colour launches of 4096), profiles/dram_3d_hydrogen_128x128x128_mixed.md
 NCU_BYTES_PER_SUBVOLUME = {("factor", 0): (867072 + 287257600) / 4096,
                            ("sweep", 0): (390778880 + 216064) / 4096,
-                           ("factor_wide", 1): (34818816 + 9068101376) / 32768,
+                           ("factor_wide", 1): (33378560 + 9068625920) / 32768,
                            ("sweep_wide", 1): (10943546368 + 56069376) / 32768}
 FP64_PEAK_TFLOPS = 152 * 4 * 2070e6 / 1e12   # 152 SMs x 4 FP64 flop/clk/SM x 2070 MHz (derived)
 FP32_PEAK_TFLOPS = 152 * 256 * 2070e6 / 1e12  # 152 SMs x 128 FP32 lanes x 2 flop (FMA) x 2070 MHz (derived)
