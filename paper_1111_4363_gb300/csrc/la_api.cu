@@ -289,26 +289,6 @@ static bool build_time_constants(la_ctx* c) {
   return true;
 }
 
-// Block bandwidth of a finest-level subvolume factor (see LevelGeom::band).  G_UU couples two unknowns
-// only when their points are at most two grid steps apart (Manhattan), which in the subvolume's x-fastest
-// point order means point indices at most d_max apart; the Cholesky factor keeps that envelope.  Block
-// (I, J) holds the points floor(16 I / K) .. and .. floor((16 J + 15) / K), so it is zero when the
-// nearest two are more than d_max apart; the band is the largest I - J of a block that may be nonzero.
-static int fine_band_blocks(int dim, const int sub[3], int K, int nblk) {
-  int maxd = 0;
-  for (int dz = -2; dz <= 2; ++dz)
-    for (int dy = -2; dy <= 2; ++dy)
-      for (int dx = -2; dx <= 2; ++dx) {
-        if (abs(dx) + abs(dy) + abs(dz) > 2 || (dim < 2 && dy != 0) || (dim < 3 && dz != 0)) continue;
-        maxd = std::max(maxd, abs(dx + sub[0] * dy + sub[0] * sub[1] * dz));
-      }
-  int band = 0;
-  for (int d = 1; d < nblk; ++d)
-    for (int J = 0; J + d < nblk; ++J)
-      if ((LA_BLK * (J + d)) / K - (LA_BLK * J + LA_BLK - 1) / K <= maxd) band = d;
-  return std::min(std::max(band, 1), nblk - 1);   // at least the first subdiagonal (a wider band is exact too)
-}
-
 static int round_npad(int n) {
   const int sizes[8] = {16, 32, 48, 64, 96, 128, 192, 256};
   for (int s : sizes)

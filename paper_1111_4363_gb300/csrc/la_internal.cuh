@@ -209,6 +209,30 @@ __host__ inline int colour_count(const LevelGeom& L, int colour) {
   return c;
 }
 
+// Block bandwidth of a finest-level subvolume factor (LevelGeom::band).  G_UU couples two unknowns only
+// when their points are at most two grid steps apart (Manhattan), which in the subvolume's x-fastest
+// point order means point indices at most d_max apart; the Cholesky factor keeps that envelope.  Block
+// (I, J) holds the points floor(16 I / K) .. and .. floor((16 J + 15) / K), so it is zero when the
+// nearest two are more than d_max apart; the band is the largest I - J of a block that may be nonzero,
+// at least 1 (a wider band is exact too) and at most nblk - 1.
+__host__ inline int fine_band_blocks(int dim, const int sub[3], int K, int nblk) {
+  int maxd = 0;
+  for (int dz = -2; dz <= 2; ++dz)
+    for (int dy = -2; dy <= 2; ++dy)
+      for (int dx = -2; dx <= 2; ++dx) {
+        const int man = (dx < 0 ? -dx : dx) + (dy < 0 ? -dy : dy) + (dz < 0 ? -dz : dz);
+        if (man > 2 || (dim < 2 && dy != 0) || (dim < 3 && dz != 0)) continue;
+        const int d = dx + sub[0] * dy + sub[0] * sub[1] * dz;
+        if ((d < 0 ? -d : d) > maxd) maxd = d < 0 ? -d : d;
+      }
+  int band = 0;
+  for (int d = 1; d < nblk; ++d)
+    for (int J = 0; J + d < nblk; ++J)
+      if ((LA_BLK * (J + d)) / K - (LA_BLK * J + LA_BLK - 1) / K <= maxd) band = d;
+  if (band < 1) band = 1;
+  return band < nblk - 1 ? band : nblk - 1;
+}
+
 template <typename R> struct C2;
 template <> struct C2<double> { typedef double2 T; };
 template <> struct C2<float> { typedef float2 T; };

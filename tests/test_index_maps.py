@@ -6,12 +6,16 @@ host program with nvcc and run here, so no GPU is needed.
 - The colour classes the sweeps launch (2 colours per axis, the j-th CTA of a colour -> subvolume)
   and the subvolume boxes: every subvolume in exactly one colour, the boxes tile the grid, and two
   subvolumes of one colour are more than 2 points apart on some axis, so their unknowns share no
-  entry of the radius-2 normal operator (exact parallel block Gauss-Seidel, Sec. II)."""
+  entry of the radius-2 normal operator (exact parallel block Gauss-Seidel, Sec. II).
+- The block band the library gives the finest-level factors, against the restatement that
+  test_oracle_band.py pins on the oracle's own Cholesky factors."""
 import os
 import shutil
 import subprocess
 
 import pytest
+
+from test_oracle_band import band_blocks
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 HEADER = os.path.join(HERE, "..", "paper_1111_4363_gb300", "csrc", "la_internal.cuh")
@@ -154,6 +158,17 @@ int main() {
     const int d = 1 + (int)(rnd31() % 0x7ffffffeu);
     check_divisor(d, 64);
   }
+  // block band of the finest-level factors: one line per case, compared with the Python restatement
+  for (int dim = 1; dim <= 3; ++dim)
+    for (int sx = 1; sx <= 8; ++sx)
+      for (int sy = 1; sy <= (dim > 1 ? 8 : 1); ++sy)
+        for (int sz = 1; sz <= (dim > 2 ? 4 : 1); ++sz)
+          for (int K = 1; K <= 8; ++K) {
+            const int sub[3] = {sx, sy, sz}, n = sx * sy * sz * K;
+            if (n > 256) continue;
+            const int nblk = (n + LA_BLK - 1) / LA_BLK;
+            printf("band %d %d %d %d %d %d %d\n", dim, sx, sy, sz, K, nblk, la::fine_band_blocks(dim, sub, K, nblk));
+          }
   printf("fails %lld\n", fails);
   return fails != 0;
 }
@@ -172,3 +187,13 @@ def test_index_maps_on_the_host(tmp_path):
     out = subprocess.run([str(exe)], capture_output=True, text=True, timeout=300)
     assert out.returncode == 0, out.stdout
     assert out.stdout.strip().endswith("fails 0")
+    bands = [tuple(int(v) for v in line.split()[1:]) for line in out.stdout.splitlines()
+             if line.startswith("band ")]
+    assert len(bands) > 300
+    seen = {}
+    for dim, sx, sy, sz, K, nblk, band in bands:
+        want = min(max(band_blocks(dim, (sx, sy, sz), K, nblk), 1), nblk - 1)
+        assert band == want, (dim, sx, sy, sz, K, nblk, band, want)
+        seen[(dim, sx, sy, sz, K)] = band
+    # the finest levels the wide factorisation runs on: 4 x 4 x 4 and 8 x 8 points with K = 4
+    assert seen[(3, 4, 4, 4, 4)] == 8 and seen[(2, 8, 8, 1, 4)] == 4
