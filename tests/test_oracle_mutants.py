@@ -1,0 +1,301 @@
+"""Planted mistakes in the oracle, each of which one of its pins must catch.
+
+The oracle is trusted because the pins in test_oracle_*.py tie it to facts outside itself: closed
+forms of Secs. I and IV, a dense KKT system with explicit multipliers, the exact block minimiser of
+Sec. II, Galerkin optimality (Sec. III), scipy's adaptive quadrature, the Sec. V facts the paper
+prints.  This file checks that those pins can fail.  Each case plants one plausible mistake in the
+oracle -- a dropped term, a wrong sign, index or Jacobian, a transposed operand, a misread
+definition -- by patching one oracle function for the duration of the case (CPU only; the CUDA path
+is not involved), then runs the named pins and requires at least one of them to fail.  A pin that
+raises an AssertionError, or a linear-algebra error (a Cholesky factor that no longer exists),
+counts as failing; any other exception is a broken case and errors the test.
+"""
+import numpy as np
+import pytest
+import scipy.linalg as sla
+import scipy.sparse as sp
+
+import test_oracle_adjoint as pa
+import test_oracle_lfa as pl
+import test_oracle_relax as pr
+import test_oracle_square as pq
+import test_oracle_system as ps
+import test_oracle_timebasis as pt
+from oracle import legendre_elements as le
+from oracle import lfa, multigrid, relax, system
+from oracle import timebasis as tb
+
+
+def _wrap(mp, module, name, make):
+    """Replace module.name by make(original)."""
+    mp.setattr(module, name, make(getattr(module, name)))
+
+
+# ------------------------------------------------------------------------------ time basis
+def b_adds_p0(mp):
+    # b_n = P_n + (-1)^n P_0 instead of P_n - (-1)^n P_0 (the initial condition of Sec. I eliminated
+    # with the wrong sign); P_0 = 1, so the mistake adds 2 (-1)^n
+    def make(orig):
+        def b_functions(K, tau):
+            b, db = orig(K, tau)
+            return b + 2.0 * np.array([(-1.0) ** n for n in range(1, K + 1)])[:, None], db
+        return b_functions
+    _wrap(mp, tb, "b_functions", make)
+    return [(pt.test_ub_closed_form, 3, 0.7), (pt.test_qb_closed_form, 3)]
+
+
+def qb_derivative_on_test_function(mp):
+    def make(orig):
+        return lambda K, dt, nquad=None: (lambda m: (m[0], m[1].T, m[2]))(orig(K, dt, nquad))
+    _wrap(mp, tb, "static_matrices", make)
+    return [(pt.test_qb_closed_form, 4), (ps.test_scalar_matches_symbolic, 3)]
+
+
+def ub_without_jacobian(mp):
+    # int b_m b_n dtau without the dt/2 of dt = (dt/2) dtau
+    def make(orig):
+        return lambda K, dt, nquad=None: (lambda m: (m[0] * 2.0 / dt, m[1], m[2] * 2.0 / dt))(orig(K, dt, nquad))
+    _wrap(mp, tb, "static_matrices", make)
+    return [(pt.test_ub_closed_form, 3, 0.7), (ps.test_scalar_K1_closed_form, 0.5)]
+
+
+def envelope_two_sigma_squared(mp):
+    # exp(-(t - tc)^2 / (2 sigma^2)) instead of exp(-((t - tc) / sigma)^2)
+    def pulse_field(pulse, t):
+        t = np.asarray(t, dtype=np.float64)
+        e = np.zeros_like(t)
+        for a, w, tc, s in zip(pulse.amp, pulse.omega, pulse.t_center, pulse.sigma):
+            e = e + a * (np.exp(-(t - tc) ** 2 / (2 * s * s)) if s > 0 else 1.0) * np.sin(w * t)
+        return e
+    mp.setattr(tb, "pulse_field", pulse_field)
+    return [(pt.test_pulse_field_by_value,), (pt.test_field_matrices_against_adaptive_quadrature, 0.0)]
+
+
+def carrier_in_time_from_centre(mp):
+    # sin(omega (t - tc)) instead of sin(omega t)
+    def pulse_field(pulse, t):
+        t = np.asarray(t, dtype=np.float64)
+        e = np.zeros_like(t)
+        for a, w, tc, s in zip(pulse.amp, pulse.omega, pulse.t_center, pulse.sigma):
+            e = e + a * (np.exp(-((t - tc) / s) ** 2) if s > 0 else 1.0) * np.sin(w * (t - tc))
+        return e
+    mp.setattr(tb, "pulse_field", pulse_field)
+    return [(pt.test_pulse_field_by_value,), (pt.test_field_matrices_against_adaptive_quadrature, 4.35)]
+
+
+def step_time_centred_at_t0(mp):
+    # t = t0 + tau dt/2 instead of t0 + (tau + 1) dt/2
+    def make(orig):
+        return lambda K, dt, t0, field, nquad=None: orig(K, dt, t0 - 0.5 * dt, field, nquad)
+    _wrap(mp, tb, "field_matrices", make)
+    return [(pt.test_field_matrices_constant_and_linear,), (pt.test_field_matrices_against_adaptive_quadrature, 0.0)]
+
+
+def component_field_keeps_its_amplitude(mp):
+    # dE/da_k taken as a_k E_k instead of the unit-amplitude E_k
+    def make(orig):
+        return lambda pulse, k, t: pulse.amp[k] * orig(pulse, k, t)
+    _wrap(mp, tb, "pulse_component_field", make)
+    return [(pt.test_pulse_field_by_value,), (pa.test_amplitude_gradient_matches_finite_differences, 1)]
+
+
+def end_value_without_p0_part(mp):
+    # phi(t0 + dt) = psi0 + sum_n c_n, forgetting that b_n(+1) = 1 - (-1)^n
+    mp.setattr(tb, "end_values", lambda K: np.ones(K))
+    return [(ps.test_scalar_K1_closed_form, 0.5), (pt.test_end_values,)]
+
+
+# ------------------------------------------------------------------------------ the step's system
+def kinetic_without_half(mp):
+    _wrap(mp, system, "kinetic", lambda orig: lambda prob: (2.0 * orig(prob)).tocsr())
+    return [(ps.test_kkt_with_multipliers, 8, 2, 0.0), (ps.test_eigen_expansion_and_norm_drift,)]
+
+
+def _patch_time_matrices(mp, change):
+    def make(orig):
+        return lambda prob, t0: change(*orig(prob, t0))
+    _wrap(mp, system, "time_matrices", make)
+
+
+def time_derivative_sign(mp):
+    # -i Q instead of i Q in the stationarity rows (Eq. stationaryphase)
+    _patch_time_matrices(mp, lambda Ub, Qb, Ub0, Eb, Eb0: (Ub, -Qb, Ub0, Eb, Eb0))
+    return [(ps.test_scalar_K1_closed_form, 0.5), (ps.test_kkt_with_multipliers, 8, 2, 0.0)]
+
+
+def dipole_coupling_sign(mp):
+    _patch_time_matrices(mp, lambda Ub, Qb, Ub0, Eb, Eb0: (Ub, Qb, Ub0, -Eb, -Eb0))
+    return [(ps.test_kkt_with_multipliers, 8, 2, 0.3)]
+
+
+def initial_state_field_term_dropped(mp):
+    # f without the x_q Eb0 psi0 part of the initial condition
+    _patch_time_matrices(mp, lambda Ub, Qb, Ub0, Eb, Eb0: (Ub, Qb, Ub0, Eb, 0.0 * Eb0))
+    return [(ps.test_kkt_with_multipliers, 8, 2, 0.3)]
+
+
+def dual_weight_without_inverse(mp):
+    def make(orig):
+        def weight_matrix(prob, Ub, weight="dual"):
+            if weight == "dual":
+                return (sp.kron(sp.identity(prob.npoints), Ub) / prob.vol).tocsr()
+            return orig(prob, Ub, weight)
+        return weight_matrix
+    _wrap(mp, system, "weight_matrix", make)
+    return [(ps.test_dual_weight_is_test_basis_invariant,)]
+
+
+def stencil_row_without_potential(mp):
+    def make(orig):
+        def hamiltonian_row(prob, q):
+            cols, vals = orig(prob, q)
+            vals = vals.copy()
+            vals[0] -= prob.V0[q]
+            return cols, vals
+        return hamiltonian_row
+    _wrap(mp, system, "hamiltonian_row", make)
+    return [(ps.test_pointwise_residual_matches_the_assembled_system, "2d")]
+
+
+def action_norm_without_conjugate(mp):
+    # r^T W r instead of r^dagger W r (Eq. residnorm)
+    mp.setattr(system, "action_norm", lambda r, W: float(np.real(np.dot(r, W @ r))))
+    return [(ps.test_action_norm_is_nonnegative_and_zero_at_solution,), (pr.test_block_update_minimises_N_over_the_block,)]
+
+
+# ------------------------------------------------------------------------------ relaxation (Sec. II)
+def checkerboard_colouring(mp):
+    # two colours by the parity of the block-index sum: right for M's radius-1 rows, wrong for the
+    # radius-2 normal operator G = M^dagger W M
+    def make(orig):
+        def subvolumes(shape, sub):
+            nb = relax.block_counts(shape, sub)
+            out = orig(shape, sub)
+            return [(int(sum(np.unravel_index(b, nb))) % 2, pts) for b, (_, pts) in enumerate(out)]
+        return subvolumes
+    _wrap(mp, relax, "subvolumes", make)
+    return [(pr.test_colouring_valid_every_level, "dual")]
+
+
+def residual_once_per_sweep(mp):
+    # every colour updated from the residual taken at the start of the sweep (Jacobi across colours)
+    def sweep(self, x, g, after_colour=None):
+        s = g - self.G @ x
+        updates = [(idx, sla.cho_solve(fac, s[idx])) for _, idx, fac in self.blocks]
+        for colour in range(self.ncolours):
+            for (col, _, _), (idx, d) in zip(self.blocks, updates):
+                if col == colour:
+                    x[idx] += d
+            if after_colour is not None:
+                after_colour(colour)
+    mp.setattr(relax.BlockRelaxation, "sweep", sweep)
+    return [(pr.test_action_never_increases, "dual"), (pr.test_2d_vcycle_converges_to_direct_solution,)]
+
+
+def local_solve_with_transpose(mp):
+    # G_UU^T (= conj G_UU for the Hermitian G) factored instead of G_UU
+    def make(orig):
+        def __init__(self, G, shape, sub, K):
+            orig(self, G, shape, sub, K)
+            self.blocks = [(col, idx, sla.cho_factor(self.G[idx][:, idx].toarray().T, lower=True))
+                           for col, idx, _ in self.blocks]
+        return __init__
+    _wrap(mp, relax.BlockRelaxation, "__init__", make)
+    return [(pr.test_single_block_update_is_the_blockwise_minimiser,), (pr.test_block_update_minimises_N_over_the_block,)]
+
+
+# ------------------------------------------------------------------------------ multigrid (Sec. III)
+def interpolation_from_far_neighbour(mp):
+    # fine 2J <- 3/4 c_J + 1/4 c_{J+1} (and 2J+1 from c_{J-1}): the 1/4 weight on the wrong side
+    def interpolation_1d(nc):
+        rows, cols, vals = [], [], []
+        for J in range(nc):
+            for fi, nb in ((2 * J, J + 1), (2 * J + 1, J - 1)):
+                rows.append(fi); cols.append(J); vals.append(0.75)
+                if 0 <= nb < nc:
+                    rows.append(fi); cols.append(nb); vals.append(0.25)
+        return sp.csr_matrix((vals, (rows, cols)), shape=(2 * nc, nc))
+    mp.setattr(multigrid, "interpolation_1d", interpolation_1d)
+    return [(pr.test_fd_interpolation_reproduces_linear_functions,)]
+
+
+def coarse_operator_quartered(mp):
+    # the Galerkin operator I^T G I divided by 4, the factor a rediscretisation on a grid of twice the
+    # spacing would carry for the kinetic term: every coarse correction comes out four times too large
+    def make(orig):
+        def __init__(self, G0, shape0, K, sub, levels, *args, **kw):
+            orig(self, G0, shape0, K, sub, levels, *args, **kw)
+            for l in range(1, self.L):
+                self.G[l] = (0.25 * self.G[l]).tocsr()
+                R = self.relax[l]
+                R.G = self.G[l]
+                R.blocks = [(col, idx, (0.5 * c, low)) for col, idx, (c, low) in R.blocks]   # chol(G/4) = chol(G)/2
+        return __init__
+    _wrap(mp, multigrid.Hierarchy, "__init__", make)
+    return [(pr.test_action_never_increases, "dual")]
+
+
+# ------------------------------------------------------------------------------ square form, elements, maps
+def square_solve_with_transpose(mp):
+    def square_block_update(M, f, x, idx):
+        M = M.tocsr()
+        return np.linalg.solve(M[idx][:, idx].toarray().T, f[idx] - M[idx] @ x)
+    mp.setattr(relax, "square_block_update", square_block_update)
+    return [(pq.test_square_update_zeroes_the_block_residual,)]
+
+
+def element_children_swapped(mp):
+    # the left child's interpolation rows taken from the right child
+    def make(orig):
+        def interpolation(nmax):
+            E = orig(nmax)
+            return np.vstack([E[nmax + 1:], E[:nmax + 1]])
+        return interpolation
+    _wrap(mp, le, "interpolation", make)
+    return [(pr.test_legendre_element_transfers, 3)]
+
+
+def lfa_derivative_on_test_function(mp):
+    def make(orig):
+        return lambda nx, nt: (lambda m: (m[0], m[1], m[2].T, m[3]))(orig(nx, nt))
+    _wrap(mp, lfa, "element_matrices", make)
+    return [(pl.test_element_matrices_closed_forms, 3, 3), (pl.test_dimensionless_rows_and_their_scaling, 2.0, 2.0, 0.0)]
+
+
+def lfa_kinetic_sign(mp):
+    _wrap(mp, lfa, "element_operator", lambda orig: lambda nx, nt, kappa, nu: orig(nx, nt, -kappa, nu))
+    return [(pl.test_dimensionless_rows_and_their_scaling, 0.3, 0.05, -1.7)]
+
+
+def lfa_residual_sign(mp):
+    # relaxing with r = +A C instead of the residual -A C of Eq. actionresidual
+    solve = lfa.constrained_solve
+    mp.setattr(lfa, "relax", lambda A, B, C, solver="null": C + solve(A, B, A @ C, solver))
+    return [(pl.test_unconstrained_relaxation_is_the_exact_solve,)]
+
+
+MUTANTS = [
+    b_adds_p0, qb_derivative_on_test_function, ub_without_jacobian, envelope_two_sigma_squared,
+    carrier_in_time_from_centre, step_time_centred_at_t0, component_field_keeps_its_amplitude,
+    end_value_without_p0_part, kinetic_without_half, time_derivative_sign, dipole_coupling_sign,
+    initial_state_field_term_dropped, dual_weight_without_inverse, stencil_row_without_potential,
+    action_norm_without_conjugate, checkerboard_colouring, residual_once_per_sweep,
+    local_solve_with_transpose, interpolation_from_far_neighbour, coarse_operator_quartered,
+    square_solve_with_transpose, element_children_swapped, lfa_derivative_on_test_function,
+    lfa_kinetic_sign, lfa_residual_sign,
+]
+
+
+def _fails(pin, *args):
+    try:
+        pin(*args)
+    except (AssertionError, np.linalg.LinAlgError):
+        return True
+    return False
+
+
+@pytest.mark.parametrize("plant", MUTANTS, ids=[m.__name__ for m in MUTANTS])
+def test_a_pin_catches_the_planted_mistake(plant, monkeypatch):
+    pins = plant(monkeypatch)
+    caught = [pin.__name__ for pin, *args in pins if _fails(pin, *args)]
+    assert caught, "no pin fails under the planted mistake: " + ", ".join(p.__name__ for p, *_ in pins)
