@@ -10,6 +10,8 @@ is not involved), then runs the named pins and requires at least one of them to 
 raises an AssertionError, or a linear-algebra error (a Cholesky factor that no longer exists),
 counts as failing; any other exception is a broken case and errors the test.
 """
+import types
+
 import numpy as np
 import pytest
 import scipy.linalg as sla
@@ -21,8 +23,8 @@ import test_oracle_relax as pr
 import test_oracle_square as pq
 import test_oracle_system as ps
 import test_oracle_timebasis as pt
+from oracle import adjoint, lfa, multigrid, relax, system
 from oracle import legendre_elements as le
-from oracle import lfa, multigrid, relax, system
 from oracle import timebasis as tb
 
 
@@ -163,6 +165,14 @@ def action_norm_without_conjugate(mp):
     return [(ps.test_action_norm_is_nonnegative_and_zero_at_solution,), (pr.test_block_update_minimises_N_over_the_block,)]
 
 
+def adjoint_solve_with_transpose(mp):
+    # mu_k = M_k^{-T} B^T lambda_{k+1} instead of M_k^{-dagger}: the adjoint module's sparse LU is
+    # handed M^T (the conjugate of the M^dagger it is given); the forward solves are untouched
+    real = adjoint.spla
+    mp.setattr(adjoint, "spla", types.SimpleNamespace(splu=lambda A: real.splu(A.conj().tocsc())))
+    return [(pa.test_amplitude_gradient_matches_finite_differences, 1), (pa.test_initial_state_gradient_matches_finite_differences,)]
+
+
 # ------------------------------------------------------------------------------ relaxation (Sec. II)
 def checkerboard_colouring(mp):
     # two colours by the parity of the block-index sum: right for M's radius-1 rows, wrong for the
@@ -279,7 +289,7 @@ MUTANTS = [
     carrier_in_time_from_centre, step_time_centred_at_t0, component_field_keeps_its_amplitude,
     end_value_without_p0_part, kinetic_without_half, time_derivative_sign, dipole_coupling_sign,
     initial_state_field_term_dropped, dual_weight_without_inverse, stencil_row_without_potential,
-    action_norm_without_conjugate, checkerboard_colouring, residual_once_per_sweep,
+    action_norm_without_conjugate, adjoint_solve_with_transpose, checkerboard_colouring, residual_once_per_sweep,
     local_solve_with_transpose, interpolation_from_far_neighbour, coarse_operator_quartered,
     square_solve_with_transpose, element_children_swapped, lfa_derivative_on_test_function,
     lfa_kinetic_sign, lfa_residual_sign,
