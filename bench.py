@@ -11,7 +11,7 @@ and in mixed precision, and the 512-grid batch in FP64 and mixed precision, each
 at the same tolerance, plus the FMA peaks of this GPU measured in the run.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--precision -1|0|1]
-                  [--workload 3d|3d-small|2d|2d-small|1d|2d-square|batched|3d-adjoint|lfa]
+                  [--workload 3d|3d-small|3d-mid|2d|2d-small|1d|2d-square|batched|3d-adjoint|lfa]
                   [--trial -1|0..3] [--headline-only]
 
 N > 1 runs N independent replicas (one propagation per rank, no collective: the path does not
@@ -72,6 +72,8 @@ def workload(name: str) -> wl.Workload:
         return dataclasses.replace(wl.hydrogen_3d(n=128, nsteps=400), **PRODUCTION_3D)
     if name == "3d-small":          # the same problem on 32^3, for ncu captures of single kernels
         return dataclasses.replace(wl.hydrogen_3d(n=32, nsteps=400), **PRODUCTION_3D)
+    if name == "3d-mid":            # on 64^3: one full wave of per-point kernels (1024 CTAs) for ncu
+        return dataclasses.replace(wl.hydrogen_3d(n=64, nsteps=400), **PRODUCTION_3D)
     if name == "2d-square":         # the paper's square local form (Sec. II), single level, red-black
         return dataclasses.replace(wl.softcore_2d(n=256, levels=1, nsteps=200), local_form="square", nu1=1, nu2=1,
                                    trial=3)
@@ -244,7 +246,7 @@ def workload_config(w, precision, ws):
 
 def default_precision(name: str) -> int:
     """The arithmetic a workload is specified in: the 3D workload runs FP64 with complex64 local solves."""
-    return 1 if name in ("3d", "3d-small") else 0
+    return 1 if name in ("3d", "3d-small", "3d-mid") else 0
 
 
 def dominant_roofline(prof, w, precision, ms_total, traffic_ok, peaks=None):
@@ -878,7 +880,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="3d",
-                    choices=["3d", "3d-small", "2d", "2d-small", "1d", "2d-square", "batched", "3d-adjoint", "lfa"])
+                    choices=["3d", "3d-small", "3d-mid", "2d", "2d-small", "1d", "2d-square", "batched", "3d-adjoint", "lfa"])
     ap.add_argument("--batch", type=int, default=512)
     ap.add_argument("--n3d", type=int, default=128)
     ap.add_argument("--precision", type=int, default=-1, choices=[-1, 0, 1],

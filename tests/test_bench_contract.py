@@ -63,6 +63,9 @@ def test_workloads_named_by_the_bench(bench):
     assert w.n[:2] == (256, 256) and w.nt == 6 and w.levels == 4 and w.sub[:2] == (4, 4)
     assert (w.nu1, w.nu2, w.trial) == (1, 2, 3)
     assert bench.workload("2d-small").n[:2] == (128, 128)
+    for name, n in (("3d", 128), ("3d-mid", 64), ("3d-small", 32)):
+        w = bench.workload(name)
+        assert w.n == (n, n, n) and w.nt == 4 and w.sub == (4, 4, 4) and bench.default_precision(name) == 1
 
 
 def test_factor_store_and_l2_note(bench):
