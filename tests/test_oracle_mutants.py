@@ -10,6 +10,7 @@ is not involved), then runs the named pins and requires at least one of them to 
 raises an AssertionError, or a linear-algebra error (a Cholesky factor that no longer exists),
 counts as failing; any other exception is a broken case and errors the test.
 """
+import dataclasses
 import types
 
 import numpy as np
@@ -159,6 +160,19 @@ def stencil_row_without_potential(mp):
     return [(ps.test_pointwise_residual_matches_the_assembled_system, "2d")]
 
 
+def laplacian_spacing_on_the_wrong_axis(mp):
+    # each axis's second difference divided by another axis's h^2 (the spacings taken in x-first order)
+    _wrap(mp, system, "laplacian", lambda orig: lambda shape, h: orig(shape, tuple(reversed(h))))
+    return [(ps.test_laplacian_eigenvalues_on_an_anisotropic_grid,)]
+
+
+def stencil_row_spacing_on_the_wrong_axis(mp):
+    def make(orig):
+        return lambda prob, q: orig(dataclasses.replace(prob, h=tuple(reversed(prob.h))), q)
+    _wrap(mp, system, "hamiltonian_row", make)
+    return [(ps.test_stencil_rows_on_an_anisotropic_grid,)]
+
+
 def action_norm_without_conjugate(mp):
     # r^T W r instead of r^dagger W r (Eq. residnorm)
     mp.setattr(system, "action_norm", lambda r, W: float(np.real(np.dot(r, W @ r))))
@@ -289,6 +303,7 @@ MUTANTS = [
     carrier_in_time_from_centre, step_time_centred_at_t0, component_field_keeps_its_amplitude,
     end_value_without_p0_part, kinetic_without_half, time_derivative_sign, dipole_coupling_sign,
     initial_state_field_term_dropped, dual_weight_without_inverse, stencil_row_without_potential,
+    laplacian_spacing_on_the_wrong_axis, stencil_row_spacing_on_the_wrong_axis,
     action_norm_without_conjugate, adjoint_solve_with_transpose, checkerboard_colouring, residual_once_per_sweep,
     local_solve_with_transpose, interpolation_from_far_neighbour, coarse_operator_quartered,
     square_solve_with_transpose, element_children_swapped, lfa_derivative_on_test_function,

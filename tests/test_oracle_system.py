@@ -236,3 +236,36 @@ def test_pointwise_residual_matches_the_assembled_system(kind):
     # c = 0 gives the right-hand side itself
     np.testing.assert_allclose(system.residual_at(prob, t0, psi0, np.zeros_like(c), pts),
                                f.reshape(-1, w.nt)[pts], rtol=0, atol=1e-14 * np.max(np.abs(f)))
+
+
+def anisotropic_problem():
+    """A 3D grid with a different extent and spacing on every axis (numpy order z, y, x)."""
+    shape, h = (4, 5, 7), (0.45, 0.7, 0.3)
+    rng = np.random.default_rng(11)
+    n = int(np.prod(shape))
+    return system.Problem(dim=3, shape=shape, h=h, K=2, dt=0.05, V0=rng.uniform(-1, 1, n),
+                          xlaser=rng.uniform(-1, 1, n), pulse=None)
+
+
+def test_laplacian_eigenvalues_on_an_anisotropic_grid():
+    """The Dirichlet second difference on n points of spacing h has eigenvalues
+    -(4 / h^2) sin^2(j pi / (2 (n + 1))), j = 1..n, and the grid Laplacian's are all sums of one per axis:
+    pins which spacing belongs to which axis."""
+    prob = anisotropic_problem()
+    got = np.sort(np.linalg.eigvalsh(system.laplacian(prob.shape, prob.h).toarray()))
+    per_axis = [-4.0 / h ** 2 * np.sin(np.arange(1, n + 1) * np.pi / (2 * (n + 1))) ** 2
+                for n, h in zip(prob.shape, prob.h)]
+    want = np.sort((per_axis[0][:, None, None] + per_axis[1][None, :, None] + per_axis[2][None, None, :]).ravel())
+    np.testing.assert_allclose(got, want, rtol=0, atol=1e-12 * np.max(np.abs(want)))
+
+
+def test_stencil_rows_on_an_anisotropic_grid():
+    """hamiltonian_row (the stencil form residual_at uses) equals the assembled T + diag(V0) row by row
+    on a grid whose axes all differ."""
+    prob = anisotropic_problem()
+    Hs = system.hamiltonian_operator(prob).toarray()
+    for q in range(prob.npoints):
+        cols, vals = system.hamiltonian_row(prob, q)
+        row = np.zeros(prob.npoints)
+        np.add.at(row, cols, vals)
+        np.testing.assert_allclose(row, Hs[q], rtol=0, atol=1e-12)
