@@ -1,7 +1,8 @@
 """Edge and degenerate cases of the CUDA path against the oracle (GB300 required): every size class
 of the time basis (K = 1, 2, 5, 8, including the largest subvolume of 128 unknowns), odd K in mixed
 precision (per-point complex64 kernels instead of the TMA-staged ones), a grid that is one
-subvolume, no laser field, a ragged 3D grid, zero steps and a zero initial state."""
+subvolume, no laser field, a ragged 3D grid, zero steps, a zero initial state and a different grid
+spacing on every axis."""
 import dataclasses
 
 import numpy as np
@@ -107,3 +108,20 @@ def test_zero_initial_state_stays_zero(precision):
     st, stats = ctx.step(psi, 3, 0.0, stats=True)
     assert np.count_nonzero(psi) == 0
     assert all(s[0] == 0 and s[3] == 0.0 for s in stats)
+
+
+ANISOTROPIC = {
+    # a different spacing, and extent, on every axis: the per-axis kinetic weights of the fine stencil,
+    # of the footprint residual, of the wide factorisation's (H, H^2) table and of the Galerkin levels
+    "2d_4x4_K6": lambda: dataclasses.replace(wl.softcore_2d(n=16, levels=2), n=(16, 12, 1), h=(0.2, 0.35, 1.0)),
+    "3d_2x2x2_K4": lambda: dataclasses.replace(small_3d(), h=(0.3, 0.45, 0.25)),
+    "3d_4x4x4_K4_wide": lambda: dataclasses.replace(wl.hydrogen_3d(n=8, nsteps=4, ncomp=4, sub=4), n=(16, 8, 8),
+                                                    h=(0.3, 0.45, 0.25), levels=2),
+}
+
+
+@pytest.mark.parametrize("name", list(ANISOTROPIC))
+def test_anisotropic_spacing(name):
+    c, c_ref, N, N_ref = fixed_cycles(ANISOTROPIC[name](), 2)
+    assert rel_l2(c, c_ref) < TOL64
+    assert N == pytest.approx(N_ref, rel=1e-9)
