@@ -1,8 +1,8 @@
 """Edge and degenerate cases of the CUDA path against the oracle (GB300 required): every size class
 of the time basis (K = 1, 2, 5, 8, including the largest subvolume of 128 unknowns), odd K in mixed
 precision (per-point complex64 kernels instead of the TMA-staged ones), a grid that is one
-subvolume, no laser field, a ragged 3D grid, zero steps, a zero initial state and a different grid
-spacing on every axis."""
+subvolume, no laser field, a ragged 3D grid, zero steps, a zero initial state, a different grid
+spacing on every axis and the laser coupled along y or z."""
 import dataclasses
 
 import numpy as np
@@ -123,5 +123,26 @@ ANISOTROPIC = {
 @pytest.mark.parametrize("name", list(ANISOTROPIC))
 def test_anisotropic_spacing(name):
     c, c_ref, N, N_ref = fixed_cycles(ANISOTROPIC[name](), 2)
+    assert rel_l2(c, c_ref) < TOL64
+    assert N == pytest.approx(N_ref, rel=1e-9)
+
+
+def strong_pulse(axis):
+    """Two components, one enveloped, strong enough at t0 = 0.2 that the coupling axis shows."""
+    return wl.Pulse(amp=[0.3, -0.2], omega=[1.1, 0.7], t_center=[0.25, 0.1], sigma=[0.5, 0.0], axis=axis)
+
+
+LASER_AXES = {
+    # the dipole coupling along y and z: the laser coordinate of the residual stencils, of the
+    # footprint sweeps, of the one-CTA and wide factorisations and of the Galerkin construction
+    "2d_y": lambda: dataclasses.replace(ANISOTROPIC["2d_4x4_K6"](), pulse=strong_pulse(1)),
+    "3d_y": lambda: dataclasses.replace(ANISOTROPIC["3d_2x2x2_K4"](), pulse=strong_pulse(1)),
+    "3d_z_wide": lambda: dataclasses.replace(ANISOTROPIC["3d_4x4x4_K4_wide"](), pulse=strong_pulse(2)),
+}
+
+
+@pytest.mark.parametrize("name", list(LASER_AXES))
+def test_laser_axis(name):
+    c, c_ref, N, N_ref = fixed_cycles(LASER_AXES[name](), 2)
     assert rel_l2(c, c_ref) < TOL64
     assert N == pytest.approx(N_ref, rel=1e-9)
