@@ -253,8 +253,7 @@ la_status la_fma_peaks(double* fp64_tflops, double* fp32_tflops, int* sm_count, 
    LA_NOALLOC_MAX_POINTS points are rejected with LA_EINVAL.  All calls share that array and
    overwrite it completely, so calls that overlap on the GPU race and must be serialised by the
    caller.  The first call in a CUDA context (normally a device's primary context) looks up the
-   array's address with that device current and keeps it for that context; make it before any
-   stream capture.  Under lazy module loading (the CUDA default) that first call may also load the
+   array's address with that device current and keeps it for that context.  Under lazy module loading (the CUDA default) that first call may also load the
    library's module, which takes device memory for its code and the array: a process that must not
    allocate at all sets CUDA_MODULE_LOADING=EAGER or makes one call early.
    Synchronises cuda_stream.  Errors: LA_EINVAL (message in la_last_error(NULL)), LA_ECUDA. */

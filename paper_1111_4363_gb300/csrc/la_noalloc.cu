@@ -15,9 +15,9 @@
 //     race on it and must be serialised by the caller;
 //   * set-up: the first call in a CUDA context (normally the primary context of a device) looks up
 //     the array's device address (cudaGetSymbolAddress) with that device current and keeps it for
-//     that context; make that first call before any stream capture.  The address is keyed by the
-//     context's unique id, so a context created later on the same device (after cudaDeviceReset,
-//     or a caller-created context) gets its own lookup instead of a stale address;
+//     that context.  The address is keyed by the context's unique id, so a context created later on
+//     the same device (after cudaDeviceReset, or a caller-created context) gets its own lookup
+//     instead of a stale address;
 //   * under lazy module loading (the CUDA default) the first call in a context may load this
 //     library's module, which takes device memory for its code and this array; a process that must
 //     not allocate at all sets CUDA_MODULE_LOADING=EAGER or makes one call early.
