@@ -31,11 +31,6 @@ template <typename CT> __device__ __forceinline__ void cfma_conj(CT& acc, const 
   acc.x = fma(a.x, b.x, acc.x); acc.x = fma(a.y, b.y, acc.x);
   acc.y = fma(a.x, b.y, acc.y); acc.y = fma(-a.y, b.x, acc.y);
 }
-template <typename CT> __device__ __forceinline__ CT shfl_xor_c(CT v, int m) {
-  v.x = __shfl_xor_sync(0xffffffffu, v.x, m);
-  v.y = __shfl_xor_sync(0xffffffffu, v.y, m);
-  return v;
-}
 
 constexpr int kFactorThreads = 256;
 constexpr int kSweepThreads = 128;
@@ -1310,10 +1305,6 @@ __device__ __forceinline__ void subvol_solve_wide(const CT* __restrict__ F, int 
   }
 }
 
-// Bytes of one subvolume factor record (packed lower-triangular 16 x 16 blocks).
-__host__ __device__ constexpr size_t factor_bytes(int npad, size_t csize) {
-  return (size_t)(npad / LA_BLK) * (npad / LA_BLK + 1) / 2 * 256 * csize;
-}
 // The 128-thread solve (every step's blocks loaded together, the next step's in flight) serves every
 // complex64 factor and the wide FP64 ones; shorter FP64 factors keep the two-warp solve, whose
 // two-level reductions issue fewer adds on the slow FP64 pipe.
