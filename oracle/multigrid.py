@@ -89,9 +89,6 @@ class Hierarchy:
         for _ in range(nu2):
             self.relax[l].sweep(x, g, hook)
 
-    def fine_sweeps_per_cycle(self) -> int:
-        return self.nu1 + self.nu2
-
 
 def solve_step(M, f, W, shape, K, sub, levels, nu1, nu2, coarse_sweeps, ncycles=None, tol=None,
                max_cycles=200, after_colour=None, c0=None, coarse_sub=None, coarse_nu=None):
