@@ -142,6 +142,21 @@ def measures(A, W, C):
     return float(np.real(r.conj() @ (W @ r))), complex(C.conj() @ (A @ C))
 
 
+def parent_transfers(nx, nt):
+    """(I, P) between a parent element and its two children, acting on space only (the time basis is
+    shared): I gives the children's coefficients of parent functions, P projects back (Sec. IV)."""
+    return np.kron(le.interpolation(nx - 1), np.eye(nt)), np.kron(le.projection(nx - 1), np.eye(nt))
+
+
+def coarse_correction(A2, C, nx, nt, solver="null"):
+    """C + I dc, where dc solves the projected problem (P A2 I) dc = P r on the parent element under
+    its own conditions, r = -A2 C (Eq. residual_rough; the correction interpolated back by
+    Eq. correction_fine)."""
+    I, P = parent_transfers(nx, nt)
+    r = -A2 @ C
+    return C + I @ constrained_solve(P @ A2 @ I, constraints(nx, nt, 1), P @ r, solver)
+
+
 def relax_method(method, nx, nt, kappa, nu, C, solver="null"):
     """One relaxation of the trial coefficients C by the given method."""
     A1 = element_operator(nx, nt, kappa, nu)
@@ -151,13 +166,9 @@ def relax_method(method, nx, nt, kappa, nu, C, solver="null"):
     if method == "two":
         return relax(A2, constraints(nx, nt, 2), C, solver)
     assert method == "transfer"
-    # coarse correction on the parent element (spatial transfers; the time basis is shared)
-    I = np.kron(le.interpolation(nx - 1), np.eye(nt))        # child coefficients of parent functions
-    P = np.kron(le.projection(nx - 1), np.eye(nt))
-    r = -A2 @ C
-    Ac = P @ A2 @ I
-    C = C + I @ constrained_solve(Ac, constraints(nx, nt, 1), P @ r, solver)
-    # then each child element on its own (delta = 0 on both of its ends)
+    # coarse correction on the parent element, then each child element on its own (delta = 0 on both
+    # of its ends)
+    C = coarse_correction(A2, C, nx, nt, solver)
     n = nx * nt
     B1 = constraints(nx, nt, 1)
     out = C.copy()

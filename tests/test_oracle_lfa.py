@@ -243,3 +243,26 @@ def test_plane_wave_overlaps_closed_form(nel):
             shift = -0.5 if e == 0 else 0.5
             ax = np.exp(1j * k * shift) * np.array([2 * 1j ** i * spherical_jn(i, k / 2) for i in range(nx)])
         assert np.allclose(got[e], np.outer(ax, bt), atol=1e-13)
+
+
+@pytest.mark.parametrize("kappa,nu", [(1.0, 0.0), (0.1, -1.0), (10.0, 1.0)])
+def test_transfer_coarse_step_solves_the_projected_problem(kappa, nu):
+    """Eqs. residual_rough and correction_fine on two elements: the coarse step's correction is
+    interpolated from the parent (delta = I d), d meets the parent's own conditions, and the projected
+    residual P (r - A delta) has no component in the directions those conditions leave free.  I and P
+    are the element transfers pinned against their definitions (children's expansions, L2 projection)."""
+    from scipy.linalg import null_space
+    nx, nt = 5, 4
+    A2 = np.kron(np.eye(2), lfa.element_operator(nx, nt, kappa, nu))
+    C = lfa.project(nx, nt, 2, lfa.plane_wave_overlaps(nx, nt, 2, 1.7, -0.9))
+    delta = lfa.coarse_correction(A2, C, nx, nt) - C
+    I = np.kron(le.interpolation(nx - 1), np.eye(nt))
+    P = np.kron(le.projection(nx - 1), np.eye(nt))
+    d = P @ delta
+    assert np.linalg.norm(delta - I @ d) < 1e-12 * np.linalg.norm(delta)
+    B1 = lfa.constraints(nx, nt, 1)
+    assert np.linalg.norm(B1 @ d) < 1e-12 * np.linalg.norm(d)
+    Z = null_space(B1)
+    rc = P @ (-A2 @ (C + delta))
+    assert np.linalg.norm(Z.T @ rc) < 1e-10 * np.linalg.norm(P @ (A2 @ C))
+    assert np.linalg.norm(delta) > 1e-3 * np.linalg.norm(C)

@@ -279,6 +279,20 @@ def element_children_swapped(mp):
     return [(pr.test_legendre_element_transfers, 3)]
 
 
+def projection_without_overlap_weights(mp):
+    # the unweighted left inverse (E^T E)^{-1} E^T of the interpolation instead of the L2 projection
+    # (it too gives P I = identity)
+    _wrap(mp, le, "projection", lambda orig: lambda nmax: np.linalg.pinv(le.interpolation(nmax)))
+    return [(pr.test_legendre_element_projection_is_the_l2_projection, 3)]
+
+
+def transfer_restricts_with_the_plain_transpose(mp):
+    # the residual taken to the parent element by I^T instead of the projection P
+    _wrap(mp, lfa, "parent_transfers", lambda orig: lambda nx, nt: (lambda IP: (IP[0], IP[0].T))(orig(nx, nt)))
+    return [(pl.test_transfer_coarse_step_solves_the_projected_problem, 1.0, 0.0),
+            (pl.test_maps_follow_sec_v,)]
+
+
 def lfa_derivative_on_test_function(mp):
     def make(orig):
         return lambda nx, nt: (lambda m: (m[0], m[1], m[2].T, m[3]))(orig(nx, nt))
@@ -306,7 +320,8 @@ MUTANTS = [
     laplacian_spacing_on_the_wrong_axis, stencil_row_spacing_on_the_wrong_axis,
     action_norm_without_conjugate, adjoint_solve_with_transpose, checkerboard_colouring, residual_once_per_sweep,
     local_solve_with_transpose, interpolation_from_far_neighbour, coarse_operator_quartered,
-    square_solve_with_transpose, element_children_swapped, lfa_derivative_on_test_function,
+    square_solve_with_transpose, element_children_swapped, projection_without_overlap_weights,
+    transfer_restricts_with_the_plain_transpose, lfa_derivative_on_test_function,
     lfa_kinetic_sign, lfa_residual_sign,
 ]
 

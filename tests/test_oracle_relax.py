@@ -306,3 +306,25 @@ def test_trial_weights_extrapolate_polynomials_exactly():
                 assert abs(pred - p(n)) < 1e-9 * max(1.0, abs(p(n)))
             else:
                 assert abs(pred - p(n)) > 1e-6
+
+
+@pytest.mark.parametrize("nmax", [1, 2, 3, 5])
+def test_legendre_element_projection_is_the_l2_projection(nmax):
+    """Sec. IV: P takes a function given on the two children to the parent coefficients of its L2-best
+    approximation, a_j = (2j + 1)/2 int_{-1}^{1} f P_j dx.  Computed here by quadrature of the piecewise
+    function itself (left child on [-1, 0] with local coordinate 2x + 1, right child on [0, 1] with
+    2x - 1): any other left inverse of the interpolation (P I = identity alone does not fix P) fails."""
+    from numpy.polynomial import legendre as L
+    rng = np.random.default_rng(10 + nmax)
+    cl, cr = rng.standard_normal(nmax + 1), rng.standard_normal(nmax + 1)
+    q, wq = L.leggauss(nmax + 4)
+    a = np.zeros(nmax + 1)
+    for c, lo in ((cl, -1.0), (cr, 0.0)):
+        x = lo + 0.5 * (q + 1.0)                      # Gauss nodes on the child's half of [-1, 1]
+        local = 2.0 * x - (2.0 * lo + 1.0)            # the child's own Legendre coordinate
+        f = L.legval(local, c)
+        for j in range(nmax + 1):
+            e = np.zeros(j + 1)
+            e[j] = 1.0
+            a[j] += 0.5 * np.sum(wq * f * L.legval(x, e)) * (2 * j + 1) / 2.0
+    np.testing.assert_allclose(le.projection(nmax) @ np.concatenate([cl, cr]), a, atol=1e-13)
