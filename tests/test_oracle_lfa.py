@@ -266,3 +266,46 @@ def test_transfer_coarse_step_solves_the_projected_problem(kappa, nu):
     rc = P @ (-A2 @ (C + delta))
     assert np.linalg.norm(Z.T @ rc) < 1e-10 * np.linalg.norm(P @ (A2 @ C))
     assert np.linalg.norm(delta) > 1e-3 * np.linalg.norm(C)
+
+
+@pytest.mark.parametrize("method", ["one", "two", "transfer"])
+def test_correction_vanishes_at_the_initial_time_and_the_volume_ends(method):
+    """Eqs. ic_correction, bc1_correction, bc2_correction and continuity, read off the correction as a
+    function: delta(x, t) of one relaxation is zero at the initial time (tau = -1) everywhere and at
+    both outer ends of the relaxation volume at all times, continuous across the inner boundary, and
+    not zero at the end of the step (tau = +1).  Evaluated from the Legendre expansions themselves,
+    not through the constraint rows."""
+    from numpy.polynomial import legendre as L
+    nx, nt = 5, 4
+    nel = 1 if method == "one" else 2
+    C = lfa.project(nx, nt, nel, lfa.plane_wave_overlaps(nx, nt, nel, -1.7, 2.2))
+    D = (lfa.relax_method(method, nx, nt, 1.0, 1.0, C) - C).reshape(nel, nx, nt)
+    s = np.linspace(-1.0, 1.0, 9)
+    scale = max(np.abs(L.legval2d(a, b, D[e])) for e in range(nel) for a in s for b in s)
+    for e in range(nel):
+        assert np.max(np.abs(L.legval2d(s, -np.ones_like(s), D[e]))) < 1e-12 * scale
+    assert np.max(np.abs(L.legval2d(-np.ones_like(s), s, D[0]))) < 1e-12 * scale
+    assert np.max(np.abs(L.legval2d(np.ones_like(s), s, D[nel - 1]))) < 1e-12 * scale
+    if nel == 2:
+        jump = L.legval2d(np.ones_like(s), s, D[0]) - L.legval2d(-np.ones_like(s), s, D[1])
+        assert np.max(np.abs(jump)) < 1e-12 * scale
+    assert max(np.max(np.abs(L.legval2d(s, np.ones_like(s), D[e]))) for e in range(nel)) > 1e-3 * scale
+
+
+@pytest.mark.parametrize("kappa,nu", [(1.0, 0.0), (0.3, -1.0)])
+def test_action_by_quadrature_of_the_trial_function(kappa, nu):
+    """S = C^H A C against the integral of conj(phi) (i d/dtau + kappa d^2/dy^2 - nu) phi over the
+    element for the trial phi(y, tau) = sum C[i, n] P_i(y) P_n(tau), by a Gauss rule (the
+    dimensionless rows of Eq. leastaction_dimensionless as an integral; the trial enters conjugated)."""
+    from numpy.polynomial import legendre as L
+    nx, nt = 5, 4
+    C = lfa.project(nx, nt, 1, lfa.plane_wave_overlaps(nx, nt, 1, 1.3, -0.7))
+    _, S = lfa.measures(lfa.element_operator(nx, nt, kappa, nu), lfa.weight(nx, nt, 1), C)
+    q, wq = L.leggauss(12)
+    Cm = C.reshape(nx, nt)
+    Y, T = np.meshgrid(q, q, indexing="ij")
+    phi = L.legval2d(Y, T, Cm)
+    phi_t = L.legval2d(Y, T, L.legder(Cm, axis=1))
+    phi_yy = L.legval2d(Y, T, L.legder(Cm, m=2, axis=0))
+    S_quad = np.sum(np.outer(wq, wq) * np.conj(phi) * (1j * phi_t + kappa * phi_yy - nu * phi))
+    assert abs(S - S_quad) < 1e-12 * max(1.0, abs(S_quad))

@@ -293,6 +293,31 @@ def transfer_restricts_with_the_plain_transpose(mp):
             (pl.test_maps_follow_sec_v,)]
 
 
+def lfa_initial_condition_at_the_step_end(mp):
+    # the correction held at tau = +1 (P_n(1) = 1) instead of the initial time tau = -1
+    def make(orig):
+        def constraints(nx, nt, nel, left=True, right=True, initial=True, continuity=True):
+            rest = orig(nx, nt, nel, left, right, False, continuity)
+            if not initial:
+                return rest
+            n = nx * nt
+            rows = np.zeros((nel * nx, nel * n))
+            for e in range(nel):
+                for i in range(nx):
+                    rows[e * nx + i, e * n + i * nt: e * n + (i + 1) * nt] = 1.0
+            return np.vstack([rows, rest.reshape(-1, nel * n)])
+        return constraints
+    _wrap(mp, lfa, "constraints", make)
+    return [(pl.test_correction_vanishes_at_the_initial_time_and_the_volume_ends, "one"),
+            (pl.test_relaxation_keeps_initial_and_boundary_values, "one")]
+
+
+def lfa_action_without_conjugate(mp):
+    # S = C^T A C instead of C^H A C
+    _wrap(mp, lfa, "measures", lambda orig: lambda A, W, C: (orig(A, W, C)[0], complex(C @ (A @ C))))
+    return [(pl.test_action_by_quadrature_of_the_trial_function, 1.0, 0.0)]
+
+
 def lfa_derivative_on_test_function(mp):
     def make(orig):
         return lambda nx, nt: (lambda m: (m[0], m[1], m[2].T, m[3]))(orig(nx, nt))
@@ -322,7 +347,7 @@ MUTANTS = [
     local_solve_with_transpose, interpolation_from_far_neighbour, coarse_operator_quartered,
     square_solve_with_transpose, element_children_swapped, projection_without_overlap_weights,
     transfer_restricts_with_the_plain_transpose, lfa_derivative_on_test_function,
-    lfa_kinetic_sign, lfa_residual_sign,
+    lfa_kinetic_sign, lfa_residual_sign, lfa_initial_condition_at_the_step_end, lfa_action_without_conjugate,
 ]
 
 
