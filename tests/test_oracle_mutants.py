@@ -148,6 +148,26 @@ def dual_weight_without_inverse(mp):
     return [(ps.test_dual_weight_is_test_basis_invariant,)]
 
 
+def _patch_weight(mp, name, build):
+    def make(orig):
+        def weight_matrix(prob, Ub, weight="dual"):
+            return build(prob, Ub) if weight == name else orig(prob, Ub, weight)
+        return weight_matrix
+    _wrap(mp, system, "weight_matrix", make)
+
+
+def literal_weight_overlap_inverted(mp):
+    # O (x) U with the grid overlap h^d divided instead of multiplied
+    _patch_weight(mp, "literal", lambda prob, Ub: (sp.kron(sp.identity(prob.npoints), Ub) / prob.vol).tocsr())
+    return [(ps.test_weights_are_l2_norms_of_residual_functions, "literal")]
+
+
+def dual_weight_overlap_inverted(mp):
+    # (O (x) U)^{-1} with h^d multiplied instead of divided (the basis invariance holds for any scale)
+    _patch_weight(mp, "dual", lambda prob, Ub: (prob.vol * sp.kron(sp.identity(prob.npoints), np.linalg.inv(Ub))).tocsr())
+    return [(ps.test_weights_are_l2_norms_of_residual_functions, "dual"), (ps.test_dual_weight_is_test_basis_invariant,)]
+
+
 def stencil_row_without_potential(mp):
     def make(orig):
         def hamiltonian_row(prob, q):
@@ -185,6 +205,12 @@ def adjoint_solve_with_transpose(mp):
     real = adjoint.spla
     mp.setattr(adjoint, "spla", types.SimpleNamespace(splu=lambda A: real.splu(A.conj().tocsc())))
     return [(pa.test_amplitude_gradient_matches_finite_differences, 1), (pa.test_initial_state_gradient_matches_finite_differences,)]
+
+
+def dipole_without_overlap(mp):
+    # the objective sum_p x_p |psi_p|^2 without h^d, while its derivative keeps it
+    mp.setattr(system, "dipole", lambda prob, psi: float(np.sum(prob.xlaser * np.abs(psi) ** 2)))
+    return [(pa.test_initial_state_gradient_matches_finite_differences,)]
 
 
 # ------------------------------------------------------------------------------ relaxation (Sec. II)
@@ -341,9 +367,10 @@ MUTANTS = [
     b_adds_p0, qb_derivative_on_test_function, ub_without_jacobian, envelope_two_sigma_squared,
     carrier_in_time_from_centre, step_time_centred_at_t0, component_field_keeps_its_amplitude,
     end_value_without_p0_part, kinetic_without_half, time_derivative_sign, dipole_coupling_sign,
-    initial_state_field_term_dropped, dual_weight_without_inverse, stencil_row_without_potential,
+    initial_state_field_term_dropped, dual_weight_without_inverse, literal_weight_overlap_inverted,
+    dual_weight_overlap_inverted, stencil_row_without_potential,
     laplacian_spacing_on_the_wrong_axis, stencil_row_spacing_on_the_wrong_axis,
-    action_norm_without_conjugate, adjoint_solve_with_transpose, checkerboard_colouring, residual_once_per_sweep,
+    action_norm_without_conjugate, adjoint_solve_with_transpose, dipole_without_overlap, checkerboard_colouring, residual_once_per_sweep,
     local_solve_with_transpose, interpolation_from_far_neighbour, coarse_operator_quartered,
     square_solve_with_transpose, element_children_swapped, projection_without_overlap_weights,
     transfer_restricts_with_the_plain_transpose, lfa_derivative_on_test_function,

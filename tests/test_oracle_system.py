@@ -269,3 +269,29 @@ def test_stencil_rows_on_an_anisotropic_grid():
         row = np.zeros(prob.npoints)
         np.add.at(row, cols, vals)
         np.testing.assert_allclose(row, Hs[q], rtol=0, atol=1e-12)
+
+
+@pytest.mark.parametrize("weight", ["literal", "dual"])
+def test_weights_are_l2_norms_of_residual_functions(weight):
+    """Eq. residnorm read as a squared L2 norm over the step's space-time slab, by a Gauss rule in time
+    with the b_n from scipy's Legendre polynomials and the grid functions' overlap h^d.  "literal":
+    N = r O U r* is the norm of the function whose expansion coefficients are r,
+    h^d sum_p int |sum_n r_pn b_n(t)|^2 dt.  "dual": the norm of the function g in the trial space
+    whose projections onto the test functions are r (its coefficients solve the overlap system
+    h^d U g_p = r_p)."""
+    from scipy.special import eval_legendre
+    w = wl.softcore_2d(n=6, levels=1)
+    prob = system.Problem.from_workload(w)
+    psi0 = wl.initial_state(w).ravel()
+    M, f, W = system.assemble(prob, 0.2, psi0, weight)
+    r = system.residual(M, f, wl.random_state(M.shape[1], 8)).reshape(-1, prob.K)
+    q, wq = np.polynomial.legendre.leggauss(prob.K + 4)
+    b = np.array([eval_legendre(n, q) - (-1.0) ** n for n in range(1, prob.K + 1)])   # b_n(tau_q)
+    jac = 0.5 * prob.dt                                                                # dt = (dt/2) dtau
+    if weight == "literal":
+        coef = r
+    else:
+        gram = prob.vol * jac * (b * wq) @ b.T                                         # h^d int b_m b_n dt
+        coef = np.linalg.solve(gram, r.T).T
+    N_quad = prob.vol * jac * np.sum(wq * np.abs(coef @ b) ** 2)
+    assert system.action_norm(r.ravel(), W) == pytest.approx(N_quad, rel=1e-12)
