@@ -269,6 +269,18 @@ def interpolation_from_far_neighbour(mp):
     return [(pr.test_fd_interpolation_reproduces_linear_functions,)]
 
 
+def interpolation_axes_reversed(mp):
+    # the 1D factors of the tensor product taken in x-first order while the grid is stored z-first
+    def interpolation(coarse_shape, K):
+        I = None
+        for n in reversed(coarse_shape):
+            m = multigrid.interpolation_1d(n)
+            I = m if I is None else sp.kron(I, m, format="csr")
+        return sp.kron(I, sp.identity(K), format="csr")
+    mp.setattr(multigrid, "interpolation", interpolation)
+    return [(pr.test_fd_interpolation_reproduces_linear_functions_on_a_box,)]
+
+
 def coarse_operator_quartered(mp):
     # the Galerkin operator I^T G I divided by 4, the factor a rediscretisation on a grid of twice the
     # spacing would carry for the kinetic term: every coarse correction comes out four times too large
@@ -371,7 +383,8 @@ MUTANTS = [
     dual_weight_overlap_inverted, stencil_row_without_potential,
     laplacian_spacing_on_the_wrong_axis, stencil_row_spacing_on_the_wrong_axis,
     action_norm_without_conjugate, adjoint_solve_with_transpose, dipole_without_overlap, checkerboard_colouring, residual_once_per_sweep,
-    local_solve_with_transpose, interpolation_from_far_neighbour, coarse_operator_quartered,
+    local_solve_with_transpose, interpolation_from_far_neighbour, interpolation_axes_reversed,
+    coarse_operator_quartered,
     square_solve_with_transpose, element_children_swapped, projection_without_overlap_weights,
     transfer_restricts_with_the_plain_transpose, lfa_derivative_on_test_function,
     lfa_kinetic_sign, lfa_residual_sign, lfa_initial_condition_at_the_step_end, lfa_action_without_conjugate,

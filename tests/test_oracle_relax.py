@@ -328,3 +328,23 @@ def test_legendre_element_projection_is_the_l2_projection(nmax):
             e[j] = 1.0
             a[j] += 0.5 * np.sum(wq * f * L.legval(x, e)) * (2 * j + 1) / 2.0
     np.testing.assert_allclose(le.projection(nmax) @ np.concatenate([cl, cr]), a, atol=1e-13)
+
+
+def test_fd_interpolation_reproduces_linear_functions_on_a_box():
+    """The tensor-product interpolation on a 3D grid whose axes all differ (numpy order z, y, x):
+    a linear function of the coarse cell centres comes out as the same linear function at the fine
+    points away from the walls, for each of the K time functions separately.  Pins which 1D factor
+    acts on which axis (a square grid cannot tell)."""
+    coarse = (3, 4, 5)
+    K = 2
+    Hc = (0.8, 0.6, 0.5)                                  # coarse spacings; fine ones are half
+    I = multigrid.interpolation(coarse, K)
+    Xc = np.meshgrid(*[wl.axis_coordinates(n, h) for n, h in zip(coarse, Hc)], indexing="ij")
+    Xf = np.meshgrid(*[wl.axis_coordinates(2 * n, h / 2) for n, h in zip(coarse, Hc)], indexing="ij")
+    lin = lambda X: 0.3 + 1.7 * X[0] - 0.9 * X[1] + 0.4 * X[2]
+    u = np.stack([lin(Xc).ravel(), -2.0 * lin(Xc).ravel()], axis=1).ravel()    # point-major, K = 2
+    v = (I @ u).reshape(tuple(2 * n for n in coarse) + (K,))
+    want = lin(Xf)
+    inner = tuple(slice(1, 2 * n - 1) for n in coarse)
+    np.testing.assert_allclose(v[inner + (0,)], want[inner], atol=1e-13)
+    np.testing.assert_allclose(v[inner + (1,)], -2.0 * want[inner], atol=1e-13)
