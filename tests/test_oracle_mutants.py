@@ -102,6 +102,14 @@ def component_field_keeps_its_amplitude(mp):
     return [(pt.test_pulse_field_by_value,), (pa.test_amplitude_gradient_matches_finite_differences, 1)]
 
 
+def field_quadrature_too_coarse(mp):
+    # K + 1 Gauss nodes for the field matrices: exact for polynomials only, not for the pulses
+    def make(orig):
+        return lambda K, dt, t0, field, nquad=None: orig(K, dt, t0, field, nquad if nquad else K + 1)
+    _wrap(mp, tb, "field_matrices", make)
+    return [(pt.test_quadrature_converged_for_pulses,)]
+
+
 def end_value_without_p0_part(mp):
     # phi(t0 + dt) = psi0 + sum_n c_n, forgetting that b_n(+1) = 1 - (-1)^n
     mp.setattr(tb, "end_values", lambda K: np.ones(K))
@@ -112,6 +120,18 @@ def end_value_without_p0_part(mp):
 def kinetic_without_half(mp):
     _wrap(mp, system, "kinetic", lambda orig: lambda prob: (2.0 * orig(prob)).tocsr())
     return [(ps.test_kkt_with_multipliers, 8, 2, 0.0), (ps.test_eigen_expansion_and_norm_drift,)]
+
+
+def laplacian_with_neumann_walls(mp):
+    # the end rows of the second difference with -1/h^2 (a reflecting wall) instead of Dirichlet's -2/h^2
+    def make(orig):
+        def second_difference_1d(n, h):
+            A = orig(n, h).tolil()
+            A[0, 0] = A[n - 1, n - 1] = -1.0 / (h * h)
+            return A.tocsr()
+        return second_difference_1d
+    _wrap(mp, system, "second_difference_1d", make)
+    return [(ps.test_laplacian_eigenvalues_on_an_anisotropic_grid,), (ps.test_scalar_K1_closed_form, 0.5)]
 
 
 def _patch_time_matrices(mp, change):
@@ -281,6 +301,29 @@ def interpolation_axes_reversed(mp):
     return [(pr.test_fd_interpolation_reproduces_linear_functions_on_a_box,)]
 
 
+def coarse_residual_before_presmoothing(mp):
+    # the V-cycle restricts the residual taken before its pre-smoothing sweeps instead of after them
+    def make(orig):
+        def vcycle(self, l, x, g, after_colour=None):
+            if self.L == 1 or l == self.L - 1:
+                return orig(self, l, x, g, after_colour)
+            hook = after_colour if l == 0 else None
+            nu1, nu2 = (self.nu1, self.nu2) if l == 0 else self.coarse_nu
+            s = g - self.G[l] @ x
+            for _ in range(nu1):
+                self.relax[l].sweep(x, g, hook)
+            xc = np.zeros(self.I[l].shape[1], dtype=x.dtype)
+            self.vcycle(l + 1, xc, self.I[l].T @ s)
+            x += self.I[l] @ xc
+            if after_colour is not None and l == 0:
+                after_colour(-1)
+            for _ in range(nu2):
+                self.relax[l].sweep(x, g, hook)
+        return vcycle
+    _wrap(mp, multigrid.Hierarchy, "vcycle", make)
+    return [(pr.test_action_never_increases, "dual")]
+
+
 def coarse_operator_quartered(mp):
     # the Galerkin operator I^T G I divided by 4, the factor a rediscretisation on a grid of twice the
     # spacing would carry for the kinetic term: every coarse correction comes out four times too large
@@ -368,6 +411,22 @@ def lfa_kinetic_sign(mp):
     return [(pl.test_dimensionless_rows_and_their_scaling, 0.3, 0.05, -1.7)]
 
 
+def lfa_potential_sign(mp):
+    # +nu O U in the element rows (the potential term with the wrong sign)
+    _wrap(mp, lfa, "element_operator", lambda orig: lambda nx, nt, kappa, nu: orig(nx, nt, kappa, -nu))
+    return [(pl.test_dimensionless_rows_and_their_scaling, 0.3, 0.05, -1.7),
+            (pl.test_slow_convergence_only_near_the_dispersion_curve,)]
+
+
+def lfa_weight_inverted(mp):
+    # the element weight (O x U)^{-1} instead of the printed O x U
+    def weight(nx, nt, nel):
+        O, U, _, _ = lfa.element_matrices(nx, nt)
+        return np.kron(np.eye(nel), np.kron(np.linalg.inv(O), np.linalg.inv(U)))
+    mp.setattr(lfa, "weight", weight)
+    return [(pl.test_continuous_projection,)]
+
+
 def lfa_residual_sign(mp):
     # relaxing with r = +A C instead of the residual -A C of Eq. actionresidual
     solve = lfa.constrained_solve
@@ -376,18 +435,25 @@ def lfa_residual_sign(mp):
 
 
 MUTANTS = [
+    # time basis
     b_adds_p0, qb_derivative_on_test_function, ub_without_jacobian, envelope_two_sigma_squared,
     carrier_in_time_from_centre, step_time_centred_at_t0, component_field_keeps_its_amplitude,
-    end_value_without_p0_part, kinetic_without_half, time_derivative_sign, dipole_coupling_sign,
+    field_quadrature_too_coarse, end_value_without_p0_part,
+    # the step's system and its adjoint
+    kinetic_without_half, laplacian_with_neumann_walls, time_derivative_sign, dipole_coupling_sign,
     initial_state_field_term_dropped, dual_weight_without_inverse, literal_weight_overlap_inverted,
-    dual_weight_overlap_inverted, stencil_row_without_potential,
-    laplacian_spacing_on_the_wrong_axis, stencil_row_spacing_on_the_wrong_axis,
-    action_norm_without_conjugate, adjoint_solve_with_transpose, dipole_without_overlap, checkerboard_colouring, residual_once_per_sweep,
-    local_solve_with_transpose, interpolation_from_far_neighbour, interpolation_axes_reversed,
+    dual_weight_overlap_inverted, stencil_row_without_potential, laplacian_spacing_on_the_wrong_axis,
+    stencil_row_spacing_on_the_wrong_axis, action_norm_without_conjugate, adjoint_solve_with_transpose,
+    dipole_without_overlap,
+    # relaxation and multigrid
+    checkerboard_colouring, residual_once_per_sweep, local_solve_with_transpose,
+    interpolation_from_far_neighbour, interpolation_axes_reversed, coarse_residual_before_presmoothing,
     coarse_operator_quartered,
+    # square form, Legendre elements, plane-wave maps
     square_solve_with_transpose, element_children_swapped, projection_without_overlap_weights,
-    transfer_restricts_with_the_plain_transpose, lfa_derivative_on_test_function,
-    lfa_kinetic_sign, lfa_residual_sign, lfa_initial_condition_at_the_step_end, lfa_action_without_conjugate,
+    transfer_restricts_with_the_plain_transpose, lfa_derivative_on_test_function, lfa_kinetic_sign,
+    lfa_potential_sign, lfa_weight_inverted, lfa_residual_sign, lfa_initial_condition_at_the_step_end,
+    lfa_action_without_conjugate,
 ]
 
 
