@@ -39,7 +39,8 @@ def band_blocks(dim, sub_xyz, K, nblk):
 def cases():
     w3 = dataclasses.replace(wl.hydrogen_3d(n=8, nsteps=4, ncomp=4, sub=4), n=(10, 8, 8), levels=1)
     w2 = dataclasses.replace(wl.softcore_2d(n=16, levels=1), nt=4, sub=(8, 8, 1), n=(20, 16, 1))
-    return [("3d_4x4x4_K4", w3), ("2d_8x8_K4", w2)]
+    w1 = dataclasses.replace(wl.harmonic_1d(), nt=8, sub=(32, 1, 1), n=(70, 1, 1), levels=1)
+    return [("3d_4x4x4_K4", w3), ("2d_8x8_K4", w2), ("1d_32_K8", w1)]
 
 
 @pytest.mark.parametrize("name,w", cases(), ids=[c[0] for c in cases()])
@@ -81,3 +82,5 @@ def test_band_of_the_production_subvolumes():
     assert band_blocks(2, (8, 8, 1), 4, 16) == 4
     # 2D 4 x 4 x K = 4 (four blocks): d_max = 8, band 2
     assert band_blocks(2, (4, 4, 1), 4, 4) == 2
+    # 1D 32 points x K = 8: d_max = 2, two points per block, band 1
+    assert band_blocks(1, (32, 1, 1), 8, 16) == 1
