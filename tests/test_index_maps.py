@@ -15,7 +15,7 @@ import subprocess
 
 import pytest
 
-from test_oracle_band import band_blocks
+from tests.test_oracle_band import band_blocks
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 HEADER = os.path.join(HERE, "..", "paper_1111_4363_gb300", "csrc", "la_internal.cuh")

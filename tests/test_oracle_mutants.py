@@ -18,15 +18,15 @@ import pytest
 import scipy.linalg as sla
 import scipy.sparse as sp
 
-import test_oracle_adjoint as pa
-import test_oracle_lfa as pl
-import test_oracle_relax as pr
-import test_oracle_square as pq
-import test_oracle_system as ps
-import test_oracle_timebasis as pt
 from oracle import adjoint, lfa, multigrid, relax, system
 from oracle import legendre_elements as le
 from oracle import timebasis as tb
+from tests import test_oracle_adjoint as pa
+from tests import test_oracle_lfa as pl
+from tests import test_oracle_relax as pr
+from tests import test_oracle_square as pq
+from tests import test_oracle_system as ps
+from tests import test_oracle_timebasis as pt
 
 
 def _wrap(mp, module, name, make):
