@@ -744,13 +744,8 @@ __device__ __forceinline__ typename C2<R>::T wide_entry(const WideRow<R>& w, int
   return mkc<CT>(re, im);
 }
 
-// Block column J, rows 16 J + row of this thread (columns c0 .. c0 + CPT - 1): assemble, subtract
-// sum_{k < 16 J} L[r][k] conj(L[16 J + c][k]) (row r of the finished blocks (I, 0..J-1) from global
-// memory, the block row J transposed in shared memory), and write the result to sPan.
-// Rows 16 J' + q of block column J' assembled and updated with the finished block columns Kb < kb_end:
-// acc[c] = G[r][16 J' + c0 + c] - sum_{k < 16 kb_end} L[r][k] conj(L[16 J' + c0 + c][k]), the finished rows
-// read back from the factor store, the block row J' transposed in sRow.
-// acc[c] = G[r][16 Jc + c0 + c], c < CPT (zero for a block beyond the band).
+// Row r of block column Jc, columns c0 .. c0 + CPT - 1, assembled: acc[c] = G[r][16 Jc + c0 + c]
+// (zero for a block beyond the band).  wide_partial_update then subtracts the finished block columns.
 template <typename R, int CPT>
 __device__ __forceinline__ void wide_assemble(int Jc, int band, int r, int c0, int n, const FastDiv& dK, int K,
                                               const WideTables<R>& T, typename C2<R>::T* acc) {
@@ -765,7 +760,8 @@ __device__ __forceinline__ void wide_assemble(int Jc, int band, int r, int c0, i
   for (int q = 0; q < CPT; ++q) acc[q] = wide_entry<R>(w, LA_BLK * Jc + c0 + q, n, dK, K, T);
 }
 
-// acc (the assembled entries) -= sum over the finished block columns Kb < kb_end inside the band.
+// acc[c] -= sum_{k < 16 kb_end} L[r][k] conj(L[16 Jc + c0 + c][k]) over the finished block columns inside
+// the band: row r's blocks read back from the factor store, block row Jc transposed in sRow.
 template <typename R, int CPT>
 __device__ __forceinline__ void wide_partial_update(int Jc, int kb_end, int band, int r, int c0,
                                                     const typename C2<R>::T* __restrict__ F,
