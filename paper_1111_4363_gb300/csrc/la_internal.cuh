@@ -16,6 +16,11 @@
 #include <stdint.h>
 #include <stddef.h>
 
+#include <cmath>
+#include <cstring>
+#include <utility>
+#include <vector>
+
 #define LA_KMAX 8          // largest K (free time functions per point)
 #define LA_NPAIR 9         // (k, k') pairs of the Kronecker normal operator
 #define LA_BLK 16          // block size of the subvolume factor layout
@@ -56,6 +61,90 @@ __host__ __device__ inline int theta_phase(int kk) {  // 0: real +1, 1: +i, 2: -
   if (k == 0 && kp != 0) return 1;
   if (kp == 0 && k != 0) return 2;
   return 0;
+}
+
+// ------------------------------------------------------------------ time-basis constants (host)
+// Legendre P_0..P_n at y by the three-term recurrence.
+__host__ inline void legendre_all(int n, double y, double* P) {
+  P[0] = 1.0;
+  if (n >= 1) P[1] = y;
+  for (int k = 2; k <= n; ++k) P[k] = ((2.0 * k - 1.0) * y * P[k - 1] - (k - 1.0) * P[k - 2]) / k;
+}
+// Gauss-Legendre nodes and weights on [-1, 1] by Newton iteration on P_q.
+__host__ inline void gauss_legendre(int q, double* x, double* w) {
+  std::vector<double> P(q + 1);
+  for (int i = 0; i < q; ++i) {
+    double y = std::cos(M_PI * (i + 0.75) / (q + 0.5));
+    for (int it = 0; it < 100; ++it) {
+      legendre_all(q, y, P.data());
+      double dp = q * (y * P[q] - P[q - 1]) / (y * y - 1.0);
+      double dy = P[q] / dp;
+      y -= dy;
+      if (std::fabs(dy) < 1e-16) break;
+    }
+    legendre_all(q, y, P.data());
+    double dp = q * (y * P[q] - P[q - 1]) / (y * y - 1.0);
+    x[i] = y;
+    w[i] = 2.0 / ((1.0 - y * y) * dp * dp);
+  }
+}
+// Inverse of a small n x n matrix (n <= LA_KMAX) by Gauss-Jordan elimination with partial pivoting.
+__host__ inline bool invert_small(int n, const double* A, double* Ainv) {
+  double M[LA_KMAX][2 * LA_KMAX];
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < 2 * n; ++j) M[i][j] = j < n ? A[i * n + j] : (j - n == i ? 1.0 : 0.0);
+  for (int col = 0; col < n; ++col) {
+    int piv = col;
+    for (int r = col + 1; r < n; ++r)
+      if (std::fabs(M[r][col]) > std::fabs(M[piv][col])) piv = r;
+    if (std::fabs(M[piv][col]) < 1e-300) return false;
+    for (int j = 0; j < 2 * n; ++j) std::swap(M[col][j], M[piv][j]);
+    double d = M[col][col];
+    for (int j = 0; j < 2 * n; ++j) M[col][j] /= d;
+    for (int r = 0; r < n; ++r) {
+      if (r == col) continue;
+      double f = M[r][col];
+      for (int j = 0; j < 2 * n; ++j) M[r][j] -= f * M[col][j];
+    }
+  }
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j) Ainv[i * n + j] = M[i][n + j];
+  return true;
+}
+// The static part of TimeMats for K time functions, step dt and residual-norm weight (0 = Ub^{-1},
+// 1 = Ub, 2 = identity), from the closed forms of Sec. IV (orthogonality 2 delta/(2n+1), Q_nm = 2 for
+// n > m with n - m odd, P_n(+-1) = (+-1)^n) in the basis b_n = P_n - (-1)^n P_0, n = 1..K, and the
+// K + 8-node Gauss rule the per-step field matrices use.  False when Ub cannot be inverted.
+__host__ inline bool fill_time_constants(int K, double dt, int weight, TimeMats& t) {
+  memset(&t, 0, sizeof t);
+  t.K = K;
+  t.dt = dt;
+  for (int m = 1; m <= K; ++m) {
+    const double sm = (m % 2) ? -1.0 : 1.0;
+    t.Ub0[m - 1] = -sm * dt;
+    t.endv[m - 1] = 1.0 - sm;
+    for (int n = 1; n <= K; ++n) {
+      const double sn = (n % 2) ? -1.0 : 1.0;
+      t.Ub[(m - 1) * K + (n - 1)] = dt * ((m == n ? 1.0 / (2 * m + 1) : 0.0) + sm * sn);
+      const double q = (n > m && ((n - m) % 2 == 1)) ? 2.0 : 0.0;
+      t.Qb[(m - 1) * K + (n - 1)] = q - sm * (1.0 - sn);
+    }
+  }
+  if (weight == 0) {
+    if (!invert_small(K, t.Ub, t.Wt)) return false;
+  } else if (weight == 1) {
+    memcpy(t.Wt, t.Ub, sizeof(double) * K * K);
+  } else {
+    for (int i = 0; i < K; ++i) t.Wt[i * K + i] = 1.0;
+  }
+  t.nq = K + 8;
+  gauss_legendre(t.nq, t.tau, t.wq);
+  std::vector<double> P(K + 1);
+  for (int q = 0; q < t.nq; ++q) {
+    legendre_all(K, t.tau[q], P.data());
+    for (int m = 1; m <= K; ++m) t.bq[q * LA_KMAX + (m - 1)] = P[m] - ((m % 2) ? -1.0 : 1.0);
+  }
+  return true;
 }
 
 // Geometry of one multigrid level.
