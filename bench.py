@@ -201,7 +201,7 @@ def hbm_peak():
     try:
         with open(path) as fh:
             return float(json.load(fh)["hbm_gbs"]), "of measured (MEASURED_PEAKS.json hbm_gbs)"
-    except (OSError, KeyError, ValueError):
+    except (OSError, KeyError, TypeError, ValueError):
         return 6800.0, "of fallback (6.8 TB/s)"
 
 
