@@ -200,6 +200,18 @@ def stencil_row_without_potential(mp):
     return [(ps.test_pointwise_residual_matches_the_assembled_system, "2d")]
 
 
+def problem_spacings_in_workload_order(mp):
+    # Problem.from_workload keeping the workload's x-first spacings on the slowest-first grid
+    def make(orig):
+        def from_workload(w):
+            prob = orig(w)
+            prob.h = tuple(reversed(prob.h))
+            return prob
+        return staticmethod(from_workload)
+    mp.setattr(system.Problem, "from_workload", make(system.Problem.from_workload))
+    return [(ps.test_problem_from_an_anisotropic_workload_pairs_extents_with_spacings,)]
+
+
 def laplacian_spacing_on_the_wrong_axis(mp):
     # each axis's second difference divided by another axis's h^2 (the spacings taken in x-first order)
     _wrap(mp, system, "laplacian", lambda orig: lambda shape, h: orig(shape, tuple(reversed(h))))
@@ -442,7 +454,8 @@ MUTANTS = [
     # the step's system and its adjoint
     kinetic_without_half, laplacian_with_neumann_walls, time_derivative_sign, dipole_coupling_sign,
     initial_state_field_term_dropped, dual_weight_without_inverse, literal_weight_overlap_inverted,
-    dual_weight_overlap_inverted, stencil_row_without_potential, laplacian_spacing_on_the_wrong_axis,
+    dual_weight_overlap_inverted, stencil_row_without_potential, problem_spacings_in_workload_order,
+    laplacian_spacing_on_the_wrong_axis,
     stencil_row_spacing_on_the_wrong_axis, action_norm_without_conjugate, adjoint_solve_with_transpose,
     dipole_without_overlap,
     # relaxation and multigrid

@@ -295,3 +295,21 @@ def test_weights_are_l2_norms_of_residual_functions(weight):
         coef = np.linalg.solve(gram, r.T).T
     N_quad = prob.vol * jac * np.sum(wq * np.abs(coef @ b) ** 2)
     assert system.action_norm(r.ravel(), W) == pytest.approx(N_quad, rel=1e-12)
+
+
+def test_problem_from_an_anisotropic_workload_pairs_extents_with_spacings():
+    """Problem.from_workload stores the grid slowest axis first; each axis keeps its own extent and
+    spacing: the Laplacian's spectrum is the sum over the workload's axes a of
+    -(4 / h_a^2) sin^2(j pi / (2 (n_a + 1))), and the laser coordinate varies along its axis only."""
+    import dataclasses
+    w = dataclasses.replace(wl.hydrogen_3d(n=8, nsteps=4, ncomp=2, sub=2), n=(7, 5, 4), h=(0.3, 0.7, 0.45))
+    w = dataclasses.replace(w, pulse=dataclasses.replace(w.pulse, axis=1))
+    prob = system.Problem.from_workload(w)
+    got = np.sort(np.linalg.eigvalsh(system.laplacian(prob.shape, prob.h).toarray()))
+    per_axis = [-4.0 / w.h[a] ** 2 * np.sin(np.arange(1, w.n[a] + 1) * np.pi / (2 * (w.n[a] + 1))) ** 2
+                for a in range(3)]
+    want = np.sort((per_axis[0][:, None, None] + per_axis[1][None, :, None] + per_axis[2][None, None, :]).ravel())
+    np.testing.assert_allclose(got, want, rtol=0, atol=1e-12 * np.max(np.abs(want)))
+    X = prob.xlaser.reshape(prob.shape)                     # numpy order (z, y, x): y is numpy axis 1
+    np.testing.assert_array_equal(X, np.broadcast_to(X[:1, :, :1], X.shape))
+    np.testing.assert_allclose(X[0, :, 0], (np.arange(w.n[1]) - (w.n[1] - 1) / 2) * w.h[1], atol=1e-15)
