@@ -112,3 +112,36 @@ def test_noalloc_rejects_oversized_grids_and_host_pointers_without_the_gpu():
         B.action_noalloc(cfg, np.zeros(w.npoints), w.pulse, np.zeros(w.npoints, np.complex128), 0.0,
                          np.zeros(w.nunknowns, np.complex128))
     assert e.value.status == B.LA_EINVAL
+
+
+def test_null_arguments_are_rejected_without_touching_the_gpu():
+    """Every entry point checks its context and required pointers before any CUDA call: a null one
+    returns LA_EINVAL (here, on a machine without a GPU), and la_last_error still answers."""
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1111_4363_gb300 import binding as B
+    L = B.lib()
+    d = ctypes.c_double(0.0)
+    calls = {
+        "la_init": lambda: L.la_init(None, None, None),
+        "la_set_hamiltonian": lambda: L.la_set_hamiltonian(None, None, None),
+        "la_step": lambda: L.la_step(None, None, 1, d, None),
+        "la_action": lambda: L.la_action(None, None, None),
+        "la_solve_step": lambda: L.la_solve_step(None, None, d, 1, None, None),
+        "la_residual": lambda: L.la_residual(None, None, d, None, None, None),
+        "la_relax_colour": lambda: L.la_relax_colour(None, None, d, 0, None),
+        "la_time_matrices": lambda: L.la_time_matrices(None, d, None),
+        "la_backward": lambda: L.la_backward(None, None, None, None),
+        "la_step_batch": lambda: L.la_step_batch(None, 1, None, 1, None, None),
+        "la_profile_enable": lambda: L.la_profile_enable(None, 1),
+        "la_profile_read": lambda: L.la_profile_read(None, None),
+        "la_action_noalloc": lambda: L.la_action_noalloc(None, None, None, None, d, None, None, None),
+        "la_lfa_maps": lambda: L.la_lfa_maps(None, 1, None, 1, None, 1, None, None),
+        "la_wait_selftest": lambda: L.la_wait_selftest(0, None, None),
+        "la_fma_peaks": lambda: L.la_fma_peaks(None, None, None, None),
+        "la_finalize": lambda: L.la_finalize(None),
+    }
+    assert set(calls) == set(B.EXPORTS) - {"la_last_error", "la_version"}
+    for name, call in calls.items():
+        assert call() == B.LA_EINVAL, name
+    assert L.la_last_error(None)
